@@ -1,0 +1,152 @@
+"""ctypes wrapper around ``oracle.c`` (test infrastructure only; see package doc)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+BEAMS = {"gauss": 0, "airy": 1, "uniform": 2}
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so with gcc + OpenMP (no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Problem(C.Structure):
+    _fields_ = [("n_ant", C.c_int), ("ant_enu", C.POINTER(C.c_double)),
+                ("n_bl", C.c_int), ("pairs", C.POINTER(C.c_int)),
+                ("n_src", C.c_long), ("ra", C.POINTER(C.c_double)), ("dec", C.POINTER(C.c_double)),
+                ("n_stokes", C.c_int), ("flux", C.POINTER(C.c_double)),
+                ("n_freq", C.c_int), ("freq_hz", C.POINTER(C.c_double)),
+                ("n_time", C.c_int), ("lst_rad", C.POINTER(C.c_double)),
+                ("latitude_rad", C.c_double), ("beam_kind", C.c_int),
+                ("beam_param", C.c_double * 3), ("polarized", C.c_int)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            lib.oracle_vis.argtypes = [C.POINTER(_Problem), C.POINTER(C.c_double), C.c_int, C.c_int]
+            lib.oracle_vis.restype = C.c_int
+            lib.oracle_enu.argtypes = [C.c_double] * 4 + [C.POINTER(C.c_double)]
+            lib.oracle_enu.restype = None
+            lib.oracle_voltage.argtypes = [C.c_int, C.POINTER(C.c_double), C.c_double, C.c_double]
+            lib.oracle_voltage.restype = C.c_double
+            lib.oracle_strength.argtypes = [C.c_int, C.POINTER(C.c_double), C.c_int,
+                                            C.POINTER(C.c_double), C.c_double,
+                                            C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            lib.oracle_strength.restype = None
+            lib.oracle_max_threads.restype = C.c_int
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double if a.dtype == np.float64 else C.c_int))
+
+
+@dataclass
+class OracleProblem:
+    ant_enu: np.ndarray
+    pairs: np.ndarray
+    ra: np.ndarray
+    dec: np.ndarray
+    flux: np.ndarray            # [n_stokes][n_src][n_freq]
+    freqs_hz: np.ndarray
+    lsts_rad: np.ndarray
+    latitude_rad: float
+    beam: str = "gauss"
+    beam_param: tuple = ()
+    polarized: bool = False
+
+    @classmethod
+    def from_workload(cls, prob, pairs=None, freq_idx=None, time_idx=None, src_idx=None):
+        """Build from a workloads.Problem, optionally restricted to subsets."""
+        sky = prob.sky
+        flux = sky.flux
+        freqs = prob.freqs_hz
+        lsts = prob.lsts_rad
+        ra, dec = sky.ra, sky.dec
+        if src_idx is not None:
+            ra, dec, flux = ra[src_idx], dec[src_idx], flux[:, src_idx]
+        if freq_idx is not None:
+            freqs = freqs[freq_idx]
+            flux = flux[:, :, freq_idx]
+        if time_idx is not None:
+            lsts = lsts[time_idx]
+        return cls(prob.ant_enu, prob.pairs if pairs is None else pairs, ra, dec, flux, freqs,
+                   lsts, prob.latitude_rad, prob.beam, tuple(prob.beam_param), prob.polarized)
+
+
+def oracle_vis(p: OracleProblem, mode: str = "factored", n_threads: int = 0) -> np.ndarray:
+    """Complex128 visibilities [n_freq][n_time][n_bl][n_pol] by FP64 direct sum."""
+    lib = _load()
+    ant = np.ascontiguousarray(p.ant_enu, dtype=np.float64)
+    pairs = np.ascontiguousarray(p.pairs, dtype=np.int32)
+    ra = np.ascontiguousarray(p.ra, dtype=np.float64)
+    dec = np.ascontiguousarray(p.dec, dtype=np.float64)
+    flux = np.ascontiguousarray(p.flux, dtype=np.float64)
+    freqs = np.ascontiguousarray(p.freqs_hz, dtype=np.float64)
+    lsts = np.ascontiguousarray(p.lsts_rad, dtype=np.float64)
+    n_pol = 4 if p.polarized else 1
+    bp = (C.c_double * 3)(*(list(p.beam_param) + [0.0] * (3 - len(p.beam_param))))
+    prob = _Problem(len(ant), _p(ant), len(pairs), pairs.ctypes.data_as(C.POINTER(C.c_int)),
+                    len(ra), _p(ra), _p(dec), flux.shape[0], _p(flux), len(freqs), _p(freqs),
+                    len(lsts), _p(lsts), float(p.latitude_rad), BEAMS[p.beam], bp,
+                    1 if p.polarized else 0)
+    out = np.zeros((len(freqs), len(lsts), len(pairs), n_pol, 2), dtype=np.float64)
+    rc = lib.oracle_vis(C.byref(prob), _p(out), 0 if mode == "literal" else 1, int(n_threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_vis failed with code {rc}")
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def oracle_enu(ra: float, dec: float, lst: float, lat: float) -> np.ndarray:
+    out = np.zeros(3)
+    _load().oracle_enu(ra, dec, lst, lat, _p(out))
+    return out
+
+
+def oracle_voltage(beam: str, param, theta: float, nu: float) -> float:
+    bp = np.array(list(param) + [0.0] * (3 - len(param)), dtype=np.float64)
+    return _load().oracle_voltage(BEAMS[beam], _p(bp), theta, nu)
+
+
+def oracle_strength(beam: str, param, polarized: bool, s, nu: float, stokes) -> np.ndarray:
+    bp = np.array(list(param) + [0.0] * (3 - len(param)), dtype=np.float64)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    st = np.ascontiguousarray(list(stokes) + [0.0] * (4 - len(stokes)), dtype=np.float64)
+    n_pol = 4 if polarized else 1
+    out = np.zeros(2 * n_pol)
+    _load().oracle_strength(BEAMS[beam], _p(bp), 1 if polarized else 0, _p(s), nu, _p(st), _p(out))
+    return out[0::2] + 1j * out[1::2]
+
+
+def max_threads() -> int:
+    return _load().oracle_max_threads()
+
+
+def rel_l2(a, b) -> float:
+    """Relative L2 error ||a - b|| / ||b||."""
+    a = np.asarray(a); b = np.asarray(b)
+    nb = np.linalg.norm(b.ravel())
+    return float(np.linalg.norm((a - b).ravel()) / nb) if nb > 0 else float(np.linalg.norm(a.ravel()))

@@ -1,0 +1,258 @@
+"""Pins for the FP64 oracle: facts fixed by the paper's equations and by
+mathematics, checked independently of the oracle's own code.
+
+Each test targets a plausible mistake: a wrong rotation row or sign, a swapped
+baseline orientation, a wrong fringe sign, J^dagger C J instead of J C J^dagger
+(Eq. 1 vs the form quoted under Eq. 3), a missing horizon cut, a beam with the
+wrong width law, a dropped polarisation term.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import special
+
+from oracle.oracle import (OracleProblem, oracle_enu, oracle_strength, oracle_vis,
+                           oracle_voltage, rel_l2)
+from paper_2506_02130_gb300 import workloads as W
+from tests import _analytic as A
+
+C = 299792458.0
+LAT = W.HERA_LATITUDE_RAD
+
+
+# ---------------------------------------------------------------- rotation
+def test_zenith_source():
+    s = oracle_enu(1.234, LAT, 1.234, LAT)
+    np.testing.assert_allclose(s, [0, 0, 1], atol=1e-15)
+
+
+def test_celestial_pole_altitude_equals_latitude():
+    for lat in (math.radians(40.0), LAT):
+        s = oracle_enu(0.7, math.pi / 2, 2.1, lat)
+        np.testing.assert_allclose(s, [0, math.cos(lat), math.sin(lat)], atol=1e-15)
+
+
+def test_equator_source_rises_due_east():
+    # hour angle -90 deg: on the horizon, due east, at any latitude
+    for lat in (0.3, -0.9):
+        lst = 0.4
+        s = oracle_enu(lst + math.pi / 2, 0.0, lst, lat)
+        np.testing.assert_allclose(s, [1, 0, 0], atol=1e-15)
+
+
+def test_meridian_transit_north_of_zenith():
+    # on the meridian 30 deg north of the zenith: (0, sin 30, cos 30)
+    dec = LAT + math.radians(30)
+    s = oracle_enu(2.0, dec, 2.0, LAT)
+    np.testing.assert_allclose(s, [0, 0.5, math.sqrt(3) / 2], atol=1e-15)
+
+
+def test_rotation_preserves_angles_and_moves_west():
+    rng = np.random.default_rng(0)
+    ra, dec = W.uniform_sphere(20, rng)
+    eq = np.stack([np.cos(dec) * np.cos(ra), np.cos(dec) * np.sin(ra), np.sin(dec)], 1)
+    enu = np.array([oracle_enu(a, d, 0.77, LAT) for a, d in zip(ra, dec)])
+    np.testing.assert_allclose(enu @ enu.T, eq @ eq.T, atol=1e-14)
+    # a proper rotation (det +1): handedness of the frame is kept
+    assert np.linalg.det(enu[:3]) * np.linalg.det(eq[:3]) > 0
+    # a transiting source moves west (E decreases) as LST grows
+    s0 = oracle_enu(1.0, LAT, 1.0, LAT)
+    s1 = oracle_enu(1.0, LAT, 1.001, LAT)
+    assert s1[0] < s0[0]
+
+
+# ---------------------------------------------------------------- beams
+def test_gaussian_beam_half_power_at_half_fwhm_scaling_with_frequency():
+    fwhm, ref = W.GAUSS_FWHM_150
+    for nu in (150e6, 300e6, 100e6):
+        theta = 0.5 * fwhm * ref / nu
+        assert oracle_voltage("gauss", (fwhm, ref), theta, nu) ** 2 == pytest.approx(0.5, rel=1e-14)
+    assert oracle_voltage("gauss", (fwhm, ref), 0.0, 123e6) == 1.0
+
+
+def test_airy_beam_against_scipy_and_first_null():
+    D = 14.0
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        theta = rng.uniform(1e-3, 1.5)
+        nu = rng.uniform(100e6, 200e6)
+        x = math.pi * D * nu * math.sin(theta) / C
+        assert oracle_voltage("airy", (D,), theta, nu) == pytest.approx(2 * special.j1(x) / x, rel=1e-12, abs=1e-15)
+    nu = 150e6
+    x0 = special.jn_zeros(1, 1)[0]
+    theta0 = math.asin(x0 * C / (math.pi * D * nu))
+    assert abs(oracle_voltage("airy", (D,), theta0, nu)) < 1e-12
+    assert oracle_voltage("airy", (D,), 0.0, nu) == 1.0
+
+
+# ---------------------------------------------------------------- coherency (Eq. 1-2)
+def _dir_at_az(az, za):
+    return np.array([math.sin(za) * math.sin(az), math.sin(za) * math.cos(az), math.cos(za)])
+
+
+def test_unpolarised_source_gives_identity_coherency():
+    s = _dir_at_az(1.1, 0.2)
+    A2 = oracle_voltage("airy", (14.0,), 0.2, 150e6) ** 2
+    c = oracle_strength("airy", (14.0,), True, s, 150e6, [3.0, 0, 0, 0])
+    np.testing.assert_allclose(c, A2 * 3.0 * np.array([1, 0, 0, 1]), atol=1e-14)
+    c1 = oracle_strength("airy", (14.0,), False, s, 150e6, [3.0])
+    assert c1[0] == pytest.approx(A2 * 3.0, rel=1e-14)
+
+
+def test_stokes_q_at_45_deg_azimuth_distinguishes_jcjdag_from_jdagcj():
+    # R(45) diag(Q,-Q) R(45)^T = [[0, Q], [Q, 0]];  R^T C R would give -Q off-diagonal
+    s = _dir_at_az(math.pi / 4, 0.1)
+    A2 = oracle_voltage("uniform", (), 0.1, 150e6) ** 2
+    c = oracle_strength("uniform", (), True, s, 150e6, [0, 2.0, 0, 0])
+    np.testing.assert_allclose(c, A2 * np.array([0, 2.0, 2.0, 0]), atol=1e-14)
+
+
+def test_stokes_q_due_north_is_diagonal_and_v_is_rotation_invariant():
+    s = _dir_at_az(0.0, 0.3)
+    c = oracle_strength("uniform", (), True, s, 150e6, [1.0, 0.5, 0, 0])
+    np.testing.assert_allclose(c, [1.5, 0, 0, 0.5], atol=1e-15)
+    s = _dir_at_az(0.7, 0.3)
+    c = oracle_strength("uniform", (), True, s, 150e6, [0, 0, 0, 0.25])
+    np.testing.assert_allclose(c, [0, 0.25j, -0.25j, 0], atol=1e-15)
+
+
+# ---------------------------------------------------------------- direct sum
+def _single(ant, pairs, ra, dec, flux, freqs, lst, lat=LAT, beam="uniform", param=(), pol=False):
+    return OracleProblem(np.asarray(ant, float), np.asarray(pairs, np.int32), np.atleast_1d(ra),
+                         np.atleast_1d(dec), np.asarray(flux, float), np.atleast_1d(freqs),
+                         np.atleast_1d(lst), lat, beam, param, pol)
+
+
+def test_zenith_source_has_zero_phase_on_coplanar_baselines():
+    ant = W.hex_array(2)
+    pairs = W.cross_pairs(len(ant))
+    p = _single(ant, pairs, 0.5, LAT, [[[2.5]]], 150e6, 0.5, beam="gauss", param=W.GAUSS_FWHM_150)
+    v = oracle_vis(p)
+    np.testing.assert_allclose(v, 2.5, atol=1e-13)
+
+
+def test_single_source_exact_phase_and_baseline_orientation():
+    # source 30 deg north of zenith on the meridian: s = (0, 1/2, sqrt(3)/2).
+    # antennas 0 at origin and 1 at 14.6 m north: b_01 = x_0 - x_1 = (0, -14.6, 0)
+    ant = [[0, 0, 0], [0, 14.6, 0], [10.0, 0, 0]]
+    pairs = [[0, 1], [1, 0], [0, 2]]
+    dec = LAT + math.radians(30)
+    for nu in (150e6, 187.3e6):
+        p = _single(ant, pairs, 2.0, dec, [[[1.0]]], nu, 2.0)
+        v = oracle_vis(p, "literal")[0, 0, :, 0]
+        phase01 = -2 * math.pi * nu * (-14.6 * 0.5) / C
+        np.testing.assert_allclose(v[0], np.exp(1j * phase01), rtol=1e-13)
+        np.testing.assert_allclose(v[1], np.exp(-1j * phase01), rtol=1e-13)
+        np.testing.assert_allclose(v[2], 1.0, rtol=1e-13)   # east baseline sees no phase
+
+
+def test_source_below_horizon_contributes_nothing():
+    ant = W.hex_array(1)
+    pairs = W.cross_pairs(len(ant))
+    # celestial north pole from a southern site is below the horizon
+    p = _single(ant, pairs, [0.0, 1.0], [math.pi / 2, LAT], [[[5.0], [1.0]]], 150e6, 1.0)
+    v = oracle_vis(p)
+    np.testing.assert_allclose(v, 1.0, atol=1e-13)
+
+
+@pytest.fixture(scope="module")
+def small():
+    return W.config_small(seed=3, n_src=300)
+
+
+def test_hermitian_and_zero_spacing(small):
+    n = len(small.ant_enu)
+    pairs = np.array([[i, j] for i in range(n) for j in range(n)], np.int32)
+    p = OracleProblem.from_workload(small, pairs=pairs)
+    v = oracle_vis(p, "literal")[0, 0, :, 0].reshape(n, n)
+    np.testing.assert_array_equal(v, np.conj(v.T))      # odd sine: exact
+    from oracle.oracle import oracle_enu as enu
+    tot = 0.0
+    for k in range(small.sky.n_src):
+        s = enu(small.sky.ra[k], small.sky.dec[k], small.lsts_rad[0], LAT)
+        if s[2] > 0:
+            tot += oracle_voltage("gauss", small.beam_param, math.acos(s[2]), 150e6) ** 2 * small.sky.flux[0, k, 0]
+    np.testing.assert_allclose(np.diag(v), tot, rtol=1e-12)
+
+
+def test_literal_equals_factored_and_translation_invariance(small):
+    p = OracleProblem.from_workload(small)
+    vl = oracle_vis(p, "literal")
+    vf = oracle_vis(p, "factored")
+    assert rel_l2(vf, vl) < 1e-13
+    p2 = OracleProblem.from_workload(small)
+    p2.ant_enu = small.ant_enu + np.array([123.4, -56.7, 0.0])
+    assert rel_l2(oracle_vis(p2, "literal"), vl) < 1e-12
+
+
+def test_baseline_frequency_scaling_invariance_and_linearity():
+    rng = np.random.default_rng(5)
+    ant = W.hex_array(2, z_sigma_m=0.3, rng=rng)
+    pairs = W.cross_pairs(len(ant))
+    ra, dec = W.uniform_sphere(200, rng)
+    flux = rng.uniform(0.1, 2, (1, 200, 1))
+    a = oracle_vis(_single(ant, pairs, ra, dec, flux, 160e6, 0.3), "literal")
+    b = oracle_vis(_single(2 * ant, pairs, ra, dec, flux, 80e6, 0.3), "literal")
+    assert rel_l2(b, a) < 1e-13
+    c = oracle_vis(_single(ant, pairs, ra, dec, 3 * flux, 160e6, 0.3), "literal")
+    assert rel_l2(c, 3 * a) < 1e-14
+
+
+def test_polarised_sum_of_unpolarised_sky_matches_scalar_path():
+    rng = np.random.default_rng(6)
+    ant = W.hex_array(1)
+    pairs = W.cross_pairs(len(ant))
+    ra, dec = W.uniform_sphere(100, rng)
+    I = rng.uniform(0.1, 2, (100, 2))
+    flux4 = np.zeros((4, 100, 2)); flux4[0] = I
+    freqs = np.array([120e6, 170e6])
+    pol = oracle_vis(_single(ant, pairs, ra, dec, flux4, freqs, 1.0, beam="airy", param=(14.0,), pol=True))
+    sc = oracle_vis(_single(ant, pairs, ra, dec, I[None], freqs, 1.0, beam="airy", param=(14.0,)))
+    np.testing.assert_allclose(pol[..., 0], sc[..., 0], rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(pol[..., 3], sc[..., 0], rtol=1e-13, atol=1e-13)
+    assert np.abs(pol[..., 1]).max() < 1e-13 and np.abs(pol[..., 2]).max() < 1e-13
+
+
+# ---------------------------------------------------------------- analytic diffuse (Section 4.1)
+def _diffuse_problem(nside, name, u_wl, nu=150e6):
+    # observer at the north pole: zenith angle = 90 deg - dec, no rotation needed
+    ra, dec = W.healpix_radec(nside)
+    theta = np.pi / 2 - dec
+    bright = np.where(theta < np.pi / 2, A.profile(name, np.clip(theta, 0, np.pi / 2)), 0.0)
+    flux = (bright * W.healpix_pixel_area(nside))[None, :, None]
+    lam = C / nu
+    ant = np.zeros((len(u_wl) + 1, 3))
+    ant[1:, 0] = -np.asarray(u_wl) * lam * np.cos(0.3)
+    ant[1:, 1] = -np.asarray(u_wl) * lam * np.sin(0.3)
+    pairs = np.array([[0, k] for k in range(1, len(ant))], np.int32)
+    return _single(ant, pairs, ra, dec, flux, nu, 0.9, lat=math.pi / 2)
+
+
+@pytest.mark.parametrize("name", ["monopole", "quaddome", "gauss"])
+def test_analytic_diffuse_converges_with_nside(name):
+    u = np.array([0.5, 1.7, 4.2])
+    ref = A.monopole(u) if name == "monopole" else A.radial(name, u)
+    if name == "monopole":
+        np.testing.assert_allclose(A.radial("monopole", u), ref, rtol=1e-10, atol=1e-12)
+    errs = []
+    for nside in (8, 16, 32):
+        v = oracle_vis(_diffuse_problem(nside, name, u))[0, 0, :, 0]
+        errs.append(np.abs(v - ref).max())
+    assert errs[2] < errs[1] < errs[0]
+    assert errs[2] < (0.05 if name != "quaddome" else 0.005)
+    if name == "quaddome":      # smooth to the horizon: second-order convergence
+        assert errs[2] / errs[1] < 0.3
+    if name == "monopole":      # horizon cut through a pixel ring: first order
+        assert 0.4 < errs[2] / errs[1] < 0.6
+
+
+def test_golden_fixture_reproduces():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "hex37_oracle.txt")
+    rows = np.loadtxt(path)
+    prob = W.config_small(seed=11, n_src=40)
+    pairs = prob.pairs[::17]
+    np.testing.assert_array_equal(rows[:, :2].astype(int), pairs)
+    v = oracle_vis(OracleProblem.from_workload(prob, pairs=pairs), "literal")[0, 0, :, 0]
+    np.testing.assert_allclose(v, rows[:, 2] + 1j * rows[:, 3], rtol=1e-12, atol=1e-13)
