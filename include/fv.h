@@ -1,0 +1,181 @@
+/*
+ * fv.h -- C ABI of libfftvis_gb300.so, a GB300 (sm_103a) implementation of
+ * the visibility hot path of fftvis (Cox et al. 2025).
+ *
+ * The library evaluates, for every (time, frequency) slice,
+ *
+ *   V^{pq}_{ij}(nu, t) = sum_n [J C_n J^dagger]_{pq} exp(-2 pi i nu b_ij . s_n(t) / c)
+ *
+ * (Eq. 1 with the coherency matrix of Eq. 2, under the point-source
+ * approximation of Eq. 3) as one type-3 non-uniform FFT per slice (Eq. 4 with
+ * x_k = -2 pi nu b_k / c, Section 2.2): beam x flux weighting, spreading with
+ * the exponential-of-semicircle kernel, an oversampled FFT, deconvolution and
+ * interpolation at the baselines (Fig. 1, Section 2.2 steps 1-3).  Sources are
+ * rotated from equatorial coordinates to East-North-Up by the rigid rotation
+ * fixed by local sidereal time and latitude (Section 2.3); one beam is shared
+ * by all antennas (Section 2.2.3).
+ *
+ * General rules for every entry point:
+ *  - Return FV_OK (0) on success or an fv_status code; no C++ exception and
+ *    no CUDA error escapes.  fv_last_error() gives a message for the last
+ *    failing call on a plan (valid until the next call on that plan).
+ *  - Host arrays passed in are read during the call and copied; the caller
+ *    keeps ownership.  Device pointers (flags *_on_device) are borrowed: they
+ *    must stay valid for as long as the docs of the call say.
+ *  - A plan is not thread-safe.  Use one plan per host thread.
+ *  - All device work of a plan runs on one CUDA stream: the stream given in
+ *    fv_opts.cuda_stream (borrowed), or one the plan creates and owns.
+ *  - No CPU fallback: if no CUDA device is usable, fv_plan fails with
+ *    FV_ERR_CUDA.
+ */
+#ifndef FV_H
+#define FV_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FV_ABI_VERSION 1
+
+typedef struct fv_plan_s *fv_plan_t;   /* opaque plan handle; owns its device memory */
+
+typedef enum {
+    FV_OK = 0,
+    FV_ERR_ARG = 1,          /* invalid argument (NaN coordinate, size, eps range ...) */
+    FV_ERR_OOM = 2,          /* device allocation failed */
+    FV_ERR_CUDA = 3,         /* CUDA runtime error or no usable device */
+    FV_ERR_STATE = 4,        /* call out of order (e.g. execute before set_sky) */
+    FV_ERR_TIMEOUT = 5,      /* a bounded device wait ran out */
+    FV_ERR_UNSUPPORTED = 6   /* valid request this build does not handle (e.g. grid too large) */
+} fv_status;
+
+typedef enum {
+    FV_FP64 = 0,    /* every step in FP64; output complex128 */
+    FV_MIXED = 1    /* spread, FFT and interpolation in FP32 with FP64 centring,
+                       rescaling, phases and deconvolution; output complex64 */
+} fv_precision;
+
+typedef enum {
+    FV_BEAM_GAUSS = 0,    /* power beam exp(-4 ln2 theta^2 / FWHM(nu)^2),
+                             FWHM(nu) = beam_param[0] * beam_param[1] / nu
+                             (beam_param[0] = FWHM in rad at reference frequency beam_param[1] Hz) */
+    FV_BEAM_AIRY = 1,     /* voltage 2 J1(x)/x, x = pi D nu sin(theta)/c, D = beam_param[0] m */
+    FV_BEAM_UNIFORM = 2   /* A = 1 (no beam) */
+} fv_beam_kind;
+
+/* Plan options.  Analytic beams only (Section 2.4, item i); the Jones matrix of
+ * the polarised path is A(theta) [[cos az, -sin az], [sin az, cos az]] with
+ * the azimuth measured east of north. */
+typedef struct {
+    int precision;            /* fv_precision */
+    double eps;               /* NUFFT tolerance (Section 2.2 and 4.2): 1e-14 <= eps <= 1e-2;
+                                 FV_MIXED requires eps >= 1e-7 */
+    int n_freq;               /* >= 1 */
+    const double *freq_hz;    /* [n_freq] channel frequencies, > 0, copied */
+    int n_time;               /* >= 1 */
+    const double *lst_rad;    /* [n_time] local sidereal times, copied */
+    double latitude_rad;      /* observatory latitude, |lat| <= pi/2 */
+    int beam;                 /* fv_beam_kind */
+    double beam_param[3];
+    int polarized;            /* 0: one product (B I); 1: Stokes IQUV in, four products
+                                 pq = 00, 01, 10, 11 out */
+    int dims;                 /* 0: auto (3 if any baseline has b_up != 0), 2 or 3 */
+    double upsampfac;         /* oversampling sigma (Section 2.2, Eq. 5); 0 = default 2.0;
+                                 accepted: 1.25 <= sigma <= 3 */
+    int kernel_width;         /* ES kernel width w in grid points; 0 = from eps
+                                 (w = ceil(log10(1/eps)) + 1 at sigma = 2, Section 2.2) */
+    void *cuda_stream;        /* borrowed cudaStream_t, or NULL for a plan-owned stream */
+    int device;               /* CUDA device ordinal; -1 = the current device */
+} fv_opts;
+
+/* Fill *o with defaults: FV_FP64, eps 1e-10, Gaussian beam 10 deg at 150 MHz,
+ * unpolarised, auto dims, sigma 2, NULL stream, current device.  The caller
+ * must still set freq_hz/n_freq and lst_rad/n_time. */
+void fv_opts_default(fv_opts *o);
+
+/* Create a plan on o->device.  Copies frequencies and LSTs.  Errors:
+ * FV_ERR_ARG (bad option), FV_ERR_CUDA (no device), FV_ERR_OOM. */
+fv_status fv_plan(const fv_opts *o, fv_plan_t *out);
+
+/* Set the array.  enu_m: host [n_ant][3] antenna positions (East, North, Up, m).
+ * pairs: host [n_bl][2] antenna index pairs (i, j), the baseline being
+ * b_ij = x_i - x_j; NULL means all i < j (n_bl is then ignored and becomes
+ * n_ant(n_ant-1)/2).  Identical FP64 baseline vectors share one NUFFT target
+ * (the unique baseline vectors of Fig. 1, panel E), bit-exact only.
+ * Errors: FV_ERR_ARG (n_ant < 1, index out of range, non-finite position). */
+fv_status fv_set_array(fv_plan_t p, int n_ant, const double *enu_m, int n_bl, const int *pairs);
+
+/* Set the sky: n_src point sources at (ra_rad, dec_rad), host arrays, copied.
+ * flux: [n_stokes][n_src][n_freq] Jy (n_stokes = 1: I; 4: I, Q, U, V), FP64 if
+ * flux_is_fp64 else FP32.  With flux_on_device = 0 it is a host array copied
+ * to the device; with flux_on_device = 1 it is a device pointer borrowed until
+ * the next fv_set_sky or fv_destroy.  Diffuse maps enter as sources at pixel
+ * centres with flux = brightness x pixel solid angle (Section 4.1).  Computes
+ * the source extents over all times on the device (one synchronisation).
+ * Errors: FV_ERR_ARG (n_src < 0, non-finite coordinate, n_stokes mismatch with
+ * opts.polarized), FV_ERR_STATE (before fv_set_array), FV_ERR_OOM,
+ * FV_ERR_UNSUPPORTED (a grid would exceed this build's size limits). */
+fv_status fv_set_sky(fv_plan_t p, long n_src, const double *ra_rad, const double *dec_rad,
+                     int n_stokes, const void *flux, int flux_is_fp64, int flux_on_device);
+
+/* Compute all slices.  vis: [n_freq][n_time][n_bl][n_pol] complex values
+ * (interleaved re, im), complex128 for FV_FP64 and complex64 for FV_MIXED,
+ * n_pol = 4 if polarized else 1.  vis_on_device = 0: host buffer, the call
+ * returns when it is filled.  vis_on_device = 1: device buffer; the call
+ * returns once the work is enqueued on the plan's stream (synchronise that
+ * stream before reading).  Errors: FV_ERR_STATE (no array or sky),
+ * FV_ERR_ARG (NULL vis), FV_ERR_CUDA. */
+fv_status fv_execute(fv_plan_t p, void *vis, int vis_on_device);
+
+/* Release every device and host resource of the plan.  NULL is accepted. */
+fv_status fv_destroy(fv_plan_t p);
+
+/* Message for the last failing call on p (or on plan creation when p is NULL). */
+const char *fv_last_error(fv_plan_t p);
+
+/* Read-only plan geometry for tests, logs and the autotuner. */
+typedef struct {
+    int dims;             /* 2 or 3 */
+    int kernel_width;     /* w */
+    double beta;          /* ES shape parameter */
+    double upsampfac;     /* sigma */
+    int n_unique;         /* unique baseline targets */
+    int n_bl;
+    long n_src;
+    int nf1_max[3];       /* largest spreading grid over channels, per dim (x=E, y=N, z=U) */
+    int nf2_max[3];       /* largest FFT length over channels, per dim */
+    double src_centre[3];     /* C: centre of the visible source directions */
+    double src_halfwidth[3];  /* S: half-extent of the visible source directions */
+    long long workspace_bytes;   /* device memory held by the plan */
+} fv_info;
+
+fv_status fv_get_info(fv_plan_t p, fv_info *info);
+
+/* Per-kernel timing for roofline reports (no counterpart in the paper; the
+ * paper times whole stages with a line profiler, Section 5).  While enabled,
+ * every device launch that fv_execute enqueues is bracketed by two CUDA events
+ * on the plan's stream and counted; fv_profile_read synchronises the stream,
+ * adds up the elapsed times per kernel class, copies them out and resets the
+ * counters.  Classes: "memset", "spread", "fft_x", "fft_y", "fft_z",
+ * "interp", "scatter" (FV_PROFILE_CLASSES entries; unused ones stay zero).
+ * bytes[c] is the algorithmic HBM traffic the launches of class c imply
+ * (each input read once, each output written once).  Launch counts are kept
+ * even while timing is disabled. */
+#define FV_PROFILE_CLASSES 8
+typedef struct {
+    const char *name[FV_PROFILE_CLASSES];
+    double total_ms[FV_PROFILE_CLASSES];
+    long long launches[FV_PROFILE_CLASSES];
+    double bytes[FV_PROFILE_CLASSES];
+} fv_profile_data;
+
+fv_status fv_profile_enable(fv_plan_t p, int enable);
+fv_status fv_profile_read(fv_plan_t p, fv_profile_data *out);
+
+/* ABI version (FV_ABI_VERSION of the library that was loaded). */
+int fv_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FV_H */

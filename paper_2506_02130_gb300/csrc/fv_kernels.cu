@@ -1,0 +1,372 @@
+// Device kernels of the visibility path except the FFT passes:
+// set-up tables, weighting + spreading, interpolation + deconvolution +
+// postphase, output scatter.  See fv_internal.cuh for the notation.
+#include "fv_internal.cuh"
+
+#include <math.h>
+
+namespace fv {
+
+// Exponential-of-semicircle kernel phi(z) = exp(beta (sqrt(1 - z^2) - 1)) on
+// [-1, 1], zero outside (Section 2.2, spreading step).
+__device__ __forceinline__ double es_kernel(double z, double beta)
+{
+    double t = 1.0 - z * z;
+    return t >= 0.0 ? exp(beta * (sqrt(t) - 1.0)) : 0.0;
+}
+__device__ __forceinline__ float es_kernel(float z, float beta)
+{
+    float t = 1.0f - z * z;
+    return t >= 0.0f ? expf(beta * (sqrtf(t) - 1.0f)) : 0.0f;
+}
+
+// Phihat(k) = int_{-1}^{1} phi(z) cos(k z) dz by Gauss-Legendre quadrature (FP64).
+__device__ double es_fourier(double k, double beta, const double *gl_x, const double *gl_w, int nq)
+{
+    double s = 0.0;
+    for (int q = 0; q < nq; ++q) s += gl_w[q] * es_kernel(gl_x[q], beta) * cos(k * gl_x[q]);
+    return s;
+}
+
+// ------------------------------------------------------------------ set-up
+__global__ void k_radec_to_unit(const double *ra, const double *dec, long n, double *e)
+{
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double sa, ca, sd, cd;
+    sincos(ra[i], &sa, &ca);
+    sincos(dec[i], &sd, &cd);
+    e[i] = cd * ca;
+    e[n + i] = cd * sa;
+    e[2 * n + i] = sd;
+}
+
+cudaError_t launch_radec_to_unit(const double *ra, const double *dec, long n, double *e, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_radec_to_unit<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ra, dec, n, e);
+    return cudaGetLastError();
+}
+
+__global__ void k_source_extents(const double *e, long n, const double *R_all, int n_time, double *out)
+{
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        double ex = e[i], ey = e[n + i], ez = e[2 * n + i];
+        for (int t = 0; t < n_time; ++t) {
+            const double *R = R_all + 9 * t;
+            double s2 = R[6] * ex + R[7] * ey + R[8] * ez;
+            if (!(s2 > 0.0)) continue;
+            double s0 = R[0] * ex + R[1] * ey + R[2] * ez;
+            double s1 = R[3] * ex + R[4] * ey + R[5] * ez;
+            lo[0] = fmin(lo[0], s0); hi[0] = fmax(hi[0], s0);
+            lo[1] = fmin(lo[1], s1); hi[1] = fmax(hi[1], s1);
+            lo[2] = fmin(lo[2], s2); hi[2] = fmax(hi[2], s2);
+        }
+    }
+    __shared__ double red[6][256];
+    for (int k = 0; k < 3; ++k) { red[k][threadIdx.x] = lo[k]; red[3 + k][threadIdx.x] = hi[k]; }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < 3; ++k) {
+                red[k][threadIdx.x] = fmin(red[k][threadIdx.x], red[k][threadIdx.x + s]);
+                red[3 + k][threadIdx.x] = fmax(red[3 + k][threadIdx.x], red[3 + k][threadIdx.x + s]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) out[blockIdx.x * 6 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+cudaError_t launch_source_extents(const double *e, long n, const double *R_all, int n_time, double *out,
+                                  int nblocks, cudaStream_t st)
+{
+    k_source_extents<<<nblocks, 256, 0, st>>>(e, n, R_all, n_time, out);
+    return cudaGetLastError();
+}
+
+template <class G>
+__global__ void k_prescale_table(G *tab, int nf1, int M, int w, double beta, const double *gl_x,
+                                 const double *gl_w, int nq)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nf1) return;
+    double k = (double)(j - nf1 / 2) * w * M_PI / (double)M;
+    tab[j] = (G)(1.0 / es_fourier(k, beta, gl_x, gl_w, nq));
+}
+
+template <class G>
+cudaError_t launch_prescale_table(G *tab, int nf1, int M, int w, double beta, const double *gl_x,
+                                  const double *gl_w, int nq, cudaStream_t st)
+{
+    k_prescale_table<G><<<(nf1 + 127) / 128, 128, 0, st>>>(tab, nf1, M, w, beta, gl_x, gl_w, nq);
+    return cudaGetLastError();
+}
+
+template <class G>
+__global__ void k_twiddles(cpx<G> *tw, int M)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M) return;
+    double s, c;
+    sincospi(2.0 * (double)k / (double)M, &s, &c);
+    tw[k] = cmk<G>((G)c, (G)s);
+}
+
+template <class G>
+cudaError_t launch_twiddles(cpx<G> *tw, int M, cudaStream_t st)
+{
+    k_twiddles<G><<<(M + 255) / 256, 256, 0, st>>>(tw, M);
+    return cudaGetLastError();
+}
+
+__global__ void k_target_deconv(const double *bu, int n_u, int d, double bc0, double bc1, double bc2,
+                                double bh0, double bh1, double bh2, int w, double beta, double sigma,
+                                const double *gl_x, const double *gl_w, int nq, double *dec)
+{
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n_u) return;
+    const double bc[3] = {bc0, bc1, bc2}, bh[3] = {bh0, bh1, bh2};
+    double r = 1.0;
+    for (int i = 0; i < d; ++i) {
+        double a = bh[i] > 0.0 ? (bc[i] - bu[3 * u + i]) / bh[i] * (w * M_PI / (2.0 * sigma)) : 0.0;
+        r *= (4.0 / ((double)w * w)) / es_fourier(a, beta, gl_x, gl_w, nq);
+    }
+    dec[u] = r;
+}
+
+cudaError_t launch_target_deconv(const double *bu, int n_u, int d, const double *bcen, const double *bhalf,
+                                 int w, double beta, double sigma, const double *gl_x, const double *gl_w,
+                                 int nq, double *dec, cudaStream_t st)
+{
+    if (n_u <= 0) return cudaSuccess;
+    k_target_deconv<<<(n_u + 127) / 128, 128, 0, st>>>(bu, n_u, d, bcen[0], bcen[1], bcen[2], bhalf[0],
+                                                      bhalf[1], bhalf[2], w, beta, sigma, gl_x, gl_w, nq,
+                                                      dec);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ weighting
+// Voltage beam A(theta, nu) from the direction (s0, s1, s2), s2 > 0.
+__device__ __forceinline__ double voltage_beam(const BeamParams &b, double rho, double s2, double nu)
+{
+    if (b.kind == 0) {
+        double theta = atan2(rho, s2);
+        double fwhm = b.p0 * b.p1 / nu;
+        return exp(-2.0 * M_LN2 * theta * theta / (fwhm * fwhm));
+    }
+    if (b.kind == 1) {
+        double x = M_PI * b.p0 * nu * rho / FV_C_LIGHT;
+        return x < 1e-8 ? 1.0 - 0.125 * x * x : 2.0 * j1(x) / x;
+    }
+    return 1.0;
+}
+
+__device__ __forceinline__ double load_flux(const void *flux, int fp64, size_t idx)
+{
+    return fp64 ? ((const double *)flux)[idx] : (double)((const float *)flux)[idx];
+}
+
+// Strengths c^{pq} = [J C J^dagger]_{pq} (Eq. 1-2) with J = A R(az):
+// the rotation turns (Q, U) by twice the azimuth and leaves I and V alone.
+__device__ __forceinline__ int source_strengths(const SliceGeom &g, const void *flux, int flux_fp64,
+                                                long n_src, int n_freq, int f, long n, double s0, double s1,
+                                                double s2, cpx<double> *c)
+{
+    double rho = sqrt(s0 * s0 + s1 * s1);
+    double A = voltage_beam(g.beam, rho, s2, g.nu);
+    double A2 = A * A;
+    double I = load_flux(flux, flux_fp64, (size_t)n * n_freq + f);
+    if (!g.polarized) {
+        c[0] = cmk<double>(A2 * I, 0.0);
+        return 1;
+    }
+    double Q = load_flux(flux, flux_fp64, ((size_t)n_src + n) * n_freq + f);
+    double U = load_flux(flux, flux_fp64, ((size_t)2 * n_src + n) * n_freq + f);
+    double V = load_flux(flux, flux_fp64, ((size_t)3 * n_src + n) * n_freq + f);
+    double ca = 1.0, sa = 0.0;
+    if (rho > 0.0) { ca = s1 / rho; sa = s0 / rho; }
+    double c2 = ca * ca - sa * sa, s2a = 2.0 * ca * sa;
+    double Qr = Q * c2 - U * s2a, Ur = Q * s2a + U * c2;
+    c[0] = cmk<double>(A2 * (I + Qr), 0.0);
+    c[1] = cmk<double>(A2 * Ur, A2 * V);
+    c[2] = cmk<double>(A2 * Ur, -A2 * V);
+    c[3] = cmk<double>(A2 * (I - Qr), 0.0);
+    return 4;
+}
+
+// ------------------------------------------------------------------ spreading
+template <class G>
+__global__ void __launch_bounds__(128) k_spread_direct(const double *__restrict__ e, long n_src,
+                                                       const void *__restrict__ flux, int flux_fp64, int n_freq,
+                                                       int f, SliceGeom g, cpx<G> *__restrict__ grid)
+{
+    long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (n >= n_src) return;
+    const double ex = e[n], ey = e[n_src + n], ez = e[2 * n_src + n];
+    const double s2 = g.R[6] * ex + g.R[7] * ey + g.R[8] * ez;
+    if (!(s2 > 0.0)) return;                       // horizon cut (strictly above)
+    const double s0 = g.R[0] * ex + g.R[1] * ey + g.R[2] * ez;
+    const double s1 = g.R[3] * ex + g.R[4] * ey + g.R[5] * ez;
+    cpx<double> c[4];
+    const int np = source_strengths(g, flux, flux_fp64, n_src, n_freq, f, n, s0, s1, s2, c);
+    // prephase e^{i D.(s - C)} (FP64)
+    const double st[3] = {s0 - g.dim[0].C, s1 - g.dim[1].C, s2 - g.dim[2].C};
+    double ph = 0.0;
+    for (int i = 0; i < g.d; ++i) ph += g.dim[i].D * st[i];
+    double sp, cp;
+    sincos(ph, &sp, &cp);
+    cpx<G> cg[4];
+    for (int p = 0; p < np; ++p) {
+        cpx<double> v = cmul(c[p], cmk<double>(cp, sp));
+        cg[p] = cmk<G>((G)v.x, (G)v.y);
+    }
+    // kernel weights per dimension; the cell split of q is done in FP64
+    G kv[3][16];
+    int base[3] = {0, 0, 0};
+    const int w = g.w;
+    const G two_over_w = (G)(2.0 / w);
+    for (int i = 0; i < 3; ++i) {
+        if (i >= g.d) { kv[i][0] = (G)1; base[i] = 0; continue; }
+        double q = st[i] * g.dim[i].qscale;
+        double l0 = ceil(q - 0.5 * w);
+        G fr = (G)(l0 - q);                        // offset of cell l0 from q, in [-w/2, 1-w/2)
+        for (int j = 0; j < w; ++j) kv[i][j] = es_kernel(two_over_w * (fr + (G)j), (G)g.beta);
+        int b = (int)l0 + g.dim[i].nf1 / 2;
+        base[i] = b;
+    }
+    const int nx = g.dim[0].nf1, ny = g.dim[1].nf1, nz = g.d == 3 ? g.dim[2].nf1 : 1;
+    const int wz = g.d == 3 ? w : 1;
+    const size_t plane = (size_t)nx * ny * nz;
+    for (int jz = 0; jz < wz; ++jz) {
+        int iz = base[2] + jz;
+        if (g.d == 3) { iz %= nz; if (iz < 0) iz += nz; }
+        for (int jy = 0; jy < w; ++jy) {
+            int iy = (base[1] + jy) % ny; if (iy < 0) iy += ny;
+            G wyz = kv[2][g.d == 3 ? jz : 0] * kv[1][jy];
+            for (int jx = 0; jx < w; ++jx) {
+                int ix = (base[0] + jx) % nx; if (ix < 0) ix += nx;
+                G wt = wyz * kv[0][jx];
+                size_t idx = ((size_t)iz * ny + iy) * nx + ix;
+                for (int p = 0; p < np; ++p) {
+                    atomicAdd(&grid[p * plane + idx].x, cg[p].x * wt);
+                    atomicAdd(&grid[p * plane + idx].y, cg[p].y * wt);
+                }
+            }
+        }
+    }
+}
+
+template <class G>
+cudaError_t launch_spread_direct(const double *e, long n_src, const void *flux, int flux_fp64, int n_freq, int f,
+                                 const SliceGeom &g, cpx<G> *grid, cudaStream_t st)
+{
+    if (n_src <= 0) return cudaSuccess;
+    k_spread_direct<G><<<(unsigned)((n_src + 127) / 128), 128, 0, st>>>(e, n_src, flux, flux_fp64, n_freq, f, g,
+                                                                         grid);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ interpolation
+template <class G>
+__global__ void __launch_bounds__(128) k_interp(const cpx<G> *__restrict__ band, const double *__restrict__ bu,
+                                                int n_u, const double *__restrict__ dec, SliceGeom g,
+                                                cpx<double> *__restrict__ Vu)
+{
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n_u) return;
+    const int w = g.w;
+    const G two_over_w = (G)(2.0 / w);
+    double x[3] = {0.0, 0.0, 0.0};
+    G kv[3][16];
+    int base[3] = {0, 0, 0};
+    for (int i = 0; i < 3; ++i) {
+        if (i >= g.d) { kv[i][0] = (G)1; continue; }
+        x[i] = -g.kappa * bu[3 * u + i];               // target x_k = -2 pi nu b_k / c
+        double p = (x[i] - g.dim[i].D) * g.dim[i].pscale;
+        double m0 = ceil(p - 0.5 * w);
+        G fr = (G)(p - m0);                            // offset of p from cell m0, in (w/2-1, w/2]
+        for (int j = 0; j < w; ++j) kv[i][j] = es_kernel(two_over_w * (fr - (G)j), (G)g.beta);
+        base[i] = (int)m0 + g.dim[i].H;
+    }
+    const int np = g.n_pol;
+    const int Bx = g.dim[0].B, By = g.dim[1].B;
+    const int wz = g.d == 3 ? w : 1;
+    G acc[8];
+    for (int k = 0; k < 2 * np; ++k) acc[k] = (G)0;
+    for (int jz = 0; jz < wz; ++jz) {
+        int bz = g.d == 3 ? base[2] + jz : 0;
+        for (int jy = 0; jy < w; ++jy) {
+            int by = base[1] + jy;
+            G wyz = kv[2][g.d == 3 ? jz : 0] * kv[1][jy];
+            const cpx<G> *row = band + (((size_t)bz * By + by) * Bx) * np;
+            for (int jx = 0; jx < w; ++jx) {
+                G wt = wyz * kv[0][jx];
+                const cpx<G> *cell = row + (size_t)(base[0] + jx) * np;
+                for (int p = 0; p < np; ++p) {
+                    cpx<G> v = cell[p];
+                    acc[2 * p] += wt * v.x;
+                    acc[2 * p + 1] += wt * v.y;
+                }
+            }
+        }
+    }
+    // deconvolution (FP64, channel independent) and postphase e^{i x.C} (FP64)
+    double ph = 0.0;
+    for (int i = 0; i < g.d; ++i) ph += x[i] * g.dim[i].C;
+    double sp, cp;
+    sincos(ph, &sp, &cp);
+    const double dk = dec[u];
+    for (int p = 0; p < np; ++p) {
+        cpx<double> v = cmk<double>((double)acc[2 * p] * dk, (double)acc[2 * p + 1] * dk);
+        Vu[(size_t)u * np + p] = cmul(v, cmk<double>(cp, sp));
+    }
+}
+
+template <class G>
+cudaError_t launch_interp(const cpx<G> *band, const double *bu, int n_u, const double *dec, const SliceGeom &g,
+                          cpx<double> *Vu, cudaStream_t st)
+{
+    if (n_u <= 0) return cudaSuccess;
+    k_interp<G><<<(n_u + 127) / 128, 128, 0, st>>>(band, bu, n_u, dec, g, Vu);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ output
+__global__ void k_scatter(const cpx<double> *__restrict__ Vu, const int *__restrict__ bl2u, int n_bl, int n_pol,
+                          void *out, int out_fp64)
+{
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= (long)n_bl * n_pol) return;
+    int bl = (int)(i / n_pol), p = (int)(i % n_pol);
+    cpx<double> v = Vu[(size_t)bl2u[bl] * n_pol + p];
+    if (out_fp64) ((double2 *)out)[i] = make_double2(v.x, v.y);
+    else ((float2 *)out)[i] = make_float2((float)v.x, (float)v.y);
+}
+
+cudaError_t launch_scatter(const cpx<double> *Vu, const int *bl2u, int n_bl, int n_pol, void *out, int out_fp64,
+                           cudaStream_t st)
+{
+    long n = (long)n_bl * n_pol;
+    if (n <= 0) return cudaSuccess;
+    k_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Vu, bl2u, n_bl, n_pol, out, out_fp64);
+    return cudaGetLastError();
+}
+
+// explicit instantiations
+template cudaError_t launch_prescale_table<double>(double *, int, int, int, double, const double *, const double *,
+                                                   int, cudaStream_t);
+template cudaError_t launch_prescale_table<float>(float *, int, int, int, double, const double *, const double *,
+                                                  int, cudaStream_t);
+template cudaError_t launch_twiddles<double>(cpx<double> *, int, cudaStream_t);
+template cudaError_t launch_twiddles<float>(cpx<float> *, int, cudaStream_t);
+template cudaError_t launch_spread_direct<double>(const double *, long, const void *, int, int, int,
+                                                  const SliceGeom &, cpx<double> *, cudaStream_t);
+template cudaError_t launch_spread_direct<float>(const double *, long, const void *, int, int, int,
+                                                 const SliceGeom &, cpx<float> *, cudaStream_t);
+template cudaError_t launch_interp<double>(const cpx<double> *, const double *, int, const double *,
+                                           const SliceGeom &, cpx<double> *, cudaStream_t);
+template cudaError_t launch_interp<float>(const cpx<float> *, const double *, int, const double *,
+                                          const SliceGeom &, cpx<double> *, cudaStream_t);
+
+}  // namespace fv

@@ -1,0 +1,750 @@
+// Host runtime and C ABI of libfftvis_gb300 (see include/fv.h).
+//
+// Plan-time geometry in FP64 (Section 2.2, Eq. 5 and the centring paragraph
+// after it): source centre C and half-extent S from the visible directions
+// over all times, target centre D and half-extent X from the baselines per
+// channel, grid sizes nf1 >= 2 sigma X S / pi + w (rounded up to an even
+// 2^a 3^b 5^c, at least 2w), FFT lengths M = sigma nf1, deconvolution tables.
+// Execution: per (time, channel) slice, spread -> d FFT passes -> interpolate
+// -> scatter, all enqueued on the plan's stream.
+#include "../../include/fv.h"
+#include "fv_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+using namespace fv;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int next235even(long n)
+{
+    if (n < 2) n = 2;
+    if (n % 2) ++n;
+    for (;; n += 2) {
+        long m = n;
+        while (m % 2 == 0) m /= 2;
+        while (m % 3 == 0) m /= 3;
+        while (m % 5 == 0) m /= 5;
+        if (m == 1) return (int)n;
+    }
+}
+
+// Stockham stage radices for M = 2^a 3^b 5^c (fours first).
+int radix_plan(int M, int *rad)
+{
+    int n = 0;
+    while (M % 4 == 0) { rad[n++] = 4; M /= 4; }
+    while (M % 2 == 0) { rad[n++] = 2; M /= 2; }
+    while (M % 3 == 0) { rad[n++] = 3; M /= 3; }
+    while (M % 5 == 0) { rad[n++] = 5; M /= 5; }
+    return M == 1 ? n : -1;
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    x.resize(n);
+    w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p1 = z; p0 = 1.0; }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+}  // namespace
+
+struct fv_plan_s {
+    // options
+    int precision = FV_FP64;
+    double eps = 1e-10;
+    std::vector<double> freq, lst;
+    double lat = 0.0;
+    BeamParams beam{};
+    int polarized = 0, n_pol = 1;
+    int dims_req = 0;
+    double sigma = 2.0;
+    int w = 0;
+    double beta = 0.0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+
+    // quadrature (sine-substituted Gauss-Legendre) on the device
+    int nq = 0;
+    double *d_glx = nullptr, *d_glw = nullptr;
+
+    // array
+    bool have_array = false;
+    int n_ant = 0, n_bl = 0, n_u = 0, d = 2;
+    std::vector<double> bu;          // [n_u][3]
+    std::vector<int> bl2u;           // [n_bl]
+    double bcen[3] = {0, 0, 0}, bhalf[3] = {0, 0, 0};
+    double *d_bu = nullptr, *d_dec = nullptr;
+    int *d_bl2u = nullptr;
+
+    // sky
+    bool have_sky = false;
+    long n_src = 0;
+    int n_stokes = 1;
+    double *d_e = nullptr;
+    void *d_flux_owned = nullptr;
+    const void *flux = nullptr;
+    int flux_fp64 = 0;
+    double C[3] = {0, 0, 0}, S[3] = {0, 0, 0};
+    bool any_visible = false;
+
+    // geometry
+    std::vector<double> Rt;          // [n_time][9]
+    std::vector<SliceGeom> gf;       // per channel (R filled per time)
+    std::vector<size_t> pre_off;     // [n_freq][3] element offsets into the prescale table
+    std::vector<size_t> tw_off;      // [n_freq][3] element offsets into the twiddle table
+    void *d_pre = nullptr, *d_tw = nullptr;
+    void *d_grid = nullptr, *d_bufA = nullptr, *d_bufB = nullptr;
+    cpx<double> *d_Vu = nullptr;
+    size_t grid_elems = 0, bufA_elems = 0, bufB_elems = 0;
+    long long ws_bytes = 0;
+    int nf1_max[3] = {1, 1, 1}, M_max[3] = {1, 1, 1};
+
+    // kernel timing (fv_profile_enable)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> ev_pending;   // (class, index of the start event in the pool)
+    size_t ev_next = 0;
+    double prof_ms[FV_PROFILE_CLASSES] = {};
+    long long prof_launches[FV_PROFILE_CLASSES] = {};
+    double prof_bytes[FV_PROFILE_CLASSES] = {};
+    int prof_cls = -1;
+
+    fv_status fail(fv_status s, const std::string &m)
+    {
+        err = m;
+        return s;
+    }
+    size_t elem() const { return precision == FV_FP64 ? sizeof(cpx<double>) : sizeof(cpx<float>); }
+};
+
+#define CK(call)                                                                                        \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return p->fail(e_ == cudaErrorMemoryAllocation ? FV_ERR_OOM : FV_ERR_CUDA,                  \
+                           std::string(#call " failed: ") + cudaGetErrorString(e_));                  \
+    } while (0)
+
+static void dfree(void *&ptr)
+{
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+}
+template <class T> static void dfree_t(T *&ptr)
+{
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+}
+
+static const char *k_prof_names[FV_PROFILE_CLASSES] = {"memset", "spread", "fft_x", "fft_y",
+                                                       "fft_z", "interp", "scatter", ""};
+enum { PC_MEMSET = 0, PC_SPREAD, PC_FFT_X, PC_FFT_Y, PC_FFT_Z, PC_INTERP, PC_SCATTER };
+
+// harvest finished event pairs into the per-class totals (synchronises the stream)
+static cudaError_t prof_harvest(fv_plan_s *p)
+{
+    if (p->ev_pending.empty()) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return e;
+    for (auto &pr : p->ev_pending) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, p->ev_pool[pr.second], p->ev_pool[pr.second + 1]);
+        if (e != cudaSuccess) return e;
+        p->prof_ms[pr.first] += ms;
+    }
+    p->ev_pending.clear();
+    p->ev_next = 0;
+    return cudaSuccess;
+}
+
+// bracket one launch of class cls; call prof_begin before and prof_end after it
+static cudaError_t prof_begin(fv_plan_s *p, int cls)
+{
+    p->prof_launches[cls] += 1;
+    p->prof_cls = cls;
+    if (!p->prof_on) return cudaSuccess;
+    if (p->ev_next + 2 > p->ev_pool.size()) {
+        cudaError_t e = prof_harvest(p);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaEventRecord(p->ev_pool[p->ev_next], p->stream);
+}
+
+static cudaError_t prof_end(fv_plan_s *p, double bytes)
+{
+    p->prof_bytes[p->prof_cls] += bytes;
+    if (!p->prof_on) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(p->ev_pool[p->ev_next + 1], p->stream);
+    p->ev_pending.emplace_back(p->prof_cls, (int)p->ev_next);
+    p->ev_next += 2;
+    return e;
+}
+
+static void free_geometry(fv_plan_s *p)
+{
+    dfree(p->d_pre);
+    dfree(p->d_tw);
+    dfree(p->d_grid);
+    dfree(p->d_bufA);
+    dfree(p->d_bufB);
+    dfree_t(p->d_Vu);
+}
+
+// Per-channel geometry, tables and workspace; needs the array and the sky.
+static fv_status prepare(fv_plan_s *p)
+{
+    free_geometry(p);
+    const int nf = (int)p->freq.size();
+    const int w = p->w;
+    p->gf.assign(nf, SliceGeom{});
+    p->pre_off.assign((size_t)nf * 3, 0);
+    p->tw_off.assign((size_t)nf * 3, 0);
+    size_t pre_total = 0, tw_total = 0;
+    for (int i = 0; i < 3; ++i) { p->nf1_max[i] = 1; p->M_max[i] = 1; }
+    const int maxM = fft_max_M((int)(p->precision == FV_FP64 ? sizeof(double) : sizeof(float)));
+    size_t grid_e = 0, bufA_e = 0, bufB_e = 0;
+    for (int f = 0; f < nf; ++f) {
+        SliceGeom &g = p->gf[f];
+        g.nu = p->freq[f];
+        g.kappa = 2.0 * M_PI * g.nu / FV_C_LIGHT;
+        g.d = p->d;
+        g.w = w;
+        g.beta = p->beta;
+        g.n_pol = p->n_pol;
+        g.polarized = p->polarized;
+        g.n_stokes = p->n_stokes;
+        g.beam = p->beam;
+        for (int i = 0; i < 3; ++i) {
+            DimGeom &dg = g.dim[i];
+            if (i >= p->d) {
+                dg.nf1 = 1; dg.M = 1; dg.B = 1; dg.H = 0; dg.qscale = 0; dg.pscale = 0; dg.D = 0; dg.C = 0;
+                dg.nstages = 0;
+                continue;
+            }
+            double X = g.kappa * p->bhalf[i];
+            double S = p->S[i];
+            if (!(X > 0.0)) X = S > 0.0 ? 1.0 / S : 1.0;
+            double need = 2.0 * p->sigma * X * S / M_PI + w;
+            long nf1 = (long)std::ceil(need);
+            if (nf1 < 2 * w) nf1 = 2 * w;
+            if (nf1 > (1L << 20)) return p->fail(FV_ERR_UNSUPPORTED, "spreading grid too large");
+            dg.nf1 = next235even(nf1);
+            dg.M = next235even((long)std::ceil(p->sigma * dg.nf1 - 1e-9));
+            if (dg.M > maxM)
+                return p->fail(FV_ERR_UNSUPPORTED, "FFT length " + std::to_string(dg.M) + " exceeds " +
+                                                       std::to_string(maxM) + " for one-CTA FFT passes");
+            dg.H = (int)std::ceil(dg.M / (2.0 * p->sigma) + 0.5 * w) + 1;
+            dg.B = 2 * dg.H + 1;
+            dg.qscale = p->sigma * X / M_PI;
+            dg.pscale = dg.M / (2.0 * p->sigma * X);
+            dg.D = -g.kappa * p->bcen[i];
+            dg.C = p->C[i];
+            dg.nstages = radix_plan(dg.M, dg.radix);
+            if (dg.nstages < 0 || dg.nstages > FV_MAX_STAGES) return p->fail(FV_ERR_UNSUPPORTED, "bad FFT length");
+            p->nf1_max[i] = std::max(p->nf1_max[i], dg.nf1);
+            p->M_max[i] = std::max(p->M_max[i], dg.M);
+            p->pre_off[(size_t)f * 3 + i] = pre_total;
+            pre_total += dg.nf1;
+            p->tw_off[(size_t)f * 3 + i] = tw_total;
+            tw_total += dg.M;
+        }
+        // buffer sizes (complex elements) for this channel
+        const DimGeom *D = g.dim;
+        size_t grid_c = (size_t)p->n_pol * D[0].nf1 * D[1].nf1 * D[2].nf1;
+        size_t pass1 = (size_t)D[0].B * p->n_pol * D[2].nf1 * D[1].nf1;
+        size_t pass2 = (size_t)D[1].B * D[0].B * p->n_pol * D[2].nf1;
+        size_t pass3 = p->d == 3 ? (size_t)D[2].B * D[1].B * D[0].B * p->n_pol : 0;
+        grid_e = std::max(grid_e, grid_c);
+        bufA_e = std::max(bufA_e, std::max(pass1, pass3));
+        bufB_e = std::max(bufB_e, pass2);
+    }
+    const size_t es = p->elem();
+    const size_t gs = p->precision == FV_FP64 ? sizeof(double) : sizeof(float);
+    CK(cudaMalloc(&p->d_pre, std::max<size_t>(pre_total, 1) * gs));
+    CK(cudaMalloc(&p->d_tw, std::max<size_t>(tw_total, 1) * es));
+    CK(cudaMalloc(&p->d_grid, std::max<size_t>(grid_e, 1) * es));
+    CK(cudaMalloc(&p->d_bufA, std::max<size_t>(bufA_e, 1) * es));
+    CK(cudaMalloc(&p->d_bufB, std::max<size_t>(bufB_e, 1) * es));
+    CK(cudaMalloc(&p->d_Vu, std::max<size_t>((size_t)p->n_u * p->n_pol, 1) * sizeof(cpx<double>)));
+    p->grid_elems = grid_e;
+    p->bufA_elems = bufA_e;
+    p->bufB_elems = bufB_e;
+    for (int f = 0; f < nf; ++f) {
+        for (int i = 0; i < p->d; ++i) {
+            const DimGeom &dg = p->gf[f].dim[i];
+            if (p->precision == FV_FP64) {
+                CK(launch_prescale_table<double>((double *)p->d_pre + p->pre_off[(size_t)f * 3 + i], dg.nf1, dg.M, w,
+                                                 p->beta, p->d_glx, p->d_glw, p->nq, p->stream));
+                CK(launch_twiddles<double>((cpx<double> *)p->d_tw + p->tw_off[(size_t)f * 3 + i], dg.M, p->stream));
+            } else {
+                CK(launch_prescale_table<float>((float *)p->d_pre + p->pre_off[(size_t)f * 3 + i], dg.nf1, dg.M, w,
+                                                p->beta, p->d_glx, p->d_glw, p->nq, p->stream));
+                CK(launch_twiddles<float>((cpx<float> *)p->d_tw + p->tw_off[(size_t)f * 3 + i], dg.M, p->stream));
+            }
+        }
+    }
+    p->ws_bytes = (long long)(pre_total * gs + tw_total * es + (grid_e + bufA_e + bufB_e) * es +
+                              (size_t)p->n_u * p->n_pol * sizeof(cpx<double>));
+    CK(cudaStreamSynchronize(p->stream));
+    return FV_OK;
+}
+
+template <class G>
+static fv_status execute_slices(fv_plan_s *p, char *vis, size_t slice_bytes)
+{
+    const int nf = (int)p->freq.size(), nt = (int)p->lst.size();
+    cpx<G> *grid = (cpx<G> *)p->d_grid;
+    cpx<G> *A = (cpx<G> *)p->d_bufA, *Bb = (cpx<G> *)p->d_bufB;
+    const double es = sizeof(cpx<G>);
+    const double src_bytes = (double)p->n_src * (3 * sizeof(double) + (double)p->n_stokes * (p->flux_fp64 ? 8 : 4));
+    for (int t = 0; t < nt; ++t) {
+        for (int f = 0; f < nf; ++f) {
+            SliceGeom g = p->gf[f];
+            std::memcpy(g.R, &p->Rt[(size_t)t * 9], 9 * sizeof(double));
+            const DimGeom *D = g.dim;
+            const size_t gel = (size_t)p->n_pol * D[0].nf1 * D[1].nf1 * D[2].nf1;
+            CK(prof_begin(p, PC_MEMSET));
+            CK(cudaMemsetAsync(grid, 0, gel * sizeof(cpx<G>), p->stream));
+            CK(prof_end(p, gel * es));
+            CK(prof_begin(p, PC_SPREAD));
+            CK(launch_spread_direct<G>(p->d_e, p->n_src, p->flux, p->flux_fp64, nf, f, g, grid, p->stream));
+            CK(prof_end(p, src_bytes + gel * es));
+            const G *pre = (const G *)p->d_pre;
+            const cpx<G> *tw = (const cpx<G> *)p->d_tw;
+            const size_t o0 = (size_t)f * 3;
+            // pass 1 along x: rows (pol, z, y)
+            long r1 = (long)p->n_pol * D[2].nf1 * D[1].nf1;
+            CK(prof_begin(p, PC_FFT_X));
+            CK(launch_fft_pass<G>(grid, A, r1, D[0], pre + p->pre_off[o0], tw + p->tw_off[o0], p->stream));
+            CK(prof_end(p, (double)r1 * (D[0].nf1 + D[0].B) * es));
+            // pass 2 along y: rows (bx, pol, z)
+            long r2 = (long)D[0].B * p->n_pol * D[2].nf1;
+            CK(prof_begin(p, PC_FFT_Y));
+            CK(launch_fft_pass<G>(A, Bb, r2, D[1], pre + p->pre_off[o0 + 1], tw + p->tw_off[o0 + 1], p->stream));
+            CK(prof_end(p, (double)r2 * (D[1].nf1 + D[1].B) * es));
+            const cpx<G> *band = Bb;
+            if (p->d == 3) {
+                // pass 3 along z: rows (by, bx, pol)
+                long r3 = (long)D[1].B * D[0].B * p->n_pol;
+                CK(prof_begin(p, PC_FFT_Z));
+                CK(launch_fft_pass<G>(Bb, A, r3, D[2], pre + p->pre_off[o0 + 2], tw + p->tw_off[o0 + 2], p->stream));
+                CK(prof_end(p, (double)r3 * (D[2].nf1 + D[2].B) * es));
+                band = A;
+            }
+            double wd = std::pow((double)p->w, p->d);
+            CK(prof_begin(p, PC_INTERP));
+            CK(launch_interp<G>(band, p->d_bu, p->n_u, p->d_dec, g, p->d_Vu, p->stream));
+            CK(prof_end(p, (double)p->n_u * (wd * p->n_pol * es + 4 * sizeof(double) + p->n_pol * 16.0)));
+            char *out = vis + ((size_t)f * nt + t) * slice_bytes;
+            CK(prof_begin(p, PC_SCATTER));
+            CK(launch_scatter(p->d_Vu, p->d_bl2u, p->n_bl, p->n_pol, out, p->precision == FV_FP64, p->stream));
+            CK(prof_end(p, (double)p->n_bl * (4 + p->n_pol * 16.0) + (double)slice_bytes));
+        }
+    }
+    return FV_OK;
+}
+
+extern "C" {
+
+void fv_opts_default(fv_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = FV_FP64;
+    o->eps = 1e-10;
+    o->beam = FV_BEAM_GAUSS;
+    o->beam_param[0] = 10.0 * M_PI / 180.0;
+    o->beam_param[1] = 150e6;
+    o->upsampfac = 2.0;
+    o->device = -1;
+}
+
+int fv_abi_version(void) { return FV_ABI_VERSION; }
+
+const char *fv_last_error(fv_plan_t p) { return p ? p->err.c_str() : g_create_error.c_str(); }
+
+fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
+{
+    if (!out) { g_create_error = "out is NULL"; return FV_ERR_ARG; }
+    *out = nullptr;
+    if (!o) { g_create_error = "opts is NULL"; return FV_ERR_ARG; }
+    auto bad = [](const char *m) { g_create_error = m; return FV_ERR_ARG; };
+    if (o->precision != FV_FP64 && o->precision != FV_MIXED) return bad("precision must be FV_FP64 or FV_MIXED");
+    if (!(o->eps >= 1e-14 && o->eps <= 1e-2)) return bad("eps must be in [1e-14, 1e-2]");
+    if (o->precision == FV_MIXED && o->eps < 1e-7) return bad("FV_MIXED needs eps >= 1e-7");
+    if (o->n_freq < 1 || !o->freq_hz) return bad("need n_freq >= 1 and freq_hz");
+    if (o->n_time < 1 || !o->lst_rad) return bad("need n_time >= 1 and lst_rad");
+    for (int i = 0; i < o->n_freq; ++i)
+        if (!(o->freq_hz[i] > 0.0) || !std::isfinite(o->freq_hz[i])) return bad("frequencies must be finite and > 0");
+    for (int i = 0; i < o->n_time; ++i)
+        if (!std::isfinite(o->lst_rad[i])) return bad("LSTs must be finite");
+    if (!(std::fabs(o->latitude_rad) <= M_PI / 2)) return bad("latitude out of range");
+    if (o->beam < FV_BEAM_GAUSS || o->beam > FV_BEAM_UNIFORM) return bad("unknown beam");
+    if (o->beam == FV_BEAM_GAUSS && !(o->beam_param[0] > 0 && o->beam_param[1] > 0))
+        return bad("Gaussian beam needs FWHM > 0 and reference frequency > 0");
+    if (o->beam == FV_BEAM_AIRY && !(o->beam_param[0] > 0)) return bad("Airy beam needs a diameter > 0");
+    if (o->dims != 0 && o->dims != 2 && o->dims != 3) return bad("dims must be 0, 2 or 3");
+    double sigma = o->upsampfac == 0.0 ? 2.0 : o->upsampfac;
+    if (!(sigma >= 1.25 && sigma <= 3.0)) return bad("upsampfac must be in [1.25, 3]");
+    int w = o->kernel_width;
+    if (w == 0) {
+        if (std::fabs(sigma - 2.0) < 1e-12)
+            w = (int)std::ceil(std::log10(1.0 / o->eps) - 1e-12) + 1;   // Section 2.2 rule at sigma = 2
+        else
+            w = (int)std::ceil(std::log(1.0 / o->eps) / (M_PI * std::sqrt(1.0 - 1.0 / sigma)) - 1e-12) + 1;
+        w = std::max(2, std::min(16, w));
+    }
+    if (w < 2 || w > 16) return bad("kernel_width must be in [2, 16]");
+
+    int ndev = 0;
+    cudaError_t ce = cudaGetDeviceCount(&ndev);
+    if (ce != cudaSuccess || ndev < 1) {
+        g_create_error = std::string("no usable CUDA device: ") + cudaGetErrorString(ce);
+        cudaGetLastError();
+        return FV_ERR_CUDA;
+    }
+    int dev = o->device;
+    if (dev < 0) {
+        if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    }
+    if (dev >= ndev) return bad("device ordinal out of range");
+    if (cudaSetDevice(dev) != cudaSuccess) { g_create_error = "cudaSetDevice failed"; return FV_ERR_CUDA; }
+
+    fv_plan_s *p = new (std::nothrow) fv_plan_s();
+    if (!p) { g_create_error = "host allocation failed"; return FV_ERR_OOM; }
+    p->precision = o->precision;
+    p->eps = o->eps;
+    p->freq.assign(o->freq_hz, o->freq_hz + o->n_freq);
+    p->lst.assign(o->lst_rad, o->lst_rad + o->n_time);
+    p->lat = o->latitude_rad;
+    p->beam.kind = o->beam;
+    p->beam.p0 = o->beam_param[0];
+    p->beam.p1 = o->beam_param[1];
+    p->beam.p2 = o->beam_param[2];
+    p->polarized = o->polarized ? 1 : 0;
+    p->n_pol = p->polarized ? 4 : 1;
+    p->dims_req = o->dims;
+    p->sigma = sigma;
+    p->w = w;
+    p->beta = 2.30 * w * (1.0 - 1.0 / (2.0 * sigma)) / 0.75;   // 2.3 w at sigma = 2 (Section 2.2)
+    p->device = dev;
+    if (o->cuda_stream) {
+        p->stream = (cudaStream_t)o->cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete p;
+            g_create_error = "cudaStreamCreate failed";
+            return FV_ERR_CUDA;
+        }
+        p->own_stream = true;
+    }
+    // rotation matrices, equatorial -> ENU (Section 2.3 rigid rotation)
+    p->Rt.resize((size_t)o->n_time * 9);
+    const double sphi = std::sin(p->lat), cphi = std::cos(p->lat);
+    for (int t = 0; t < o->n_time; ++t) {
+        double sl = std::sin(p->lst[t]), cl = std::cos(p->lst[t]);
+        double *R = &p->Rt[(size_t)t * 9];
+        R[0] = -sl;         R[1] = cl;          R[2] = 0.0;
+        R[3] = -sphi * cl;  R[4] = -sphi * sl;  R[5] = cphi;
+        R[6] = cphi * cl;   R[7] = cphi * sl;   R[8] = sphi;
+    }
+    // quadrature nodes for Phihat: z = sin(pi x / 2) removes the sqrt edge
+    p->nq = 4 * w + 40;
+    std::vector<double> gx, gw;
+    gauss_legendre(p->nq, gx, gw);
+    std::vector<double> zx(p->nq), zw(p->nq);
+    for (int q = 0; q < p->nq; ++q) {
+        double th = 0.5 * M_PI * gx[q];
+        zx[q] = std::sin(th);
+        zw[q] = 0.5 * M_PI * gw[q] * std::cos(th);
+    }
+    fv_status s = FV_OK;
+    if (cudaMalloc(&p->d_glx, p->nq * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&p->d_glw, p->nq * sizeof(double)) != cudaSuccess ||
+        cudaMemcpy(p->d_glx, zx.data(), p->nq * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->d_glw, zw.data(), p->nq * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        s = FV_ERR_CUDA;
+    if (s != FV_OK) {
+        g_create_error = "device set-up failed";
+        fv_destroy(p);
+        return s;
+    }
+    *out = p;
+    return FV_OK;
+}
+
+fv_status fv_set_array(fv_plan_t p, int n_ant, const double *enu_m, int n_bl, const int *pairs)
+{
+    if (!p) return FV_ERR_ARG;
+    if (cudaSetDevice(p->device) != cudaSuccess) return p->fail(FV_ERR_CUDA, "cudaSetDevice failed");
+    if (n_ant < 1 || !enu_m) return p->fail(FV_ERR_ARG, "need n_ant >= 1 and positions");
+    for (long i = 0; i < 3L * n_ant; ++i)
+        if (!std::isfinite(enu_m[i])) return p->fail(FV_ERR_ARG, "non-finite antenna position");
+    std::vector<int> pr;
+    if (pairs) {
+        if (n_bl < 0) return p->fail(FV_ERR_ARG, "n_bl < 0");
+        pr.assign(pairs, pairs + 2L * n_bl);
+        for (int v : pr)
+            if (v < 0 || v >= n_ant) return p->fail(FV_ERR_ARG, "antenna index out of range");
+    } else {
+        for (int i = 0; i < n_ant; ++i)
+            for (int j = i + 1; j < n_ant; ++j) { pr.push_back(i); pr.push_back(j); }
+        n_bl = (int)(pr.size() / 2);
+    }
+    // unique baseline vectors, bit-exact (Fig. 1, panel E)
+    std::map<std::tuple<double, double, double>, int> uid;
+    std::vector<double> bu;
+    std::vector<int> bl2u(n_bl);
+    bool nonplanar = false;
+    for (int b = 0; b < n_bl; ++b) {
+        const double *xi = enu_m + 3 * pr[2 * b], *xj = enu_m + 3 * pr[2 * b + 1];
+        double v[3] = {xi[0] - xj[0], xi[1] - xj[1], xi[2] - xj[2]};
+        if (v[2] != 0.0) nonplanar = true;
+        auto key = std::make_tuple(v[0] + 0.0, v[1] + 0.0, v[2] + 0.0);   // +0.0 folds -0 into 0
+        auto it = uid.find(key);
+        if (it == uid.end()) {
+            int id = (int)(bu.size() / 3);
+            uid.emplace(key, id);
+            bu.insert(bu.end(), v, v + 3);
+            bl2u[b] = id;
+        } else {
+            bl2u[b] = it->second;
+        }
+    }
+    int d = p->dims_req ? p->dims_req : (nonplanar ? 3 : 2);
+    if (d == 2 && nonplanar) return p->fail(FV_ERR_ARG, "dims = 2 requested for a non-coplanar array");
+    p->n_ant = n_ant;
+    p->n_bl = n_bl;
+    p->n_u = (int)(bu.size() / 3);
+    p->d = d;
+    p->bu.swap(bu);
+    p->bl2u.swap(bl2u);
+    for (int i = 0; i < 3; ++i) {
+        double lo = INFINITY, hi = -INFINITY;
+        for (int u = 0; u < p->n_u; ++u) { lo = std::min(lo, p->bu[3 * u + i]); hi = std::max(hi, p->bu[3 * u + i]); }
+        if (p->n_u == 0) lo = hi = 0.0;
+        p->bcen[i] = 0.5 * (lo + hi);
+        p->bhalf[i] = 0.5 * (hi - lo);
+    }
+    dfree_t(p->d_bu);
+    dfree_t(p->d_dec);
+    dfree_t(p->d_bl2u);
+    const size_t nu = std::max(p->n_u, 1), nb = std::max(p->n_bl, 1);
+    CK(cudaMalloc(&p->d_bu, nu * 3 * sizeof(double)));
+    CK(cudaMalloc(&p->d_dec, nu * sizeof(double)));
+    CK(cudaMalloc(&p->d_bl2u, nb * sizeof(int)));
+    if (p->n_u) CK(cudaMemcpyAsync(p->d_bu, p->bu.data(), (size_t)p->n_u * 3 * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    if (p->n_bl) CK(cudaMemcpyAsync(p->d_bl2u, p->bl2u.data(), (size_t)p->n_bl * sizeof(int), cudaMemcpyHostToDevice, p->stream));
+    CK(launch_target_deconv(p->d_bu, p->n_u, p->d, p->bcen, p->bhalf, p->w, p->beta, p->sigma, p->d_glx, p->d_glw,
+                            p->nq, p->d_dec, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    p->have_array = true;
+    if (p->have_sky) return prepare(p);
+    return FV_OK;
+}
+
+fv_status fv_set_sky(fv_plan_t p, long n_src, const double *ra_rad, const double *dec_rad, int n_stokes,
+                     const void *flux, int flux_is_fp64, int flux_on_device)
+{
+    if (!p) return FV_ERR_ARG;
+    if (cudaSetDevice(p->device) != cudaSuccess) return p->fail(FV_ERR_CUDA, "cudaSetDevice failed");
+    if (!p->have_array) return p->fail(FV_ERR_STATE, "fv_set_array must come before fv_set_sky");
+    if (n_src < 0) return p->fail(FV_ERR_ARG, "n_src < 0");
+    if (n_stokes != (p->polarized ? 4 : 1) && !(n_stokes == 4 && !p->polarized))
+        return p->fail(FV_ERR_ARG, p->polarized ? "polarised plan needs n_stokes = 4" : "n_stokes must be 1 or 4");
+    if (n_src > 0 && (!ra_rad || !dec_rad || !flux)) return p->fail(FV_ERR_ARG, "NULL sky array");
+    for (long i = 0; i < n_src; ++i)
+        if (!std::isfinite(ra_rad[i]) || !std::isfinite(dec_rad[i]))
+            return p->fail(FV_ERR_ARG, "non-finite source coordinate");
+    p->have_sky = false;
+    dfree_t(p->d_e);
+    dfree(p->d_flux_owned);
+    p->flux = nullptr;
+    p->n_src = n_src;
+    p->n_stokes = n_stokes;
+    p->flux_fp64 = flux_is_fp64 ? 1 : 0;
+    const size_t ns = std::max<long>(n_src, 1);
+    CK(cudaMalloc(&p->d_e, ns * 3 * sizeof(double)));
+    double *d_tmp = nullptr;
+    CK(cudaMalloc(&d_tmp, ns * 2 * sizeof(double)));
+    if (n_src) {
+        CK(cudaMemcpyAsync(d_tmp, ra_rad, n_src * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+        CK(cudaMemcpyAsync(d_tmp + ns, dec_rad, n_src * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    }
+    CK(launch_radec_to_unit(d_tmp, d_tmp + ns, n_src, p->d_e, p->stream));
+    const size_t fbytes = (size_t)n_stokes * n_src * p->freq.size() * (p->flux_fp64 ? 8 : 4);
+    if (flux_on_device) {
+        p->flux = flux;
+    } else if (n_src) {
+        CK(cudaMalloc(&p->d_flux_owned, fbytes));
+        CK(cudaMemcpyAsync(p->d_flux_owned, flux, fbytes, cudaMemcpyHostToDevice, p->stream));
+        p->flux = p->d_flux_owned;
+    }
+    // source extents over all times (visible directions only)
+    const int nb = 304;
+    double *d_R = nullptr, *d_ext = nullptr;
+    CK(cudaMalloc(&d_R, p->Rt.size() * sizeof(double)));
+    CK(cudaMalloc(&d_ext, (size_t)nb * 6 * sizeof(double)));
+    CK(cudaMemcpyAsync(d_R, p->Rt.data(), p->Rt.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    CK(launch_source_extents(p->d_e, n_src, d_R, (int)p->lst.size(), d_ext, nb, p->stream));
+    std::vector<double> ext((size_t)nb * 6);
+    CK(cudaMemcpyAsync(ext.data(), d_ext, ext.size() * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    cudaFree(d_R);
+    cudaFree(d_ext);
+    cudaFree(d_tmp);
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = 0; b < nb; ++b)
+        for (int i = 0; i < 3; ++i) {
+            lo[i] = std::min(lo[i], ext[(size_t)b * 6 + i]);
+            hi[i] = std::max(hi[i], ext[(size_t)b * 6 + 3 + i]);
+        }
+    p->any_visible = std::isfinite(lo[0]);
+    for (int i = 0; i < 3; ++i) {
+        if (p->any_visible) {
+            p->C[i] = 0.5 * (lo[i] + hi[i]);
+            p->S[i] = 0.5 * (hi[i] - lo[i]);
+        } else {
+            p->C[i] = 0.0;
+            p->S[i] = 0.0;
+        }
+    }
+    fv_status s = prepare(p);
+    if (s != FV_OK) return s;
+    p->have_sky = true;
+    return FV_OK;
+}
+
+fv_status fv_execute(fv_plan_t p, void *vis, int vis_on_device)
+{
+    if (!p) return FV_ERR_ARG;
+    if (!vis) return p->fail(FV_ERR_ARG, "vis is NULL");
+    if (!p->have_array || !p->have_sky) return p->fail(FV_ERR_STATE, "fv_set_array and fv_set_sky must come first");
+    if (cudaSetDevice(p->device) != cudaSuccess) return p->fail(FV_ERR_CUDA, "cudaSetDevice failed");
+    const size_t cb = p->precision == FV_FP64 ? 16 : 8;
+    const size_t slice_bytes = (size_t)p->n_bl * p->n_pol * cb;
+    const size_t total = slice_bytes * p->freq.size() * p->lst.size();
+    char *dst = (char *)vis;
+    void *tmp = nullptr;
+    if (!vis_on_device) {
+        CK(cudaMallocAsync(&tmp, std::max<size_t>(total, 1), p->stream));
+        dst = (char *)tmp;
+    }
+    fv_status s;
+    if (!p->any_visible || p->n_src == 0) {
+        CK(cudaMemsetAsync(dst, 0, total, p->stream));
+        s = FV_OK;
+    } else {
+        s = p->precision == FV_FP64 ? execute_slices<double>(p, dst, slice_bytes)
+                                    : execute_slices<float>(p, dst, slice_bytes);
+    }
+    if (!vis_on_device) {
+        if (s == FV_OK) CK(cudaMemcpyAsync(vis, tmp, total, cudaMemcpyDeviceToHost, p->stream));
+        cudaFreeAsync(tmp, p->stream);
+        CK(cudaStreamSynchronize(p->stream));
+    }
+    return s;
+}
+
+fv_status fv_destroy(fv_plan_t p)
+{
+    if (!p) return FV_OK;
+    cudaSetDevice(p->device);
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    free_geometry(p);
+    dfree_t(p->d_glx);
+    dfree_t(p->d_glw);
+    dfree_t(p->d_bu);
+    dfree_t(p->d_dec);
+    dfree_t(p->d_bl2u);
+    dfree_t(p->d_e);
+    dfree(p->d_flux_owned);
+    for (cudaEvent_t ev : p->ev_pool) cudaEventDestroy(ev);
+    if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+    delete p;
+    return FV_OK;
+}
+
+fv_status fv_get_info(fv_plan_t p, fv_info *info)
+{
+    if (!p || !info) return FV_ERR_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->dims = p->d;
+    info->kernel_width = p->w;
+    info->beta = p->beta;
+    info->upsampfac = p->sigma;
+    info->n_unique = p->n_u;
+    info->n_bl = p->n_bl;
+    info->n_src = p->n_src;
+    for (int i = 0; i < 3; ++i) {
+        info->nf1_max[i] = p->nf1_max[i];
+        info->nf2_max[i] = p->M_max[i];
+        info->src_centre[i] = p->C[i];
+        info->src_halfwidth[i] = p->S[i];
+    }
+    info->workspace_bytes = p->ws_bytes;
+    return FV_OK;
+}
+
+fv_status fv_profile_enable(fv_plan_t p, int enable)
+{
+    if (!p) return FV_ERR_ARG;
+    if (cudaSetDevice(p->device) != cudaSuccess) return p->fail(FV_ERR_CUDA, "cudaSetDevice failed");
+    if (enable && p->ev_pool.empty()) {
+        p->ev_pool.resize(8192);
+        for (auto &ev : p->ev_pool) CK(cudaEventCreate(&ev));
+    }
+    if (!enable) CK(prof_harvest(p));
+    p->prof_on = enable != 0;
+    return FV_OK;
+}
+
+fv_status fv_profile_read(fv_plan_t p, fv_profile_data *out)
+{
+    if (!p || !out) return FV_ERR_ARG;
+    if (cudaSetDevice(p->device) != cudaSuccess) return p->fail(FV_ERR_CUDA, "cudaSetDevice failed");
+    CK(prof_harvest(p));
+    for (int c = 0; c < FV_PROFILE_CLASSES; ++c) {
+        out->name[c] = k_prof_names[c];
+        out->total_ms[c] = p->prof_ms[c];
+        out->launches[c] = p->prof_launches[c];
+        out->bytes[c] = p->prof_bytes[c];
+        p->prof_ms[c] = 0.0;
+        p->prof_launches[c] = 0;
+        p->prof_bytes[c] = 0.0;
+    }
+    return FV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative L2 over all outputs of a case): 1e-9 for FV_FP64,
+2e-5 for FV_MIXED (FP32 spread/FFT/interp with FP64 phases).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import OracleProblem, oracle_vis, rel_l2
+from paper_2506_02130_gb300 import fv, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {fv.FV_FP64: 1e-9, fv.FV_MIXED: 2e-5}
+EPS = {fv.FV_FP64: 1e-11, fv.FV_MIXED: 1e-6}
+
+
+def run_gpu(prob, precision, eps=None, pairs=None, **kw):
+    p = fv.Plan.create(prob.freqs_hz, prob.lsts_rad, prob.latitude_rad, prob.beam, prob.beam_param, precision,
+                       EPS[precision] if eps is None else eps, prob.polarized, **kw)
+    p.set_array(prob.ant_enu, prob.pairs if pairs is None else pairs)
+    p.set_sky(prob.sky.ra, prob.sky.dec, prob.sky.flux)
+    out = p.run()
+    info = p.info()
+    p.close()
+    return out, info
+
+
+def oracle(prob, pairs=None, mode="factored"):
+    return oracle_vis(OracleProblem.from_workload(prob, pairs=pairs), mode)
+
+
+def small_3d(seed=7, n_point=1500, nside=8, n_chan=3, n_time=2, radius=3):
+    return W.config_hex127(seed=seed, n_chan=n_chan, n_time=n_time, n_point=n_point, nside=nside, radius=radius)
+
+
+def small_pol(seed=8, n_chan=2, n_time=2):
+    return W.config_hex350_pol(seed=seed, n_chan=n_chan, n_time=n_time, n_point=400, nside=8, n_keep=None,
+                               radius=2)
+
+
+@pytest.mark.parametrize("precision", [fv.FV_FP64, fv.FV_MIXED])
+def test_hex37_one_slice(precision):
+    prob = W.config_small(seed=0, n_src=1000)
+    out, info = run_gpu(prob, precision, eps=1e-10 if precision == fv.FV_FP64 else 1e-6)
+    assert info["dims"] == 2
+    err = rel_l2(out, oracle(prob, mode="literal"))
+    assert err <= TOL[precision], err
+
+
+@pytest.mark.parametrize("precision", [fv.FV_FP64, fv.FV_MIXED])
+def test_non_coplanar_multichannel_point_plus_diffuse(precision):
+    prob = small_3d()
+    out, info = run_gpu(prob, precision)
+    assert info["dims"] == 3
+    ref = oracle(prob)
+    err = rel_l2(out, ref)
+    assert err <= TOL[precision], err
+    # every slice on its own, too
+    for f in range(out.shape[0]):
+        for t in range(out.shape[1]):
+            assert rel_l2(out[f, t], ref[f, t]) <= TOL[precision] * 3
+
+
+@pytest.mark.parametrize("precision", [fv.FV_FP64, fv.FV_MIXED])
+def test_polarised_airy_jones(precision):
+    prob = small_pol()
+    out, info = run_gpu(prob, precision)
+    ref = oracle(prob)
+    assert out.shape[-1] == 4
+    for p in range(4):
+        assert rel_l2(out[..., p], ref[..., p]) <= TOL[precision] * 2, p
+
+
+@pytest.mark.parametrize("precision", [fv.FV_FP64, fv.FV_MIXED])
+@pytest.mark.parametrize("sigma", [1.25, 2.0])
+def test_upsampling_factor(precision, sigma):
+    prob = small_3d(seed=9, n_chan=2, n_time=1)
+    out, _ = run_gpu(prob, precision, upsampfac=sigma)
+    assert rel_l2(out, oracle(prob)) <= TOL[precision]
+
+
+def test_single_source_error_within_eps():
+    prob = W.config_small(seed=1, n_src=1)
+    prob.beam = "uniform"
+    for eps in (1e-6, 1e-9, 1e-12):
+        out, _ = run_gpu(prob, fv.FV_FP64, eps=eps)
+        ref = oracle(prob, mode="literal")
+        assert np.abs(out - ref).max() <= 10 * eps * np.abs(prob.sky.flux).sum()
+
+
+def test_empty_and_invisible_skies_give_zeros():
+    prob = W.config_small(seed=2, n_src=5)
+    prob.sky = W.Sky(np.zeros(0), np.zeros(0), np.zeros((1, 0, 1)))
+    out, _ = run_gpu(prob, fv.FV_FP64)
+    assert np.all(out == 0)
+    prob.sky = W.Sky(np.array([0.1, 2.0]), np.array([np.pi / 2, np.pi / 2 - 1e-3]), np.ones((1, 2, 1)))
+    out, _ = run_gpu(prob, fv.FV_MIXED)     # celestial north pole region: below the horizon at -30.7 deg
+    assert np.all(out == 0)
+
+
+@pytest.mark.parametrize("precision", [fv.FV_FP64, fv.FV_MIXED])
+def test_degenerate_geometries(precision):
+    rng = np.random.default_rng(4)
+    base = W.config_small(seed=4, n_src=300)
+    # east-west line: every baseline has b_north = 0 (zero target extent in y)
+    base.ant_enu = np.array([[14.6 * k, 0.0, 0.0] for k in range(5)])
+    base.pairs = W.cross_pairs(5)
+    out, _ = run_gpu(base, precision)
+    assert rel_l2(out, oracle(base, mode="literal")) <= TOL[precision]
+    # zero spacings and both orientations in the pair list
+    pairs = np.array([[0, 0], [1, 1], [0, 3], [3, 0], [2, 4]], np.int32)
+    out, _ = run_gpu(base, precision, pairs=pairs)
+    ref = oracle(base, pairs=pairs, mode="literal")
+    assert rel_l2(out, ref) <= TOL[precision]
+    # a single baseline
+    pairs = np.array([[1, 2]], np.int32)
+    out, _ = run_gpu(base, precision, pairs=pairs)
+    assert rel_l2(out, oracle(base, pairs=pairs, mode="literal")) <= TOL[precision]
+
+
+def test_forced_3d_on_coplanar_array_and_redundancy():
+    prob = W.config_small(seed=5, n_src=500)
+    out2, i2 = run_gpu(prob, fv.FV_FP64)
+    out3, i3 = run_gpu(prob, fv.FV_FP64, dims=3)
+    assert i2["dims"] == 2 and i3["dims"] == 3
+    ref = oracle(prob, mode="literal")
+    assert rel_l2(out3, ref) <= 1e-9 and rel_l2(out2, ref) <= 1e-9
+    # redundant pairs share one target: identical outputs
+    assert i2["n_unique"] < i2["n_bl"]
+    b = prob.ant_enu[prob.pairs[:, 0]] - prob.ant_enu[prob.pairs[:, 1]]
+    _, first, inv = np.unique(b, axis=0, return_index=True, return_inverse=True)
+    inv = inv.ravel()
+    np.testing.assert_array_equal(out2[0, 0, :, 0], out2[0, 0, first[inv], 0])
+
+
+def test_device_buffers_and_translation_invariance():
+    torch = pytest.importorskip("torch")
+    prob = small_3d(seed=10, n_chan=2, n_time=2, nside=0, n_point=800)
+    ref = oracle(prob)
+    p = fv.Plan.from_problem(prob, precision=fv.FV_MIXED, eps=1e-6)
+    flux = torch.tensor(prob.sky.flux, dtype=torch.float32, device="cuda")
+    p.set_sky(prob.sky.ra, prob.sky.dec, flux)
+    out = torch.zeros(p.out_shape, dtype=torch.complex64, device="cuda")
+    p.run(out)
+    torch.cuda.synchronize()
+    assert rel_l2(out.cpu().numpy(), ref) <= 2e-5
+    # shifting every antenna by the same vector changes nothing
+    p.set_array(prob.ant_enu + np.array([31.0, -12.5, 0.7]), prob.pairs)
+    out2 = p.run()
+    p.close()
+    assert rel_l2(out2, ref) <= 2e-5
+
+
+def test_linearity_and_frequency_baseline_scaling():
+    prob = small_3d(seed=11, n_chan=1, n_time=1, nside=0, n_point=600)
+    prob.beam = "uniform"
+    a, _ = run_gpu(prob, fv.FV_FP64)
+    prob2 = small_3d(seed=11, n_chan=1, n_time=1, nside=0, n_point=600)
+    prob2.beam = "uniform"
+    prob2.sky.flux = 2.5 * prob2.sky.flux
+    b, _ = run_gpu(prob2, fv.FV_FP64)
+    assert rel_l2(b, 2.5 * a) <= 1e-9
+    prob2.sky.flux = prob.sky.flux
+    prob2.ant_enu = 2 * prob.ant_enu
+    prob2.freqs_hz = prob.freqs_hz / 2
+    c, _ = run_gpu(prob2, fv.FV_FP64)
+    assert rel_l2(c, a) <= 1e-9
