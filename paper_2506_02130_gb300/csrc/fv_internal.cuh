@@ -19,6 +19,7 @@
 
 #define FV_C_LIGHT 299792458.0
 #define FV_MAX_STAGES 24
+#define FV_ZDIRECT_MAX 16
 
 namespace fv {
 
@@ -110,6 +111,13 @@ cudaError_t launch_fft_pass(const cpx<G> *in, cpx<G> *out, long rows, const DimG
 template <class G>
 cudaError_t launch_interp(const cpx<G> *band, const double *bu, int n_u, const double *dec, const SliceGeom &g,
                           cpx<double> *Vu, cudaStream_t st);
+
+// Same, reading the band after the x and y passes only ([b_y][b_x][pol][l_z]),
+// with the z axis summed directly (nf1_z <= 16).
+template <class G>
+cudaError_t launch_interp_zdirect(const cpx<G> *band, const double *bu, int n_u, const double *dec,
+                                  const SliceGeom &g, const G *prez, const cpx<G> *twz, cpx<double> *Vu,
+                                  cudaStream_t st);
 
 // vis slice [n_bl][n_pol] (complex128 or complex64) <- Vu[bl2u[bl]].
 cudaError_t launch_scatter(const cpx<double> *Vu, const int *bl2u, int n_bl, int n_pol, void *out,

@@ -332,6 +332,98 @@ cudaError_t launch_interp(const cpx<G> *band, const double *bu, int n_u, const d
     return cudaGetLastError();
 }
 
+// Interpolation with the z axis evaluated directly (3-D transforms whose z
+// grid is short, and 2-D transforms with Nz = 1).  The z FFT followed by the
+// z interpolation of one target,
+//     sum_{m_z in footprint} phi((2/w)(p_z - m_z)) sum_{l_z} a_{l_z} e^{2 pi i l_z m_z / M_z},
+// is regrouped exactly as sum_{l_z} a_{l_z} K(l_z) with
+//     K(l_z) = sum_{m_z} phi((2/w)(p_z - m_z)) e^{2 pi i l_z m_z / M_z},
+// so the band after the x and y passes, [b_y][b_x][pol][l_z], is read with
+// the z prescale folded into K.  One warp per target: the lanes split the
+// w x w footprint in (y, x) and reduce with shuffles.
+template <class G>
+__global__ void __launch_bounds__(256) k_interp_zdirect(const cpx<G> *__restrict__ band, const double *__restrict__ bu,
+                                                        int n_u, const double *__restrict__ dec, SliceGeom g,
+                                                        const G *__restrict__ prez, const cpx<G> *__restrict__ twz,
+                                                        cpx<double> *__restrict__ Vu)
+{
+    const int lane = threadIdx.x & 31;
+    const int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (u >= n_u) return;
+    const int w = g.w;
+    const G two_over_w = (G)(2.0 / w);
+    const G beta = (G)g.beta;
+    double x[3] = {0.0, 0.0, 0.0};
+    G fr[3];
+    int m0[3] = {0, 0, 0};
+    for (int i = 0; i < g.d; ++i) {
+        x[i] = -g.kappa * bu[3 * u + i];
+        double p = (x[i] - g.dim[i].D) * g.dim[i].pscale;
+        double m = ceil(p - 0.5 * w);
+        m0[i] = (int)m;
+        fr[i] = (G)(p - m);
+    }
+    const int Nz = g.d == 3 ? g.dim[2].nf1 : 1;
+    cpx<G> K[16];
+    if (g.d == 3) {
+        const int Mz = g.dim[2].M;
+        for (int lz = 0; lz < Nz; ++lz) {
+            const int lc = lz - Nz / 2;
+            cpx<G> acc = cmk<G>((G)0, (G)0);
+            for (int jz = 0; jz < w; ++jz) {
+                G wt = es_kernel(two_over_w * (fr[2] - (G)jz), beta);
+                int e = (lc * (m0[2] + jz)) % Mz;
+                if (e < 0) e += Mz;
+                acc = cadd(acc, cscale(twz[e], wt));
+            }
+            K[lz] = cscale(acc, prez[lz]);
+        }
+    } else {
+        K[0] = cmk<G>((G)1, (G)0);
+    }
+    const int np = g.n_pol;
+    const int Bx = g.dim[0].B;
+    const int bx0 = m0[0] + g.dim[0].H, by0 = m0[1] + g.dim[1].H;
+    G acc[8];
+    for (int k = 0; k < 2 * np; ++k) acc[k] = (G)0;
+    for (int idx = lane; idx < w * w; idx += 32) {
+        const int jy = idx / w, jx = idx - jy * w;
+        const G wt = es_kernel(two_over_w * (fr[1] - (G)jy), beta) * es_kernel(two_over_w * (fr[0] - (G)jx), beta);
+        const cpx<G> *cell = band + (((size_t)(by0 + jy) * Bx + (bx0 + jx)) * np) * Nz;
+        for (int p = 0; p < np; ++p) {
+            cpx<G> s = cmk<G>((G)0, (G)0);
+            for (int lz = 0; lz < Nz; ++lz) s = cadd(s, cmul(cell[p * Nz + lz], K[lz]));
+            acc[2 * p] += wt * s.x;
+            acc[2 * p + 1] += wt * s.y;
+        }
+    }
+    for (int k = 0; k < 2 * np; ++k)
+        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+    if (lane == 0) {
+        double ph = 0.0;
+        for (int i = 0; i < g.d; ++i) ph += x[i] * g.dim[i].C;
+        double sp, cp;
+        sincos(ph, &sp, &cp);
+        const double dk = dec[u];
+        for (int p = 0; p < np; ++p) {
+            cpx<double> v = cmk<double>((double)acc[2 * p] * dk, (double)acc[2 * p + 1] * dk);
+            Vu[(size_t)u * np + p] = cmul(v, cmk<double>(cp, sp));
+        }
+    }
+}
+
+template <class G>
+cudaError_t launch_interp_zdirect(const cpx<G> *band, const double *bu, int n_u, const double *dec,
+                                  const SliceGeom &g, const G *prez, const cpx<G> *twz, cpx<double> *Vu,
+                                  cudaStream_t st)
+{
+    if (n_u <= 0) return cudaSuccess;
+    if (g.d == 3 && g.dim[2].nf1 > 16) return cudaErrorInvalidValue;
+    long threads = (long)n_u * 32;
+    k_interp_zdirect<G><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(band, bu, n_u, dec, g, prez, twz, Vu);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ output
 __global__ void k_scatter(const cpx<double> *__restrict__ Vu, const int *__restrict__ bl2u, int n_bl, int n_pol,
                           void *out, int out_fp64)
@@ -366,6 +458,12 @@ template cudaError_t launch_spread_direct<float>(const double *, long, const voi
                                                  const SliceGeom &, cpx<float> *, cudaStream_t);
 template cudaError_t launch_interp<double>(const cpx<double> *, const double *, int, const double *,
                                            const SliceGeom &, cpx<double> *, cudaStream_t);
+template cudaError_t launch_interp_zdirect<double>(const cpx<double> *, const double *, int, const double *,
+                                                   const SliceGeom &, const double *, const cpx<double> *,
+                                                   cpx<double> *, cudaStream_t);
+template cudaError_t launch_interp_zdirect<float>(const cpx<float> *, const double *, int, const double *,
+                                                  const SliceGeom &, const float *, const cpx<float> *,
+                                                  cpx<double> *, cudaStream_t);
 template cudaError_t launch_interp<float>(const cpx<float> *, const double *, int, const double *,
                                           const SliceGeom &, cpx<double> *, cudaStream_t);
 

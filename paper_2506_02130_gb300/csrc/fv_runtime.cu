@@ -4,7 +4,7 @@
 // after it): source centre C and half-extent S from the visible directions
 // over all times, target centre D and half-extent X from the baselines per
 // channel, grid sizes nf1 >= 2 sigma X S / pi + w (rounded up to an even
-// 2^a 3^b 5^c, at least 2w), FFT lengths M = sigma nf1, deconvolution tables.
+// 2^a 3^b 5^c, at least w + 2), FFT lengths M = sigma nf1, deconvolution tables.
 // Execution: per (time, channel) slice, spread -> d FFT passes -> interpolate
 // -> scatter, all enqueued on the plan's stream.
 #include "../../include/fv.h"
@@ -38,10 +38,11 @@ int next235even(long n)
     }
 }
 
-// Stockham stage radices for M = 2^a 3^b 5^c (fours first).
+// Stockham stage radices for M = 2^a 3^b 5^c (eights first).
 int radix_plan(int M, int *rad)
 {
     int n = 0;
+    while (M % 8 == 0) { rad[n++] = 8; M /= 8; }
     while (M % 4 == 0) { rad[n++] = 4; M /= 4; }
     while (M % 2 == 0) { rad[n++] = 2; M /= 2; }
     while (M % 3 == 0) { rad[n++] = 3; M /= 3; }
@@ -257,7 +258,7 @@ static fv_status prepare(fv_plan_s *p)
             if (!(X > 0.0)) X = S > 0.0 ? 1.0 / S : 1.0;
             double need = 2.0 * p->sigma * X * S / M_PI + w;
             long nf1 = (long)std::ceil(need);
-            if (nf1 < 2 * w) nf1 = 2 * w;
+            if (nf1 < w + 2) nf1 = w + 2;     // Eq. 5 is the requirement; no 2w floor is needed
             if (nf1 > (1L << 20)) return p->fail(FV_ERR_UNSUPPORTED, "spreading grid too large");
             dg.nf1 = next235even(nf1);
             dg.M = next235even((long)std::ceil(p->sigma * dg.nf1 - 1e-9));
@@ -354,6 +355,14 @@ static fv_status execute_slices(fv_plan_s *p, char *vis, size_t slice_bytes)
             CK(launch_fft_pass<G>(A, Bb, r2, D[1], pre + p->pre_off[o0 + 1], tw + p->tw_off[o0 + 1], p->stream));
             CK(prof_end(p, (double)r2 * (D[1].nf1 + D[1].B) * es));
             const cpx<G> *band = Bb;
+            if (p->d == 2 || D[2].nf1 <= FV_ZDIRECT_MAX) {
+                // z (if any) summed directly inside the interpolation: no z pass
+                const double wd = (double)p->w * p->w * D[2].nf1;
+                CK(prof_begin(p, PC_INTERP));
+                CK(launch_interp_zdirect<G>(Bb, p->d_bu, p->n_u, p->d_dec, g, pre + p->pre_off[o0 + 2],
+                                            tw + p->tw_off[o0 + 2], p->d_Vu, p->stream));
+                CK(prof_end(p, (double)p->n_u * (wd * p->n_pol * es + 4 * sizeof(double) + p->n_pol * 16.0)));
+            } else {
             if (p->d == 3) {
                 // pass 3 along z: rows (by, bx, pol)
                 long r3 = (long)D[1].B * D[0].B * p->n_pol;
@@ -366,6 +375,7 @@ static fv_status execute_slices(fv_plan_s *p, char *vis, size_t slice_bytes)
             CK(prof_begin(p, PC_INTERP));
             CK(launch_interp<G>(band, p->d_bu, p->n_u, p->d_dec, g, p->d_Vu, p->stream));
             CK(prof_end(p, (double)p->n_u * (wd * p->n_pol * es + 4 * sizeof(double) + p->n_pol * 16.0)));
+            }
             char *out = vis + ((size_t)f * nt + t) * slice_bytes;
             CK(prof_begin(p, PC_SCATTER));
             CK(launch_scatter(p->d_Vu, p->d_bl2u, p->n_bl, p->n_pol, out, p->precision == FV_FP64, p->stream));

@@ -82,13 +82,27 @@ def test_upsampling_factor(precision, sigma):
     assert rel_l2(out, oracle(prob)) <= TOL[precision]
 
 
+def _edge_amplification(w, beta):
+    """Both deconvolutions divide by the kernel transform; at the edge of the
+    target band (k = w pi / (2 sigma), sigma = 2) each one amplifies the
+    kernel's aliasing error by Phihat(0) / Phihat(k).  Independent numpy
+    quadrature (z = sin(theta) substitution, 200 nodes)."""
+    x, wq = np.polynomial.legendre.leggauss(200)
+    z = np.sin(np.pi / 2 * x)
+    ww = np.pi / 2 * wq * np.cos(np.pi / 2 * x)
+    phi = np.exp(beta * (np.sqrt(np.maximum(1 - z * z, 0)) - 1))
+    ph = lambda k: (ww * phi * np.cos(k * z)).sum()
+    return (ph(0.0) / ph(w * np.pi / 4)) ** 2
+
+
 def test_single_source_error_within_eps():
     prob = W.config_small(seed=1, n_src=1)
     prob.beam = "uniform"
     for eps in (1e-6, 1e-9, 1e-12):
-        out, _ = run_gpu(prob, fv.FV_FP64, eps=eps)
+        out, info = run_gpu(prob, fv.FV_FP64, eps=eps)
         ref = oracle(prob, mode="literal")
-        assert np.abs(out - ref).max() <= 10 * eps * np.abs(prob.sky.flux).sum()
+        amp = _edge_amplification(info["kernel_width"], info["beta"])
+        assert np.abs(out - ref).max() <= 2 * amp * eps * np.abs(prob.sky.flux).sum()
 
 
 def test_empty_and_invisible_skies_give_zeros():
