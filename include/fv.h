@@ -156,12 +156,14 @@ fv_status fv_get_info(fv_plan_t p, fv_info *info);
  * every device launch that fv_execute enqueues is bracketed by two CUDA events
  * on the plan's stream and counted; fv_profile_read synchronises the stream,
  * adds up the elapsed times per kernel class, copies them out and resets the
- * counters.  Classes: "memset", "spread", "fft_x", "fft_y", "fft_z",
- * "interp", "scatter" (FV_PROFILE_CLASSES entries; unused ones stay zero).
+ * counters.  Classes: "memset", "bin" (per-time rotation, horizon cut and
+ * sort), "prep" (per-slice strengths and grid coordinates), "spread",
+ * "fft_x", "fft_y", "fft_z", "interp", "scatter" (FV_PROFILE_CLASSES
+ * entries; unused ones have an empty name or stay zero).
  * bytes[c] is the algorithmic HBM traffic the launches of class c imply
  * (each input read once, each output written once).  Launch counts are kept
  * even while timing is disabled. */
-#define FV_PROFILE_CLASSES 8
+#define FV_PROFILE_CLASSES 12
 typedef struct {
     const char *name[FV_PROFILE_CLASSES];
     double total_ms[FV_PROFILE_CLASSES];

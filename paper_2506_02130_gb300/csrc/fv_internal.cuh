@@ -54,6 +54,19 @@ struct BeamParams {
     double p0, p1, p2;
 };
 
+// Per-time binning geometry: bins are tiles of the top (highest-frequency)
+// channel's grid in (x, y).
+struct TimeBin {
+    double R[9];            // equatorial -> ENU rotation at this time
+    double C[3];            // source centre
+    double qscale_top[3];   // grid scale of the top channel
+    int nf1_top[3];
+    int T[2];               // tile (= bin) size in cells
+    int nbx, nby;           // bins per axis
+};
+
+#define FV_SPREAD_SMEM_MAX (96 * 1024)
+
 // Everything a slice's kernels need, passed by value.
 struct SliceGeom {
     double R[9];        // equatorial -> ENU rotation at this time (row major)
@@ -99,6 +112,24 @@ cudaError_t launch_target_deconv(const double *bu, int n_u, int d, const double 
 template <class G>
 cudaError_t launch_spread_direct(const double *e, long n_src, const void *flux, int flux_fp64, int n_freq,
                                  int f, const SliceGeom &g, cpx<G> *grid, cudaStream_t st);
+
+// Per time: rotate, horizon cut and counting sort of the visible sources by
+// top-channel tile.  sdir[3][n_src] and sidx[n_src] hold the sorted visible
+// directions and source indices; offsets[nb] is the visible count.
+cudaError_t launch_time_binning(const double *e, long n_src, const TimeBin &tb, int *bin_of, int *counts,
+                                int *offsets, int *cursor, double *sdir, int *sidx, cudaStream_t st);
+
+// Per slice: strengths with prephase and split grid coordinates of the sorted sources.
+template <class G>
+cudaError_t launch_prep(const double *sdir, const int *sidx, const int *nv_ptr, long n_src, const void *flux,
+                        int flux_fp64, int n_freq, int f, const SliceGeom &g, int *cell, G *frac, cpx<G> *cs,
+                        cudaStream_t st);
+
+// Per slice: tiled spreading; writes every cell of grid [n_pol][nz][ny][nx].
+template <class G>
+cudaError_t launch_spread_tile(const int *offsets, const int *cell, const G *frac, const cpx<G> *cs, long n_src,
+                               const SliceGeom &g, const TimeBin &tb, double r0, double r1, cpx<G> *grid,
+                               cudaStream_t st);
 
 // One FFT pass: rows of length N (input rows contiguous), prescale by pre[l],
 // zero-pad to M, FFT with e^{+2 pi i l m / M}, write band outputs transposed:

@@ -128,6 +128,15 @@ struct fv_plan_s {
     void *d_grid = nullptr, *d_bufA = nullptr, *d_bufB = nullptr;
     cpx<double> *d_Vu = nullptr;
     size_t grid_elems = 0, bufA_elems = 0, bufB_elems = 0;
+    // binned spreading
+    bool tiled = false;
+    int T[2] = {32, 32}, nbx = 1, nby = 1, f_top = 0;
+    double qscale_top[3] = {0, 0, 0};
+    int nf1_top[3] = {1, 1, 1};
+    int *d_bin_of = nullptr, *d_counts = nullptr, *d_offsets = nullptr, *d_cursor = nullptr, *d_sidx = nullptr;
+    int *d_cell = nullptr;
+    double *d_sdir = nullptr;
+    void *d_frac = nullptr, *d_cs = nullptr;
     long long ws_bytes = 0;
     int nf1_max[3] = {1, 1, 1}, M_max[3] = {1, 1, 1};
 
@@ -168,9 +177,9 @@ template <class T> static void dfree_t(T *&ptr)
     ptr = nullptr;
 }
 
-static const char *k_prof_names[FV_PROFILE_CLASSES] = {"memset", "spread", "fft_x", "fft_y",
-                                                       "fft_z", "interp", "scatter", ""};
-enum { PC_MEMSET = 0, PC_SPREAD, PC_FFT_X, PC_FFT_Y, PC_FFT_Z, PC_INTERP, PC_SCATTER };
+static const char *k_prof_names[FV_PROFILE_CLASSES] = {"memset", "bin",   "prep",   "spread", "fft_x", "fft_y",
+                                                       "fft_z",  "interp", "scatter", "",      "",      ""};
+enum { PC_MEMSET = 0, PC_BIN, PC_PREP, PC_SPREAD, PC_FFT_X, PC_FFT_Y, PC_FFT_Z, PC_INTERP, PC_SCATTER };
 
 // harvest finished event pairs into the per-class totals (synchronises the stream)
 static cudaError_t prof_harvest(fv_plan_s *p)
@@ -220,6 +229,15 @@ static void free_geometry(fv_plan_s *p)
     dfree(p->d_bufA);
     dfree(p->d_bufB);
     dfree_t(p->d_Vu);
+    dfree_t(p->d_bin_of);
+    dfree_t(p->d_counts);
+    dfree_t(p->d_offsets);
+    dfree_t(p->d_cursor);
+    dfree_t(p->d_sidx);
+    dfree_t(p->d_cell);
+    dfree_t(p->d_sdir);
+    dfree(p->d_frac);
+    dfree(p->d_cs);
 }
 
 // Per-channel geometry, tables and workspace; needs the array and the sky.
@@ -315,8 +333,40 @@ static fv_status prepare(fv_plan_s *p)
             }
         }
     }
+    // binned spreading: tiles of 32 x T_y cells (all z), bins = tiles of the top channel's grid
+    p->f_top = 0;
+    for (int f = 1; f < nf; ++f)
+        if (p->freq[f] > p->freq[p->f_top]) p->f_top = f;
+    for (int i = 0; i < 3; ++i) {
+        p->qscale_top[i] = p->gf[p->f_top].dim[i].qscale;
+        p->nf1_top[i] = p->gf[p->f_top].dim[i].nf1;
+    }
+    {
+        const size_t budget = p->precision == FV_FP64 ? 96 * 1024 : 48 * 1024;
+        const size_t nzm = p->d == 3 ? (size_t)p->nf1_max[2] : 1;
+        p->T[0] = 32;
+        p->T[1] = 32;
+        while ((size_t)p->T[0] * p->T[1] * nzm * p->n_pol * es > budget && p->T[1] > 4) p->T[1] /= 2;
+        p->tiled = (size_t)p->T[0] * p->T[1] * nzm * p->n_pol * es <= budget && p->d >= 2 && w <= 16;
+        p->nbx = (p->nf1_top[0] + p->T[0] - 1) / p->T[0];
+        p->nby = (p->nf1_top[1] + p->T[1] - 1) / p->T[1];
+    }
+    size_t bin_bytes = 0;
+    if (p->tiled) {
+        const size_t ns = std::max<long>(p->n_src, 1), nb = (size_t)p->nbx * p->nby;
+        CK(cudaMalloc(&p->d_bin_of, ns * sizeof(int)));
+        CK(cudaMalloc(&p->d_counts, nb * sizeof(int)));
+        CK(cudaMalloc(&p->d_offsets, (nb + 1) * sizeof(int)));
+        CK(cudaMalloc(&p->d_cursor, nb * sizeof(int)));
+        CK(cudaMalloc(&p->d_sidx, ns * sizeof(int)));
+        CK(cudaMalloc(&p->d_cell, 3 * ns * sizeof(int)));
+        CK(cudaMalloc(&p->d_sdir, 3 * ns * sizeof(double)));
+        CK(cudaMalloc(&p->d_frac, 3 * ns * gs));
+        CK(cudaMalloc(&p->d_cs, (size_t)p->n_pol * ns * es));
+        bin_bytes = ns * (4 + 4 + 12 + 24 + 3 * gs + p->n_pol * es) + nb * 12;
+    }
     p->ws_bytes = (long long)(pre_total * gs + tw_total * es + (grid_e + bufA_e + bufB_e) * es +
-                              (size_t)p->n_u * p->n_pol * sizeof(cpx<double>));
+                              (size_t)p->n_u * p->n_pol * sizeof(cpx<double>) + bin_bytes);
     CK(cudaStreamSynchronize(p->stream));
     return FV_OK;
 }
@@ -329,18 +379,54 @@ static fv_status execute_slices(fv_plan_s *p, char *vis, size_t slice_bytes)
     cpx<G> *A = (cpx<G> *)p->d_bufA, *Bb = (cpx<G> *)p->d_bufB;
     const double es = sizeof(cpx<G>);
     const double src_bytes = (double)p->n_src * (3 * sizeof(double) + (double)p->n_stokes * (p->flux_fp64 ? 8 : 4));
+    // prep and spread touch the visible sources only; about half the sky is up at any time
+    const double nvis = 0.5 * p->n_src;
+    const double prep_bytes = nvis * (24.0 + 4.0 + p->n_stokes * (p->flux_fp64 ? 8.0 : 4.0) + 12.0 +
+                                      3.0 * sizeof(G) + p->n_pol * es);
+    const double spread_in_bytes = nvis * (12.0 + 3.0 * sizeof(G) + p->n_pol * es);
+    const int nb = p->nbx * p->nby;
     for (int t = 0; t < nt; ++t) {
+        TimeBin tb{};
+        if (p->tiled) {
+            std::memcpy(tb.R, &p->Rt[(size_t)t * 9], 9 * sizeof(double));
+            for (int i = 0; i < 3; ++i) {
+                tb.C[i] = p->C[i];
+                tb.qscale_top[i] = p->qscale_top[i];
+                tb.nf1_top[i] = p->nf1_top[i];
+            }
+            tb.T[0] = p->T[0];
+            tb.T[1] = p->T[1];
+            tb.nbx = p->nbx;
+            tb.nby = p->nby;
+            CK(prof_begin(p, PC_BIN));
+            CK(launch_time_binning(p->d_e, p->n_src, tb, p->d_bin_of, p->d_counts, p->d_offsets, p->d_cursor,
+                                   p->d_sdir, p->d_sidx, p->stream));
+            CK(prof_end(p, (double)p->n_src * 80.0 + nb * 12.0));
+        }
         for (int f = 0; f < nf; ++f) {
             SliceGeom g = p->gf[f];
             std::memcpy(g.R, &p->Rt[(size_t)t * 9], 9 * sizeof(double));
             const DimGeom *D = g.dim;
             const size_t gel = (size_t)p->n_pol * D[0].nf1 * D[1].nf1 * D[2].nf1;
-            CK(prof_begin(p, PC_MEMSET));
-            CK(cudaMemsetAsync(grid, 0, gel * sizeof(cpx<G>), p->stream));
-            CK(prof_end(p, gel * es));
-            CK(prof_begin(p, PC_SPREAD));
-            CK(launch_spread_direct<G>(p->d_e, p->n_src, p->flux, p->flux_fp64, nf, f, g, grid, p->stream));
-            CK(prof_end(p, src_bytes + gel * es));
+            if (p->tiled) {
+                G *frac = (G *)p->d_frac;
+                cpx<G> *cs = (cpx<G> *)p->d_cs;
+                CK(prof_begin(p, PC_PREP));
+                CK(launch_prep<G>(p->d_sdir, p->d_sidx, p->d_offsets + nb, p->n_src, p->flux, p->flux_fp64, nf, f, g,
+                                  p->d_cell, frac, cs, p->stream));
+                CK(prof_end(p, prep_bytes));
+                const double r0 = D[0].qscale / p->qscale_top[0], r1 = D[1].qscale / p->qscale_top[1];
+                CK(prof_begin(p, PC_SPREAD));
+                CK(launch_spread_tile<G>(p->d_offsets, p->d_cell, frac, cs, p->n_src, g, tb, r0, r1, grid, p->stream));
+                CK(prof_end(p, spread_in_bytes + gel * es));
+            } else {
+                CK(prof_begin(p, PC_MEMSET));
+                CK(cudaMemsetAsync(grid, 0, gel * sizeof(cpx<G>), p->stream));
+                CK(prof_end(p, gel * es));
+                CK(prof_begin(p, PC_SPREAD));
+                CK(launch_spread_direct<G>(p->d_e, p->n_src, p->flux, p->flux_fp64, nf, f, g, grid, p->stream));
+                CK(prof_end(p, src_bytes + gel * es));
+            }
             const G *pre = (const G *)p->d_pre;
             const cpx<G> *tw = (const cpx<G> *)p->d_tw;
             const size_t o0 = (size_t)f * 3;

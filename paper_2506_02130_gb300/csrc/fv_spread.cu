@@ -1,0 +1,329 @@
+// Binned, tiled ES-kernel spreading (Section 2.2, step 1).
+//
+// Per time (shared by every channel of that time):
+//   k_bin_count    rotate equatorial -> ENU (Section 2.3), cut the horizon, and
+//                  count the visible sources per tile of the top channel's grid;
+//   k_bin_scan     exclusive scan of the counts (one CTA);
+//   k_bin_scatter  counting-sort the visible directions by tile.
+// Per (time, channel) slice:
+//   k_prep         beam x flux strengths (Eq. 1-3), prephase e^{i D.(s-C)}
+//                  with the argument and its 2 pi reduction in FP64, and the
+//                  grid coordinate q = (s - C) sigma X / pi split in FP64 into
+//                  the first footprint cell (int) and an offset (FP32 or FP64);
+//   k_spread_tile  one CTA per output tile: accumulate every source whose
+//                  footprint meets the tile with shared-memory atomics, then
+//                  store the whole tile once.  Every grid cell is written by
+//                  exactly one CTA, so the grid needs no clearing and no
+//                  global atomics.
+// A channel's grid coordinates are the top channel's scaled by r = qscale_f /
+// qscale_top <= 1 per axis, so a tile of channel f maps to a rectangle of top
+// bins, i.e. one contiguous range of sorted sources per bin row.
+#include "fv_internal.cuh"
+
+#include <math.h>
+
+namespace fv {
+
+__device__ __forceinline__ double es_kernel_d(double z, double beta)
+{
+    double t = 1.0 - z * z;
+    return t >= 0.0 ? exp(beta * (sqrt(t) - 1.0)) : 0.0;
+}
+__device__ __forceinline__ float es_kernel_f(float z, float beta)
+{
+    float t = 1.0f - z * z;
+    return t >= 0.0f ? __expf(beta * (sqrtf(t) - 1.0f)) : 0.0f;
+}
+template <class G> __device__ __forceinline__ G es_k(G z, G beta);
+template <> __device__ __forceinline__ double es_k<double>(double z, double beta) { return es_kernel_d(z, beta); }
+template <> __device__ __forceinline__ float es_k<float>(float z, float beta) { return es_kernel_f(z, beta); }
+
+__device__ __forceinline__ int top_cell(double q, int nf1)
+{
+    double c = floor(q) + (double)(nf1 / 2);
+    int ci = (int)fmax(0.0, fmin(c, (double)(nf1 - 1)));
+    return ci;
+}
+
+// ------------------------------------------------------------------ per time
+__global__ void k_bin_count(const double *__restrict__ e, long n_src, TimeBin tb, int *__restrict__ bin_of,
+                            int *__restrict__ counts)
+{
+    long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (n >= n_src) return;
+    const double ex = e[n], ey = e[n_src + n], ez = e[2 * n_src + n];
+    const double s2 = tb.R[6] * ex + tb.R[7] * ey + tb.R[8] * ez;
+    if (!(s2 > 0.0)) {
+        bin_of[n] = -1;
+        return;
+    }
+    const double s0 = tb.R[0] * ex + tb.R[1] * ey + tb.R[2] * ez;
+    const double s1 = tb.R[3] * ex + tb.R[4] * ey + tb.R[5] * ez;
+    int cx = top_cell((s0 - tb.C[0]) * tb.qscale_top[0], tb.nf1_top[0]);
+    int cy = top_cell((s1 - tb.C[1]) * tb.qscale_top[1], tb.nf1_top[1]);
+    int b = (cy / tb.T[1]) * tb.nbx + cx / tb.T[0];
+    bin_of[n] = b;
+    atomicAdd(&counts[b], 1);
+}
+
+// exclusive scan of counts[0..nb) into offsets[0..nb], cursor = offsets (one CTA of 1024 threads)
+__global__ void k_bin_scan(const int *__restrict__ counts, int nb, int *__restrict__ offsets, int *__restrict__ cursor)
+{
+    __shared__ int part[1024];
+    const int t = threadIdx.x;
+    const int per = (nb + 1023) / 1024;
+    const int lo = t * per, hi = min(nb, lo + per);
+    int s = 0;
+    for (int i = lo; i < hi; ++i) s += counts[i];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int run = part[t] - s;   // exclusive prefix of this thread's chunk
+    for (int i = lo; i < hi; ++i) {
+        offsets[i] = run;
+        cursor[i] = run;
+        run += counts[i];
+    }
+    if (t == 1023) offsets[nb] = part[1023];
+}
+
+__global__ void k_bin_scatter(const double *__restrict__ e, long n_src, TimeBin tb, const int *__restrict__ bin_of,
+                              int *__restrict__ cursor, double *__restrict__ sdir, int *__restrict__ sidx)
+{
+    long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (n >= n_src) return;
+    const int b = bin_of[n];
+    if (b < 0) return;
+    const int pos = atomicAdd(&cursor[b], 1);
+    const double ex = e[n], ey = e[n_src + n], ez = e[2 * n_src + n];
+    sdir[pos] = tb.R[0] * ex + tb.R[1] * ey + tb.R[2] * ez;
+    sdir[n_src + pos] = tb.R[3] * ex + tb.R[4] * ey + tb.R[5] * ez;
+    sdir[2 * n_src + pos] = tb.R[6] * ex + tb.R[7] * ey + tb.R[8] * ez;
+    sidx[pos] = (int)n;
+}
+
+cudaError_t launch_time_binning(const double *e, long n_src, const TimeBin &tb, int *bin_of, int *counts,
+                                int *offsets, int *cursor, double *sdir, int *sidx, cudaStream_t st)
+{
+    const int nb = tb.nbx * tb.nby;
+    cudaError_t err = cudaMemsetAsync(counts, 0, (size_t)nb * sizeof(int), st);
+    if (err != cudaSuccess) return err;
+    if (n_src > 0) k_bin_count<<<(unsigned)((n_src + 255) / 256), 256, 0, st>>>(e, n_src, tb, bin_of, counts);
+    k_bin_scan<<<1, 1024, 0, st>>>(counts, nb, offsets, cursor);
+    if (n_src > 0)
+        k_bin_scatter<<<(unsigned)((n_src + 255) / 256), 256, 0, st>>>(e, n_src, tb, bin_of, cursor, sdir, sidx);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ per slice
+template <class G> __device__ __forceinline__ G voltage(const BeamParams &b, G rho, G s2, G nu);
+template <> __device__ __forceinline__ double voltage<double>(const BeamParams &b, double rho, double s2, double nu)
+{
+    if (b.kind == 0) {
+        double theta = atan2(rho, s2);
+        double fwhm = b.p0 * b.p1 / nu;
+        return exp(-2.0 * M_LN2 * theta * theta / (fwhm * fwhm));
+    }
+    if (b.kind == 1) {
+        double x = M_PI * b.p0 * nu * rho / FV_C_LIGHT;
+        return x < 1e-8 ? 1.0 - 0.125 * x * x : 2.0 * j1(x) / x;
+    }
+    return 1.0;
+}
+template <> __device__ __forceinline__ float voltage<float>(const BeamParams &b, float rho, float s2, float nu)
+{
+    if (b.kind == 0) {
+        float theta = atan2f(rho, s2);
+        float fwhm = (float)(b.p0 * b.p1) / nu;
+        return expf(-2.0f * 0.69314718055994531f * theta * theta / (fwhm * fwhm));
+    }
+    if (b.kind == 1) {
+        float x = (float)(M_PI * b.p0 / FV_C_LIGHT) * nu * rho;
+        return x < 1e-4f ? 1.0f - 0.125f * x * x : 2.0f * j1f(x) / x;
+    }
+    return 1.0f;
+}
+
+template <class G>
+__global__ void __launch_bounds__(256) k_prep(const double *__restrict__ sdir, const int *__restrict__ sidx,
+                                              const int *__restrict__ nv_ptr, long n_src,
+                                              const void *__restrict__ flux, int flux_fp64, int n_freq, int f,
+                                              SliceGeom g, int *__restrict__ cell, G *__restrict__ frac,
+                                              cpx<G> *__restrict__ cs)
+{
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= *nv_ptr) return;
+    const double s0 = sdir[i], s1 = sdir[n_src + i], s2 = sdir[2 * n_src + i];
+    const long n = sidx[i];
+    // strengths (Eq. 1-2); beam in the grid precision
+    const G rho = (G)sqrt(s0 * s0 + s1 * s1);
+    const G A = voltage<G>(g.beam, rho, (G)s2, (G)g.nu);
+    const G A2 = A * A;
+    auto ld = [&](int k) -> G {
+        size_t idx = ((size_t)k * n_src + n) * n_freq + f;
+        return flux_fp64 ? (G)((const double *)flux)[idx] : (G)((const float *)flux)[idx];
+    };
+    cpx<G> c[4];
+    int np = 1;
+    if (!g.polarized) {
+        c[0] = cmk<G>(A2 * ld(0), (G)0);
+    } else {
+        np = 4;
+        const G I = ld(0), Q = ld(1), U = ld(2), V = ld(3);
+        G ca = (G)1, sa = (G)0;
+        if (rho > (G)0) { ca = (G)s1 / rho; sa = (G)s0 / rho; }
+        const G c2 = ca * ca - sa * sa, s2a = (G)2 * ca * sa;
+        const G Qr = Q * c2 - U * s2a, Ur = Q * s2a + U * c2;
+        c[0] = cmk<G>(A2 * (I + Qr), (G)0);
+        c[1] = cmk<G>(A2 * Ur, A2 * V);
+        c[2] = cmk<G>(A2 * Ur, -A2 * V);
+        c[3] = cmk<G>(A2 * (I - Qr), (G)0);
+    }
+    // prephase: argument and reduction to [-pi, pi] in FP64, sincos in G
+    const double st[3] = {s0 - g.dim[0].C, s1 - g.dim[1].C, s2 - g.dim[2].C};
+    double ph = 0.0;
+    for (int k = 0; k < g.d; ++k) ph += g.dim[k].D * st[k];
+    ph -= 6.283185307179586476925 * rint(ph * 0.15915494309189533577);
+    G sp, cp;
+    if (sizeof(G) == 4) { float a, b; sincosf((float)ph, &a, &b); sp = (G)a; cp = (G)b; }
+    else { double a, b; sincos(ph, &a, &b); sp = (G)a; cp = (G)b; }
+    for (int p = 0; p < np; ++p) cs[(size_t)p * n_src + i] = cmul(c[p], cmk<G>(cp, sp));
+    // grid coordinates, split in FP64
+    for (int k = 0; k < 3; ++k) {
+        if (k < g.d) {
+            const double q = st[k] * g.dim[k].qscale;
+            const double l0 = ceil(q - 0.5 * g.w);
+            cell[(size_t)k * n_src + i] = (int)l0 + g.dim[k].nf1 / 2;
+            frac[(size_t)k * n_src + i] = (G)(l0 - q);
+        } else {
+            cell[(size_t)k * n_src + i] = 0;
+            frac[(size_t)k * n_src + i] = (G)0;
+        }
+    }
+}
+
+template <class G>
+cudaError_t launch_prep(const double *sdir, const int *sidx, const int *nv_ptr, long n_src, const void *flux,
+                        int flux_fp64, int n_freq, int f, const SliceGeom &g, int *cell, G *frac, cpx<G> *cs,
+                        cudaStream_t st)
+{
+    if (n_src <= 0) return cudaSuccess;
+    k_prep<G><<<(unsigned)((n_src + 255) / 256), 256, 0, st>>>(sdir, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f,
+                                                               g, cell, frac, cs);
+    return cudaGetLastError();
+}
+
+template <class G>
+__global__ void __launch_bounds__(256) k_spread_tile(const int *__restrict__ offsets, const int *__restrict__ cell,
+                                                     const G *__restrict__ frac, const cpx<G> *__restrict__ cs,
+                                                     long n_src, SliceGeom g, TimeBin tb, double r0, double r1,
+                                                     cpx<G> *__restrict__ grid)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<G> *tile = reinterpret_cast<cpx<G> *>(smem_raw);
+    const int Tx = tb.T[0], Ty = tb.T[1];
+    const int nx = g.dim[0].nf1, ny = g.dim[1].nf1, nz = g.d == 3 ? g.dim[2].nf1 : 1;
+    const int np = g.n_pol, w = g.w;
+    const int x0 = blockIdx.x * Tx, y0 = blockIdx.y * Ty;
+    const int tsz = Tx * Ty * nz * np;
+    for (int i = threadIdx.x; i < tsz; i += blockDim.x) tile[i] = cmk<G>((G)0, (G)0);
+    // sources whose footprint can meet this tile have q in [x0 - nf1/2 - w/2, x0 + T - nf1/2 + w/2 - 1];
+    // map to top cells with a one-cell margin on each side
+    const double qx_lo = (x0 - nx / 2 - 0.5 * w) / r0, qx_hi = (x0 + Tx - nx / 2 + 0.5 * w - 1) / r0;
+    const double qy_lo = (y0 - ny / 2 - 0.5 * w) / r1, qy_hi = (y0 + Ty - ny / 2 + 0.5 * w - 1) / r1;
+    const int bx_lo = top_cell(qx_lo - 1.0, tb.nf1_top[0]) / Tx, bx_hi = top_cell(qx_hi + 1.0, tb.nf1_top[0]) / Tx;
+    const int by_lo = top_cell(qy_lo - 1.0, tb.nf1_top[1]) / Ty, by_hi = top_cell(qy_hi + 1.0, tb.nf1_top[1]) / Ty;
+    __syncthreads();
+    const G two_over_w = (G)(2.0 / w), beta = (G)g.beta;
+    for (int by = by_lo; by <= by_hi; ++by) {
+        const int i0 = offsets[by * tb.nbx + bx_lo], i1 = offsets[by * tb.nbx + bx_hi + 1];
+        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const int cx = cell[i], cy = cell[n_src + i];
+            const int jx0 = max(0, x0 - cx), jx1 = min(w, x0 + Tx - cx);
+            const int jy0 = max(0, y0 - cy), jy1 = min(w, y0 + Ty - cy);
+            if (jx0 >= jx1 || jy0 >= jy1) continue;
+            const G fx = frac[i], fy = frac[n_src + i];
+            G wz[16];
+            int cz = 0;
+            if (g.d == 3) {
+                cz = cell[2 * n_src + i];
+                const G fz = frac[2 * n_src + i];
+                for (int j = 0; j < w; ++j) wz[j] = es_k<G>(two_over_w * (fz + (G)j), beta);
+            } else {
+                wz[0] = (G)1;
+            }
+            const int wzn = g.d == 3 ? w : 1;
+            cpx<G> c[4];
+            for (int p = 0; p < np; ++p) c[p] = cs[(size_t)p * n_src + i];
+            for (int jy = jy0; jy < jy1; ++jy) {
+                const G wy = es_k<G>(two_over_w * (fy + (G)jy), beta);
+                const int ly = cy + jy - y0;
+                for (int jx = jx0; jx < jx1; ++jx) {
+                    const G wxy = wy * es_k<G>(two_over_w * (fx + (G)jx), beta);
+                    const int lx = cx + jx - x0;
+                    for (int jz = 0; jz < wzn; ++jz) {
+                        const G wt = wxy * wz[jz];
+                        const int z = cz + jz;
+                        if (z < 0 || z >= nz) continue;    // only reachable through rounding at the grid edge
+                        for (int p = 0; p < np; ++p) {
+                            cpx<G> *dst = &tile[((p * nz + z) * Ty + ly) * Tx + lx];
+                            atomicAdd(&dst->x, wt * c[p].x);
+                            atomicAdd(&dst->y, wt * c[p].y);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // store the whole tile (rows of Tx consecutive x)
+    for (int idx = threadIdx.x; idx < tsz; idx += blockDim.x) {
+        const int lx = idx % Tx;
+        int rest = idx / Tx;
+        const int ly = rest % Ty;
+        rest /= Ty;                       // rest = p * nz + z
+        const int x = x0 + lx, y = y0 + ly;
+        if (x < nx && y < ny) grid[((size_t)rest * ny + y) * nx + x] = tile[idx];
+    }
+}
+
+template <class G>
+cudaError_t launch_spread_tile(const int *offsets, const int *cell, const G *frac, const cpx<G> *cs, long n_src,
+                               const SliceGeom &g, const TimeBin &tb, double r0, double r1, cpx<G> *grid,
+                               cudaStream_t st)
+{
+    const int nz = g.d == 3 ? g.dim[2].nf1 : 1;
+    const size_t smem = (size_t)tb.T[0] * tb.T[1] * nz * g.n_pol * sizeof(cpx<G>);
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set[dev]) {
+        e = cudaFuncSetAttribute(k_spread_tile<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, FV_SPREAD_SMEM_MAX);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    if (smem > FV_SPREAD_SMEM_MAX) return cudaErrorInvalidValue;
+    dim3 blocks((g.dim[0].nf1 + tb.T[0] - 1) / tb.T[0], (g.dim[1].nf1 + tb.T[1] - 1) / tb.T[1]);
+    k_spread_tile<G><<<blocks, 256, smem, st>>>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_prep<double>(const double *, const int *, const int *, long, const void *, int, int, int,
+                                         const SliceGeom &, int *, double *, cpx<double> *, cudaStream_t);
+template cudaError_t launch_prep<float>(const double *, const int *, const int *, long, const void *, int, int, int,
+                                        const SliceGeom &, int *, float *, cpx<float> *, cudaStream_t);
+template cudaError_t launch_spread_tile<double>(const int *, const int *, const double *, const cpx<double> *, long,
+                                                const SliceGeom &, const TimeBin &, double, double, cpx<double> *,
+                                                cudaStream_t);
+template cudaError_t launch_spread_tile<float>(const int *, const int *, const float *, const cpx<float> *, long,
+                                               const SliceGeom &, const TimeBin &, double, double, cpx<float> *,
+                                               cudaStream_t);
+
+}  // namespace fv

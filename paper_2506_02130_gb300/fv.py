@@ -50,7 +50,7 @@ class fv_info(C.Structure):
                 ("src_halfwidth", C.c_double * 3), ("workspace_bytes", C.c_longlong)]
 
 
-PROFILE_CLASSES = 8
+PROFILE_CLASSES = 12
 
 
 class fv_profile_data(C.Structure):
