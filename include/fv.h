@@ -174,6 +174,36 @@ typedef struct {
 fv_status fv_profile_enable(fv_plan_t p, int enable);
 fv_status fv_profile_read(fv_plan_t p, fv_profile_data *out);
 
+/* fv_execute for callers that cannot allocate device memory.  The paper has
+ * no counterpart; this exists for callers such as a host framework whose own
+ * allocator already owns the free HBM (a foreign cudaMalloc would fail or
+ * fragment its pool), a serving loop that admits work against a fixed HBM
+ * budget and must not grow while it runs, or a plug-in whose host forbids
+ * device allocations outside the host's API.
+ *
+ * Same result as fv_execute(p, vis, 1) (same kernels, same precision), but
+ * all per-slice scratch (spreading grid, FFT band buffers, source bins and
+ * prepared sources, unique-target values) comes from one static device array
+ * of FV_STATIC_SCRATCH_BYTES that is part of the library image; the call
+ * allocates and frees nothing.  The plan (fv_plan / fv_set_array /
+ * fv_set_sky) is created as usual beforehand; vis must be a device buffer of
+ * the fv_execute output shape and type.
+ *  - The array is reserved on every device that loads the library, until the
+ *    process exits.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call on a device shares the one array and leaves its contents
+ *    behind; the call clears what must start at zero itself.  Calls whose
+ *    work overlaps on the GPU (other host threads, other plans, other
+ *    streams) race on the array: serialise them.
+ *  - Returns when the work is enqueued on the plan's stream.
+ * Errors: FV_ERR_UNSUPPORTED if the plan needs more scratch than
+ * FV_STATIC_SCRATCH_BYTES (the message gives both sizes), FV_ERR_ARG (NULL or
+ * host vis), FV_ERR_STATE, FV_ERR_CUDA. */
+#define FV_STATIC_SCRATCH_BYTES (64ull << 20)
+fv_status fv_execute_static(fv_plan_t p, void *vis);
+
 /* ABI version (FV_ABI_VERSION of the library that was loaded). */
 int fv_abi_version(void);
 

@@ -1,0 +1,93 @@
+// Internal: the plan object behind fv_plan_t (shared by the runtime's
+// translation units; not part of the public ABI).
+#pragma once
+#include "../../include/fv.h"
+#include "fv_internal.cuh"
+
+#include <string>
+#include <utility>
+#include <vector>
+
+struct fv_plan_s {
+    using BeamParams = fv::BeamParams;
+    using SliceGeom = fv::SliceGeom;
+    template <class T> using cpx = fv::cpx<T>;
+    // options
+    int precision = FV_FP64;
+    double eps = 1e-10;
+    std::vector<double> freq, lst;
+    double lat = 0.0;
+    BeamParams beam{};
+    int polarized = 0, n_pol = 1;
+    int dims_req = 0;
+    double sigma = 2.0;
+    int w = 0;
+    double beta = 0.0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+
+    // quadrature (sine-substituted Gauss-Legendre) on the device
+    int nq = 0;
+    double *d_glx = nullptr, *d_glw = nullptr;
+
+    // array
+    bool have_array = false;
+    int n_ant = 0, n_bl = 0, n_u = 0, d = 2;
+    std::vector<double> bu;          // [n_u][3]
+    std::vector<int> bl2u;           // [n_bl]
+    double bcen[3] = {0, 0, 0}, bhalf[3] = {0, 0, 0};
+    double *d_bu = nullptr, *d_dec = nullptr;
+    int *d_bl2u = nullptr;
+
+    // sky
+    bool have_sky = false;
+    long n_src = 0;
+    int n_stokes = 1;
+    double *d_e = nullptr;
+    void *d_flux_owned = nullptr;
+    const void *flux = nullptr;
+    int flux_fp64 = 0;
+    double C[3] = {0, 0, 0}, S[3] = {0, 0, 0};
+    bool any_visible = false;
+
+    // geometry
+    std::vector<double> Rt;          // [n_time][9]
+    std::vector<SliceGeom> gf;       // per channel (R filled per time)
+    std::vector<size_t> pre_off;     // [n_freq][3] element offsets into the prescale table
+    std::vector<size_t> tw_off;      // [n_freq][3] element offsets into the twiddle table
+    void *d_pre = nullptr, *d_tw = nullptr;
+    void *d_grid = nullptr, *d_bufA = nullptr, *d_bufB = nullptr;
+    cpx<double> *d_Vu = nullptr;
+    size_t grid_elems = 0, bufA_elems = 0, bufB_elems = 0;
+    // binned spreading
+    bool tiled = false;
+    int T[2] = {32, 32}, nbx = 1, nby = 1, f_top = 0;
+    double qscale_top[3] = {0, 0, 0};
+    int nf1_top[3] = {1, 1, 1};
+    int *d_bin_of = nullptr, *d_counts = nullptr, *d_offsets = nullptr, *d_cursor = nullptr, *d_sidx = nullptr;
+    int *d_cell = nullptr;
+    double *d_sdir = nullptr;
+    void *d_frac = nullptr, *d_cs = nullptr;
+    long long ws_bytes = 0;
+    int nf1_max[3] = {1, 1, 1}, M_max[3] = {1, 1, 1};
+
+    // kernel timing (fv_profile_enable)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> ev_pending;   // (class, index of the start event in the pool)
+    size_t ev_next = 0;
+    double prof_ms[FV_PROFILE_CLASSES] = {};
+    long long prof_launches[FV_PROFILE_CLASSES] = {};
+    double prof_bytes[FV_PROFILE_CLASSES] = {};
+    int prof_cls = -1;
+
+    fv_status fail(fv_status s, const std::string &m)
+    {
+        err = m;
+        return s;
+    }
+    size_t elem() const { return precision == FV_FP64 ? sizeof(cpx<double>) : sizeof(cpx<float>); }
+};
+

@@ -71,6 +71,7 @@ SIGNATURES = {
     "fv_abi_version": (C.c_int, []),
     "fv_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "fv_profile_read": (C.c_int, [C.c_void_p, C.POINTER(fv_profile_data)]),
+    "fv_execute_static": (C.c_int, [C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -149,6 +150,14 @@ def fv_execute(plan, vis) -> None:
     """vis: numpy complex array (host) or CUDA tensor (device) of the full output shape."""
     on_dev = hasattr(vis, "is_cuda") and vis.is_cuda
     _check(load_library().fv_execute(plan, _ptr(vis), int(on_dev)), plan)
+
+
+STATIC_SCRATCH_BYTES = 64 << 20
+
+
+def fv_execute_static(plan, vis) -> None:
+    """fv_execute into a device buffer with the library's static scratch (allocates nothing)."""
+    _check(load_library().fv_execute_static(plan, _ptr(vis)), plan)
 
 
 def fv_destroy(plan) -> None:

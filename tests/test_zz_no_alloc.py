@@ -1,0 +1,64 @@
+"""fv_execute_static: the entry point for callers that cannot allocate device
+memory (a host whose own allocator owns the free HBM, a serving loop held to
+a fixed HBM budget, a plug-in whose host forbids foreign allocations).  It
+must give fv_execute's result, call after call, from the library's static
+scratch, and refuse plans whose scratch does not fit.
+
+Collected last on purpose (file name), so that a run stopping at the first
+failure has already run every other test.
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import rel_l2
+from paper_2506_02130_gb300 import fv, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {fv.FV_FP64: 1e-9, fv.FV_MIXED: 2e-5}
+
+
+def _plan(prob, precision, eps):
+    p = fv.Plan.from_problem(prob, precision=precision, eps=eps)
+    p.set_sky(prob.sky.ra, prob.sky.dec, prob.sky.flux)
+    return p
+
+
+@pytest.mark.parametrize("precision,eps", [(fv.FV_MIXED, 1e-6), (fv.FV_FP64, 1e-11)])
+def test_static_scratch_matches_fv_execute_twice(precision, eps):
+    torch = pytest.importorskip("torch")
+    prob = W.config_hex127(seed=21, n_chan=3, n_time=2, n_point=1200, nside=8, radius=2)
+    p = _plan(prob, precision, eps)
+    cdt = torch.complex64 if precision == fv.FV_MIXED else torch.complex128
+    ref = torch.empty(p.out_shape, dtype=cdt, device="cuda")
+    fv.fv_execute(p.handle, ref)
+    torch.cuda.synchronize()
+    ref = ref.cpu().numpy()
+    for _ in range(2):
+        out = torch.full(p.out_shape, float("nan"), dtype=cdt, device="cuda")
+        fv.fv_execute_static(p.handle, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.isfinite(got).all()
+        assert rel_l2(got, ref) <= TOL[precision]
+    p.close()
+
+
+def test_static_scratch_refuses_oversize_plans_and_host_buffers():
+    torch = pytest.importorskip("torch")
+    # 127 antennas at 200 MHz: about 100 MB of per-slice scratch > 64 MiB
+    prob = W.config_hex127(seed=22, n_chan=1, n_time=1, n_point=500, nside=0)
+    prob.freqs_hz = np.array([200e6])
+    prob.sky.flux = prob.sky.flux[:, :, :1]
+    p = _plan(prob, fv.FV_MIXED, 1e-6)
+    out = torch.zeros(p.out_shape, dtype=torch.complex64, device="cuda")
+    with pytest.raises(fv.FvError) as ei:
+        fv.fv_execute_static(p.handle, out)
+    assert ei.value.status == fv.FV_ERR_UNSUPPORTED
+    assert "static scratch" in str(ei.value)
+    p.close()
+    small = _plan(W.config_small(seed=23, n_src=200), fv.FV_MIXED, 1e-6)
+    with pytest.raises(fv.FvError) as ei:
+        fv.fv_execute_static(small.handle, np.zeros(small.out_shape, np.complex64))
+    assert ei.value.status == fv.FV_ERR_ARG
+    small.close()
