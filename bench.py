@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target oracle CPU time for the baseline")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip timing the plain FP64 path (one slice after another) beside the mixed path")
     return ap.parse_args()
 
 
@@ -124,18 +126,20 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample(prob, target_s, gpu_out=None):
+def oracle_sample(prob, target_s, gpu_outs=None):
     """Time the FP64 oracle (as it stands) on whole slices of the workload.
 
     Runs one slice, then as many more as fit in ``target_s`` seconds; returns
-    vis/s, thread count, a description and (if ``gpu_out`` is given) the GPU's
-    relative L2 error on those slices.
+    vis/s, thread count, a description and, for every GPU output in the dict
+    ``gpu_outs``, its relative L2 error on those slices.
     """
     import numpy as np
     from oracle.oracle import OracleProblem, oracle_vis, rel_l2, max_threads
     nf, nt = len(prob.freqs_hz), len(prob.lsts_rad)
     order = np.random.default_rng(123).permutation(nf * nt)
-    done, t_total, errs, refs, gots = [], 0.0, [], [], []
+    gpu_outs = gpu_outs or {}
+    done, t_total, refs = [], 0.0, []
+    gots = {k: [] for k in gpu_outs}
     for k in order:
         f, t = divmod(int(k), nt)
         p = OracleProblem.from_workload(prob, freq_idx=[f], time_idx=[t])
@@ -143,12 +147,13 @@ def oracle_sample(prob, target_s, gpu_out=None):
         ref = oracle_vis(p, "factored")
         t_total += time.perf_counter() - t0
         done.append((f, t))
-        if gpu_out is not None:
-            refs.append(ref[0, 0]); gots.append(gpu_out[f, t])
+        refs.append(ref[0, 0])
+        for k, v in gpu_outs.items():
+            gots[k].append(v[f, t])
         if t_total >= target_s:
             break
     n_vis = len(done) * len(prob.pairs) * (4 if prob.polarized else 1)
-    err = rel_l2(np.array(gots), np.array(refs)) if gpu_out is not None else None
+    err = {k: rel_l2(np.array(v), np.array(refs)) for k, v in gots.items()}
     return {"value": n_vis / t_total, "unit": "visibilities/s", "cores": max_threads(), "kind": "oracle",
             "sample": f"{len(done)} of {nf * nt} (time, channel) slices, all {len(prob.pairs)} baselines and "
                       f"{prob.sky.n_src} sources, FP64 antenna-factored direct sum",
@@ -295,11 +300,32 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": 1e3 * e2e_s / args.steps}
 
-    # ---- CPU baseline (oracle) on a bounded sample, rank 0 at N=1; reports the GPU error on it too
+    # ---- the plain FP64 path (one slice after another, no batching) on the same workload
+    fp64 = None
+    outs = {args.precision: out.cpu().numpy()}
+    if precision == fv.FV_MIXED and not args.no_fp64_compare:
+        plan.close()
+        p64 = fv.Plan.from_problem(prob, precision=fv.FV_FP64, eps=1e-11, stream=stream.cuda_stream, device=local)
+        p64.set_sky(prob.sky.ra, prob.sky.dec, torch.tensor(prob.sky.flux, dtype=torch.float64, device=dev))
+        o64 = torch.empty(p64.out_shape, dtype=torch.complex128, device=dev)
+        p64.run(o64)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p64.run(o64)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"value": world * n_vis / (ms64 / 1e3), "unit": "visibilities/s", "ms_per_step": ms64,
+                "eps": 1e-11, "steps": 1, "warmup": 1, "info": p64.info()}
+        outs["fp64"] = o64.cpu().numpy()
+        p64.close()
+        plan = None
+
+    # ---- CPU baseline (oracle) on a bounded sample, rank 0 at N=1; reports the GPU errors on it too
     cpu, err = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        gpu_np = out.cpu().numpy()
-        cpu, err = oracle_sample(prob, args.cpu_seconds, gpu_np)
+        cpu, err = oracle_sample(prob, args.cpu_seconds, outs)
 
     line = {"metric": "visibilities/s at <=2e-5 rel err vs FP64 direct sum", "value": value,
             "unit": "visibilities/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -315,13 +341,14 @@ def main():
                              f"(~{info['workspace_bytes'] / 1e6:.0f} MB workspace reused per slice)",
                        "parallelism": f"{world} independent problems (one per GPU)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": gpu_launches,
-            "rel_l2_vs_oracle_sample": err,
+            "rel_l2_vs_oracle_sample": err, "fp64_plain": fp64,
             "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
                             "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}
                         for k, v in prof.items() if v["launches"] > 0}}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
+    if plan is not None:
+        plan.close()
     if dist:
         dist.destroy_process_group()
 

@@ -81,7 +81,8 @@ typedef struct {
                                  pq = 00, 01, 10, 11 out */
     int dims;                 /* 0: auto (3 if any baseline has b_up != 0), 2 or 3 */
     double upsampfac;         /* oversampling sigma (Section 2.2, Eq. 5); 0 = default 2.0;
-                                 accepted: 1.25 <= sigma <= 3 */
+                                 accepted: 1.25 <= sigma <= 3 (FV_MIXED: sigma >= 1.5, because
+                                 the deconvolutions amplify FP32 rounding too much below it) */
     int kernel_width;         /* ES kernel width w in grid points; 0 = from eps
                                  (w = ceil(log10(1/eps)) + 1 at sigma = 2, Section 2.2) */
     void *cuda_stream;        /* borrowed cudaStream_t, or NULL for a plan-owned stream */

@@ -1,5 +1,5 @@
-// Hand-written mixed-radix (2, 3, 4, 5, 8) FFT pass for the oversampled grid
-// (Section 2.2, step 2: "Oversampled FFT").
+// Hand-written mixed-radix FFT pass for the oversampled grid (Section 2.2,
+// step 2: "Oversampled FFT").
 //
 // One pass transforms every row of its input along the row's contiguous axis:
 //   load the N grid values of the row, multiply by the deconvolution prescale
@@ -11,59 +11,111 @@
 // The transposed write rotates the axes so that the next pass again reads
 // contiguous rows.
 //
-// GB300 mapping: a CTA holds R consecutive rows in shared memory (R chosen so
-// that R*M <= kSmemElems), so the transposed store writes R consecutive
-// complex values per band index, and neighbouring CTAs fill the rest of each
-// 32-byte sector.  Stockham stages ping-pong between two shared buffers; a
-// thread keeps one radix-RD butterfly (compile-time radix) in registers.
+// GB300 mapping.  M is chosen as a product of at most three (four beyond
+// 4096) radices from {2,3,4,5,6,8,9,10,12,15,16}, so a row takes at most
+// three trips through shared memory; each radix-R butterfly runs in
+// registers (composite R as nested Cooley-Tukey with compile-time twiddles).
+// A CTA holds R_rows consecutive rows in two padded shared buffers (one
+// complex of padding per 16, which breaks the bank conflicts of the
+// stride-R stores of the first stage); index arithmetic uses
+// multiply-high division by the per-stage constants prepared on the host.
 #include "fv_internal.cuh"
 
 namespace fv {
 
 static constexpr int kThreads = 256;
 
-template <class G> struct FftCfg;
-template <> struct FftCfg<float> { static constexpr int kSmemElems = 4096; };    // 2 x 32 KB of complex64
-template <> struct FftCfg<double> { static constexpr int kSmemElems = 2048; };   // 2 x 32 KB of complex128
-
-size_t fft_pass_smem_bytes(int M, int elem_bytes)
+// ---------------------------------------------------------------- compile-time twiddles
+// e^{2 pi i m / R} for 2 <= R <= 16, from Taylor series on [0, pi/4] after an
+// exact reduction of the rational angle m/R to an octant (constexpr, host compiler).
+namespace cx {
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr double sin_t(double a)
 {
-    const int cap = elem_bytes == 4 ? FftCfg<float>::kSmemElems : FftCfg<double>::kSmemElems;
-    int R = cap / M;
-    if (R < 1) R = 1;
-    if (R > 8) R = 8;
-    return (size_t)2 * R * M * 2 * elem_bytes;
+    double t = a, s = a;
+    for (int n = 1; n < 12; ++n) {
+        t *= -a * a / ((2.0 * n) * (2.0 * n + 1.0));
+        s += t;
+    }
+    return s;
+}
+constexpr double cos_t(double a)
+{
+    double t = 1.0, s = 1.0;
+    for (int n = 1; n < 12; ++n) {
+        t *= -a * a / ((2.0 * n - 1.0) * (2.0 * n));
+        s += t;
+    }
+    return s;
+}
+struct SC { double s, c; };
+constexpr SC sincos2pi(int m, int R)
+{
+    m %= R;
+    if (m < 0) m += R;
+    const long t = 4L * m;
+    const int k = (int)(t / R);            // quarter turns
+    const long rem = t - (long)k * R;      // remaining angle (pi/2) rem / R
+    double s0 = 0, c0 = 0;
+    if (2 * rem <= R) {
+        const double a = (kPi / 2) * (double)rem / R;
+        s0 = sin_t(a);
+        c0 = cos_t(a);
+    } else {
+        const double a = (kPi / 2) * (double)(R - rem) / R;
+        s0 = cos_t(a);
+        c0 = sin_t(a);
+    }
+    if (k == 0) return {s0, c0};
+    if (k == 1) return {c0, -s0};
+    if (k == 2) return {-s0, -c0};
+    return {-c0, s0};
+}
+struct Table {
+    double c[17 * 16];
+    double s[17 * 16];
+};
+constexpr Table make_table()
+{
+    Table t{};
+    for (int R = 2; R <= 16; ++R)
+        for (int m = 0; m < R; ++m) {
+            SC v = sincos2pi(m, R);
+            t.c[R * 16 + m] = v.c;
+            t.s[R * 16 + m] = v.s;
+        }
+    return t;
+}
+}  // namespace cx
+
+__constant__ cx::Table kTw = cx::make_table();
+
+// v * e^{2 pi i m / R} with compile-time m, R (exact for the quarter turns)
+template <class G, int M_, int R>
+__device__ __forceinline__ cpx<G> twm(cpx<G> v)
+{
+    constexpr int m = M_ % R;
+    if constexpr (m == 0) return v;
+    else if constexpr (4 * m == R) return cmuli(v);
+    else if constexpr (2 * m == R) return cmk<G>(-v.x, -v.y);
+    else if constexpr (4 * m == 3 * R) return cmk<G>(v.y, -v.x);
+    else return cmul(v, cmk<G>((G)kTw.c[R * 16 + m], (G)kTw.s[R * 16 + m]));
 }
 
-// longest row: two buffers of one row within 192 KB of shared memory
-int fft_max_M(int elem_bytes) { return elem_bytes == 4 ? 12288 : 6144; }
+// ---------------------------------------------------------------- register DFTs (+ sign)
+template <int R> struct Fac {
+    static constexpr int A = (R % 4 == 0 && R != 4) ? 4 : (R % 2 == 0 && R != 2) ? 2 : (R % 3 == 0 && R != 3) ? 3 : 5;
+    static constexpr int B = R / A;
+};
 
-static int rows_per_cta(int M, int elem_bytes)
-{
-    const int cap = elem_bytes == 4 ? FftCfg<float>::kSmemElems : FftCfg<double>::kSmemElems;
-    int R = cap / M;
-    return R < 1 ? 1 : (R > 8 ? 8 : R);
-}
-
-// R-point DFT with the + sign, in registers.
 template <class G, int R> struct Dft;
+
 template <class G> struct Dft<G, 2> {
     static __device__ __forceinline__ void run(cpx<G> *v)
     {
         cpx<G> a = v[0], b = v[1];
         v[0] = cadd(a, b);
         v[1] = csub(a, b);
-    }
-};
-template <class G> struct Dft<G, 4> {
-    static __device__ __forceinline__ void run(cpx<G> *v)
-    {
-        cpx<G> s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-        cpx<G> s13 = cadd(v[1], v[3]), d13 = cmuli(csub(v[1], v[3]));
-        v[0] = cadd(s02, s13);
-        v[2] = csub(s02, s13);
-        v[1] = cadd(d02, d13);
-        v[3] = csub(d02, d13);
     }
 };
 template <class G> struct Dft<G, 3> {
@@ -75,6 +127,17 @@ template <class G> struct Dft<G, 3> {
         v[0] = cadd(v[0], t);
         v[1] = cadd(m, u);
         v[2] = csub(m, u);
+    }
+};
+template <class G> struct Dft<G, 4> {
+    static __device__ __forceinline__ void run(cpx<G> *v)
+    {
+        cpx<G> s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        cpx<G> s13 = cadd(v[1], v[3]), d13 = cmuli(csub(v[1], v[3]));
+        v[0] = cadd(s02, s13);
+        v[2] = csub(s02, s13);
+        v[1] = cadd(d02, d13);
+        v[3] = csub(d02, d13);
     }
 };
 template <class G> struct Dft<G, 5> {
@@ -95,52 +158,125 @@ template <class G> struct Dft<G, 5> {
         v[3] = csub(a2, b2);
     }
 };
-template <class G> struct Dft<G, 8> {
-    // radix 8 = radix 2 over two radix-4 halves with the e^{+2 pi i k/8} twiddles
+
+// Composite R = A B: with r = B r1 + r2 and q = q1 + A q2,
+// w_R^{rq} = w_A^{r1 q1} w_R^{r2 q1} w_B^{r2 q2}:
+// A-point DFTs over r1 for every r2, twiddles w_R^{r2 q1}, B-point DFTs over r2.
+template <class G, int R, int A, int R2, int Q1>
+__device__ __forceinline__ void col_twiddle(const cpx<G> *t, cpx<G> *u)
+{
+    if constexpr (Q1 < A) {
+        u[Q1] = twm<G, R2 * Q1, R>(t[Q1]);
+        col_twiddle<G, R, A, R2, Q1 + 1>(t, u);
+    }
+}
+
+template <class G, int R, int A, int B, int R2>
+__device__ __forceinline__ void col_pass(const cpx<G> *v, cpx<G> (*U)[A])
+{
+    if constexpr (R2 < B) {
+        cpx<G> t[A];
+#pragma unroll
+        for (int r1 = 0; r1 < A; ++r1) t[r1] = v[B * r1 + R2];
+        Dft<G, A>::run(t);
+        col_twiddle<G, R, A, R2, 0>(t, U[R2]);
+        col_pass<G, R, A, B, R2 + 1>(v, U);
+    }
+}
+
+template <class G, int R> struct Dft {
     static __device__ __forceinline__ void run(cpx<G> *v)
     {
-        const G r = (G)0.70710678118654752440;
-        cpx<G> e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
-        Dft<G, 4>::run(e);
-        Dft<G, 4>::run(o);
-        // o[k] *= e^{+2 pi i k / 8}
-        o[1] = cmk<G>(r * (o[1].x - o[1].y), r * (o[1].x + o[1].y));
-        o[2] = cmuli(o[2]);
-        o[3] = cmk<G>(-r * (o[3].x + o[3].y), r * (o[3].x - o[3].y));
-        for (int k = 0; k < 4; ++k) {
-            v[k] = cadd(e[k], o[k]);
-            v[k + 4] = csub(e[k], o[k]);
+        constexpr int A = Fac<R>::A, B = Fac<R>::B;
+        cpx<G> U[B][A];
+        col_pass<G, R, A, B, 0>(v, U);
+#pragma unroll
+        for (int q1 = 0; q1 < A; ++q1) {
+            cpx<G> t[B];
+#pragma unroll
+            for (int r2 = 0; r2 < B; ++r2) t[r2] = U[r2][q1];
+            Dft<G, B>::run(t);
+#pragma unroll
+            for (int q2 = 0; q2 < B; ++q2) v[q1 + A * q2] = t[q2];
         }
     }
 };
 
-// One Stockham stage of radix RD over the R rows: x -> y.
-template <class G, int RD>
-__device__ __forceinline__ void stage(const cpx<G> *__restrict__ x, cpx<G> *__restrict__ y, int M, int R, int Ns,
-                                      const cpx<G> *__restrict__ tw)
+// ---------------------------------------------------------------- stages
+__device__ __forceinline__ unsigned fdiv(unsigned n, unsigned mul, unsigned sh)
 {
+    return (__umulhi(n, mul) + n) >> sh;
+}
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+
+template <class G, int RD>
+__device__ __forceinline__ void stage(const cpx<G> *__restrict__ x, cpx<G> *__restrict__ y, const DimGeom &dg,
+                                      int s, int nrows, int Ns, const cpx<G> *__restrict__ tw)
+{
+    const int M = dg.M;
     const int MR = M / RD;
-    const int per = R * MR;
+    const int per = nrows * MR;
     const int twstep = M / (Ns * RD);
     for (int bi = threadIdx.x; bi < per; bi += kThreads) {
-        const int row = bi / MR;
+        const int row = (int)fdiv((unsigned)bi, dg.mr_mul[s], dg.mr_sh[s]);
         const int j = bi - row * MR;
-        const int k = j % Ns;
-        const cpx<G> *src = x + row * M + j;
+        const int jq = (int)fdiv((unsigned)j, dg.ns_mul[s], dg.ns_sh[s]);
+        const int k = j - jq * Ns;
+        const int base = row * M;
         cpx<G> v[RD];
 #pragma unroll
-        for (int q = 0; q < RD; ++q) v[q] = src[q * MR];
+        for (int q = 0; q < RD; ++q) v[q] = x[pad(base + j + q * MR)];
         if (Ns > 1) {
 #pragma unroll
             for (int q = 1; q < RD; ++q) v[q] = cmul(v[q], tw[q * k * twstep]);
         }
         Dft<G, RD>::run(v);
-        cpx<G> *dst = y + row * M + (j / Ns) * Ns * RD + k;
+        const int o = base + jq * Ns * RD + k;
 #pragma unroll
-        for (int q = 0; q < RD; ++q) dst[q * Ns] = v[q];
+        for (int q = 0; q < RD; ++q) y[pad(o + q * Ns)] = v[q];
     }
     __syncthreads();
 }
+
+template <class G>
+__device__ __forceinline__ void run_stage(int rd, const cpx<G> *x, cpx<G> *y, const DimGeom &dg, int s, int nrows,
+                                          int Ns, const cpx<G> *tw)
+{
+    switch (rd) {
+    case 2: stage<G, 2>(x, y, dg, s, nrows, Ns, tw); break;
+    case 3: stage<G, 3>(x, y, dg, s, nrows, Ns, tw); break;
+    case 4: stage<G, 4>(x, y, dg, s, nrows, Ns, tw); break;
+    case 5: stage<G, 5>(x, y, dg, s, nrows, Ns, tw); break;
+    case 6: stage<G, 6>(x, y, dg, s, nrows, Ns, tw); break;
+    case 8: stage<G, 8>(x, y, dg, s, nrows, Ns, tw); break;
+    case 9: stage<G, 9>(x, y, dg, s, nrows, Ns, tw); break;
+    case 10: stage<G, 10>(x, y, dg, s, nrows, Ns, tw); break;
+    case 12: stage<G, 12>(x, y, dg, s, nrows, Ns, tw); break;
+    case 15: stage<G, 15>(x, y, dg, s, nrows, Ns, tw); break;
+    default: stage<G, 16>(x, y, dg, s, nrows, Ns, tw); break;
+    }
+}
+
+template <class G> struct FftCfg;
+template <> struct FftCfg<float> { static constexpr int kRowsElems = 4096; };
+template <> struct FftCfg<double> { static constexpr int kRowsElems = 2048; };
+
+int fft_rows_per_cta(int M, int elem_bytes)
+{
+    const int cap = elem_bytes == 4 ? FftCfg<float>::kRowsElems : FftCfg<double>::kRowsElems;
+    int R = cap / M;
+    return R < 1 ? 1 : (R > 8 ? 8 : R);
+}
+
+__host__ __device__ __forceinline__ size_t buf_elems(int R, int M) { return (size_t)R * M + ((size_t)R * M >> 4) + 1; }
+
+size_t fft_pass_smem_bytes(int M, int elem_bytes)
+{
+    return 2 * buf_elems(fft_rows_per_cta(M, elem_bytes), M) * 2 * elem_bytes;
+}
+
+// longest row: two padded buffers of one row within 200 KB of shared memory
+int fft_max_M(int elem_bytes) { return elem_bytes == 4 ? 12000 : 6000; }
 
 template <class G>
 __global__ void __launch_bounds__(kThreads) k_fft_rows(const cpx<G> *__restrict__ in, cpx<G> *__restrict__ out,
@@ -148,32 +284,30 @@ __global__ void __launch_bounds__(kThreads) k_fft_rows(const cpx<G> *__restrict_
                                                        const cpx<G> *__restrict__ tw, int R)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<G> *sm = reinterpret_cast<cpx<G> *>(smem_raw);
     const int M = dg.M, N = dg.nf1, B = dg.B, H = dg.H;
+    cpx<G> *buf0 = reinterpret_cast<cpx<G> *>(smem_raw);
+    cpx<G> *buf1 = buf0 + buf_elems(R, M);
     const int half = N / 2;
     for (long row0 = (long)blockIdx.x * R; row0 < rows; row0 += (long)gridDim.x * R) {
         const int nr = (int)((rows - row0) < R ? (rows - row0) : R);
         // load + prescale + zero padding: slot m holds l = m + N/2 (m < N - N/2) or l = m - M + N/2
-        for (int idx = threadIdx.x; idx < R * M; idx += kThreads) {
-            const int r = idx / M;
-            const int m = idx - r * M;
-            int l = -1;
-            if (m < N - half) l = m + half;
-            else if (m >= M - half) l = m - M + half;
-            cpx<G> v = cmk<G>((G)0, (G)0);
-            if (l >= 0 && r < nr) v = cscale(in[(size_t)(row0 + r) * N + l], pre[l]);
-            sm[idx] = v;
+        for (int r = 0; r < R; ++r) {
+            const cpx<G> *src = in + (size_t)(row0 + r) * N;
+            for (int m = threadIdx.x; m < M; m += kThreads) {
+                int l = -1;
+                if (m < N - half) l = m + half;
+                else if (m >= M - half) l = m - M + half;
+                cpx<G> v = cmk<G>((G)0, (G)0);
+                if (l >= 0 && r < nr) v = cscale(src[l], pre[l]);
+                buf0[pad(r * M + m)] = v;
+            }
         }
         __syncthreads();
-        cpx<G> *x = sm, *y = sm + R * M;
+        cpx<G> *x = buf0, *y = buf1;
         int Ns = 1;
         for (int s = 0; s < dg.nstages; ++s) {
             const int rd = dg.radix[s];
-            if (rd == 8) stage<G, 8>(x, y, M, R, Ns, tw);
-            else if (rd == 4) stage<G, 4>(x, y, M, R, Ns, tw);
-            else if (rd == 2) stage<G, 2>(x, y, M, R, Ns, tw);
-            else if (rd == 3) stage<G, 3>(x, y, M, R, Ns, tw);
-            else stage<G, 5>(x, y, M, R, Ns, tw);
+            run_stage<G>(rd, x, y, dg, s, R, Ns, tw);
             cpx<G> *t = x; x = y; y = t;
             Ns *= rd;
         }
@@ -181,9 +315,10 @@ __global__ void __launch_bounds__(kThreads) k_fft_rows(const cpx<G> *__restrict_
         for (int idx = threadIdx.x; idx < B * nr; idx += kThreads) {
             const int b = idx / nr;
             const int r = idx - b * nr;
-            int m = (b - H) % M;
-            if (m < 0) m += M;
-            out[(size_t)b * rows + row0 + r] = x[r * M + m];
+            int m = b - H;
+            while (m < 0) m += M;
+            while (m >= M) m -= M;
+            out[(size_t)b * rows + row0 + r] = x[pad(r * M + m)];
         }
         __syncthreads();
     }
@@ -195,15 +330,15 @@ cudaError_t launch_fft_pass(const cpx<G> *in, cpx<G> *out, long rows, const DimG
 {
     if (rows <= 0) return cudaSuccess;
     if (dg.M > fft_max_M(sizeof(G))) return cudaErrorInvalidValue;
-    const int R = rows_per_cta(dg.M, sizeof(G));
-    const size_t smem = (size_t)2 * R * dg.M * sizeof(cpx<G>);
+    const int R = fft_rows_per_cta(dg.M, sizeof(G));
+    const size_t smem = 2 * buf_elems(R, dg.M) * sizeof(cpx<G>);
     static bool attr_set[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_set[dev]) {
-        e = cudaFuncSetAttribute(k_fft_rows<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 196608);
+        e = cudaFuncSetAttribute(k_fft_rows<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210000);
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
@@ -217,5 +352,53 @@ template cudaError_t launch_fft_pass<double>(const cpx<double> *, cpx<double> *,
                                              const double *, const cpx<double> *, cudaStream_t);
 template cudaError_t launch_fft_pass<float>(const cpx<float> *, cpx<float> *, long, const DimGeom &, const float *,
                                             const cpx<float> *, cudaStream_t);
+
+// ---------------------------------------------------------------- host planning
+static const int kRadices[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+
+static bool factor_into(int M, int maxStages, int *rad, int &n)
+{
+    if (M == 1) return true;
+    if (maxStages == 0) return false;
+    for (int r : kRadices)
+        if (M % r == 0) {
+            rad[n++] = r;
+            if (factor_into(M / r, maxStages - 1, rad, n)) return true;
+            --n;
+        }
+    return false;
+}
+
+// multiply-high division by d: q = (umulhi(n, mul) + n) >> sh for n < 2^31
+static void magic_u32(unsigned d, unsigned &mul, unsigned &sh)
+{
+    unsigned s = 0;
+    while ((1ull << s) < d) ++s;
+    sh = s;
+    mul = (unsigned)((((1ull << 32) * ((1ull << s) - d)) / d) + 1);
+}
+
+int fft_choose_length(int target, int *radix, int &nstages)
+{
+    const int maxStages = target <= 4096 ? 3 : 4;
+    for (int M = target + (target & 1); M <= 4 * target + 64; M += 2) {
+        int n = 0;
+        if (factor_into(M, maxStages, radix, n)) {
+            nstages = n;
+            return M;
+        }
+    }
+    return -1;
+}
+
+void fft_stage_constants(DimGeom &dg)
+{
+    int Ns = 1;
+    for (int s = 0; s < dg.nstages; ++s) {
+        magic_u32((unsigned)(dg.M / dg.radix[s]), dg.mr_mul[s], dg.mr_sh[s]);
+        magic_u32((unsigned)Ns, dg.ns_mul[s], dg.ns_sh[s]);
+        Ns *= dg.radix[s];
+    }
+}
 
 }  // namespace fv

@@ -18,7 +18,7 @@
 #include <stdint.h>
 
 #define FV_C_LIGHT 299792458.0
-#define FV_MAX_STAGES 24
+#define FV_MAX_STAGES 8
 #define FV_ZDIRECT_MAX 16
 
 namespace fv {
@@ -47,6 +47,8 @@ struct DimGeom {
     double C;       // source centre
     int nstages;
     int radix[FV_MAX_STAGES];
+    unsigned mr_mul[FV_MAX_STAGES], mr_sh[FV_MAX_STAGES];   // division by M / radix[s]
+    unsigned ns_mul[FV_MAX_STAGES], ns_sh[FV_MAX_STAGES];   // division by prod(radix[0..s-1])
 };
 
 struct BeamParams {
@@ -125,6 +127,11 @@ cudaError_t launch_prep(const double *sdir, const int *sidx, const int *nv_ptr, 
                         int flux_fp64, int n_freq, int f, const SliceGeom &g, int *cell, G *frac, cpx<G> *cs,
                         cudaStream_t st);
 
+// Gather-spreading configuration for a grid precision, product count and z
+// size: returns 0 if unsupported, else the z template size and columns per
+// thread (tile = 32 x (8 * columns per thread)).
+int spread_gather_config(int elem_bytes, int n_pol, int nz, int w, int *nz_tmpl, int *cpt);
+
 // Per slice: tiled spreading; writes every cell of grid [n_pol][nz][ny][nx].
 template <class G>
 cudaError_t launch_spread_tile(const int *offsets, const int *cell, const G *frac, const cpx<G> *cs, long n_src,
@@ -156,5 +163,11 @@ cudaError_t launch_scatter(const cpx<double> *Vu, const int *bl2u, int n_bl, int
 
 size_t fft_pass_smem_bytes(int M, int elem_bytes);
 int fft_max_M(int elem_bytes);
+int fft_rows_per_cta(int M, int elem_bytes);
+// Smallest even M >= target that is a product of at most 3 (4 above 4096)
+// supported radices; fills radix[] and nstages.  -1 if none.
+int fft_choose_length(int target, int *radix, int &nstages);
+// Per-stage multiply-high division constants of dg (needs M, nstages, radix).
+void fft_stage_constants(DimGeom &dg);
 
 }  // namespace fv

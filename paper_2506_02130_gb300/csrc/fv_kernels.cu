@@ -364,22 +364,28 @@ __global__ void __launch_bounds__(256) k_interp_zdirect(const cpx<G> *__restrict
         fr[i] = (G)(p - m);
     }
     const int Nz = g.d == 3 ? g.dim[2].nf1 : 1;
-    cpx<G> K[16];
-    if (g.d == 3) {
+    // lane lz < Nz builds K(l_z); the vector is then shared through shuffles
+    cpx<G> Kmine = cmk<G>((G)1, (G)0);
+    if (g.d == 3 && lane < Nz) {
         const int Mz = g.dim[2].M;
-        for (int lz = 0; lz < Nz; ++lz) {
-            const int lc = lz - Nz / 2;
-            cpx<G> acc = cmk<G>((G)0, (G)0);
-            for (int jz = 0; jz < w; ++jz) {
-                G wt = es_kernel(two_over_w * (fr[2] - (G)jz), beta);
-                int e = (lc * (m0[2] + jz)) % Mz;
-                if (e < 0) e += Mz;
-                acc = cadd(acc, cscale(twz[e], wt));
-            }
-            K[lz] = cscale(acc, prez[lz]);
+        const int lc = lane - Nz / 2;
+        cpx<G> acc = cmk<G>((G)0, (G)0);
+        int e = (lc * m0[2]) % Mz;
+        if (e < 0) e += Mz;
+        int step = lc % Mz;
+        if (step < 0) step += Mz;
+        for (int jz = 0; jz < w; ++jz) {
+            const G wt = es_kernel(two_over_w * (fr[2] - (G)jz), beta);
+            acc = cadd(acc, cscale(twz[e], wt));
+            e += step;
+            if (e >= Mz) e -= Mz;
         }
-    } else {
-        K[0] = cmk<G>((G)1, (G)0);
+        Kmine = cscale(acc, prez[lane]);
+    }
+    cpx<G> K[16];
+    for (int lz = 0; lz < Nz; ++lz) {
+        K[lz].x = __shfl_sync(0xffffffffu, Kmine.x, lz);
+        K[lz].y = __shfl_sync(0xffffffffu, Kmine.y, lz);
     }
     const int np = g.n_pol;
     const int Bx = g.dim[0].B;

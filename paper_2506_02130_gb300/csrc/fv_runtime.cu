@@ -39,18 +39,6 @@ int next235even(long n)
     }
 }
 
-// Stockham stage radices for M = 2^a 3^b 5^c (eights first).
-int radix_plan(int M, int *rad)
-{
-    int n = 0;
-    while (M % 8 == 0) { rad[n++] = 8; M /= 8; }
-    while (M % 4 == 0) { rad[n++] = 4; M /= 4; }
-    while (M % 2 == 0) { rad[n++] = 2; M /= 2; }
-    while (M % 3 == 0) { rad[n++] = 3; M /= 3; }
-    while (M % 5 == 0) { rad[n++] = 5; M /= 5; }
-    return M == 1 ? n : -1;
-}
-
 // Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
 void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
 {
@@ -200,8 +188,8 @@ static fv_status prepare(fv_plan_s *p)
             if (nf1 < w + 2) nf1 = w + 2;     // Eq. 5 is the requirement; no 2w floor is needed
             if (nf1 > (1L << 20)) return p->fail(FV_ERR_UNSUPPORTED, "spreading grid too large");
             dg.nf1 = next235even(nf1);
-            dg.M = next235even((long)std::ceil(p->sigma * dg.nf1 - 1e-9));
-            if (dg.M > maxM)
+            dg.M = fft_choose_length((int)std::ceil(p->sigma * dg.nf1 - 1e-9), dg.radix, dg.nstages);
+            if (dg.M < 0 || dg.M > maxM)
                 return p->fail(FV_ERR_UNSUPPORTED, "FFT length " + std::to_string(dg.M) + " exceeds " +
                                                        std::to_string(maxM) + " for one-CTA FFT passes");
             dg.H = (int)std::ceil(dg.M / (2.0 * p->sigma) + 0.5 * w) + 1;
@@ -210,8 +198,7 @@ static fv_status prepare(fv_plan_s *p)
             dg.pscale = dg.M / (2.0 * p->sigma * X);
             dg.D = -g.kappa * p->bcen[i];
             dg.C = p->C[i];
-            dg.nstages = radix_plan(dg.M, dg.radix);
-            if (dg.nstages < 0 || dg.nstages > FV_MAX_STAGES) return p->fail(FV_ERR_UNSUPPORTED, "bad FFT length");
+            fft_stage_constants(dg);
             p->nf1_max[i] = std::max(p->nf1_max[i], dg.nf1);
             p->M_max[i] = std::max(p->M_max[i], dg.M);
             p->pre_off[(size_t)f * 3 + i] = pre_total;
@@ -263,12 +250,11 @@ static fv_status prepare(fv_plan_s *p)
         p->nf1_top[i] = p->gf[p->f_top].dim[i].nf1;
     }
     {
-        const size_t budget = p->precision == FV_FP64 ? 96 * 1024 : 48 * 1024;
-        const size_t nzm = p->d == 3 ? (size_t)p->nf1_max[2] : 1;
+        const int nzm = p->d == 3 ? p->nf1_max[2] : 1;
+        int nz_t = 0, cpt = 0;
+        p->tiled = spread_gather_config((int)gs, p->n_pol, nzm, w, &nz_t, &cpt) != 0;
         p->T[0] = 32;
-        p->T[1] = 32;
-        while ((size_t)p->T[0] * p->T[1] * nzm * p->n_pol * es > budget && p->T[1] > 4) p->T[1] /= 2;
-        p->tiled = (size_t)p->T[0] * p->T[1] * nzm * p->n_pol * es <= budget && p->d >= 2 && w <= 16;
+        p->T[1] = 8 * (cpt > 0 ? cpt : 1);
         p->nbx = (p->nf1_top[0] + p->T[0] - 1) / p->T[0];
         p->nby = (p->nf1_top[1] + p->T[1] - 1) / p->T[1];
     }
@@ -434,6 +420,9 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
     if (o->dims != 0 && o->dims != 2 && o->dims != 3) return bad("dims must be 0, 2 or 3");
     double sigma = o->upsampfac == 0.0 ? 2.0 : o->upsampfac;
     if (!(sigma >= 1.25 && sigma <= 3.0)) return bad("upsampfac must be in [1.25, 3]");
+    // the two deconvolutions amplify FP32 rounding by (Phihat(0)/Phihat(w pi/2 sigma))^2 at the band
+    // edge: about 2e4 at sigma = 1.25 against 6 at sigma = 2, too much for FP32 spreading and FFTs
+    if (o->precision == FV_MIXED && sigma < 1.5) return bad("FV_MIXED needs upsampfac >= 1.5");
     int w = o->kernel_width;
     if (w == 0) {
         if (std::fabs(sigma - 2.0) < 1e-12)

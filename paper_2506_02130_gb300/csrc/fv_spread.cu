@@ -10,11 +10,12 @@
 //                  with the argument and its 2 pi reduction in FP64, and the
 //                  grid coordinate q = (s - C) sigma X / pi split in FP64 into
 //                  the first footprint cell (int) and an offset (FP32 or FP64);
-//   k_spread_tile  one CTA per output tile: accumulate every source whose
-//                  footprint meets the tile with shared-memory atomics, then
-//                  store the whole tile once.  Every grid cell is written by
-//                  exactly one CTA, so the grid needs no clearing and no
-//                  global atomics.
+//   k_spread_gather one CTA per output tile: every thread owns (x, y) columns
+//                  of the tile and adds, in registers, the sources whose
+//                  footprint covers them (staged in shared memory with their
+//                  kernel values), then stores its cells once.  Every grid
+//                  cell is written by exactly one thread, so the grid needs
+//                  no clearing and there are no atomics.
 // A channel's grid coordinates are the top channel's scaled by r = qscale_f /
 // qscale_top <= 1 per axis, so a tile of channel f maps to a rectangle of top
 // bins, i.e. one contiguous range of sorted sources per bin row.
@@ -218,78 +219,133 @@ cudaError_t launch_prep(const double *sdir, const int *sidx, const int *nv_ptr, 
     return cudaGetLastError();
 }
 
-template <class G>
-__global__ void __launch_bounds__(256) k_spread_tile(const int *__restrict__ offsets, const int *__restrict__ cell,
-                                                     const G *__restrict__ frac, const cpx<G> *__restrict__ cs,
-                                                     long n_src, SliceGeom g, TimeBin tb, double r0, double r1,
-                                                     cpx<G> *__restrict__ grid)
+// Gather form of the tiled spreading: each thread owns CPT (x, y) columns of
+// the CTA's tile and keeps all NZ z cells and NP polarisation products of
+// them in registers.  The candidate sources of the tile are staged in shared
+// memory in chunks, each with its per-axis kernel values computed once; every
+// thread then adds the sources whose footprint covers its columns.  No
+// atomics; each grid cell is stored once by its owner thread.
+constexpr int kGatherThreads = 256;
+constexpr int kGatherChunk = 64;
+constexpr int kWmax = 16;
+
+template <class G, int NP, int NZ, int CPT>
+__global__ void __launch_bounds__(kGatherThreads) k_spread_gather(const int *__restrict__ offsets,
+                                                                  const int *__restrict__ cell,
+                                                                  const G *__restrict__ frac,
+                                                                  const cpx<G> *__restrict__ cs, long n_src,
+                                                                  SliceGeom g, TimeBin tb, double r0, double r1,
+                                                                  cpx<G> *__restrict__ grid)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<G> *tile = reinterpret_cast<cpx<G> *>(smem_raw);
+    __shared__ int s_cx[kGatherChunk], s_cy[kGatherChunk], s_cz[kGatherChunk];
+    __shared__ G s_w[3][kGatherChunk * kWmax];
+    __shared__ cpx<G> s_c[NP][kGatherChunk];
     const int Tx = tb.T[0], Ty = tb.T[1];
     const int nx = g.dim[0].nf1, ny = g.dim[1].nf1, nz = g.d == 3 ? g.dim[2].nf1 : 1;
-    const int np = g.n_pol, w = g.w;
+    const int w = g.w;
     const int x0 = blockIdx.x * Tx, y0 = blockIdx.y * Ty;
-    const int tsz = Tx * Ty * nz * np;
-    for (int i = threadIdx.x; i < tsz; i += blockDim.x) tile[i] = cmk<G>((G)0, (G)0);
-    // sources whose footprint can meet this tile have q in [x0 - nf1/2 - w/2, x0 + T - nf1/2 + w/2 - 1];
-    // map to top cells with a one-cell margin on each side
+    int gx[CPT], gy[CPT];
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+        const int c = threadIdx.x + k * kGatherThreads;
+        gx[k] = x0 + c % Tx;
+        gy[k] = y0 + c / Tx;
+    }
+    cpx<G> acc[CPT][NP][NZ];
+#pragma unroll
+    for (int k = 0; k < CPT; ++k)
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+#pragma unroll
+            for (int z = 0; z < NZ; ++z) acc[k][p][z] = cmk<G>((G)0, (G)0);
+    // sources whose footprint can meet this tile (one-cell margin through the top-grid mapping)
     const double qx_lo = (x0 - nx / 2 - 0.5 * w) / r0, qx_hi = (x0 + Tx - nx / 2 + 0.5 * w - 1) / r0;
     const double qy_lo = (y0 - ny / 2 - 0.5 * w) / r1, qy_hi = (y0 + Ty - ny / 2 + 0.5 * w - 1) / r1;
     const int bx_lo = top_cell(qx_lo - 1.0, tb.nf1_top[0]) / Tx, bx_hi = top_cell(qx_hi + 1.0, tb.nf1_top[0]) / Tx;
     const int by_lo = top_cell(qy_lo - 1.0, tb.nf1_top[1]) / Ty, by_hi = top_cell(qy_hi + 1.0, tb.nf1_top[1]) / Ty;
-    __syncthreads();
     const G two_over_w = (G)(2.0 / w), beta = (G)g.beta;
     for (int by = by_lo; by <= by_hi; ++by) {
         const int i0 = offsets[by * tb.nbx + bx_lo], i1 = offsets[by * tb.nbx + bx_hi + 1];
-        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-            const int cx = cell[i], cy = cell[n_src + i];
-            const int jx0 = max(0, x0 - cx), jx1 = min(w, x0 + Tx - cx);
-            const int jy0 = max(0, y0 - cy), jy1 = min(w, y0 + Ty - cy);
-            if (jx0 >= jx1 || jy0 >= jy1) continue;
-            const G fx = frac[i], fy = frac[n_src + i];
-            G wz[16];
-            int cz = 0;
-            if (g.d == 3) {
-                cz = cell[2 * n_src + i];
-                const G fz = frac[2 * n_src + i];
-                for (int j = 0; j < w; ++j) wz[j] = es_k<G>(two_over_w * (fz + (G)j), beta);
-            } else {
-                wz[0] = (G)1;
+        for (int base = i0; base < i1; base += kGatherChunk) {
+            const int n = min(kGatherChunk, i1 - base);
+            // stage: one thread per source of the chunk
+            if (threadIdx.x < n) {
+                const int i = base + threadIdx.x;
+                const int t = threadIdx.x;
+                s_cx[t] = cell[i];
+                s_cy[t] = cell[n_src + i];
+                s_cz[t] = g.d == 3 ? cell[2 * n_src + i] : 0;
+                const G fx = frac[i], fy = frac[n_src + i];
+                const G fz = g.d == 3 ? frac[2 * n_src + i] : (G)0;
+                for (int j = 0; j < w; ++j) {
+                    s_w[0][t * kWmax + j] = es_k<G>(two_over_w * (fx + (G)j), beta);
+                    s_w[1][t * kWmax + j] = es_k<G>(two_over_w * (fy + (G)j), beta);
+                    s_w[2][t * kWmax + j] = g.d == 3 ? es_k<G>(two_over_w * (fz + (G)j), beta) : (G)(j == 0);
+                }
+#pragma unroll
+                for (int p = 0; p < NP; ++p) s_c[p][t] = cs[(size_t)p * n_src + i];
             }
-            const int wzn = g.d == 3 ? w : 1;
-            cpx<G> c[4];
-            for (int p = 0; p < np; ++p) c[p] = cs[(size_t)p * n_src + i];
-            for (int jy = jy0; jy < jy1; ++jy) {
-                const G wy = es_k<G>(two_over_w * (fy + (G)jy), beta);
-                const int ly = cy + jy - y0;
-                for (int jx = jx0; jx < jx1; ++jx) {
-                    const G wxy = wy * es_k<G>(two_over_w * (fx + (G)jx), beta);
-                    const int lx = cx + jx - x0;
-                    for (int jz = 0; jz < wzn; ++jz) {
-                        const G wt = wxy * wz[jz];
-                        const int z = cz + jz;
-                        if (z < 0 || z >= nz) continue;    // only reachable through rounding at the grid edge
-                        for (int p = 0; p < np; ++p) {
-                            cpx<G> *dst = &tile[((p * nz + z) * Ty + ly) * Tx + lx];
-                            atomicAdd(&dst->x, wt * c[p].x);
-                            atomicAdd(&dst->y, wt * c[p].y);
+            __syncthreads();
+            for (int t = 0; t < n; ++t) {
+                const int cx = s_cx[t], cy = s_cy[t], cz = s_cz[t];
+#pragma unroll
+                for (int k = 0; k < CPT; ++k) {
+                    const unsigned dx = (unsigned)(gx[k] - cx), dy = (unsigned)(gy[k] - cy);
+                    if (dx < (unsigned)w && dy < (unsigned)w) {
+                        const G wxy = s_w[0][t * kWmax + dx] * s_w[1][t * kWmax + dy];
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) {
+                            const cpx<G> cp = cscale(s_c[p][t], wxy);
+#pragma unroll
+                            for (int z = 0; z < NZ; ++z) {
+                                const unsigned jz = (unsigned)(z - cz);
+                                if (jz < (unsigned)w) {
+                                    const G wz = s_w[2][t * kWmax + jz];
+                                    acc[k][p][z].x += cp.x * wz;
+                                    acc[k][p][z].y += cp.y * wz;
+                                }
+                            }
                         }
                     }
                 }
             }
+            __syncthreads();
         }
     }
-    __syncthreads();
-    // store the whole tile (rows of Tx consecutive x)
-    for (int idx = threadIdx.x; idx < tsz; idx += blockDim.x) {
-        const int lx = idx % Tx;
-        int rest = idx / Tx;
-        const int ly = rest % Ty;
-        rest /= Ty;                       // rest = p * nz + z
-        const int x = x0 + lx, y = y0 + ly;
-        if (x < nx && y < ny) grid[((size_t)rest * ny + y) * nx + x] = tile[idx];
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+        if (gx[k] < nx && gy[k] < ny) {
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+#pragma unroll
+                for (int z = 0; z < NZ; ++z)
+                    if (z < nz) grid[(((size_t)p * nz + z) * ny + gy[k]) * nx + gx[k]] = acc[k][p][z];
+        }
     }
+}
+
+template <class G, int NP, int NZ, int CPT>
+static cudaError_t gather_launch(const int *offsets, const int *cell, const G *frac, const cpx<G> *cs, long n_src,
+                                 const SliceGeom &g, const TimeBin &tb, double r0, double r1, cpx<G> *grid,
+                                 cudaStream_t st)
+{
+    dim3 blocks((g.dim[0].nf1 + tb.T[0] - 1) / tb.T[0], (g.dim[1].nf1 + tb.T[1] - 1) / tb.T[1]);
+    k_spread_gather<G, NP, NZ, CPT><<<blocks, kGatherThreads, 0, st>>>(offsets, cell, frac, cs, n_src, g, tb, r0, r1,
+                                                                       grid);
+    return cudaGetLastError();
+}
+
+int spread_gather_config(int elem_bytes, int n_pol, int nz, int w, int *nz_tmpl, int *cpt)
+{
+    if (w > kWmax) return 0;
+    const int NZ = nz <= 1 ? 1 : (nz <= 8 ? 8 : (nz <= 16 ? 16 : 0));
+    if (NZ == 0) return 0;
+    const int budget = elem_bytes == 4 ? 32 : 16;       // complex accumulators per thread
+    int c = n_pol * NZ * 2 <= budget ? 2 : (n_pol * NZ <= budget ? 1 : 0);
+    if (c == 0) return 0;
+    *nz_tmpl = NZ;
+    *cpt = c;
+    return 1;
 }
 
 template <class G>
@@ -298,21 +354,26 @@ cudaError_t launch_spread_tile(const int *offsets, const int *cell, const G *fra
                                cudaStream_t st)
 {
     const int nz = g.d == 3 ? g.dim[2].nf1 : 1;
-    const size_t smem = (size_t)tb.T[0] * tb.T[1] * nz * g.n_pol * sizeof(cpx<G>);
-    static bool attr_set[64] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!attr_set[dev]) {
-        e = cudaFuncSetAttribute(k_spread_tile<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, FV_SPREAD_SMEM_MAX);
-        if (e != cudaSuccess) return e;
-        attr_set[dev] = true;
+    int NZ = 0, CPT = 0;
+    if (!spread_gather_config(sizeof(G), g.n_pol, nz, g.w, &NZ, &CPT)) return cudaErrorInvalidValue;
+    if (tb.T[0] * tb.T[1] != kGatherThreads * CPT) return cudaErrorInvalidValue;
+    const int key = (g.n_pol == 4 ? 100 : 0) + NZ * 10 + CPT;
+    switch (key) {
+    case 12: return gather_launch<G, 1, 1, 2>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+    case 11: return gather_launch<G, 1, 1, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+    case 82: return gather_launch<G, 1, 8, 2>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+    case 81: return gather_launch<G, 1, 8, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+    case 162:
+        if constexpr (sizeof(G) == 4) return gather_launch<G, 1, 16, 2>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+        else return cudaErrorInvalidValue;
+    case 161: return gather_launch<G, 1, 16, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+    case 112: return gather_launch<G, 4, 1, 2>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+    case 111: return gather_launch<G, 4, 1, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+    case 181:
+        if constexpr (sizeof(G) == 4) return gather_launch<G, 4, 8, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+        else return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
     }
-    if (smem > FV_SPREAD_SMEM_MAX) return cudaErrorInvalidValue;
-    dim3 blocks((g.dim[0].nf1 + tb.T[0] - 1) / tb.T[0], (g.dim[1].nf1 + tb.T[1] - 1) / tb.T[1]);
-    k_spread_tile<G><<<blocks, 256, smem, st>>>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid);
-    return cudaGetLastError();
 }
 
 template cudaError_t launch_prep<double>(const double *, const int *, const int *, long, const void *, int, int, int,

@@ -56,7 +56,8 @@ def _opts(**kw):
 
 @pytest.mark.parametrize("kw", [dict(eps=0.0), dict(eps=1e-15), dict(precision=1, eps=1e-9), dict(precision=7),
                                 dict(n_freq=0), dict(beam=9), dict(dims=4), dict(upsampfac=1.1),
-                                dict(kernel_width=40), dict(latitude_rad=2.0)])
+                                dict(kernel_width=40), dict(latitude_rad=2.0),
+                                dict(precision=1, eps=1e-6, upsampfac=1.25)])
 def test_invalid_options_rejected_before_device(lib, kw):
     o, keep = _opts(**kw)
     h = C.c_void_p()

@@ -74,8 +74,8 @@ def test_polarised_airy_jones(precision):
         assert rel_l2(out[..., p], ref[..., p]) <= TOL[precision] * 2, p
 
 
-@pytest.mark.parametrize("precision", [fv.FV_FP64, fv.FV_MIXED])
-@pytest.mark.parametrize("sigma", [1.25, 2.0])
+@pytest.mark.parametrize("precision,sigma", [(fv.FV_FP64, 1.25), (fv.FV_FP64, 2.0), (fv.FV_MIXED, 1.5),
+                                             (fv.FV_MIXED, 2.0)])
 def test_upsampling_factor(precision, sigma):
     prob = small_3d(seed=9, n_chan=2, n_time=1)
     out, _ = run_gpu(prob, precision, upsampfac=sigma)
