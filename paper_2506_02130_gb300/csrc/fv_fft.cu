@@ -278,6 +278,26 @@ size_t fft_pass_smem_bytes(int M, int elem_bytes)
 // longest row: two padded buffers of one row within 200 KB of shared memory
 int fft_max_M(int elem_bytes) { return elem_bytes == 4 ? 12000 : 6000; }
 
+// Input of one row block, held in registers between blocks so that the
+// global loads of block i+1 are in flight while block i runs its stages.
+template <class G> struct Prefetch {
+    static constexpr int kMax = FftCfg<G>::kRowsElems / kThreads;   // values per thread
+    cpx<G> v[kMax];
+};
+
+template <class G>
+__device__ __forceinline__ void prefetch_rows(Prefetch<G> &pf, const cpx<G> *__restrict__ in, long rows, long row0,
+                                              int R, int N)
+{
+    const int tot = R * N;
+#pragma unroll
+    for (int k = 0; k < Prefetch<G>::kMax; ++k) {
+        const int idx = threadIdx.x + k * kThreads;
+        const long r = row0 + idx / N;
+        pf.v[k] = (idx < tot && r < rows) ? in[row0 * N + idx] : cmk<G>((G)0, (G)0);
+    }
+}
+
 template <class G>
 __global__ void __launch_bounds__(kThreads) k_fft_rows(const cpx<G> *__restrict__ in, cpx<G> *__restrict__ out,
                                                        long rows, DimGeom dg, const G *__restrict__ pre,
@@ -288,21 +308,32 @@ __global__ void __launch_bounds__(kThreads) k_fft_rows(const cpx<G> *__restrict_
     cpx<G> *buf0 = reinterpret_cast<cpx<G> *>(smem_raw);
     cpx<G> *buf1 = buf0 + buf_elems(R, M);
     const int half = N / 2;
-    for (long row0 = (long)blockIdx.x * R; row0 < rows; row0 += (long)gridDim.x * R) {
+    const long stride = (long)gridDim.x * R;
+    Prefetch<G> pf;
+    long row0 = (long)blockIdx.x * R;
+    if (row0 < rows) prefetch_rows(pf, in, rows, row0, R, N);
+    for (; row0 < rows; row0 += stride) {
         const int nr = (int)((rows - row0) < R ? (rows - row0) : R);
-        // load + prescale + zero padding: slot m holds l = m + N/2 (m < N - N/2) or l = m - M + N/2
-        for (int r = 0; r < R; ++r) {
-            const cpx<G> *src = in + (size_t)(row0 + r) * N;
-            for (int m = threadIdx.x; m < M; m += kThreads) {
-                int l = -1;
-                if (m < N - half) l = m + half;
-                else if (m >= M - half) l = m - M + half;
-                cpx<G> v = cmk<G>((G)0, (G)0);
-                if (l >= 0 && r < nr) v = cscale(src[l], pre[l]);
-                buf0[pad(r * M + m)] = v;
+        // zero padding, then the prefetched row values with the prescale: l -> slot (l - N/2) mod M
+        for (int idx = threadIdx.x; idx < R * M; idx += kThreads) {
+            const int r = idx / M;
+            const int m = idx - r * M;
+            if (m >= N - half && m < M - half) buf0[pad(idx)] = cmk<G>((G)0, (G)0);
+        }
+#pragma unroll
+        for (int k = 0; k < Prefetch<G>::kMax; ++k) {
+            const int idx = threadIdx.x + k * kThreads;
+            if (idx < R * N) {
+                const int r = idx / N;
+                const int l = idx - r * N;
+                int m = l - half;
+                if (m < 0) m += M;
+                buf0[pad(r * M + m)] = cscale(pf.v[k], pre[l]);
             }
         }
         __syncthreads();
+        // issue the next block's loads before the stages
+        if (row0 + stride < rows) prefetch_rows(pf, in, rows, row0 + stride, R, N);
         cpx<G> *x = buf0, *y = buf1;
         int Ns = 1;
         for (int s = 0; s < dg.nstages; ++s) {
@@ -342,8 +373,18 @@ cudaError_t launch_fft_pass(const cpx<G> *in, cpx<G> *out, long rows, const DimG
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
+    // persistent CTAs: as many as fit on the device (each keeps a row block of prefetch in registers)
+    static int max_ctas[64] = {};
+    if (!max_ctas[dev]) {
+        int sms = 0, per_sm = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fft_rows<G>, kThreads, smem);
+        if (e != cudaSuccess) return e;
+        max_ctas[dev] = sms * (per_sm > 0 ? per_sm : 1);
+    }
     long ctas = (rows + R - 1) / R;
-    unsigned grid = (unsigned)(ctas < 1048576 ? ctas : 1048576);
+    unsigned grid = (unsigned)(ctas < max_ctas[dev] ? ctas : max_ctas[dev]);
     k_fft_rows<G><<<grid, kThreads, smem, st>>>(in, out, rows, dg, pre, tw, R);
     return cudaGetLastError();
 }

@@ -128,9 +128,9 @@ cudaError_t launch_prep(const double *sdir, const int *sidx, const int *nv_ptr, 
                         cudaStream_t st);
 
 // Gather-spreading configuration for a grid precision, product count and z
-// size: returns 0 if unsupported, else the z template size and columns per
-// thread (tile = 32 x (8 * columns per thread)).
-int spread_gather_config(int elem_bytes, int n_pol, int nz, int w, int *nz_tmpl, int *cpt);
+// size: returns 0 if unsupported, else the z template size and the bin size
+// (top-channel cells per bin in x and y).
+int spread_gather_config(int elem_bytes, int n_pol, int nz, int w, int *nz_tmpl, int *bin_x, int *bin_y);
 
 // Per slice: tiled spreading; writes every cell of grid [n_pol][nz][ny][nx].
 template <class G>

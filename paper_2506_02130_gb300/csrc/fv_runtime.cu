@@ -251,10 +251,10 @@ static fv_status prepare(fv_plan_s *p)
     }
     {
         const int nzm = p->d == 3 ? p->nf1_max[2] : 1;
-        int nz_t = 0, cpt = 0;
-        p->tiled = spread_gather_config((int)gs, p->n_pol, nzm, w, &nz_t, &cpt) != 0;
-        p->T[0] = 32;
-        p->T[1] = 8 * (cpt > 0 ? cpt : 1);
+        int nz_t = 0, bx = 8, by = 4;
+        p->tiled = spread_gather_config((int)gs, p->n_pol, nzm, w, &nz_t, &bx, &by) != 0;
+        p->T[0] = bx;
+        p->T[1] = by;
         p->nbx = (p->nf1_top[0] + p->T[0] - 1) / p->T[0];
         p->nby = (p->nf1_top[1] + p->T[1] - 1) / p->T[1];
     }

@@ -219,17 +219,21 @@ cudaError_t launch_prep(const double *sdir, const int *sidx, const int *nv_ptr, 
     return cudaGetLastError();
 }
 
-// Gather form of the tiled spreading: each thread owns CPT (x, y) columns of
-// the CTA's tile and keeps all NZ z cells and NP polarisation products of
-// them in registers.  The candidate sources of the tile are staged in shared
-// memory in chunks, each with its per-axis kernel values computed once; every
-// thread then adds the sources whose footprint covers its columns.  No
-// atomics; each grid cell is stored once by its owner thread.
+// Gather form of the tiled spreading.  A CTA of 8 warps owns a 32 x 8 tile
+// of (x, y) columns; warp k owns an 8 x 4 patch of it and each lane one
+// column, holding that column's NZ z cells and NP products in registers.  The
+// tile's candidate sources (bins of 8 x 4 top-channel cells, so the candidate
+// set overshoots the tile's footprint region by little) are staged in shared
+// memory in chunks with their per-axis kernel values; each warp tests a
+// candidate's footprint box against its patch (a warp-uniform branch) and only
+// the overlapping warps add it.  No atomics; every grid cell is stored once.
 constexpr int kGatherThreads = 256;
-constexpr int kGatherChunk = 64;
+constexpr int kGatherChunk = 128;
 constexpr int kWmax = 16;
+constexpr int kPatchX = 8, kPatchY = 4;     // one warp
+constexpr int kTileX = 32, kTileY = 8;      // one CTA (4 x 2 patches)
 
-template <class G, int NP, int NZ, int CPT>
+template <class G, int NP, int NZ>
 __global__ void __launch_bounds__(kGatherThreads) k_spread_gather(const int *__restrict__ offsets,
                                                                   const int *__restrict__ cell,
                                                                   const G *__restrict__ frac,
@@ -240,35 +244,29 @@ __global__ void __launch_bounds__(kGatherThreads) k_spread_gather(const int *__r
     __shared__ int s_cx[kGatherChunk], s_cy[kGatherChunk], s_cz[kGatherChunk];
     __shared__ G s_w[3][kGatherChunk * kWmax];
     __shared__ cpx<G> s_c[NP][kGatherChunk];
-    const int Tx = tb.T[0], Ty = tb.T[1];
     const int nx = g.dim[0].nf1, ny = g.dim[1].nf1, nz = g.d == 3 ? g.dim[2].nf1 : 1;
     const int w = g.w;
-    const int x0 = blockIdx.x * Tx, y0 = blockIdx.y * Ty;
-    int gx[CPT], gy[CPT];
+    const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int px0 = x0 + (warp & 3) * kPatchX, py0 = y0 + (warp >> 2) * kPatchY;   // this warp's patch
+    const int gx = px0 + (lane & 7), gy = py0 + (lane >> 3);                         // this lane's column
+    cpx<G> acc[NP][NZ];
 #pragma unroll
-    for (int k = 0; k < CPT; ++k) {
-        const int c = threadIdx.x + k * kGatherThreads;
-        gx[k] = x0 + c % Tx;
-        gy[k] = y0 + c / Tx;
-    }
-    cpx<G> acc[CPT][NP][NZ];
+    for (int p = 0; p < NP; ++p)
 #pragma unroll
-    for (int k = 0; k < CPT; ++k)
-#pragma unroll
-        for (int p = 0; p < NP; ++p)
-#pragma unroll
-            for (int z = 0; z < NZ; ++z) acc[k][p][z] = cmk<G>((G)0, (G)0);
+        for (int z = 0; z < NZ; ++z) acc[p][z] = cmk<G>((G)0, (G)0);
     // sources whose footprint can meet this tile (one-cell margin through the top-grid mapping)
-    const double qx_lo = (x0 - nx / 2 - 0.5 * w) / r0, qx_hi = (x0 + Tx - nx / 2 + 0.5 * w - 1) / r0;
-    const double qy_lo = (y0 - ny / 2 - 0.5 * w) / r1, qy_hi = (y0 + Ty - ny / 2 + 0.5 * w - 1) / r1;
-    const int bx_lo = top_cell(qx_lo - 1.0, tb.nf1_top[0]) / Tx, bx_hi = top_cell(qx_hi + 1.0, tb.nf1_top[0]) / Tx;
-    const int by_lo = top_cell(qy_lo - 1.0, tb.nf1_top[1]) / Ty, by_hi = top_cell(qy_hi + 1.0, tb.nf1_top[1]) / Ty;
+    const double qx_lo = (x0 - nx / 2 - 0.5 * w) / r0, qx_hi = (x0 + kTileX - nx / 2 + 0.5 * w - 1) / r0;
+    const double qy_lo = (y0 - ny / 2 - 0.5 * w) / r1, qy_hi = (y0 + kTileY - ny / 2 + 0.5 * w - 1) / r1;
+    const int bx_lo = top_cell(qx_lo - 1.0, tb.nf1_top[0]) / tb.T[0];
+    const int bx_hi = top_cell(qx_hi + 1.0, tb.nf1_top[0]) / tb.T[0];
+    const int by_lo = top_cell(qy_lo - 1.0, tb.nf1_top[1]) / tb.T[1];
+    const int by_hi = top_cell(qy_hi + 1.0, tb.nf1_top[1]) / tb.T[1];
     const G two_over_w = (G)(2.0 / w), beta = (G)g.beta;
     for (int by = by_lo; by <= by_hi; ++by) {
         const int i0 = offsets[by * tb.nbx + bx_lo], i1 = offsets[by * tb.nbx + bx_hi + 1];
         for (int base = i0; base < i1; base += kGatherChunk) {
             const int n = min(kGatherChunk, i1 - base);
-            // stage: one thread per source of the chunk
             if (threadIdx.x < n) {
                 const int i = base + threadIdx.x;
                 const int t = threadIdx.x;
@@ -287,23 +285,23 @@ __global__ void __launch_bounds__(kGatherThreads) k_spread_gather(const int *__r
             }
             __syncthreads();
             for (int t = 0; t < n; ++t) {
-                const int cx = s_cx[t], cy = s_cy[t], cz = s_cz[t];
+                const int cx = s_cx[t], cy = s_cy[t];
+                // footprint [cx, cx+w) x [cy, cy+w) against the warp's patch: uniform across the warp
+                if (cx + w <= px0 || cx >= px0 + kPatchX || cy + w <= py0 || cy >= py0 + kPatchY) continue;
+                const unsigned dx = (unsigned)(gx - cx), dy = (unsigned)(gy - cy);
+                if (dx < (unsigned)w && dy < (unsigned)w) {
+                    const int cz = s_cz[t];
+                    const G wxy = s_w[0][t * kWmax + dx] * s_w[1][t * kWmax + dy];
 #pragma unroll
-                for (int k = 0; k < CPT; ++k) {
-                    const unsigned dx = (unsigned)(gx[k] - cx), dy = (unsigned)(gy[k] - cy);
-                    if (dx < (unsigned)w && dy < (unsigned)w) {
-                        const G wxy = s_w[0][t * kWmax + dx] * s_w[1][t * kWmax + dy];
+                    for (int p = 0; p < NP; ++p) {
+                        const cpx<G> cp = cscale(s_c[p][t], wxy);
 #pragma unroll
-                        for (int p = 0; p < NP; ++p) {
-                            const cpx<G> cp = cscale(s_c[p][t], wxy);
-#pragma unroll
-                            for (int z = 0; z < NZ; ++z) {
-                                const unsigned jz = (unsigned)(z - cz);
-                                if (jz < (unsigned)w) {
-                                    const G wz = s_w[2][t * kWmax + jz];
-                                    acc[k][p][z].x += cp.x * wz;
-                                    acc[k][p][z].y += cp.y * wz;
-                                }
+                        for (int z = 0; z < NZ; ++z) {
+                            const unsigned jz = (unsigned)(z - cz);
+                            if (jz < (unsigned)w) {
+                                const G wz = s_w[2][t * kWmax + jz];
+                                acc[p][z].x += cp.x * wz;
+                                acc[p][z].y += cp.y * wz;
                             }
                         }
                     }
@@ -312,39 +310,36 @@ __global__ void __launch_bounds__(kGatherThreads) k_spread_gather(const int *__r
             __syncthreads();
         }
     }
+    if (gx < nx && gy < ny) {
 #pragma unroll
-    for (int k = 0; k < CPT; ++k) {
-        if (gx[k] < nx && gy[k] < ny) {
+        for (int p = 0; p < NP; ++p)
 #pragma unroll
-            for (int p = 0; p < NP; ++p)
-#pragma unroll
-                for (int z = 0; z < NZ; ++z)
-                    if (z < nz) grid[(((size_t)p * nz + z) * ny + gy[k]) * nx + gx[k]] = acc[k][p][z];
-        }
+            for (int z = 0; z < NZ; ++z)
+                if (z < nz) grid[(((size_t)p * nz + z) * ny + gy) * nx + gx] = acc[p][z];
     }
 }
 
-template <class G, int NP, int NZ, int CPT>
+template <class G, int NP, int NZ>
 static cudaError_t gather_launch(const int *offsets, const int *cell, const G *frac, const cpx<G> *cs, long n_src,
                                  const SliceGeom &g, const TimeBin &tb, double r0, double r1, cpx<G> *grid,
                                  cudaStream_t st)
 {
-    dim3 blocks((g.dim[0].nf1 + tb.T[0] - 1) / tb.T[0], (g.dim[1].nf1 + tb.T[1] - 1) / tb.T[1]);
-    k_spread_gather<G, NP, NZ, CPT><<<blocks, kGatherThreads, 0, st>>>(offsets, cell, frac, cs, n_src, g, tb, r0, r1,
-                                                                       grid);
+    dim3 blocks((g.dim[0].nf1 + kTileX - 1) / kTileX, (g.dim[1].nf1 + kTileY - 1) / kTileY);
+    k_spread_gather<G, NP, NZ><<<blocks, kGatherThreads, 0, st>>>(offsets, cell, frac, cs, n_src, g, tb, r0, r1,
+                                                                   grid);
     return cudaGetLastError();
 }
 
-int spread_gather_config(int elem_bytes, int n_pol, int nz, int w, int *nz_tmpl, int *cpt)
+int spread_gather_config(int elem_bytes, int n_pol, int nz, int w, int *nz_tmpl, int *bin_x, int *bin_y)
 {
     if (w > kWmax) return 0;
     const int NZ = nz <= 1 ? 1 : (nz <= 8 ? 8 : (nz <= 16 ? 16 : 0));
     if (NZ == 0) return 0;
-    const int budget = elem_bytes == 4 ? 32 : 16;       // complex accumulators per thread
-    int c = n_pol * NZ * 2 <= budget ? 2 : (n_pol * NZ <= budget ? 1 : 0);
-    if (c == 0) return 0;
+    const int budget = elem_bytes == 4 ? 32 : 16;       // complex accumulators per lane
+    if (n_pol * NZ > budget) return 0;
     *nz_tmpl = NZ;
-    *cpt = c;
+    *bin_x = kPatchX;
+    *bin_y = kPatchY;
     return 1;
 }
 
@@ -354,23 +349,16 @@ cudaError_t launch_spread_tile(const int *offsets, const int *cell, const G *fra
                                cudaStream_t st)
 {
     const int nz = g.d == 3 ? g.dim[2].nf1 : 1;
-    int NZ = 0, CPT = 0;
-    if (!spread_gather_config(sizeof(G), g.n_pol, nz, g.w, &NZ, &CPT)) return cudaErrorInvalidValue;
-    if (tb.T[0] * tb.T[1] != kGatherThreads * CPT) return cudaErrorInvalidValue;
-    const int key = (g.n_pol == 4 ? 100 : 0) + NZ * 10 + CPT;
+    int NZ = 0, bx = 0, by = 0;
+    if (!spread_gather_config(sizeof(G), g.n_pol, nz, g.w, &NZ, &bx, &by)) return cudaErrorInvalidValue;
+    const int key = (g.n_pol == 4 ? 100 : 0) + NZ;
     switch (key) {
-    case 12: return gather_launch<G, 1, 1, 2>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
-    case 11: return gather_launch<G, 1, 1, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
-    case 82: return gather_launch<G, 1, 8, 2>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
-    case 81: return gather_launch<G, 1, 8, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
-    case 162:
-        if constexpr (sizeof(G) == 4) return gather_launch<G, 1, 16, 2>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
-        else return cudaErrorInvalidValue;
-    case 161: return gather_launch<G, 1, 16, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
-    case 112: return gather_launch<G, 4, 1, 2>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
-    case 111: return gather_launch<G, 4, 1, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
-    case 181:
-        if constexpr (sizeof(G) == 4) return gather_launch<G, 4, 8, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+    case 1: return gather_launch<G, 1, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+    case 8: return gather_launch<G, 1, 8>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+    case 16: return gather_launch<G, 1, 16>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+    case 101: return gather_launch<G, 4, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+    case 108:
+        if constexpr (sizeof(G) == 4) return gather_launch<G, 4, 8>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
         else return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
