@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target oracle CPU time for the baseline")
+    ap.add_argument("--streams", type=int, default=0, help="execution streams per plan (0 = library default)")
+    ap.add_argument("--spread", default="auto", choices=["auto", "gather", "scatter", "atomic"])
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip timing the plain FP64 path (one slice after another) beside the mixed path")
     return ap.parse_args()
@@ -217,7 +219,8 @@ def main():
     eps = 1e-6 if precision == fv.FV_MIXED else 1e-11
     prob = workload(1 + rank)             # each rank simulates its own independent problem (weak scaling)
     stream = torch.cuda.current_stream(dev)
-    plan = fv.Plan.from_problem(prob, precision=precision, eps=eps, stream=stream.cuda_stream, device=local)
+    plan = fv.Plan.from_problem(prob, precision=precision, eps=eps, stream=stream.cuda_stream, device=local,
+                                n_streams=args.streams, spread=args.spread)
     fdt = torch.float32 if precision == fv.FV_MIXED else torch.float64
     cdt = torch.complex64 if precision == fv.FV_MIXED else torch.complex128
     flux_dev = torch.tensor(prob.sky.flux, dtype=fdt, device=dev)
@@ -230,10 +233,8 @@ def main():
         plan.run(out)
     torch.cuda.synchronize(dev)
 
-    # ---- timed region: K steps, device-resident inputs and outputs
+    # ---- timed region: K steps, device-resident inputs and outputs, no per-launch instrumentation
     clocks = Clocks(local)
-    fv.fv_profile_read(plan.handle)                       # reset counters
-    fv.fv_profile_enable(plan.handle, True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -249,13 +250,21 @@ def main():
     if dist:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
-    prof = fv.fv_profile_read(plan.handle)
-    fv.fv_profile_enable(plan.handle, False)
     if dist:
         t = torch.tensor([ms], dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world * n_vis * args.steps / (ms / 1e3)
+
+    # ---- per-kernel times: one more step with CUDA events around every launch, each on the
+    # stream it runs on (event records between launches would perturb the timed region above)
+    fv.fv_profile_read(plan.handle)                       # reset counters
+    fv.fv_profile_enable(plan.handle, True)
+    plan.run(out)
+    torch.cuda.synchronize(dev)
+    prof = fv.fv_profile_read(plan.handle)
+    fv.fv_profile_enable(plan.handle, False)
+    prof_steps = 1
 
     # ---- roofline of the dominant kernel class
     ours = {k: v for k, v in prof.items() if k != "memset" and v["launches"] > 0}
@@ -270,8 +279,9 @@ def main():
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": tr, "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
                 "avg_launch_ms": d["ms"] / d["launches"],
-                "share_of_step": d["ms"] / sum(v["ms"] for v in prof.values())}
-    gpu_launches = int(sum(v["launches"] for k, v in prof.items() if k != "memset"))
+                "share_of_kernel_time": d["ms"] / sum(v["ms"] for v in prof.values()),
+                "timing": "CUDA events around each launch on its own stream, one profiled step after the timed region"}
+    gpu_launches = int(sum(v["launches"] for k, v in prof.items() if k != "memset")) * args.steps // prof_steps
 
     # ---- end to end through the C ABI with host buffers (pinned)
     e2e = None
@@ -335,14 +345,15 @@ def main():
                        "n_unique_targets": info["n_unique"], "n_freq": 64, "n_time": 10,
                        "n_src": int(prob.sky.n_src), "dims": info["dims"], "precision": args.precision,
                        "eps": eps, "kernel_width": info["kernel_width"], "upsampfac": info["upsampfac"],
-                       "nf1_max": info["nf1_max"], "nf2_max": info["nf2_max"],
+                       "nf1_max": info["nf1_max"], "nf2_max": info["nf2_max"], "streams": args.streams or 4,
+                       "spread": args.spread,
                        "vis_per_step": n_vis,
                        "l2": "inputs larger than L2: a step streams the 640 slices' grids "
                              f"(~{info['workspace_bytes'] / 1e6:.0f} MB workspace reused per slice)",
                        "parallelism": f"{world} independent problems (one per GPU)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": gpu_launches,
             "rel_l2_vs_oracle_sample": err, "fp64_plain": fp64,
-            "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+            "kernels": {k: {"ms_per_step": v["ms"] / prof_steps, "launches_per_step": v["launches"] / prof_steps,
                             "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}
                         for k, v in prof.items() if v["launches"] > 0}}
     if rank == 0:

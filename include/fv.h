@@ -87,7 +87,20 @@ typedef struct {
                                  (w = ceil(log10(1/eps)) + 1 at sigma = 2, Section 2.2) */
     void *cuda_stream;        /* borrowed cudaStream_t, or NULL for a plan-owned stream */
     int device;               /* CUDA device ordinal; -1 = the current device */
+    int n_streams;            /* slices run concurrently on this many streams, each with its own
+                                 workspace (forked from and joined back to cuda_stream); 0 = 4 */
+    int spread_method;        /* fv_spread_method; FV_SPREAD_AUTO picks the fastest that fits */
+    int fft_max_radix;        /* largest FFT stage radix: 8 (fewer registers, more stages) or 16;
+                                 0 = 8 for FV_MIXED, 16 for FV_FP64 */
 } fv_opts;
+
+/* How the ES spreading step is run (all give the same result up to rounding). */
+typedef enum {
+    FV_SPREAD_AUTO = 0,
+    FV_SPREAD_GATHER = 1,     /* per-tile, each thread sums the sources covering its cells */
+    FV_SPREAD_SCATTER = 2,    /* per-tile, warps add each source's footprint with shared atomics */
+    FV_SPREAD_ATOMIC = 3      /* one thread per source, global atomics on a cleared grid */
+} fv_spread_method;
 
 /* Fill *o with defaults: FV_FP64, eps 1e-10, Gaussian beam 10 deg at 150 MHz,
  * unpolarised, auto dims, sigma 2, NULL stream, current device.  The caller

@@ -238,7 +238,7 @@ __device__ __forceinline__ void stage(const cpx<G> *__restrict__ x, cpx<G> *__re
     __syncthreads();
 }
 
-template <class G>
+template <class G, int MAXRD>
 __device__ __forceinline__ void run_stage(int rd, const cpx<G> *x, cpx<G> *y, const DimGeom &dg, int s, int nrows,
                                           int Ns, const cpx<G> *tw)
 {
@@ -249,11 +249,17 @@ __device__ __forceinline__ void run_stage(int rd, const cpx<G> *x, cpx<G> *y, co
     case 5: stage<G, 5>(x, y, dg, s, nrows, Ns, tw); break;
     case 6: stage<G, 6>(x, y, dg, s, nrows, Ns, tw); break;
     case 8: stage<G, 8>(x, y, dg, s, nrows, Ns, tw); break;
-    case 9: stage<G, 9>(x, y, dg, s, nrows, Ns, tw); break;
-    case 10: stage<G, 10>(x, y, dg, s, nrows, Ns, tw); break;
-    case 12: stage<G, 12>(x, y, dg, s, nrows, Ns, tw); break;
-    case 15: stage<G, 15>(x, y, dg, s, nrows, Ns, tw); break;
-    default: stage<G, 16>(x, y, dg, s, nrows, Ns, tw); break;
+    default:
+        if constexpr (MAXRD > 8) {
+            switch (rd) {
+            case 9: stage<G, 9>(x, y, dg, s, nrows, Ns, tw); break;
+            case 10: stage<G, 10>(x, y, dg, s, nrows, Ns, tw); break;
+            case 12: stage<G, 12>(x, y, dg, s, nrows, Ns, tw); break;
+            case 15: stage<G, 15>(x, y, dg, s, nrows, Ns, tw); break;
+            default: stage<G, 16>(x, y, dg, s, nrows, Ns, tw); break;
+            }
+        }
+        break;
     }
 }
 
@@ -298,7 +304,7 @@ __device__ __forceinline__ void prefetch_rows(Prefetch<G> &pf, const cpx<G> *__r
     }
 }
 
-template <class G>
+template <class G, int MAXRD>
 __global__ void __launch_bounds__(kThreads) k_fft_rows(const cpx<G> *__restrict__ in, cpx<G> *__restrict__ out,
                                                        long rows, DimGeom dg, const G *__restrict__ pre,
                                                        const cpx<G> *__restrict__ tw, int R)
@@ -338,7 +344,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_rows(const cpx<G> *__restrict_
         int Ns = 1;
         for (int s = 0; s < dg.nstages; ++s) {
             const int rd = dg.radix[s];
-            run_stage<G>(rd, x, y, dg, s, R, Ns, tw);
+            run_stage<G, MAXRD>(rd, x, y, dg, s, R, Ns, tw);
             cpx<G> *t = x; x = y; y = t;
             Ns *= rd;
         }
@@ -355,38 +361,51 @@ __global__ void __launch_bounds__(kThreads) k_fft_rows(const cpx<G> *__restrict_
     }
 }
 
+template <class G, int MAXRD>
+static cudaError_t launch_rows(const cpx<G> *in, cpx<G> *out, long rows, const DimGeom &dg, const G *pre,
+                               const cpx<G> *tw, cudaStream_t st)
+{
+    const int R = fft_rows_per_cta(dg.M, sizeof(G));
+    const size_t smem = 2 * buf_elems(R, dg.M) * sizeof(cpx<G>);
+    static bool attr_set[64] = {};
+    static int max_ctas[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set[dev]) {
+        e = cudaFuncSetAttribute(k_fft_rows<G, MAXRD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210000);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    // persistent CTAs: as many as fit on the device for the largest configuration (each keeps a
+    // row block of prefetch in registers)
+    if (!max_ctas[dev]) {
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        max_ctas[dev] = sms;
+    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fft_rows<G, MAXRD>, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    const long cap = (long)max_ctas[dev] * (per_sm > 0 ? per_sm : 1);
+    const long ctas = (rows + R - 1) / R;
+    const unsigned grid = (unsigned)(ctas < cap ? ctas : cap);
+    k_fft_rows<G, MAXRD><<<grid, kThreads, smem, st>>>(in, out, rows, dg, pre, tw, R);
+    return cudaGetLastError();
+}
+
 template <class G>
 cudaError_t launch_fft_pass(const cpx<G> *in, cpx<G> *out, long rows, const DimGeom &dg, const G *pre,
                             const cpx<G> *tw, cudaStream_t st)
 {
     if (rows <= 0) return cudaSuccess;
     if (dg.M > fft_max_M(sizeof(G))) return cudaErrorInvalidValue;
-    const int R = fft_rows_per_cta(dg.M, sizeof(G));
-    const size_t smem = 2 * buf_elems(R, dg.M) * sizeof(cpx<G>);
-    static bool attr_set[64] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!attr_set[dev]) {
-        e = cudaFuncSetAttribute(k_fft_rows<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210000);
-        if (e != cudaSuccess) return e;
-        attr_set[dev] = true;
-    }
-    // persistent CTAs: as many as fit on the device (each keeps a row block of prefetch in registers)
-    static int max_ctas[64] = {};
-    if (!max_ctas[dev]) {
-        int sms = 0, per_sm = 0;
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fft_rows<G>, kThreads, smem);
-        if (e != cudaSuccess) return e;
-        max_ctas[dev] = sms * (per_sm > 0 ? per_sm : 1);
-    }
-    long ctas = (rows + R - 1) / R;
-    unsigned grid = (unsigned)(ctas < max_ctas[dev] ? ctas : max_ctas[dev]);
-    k_fft_rows<G><<<grid, kThreads, smem, st>>>(in, out, rows, dg, pre, tw, R);
-    return cudaGetLastError();
+    int maxrd = 1;
+    for (int s = 0; s < dg.nstages; ++s) maxrd = dg.radix[s] > maxrd ? dg.radix[s] : maxrd;
+    if (maxrd <= 8) return launch_rows<G, 8>(in, out, rows, dg, pre, tw, st);
+    return launch_rows<G, 16>(in, out, rows, dg, pre, tw, st);
 }
 
 template cudaError_t launch_fft_pass<double>(const cpx<double> *, cpx<double> *, long, const DimGeom &,
@@ -397,14 +416,14 @@ template cudaError_t launch_fft_pass<float>(const cpx<float> *, cpx<float> *, lo
 // ---------------------------------------------------------------- host planning
 static const int kRadices[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
 
-static bool factor_into(int M, int maxStages, int *rad, int &n)
+static bool factor_into(int M, int maxStages, int maxRadix, int *rad, int &n)
 {
     if (M == 1) return true;
     if (maxStages == 0) return false;
     for (int r : kRadices)
-        if (M % r == 0) {
+        if (r <= maxRadix && M % r == 0) {
             rad[n++] = r;
-            if (factor_into(M / r, maxStages - 1, rad, n)) return true;
+            if (factor_into(M / r, maxStages - 1, maxRadix, rad, n)) return true;
             --n;
         }
     return false;
@@ -419,12 +438,16 @@ static void magic_u32(unsigned d, unsigned &mul, unsigned &sh)
     mul = (unsigned)((((1ull << 32) * ((1ull << s) - d)) / d) + 1);
 }
 
-int fft_choose_length(int target, int *radix, int &nstages)
+int fft_choose_length(int target, int *radix, int &nstages, int maxRadix)
 {
-    const int maxStages = target <= 4096 ? 3 : 4;
+    if (maxRadix < 2) maxRadix = 16;
+    // stage budget: enough stages of maxRadix to reach the target, at least 3
+    int maxStages = 3;
+    for (long span = (long)maxRadix * maxRadix * maxRadix; span < target && maxStages < FV_MAX_STAGES; span *= maxRadix)
+        ++maxStages;
     for (int M = target + (target & 1); M <= 4 * target + 64; M += 2) {
         int n = 0;
-        if (factor_into(M, maxStages, radix, n)) {
+        if (factor_into(M, maxStages, maxRadix, radix, n)) {
             nstages = n;
             return M;
         }

@@ -138,6 +138,14 @@ cudaError_t launch_spread_tile(const int *offsets, const int *cell, const G *fra
                                const SliceGeom &g, const TimeBin &tb, double r0, double r1, cpx<G> *grid,
                                cudaStream_t st);
 
+// Scatter variant of the tiled spreading (shared-memory tile + atomics);
+// same inputs and output as launch_spread_tile.
+template <class G>
+cudaError_t launch_spread_scatter(const int *offsets, const int *cell, const G *frac, const cpx<G> *cs, long n_src,
+                                  const SliceGeom &g, const TimeBin &tb, double r0, double r1, cpx<G> *grid,
+                                  cudaStream_t st);
+size_t spread_scatter_smem(int elem_bytes, int n_pol, int nz);
+
 // One FFT pass: rows of length N (input rows contiguous), prescale by pre[l],
 // zero-pad to M, FFT with e^{+2 pi i l m / M}, write band outputs transposed:
 // out[b][row] = P[(b - H) mod M].
@@ -166,7 +174,7 @@ int fft_max_M(int elem_bytes);
 int fft_rows_per_cta(int M, int elem_bytes);
 // Smallest even M >= target that is a product of at most 3 (4 above 4096)
 // supported radices; fills radix[] and nstages.  -1 if none.
-int fft_choose_length(int target, int *radix, int &nstages);
+int fft_choose_length(int target, int *radix, int &nstages, int maxRadix);
 // Per-stage multiply-high division constants of dg (needs M, nstages, radix).
 void fft_stage_constants(DimGeom &dg);
 

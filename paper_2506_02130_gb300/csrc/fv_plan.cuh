@@ -58,18 +58,30 @@ struct fv_plan_s {
     std::vector<size_t> pre_off;     // [n_freq][3] element offsets into the prescale table
     std::vector<size_t> tw_off;      // [n_freq][3] element offsets into the twiddle table
     void *d_pre = nullptr, *d_tw = nullptr;
-    void *d_grid = nullptr, *d_bufA = nullptr, *d_bufB = nullptr;
-    cpx<double> *d_Vu = nullptr;
+    // one workspace per execution stream (slices on different streams run concurrently)
+    struct Workspace {
+        void *grid = nullptr, *bufA = nullptr, *bufB = nullptr;
+        cpx<double> *Vu = nullptr;
+        int *bin_of = nullptr, *counts = nullptr, *offsets = nullptr, *cursor = nullptr, *sidx = nullptr;
+        int *cell = nullptr;
+        double *sdir = nullptr;
+        void *frac = nullptr, *cs = nullptr;
+    };
+    std::vector<Workspace> ws;
+    int n_streams = 1;
+    std::vector<cudaStream_t> sub;       // sub[0] is the plan's stream
+    std::vector<cudaEvent_t> ev_join;
+    cudaEvent_t ev_fork = nullptr;
     size_t grid_elems = 0, bufA_elems = 0, bufB_elems = 0;
     // binned spreading
     bool tiled = false;
+    int spread_req = 0;         // fv_opts.spread_method
+    int fft_max_radix = 16;
+    int spread_method = 0;      // resolved method
     int T[2] = {32, 32}, nbx = 1, nby = 1, f_top = 0;
     double qscale_top[3] = {0, 0, 0};
     int nf1_top[3] = {1, 1, 1};
-    int *d_bin_of = nullptr, *d_counts = nullptr, *d_offsets = nullptr, *d_cursor = nullptr, *d_sidx = nullptr;
-    int *d_cell = nullptr;
-    double *d_sdir = nullptr;
-    void *d_frac = nullptr, *d_cs = nullptr;
+
     long long ws_bytes = 0;
     int nf1_max[3] = {1, 1, 1}, M_max[3] = {1, 1, 1};
 
@@ -77,6 +89,7 @@ struct fv_plan_s {
     bool prof_on = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, int>> ev_pending;   // (class, index of the start event in the pool)
+    cudaStream_t prof_stream = nullptr;
     size_t ev_next = 0;
     double prof_ms[FV_PROFILE_CLASSES] = {};
     long long prof_launches[FV_PROFILE_CLASSES] = {};

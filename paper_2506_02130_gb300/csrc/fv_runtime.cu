@@ -94,8 +94,11 @@ enum { PC_MEMSET = 0, PC_BIN, PC_PREP, PC_SPREAD, PC_FFT_X, PC_FFT_Y, PC_FFT_Z, 
 static cudaError_t prof_harvest(fv_plan_s *p)
 {
     if (p->ev_pending.empty()) return cudaSuccess;
-    cudaError_t e = cudaStreamSynchronize(p->stream);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    for (cudaStream_t st : p->sub) {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+    }
     for (auto &pr : p->ev_pending) {
         float ms = 0.f;
         e = cudaEventElapsedTime(&ms, p->ev_pool[pr.second], p->ev_pool[pr.second + 1]);
@@ -107,24 +110,25 @@ static cudaError_t prof_harvest(fv_plan_s *p)
     return cudaSuccess;
 }
 
-// bracket one launch of class cls; call prof_begin before and prof_end after it
-static cudaError_t prof_begin(fv_plan_s *p, int cls)
+// bracket one launch of class cls on stream st; call prof_begin before and prof_end after it
+static cudaError_t prof_begin(fv_plan_s *p, int cls, cudaStream_t st)
 {
     p->prof_launches[cls] += 1;
     p->prof_cls = cls;
+    p->prof_stream = st;
     if (!p->prof_on) return cudaSuccess;
     if (p->ev_next + 2 > p->ev_pool.size()) {
         cudaError_t e = prof_harvest(p);
         if (e != cudaSuccess) return e;
     }
-    return cudaEventRecord(p->ev_pool[p->ev_next], p->stream);
+    return cudaEventRecord(p->ev_pool[p->ev_next], st);
 }
 
 static cudaError_t prof_end(fv_plan_s *p, double bytes)
 {
     p->prof_bytes[p->prof_cls] += bytes;
     if (!p->prof_on) return cudaSuccess;
-    cudaError_t e = cudaEventRecord(p->ev_pool[p->ev_next + 1], p->stream);
+    cudaError_t e = cudaEventRecord(p->ev_pool[p->ev_next + 1], p->prof_stream);
     p->ev_pending.emplace_back(p->prof_cls, (int)p->ev_next);
     p->ev_next += 2;
     return e;
@@ -134,19 +138,22 @@ static void free_geometry(fv_plan_s *p)
 {
     dfree(p->d_pre);
     dfree(p->d_tw);
-    dfree(p->d_grid);
-    dfree(p->d_bufA);
-    dfree(p->d_bufB);
-    dfree_t(p->d_Vu);
-    dfree_t(p->d_bin_of);
-    dfree_t(p->d_counts);
-    dfree_t(p->d_offsets);
-    dfree_t(p->d_cursor);
-    dfree_t(p->d_sidx);
-    dfree_t(p->d_cell);
-    dfree_t(p->d_sdir);
-    dfree(p->d_frac);
-    dfree(p->d_cs);
+    for (auto &w : p->ws) {
+        dfree(w.grid);
+        dfree(w.bufA);
+        dfree(w.bufB);
+        dfree_t(w.Vu);
+        dfree_t(w.bin_of);
+        dfree_t(w.counts);
+        dfree_t(w.offsets);
+        dfree_t(w.cursor);
+        dfree_t(w.sidx);
+        dfree_t(w.cell);
+        dfree_t(w.sdir);
+        dfree(w.frac);
+        dfree(w.cs);
+    }
+    p->ws.clear();
 }
 
 // Per-channel geometry, tables and workspace; needs the array and the sky.
@@ -188,7 +195,7 @@ static fv_status prepare(fv_plan_s *p)
             if (nf1 < w + 2) nf1 = w + 2;     // Eq. 5 is the requirement; no 2w floor is needed
             if (nf1 > (1L << 20)) return p->fail(FV_ERR_UNSUPPORTED, "spreading grid too large");
             dg.nf1 = next235even(nf1);
-            dg.M = fft_choose_length((int)std::ceil(p->sigma * dg.nf1 - 1e-9), dg.radix, dg.nstages);
+            dg.M = fft_choose_length((int)std::ceil(p->sigma * dg.nf1 - 1e-9), dg.radix, dg.nstages, p->fft_max_radix);
             if (dg.M < 0 || dg.M > maxM)
                 return p->fail(FV_ERR_UNSUPPORTED, "FFT length " + std::to_string(dg.M) + " exceeds " +
                                                        std::to_string(maxM) + " for one-CTA FFT passes");
@@ -220,10 +227,13 @@ static fv_status prepare(fv_plan_s *p)
     const size_t gs = p->precision == FV_FP64 ? sizeof(double) : sizeof(float);
     CK(cudaMalloc(&p->d_pre, std::max<size_t>(pre_total, 1) * gs));
     CK(cudaMalloc(&p->d_tw, std::max<size_t>(tw_total, 1) * es));
-    CK(cudaMalloc(&p->d_grid, std::max<size_t>(grid_e, 1) * es));
-    CK(cudaMalloc(&p->d_bufA, std::max<size_t>(bufA_e, 1) * es));
-    CK(cudaMalloc(&p->d_bufB, std::max<size_t>(bufB_e, 1) * es));
-    CK(cudaMalloc(&p->d_Vu, std::max<size_t>((size_t)p->n_u * p->n_pol, 1) * sizeof(cpx<double>)));
+    p->ws.assign(p->n_streams, fv_plan_s::Workspace{});
+    for (auto &wk : p->ws) {
+        CK(cudaMalloc(&wk.grid, std::max<size_t>(grid_e, 1) * es));
+        CK(cudaMalloc(&wk.bufA, std::max<size_t>(bufA_e, 1) * es));
+        CK(cudaMalloc(&wk.bufB, std::max<size_t>(bufB_e, 1) * es));
+        CK(cudaMalloc(&wk.Vu, std::max<size_t>((size_t)p->n_u * p->n_pol, 1) * sizeof(cpx<double>)));
+    }
     p->grid_elems = grid_e;
     p->bufA_elems = bufA_e;
     p->bufB_elems = bufB_e;
@@ -252,7 +262,16 @@ static fv_status prepare(fv_plan_s *p)
     {
         const int nzm = p->d == 3 ? p->nf1_max[2] : 1;
         int nz_t = 0, bx = 8, by = 4;
-        p->tiled = spread_gather_config((int)gs, p->n_pol, nzm, w, &nz_t, &bx, &by) != 0;
+        const bool gather_ok = spread_gather_config((int)gs, p->n_pol, nzm, w, &nz_t, &bx, &by) != 0;
+        const bool scatter_ok = spread_scatter_smem((int)gs, p->n_pol, nzm) <= FV_SPREAD_SMEM_MAX && w <= 32;
+        int m = p->spread_req;
+        if (m == FV_SPREAD_AUTO) m = scatter_ok ? FV_SPREAD_SCATTER : (gather_ok ? FV_SPREAD_GATHER : FV_SPREAD_ATOMIC);
+        if (m == FV_SPREAD_GATHER && !gather_ok) m = FV_SPREAD_ATOMIC;
+        if (m == FV_SPREAD_SCATTER && !scatter_ok) m = FV_SPREAD_ATOMIC;
+        p->spread_method = m;
+        p->tiled = m != FV_SPREAD_ATOMIC;
+        bx = 8;
+        by = 4;
         p->T[0] = bx;
         p->T[1] = by;
         p->nbx = (p->nf1_top[0] + p->T[0] - 1) / p->T[0];
@@ -261,29 +280,33 @@ static fv_status prepare(fv_plan_s *p)
     size_t bin_bytes = 0;
     if (p->tiled) {
         const size_t ns = std::max<long>(p->n_src, 1), nb = (size_t)p->nbx * p->nby;
-        CK(cudaMalloc(&p->d_bin_of, ns * sizeof(int)));
-        CK(cudaMalloc(&p->d_counts, nb * sizeof(int)));
-        CK(cudaMalloc(&p->d_offsets, (nb + 1) * sizeof(int)));
-        CK(cudaMalloc(&p->d_cursor, nb * sizeof(int)));
-        CK(cudaMalloc(&p->d_sidx, ns * sizeof(int)));
-        CK(cudaMalloc(&p->d_cell, 3 * ns * sizeof(int)));
-        CK(cudaMalloc(&p->d_sdir, 3 * ns * sizeof(double)));
-        CK(cudaMalloc(&p->d_frac, 3 * ns * gs));
-        CK(cudaMalloc(&p->d_cs, (size_t)p->n_pol * ns * es));
+        for (auto &wk : p->ws) {
+            CK(cudaMalloc(&wk.bin_of, ns * sizeof(int)));
+            CK(cudaMalloc(&wk.counts, nb * sizeof(int)));
+            CK(cudaMalloc(&wk.offsets, (nb + 1) * sizeof(int)));
+            CK(cudaMalloc(&wk.cursor, nb * sizeof(int)));
+            CK(cudaMalloc(&wk.sidx, ns * sizeof(int)));
+            CK(cudaMalloc(&wk.cell, 3 * ns * sizeof(int)));
+            CK(cudaMalloc(&wk.sdir, 3 * ns * sizeof(double)));
+            CK(cudaMalloc(&wk.frac, 3 * ns * gs));
+            CK(cudaMalloc(&wk.cs, (size_t)p->n_pol * ns * es));
+        }
         bin_bytes = ns * (4 + 4 + 12 + 24 + 3 * gs + p->n_pol * es) + nb * 12;
     }
-    p->ws_bytes = (long long)(pre_total * gs + tw_total * es + (grid_e + bufA_e + bufB_e) * es +
-                              (size_t)p->n_u * p->n_pol * sizeof(cpx<double>) + bin_bytes);
+    p->ws_bytes = (long long)(pre_total * gs + tw_total * es +
+                              p->n_streams * ((grid_e + bufA_e + bufB_e) * es +
+                                              (size_t)p->n_u * p->n_pol * sizeof(cpx<double>) + bin_bytes));
     CK(cudaStreamSynchronize(p->stream));
     return FV_OK;
 }
 
 template <class G>
-static fv_status execute_slices(fv_plan_s *p, char *vis, size_t slice_bytes)
+static fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, char *vis, size_t slice_bytes,
+                            long k_begin, long k_end)
 {
     const int nf = (int)p->freq.size(), nt = (int)p->lst.size();
-    cpx<G> *grid = (cpx<G> *)p->d_grid;
-    cpx<G> *A = (cpx<G> *)p->d_bufA, *Bb = (cpx<G> *)p->d_bufB;
+    cpx<G> *grid = (cpx<G> *)wk.grid;
+    cpx<G> *A = (cpx<G> *)wk.bufA, *Bb = (cpx<G> *)wk.bufB;
     const double es = sizeof(cpx<G>);
     const double src_bytes = (double)p->n_src * (3 * sizeof(double) + (double)p->n_stokes * (p->flux_fp64 ? 8 : 4));
     // prep and spread touch the visible sources only; about half the sky is up at any time
@@ -292,9 +315,13 @@ static fv_status execute_slices(fv_plan_s *p, char *vis, size_t slice_bytes)
                                       3.0 * sizeof(G) + p->n_pol * es);
     const double spread_in_bytes = nvis * (12.0 + 3.0 * sizeof(G) + p->n_pol * es);
     const int nb = p->nbx * p->nby;
-    for (int t = 0; t < nt; ++t) {
-        TimeBin tb{};
-        if (p->tiled) {
+    const G *pre = (const G *)p->d_pre;
+    const cpx<G> *tw = (const cpx<G> *)p->d_tw;
+    int t_binned = -1;
+    TimeBin tb{};
+    for (long k = k_begin; k < k_end; ++k) {
+        const int t = (int)(k / nf), f = (int)(k % nf);
+        if (p->tiled && t != t_binned) {
             std::memcpy(tb.R, &p->Rt[(size_t)t * 9], 9 * sizeof(double));
             for (int i = 0; i < 3; ++i) {
                 tb.C[i] = p->C[i];
@@ -305,74 +332,96 @@ static fv_status execute_slices(fv_plan_s *p, char *vis, size_t slice_bytes)
             tb.T[1] = p->T[1];
             tb.nbx = p->nbx;
             tb.nby = p->nby;
-            CK(prof_begin(p, PC_BIN));
-            CK(launch_time_binning(p->d_e, p->n_src, tb, p->d_bin_of, p->d_counts, p->d_offsets, p->d_cursor,
-                                   p->d_sdir, p->d_sidx, p->stream));
+            CK(prof_begin(p, PC_BIN, st));
+            CK(launch_time_binning(p->d_e, p->n_src, tb, wk.bin_of, wk.counts, wk.offsets, wk.cursor, wk.sdir,
+                                   wk.sidx, st));
             CK(prof_end(p, (double)p->n_src * 80.0 + nb * 12.0));
+            t_binned = t;
         }
-        for (int f = 0; f < nf; ++f) {
-            SliceGeom g = p->gf[f];
-            std::memcpy(g.R, &p->Rt[(size_t)t * 9], 9 * sizeof(double));
-            const DimGeom *D = g.dim;
-            const size_t gel = (size_t)p->n_pol * D[0].nf1 * D[1].nf1 * D[2].nf1;
-            if (p->tiled) {
-                G *frac = (G *)p->d_frac;
-                cpx<G> *cs = (cpx<G> *)p->d_cs;
-                CK(prof_begin(p, PC_PREP));
-                CK(launch_prep<G>(p->d_sdir, p->d_sidx, p->d_offsets + nb, p->n_src, p->flux, p->flux_fp64, nf, f, g,
-                                  p->d_cell, frac, cs, p->stream));
-                CK(prof_end(p, prep_bytes));
-                const double r0 = D[0].qscale / p->qscale_top[0], r1 = D[1].qscale / p->qscale_top[1];
-                CK(prof_begin(p, PC_SPREAD));
-                CK(launch_spread_tile<G>(p->d_offsets, p->d_cell, frac, cs, p->n_src, g, tb, r0, r1, grid, p->stream));
-                CK(prof_end(p, spread_in_bytes + gel * es));
-            } else {
-                CK(prof_begin(p, PC_MEMSET));
-                CK(cudaMemsetAsync(grid, 0, gel * sizeof(cpx<G>), p->stream));
-                CK(prof_end(p, gel * es));
-                CK(prof_begin(p, PC_SPREAD));
-                CK(launch_spread_direct<G>(p->d_e, p->n_src, p->flux, p->flux_fp64, nf, f, g, grid, p->stream));
-                CK(prof_end(p, src_bytes + gel * es));
-            }
-            const G *pre = (const G *)p->d_pre;
-            const cpx<G> *tw = (const cpx<G> *)p->d_tw;
-            const size_t o0 = (size_t)f * 3;
-            // pass 1 along x: rows (pol, z, y)
-            long r1 = (long)p->n_pol * D[2].nf1 * D[1].nf1;
-            CK(prof_begin(p, PC_FFT_X));
-            CK(launch_fft_pass<G>(grid, A, r1, D[0], pre + p->pre_off[o0], tw + p->tw_off[o0], p->stream));
-            CK(prof_end(p, (double)r1 * (D[0].nf1 + D[0].B) * es));
-            // pass 2 along y: rows (bx, pol, z)
-            long r2 = (long)D[0].B * p->n_pol * D[2].nf1;
-            CK(prof_begin(p, PC_FFT_Y));
-            CK(launch_fft_pass<G>(A, Bb, r2, D[1], pre + p->pre_off[o0 + 1], tw + p->tw_off[o0 + 1], p->stream));
-            CK(prof_end(p, (double)r2 * (D[1].nf1 + D[1].B) * es));
-            const cpx<G> *band = Bb;
-            if (p->d == 2 || D[2].nf1 <= FV_ZDIRECT_MAX) {
-                // z (if any) summed directly inside the interpolation: no z pass
-                const double wd = (double)p->w * p->w * D[2].nf1;
-                CK(prof_begin(p, PC_INTERP));
-                CK(launch_interp_zdirect<G>(Bb, p->d_bu, p->n_u, p->d_dec, g, pre + p->pre_off[o0 + 2],
-                                            tw + p->tw_off[o0 + 2], p->d_Vu, p->stream));
-                CK(prof_end(p, (double)p->n_u * (wd * p->n_pol * es + 4 * sizeof(double) + p->n_pol * 16.0)));
-            } else {
-            if (p->d == 3) {
-                // pass 3 along z: rows (by, bx, pol)
-                long r3 = (long)D[1].B * D[0].B * p->n_pol;
-                CK(prof_begin(p, PC_FFT_Z));
-                CK(launch_fft_pass<G>(Bb, A, r3, D[2], pre + p->pre_off[o0 + 2], tw + p->tw_off[o0 + 2], p->stream));
-                CK(prof_end(p, (double)r3 * (D[2].nf1 + D[2].B) * es));
-                band = A;
-            }
-            double wd = std::pow((double)p->w, p->d);
-            CK(prof_begin(p, PC_INTERP));
-            CK(launch_interp<G>(band, p->d_bu, p->n_u, p->d_dec, g, p->d_Vu, p->stream));
+        SliceGeom g = p->gf[f];
+        std::memcpy(g.R, &p->Rt[(size_t)t * 9], 9 * sizeof(double));
+        const DimGeom *D = g.dim;
+        const size_t gel = (size_t)p->n_pol * D[0].nf1 * D[1].nf1 * D[2].nf1;
+        if (p->tiled) {
+            G *frac = (G *)wk.frac;
+            cpx<G> *cs = (cpx<G> *)wk.cs;
+            CK(prof_begin(p, PC_PREP, st));
+            CK(launch_prep<G>(wk.sdir, wk.sidx, wk.offsets + nb, p->n_src, p->flux, p->flux_fp64, nf, f, g, wk.cell,
+                              frac, cs, st));
+            CK(prof_end(p, prep_bytes));
+            const double r0 = D[0].qscale / p->qscale_top[0], r1 = D[1].qscale / p->qscale_top[1];
+            CK(prof_begin(p, PC_SPREAD, st));
+            if (p->spread_method == FV_SPREAD_SCATTER)
+                CK(launch_spread_scatter<G>(wk.offsets, wk.cell, frac, cs, p->n_src, g, tb, r0, r1, grid, st));
+            else
+                CK(launch_spread_tile<G>(wk.offsets, wk.cell, frac, cs, p->n_src, g, tb, r0, r1, grid, st));
+            CK(prof_end(p, spread_in_bytes + gel * es));
+        } else {
+            CK(prof_begin(p, PC_MEMSET, st));
+            CK(cudaMemsetAsync(grid, 0, gel * sizeof(cpx<G>), st));
+            CK(prof_end(p, gel * es));
+            CK(prof_begin(p, PC_SPREAD, st));
+            CK(launch_spread_direct<G>(p->d_e, p->n_src, p->flux, p->flux_fp64, nf, f, g, grid, st));
+            CK(prof_end(p, src_bytes + gel * es));
+        }
+        const size_t o0 = (size_t)f * 3;
+        // pass 1 along x: rows (pol, z, y)
+        const long r1 = (long)p->n_pol * D[2].nf1 * D[1].nf1;
+        CK(prof_begin(p, PC_FFT_X, st));
+        CK(launch_fft_pass<G>(grid, A, r1, D[0], pre + p->pre_off[o0], tw + p->tw_off[o0], st));
+        CK(prof_end(p, (double)r1 * (D[0].nf1 + D[0].B) * es));
+        // pass 2 along y: rows (bx, pol, z)
+        const long r2 = (long)D[0].B * p->n_pol * D[2].nf1;
+        CK(prof_begin(p, PC_FFT_Y, st));
+        CK(launch_fft_pass<G>(A, Bb, r2, D[1], pre + p->pre_off[o0 + 1], tw + p->tw_off[o0 + 1], st));
+        CK(prof_end(p, (double)r2 * (D[1].nf1 + D[1].B) * es));
+        if (p->d == 2 || D[2].nf1 <= FV_ZDIRECT_MAX) {
+            // z (if any) summed directly inside the interpolation: no z pass
+            const double wd = (double)p->w * p->w * D[2].nf1;
+            CK(prof_begin(p, PC_INTERP, st));
+            CK(launch_interp_zdirect<G>(Bb, p->d_bu, p->n_u, p->d_dec, g, pre + p->pre_off[o0 + 2],
+                                        tw + p->tw_off[o0 + 2], wk.Vu, st));
             CK(prof_end(p, (double)p->n_u * (wd * p->n_pol * es + 4 * sizeof(double) + p->n_pol * 16.0)));
-            }
-            char *out = vis + ((size_t)f * nt + t) * slice_bytes;
-            CK(prof_begin(p, PC_SCATTER));
-            CK(launch_scatter(p->d_Vu, p->d_bl2u, p->n_bl, p->n_pol, out, p->precision == FV_FP64, p->stream));
-            CK(prof_end(p, (double)p->n_bl * (4 + p->n_pol * 16.0) + (double)slice_bytes));
+        } else {
+            // pass 3 along z: rows (by, bx, pol)
+            const long r3 = (long)D[1].B * D[0].B * p->n_pol;
+            CK(prof_begin(p, PC_FFT_Z, st));
+            CK(launch_fft_pass<G>(Bb, A, r3, D[2], pre + p->pre_off[o0 + 2], tw + p->tw_off[o0 + 2], st));
+            CK(prof_end(p, (double)r3 * (D[2].nf1 + D[2].B) * es));
+            const double wd = std::pow((double)p->w, p->d);
+            CK(prof_begin(p, PC_INTERP, st));
+            CK(launch_interp<G>(A, p->d_bu, p->n_u, p->d_dec, g, wk.Vu, st));
+            CK(prof_end(p, (double)p->n_u * (wd * p->n_pol * es + 4 * sizeof(double) + p->n_pol * 16.0)));
+        }
+        char *out = vis + ((size_t)f * nt + t) * slice_bytes;
+        CK(prof_begin(p, PC_SCATTER, st));
+        CK(launch_scatter(wk.Vu, p->d_bl2u, p->n_bl, p->n_pol, out, p->precision == FV_FP64, st));
+        CK(prof_end(p, (double)p->n_bl * (4 + p->n_pol * 16.0) + (double)slice_bytes));
+    }
+    return FV_OK;
+}
+
+// All slices, t-major, split into contiguous chunks over the plan's streams
+// (each with its own workspace); the streams fork from and join back to the
+// plan's stream.
+template <class G>
+static fv_status execute_slices(fv_plan_s *p, char *vis, size_t slice_bytes)
+{
+    const long total = (long)p->freq.size() * p->lst.size();
+    const int S = (int)std::min<long>(p->n_streams, std::max<long>(total, 1));
+    if (S > 1) {
+        CK(cudaEventRecord(p->ev_fork, p->stream));
+        for (int s = 1; s < S; ++s) CK(cudaStreamWaitEvent(p->sub[s], p->ev_fork, 0));
+    }
+    for (int s = 0; s < S; ++s) {
+        const long k0 = total * s / S, k1 = total * (s + 1) / S;
+        fv_status st = run_slices<G>(p, p->ws[s], p->sub[s], vis, slice_bytes, k0, k1);
+        if (st != FV_OK) return st;
+    }
+    if (S > 1) {
+        for (int s = 1; s < S; ++s) {
+            CK(cudaEventRecord(p->ev_join[s], p->sub[s]));
+            CK(cudaStreamWaitEvent(p->stream, p->ev_join[s], 0));
         }
     }
     return FV_OK;
@@ -418,6 +467,9 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
         return bad("Gaussian beam needs FWHM > 0 and reference frequency > 0");
     if (o->beam == FV_BEAM_AIRY && !(o->beam_param[0] > 0)) return bad("Airy beam needs a diameter > 0");
     if (o->dims != 0 && o->dims != 2 && o->dims != 3) return bad("dims must be 0, 2 or 3");
+    if (o->spread_method < FV_SPREAD_AUTO || o->spread_method > FV_SPREAD_ATOMIC) return bad("unknown spread_method");
+    if (o->n_streams < 0) return bad("n_streams < 0");
+    if (o->fft_max_radix != 0 && o->fft_max_radix != 8 && o->fft_max_radix != 16) return bad("fft_max_radix must be 0, 8 or 16");
     double sigma = o->upsampfac == 0.0 ? 2.0 : o->upsampfac;
     if (!(sigma >= 1.25 && sigma <= 3.0)) return bad("upsampfac must be in [1.25, 3]");
     // the two deconvolutions amplify FP32 rounding by (Phihat(0)/Phihat(w pi/2 sigma))^2 at the band
@@ -474,6 +526,25 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
             return FV_ERR_CUDA;
         }
         p->own_stream = true;
+    }
+    // execution streams: sub[0] is the plan's stream, the others are owned by the plan
+    p->n_streams = o->n_streams > 0 ? std::min(o->n_streams, 16) : 4;
+    p->spread_req = o->spread_method;
+    // radix 8 needs fewer registers (more CTAs per SM), which wins in FP32; FP64 uses the same
+    // register count either way and prefers fewer stages
+    p->fft_max_radix = o->fft_max_radix > 0 ? o->fft_max_radix : (o->precision == FV_MIXED ? 8 : 16);
+    p->sub.assign(p->n_streams, nullptr);
+    p->ev_join.assign(p->n_streams, nullptr);
+    p->sub[0] = p->stream;
+    bool ok = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int s = 1; s < p->n_streams && ok; ++s) {
+        ok = cudaStreamCreateWithFlags(&p->sub[s], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&p->ev_join[s], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+        g_create_error = "stream or event creation failed";
+        fv_destroy(p);
+        return FV_ERR_CUDA;
     }
     // rotation matrices, equatorial -> ENU (Section 2.3 rigid rotation)
     p->Rt.resize((size_t)o->n_time * 9);
@@ -687,6 +758,8 @@ fv_status fv_destroy(fv_plan_t p)
 {
     if (!p) return FV_OK;
     cudaSetDevice(p->device);
+    for (cudaStream_t st : p->sub)
+        if (st) cudaStreamSynchronize(st);
     if (p->stream) cudaStreamSynchronize(p->stream);
     free_geometry(p);
     dfree_t(p->d_glx);
@@ -697,6 +770,11 @@ fv_status fv_destroy(fv_plan_t p)
     dfree_t(p->d_e);
     dfree(p->d_flux_owned);
     for (cudaEvent_t ev : p->ev_pool) cudaEventDestroy(ev);
+    for (size_t s = 1; s < p->sub.size(); ++s) {
+        if (p->sub[s]) cudaStreamDestroy(p->sub[s]);
+        if (p->ev_join[s]) cudaEventDestroy(p->ev_join[s]);
+    }
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
     delete p;
     return FV_OK;

@@ -319,6 +319,132 @@ __global__ void __launch_bounds__(kGatherThreads) k_spread_gather(const int *__r
     }
 }
 
+// Scatter form of the tiled spreading: a CTA owns a kScatX x kScatY tile with
+// all z cells in shared memory (real and imaginary parts in separate planes,
+// rows padded to kScatRS floats so that the lanes of a footprint fall in
+// different banks); each warp takes one candidate source at a time, its lanes
+// cover the source's (x, y) footprint inside the tile and loop over the z
+// footprint, adding with shared-memory atomics; the tile is stored once.
+constexpr int kScatX = 32, kScatY = 16, kScatRS = 40;
+
+template <class G, int NP>
+__global__ void __launch_bounds__(256) k_spread_scatter(const int *__restrict__ offsets, const int *__restrict__ cell,
+                                                        const G *__restrict__ frac, const cpx<G> *__restrict__ cs,
+                                                        long n_src, SliceGeom g, TimeBin tb, double r0, double r1,
+                                                        cpx<G> *__restrict__ grid)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nx = g.dim[0].nf1, ny = g.dim[1].nf1, nz = g.d == 3 ? g.dim[2].nf1 : 1;
+    const int plane = nz * NP * kScatY * kScatRS;
+    G *tre = reinterpret_cast<G *>(smem_raw), *tim = tre + plane;
+    const int w = g.w;
+    const int x0 = blockIdx.x * kScatX, y0 = blockIdx.y * kScatY;
+    for (int i = threadIdx.x; i < 2 * plane; i += blockDim.x) tre[i] = (G)0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const double qx_lo = (x0 - nx / 2 - 0.5 * w) / r0, qx_hi = (x0 + kScatX - nx / 2 + 0.5 * w - 1) / r0;
+    const double qy_lo = (y0 - ny / 2 - 0.5 * w) / r1, qy_hi = (y0 + kScatY - ny / 2 + 0.5 * w - 1) / r1;
+    const int bx_lo = top_cell(qx_lo - 1.0, tb.nf1_top[0]) / tb.T[0];
+    const int bx_hi = top_cell(qx_hi + 1.0, tb.nf1_top[0]) / tb.T[0];
+    const int by_lo = top_cell(qy_lo - 1.0, tb.nf1_top[1]) / tb.T[1];
+    const int by_hi = top_cell(qy_hi + 1.0, tb.nf1_top[1]) / tb.T[1];
+    const G two_over_w = (G)(2.0 / w), beta = (G)g.beta;
+    __syncthreads();
+    int k = 0;   // running candidate count across bin rows, dealt to warps round robin
+    for (int by = by_lo; by <= by_hi; ++by) {
+        const int i0 = offsets[by * tb.nbx + bx_lo], i1 = offsets[by * tb.nbx + bx_hi + 1];
+        const int n = i1 - i0;
+        int j = (warp - k % nwarps + nwarps) % nwarps;
+        k += n;
+        for (; j < n; j += nwarps) {
+            const int i = i0 + j;
+            const int cx = cell[i], cy = cell[n_src + i];
+            if (cx + w <= x0 || cx >= x0 + kScatX || cy + w <= y0 || cy >= y0 + kScatY) continue;   // warp-uniform
+            const int cz = g.d == 3 ? cell[2 * n_src + i] : 0;
+            const G fx = frac[i], fy = frac[n_src + i];
+            const G fz = g.d == 3 ? frac[2 * n_src + i] : (G)0;
+            // z kernel values: lane jz < w computes one, every lane reads them by shuffle
+            const G wz_mine = (g.d == 3 && lane < w) ? es_k<G>(two_over_w * (fz + (G)lane), beta) : (G)(lane == 0);
+            cpx<G> c[NP];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) c[p] = cs[(size_t)p * n_src + i];
+            const int wzn = g.d == 3 ? w : 1;
+            // every lane runs the same number of iterations: the shuffles below need the whole warp
+            for (int pr0 = 0; pr0 < w * w; pr0 += 32) {
+                const int pr = pr0 + lane;
+                const int jy = pr / w, jx = pr - jy * w;
+                const int lx = cx + jx - x0, ly = cy + jy - y0;
+                const bool in = pr < w * w && lx >= 0 && lx < kScatX && ly >= 0 && ly < kScatY;
+                const G wxy = in ? es_k<G>(two_over_w * (fx + (G)jx), beta) * es_k<G>(two_over_w * (fy + (G)jy), beta)
+                                 : (G)0;
+                const int cell_off = ly * kScatRS + lx;
+                for (int jz = 0; jz < wzn; ++jz) {
+                    const G wt = wxy * __shfl_sync(0xffffffffu, wz_mine, jz);
+                    const int z = cz + jz;
+                    if (in && z >= 0 && z < nz) {
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) {
+                            const int o = (p * nz + z) * kScatY * kScatRS + cell_off;
+                            atomicAdd(&tre[o], wt * c[p].x);
+                            atomicAdd(&tim[o], wt * c[p].y);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int tsz = NP * nz * kScatY * kScatX;
+    for (int idx = threadIdx.x; idx < tsz; idx += blockDim.x) {
+        const int lx = idx % kScatX;
+        int rest = idx / kScatX;
+        const int ly = rest % kScatY;
+        rest /= kScatY;   // p * nz + z
+        const int x = x0 + lx, y = y0 + ly;
+        const int o = rest * kScatY * kScatRS + ly * kScatRS + lx;
+        if (x < nx && y < ny) grid[((size_t)rest * ny + y) * nx + x] = cmk<G>(tre[o], tim[o]);
+    }
+}
+
+template <class G>
+cudaError_t launch_spread_scatter(const int *offsets, const int *cell, const G *frac, const cpx<G> *cs, long n_src,
+                                  const SliceGeom &g, const TimeBin &tb, double r0, double r1, cpx<G> *grid,
+                                  cudaStream_t st)
+{
+    const int nz = g.d == 3 ? g.dim[2].nf1 : 1;
+    const size_t smem = spread_scatter_smem(sizeof(G), g.n_pol, nz);
+    if (smem > FV_SPREAD_SMEM_MAX || g.w > 32) return cudaErrorInvalidValue;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set[dev]) {
+        e = cudaFuncSetAttribute(k_spread_scatter<G, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, FV_SPREAD_SMEM_MAX);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_spread_scatter<G, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, FV_SPREAD_SMEM_MAX);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    dim3 blocks((g.dim[0].nf1 + kScatX - 1) / kScatX, (g.dim[1].nf1 + kScatY - 1) / kScatY);
+    if (g.n_pol == 4)
+        k_spread_scatter<G, 4><<<blocks, 256, smem, st>>>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid);
+    else
+        k_spread_scatter<G, 1><<<blocks, 256, smem, st>>>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid);
+    return cudaGetLastError();
+}
+
+size_t spread_scatter_smem(int elem_bytes, int n_pol, int nz)
+{
+    return (size_t)2 * n_pol * nz * kScatY * kScatRS * elem_bytes;
+}
+
+template cudaError_t launch_spread_scatter<double>(const int *, const int *, const double *, const cpx<double> *, long,
+                                                   const SliceGeom &, const TimeBin &, double, double,
+                                                   cpx<double> *, cudaStream_t);
+template cudaError_t launch_spread_scatter<float>(const int *, const int *, const float *, const cpx<float> *, long,
+                                                  const SliceGeom &, const TimeBin &, double, double, cpx<float> *,
+                                                  cudaStream_t);
+
 template <class G, int NP, int NZ>
 static cudaError_t gather_launch(const int *offsets, const int *cell, const G *frac, const cpx<G> *cs, long n_src,
                                  const SliceGeom &g, const TimeBin &tb, double r0, double r1, cpx<G> *grid,

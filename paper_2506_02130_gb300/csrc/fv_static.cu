@@ -132,8 +132,12 @@ fv_status run_static(fv_plan_s *p, const Scratch &sc, char *vis, size_t slice_by
                                    sc.cell, (G *)sc.frac, (cpx<G> *)sc.cs, p->stream));
                 const double r0 = D[0].qscale / p->qscale_top[0], r1 = D[1].qscale / p->qscale_top[1];
                 // every grid cell is stored by exactly one tile: no clearing needed
-                CKS(launch_spread_tile<G>(sc.offsets, sc.cell, (const G *)sc.frac, (const cpx<G> *)sc.cs, p->n_src,
-                                          g, tb, r0, r1, grid, p->stream));
+                if (p->spread_method == FV_SPREAD_SCATTER)
+                    CKS(launch_spread_scatter<G>(sc.offsets, sc.cell, (const G *)sc.frac, (const cpx<G> *)sc.cs,
+                                                 p->n_src, g, tb, r0, r1, grid, p->stream));
+                else
+                    CKS(launch_spread_tile<G>(sc.offsets, sc.cell, (const G *)sc.frac, (const cpx<G> *)sc.cs, p->n_src,
+                                              g, tb, r0, r1, grid, p->stream));
             } else {
                 // the atomic spreader accumulates: the grid must start at zero
                 const size_t gel = (size_t)p->n_pol * D[0].nf1 * D[1].nf1 * D[2].nf1;

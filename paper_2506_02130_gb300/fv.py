@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_PKG, "libfftvis_gb300.so")
 
 FV_OK, FV_ERR_ARG, FV_ERR_OOM, FV_ERR_CUDA, FV_ERR_STATE, FV_ERR_TIMEOUT, FV_ERR_UNSUPPORTED = range(7)
 FV_FP64, FV_MIXED = 0, 1
+SPREAD = {"auto": 0, "gather": 1, "scatter": 2, "atomic": 3}
 BEAMS = {"gauss": 0, "airy": 1, "uniform": 2}
 STATUS_NAMES = {0: "FV_OK", 1: "FV_ERR_ARG", 2: "FV_ERR_OOM", 3: "FV_ERR_CUDA", 4: "FV_ERR_STATE",
                 5: "FV_ERR_TIMEOUT", 6: "FV_ERR_UNSUPPORTED"}
@@ -40,7 +41,8 @@ class fv_opts(C.Structure):
                 ("n_time", C.c_int), ("lst_rad", C.POINTER(C.c_double)),
                 ("latitude_rad", C.c_double), ("beam", C.c_int), ("beam_param", C.c_double * 3),
                 ("polarized", C.c_int), ("dims", C.c_int), ("upsampfac", C.c_double),
-                ("kernel_width", C.c_int), ("cuda_stream", C.c_void_p), ("device", C.c_int)]
+                ("kernel_width", C.c_int), ("cuda_stream", C.c_void_p), ("device", C.c_int),
+                ("n_streams", C.c_int), ("spread_method", C.c_int), ("fft_max_radix", C.c_int)]
 
 
 class fv_info(C.Structure):
@@ -203,7 +205,8 @@ class Plan:
 
     @classmethod
     def create(cls, freqs_hz, lsts_rad, latitude_rad, beam="gauss", beam_param=(), precision=FV_FP64,
-               eps=1e-10, polarized=False, dims=0, upsampfac=0.0, kernel_width=0, stream=None, device=-1):
+               eps=1e-10, polarized=False, dims=0, upsampfac=0.0, kernel_width=0, stream=None, device=-1,
+               n_streams=0, spread="auto", fft_max_radix=0):
         o = fv_opts_default()
         freqs = np.ascontiguousarray(freqs_hz, dtype=np.float64)
         lsts = np.ascontiguousarray(lsts_rad, dtype=np.float64)
@@ -223,6 +226,9 @@ class Plan:
         o.kernel_width = kernel_width
         o.cuda_stream = None if stream is None else C.c_void_p(stream)
         o.device = device
+        o.n_streams = n_streams
+        o.spread_method = SPREAD[spread]
+        o.fft_max_radix = fft_max_radix
         h = fv_plan(o)
         return cls(h, len(freqs), len(lsts), 0, 4 if polarized else 1, precision)
 

@@ -182,3 +182,24 @@ def test_linearity_and_frequency_baseline_scaling():
     prob2.freqs_hz = prob.freqs_hz / 2
     c, _ = run_gpu(prob2, fv.FV_FP64)
     assert rel_l2(c, a) <= 1e-9
+
+
+@pytest.mark.parametrize("spread", ["gather", "scatter", "atomic"])
+@pytest.mark.parametrize("precision", [fv.FV_FP64, fv.FV_MIXED])
+def test_spreading_methods_agree_with_oracle(spread, precision):
+    prob = small_3d(seed=12, n_chan=2, n_time=2)
+    out, _ = run_gpu(prob, precision, spread=spread)
+    assert rel_l2(out, oracle(prob)) <= TOL[precision]
+    pol = small_pol(seed=13, n_chan=1, n_time=1)
+    out, _ = run_gpu(pol, precision, spread=spread)
+    assert rel_l2(out, oracle(pol)) <= 2 * TOL[precision]
+
+
+@pytest.mark.parametrize("max_radix", [8, 16])
+@pytest.mark.parametrize("n_streams", [1, 3])
+def test_fft_radix_cap_and_streams(max_radix, n_streams):
+    prob = small_3d(seed=14, n_chan=3, n_time=2)
+    ref = oracle(prob)
+    for precision in (fv.FV_FP64, fv.FV_MIXED):
+        out, _ = run_gpu(prob, precision, fft_max_radix=max_radix, n_streams=n_streams)
+        assert rel_l2(out, ref) <= TOL[precision]
