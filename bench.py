@@ -218,7 +218,8 @@ def main():
     precision = fv.FV_MIXED if args.precision == "mixed" else fv.FV_FP64
     eps = 1e-6 if precision == fv.FV_MIXED else 1e-11
     prob = workload(1 + rank)             # each rank simulates its own independent problem (weak scaling)
-    stream = torch.cuda.current_stream(dev)
+    # a dedicated stream: the plan runs on it and the timing events are recorded on it
+    stream = torch.cuda.Stream(device=dev)
     plan = fv.Plan.from_problem(prob, precision=precision, eps=eps, stream=stream.cuda_stream, device=local,
                                 n_streams=args.streams, spread=args.spread)
     fdt = torch.float32 if precision == fv.FV_MIXED else torch.float64

@@ -85,7 +85,8 @@ typedef struct {
                                  the deconvolutions amplify FP32 rounding too much below it) */
     int kernel_width;         /* ES kernel width w in grid points; 0 = from eps
                                  (w = ceil(log10(1/eps)) + 1 at sigma = 2, Section 2.2) */
-    void *cuda_stream;        /* borrowed cudaStream_t, or NULL for a plan-owned stream */
+    void *cuda_stream;        /* borrowed cudaStream_t, or NULL for a plan-owned stream (so the
+                                 legacy default stream is named by cudaStreamLegacy, not 0) */
     int device;               /* CUDA device ordinal; -1 = the current device */
     int n_streams;            /* slices run concurrently on this many streams, each with its own
                                  workspace (forked from and joined back to cuda_stream); 0 = 4 */

@@ -20,6 +20,21 @@ __device__ __forceinline__ float es_kernel(float z, float beta)
     return t >= 0.0f ? expf(beta * (sqrtf(t) - 1.0f)) : 0.0f;
 }
 
+// Two consecutive complex values in one vector load (the address is a multiple of 2 complex).
+__device__ __forceinline__ void load_pair(const cpx<float> *p, cpx<float> &a, cpx<float> &b)
+{
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    a = cmk<float>(v.x, v.y);
+    b = cmk<float>(v.z, v.w);
+}
+__device__ __forceinline__ void load_pair(const cpx<double> *p, cpx<double> &a, cpx<double> &b)
+{
+    const double2 v0 = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 v1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    a = cmk<double>(v0.x, v0.y);
+    b = cmk<double>(v1.x, v1.y);
+}
+
 // Phihat(k) = int_{-1}^{1} phi(z) cos(k z) dz by Gauss-Legendre quadrature (FP64).
 __device__ double es_fourier(double k, double beta, const double *gl_x, const double *gl_w, int nq)
 {
@@ -390,17 +405,34 @@ __global__ void __launch_bounds__(256) k_interp_zdirect(const cpx<G> *__restrict
     const int np = g.n_pol;
     const int Bx = g.dim[0].B;
     const int bx0 = m0[0] + g.dim[0].H, by0 = m0[1] + g.dim[1].H;
+    // x and y kernel values: lane j < w holds the j-th, the others read them by shuffle
+    const G wxm = lane < w ? es_kernel(two_over_w * (fr[0] - (G)lane), beta) : (G)0;
+    const G wym = lane < w ? es_kernel(two_over_w * (fr[1] - (G)lane), beta) : (G)0;
     G acc[8];
     for (int k = 0; k < 2 * np; ++k) acc[k] = (G)0;
-    for (int idx = lane; idx < w * w; idx += 32) {
-        const int jy = idx / w, jx = idx - jy * w;
-        const G wt = es_kernel(two_over_w * (fr[1] - (G)jy), beta) * es_kernel(two_over_w * (fr[0] - (G)jx), beta);
-        const cpx<G> *cell = band + (((size_t)(by0 + jy) * Bx + (bx0 + jx)) * np) * Nz;
-        for (int p = 0; p < np; ++p) {
-            cpx<G> s = cmk<G>((G)0, (G)0);
-            for (int lz = 0; lz < Nz; ++lz) s = cadd(s, cmul(cell[p * Nz + lz], K[lz]));
-            acc[2 * p] += wt * s.x;
-            acc[2 * p + 1] += wt * s.y;
+    const bool vec2 = (Nz % 2) == 0;   // z runs of even length are read as pairs of complex values
+    for (int base = 0; base < w * w; base += 32) {   // same trip count on every lane (shuffles)
+        const int idx = base + lane;
+        const bool valid = idx < w * w;
+        const int jy = valid ? idx / w : 0, jx = valid ? idx - jy * w : 0;
+        const G wt = __shfl_sync(0xffffffffu, wym, jy) * __shfl_sync(0xffffffffu, wxm, jx);
+        if (valid) {
+            const cpx<G> *cell = band + (((size_t)(by0 + jy) * Bx + (bx0 + jx)) * np) * Nz;
+            for (int p = 0; p < np; ++p) {
+                cpx<G> s = cmk<G>((G)0, (G)0);
+                const cpx<G> *c = cell + p * Nz;
+                if (vec2) {
+                    for (int lz = 0; lz < Nz; lz += 2) {
+                        cpx<G> v0, v1;
+                        load_pair(c + lz, v0, v1);
+                        s = cadd(s, cadd(cmul(v0, K[lz]), cmul(v1, K[lz + 1])));
+                    }
+                } else {
+                    for (int lz = 0; lz < Nz; ++lz) s = cadd(s, cmul(c[lz], K[lz]));
+                }
+                acc[2 * p] += wt * s.x;
+                acc[2 * p + 1] += wt * s.y;
+            }
         }
     }
     for (int k = 0; k < 2 * np; ++k)

@@ -83,6 +83,7 @@ struct fv_plan_s {
     int nf1_top[3] = {1, 1, 1};
 
     long long ws_bytes = 0;
+    std::vector<long> geo_sig;       // sizes behind the current tables and workspaces
     int nf1_max[3] = {1, 1, 1}, M_max[3] = {1, 1, 1};
 
     // kernel timing (fv_profile_enable)

@@ -156,10 +156,36 @@ static void free_geometry(fv_plan_s *p)
     p->ws.clear();
 }
 
+// Top channel, spreading method and bin geometry (needs the per-channel geometry).
+static void resolve_spread(fv_plan_s *p, int gs, int w)
+{
+    const int nf = (int)p->freq.size();
+    p->f_top = 0;
+    for (int f = 1; f < nf; ++f)
+        if (p->freq[f] > p->freq[p->f_top]) p->f_top = f;
+    for (int i = 0; i < 3; ++i) {
+        p->qscale_top[i] = p->gf[p->f_top].dim[i].qscale;
+        p->nf1_top[i] = p->gf[p->f_top].dim[i].nf1;
+    }
+    const int nzm = p->d == 3 ? p->nf1_max[2] : 1;
+    int nz_t = 0, bx = 8, by = 4;
+    const bool gather_ok = spread_gather_config(gs, p->n_pol, nzm, w, &nz_t, &bx, &by) != 0;
+    const bool scatter_ok = spread_scatter_smem(gs, p->n_pol, nzm) <= FV_SPREAD_SMEM_MAX && w <= 32;
+    int m = p->spread_req;
+    if (m == FV_SPREAD_AUTO) m = gather_ok ? FV_SPREAD_GATHER : (scatter_ok ? FV_SPREAD_SCATTER : FV_SPREAD_ATOMIC);
+    if (m == FV_SPREAD_GATHER && !gather_ok) m = FV_SPREAD_ATOMIC;
+    if (m == FV_SPREAD_SCATTER && !scatter_ok) m = FV_SPREAD_ATOMIC;
+    p->spread_method = m;
+    p->tiled = m != FV_SPREAD_ATOMIC;
+    p->T[0] = 8;
+    p->T[1] = 4;
+    p->nbx = (p->nf1_top[0] + p->T[0] - 1) / p->T[0];
+    p->nby = (p->nf1_top[1] + p->T[1] - 1) / p->T[1];
+}
+
 // Per-channel geometry, tables and workspace; needs the array and the sky.
 static fv_status prepare(fv_plan_s *p)
 {
-    free_geometry(p);
     const int nf = (int)p->freq.size();
     const int w = p->w;
     p->gf.assign(nf, SliceGeom{});
@@ -192,7 +218,7 @@ static fv_status prepare(fv_plan_s *p)
             if (!(X > 0.0)) X = S > 0.0 ? 1.0 / S : 1.0;
             double need = 2.0 * p->sigma * X * S / M_PI + w;
             long nf1 = (long)std::ceil(need);
-            if (nf1 < w + 2) nf1 = w + 2;     // Eq. 5 is the requirement; no 2w floor is needed
+            if (nf1 < w + 1) nf1 = w + 1;     // Eq. 5 is the requirement; no 2w floor is needed
             if (nf1 > (1L << 20)) return p->fail(FV_ERR_UNSUPPORTED, "spreading grid too large");
             dg.nf1 = next235even(nf1);
             dg.M = fft_choose_length((int)std::ceil(p->sigma * dg.nf1 - 1e-9), dg.radix, dg.nstages, p->fft_max_radix);
@@ -225,6 +251,23 @@ static fv_status prepare(fv_plan_s *p)
     }
     const size_t es = p->elem();
     const size_t gs = p->precision == FV_FP64 ? sizeof(double) : sizeof(float);
+    // a new sky with the same grid sizes (the usual case: same array, same channels) keeps the
+    // tables and workspaces of the previous one
+    std::vector<long> sig = {(long)p->n_src, (long)p->n_pol, (long)p->n_streams, (long)p->spread_req, (long)p->d,
+                             (long)grid_e, (long)bufA_e, (long)bufB_e};
+    for (int f = 0; f < nf; ++f)
+        for (int i = 0; i < 3; ++i) {
+            sig.push_back(p->gf[f].dim[i].nf1);
+            sig.push_back(p->gf[f].dim[i].M);
+        }
+    const bool reuse = !p->ws.empty() && sig == p->geo_sig;
+    if (!reuse) free_geometry(p);
+    p->geo_sig.clear();
+    if (reuse) {
+        resolve_spread(p, (int)gs, w);
+        p->geo_sig = sig;
+        return FV_OK;
+    }
     CK(cudaMalloc(&p->d_pre, std::max<size_t>(pre_total, 1) * gs));
     CK(cudaMalloc(&p->d_tw, std::max<size_t>(tw_total, 1) * es));
     p->ws.assign(p->n_streams, fv_plan_s::Workspace{});
@@ -251,32 +294,7 @@ static fv_status prepare(fv_plan_s *p)
             }
         }
     }
-    // binned spreading: tiles of 32 x T_y cells (all z), bins = tiles of the top channel's grid
-    p->f_top = 0;
-    for (int f = 1; f < nf; ++f)
-        if (p->freq[f] > p->freq[p->f_top]) p->f_top = f;
-    for (int i = 0; i < 3; ++i) {
-        p->qscale_top[i] = p->gf[p->f_top].dim[i].qscale;
-        p->nf1_top[i] = p->gf[p->f_top].dim[i].nf1;
-    }
-    {
-        const int nzm = p->d == 3 ? p->nf1_max[2] : 1;
-        int nz_t = 0, bx = 8, by = 4;
-        const bool gather_ok = spread_gather_config((int)gs, p->n_pol, nzm, w, &nz_t, &bx, &by) != 0;
-        const bool scatter_ok = spread_scatter_smem((int)gs, p->n_pol, nzm) <= FV_SPREAD_SMEM_MAX && w <= 32;
-        int m = p->spread_req;
-        if (m == FV_SPREAD_AUTO) m = scatter_ok ? FV_SPREAD_SCATTER : (gather_ok ? FV_SPREAD_GATHER : FV_SPREAD_ATOMIC);
-        if (m == FV_SPREAD_GATHER && !gather_ok) m = FV_SPREAD_ATOMIC;
-        if (m == FV_SPREAD_SCATTER && !scatter_ok) m = FV_SPREAD_ATOMIC;
-        p->spread_method = m;
-        p->tiled = m != FV_SPREAD_ATOMIC;
-        bx = 8;
-        by = 4;
-        p->T[0] = bx;
-        p->T[1] = by;
-        p->nbx = (p->nf1_top[0] + p->T[0] - 1) / p->T[0];
-        p->nby = (p->nf1_top[1] + p->T[1] - 1) / p->T[1];
-    }
+    resolve_spread(p, (int)gs, w);
     size_t bin_bytes = 0;
     if (p->tiled) {
         const size_t ns = std::max<long>(p->n_src, 1), nb = (size_t)p->nbx * p->nby;
@@ -297,6 +315,7 @@ static fv_status prepare(fv_plan_s *p)
                               p->n_streams * ((grid_e + bufA_e + bufB_e) * es +
                                               (size_t)p->n_u * p->n_pol * sizeof(cpx<double>) + bin_bytes));
     CK(cudaStreamSynchronize(p->stream));
+    p->geo_sig = sig;
     return FV_OK;
 }
 

@@ -222,16 +222,18 @@ cudaError_t launch_prep(const double *sdir, const int *sidx, const int *nv_ptr, 
 // Gather form of the tiled spreading.  A CTA of 8 warps owns a 32 x 8 tile
 // of (x, y) columns; warp k owns an 8 x 4 patch of it and each lane one
 // column, holding that column's NZ z cells and NP products in registers.  The
-// tile's candidate sources (bins of 8 x 4 top-channel cells, so the candidate
-// set overshoots the tile's footprint region by little) are staged in shared
-// memory in chunks with their per-axis kernel values; each warp tests a
-// candidate's footprint box against its patch (a warp-uniform branch) and only
-// the overlapping warps add it.  No atomics; every grid cell is stored once.
+// tile's candidate sources (bins of 8 x 4 top-channel cells) are staged in
+// shared memory in chunks: per source its x and y kernel values, its z kernel
+// values placed at absolute z (zero elsewhere) and its strengths.  While
+// staging, each source is appended to the candidate list of every patch its
+// footprint overlaps (shared-memory integer atomics); each warp then adds the
+// sources of its own list.  No float atomics; every grid cell is stored once.
 constexpr int kGatherThreads = 256;
 constexpr int kGatherChunk = 128;
 constexpr int kWmax = 16;
 constexpr int kPatchX = 8, kPatchY = 4;     // one warp
 constexpr int kTileX = 32, kTileY = 8;      // one CTA (4 x 2 patches)
+constexpr int kPatches = 8;
 
 template <class G, int NP, int NZ>
 __global__ void __launch_bounds__(kGatherThreads) k_spread_gather(const int *__restrict__ offsets,
@@ -241,9 +243,12 @@ __global__ void __launch_bounds__(kGatherThreads) k_spread_gather(const int *__r
                                                                   SliceGeom g, TimeBin tb, double r0, double r1,
                                                                   cpx<G> *__restrict__ grid)
 {
-    __shared__ int s_cx[kGatherChunk], s_cy[kGatherChunk], s_cz[kGatherChunk];
-    __shared__ G s_w[3][kGatherChunk * kWmax];
+    __shared__ int s_cx[kGatherChunk], s_cy[kGatherChunk];
+    __shared__ G s_wx[kGatherChunk][kWmax], s_wy[kGatherChunk][kWmax];
+    __shared__ __align__(16) G s_wz[kGatherChunk][NZ];
     __shared__ cpx<G> s_c[NP][kGatherChunk];
+    __shared__ unsigned char s_list[kPatches][kGatherChunk];
+    __shared__ int s_cnt[kPatches];
     const int nx = g.dim[0].nf1, ny = g.dim[1].nf1, nz = g.d == 3 ? g.dim[2].nf1 : 1;
     const int w = g.w;
     const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
@@ -255,6 +260,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_spread_gather(const int *__r
     for (int p = 0; p < NP; ++p)
 #pragma unroll
         for (int z = 0; z < NZ; ++z) acc[p][z] = cmk<G>((G)0, (G)0);
+    if (threadIdx.x < kPatches) s_cnt[threadIdx.x] = 0;
     // sources whose footprint can meet this tile (one-cell margin through the top-grid mapping)
     const double qx_lo = (x0 - nx / 2 - 0.5 * w) / r0, qx_hi = (x0 + kTileX - nx / 2 + 0.5 * w - 1) / r0;
     const double qy_lo = (y0 - ny / 2 - 0.5 * w) / r1, qy_hi = (y0 + kTileY - ny / 2 + 0.5 * w - 1) / r1;
@@ -263,6 +269,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_spread_gather(const int *__r
     const int by_lo = top_cell(qy_lo - 1.0, tb.nf1_top[1]) / tb.T[1];
     const int by_hi = top_cell(qy_hi + 1.0, tb.nf1_top[1]) / tb.T[1];
     const G two_over_w = (G)(2.0 / w), beta = (G)g.beta;
+    __syncthreads();
     for (int by = by_lo; by <= by_hi; ++by) {
         const int i0 = offsets[by * tb.nbx + bx_lo], i1 = offsets[by * tb.nbx + bx_hi + 1];
         for (int base = i0; base < i1; base += kGatherChunk) {
@@ -270,43 +277,63 @@ __global__ void __launch_bounds__(kGatherThreads) k_spread_gather(const int *__r
             if (threadIdx.x < n) {
                 const int i = base + threadIdx.x;
                 const int t = threadIdx.x;
-                s_cx[t] = cell[i];
-                s_cy[t] = cell[n_src + i];
-                s_cz[t] = g.d == 3 ? cell[2 * n_src + i] : 0;
-                const G fx = frac[i], fy = frac[n_src + i];
-                const G fz = g.d == 3 ? frac[2 * n_src + i] : (G)0;
-                for (int j = 0; j < w; ++j) {
-                    s_w[0][t * kWmax + j] = es_k<G>(two_over_w * (fx + (G)j), beta);
-                    s_w[1][t * kWmax + j] = es_k<G>(two_over_w * (fy + (G)j), beta);
-                    s_w[2][t * kWmax + j] = g.d == 3 ? es_k<G>(two_over_w * (fz + (G)j), beta) : (G)(j == 0);
-                }
+                const int cx = cell[i], cy = cell[n_src + i];
+                // patches of this tile that the footprint [cx, cx+w) x [cy, cy+w) overlaps
+                const int ax = max(cx - x0, 0), bx = min(cx + w - 1 - x0, kTileX - 1);
+                const int ay = max(cy - y0, 0), by2 = min(cy + w - 1 - y0, kTileY - 1);
+                if (ax <= bx && ay <= by2) {
+                    s_cx[t] = cx;
+                    s_cy[t] = cy;
+                    const G fx = frac[i], fy = frac[n_src + i];
+                    for (int j = 0; j < w; ++j) {
+                        s_wx[t][j] = es_k<G>(two_over_w * (fx + (G)j), beta);
+                        s_wy[t][j] = es_k<G>(two_over_w * (fy + (G)j), beta);
+                    }
+                    if (g.d == 3) {
+                        const int cz = cell[2 * n_src + i];
+                        const G fz = frac[2 * n_src + i];
 #pragma unroll
-                for (int p = 0; p < NP; ++p) s_c[p][t] = cs[(size_t)p * n_src + i];
+                        for (int z = 0; z < NZ; ++z) {
+                            const int jz = z - cz;
+                            s_wz[t][z] = (jz >= 0 && jz < w) ? es_k<G>(two_over_w * (fz + (G)jz), beta) : (G)0;
+                        }
+                    } else {
+#pragma unroll
+                        for (int z = 0; z < NZ; ++z) s_wz[t][z] = (G)(z == 0);
+                    }
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) s_c[p][t] = cs[(size_t)p * n_src + i];
+                    for (int qy = ay / kPatchY; qy <= by2 / kPatchY; ++qy)
+                        for (int qx = ax / kPatchX; qx <= bx / kPatchX; ++qx) {
+                            const int q = qy * 4 + qx;
+                            const int pos = atomicAdd(&s_cnt[q], 1);
+                            s_list[q][pos] = (unsigned char)t;
+                        }
+                }
             }
             __syncthreads();
-            for (int t = 0; t < n; ++t) {
-                const int cx = s_cx[t], cy = s_cy[t];
-                // footprint [cx, cx+w) x [cy, cy+w) against the warp's patch: uniform across the warp
-                if (cx + w <= px0 || cx >= px0 + kPatchX || cy + w <= py0 || cy >= py0 + kPatchY) continue;
-                const unsigned dx = (unsigned)(gx - cx), dy = (unsigned)(gy - cy);
+            const int cnt = s_cnt[warp];
+            for (int e = 0; e < cnt; ++e) {
+                const int t = s_list[warp][e];
+                const unsigned dx = (unsigned)(gx - s_cx[t]), dy = (unsigned)(gy - s_cy[t]);
                 if (dx < (unsigned)w && dy < (unsigned)w) {
-                    const int cz = s_cz[t];
-                    const G wxy = s_w[0][t * kWmax + dx] * s_w[1][t * kWmax + dy];
+                    const G wxy = s_wx[t][dx] * s_wy[t][dy];
+                    G wz[NZ];
+#pragma unroll
+                    for (int z = 0; z < NZ; ++z) wz[z] = s_wz[t][z];
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
                         const cpx<G> cp = cscale(s_c[p][t], wxy);
 #pragma unroll
                         for (int z = 0; z < NZ; ++z) {
-                            const unsigned jz = (unsigned)(z - cz);
-                            if (jz < (unsigned)w) {
-                                const G wz = s_w[2][t * kWmax + jz];
-                                acc[p][z].x += cp.x * wz;
-                                acc[p][z].y += cp.y * wz;
-                            }
+                            acc[p][z].x += cp.x * wz[z];
+                            acc[p][z].y += cp.y * wz[z];
                         }
                     }
                 }
             }
+            __syncthreads();
+            if (threadIdx.x < kPatches) s_cnt[threadIdx.x] = 0;
             __syncthreads();
         }
     }
@@ -316,6 +343,54 @@ __global__ void __launch_bounds__(kGatherThreads) k_spread_gather(const int *__r
 #pragma unroll
             for (int z = 0; z < NZ; ++z)
                 if (z < nz) grid[(((size_t)p * nz + z) * ny + gy) * nx + gx] = acc[p][z];
+    }
+}
+
+template <class G, int NP, int NZ>
+static cudaError_t gather_launch(const int *offsets, const int *cell, const G *frac, const cpx<G> *cs, long n_src,
+                                 const SliceGeom &g, const TimeBin &tb, double r0, double r1, cpx<G> *grid,
+                                 cudaStream_t st)
+{
+    dim3 blocks((g.dim[0].nf1 + kTileX - 1) / kTileX, (g.dim[1].nf1 + kTileY - 1) / kTileY);
+    k_spread_gather<G, NP, NZ><<<blocks, kGatherThreads, 0, st>>>(offsets, cell, frac, cs, n_src, g, tb, r0, r1,
+                                                                   grid);
+    return cudaGetLastError();
+}
+
+int spread_gather_config(int elem_bytes, int n_pol, int nz, int w, int *nz_tmpl, int *bin_x, int *bin_y)
+{
+    if (w > kWmax) return 0;
+    const int NZ = nz <= 1 ? 1 : (nz <= 8 ? 8 : (nz <= 16 ? 16 : 0));
+    if (NZ == 0) return 0;
+    const int budget = elem_bytes == 4 ? 32 : 16;       // complex accumulators per lane
+    if (n_pol * NZ > budget) return 0;
+    if (elem_bytes == 8 && NZ == 16) return 0;           // shared staging would exceed 48 KB
+    *nz_tmpl = NZ;
+    *bin_x = kPatchX;
+    *bin_y = kPatchY;
+    return 1;
+}
+
+template <class G>
+cudaError_t launch_spread_tile(const int *offsets, const int *cell, const G *frac, const cpx<G> *cs, long n_src,
+                               const SliceGeom &g, const TimeBin &tb, double r0, double r1, cpx<G> *grid,
+                               cudaStream_t st)
+{
+    const int nz = g.d == 3 ? g.dim[2].nf1 : 1;
+    int NZ = 0, bx = 0, by = 0;
+    if (!spread_gather_config(sizeof(G), g.n_pol, nz, g.w, &NZ, &bx, &by)) return cudaErrorInvalidValue;
+    const int key = (g.n_pol == 4 ? 100 : 0) + NZ;
+    switch (key) {
+    case 1: return gather_launch<G, 1, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+    case 8: return gather_launch<G, 1, 8>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+    case 16:
+        if constexpr (sizeof(G) == 4) return gather_launch<G, 1, 16>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+        else return cudaErrorInvalidValue;
+    case 101: return gather_launch<G, 4, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+    case 108:
+        if constexpr (sizeof(G) == 4) return gather_launch<G, 4, 8>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+        else return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
     }
 }
 
@@ -444,51 +519,6 @@ template cudaError_t launch_spread_scatter<double>(const int *, const int *, con
 template cudaError_t launch_spread_scatter<float>(const int *, const int *, const float *, const cpx<float> *, long,
                                                   const SliceGeom &, const TimeBin &, double, double, cpx<float> *,
                                                   cudaStream_t);
-
-template <class G, int NP, int NZ>
-static cudaError_t gather_launch(const int *offsets, const int *cell, const G *frac, const cpx<G> *cs, long n_src,
-                                 const SliceGeom &g, const TimeBin &tb, double r0, double r1, cpx<G> *grid,
-                                 cudaStream_t st)
-{
-    dim3 blocks((g.dim[0].nf1 + kTileX - 1) / kTileX, (g.dim[1].nf1 + kTileY - 1) / kTileY);
-    k_spread_gather<G, NP, NZ><<<blocks, kGatherThreads, 0, st>>>(offsets, cell, frac, cs, n_src, g, tb, r0, r1,
-                                                                   grid);
-    return cudaGetLastError();
-}
-
-int spread_gather_config(int elem_bytes, int n_pol, int nz, int w, int *nz_tmpl, int *bin_x, int *bin_y)
-{
-    if (w > kWmax) return 0;
-    const int NZ = nz <= 1 ? 1 : (nz <= 8 ? 8 : (nz <= 16 ? 16 : 0));
-    if (NZ == 0) return 0;
-    const int budget = elem_bytes == 4 ? 32 : 16;       // complex accumulators per lane
-    if (n_pol * NZ > budget) return 0;
-    *nz_tmpl = NZ;
-    *bin_x = kPatchX;
-    *bin_y = kPatchY;
-    return 1;
-}
-
-template <class G>
-cudaError_t launch_spread_tile(const int *offsets, const int *cell, const G *frac, const cpx<G> *cs, long n_src,
-                               const SliceGeom &g, const TimeBin &tb, double r0, double r1, cpx<G> *grid,
-                               cudaStream_t st)
-{
-    const int nz = g.d == 3 ? g.dim[2].nf1 : 1;
-    int NZ = 0, bx = 0, by = 0;
-    if (!spread_gather_config(sizeof(G), g.n_pol, nz, g.w, &NZ, &bx, &by)) return cudaErrorInvalidValue;
-    const int key = (g.n_pol == 4 ? 100 : 0) + NZ;
-    switch (key) {
-    case 1: return gather_launch<G, 1, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
-    case 8: return gather_launch<G, 1, 8>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
-    case 16: return gather_launch<G, 1, 16>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
-    case 101: return gather_launch<G, 4, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
-    case 108:
-        if constexpr (sizeof(G) == 4) return gather_launch<G, 4, 8>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
-        else return cudaErrorInvalidValue;
-    default: return cudaErrorInvalidValue;
-    }
-}
 
 template cudaError_t launch_prep<double>(const double *, const int *, const int *, long, const void *, int, int, int,
                                          const SliceGeom &, int *, double *, cpx<double> *, cudaStream_t);

@@ -224,6 +224,9 @@ class Plan:
         o.dims = dims
         o.upsampfac = upsampfac
         o.kernel_width = kernel_width
+        if stream == 0:
+            raise ValueError("stream 0 (the legacy default stream) cannot be passed as a handle: "
+                             "pass a non-default stream, or None for a plan-owned stream")
         o.cuda_stream = None if stream is None else C.c_void_p(stream)
         o.device = device
         o.n_streams = n_streams
