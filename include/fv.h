@@ -189,6 +189,33 @@ typedef struct {
 fv_status fv_profile_enable(fv_plan_t p, int enable);
 fv_status fv_profile_read(fv_plan_t p, fv_profile_data *out);
 
+/* Batches: slices of many plans executed together (Section 5.3 runs (time,
+ * frequency) work in parallel processes; here independent slices share the
+ * GPU).  A batch owns n_lanes execution lanes (a stream and a workspace sized
+ * for its largest member); plans added to a batch need no workspace of their
+ * own.  Items are dealt to lanes longest first; the lanes fork from and join
+ * back to the batch's stream (cuda_stream, borrowed, or NULL for an owned one).
+ *  - fv_batch_add: slices t in [t_lo, t_hi), f in [f_lo, f_hi) of plan p,
+ *    written into vis, a device buffer of p's full fv_execute output shape.
+ *    p must stay alive, keep its array and sky, and be on the batch's device
+ *    until the batch is cleared or destroyed.
+ *  - fv_batch_execute: enqueues every item on the batch's stream and returns.
+ *    With use_graph != 0 the first execution after a change of the item list
+ *    runs once plainly, then captures the whole launch sequence into a CUDA
+ *    graph; later executions replay the graph.
+ *  - fv_batch_clear: removes all items (and the graph).
+ * Errors: FV_ERR_ARG (bad range, host output, device mismatch), FV_ERR_STATE,
+ * FV_ERR_OOM, FV_ERR_CUDA; fv_batch_last_error gives the message. */
+typedef struct fv_batch_s *fv_batch_t;
+fv_status fv_batch_create(int device, void *cuda_stream, int n_lanes, fv_batch_t *out);
+fv_status fv_batch_add(fv_batch_t b, fv_plan_t p, void *vis, int t_lo, int t_hi, int f_lo, int f_hi);
+fv_status fv_batch_execute(fv_batch_t b, int use_graph);
+fv_status fv_batch_clear(fv_batch_t b);
+fv_status fv_batch_destroy(fv_batch_t b);
+const char *fv_batch_last_error(fv_batch_t b);
+/* Device memory held by the batch's lane workspaces. */
+long long fv_batch_workspace_bytes(fv_batch_t b);
+
 /* fv_execute for callers that cannot allocate device memory.  The paper has
  * no counterpart; this exists for callers such as a host framework whose own
  * allocator already owns the free HBM (a foreign cudaMalloc would fail or

@@ -1,0 +1,259 @@
+// Batches: many slices of many plans in one execution (and one CUDA graph).
+//
+// A batch holds a list of items, each a run of slices of one plan (one time,
+// a channel range) with the plan's output buffer.  Execution lanes (a stream
+// and a workspace sized for the largest member) belong to the batch, not to
+// the plans, so thousands of small plans share a few workspaces.  Items are
+// dealt to lanes longest first; lanes fork from and join back to the batch's
+// stream.  With use_graph the whole launch sequence is captured once into a
+// CUDA graph and replayed by later executions until the item list changes.
+#include "fv_plan.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+struct fv_batch_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int n_lanes = 4;
+    std::vector<cudaStream_t> lanes;
+    std::vector<cudaEvent_t> ev_join;
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<fv_plan_s::Workspace> ws;
+    fv_plan_s::WsNeed ws_need;                 // what the lane workspaces were sized for
+    struct Item {
+        fv_plan_s *p;
+        char *vis;
+        long k0, k1;
+        double cost;
+    };
+    std::vector<Item> items;
+    bool graph_valid = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::string err;
+    fv_status fail(fv_status s, const std::string &m)
+    {
+        err = m;
+        return s;
+    }
+};
+
+#define CKB(call)                                                                                       \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return b->fail(e_ == cudaErrorMemoryAllocation ? FV_ERR_OOM : FV_ERR_CUDA,                  \
+                           std::string(#call " failed: ") + cudaGetErrorString(e_));                  \
+    } while (0)
+
+static void drop_graph(fv_batch_s *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_valid = false;
+}
+
+static bool covers(const fv_plan_s::WsNeed &have, const fv_plan_s::WsNeed &need)
+{
+    return have.grid >= need.grid && have.bufA >= need.bufA && have.bufB >= need.bufB && have.vu >= need.vu &&
+           (!need.tiled || (have.tiled && have.n_src >= need.n_src && have.nb >= need.nb &&
+                            have.frac_per_src >= need.frac_per_src && have.cs_per_src >= need.cs_per_src));
+}
+
+// Enqueue every item on its lane (fork/join around the batch stream).
+static fv_status enqueue(fv_batch_s *b)
+{
+    const int L = b->n_lanes;
+    std::vector<std::vector<int>> per(L);
+    std::vector<double> load(L, 0.0);
+    std::vector<int> order(b->items.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->items[a].cost > b->items[c].cost; });
+    for (int i : order) {
+        int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        per[l].push_back(i);
+        load[l] += b->items[i].cost;
+    }
+    CKB(cudaEventRecord(b->ev_fork, b->stream));
+    for (int l = 0; l < L; ++l) CKB(cudaStreamWaitEvent(b->lanes[l], b->ev_fork, 0));
+    for (int l = 0; l < L; ++l) {
+        for (int i : per[l]) {
+            const auto &it = b->items[i];
+            const size_t cb = it.p->precision == FV_FP64 ? 16 : 8;
+            const size_t slice_bytes = (size_t)it.p->n_bl * it.p->n_pol * cb;
+            fv_status st = it.p->precision == FV_FP64
+                               ? run_slices<double>(it.p, b->ws[l], b->lanes[l], it.vis, slice_bytes, it.k0, it.k1)
+                               : run_slices<float>(it.p, b->ws[l], b->lanes[l], it.vis, slice_bytes, it.k0, it.k1);
+            if (st != FV_OK) return b->fail(st, "slice execution failed: " + it.p->err);
+        }
+        CKB(cudaEventRecord(b->ev_join[l], b->lanes[l]));
+        CKB(cudaStreamWaitEvent(b->stream, b->ev_join[l], 0));
+    }
+    return FV_OK;
+}
+
+extern "C" {
+
+fv_status fv_batch_create(int device, void *cuda_stream, int n_lanes, fv_batch_t *out)
+{
+    if (!out) return FV_ERR_ARG;
+    *out = nullptr;
+    if (n_lanes < 0 || n_lanes > 32) return FV_ERR_ARG;
+    int dev = device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return FV_ERR_CUDA;
+    if (cudaSetDevice(dev) != cudaSuccess) return FV_ERR_CUDA;
+    fv_batch_s *b = new (std::nothrow) fv_batch_s();
+    if (!b) return FV_ERR_OOM;
+    b->device = dev;
+    b->n_lanes = n_lanes > 0 ? n_lanes : 4;
+    bool ok = true;
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess;
+        b->own_stream = ok;
+    }
+    ok = ok && cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    b->lanes.assign(b->n_lanes, nullptr);
+    b->ev_join.assign(b->n_lanes, nullptr);
+    for (int l = 0; l < b->n_lanes && ok; ++l)
+        ok = cudaStreamCreateWithFlags(&b->lanes[l], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->ev_join[l], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        fv_batch_destroy(b);
+        return FV_ERR_CUDA;
+    }
+    *out = b;
+    return FV_OK;
+}
+
+fv_status fv_batch_add(fv_batch_t b, fv_plan_t p, void *vis, int t_lo, int t_hi, int f_lo, int f_hi)
+{
+    if (!b) return FV_ERR_ARG;
+    if (!p || !vis) return b->fail(FV_ERR_ARG, "NULL plan or output");
+    if (p->device != b->device) return b->fail(FV_ERR_ARG, "plan and batch are on different devices");
+    if (!p->have_array || !p->have_sky) return b->fail(FV_ERR_STATE, "plan needs its array and sky first");
+    const int nt = (int)p->lst.size(), nf = (int)p->freq.size();
+    if (t_lo < 0 || t_hi > nt || t_lo >= t_hi || f_lo < 0 || f_hi > nf || f_lo >= f_hi)
+        return b->fail(FV_ERR_ARG, "slice range out of bounds");
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, vis) != cudaSuccess ||
+        (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        return b->fail(FV_ERR_ARG, "batch outputs must be device buffers");
+    }
+    if (!p->any_visible || p->n_src == 0) {
+        // nothing above the horizon: the caller's buffer is cleared once here
+        const size_t cb = p->precision == FV_FP64 ? 16 : 8;
+        const size_t slice_bytes = (size_t)p->n_bl * p->n_pol * cb;
+        if (cudaSetDevice(b->device) != cudaSuccess) return b->fail(FV_ERR_CUDA, "cudaSetDevice failed");
+        for (int f = f_lo; f < f_hi; ++f)
+            for (int t = t_lo; t < t_hi; ++t)
+                CKB(cudaMemsetAsync((char *)vis + ((size_t)f * nt + t) * slice_bytes, 0, slice_bytes, b->stream));
+        return FV_OK;
+    }
+    const double per_slice = (double)(p->need.grid + p->need.bufA + p->need.bufB) + 64.0 * p->n_src;
+    for (int t = t_lo; t < t_hi; ++t) {
+        fv_batch_s::Item it{p, (char *)vis, (long)t * nf + f_lo, (long)t * nf + f_hi, per_slice * (f_hi - f_lo)};
+        b->items.push_back(it);
+    }
+    b->graph_valid = false;
+    return FV_OK;
+}
+
+fv_status fv_batch_clear(fv_batch_t b)
+{
+    if (!b) return FV_ERR_ARG;
+    b->items.clear();
+    drop_graph(b);
+    return FV_OK;
+}
+
+fv_status fv_batch_execute(fv_batch_t b, int use_graph)
+{
+    if (!b) return FV_ERR_ARG;
+    if (cudaSetDevice(b->device) != cudaSuccess) return b->fail(FV_ERR_CUDA, "cudaSetDevice failed");
+    if (b->items.empty()) return FV_OK;
+    fv_plan_s::WsNeed need;
+    for (const auto &it : b->items) {
+        const auto &n = it.p->need;
+        need.grid = std::max(need.grid, n.grid);
+        need.bufA = std::max(need.bufA, n.bufA);
+        need.bufB = std::max(need.bufB, n.bufB);
+        need.vu = std::max(need.vu, n.vu);
+        if (n.tiled) {
+            need.tiled = true;
+            need.n_src = std::max(need.n_src, n.n_src);
+            need.nb = std::max(need.nb, n.nb);
+            need.frac_per_src = std::max(need.frac_per_src, n.frac_per_src);
+            need.cs_per_src = std::max(need.cs_per_src, n.cs_per_src);
+        }
+    }
+    if (b->ws.empty() || !covers(b->ws_need, need)) {
+        drop_graph(b);
+        CKB(cudaStreamSynchronize(b->stream));
+        for (auto &w : b->ws)
+            if (w.block) cudaFree(w.block);
+        b->ws.clear();
+        CKB(alloc_workspaces(need, b->n_lanes, b->ws));
+        b->ws_need = need;
+    }
+    if (!use_graph) return enqueue(b);
+    if (!b->graph_valid) {
+        drop_graph(b);
+        // one plain execution first, so that every kernel's one-time attributes are set outside capture
+        fv_status st = enqueue(b);
+        if (st != FV_OK) return st;
+        CKB(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        st = enqueue(b);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (st != FV_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return b->fail(FV_ERR_CUDA, std::string("capture failed: ") + cudaGetErrorString(e));
+        b->graph = g;
+        CKB(cudaGraphInstantiate(&b->exec, b->graph, 0));
+        b->graph_valid = true;
+    }
+    CKB(cudaGraphLaunch(b->exec, b->stream));
+    return FV_OK;
+}
+
+fv_status fv_batch_destroy(fv_batch_t b)
+{
+    if (!b) return FV_OK;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (auto st : b->lanes)
+        if (st) cudaStreamSynchronize(st);
+    drop_graph(b);
+    for (auto &w : b->ws)
+        if (w.block) cudaFree(w.block);
+    for (size_t l = 0; l < b->lanes.size(); ++l) {
+        if (b->lanes[l]) cudaStreamDestroy(b->lanes[l]);
+        if (b->ev_join[l]) cudaEventDestroy(b->ev_join[l]);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return FV_OK;
+}
+
+const char *fv_batch_last_error(fv_batch_t b) { return b ? b->err.c_str() : ""; }
+
+long long fv_batch_workspace_bytes(fv_batch_t b)
+{
+    if (!b) return 0;
+    long long s = 0;
+    for (auto &w : b->ws) s += (long long)w.bytes;
+    return s;
+}
+
+}  // extern "C"

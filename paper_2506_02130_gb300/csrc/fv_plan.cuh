@@ -60,6 +60,8 @@ struct fv_plan_s {
     void *d_pre = nullptr, *d_tw = nullptr;
     // one workspace per execution stream (slices on different streams run concurrently)
     struct Workspace {
+        void *block = nullptr;   // one allocation, carved into the pieces below
+        size_t bytes = 0;
         void *grid = nullptr, *bufA = nullptr, *bufB = nullptr;
         cpx<double> *Vu = nullptr;
         int *bin_of = nullptr, *counts = nullptr, *offsets = nullptr, *cursor = nullptr, *sidx = nullptr;
@@ -68,6 +70,14 @@ struct fv_plan_s {
         void *frac = nullptr, *cs = nullptr;
     };
     std::vector<Workspace> ws;
+    // what one execution workspace must hold for this plan (set by prepare)
+    struct WsNeed {
+        size_t grid = 0, bufA = 0, bufB = 0, vu = 0;   // bytes
+        long n_src = 0;
+        int nb = 0;
+        size_t frac_per_src = 0, cs_per_src = 0;       // bytes per source
+        bool tiled = false;
+    } need;
     int n_streams = 1;
     std::vector<cudaStream_t> sub;       // sub[0] is the plan's stream
     std::vector<cudaEvent_t> ev_join;
@@ -105,3 +115,12 @@ struct fv_plan_s {
     size_t elem() const { return precision == FV_FP64 ? sizeof(cpx<double>) : sizeof(cpx<float>); }
 };
 
+
+// Shared by the runtime's translation units.
+size_t workspace_layout(const fv_plan_s::WsNeed &need, char *base, fv_plan_s::Workspace *w);
+cudaError_t alloc_workspaces(const fv_plan_s::WsNeed &need, int n, std::vector<fv_plan_s::Workspace> &ws);
+// Slices [k_begin, k_end) (index t * n_freq + f) of plan p, on stream st with workspace wk,
+// written into vis (the plan's full output, slice_bytes per slice).
+template <class G>
+fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, char *vis, size_t slice_bytes,
+                     long k_begin, long k_end);

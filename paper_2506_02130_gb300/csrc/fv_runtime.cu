@@ -134,26 +134,63 @@ static cudaError_t prof_end(fv_plan_s *p, double bytes)
     return e;
 }
 
+// Carve one execution workspace for `need` out of `base` (nullptr: only size it).
+size_t workspace_layout(const fv_plan_s::WsNeed &need, char *base, fv_plan_s::Workspace *w)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void * {
+        off = (off + 255) & ~(size_t)255;
+        void *ptr = base ? base + off : nullptr;
+        off += bytes;
+        return ptr;
+    };
+    fv_plan_s::Workspace tmp;
+    fv_plan_s::Workspace &o = w ? *w : tmp;
+    o.grid = take(need.grid);
+    o.bufA = take(need.bufA);
+    o.bufB = take(need.bufB);
+    o.Vu = (cpx<double> *)take(need.vu);
+    if (need.tiled) {
+        const size_t ns = (size_t)need.n_src, nb = (size_t)need.nb;
+        o.bin_of = (int *)take(ns * sizeof(int));
+        o.counts = (int *)take(nb * sizeof(int));
+        o.offsets = (int *)take((nb + 1) * sizeof(int));
+        o.cursor = (int *)take(nb * sizeof(int));
+        o.sidx = (int *)take(ns * sizeof(int));
+        o.cell = (int *)take(3 * ns * sizeof(int));
+        o.sdir = (double *)take(3 * ns * sizeof(double));
+        o.frac = take(ns * need.frac_per_src);
+        o.cs = take(ns * need.cs_per_src);
+    }
+    return off;
+}
+
+// Allocate n workspaces for `need` (one cudaMalloc each).
+cudaError_t alloc_workspaces(const fv_plan_s::WsNeed &need, int n, std::vector<fv_plan_s::Workspace> &ws)
+{
+    const size_t bytes = workspace_layout(need, nullptr, nullptr);
+    ws.assign(n, fv_plan_s::Workspace{});
+    for (auto &w : ws) {
+        cudaError_t e = cudaMalloc(&w.block, std::max<size_t>(bytes, 256));
+        if (e != cudaSuccess) return e;
+        w.bytes = bytes;
+        workspace_layout(need, (char *)w.block, &w);
+    }
+    return cudaSuccess;
+}
+
+static void free_workspaces(std::vector<fv_plan_s::Workspace> &ws)
+{
+    for (auto &w : ws)
+        if (w.block) cudaFree(w.block);
+    ws.clear();
+}
+
 static void free_geometry(fv_plan_s *p)
 {
     dfree(p->d_pre);
     dfree(p->d_tw);
-    for (auto &w : p->ws) {
-        dfree(w.grid);
-        dfree(w.bufA);
-        dfree(w.bufB);
-        dfree_t(w.Vu);
-        dfree_t(w.bin_of);
-        dfree_t(w.counts);
-        dfree_t(w.offsets);
-        dfree_t(w.cursor);
-        dfree_t(w.sidx);
-        dfree_t(w.cell);
-        dfree_t(w.sdir);
-        dfree(w.frac);
-        dfree(w.cs);
-    }
-    p->ws.clear();
+    free_workspaces(p->ws);
 }
 
 // Top channel, spreading method and bin geometry (needs the per-channel geometry).
@@ -260,7 +297,7 @@ static fv_status prepare(fv_plan_s *p)
             sig.push_back(p->gf[f].dim[i].nf1);
             sig.push_back(p->gf[f].dim[i].M);
         }
-    const bool reuse = !p->ws.empty() && sig == p->geo_sig;
+    const bool reuse = p->d_pre != nullptr && sig == p->geo_sig;
     if (!reuse) free_geometry(p);
     p->geo_sig.clear();
     if (reuse) {
@@ -270,16 +307,10 @@ static fv_status prepare(fv_plan_s *p)
     }
     CK(cudaMalloc(&p->d_pre, std::max<size_t>(pre_total, 1) * gs));
     CK(cudaMalloc(&p->d_tw, std::max<size_t>(tw_total, 1) * es));
-    p->ws.assign(p->n_streams, fv_plan_s::Workspace{});
-    for (auto &wk : p->ws) {
-        CK(cudaMalloc(&wk.grid, std::max<size_t>(grid_e, 1) * es));
-        CK(cudaMalloc(&wk.bufA, std::max<size_t>(bufA_e, 1) * es));
-        CK(cudaMalloc(&wk.bufB, std::max<size_t>(bufB_e, 1) * es));
-        CK(cudaMalloc(&wk.Vu, std::max<size_t>((size_t)p->n_u * p->n_pol, 1) * sizeof(cpx<double>)));
-    }
-    p->grid_elems = grid_e;
-    p->bufA_elems = bufA_e;
-    p->bufB_elems = bufB_e;
+    p->need.grid = std::max<size_t>(grid_e, 1) * es;
+    p->need.bufA = std::max<size_t>(bufA_e, 1) * es;
+    p->need.bufB = std::max<size_t>(bufB_e, 1) * es;
+    p->need.vu = std::max<size_t>((size_t)p->n_u * p->n_pol, 1) * sizeof(cpx<double>);
     for (int f = 0; f < nf; ++f) {
         for (int i = 0; i < p->d; ++i) {
             const DimGeom &dg = p->gf[f].dim[i];
@@ -295,22 +326,14 @@ static fv_status prepare(fv_plan_s *p)
         }
     }
     resolve_spread(p, (int)gs, w);
-    size_t bin_bytes = 0;
-    if (p->tiled) {
-        const size_t ns = std::max<long>(p->n_src, 1), nb = (size_t)p->nbx * p->nby;
-        for (auto &wk : p->ws) {
-            CK(cudaMalloc(&wk.bin_of, ns * sizeof(int)));
-            CK(cudaMalloc(&wk.counts, nb * sizeof(int)));
-            CK(cudaMalloc(&wk.offsets, (nb + 1) * sizeof(int)));
-            CK(cudaMalloc(&wk.cursor, nb * sizeof(int)));
-            CK(cudaMalloc(&wk.sidx, ns * sizeof(int)));
-            CK(cudaMalloc(&wk.cell, 3 * ns * sizeof(int)));
-            CK(cudaMalloc(&wk.sdir, 3 * ns * sizeof(double)));
-            CK(cudaMalloc(&wk.frac, 3 * ns * gs));
-            CK(cudaMalloc(&wk.cs, (size_t)p->n_pol * ns * es));
-        }
-        bin_bytes = ns * (4 + 4 + 12 + 24 + 3 * gs + p->n_pol * es) + nb * 12;
-    }
+    p->need.tiled = p->tiled;
+    p->need.n_src = std::max<long>(p->n_src, 1);
+    p->need.nb = p->nbx * p->nby;
+    p->need.frac_per_src = 3 * gs;
+    p->need.cs_per_src = (size_t)p->n_pol * es;
+    const size_t bin_bytes = p->tiled ? workspace_layout(p->need, nullptr, nullptr) -
+                                            (p->need.grid + p->need.bufA + p->need.bufB + p->need.vu)
+                                      : 0;
     p->ws_bytes = (long long)(pre_total * gs + tw_total * es +
                               p->n_streams * ((grid_e + bufA_e + bufB_e) * es +
                                               (size_t)p->n_u * p->n_pol * sizeof(cpx<double>) + bin_bytes));
@@ -320,8 +343,8 @@ static fv_status prepare(fv_plan_s *p)
 }
 
 template <class G>
-static fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, char *vis, size_t slice_bytes,
-                            long k_begin, long k_end)
+fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, char *vis, size_t slice_bytes,
+                     long k_begin, long k_end)
 {
     const int nf = (int)p->freq.size(), nt = (int)p->lst.size();
     cpx<G> *grid = (cpx<G> *)wk.grid;
@@ -420,12 +443,20 @@ static fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t
     return FV_OK;
 }
 
+template fv_status run_slices<float>(fv_plan_s *, fv_plan_s::Workspace &, cudaStream_t, char *, size_t, long, long);
+template fv_status run_slices<double>(fv_plan_s *, fv_plan_s::Workspace &, cudaStream_t, char *, size_t, long, long);
+
 // All slices, t-major, split into contiguous chunks over the plan's streams
 // (each with its own workspace); the streams fork from and join back to the
 // plan's stream.
 template <class G>
 static fv_status execute_slices(fv_plan_s *p, char *vis, size_t slice_bytes)
 {
+    if ((int)p->ws.size() < p->n_streams) {
+        // execution workspaces are allocated on first use (a plan run only through a batch never needs them)
+        free_workspaces(p->ws);
+        CK(alloc_workspaces(p->need, p->n_streams, p->ws));
+    }
     const long total = (long)p->freq.size() * p->lst.size();
     const int S = (int)std::min<long>(p->n_streams, std::max<long>(total, 1));
     if (S > 1) {

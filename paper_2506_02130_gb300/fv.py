@@ -74,6 +74,13 @@ SIGNATURES = {
     "fv_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "fv_profile_read": (C.c_int, [C.c_void_p, C.POINTER(fv_profile_data)]),
     "fv_execute_static": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "fv_batch_create": (C.c_int, [C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    "fv_batch_add": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "fv_batch_execute": (C.c_int, [C.c_void_p, C.c_int]),
+    "fv_batch_clear": (C.c_int, [C.c_void_p]),
+    "fv_batch_destroy": (C.c_int, [C.c_void_p]),
+    "fv_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "fv_batch_workspace_bytes": (C.c_longlong, [C.c_void_p]),
 }
 
 _lib = None
@@ -189,6 +196,54 @@ def fv_profile_read(plan) -> dict:
         if name:
             out[name] = {"ms": d.total_ms[c], "launches": d.launches[c], "bytes": d.bytes[c]}
     return out
+
+
+def _check_batch(status, b):
+    if status != FV_OK:
+        msg = load_library().fv_batch_last_error(b)
+        raise FvError(status, msg.decode() if msg else "")
+
+
+class Batch:
+    """Slices of many plans executed together on shared lanes (fv_batch_*)."""
+
+    def __init__(self, device: int = -1, stream=None, n_lanes: int = 0):
+        if stream == 0:
+            raise ValueError("pass a non-default stream, or None for a batch-owned stream")
+        h = C.c_void_p()
+        _check_batch(load_library().fv_batch_create(device, None if stream is None else C.c_void_p(stream),
+                                                    n_lanes, C.byref(h)), None)
+        self.handle = h
+        self._keep = []
+
+    def add(self, plan: "Plan", vis, t_range=None, f_range=None):
+        t_lo, t_hi = t_range or (0, plan.n_time)
+        f_lo, f_hi = f_range or (0, plan.n_freq)
+        self._keep.append((plan, vis))
+        _check_batch(load_library().fv_batch_add(self.handle, plan.handle, _ptr(vis), t_lo, t_hi, f_lo, f_hi),
+                     self.handle)
+
+    def execute(self, use_graph: bool = False):
+        _check_batch(load_library().fv_batch_execute(self.handle, int(use_graph)), self.handle)
+
+    def clear(self):
+        _check_batch(load_library().fv_batch_clear(self.handle), self.handle)
+        self._keep = []
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(load_library().fv_batch_workspace_bytes(self.handle))
+
+    def close(self):
+        if self.handle:
+            load_library().fv_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------- convenience

@@ -266,7 +266,8 @@ class Sky:
 
 def diffuse_map(nside: int, freqs_hz: np.ndarray, rng: np.random.Generator,
                 brightness_jy_sr: float = 1.0e3, index: float = -2.5, index_sigma: float = 0.1,
-                polarized: bool = False, ref_hz: float = 150e6, lmax: int | None = None) -> Sky:
+                polarized: bool = False, ref_hz: float = 150e6, lmax: int | None = None,
+                dtype=np.float64) -> Sky:
     """Diffuse sky on HEALPix pixel centres as a point-source list.
 
     Brightness = B0 exp(0.5 g - 0.125) (log-normal of a unit GRF g), a
@@ -277,35 +278,35 @@ def diffuse_map(nside: int, freqs_hz: np.ndarray, rng: np.random.Generator,
     g = gaussian_random_field(nside, rng, lmax=lmax)
     bright = brightness_jy_sr * np.exp(0.5 * g - 0.125)
     alpha = rng.normal(index, index_sigma, len(ra))
-    spec = (np.asarray(freqs_hz)[None, :] / ref_hz) ** alpha[:, None]
-    stokes_i = (bright * healpix_pixel_area(nside))[:, None] * spec
+    spec = (np.asarray(freqs_hz, dtype=dtype)[None, :] / dtype(ref_hz)) ** alpha.astype(dtype)[:, None]
+    stokes_i = (bright * healpix_pixel_area(nside)).astype(dtype)[:, None] * spec
     if not polarized:
         return Sky(ra, dec, stokes_i[None], 0, len(ra))
     gq = gaussian_random_field(nside, rng, lmax=lmax)
     gu = gaussian_random_field(nside, rng, lmax=lmax)
-    flux = np.zeros((4,) + stokes_i.shape)
+    flux = np.zeros((4,) + stokes_i.shape, dtype=dtype)
     flux[0] = stokes_i
-    flux[1] = 0.1 * gq[:, None] * stokes_i
-    flux[2] = 0.1 * gu[:, None] * stokes_i
+    flux[1] = (0.1 * gq).astype(dtype)[:, None] * stokes_i
+    flux[2] = (0.1 * gu).astype(dtype)[:, None] * stokes_i
     return Sky(ra, dec, flux, 0, len(ra))
 
 
 def point_sky(n: int, freqs_hz: np.ndarray, rng: np.random.Generator, polarized: bool = False,
-              hemisphere: tuple[float, float] | None = None) -> Sky:
+              hemisphere: tuple[float, float] | None = None, dtype=np.float64) -> Sky:
     """Power-law point sources; uniform on the sphere unless ``hemisphere=(lst, lat)``."""
     if hemisphere is None:
         ra, dec = uniform_sphere(n, rng)
     else:
         ra, dec = visible_hemisphere(n, rng, *hemisphere)
-    stokes_i = powerlaw_fluxes(n, freqs_hz, rng)
+    stokes_i = powerlaw_fluxes(n, freqs_hz, rng).astype(dtype)
     if not polarized:
         return Sky(ra, dec, stokes_i[None], n, 0)
     frac = rng.uniform(0, 0.1, n)
     chi = rng.uniform(0, np.pi, n)
-    flux = np.zeros((4,) + stokes_i.shape)
+    flux = np.zeros((4,) + stokes_i.shape, dtype=dtype)
     flux[0] = stokes_i
-    flux[1] = (frac * np.cos(2 * chi))[:, None] * stokes_i
-    flux[2] = (frac * np.sin(2 * chi))[:, None] * stokes_i
+    flux[1] = (frac * np.cos(2 * chi)).astype(dtype)[:, None] * stokes_i
+    flux[2] = (frac * np.sin(2 * chi)).astype(dtype)[:, None] * stokes_i
     return Sky(ra, dec, flux, n, 0)
 
 
@@ -315,7 +316,7 @@ def concat_skies(*skies: Sky) -> Sky:
     for s in skies:
         f = s.flux
         if f.shape[0] < ns:
-            f = np.concatenate([f, np.zeros((ns - f.shape[0],) + f.shape[1:])], axis=0)
+            f = np.concatenate([f, np.zeros((ns - f.shape[0],) + f.shape[1:], dtype=f.dtype)], axis=0)
         parts.append(f)
     return Sky(np.concatenate([s.ra for s in skies]), np.concatenate([s.dec for s in skies]),
                np.concatenate(parts, axis=1), sum(s.n_point for s in skies),
@@ -383,7 +384,7 @@ def config_hex127(seed: int = 1, n_chan: int = 64, n_time: int = 10, n_point: in
 
 def config_hex350_pol(seed: int = 2, n_chan: int = 256, n_time: int = 4, n_point: int = 100000,
                       nside: int = 256, eps: float = 1e-6, n_keep: int = 350,
-                      radius: int = 11) -> Problem:
+                      radius: int = 11, dtype=np.float64) -> Problem:
     """350-antenna coplanar hexagon, polarised point + diffuse sky, 2x2 Jones
     Airy beam of a 14 m dish; defaults are the full workload."""
     rng = np.random.default_rng(seed)
@@ -392,9 +393,9 @@ def config_hex350_pol(seed: int = 2, n_chan: int = 256, n_time: int = 4, n_point
     lsts = lst_grid(n_time, 10.7, rng.uniform(0, 2 * np.pi))
     parts = []
     if n_point:
-        parts.append(point_sky(n_point, freqs, rng, polarized=True))
+        parts.append(point_sky(n_point, freqs, rng, polarized=True, dtype=dtype))
     if nside:
-        parts.append(diffuse_map(nside, freqs, rng, polarized=True))
+        parts.append(diffuse_map(nside, freqs, rng, polarized=True, dtype=dtype))
     sky = concat_skies(*parts)
     return Problem(f"hex{len(ant)}_pol_{n_chan}ch_{n_time}t", ant, cross_pairs(len(ant)), sky,
                    freqs, lsts, HERA_LATITUDE_RAD, "airy", (14.0,), True, eps)
