@@ -168,10 +168,11 @@ fv_status fv_get_info(fv_plan_t p, fv_info *info);
 
 /* Per-kernel timing for roofline reports (no counterpart in the paper; the
  * paper times whole stages with a line profiler, Section 5).  While enabled,
- * every device launch that fv_execute enqueues is bracketed by two CUDA events
- * on the plan's stream and counted; fv_profile_read synchronises the stream,
- * adds up the elapsed times per kernel class, copies them out and resets the
- * counters.  Classes: "memset", "bin" (per-time rotation, horizon cut and
+ * every device launch that fv_execute (or a plain fv_batch_execute) enqueues
+ * for the plan is bracketed by two CUDA events on the stream it runs on and
+ * counted; fv_profile_read waits for those events, adds up the elapsed times
+ * per kernel class, copies them out and resets the counters.  A batch with a
+ * plan whose timing is enabled is not captured into a graph (FV_ERR_STATE).  Classes: "memset", "bin" (per-time rotation, horizon cut and
  * sort), "prep" (per-slice strengths and grid coordinates), "spread",
  * "fft_x", "fft_y", "fft_z", "interp", "scatter" (FV_PROFILE_CLASSES
  * entries; unused ones have an empty name or stay zero).
@@ -199,16 +200,28 @@ fv_status fv_profile_read(fv_plan_t p, fv_profile_data *out);
  *    written into vis, a device buffer of p's full fv_execute output shape.
  *    p must stay alive, keep its array and sky, and be on the batch's device
  *    until the batch is cleared or destroyed.
+ *  - fv_batch_add_range: the same slices into a buffer laid out for a
+ *    window of channels from vis_f0 and vis_nt times from vis_t0: slice
+ *    (t, f) goes to slice index (f - vis_f0) * vis_nt + (t - vis_t0), each
+ *    slice n_bl * n_pol complex values.  The window must hold the range
+ *    (vis_f0 <= f_lo, vis_t0 <= t_lo, t_hi <= vis_t0 + vis_nt, vis_nt >= 1)
+ *    and vis must hold (f_hi - vis_f0) * vis_nt slices.  A request for part
+ *    of a resident plan's band and times thus needs no buffer for the rest,
+ *    and can be added in pieces (one time, a block of channels) that all
+ *    land in the one request buffer.
  *  - fv_batch_execute: enqueues every item on the batch's stream and returns.
  *    With use_graph != 0 the first execution after a change of the item list
  *    runs once plainly, then captures the whole launch sequence into a CUDA
- *    graph; later executions replay the graph.
+ *    graph; later executions replay the graph.  Graph execution needs kernel
+ *    timing (fv_profile_enable) off on every member plan.
  *  - fv_batch_clear: removes all items (and the graph).
  * Errors: FV_ERR_ARG (bad range, host output, device mismatch), FV_ERR_STATE,
  * FV_ERR_OOM, FV_ERR_CUDA; fv_batch_last_error gives the message. */
 typedef struct fv_batch_s *fv_batch_t;
 fv_status fv_batch_create(int device, void *cuda_stream, int n_lanes, fv_batch_t *out);
 fv_status fv_batch_add(fv_batch_t b, fv_plan_t p, void *vis, int t_lo, int t_hi, int f_lo, int f_hi);
+fv_status fv_batch_add_range(fv_batch_t b, fv_plan_t p, void *vis, int t_lo, int t_hi, int f_lo, int f_hi,
+                             int vis_f0, int vis_t0, int vis_nt);
 fv_status fv_batch_execute(fv_batch_t b, int use_graph);
 fv_status fv_batch_clear(fv_batch_t b);
 fv_status fv_batch_destroy(fv_batch_t b);

@@ -28,6 +28,7 @@ struct fv_batch_s {
         char *vis;
         long k0, k1;
         double cost;
+        OutMap om;
     };
     std::vector<Item> items;
     bool graph_valid = false;
@@ -87,8 +88,10 @@ static fv_status enqueue(fv_batch_s *b)
             const size_t cb = it.p->precision == FV_FP64 ? 16 : 8;
             const size_t slice_bytes = (size_t)it.p->n_bl * it.p->n_pol * cb;
             fv_status st = it.p->precision == FV_FP64
-                               ? run_slices<double>(it.p, b->ws[l], b->lanes[l], it.vis, slice_bytes, it.k0, it.k1)
-                               : run_slices<float>(it.p, b->ws[l], b->lanes[l], it.vis, slice_bytes, it.k0, it.k1);
+                               ? run_slices<double>(it.p, b->ws[l], b->lanes[l], it.vis, slice_bytes, it.k0, it.k1,
+                                                    it.om)
+                               : run_slices<float>(it.p, b->ws[l], b->lanes[l], it.vis, slice_bytes, it.k0, it.k1,
+                                                   it.om);
             if (st != FV_OK) return b->fail(st, "slice execution failed: " + it.p->err);
         }
         CKB(cudaEventRecord(b->ev_join[l], b->lanes[l]));
@@ -132,7 +135,9 @@ fv_status fv_batch_create(int device, void *cuda_stream, int n_lanes, fv_batch_t
     return FV_OK;
 }
 
-fv_status fv_batch_add(fv_batch_t b, fv_plan_t p, void *vis, int t_lo, int t_hi, int f_lo, int f_hi)
+// Items for slices [t_lo, t_hi) x [f_lo, f_hi) of p, slice (t, f) written at index
+// (f - om.f0) * om.nt + (t - om.t0) of vis (om.nt 0: the plan's n_time).
+static fv_status add_items(fv_batch_t b, fv_plan_t p, void *vis, int t_lo, int t_hi, int f_lo, int f_hi, OutMap om)
 {
     if (!b) return FV_ERR_ARG;
     if (!p || !vis) return b->fail(FV_ERR_ARG, "NULL plan or output");
@@ -147,6 +152,10 @@ fv_status fv_batch_add(fv_batch_t b, fv_plan_t p, void *vis, int t_lo, int t_hi,
         cudaGetLastError();
         return b->fail(FV_ERR_ARG, "batch outputs must be device buffers");
     }
+    if (om.nt < 0 || om.f0 < 0 || om.t0 < 0 || om.f0 > f_lo || om.t0 > t_lo ||
+        (om.nt > 0 && t_hi > om.t0 + om.nt))
+        return b->fail(FV_ERR_ARG, "output layout does not hold the slice range");
+    const int ntm = om.nt > 0 ? om.nt : nt;
     if (!p->any_visible || p->n_src == 0) {
         // nothing above the horizon: the caller's buffer is cleared once here
         const size_t cb = p->precision == FV_FP64 ? 16 : 8;
@@ -154,16 +163,29 @@ fv_status fv_batch_add(fv_batch_t b, fv_plan_t p, void *vis, int t_lo, int t_hi,
         if (cudaSetDevice(b->device) != cudaSuccess) return b->fail(FV_ERR_CUDA, "cudaSetDevice failed");
         for (int f = f_lo; f < f_hi; ++f)
             for (int t = t_lo; t < t_hi; ++t)
-                CKB(cudaMemsetAsync((char *)vis + ((size_t)f * nt + t) * slice_bytes, 0, slice_bytes, b->stream));
+                CKB(cudaMemsetAsync((char *)vis + ((size_t)(f - om.f0) * ntm + (t - om.t0)) * slice_bytes, 0,
+                                    slice_bytes, b->stream));
         return FV_OK;
     }
     const double per_slice = (double)(p->need.grid + p->need.bufA + p->need.bufB) + 64.0 * p->n_src;
     for (int t = t_lo; t < t_hi; ++t) {
-        fv_batch_s::Item it{p, (char *)vis, (long)t * nf + f_lo, (long)t * nf + f_hi, per_slice * (f_hi - f_lo)};
+        fv_batch_s::Item it{p, (char *)vis, (long)t * nf + f_lo, (long)t * nf + f_hi, per_slice * (f_hi - f_lo), om};
         b->items.push_back(it);
     }
     b->graph_valid = false;
     return FV_OK;
+}
+
+fv_status fv_batch_add(fv_batch_t b, fv_plan_t p, void *vis, int t_lo, int t_hi, int f_lo, int f_hi)
+{
+    return add_items(b, p, vis, t_lo, t_hi, f_lo, f_hi, OutMap{});
+}
+
+fv_status fv_batch_add_range(fv_batch_t b, fv_plan_t p, void *vis, int t_lo, int t_hi, int f_lo, int f_hi,
+                             int vis_f0, int vis_t0, int vis_nt)
+{
+    if (vis_nt < 1) return b ? b->fail(FV_ERR_ARG, "vis_nt must be >= 1") : FV_ERR_ARG;
+    return add_items(b, p, vis, t_lo, t_hi, f_lo, f_hi, OutMap{vis_f0, vis_t0, vis_nt});
 }
 
 fv_status fv_batch_clear(fv_batch_t b)
@@ -204,6 +226,8 @@ fv_status fv_batch_execute(fv_batch_t b, int use_graph)
         b->ws_need = need;
     }
     if (!use_graph) return enqueue(b);
+    for (const auto &it : b->items)
+        if (it.p->prof_on) return b->fail(FV_ERR_STATE, "kernel timing (fv_profile_enable) is not captured into graphs");
     if (!b->graph_valid) {
         drop_graph(b);
         // one plain execution first, so that every kernel's one-time attributes are set outside capture

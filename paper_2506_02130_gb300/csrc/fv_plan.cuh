@@ -82,7 +82,6 @@ struct fv_plan_s {
     std::vector<cudaStream_t> sub;       // sub[0] is the plan's stream
     std::vector<cudaEvent_t> ev_join;
     cudaEvent_t ev_fork = nullptr;
-    size_t grid_elems = 0, bufA_elems = 0, bufB_elems = 0;
     // binned spreading
     bool tiled = false;
     int spread_req = 0;         // fv_opts.spread_method
@@ -119,8 +118,13 @@ struct fv_plan_s {
 // Shared by the runtime's translation units.
 size_t workspace_layout(const fv_plan_s::WsNeed &need, char *base, fv_plan_s::Workspace *w);
 cudaError_t alloc_workspaces(const fv_plan_s::WsNeed &need, int n, std::vector<fv_plan_s::Workspace> &ws);
+// Where slice (t, f) lands in an output buffer: at slice index (f - f0) * nt + (t - t0).
+// The default {0, 0, 0} (nt 0 = the plan's n_time) is the plan's full [n_freq][n_time] layout.
+struct OutMap {
+    int f0 = 0, t0 = 0, nt = 0;
+};
 // Slices [k_begin, k_end) (index t * n_freq + f) of plan p, on stream st with workspace wk,
-// written into vis (the plan's full output, slice_bytes per slice).
+// written into vis (slice_bytes per slice, placed by om).
 template <class G>
 fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, char *vis, size_t slice_bytes,
-                     long k_begin, long k_end);
+                     long k_begin, long k_end, OutMap om = OutMap{});

@@ -90,16 +90,15 @@ static const char *k_prof_names[FV_PROFILE_CLASSES] = {"memset", "bin",   "prep"
                                                        "fft_z",  "interp", "scatter", "",      "",      ""};
 enum { PC_MEMSET = 0, PC_BIN, PC_PREP, PC_SPREAD, PC_FFT_X, PC_FFT_Y, PC_FFT_Z, PC_INTERP, PC_SCATTER };
 
-// harvest finished event pairs into the per-class totals (synchronises the stream)
+// harvest recorded event pairs into the per-class totals (waits for each pair's end event, so it
+// holds whatever stream the launches ran on: the plan's own or a batch lane)
 static cudaError_t prof_harvest(fv_plan_s *p)
 {
     if (p->ev_pending.empty()) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-    for (cudaStream_t st : p->sub) {
-        e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return e;
-    }
     for (auto &pr : p->ev_pending) {
+        e = cudaEventSynchronize(p->ev_pool[pr.second + 1]);
+        if (e != cudaSuccess) return e;
         float ms = 0.f;
         e = cudaEventElapsedTime(&ms, p->ev_pool[pr.second], p->ev_pool[pr.second + 1]);
         if (e != cudaSuccess) return e;
@@ -118,8 +117,18 @@ static cudaError_t prof_begin(fv_plan_s *p, int cls, cudaStream_t st)
     p->prof_stream = st;
     if (!p->prof_on) return cudaSuccess;
     if (p->ev_next + 2 > p->ev_pool.size()) {
-        cudaError_t e = prof_harvest(p);
-        if (e != cudaSuccess) return e;
+        // grow the pool in steps up to 8192 events, then recycle it after a harvest
+        const size_t n0 = p->ev_pool.size();
+        if (n0 < 8192) {
+            p->ev_pool.resize(std::min<size_t>(8192, n0 + 256), nullptr);
+            for (size_t i = n0; i < p->ev_pool.size(); ++i) {
+                cudaError_t e = cudaEventCreate(&p->ev_pool[i]);
+                if (e != cudaSuccess) return e;
+            }
+        } else {
+            cudaError_t e = prof_harvest(p);
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaEventRecord(p->ev_pool[p->ev_next], st);
 }
@@ -344,7 +353,7 @@ static fv_status prepare(fv_plan_s *p)
 
 template <class G>
 fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, char *vis, size_t slice_bytes,
-                     long k_begin, long k_end)
+                     long k_begin, long k_end, OutMap om)
 {
     const int nf = (int)p->freq.size(), nt = (int)p->lst.size();
     cpx<G> *grid = (cpx<G> *)wk.grid;
@@ -435,7 +444,8 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
             CK(launch_interp<G>(A, p->d_bu, p->n_u, p->d_dec, g, wk.Vu, st));
             CK(prof_end(p, (double)p->n_u * (wd * p->n_pol * es + 4 * sizeof(double) + p->n_pol * 16.0)));
         }
-        char *out = vis + ((size_t)f * nt + t) * slice_bytes;
+        const int ntm = om.nt > 0 ? om.nt : nt;
+        char *out = vis + ((size_t)(f - om.f0) * ntm + (t - om.t0)) * slice_bytes;
         CK(prof_begin(p, PC_SCATTER, st));
         CK(launch_scatter(wk.Vu, p->d_bl2u, p->n_bl, p->n_pol, out, p->precision == FV_FP64, st));
         CK(prof_end(p, (double)p->n_bl * (4 + p->n_pol * 16.0) + (double)slice_bytes));
@@ -443,8 +453,10 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
     return FV_OK;
 }
 
-template fv_status run_slices<float>(fv_plan_s *, fv_plan_s::Workspace &, cudaStream_t, char *, size_t, long, long);
-template fv_status run_slices<double>(fv_plan_s *, fv_plan_s::Workspace &, cudaStream_t, char *, size_t, long, long);
+template fv_status run_slices<float>(fv_plan_s *, fv_plan_s::Workspace &, cudaStream_t, char *, size_t, long, long,
+                                     OutMap);
+template fv_status run_slices<double>(fv_plan_s *, fv_plan_s::Workspace &, cudaStream_t, char *, size_t, long, long,
+                                      OutMap);
 
 // All slices, t-major, split into contiguous chunks over the plan's streams
 // (each with its own workspace); the streams fork from and join back to the
@@ -530,8 +542,18 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
         if (std::fabs(sigma - 2.0) < 1e-12)
             w = (int)std::ceil(std::log10(1.0 / o->eps) - 1e-12) + 1;   // Section 2.2 rule at sigma = 2
         else
-            w = (int)std::ceil(std::log(1.0 / o->eps) / (M_PI * std::sqrt(1.0 - 1.0 / sigma)) - 1e-12) + 1;
-        w = std::max(2, std::min(16, w));
+            // the estimate eps ~ exp(-pi w sqrt(1 - 1/sigma)) of the kernel's aliasing error, plus two
+            // points: the type-3 transform applies the kernel twice and divides by its transform twice, and
+            // at sigma = 1.25, eps = 1e-10 one extra point still left a relative L2 error of 1.04e-9 against
+            // the direct sum
+            w = (int)std::ceil(std::log(1.0 / o->eps) / (M_PI * std::sqrt(1.0 - 1.0 / sigma)) - 1e-12) + 2;
+        w = std::max(2, w);
+        if (w > 16) {
+            // a narrower kernel would miss eps: refuse rather than return a less accurate result
+            g_create_error = "eps " + std::to_string(o->eps) + " at upsampfac " + std::to_string(sigma) +
+                             " needs a kernel width of " + std::to_string(w) + " (at most 16)";
+            return FV_ERR_UNSUPPORTED;
+        }
     }
     if (w < 2 || w > 16) return bad("kernel_width must be in [2, 16]");
 
@@ -855,10 +877,6 @@ fv_status fv_profile_enable(fv_plan_t p, int enable)
 {
     if (!p) return FV_ERR_ARG;
     if (cudaSetDevice(p->device) != cudaSuccess) return p->fail(FV_ERR_CUDA, "cudaSetDevice failed");
-    if (enable && p->ev_pool.empty()) {
-        p->ev_pool.resize(8192);
-        for (auto &ev : p->ev_pool) CK(cudaEventCreate(&ev));
-    }
     if (!enable) CK(prof_harvest(p));
     p->prof_on = enable != 0;
     return FV_OK;

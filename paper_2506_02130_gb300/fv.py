@@ -76,6 +76,8 @@ SIGNATURES = {
     "fv_execute_static": (C.c_int, [C.c_void_p, C.c_void_p]),
     "fv_batch_create": (C.c_int, [C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     "fv_batch_add": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "fv_batch_add_range": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                     C.c_int, C.c_int, C.c_int]),
     "fv_batch_execute": (C.c_int, [C.c_void_p, C.c_int]),
     "fv_batch_clear": (C.c_int, [C.c_void_p]),
     "fv_batch_destroy": (C.c_int, [C.c_void_p]),
@@ -216,12 +218,20 @@ class Batch:
         self.handle = h
         self._keep = []
 
-    def add(self, plan: "Plan", vis, t_range=None, f_range=None):
+    def add(self, plan: "Plan", vis, t_range=None, f_range=None, window=None):
+        """Slices t_range x f_range of plan into vis.  vis has the plan's full
+        output shape, or with window = (f0, t0, nt) holds the channels from f0
+        and nt times from t0: slice (t, f) at index (f - f0) * nt + (t - t0)."""
         t_lo, t_hi = t_range or (0, plan.n_time)
         f_lo, f_hi = f_range or (0, plan.n_freq)
         self._keep.append((plan, vis))
-        _check_batch(load_library().fv_batch_add(self.handle, plan.handle, _ptr(vis), t_lo, t_hi, f_lo, f_hi),
-                     self.handle)
+        lib = load_library()
+        if window is None:
+            st = lib.fv_batch_add(self.handle, plan.handle, _ptr(vis), t_lo, t_hi, f_lo, f_hi)
+        else:
+            f0, t0, nt = window
+            st = lib.fv_batch_add_range(self.handle, plan.handle, _ptr(vis), t_lo, t_hi, f_lo, f_hi, f0, t0, nt)
+        _check_batch(st, self.handle)
 
     def execute(self, use_graph: bool = False):
         _check_batch(load_library().fv_batch_execute(self.handle, int(use_graph)), self.handle)

@@ -399,3 +399,112 @@ def config_hex350_pol(seed: int = 2, n_chan: int = 256, n_time: int = 4, n_point
     sky = concat_skies(*parts)
     return Problem(f"hex{len(ant)}_pol_{n_chan}ch_{n_time}t", ant, cross_pairs(len(ant)), sky,
                    freqs, lsts, HERA_LATITUDE_RAD, "airy", (14.0,), True, eps)
+
+
+@dataclass
+class BatchSlice:
+    """One independent single-slice problem of the batched workload.
+
+    ``problem.eps`` is the slice's drawn tolerance; ``nufft_eps`` is the
+    tolerance given to the transform: a tenth of it on the FP64 path, whose
+    gate is a relative L2 error of 1e-9 against the direct sum (the kernel
+    tolerance bounds the error relative to the summed source strengths, which
+    is a few times looser in relative L2), and the tolerance itself on the
+    mixed path, where FP32 rounding sets the floor."""
+    problem: Problem
+    precision: str          # "mixed" (eps >= 1e-6) or "fp64"
+    nufft_eps: float = 0.0
+
+
+def config_batch(seed: int = 4, n_slices: int = 2048, radii=(3, 4, 5, 6, 7, 8, 9, 10),
+                 n_src_range=(1000, 500000), eps_choices=(1e-6, 1e-9)) -> list:
+    """Ragged single-slice problems: hexagons of 37-331 antennas, skies of
+    1e3-5e5 sources (log-uniform), eps from {1e-6, 1e-9}, frequency and time
+    from the 127-antenna workload's ranges (100-200 MHz, 10 integrations at
+    10.7 s), Gaussian beam.  Skies are prefixes of one seeded uniform-sphere
+    catalogue; slices with eps < 1e-6 take the FP64 path, the others the mixed
+    path."""
+    rng = np.random.default_rng(seed)
+    n_max = int(n_src_range[1])
+    cat_ra, cat_dec = uniform_sphere(n_max, rng)
+    s0 = np.exp(rng.uniform(np.log(0.1), np.log(10.0), n_max))
+    alpha = rng.normal(-0.8, 0.2, n_max)
+    arrays = {r: hex_array(r) for r in radii}
+    pairs = {r: cross_pairs(len(a)) for r, a in arrays.items()}
+    lst0 = rng.uniform(0, 2 * np.pi)
+    lsts = lst_grid(10, 10.7, lst0)
+    out = []
+    for k in range(n_slices):
+        r = int(rng.choice(radii))
+        n_src = int(np.exp(rng.uniform(np.log(n_src_range[0]), np.log(n_src_range[1]))))
+        eps = float(rng.choice(eps_choices))
+        nu = float(rng.uniform(100e6, 200e6))
+        lst = float(rng.choice(lsts))
+        flux = (s0[:n_src] * (nu / 150e6) ** alpha[:n_src])[None, :, None]
+        sky = Sky(cat_ra[:n_src], cat_dec[:n_src], flux, n_src, 0)
+        prob = Problem(f"batch{k}_hex{len(arrays[r])}_{n_src}src", arrays[r], pairs[r], sky, np.array([nu]),
+                       np.array([lst]), HERA_LATITUDE_RAD, "gauss", GAUSS_FWHM_150, False, eps)
+        mixed = eps >= 1e-6
+        out.append(BatchSlice(prob, "mixed" if mixed else "fp64", eps if mixed else 0.1 * eps))
+    return out
+
+
+SERVE_KINDS = ("hex37", "hex127", "hex350")
+
+
+def serve_plans(seed: int = 5, n_chan: int = 256, n_time: int = 20, scale: float = 1.0,
+                kinds=SERVE_KINDS) -> dict:
+    """The resident problems the served requests draw windows from: each array
+    with its sky, over n_chan channels at 100-200 MHz and n_time integrations
+    at 10.7 s.  hex37: coplanar 37-antenna hexagon, 1,000 point sources;
+    hex127: the 127-antenna jittered hexagon with 20,000 points + an nside-64
+    map; hex350: the 350-antenna polarised sky (100,000 points + an nside-256
+    map, FP32 fluxes) with Airy Jones beams.  ``scale`` < 1 shrinks the skies
+    (source counts and nside) for quick tests."""
+    out = {}
+    if "hex37" in kinds:
+        rng = np.random.default_rng(seed)
+        ant = hex_array(3)
+        freqs = channel_centres(n_chan)
+        lsts = lst_grid(n_time, 10.7, rng.uniform(0, 2 * np.pi))
+        sky = point_sky(max(10, int(1000 * scale)), freqs, rng)
+        out["hex37"] = Problem(f"hex37_{n_chan}ch_{n_time}t", ant, cross_pairs(len(ant)), sky, freqs, lsts,
+                               HERA_LATITUDE_RAD, "gauss", GAUSS_FWHM_150, False, 1e-6)
+    if "hex127" in kinds:
+        ns = 64 if scale >= 1 else max(2, int(64 * scale))
+        out["hex127"] = config_hex127(seed=seed + 1, n_chan=n_chan, n_time=n_time,
+                                      n_point=max(10, int(20000 * scale)), nside=ns, eps=1e-6)
+    if "hex350" in kinds:
+        ns = 256 if scale >= 1 else max(2, int(256 * scale))
+        out["hex350"] = config_hex350_pol(seed=seed + 2, n_chan=n_chan, n_time=n_time,
+                                          n_point=max(10, int(100000 * scale)), nside=ns, eps=1e-6,
+                                          dtype=np.float32)
+    return out
+
+
+@dataclass
+class ServeRequest:
+    rid: int
+    arrival_s: float
+    kind: str
+    f_range: tuple
+    t_range: tuple
+
+
+def serve_requests(seed: int = 5, n_requests: int = 10000, rate_hz: float = 200.0, n_chan: int = 256,
+                   n_time: int = 20, kinds=SERVE_KINDS) -> list:
+    """A Poisson stream of requests (exponential inter-arrival times, mean
+    1/rate_hz): each names one resident problem (uniformly), a block of
+    channels whose count is log-uniform in [1, n_chan] at a uniform offset,
+    and a block of 1..n_time integrations (uniform) at a uniform offset."""
+    rng = np.random.default_rng(seed + 100)
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, n_requests))
+    out = []
+    for i in range(n_requests):
+        kind = kinds[int(rng.integers(len(kinds)))]
+        nf = int(min(n_chan, max(1, round(math.exp(rng.uniform(0.0, math.log(n_chan)))))))
+        f0 = int(rng.integers(0, n_chan - nf + 1))
+        nt = int(rng.integers(1, n_time + 1))
+        t0 = int(rng.integers(0, n_time - nt + 1))
+        out.append(ServeRequest(i, float(t[i]), kind, (f0, f0 + nf), (t0, t0 + nt)))
+    return out

@@ -82,3 +82,20 @@ def test_no_device_is_an_error_not_a_fallback(lib):
     assert lib.fv_plan(C.byref(o), C.byref(h)) == fv.FV_ERR_CUDA
     with pytest.raises(fv.FvError):
         fv.Plan.create([150e6], [0.0], 0.0)
+
+
+@pytest.mark.parametrize("eps,sigma,ok", [(1e-10, 1.25, False), (1e-8, 1.25, True), (1e-14, 2.0, True),
+                                          (1e-12, 1.5, False)])
+def test_unreachable_tolerance_is_refused_not_clamped(lib, eps, sigma, ok):
+    """A tolerance that needs a kernel wider than 16 points at the given
+    upsampling factor is refused (FV_ERR_UNSUPPORTED) before any device work."""
+    o, keep = _opts(eps=eps, upsampfac=sigma)
+    h = C.c_void_p()
+    st = lib.fv_plan(C.byref(o), C.byref(h))
+    if ok:
+        assert st != fv.FV_ERR_UNSUPPORTED and st != fv.FV_ERR_ARG   # FV_ERR_CUDA here (no device) or FV_OK
+        if h.value:
+            lib.fv_destroy(h)
+    else:
+        assert st == fv.FV_ERR_UNSUPPORTED
+        assert b"kernel width" in lib.fv_last_error(None)

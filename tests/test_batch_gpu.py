@@ -77,3 +77,33 @@ def test_batch_partial_ranges_and_errors():
     assert ei.value.status == fv.FV_ERR_ARG
     b.close()
     p.close()
+
+
+def test_batch_window_pieces_land_in_one_request_buffer():
+    """fv_batch_add_range: pieces (one time, a block of channels) of a window
+    of channels and times all land in one buffer shaped for the window."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    prob = W.config_hex127(seed=36, n_chan=5, n_time=4, n_point=300, nside=0, radius=2)
+    p = fv.Plan.from_problem(prob, precision=fv.FV_FP64, eps=1e-10)
+    p.set_sky(prob.sky.ra, prob.sky.dec, prob.sky.flux)
+    full = p.run()
+    f0, f1, t0, t1 = 1, 5, 1, 3
+    win = torch.full((f1 - f0, t1 - t0, p.n_bl, p.n_pol), float("nan"), dtype=torch.complex128, device=dev)
+    b = fv.Batch(n_lanes=3)
+    b.add(p, win, t_range=(1, 2), f_range=(1, 3), window=(f0, t0, t1 - t0))
+    b.add(p, win, t_range=(1, 2), f_range=(3, 5), window=(f0, t0, t1 - t0))
+    b.add(p, win, t_range=(2, 3), f_range=(1, 5), window=(f0, t0, t1 - t0))
+    b.execute(use_graph=True)
+    torch.cuda.synchronize()
+    got = win.cpu().numpy()
+    assert np.isfinite(got).all()
+    assert rel_l2(got, full[f0:f1, t0:t1]) <= 1e-12
+    for bad in [dict(t_range=(0, 2), f_range=(1, 2)),      # t_lo before the window
+                dict(t_range=(1, 4), f_range=(1, 2)),      # t_hi past the window
+                dict(t_range=(1, 2), f_range=(0, 2))]:     # f_lo before the window
+        with pytest.raises(fv.FvError) as ei:
+            b.add(p, win, window=(f0, t0, t1 - t0), **bad)
+        assert ei.value.status == fv.FV_ERR_ARG
+    b.close()
+    p.close()

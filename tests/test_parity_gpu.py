@@ -74,12 +74,13 @@ def test_polarised_airy_jones(precision):
         assert rel_l2(out[..., p], ref[..., p]) <= TOL[precision] * 2, p
 
 
-@pytest.mark.parametrize("precision,sigma", [(fv.FV_FP64, 1.25), (fv.FV_FP64, 2.0), (fv.FV_MIXED, 1.5),
-                                             (fv.FV_MIXED, 2.0)])
-def test_upsampling_factor(precision, sigma):
+@pytest.mark.parametrize("precision,sigma,eps,tol", [(fv.FV_FP64, 1.25, 1e-8, 1e-7), (fv.FV_FP64, 2.0, None, None),
+                                                     (fv.FV_MIXED, 1.5, None, None), (fv.FV_MIXED, 2.0, None, None)])
+def test_upsampling_factor(precision, sigma, eps, tol):
+    """sigma 1.25 reaches eps >= 3e-9 with its widest (16-point) kernel; it is checked at 1e-8 within 10 eps."""
     prob = small_3d(seed=9, n_chan=2, n_time=1)
-    out, _ = run_gpu(prob, precision, upsampfac=sigma)
-    assert rel_l2(out, oracle(prob)) <= TOL[precision]
+    out, _ = run_gpu(prob, precision, eps=eps, upsampfac=sigma)
+    assert rel_l2(out, oracle(prob)) <= (tol or TOL[precision])
 
 
 def _edge_amplification(w, beta):
