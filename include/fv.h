@@ -190,7 +190,7 @@ typedef struct {
 fv_status fv_profile_enable(fv_plan_t p, int enable);
 fv_status fv_profile_read(fv_plan_t p, fv_profile_data *out);
 
-/* Batches: slices of many plans executed together (Section 5.3 runs (time,
+/* Batches: slices of many plans executed together (Section 5.4 runs (time,
  * frequency) work in parallel processes; here independent slices share the
  * GPU).  A batch owns n_lanes execution lanes (a stream and a workspace sized
  * for its largest member); plans added to a batch need no workspace of their

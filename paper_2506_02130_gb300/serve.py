@@ -1,7 +1,7 @@
 """Serving: a request loop with continuous batching over resident plans.
 
 The paper runs a simulation's (time, frequency) work as independent pieces
-in parallel processes that share the read-only sky and beam (Section 5.3).
+in parallel processes that share the read-only sky and beam (Section 5.4).
 A GPU server does the same across requests: each request names a resident
 plan (an array and a sky, with the plan's band of channels and grid of
 times) and a window of channels and times.  The server

@@ -3,7 +3,7 @@
 Slices share nothing but the read-only array and sky, so N GPUs each take a
 disjoint block of channels and simulate it with their own plan; no collective
 touches the data path.  This is the paper's own multi-node scheme (frequency
-blocks as independent jobs, Section 5.3) with one process per GPU.  The only
+blocks as independent jobs, Section 5.4) with one process per GPU.  The only
 communication is on the host: the ranks' wall-clock maximum for timing and an
 optional gather of the visibility blocks.
 """

@@ -256,3 +256,19 @@ def test_golden_fixture_reproduces():
     np.testing.assert_array_equal(rows[:, :2].astype(int), pairs)
     v = oracle_vis(OracleProblem.from_workload(prob, pairs=pairs), "literal")[0, 0, :, 0]
     np.testing.assert_allclose(v, rows[:, 2] + 1j * rows[:, 3], rtol=1e-12, atol=1e-13)
+
+
+# ---------------------------------------------------------------- DFT special case
+@pytest.mark.parametrize("N,G,lst", [(16, 5, 0.7), (12, 4, 3.9)])
+def test_lattice_sky_reduces_to_numpy_fft2(N, G, lst):
+    """Sources on a direction-cosine lattice seen by a grid array: the sum is a
+    2-D DFT, evaluated by numpy's FFT (tests/_lattice.py)."""
+    from tests._lattice import lattice_case
+    L = lattice_case(N=N, G=G, lst=lst)
+    enu = np.array([oracle_enu(r, d, lst, L["lat"]) for r, d in zip(L["ra"], L["dec"])])
+    np.testing.assert_allclose(enu, L["lmn"], atol=1e-14)
+    op = OracleProblem(L["ant"], L["pairs"], L["ra"], L["dec"], L["flux"], L["freqs"], L["lsts"], L["lat"],
+                       "uniform", (), False)
+    for mode in ("literal", "factored"):
+        v = oracle_vis(op, mode)[0, 0, :, 0]
+        assert rel_l2(v, L["expected"]) <= 1e-13

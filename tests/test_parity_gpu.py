@@ -204,3 +204,17 @@ def test_fft_radix_cap_and_streams(max_radix, n_streams):
     for precision in (fv.FV_FP64, fv.FV_MIXED):
         out, _ = run_gpu(prob, precision, fft_max_radix=max_radix, n_streams=n_streams)
         assert rel_l2(out, ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", [fv.FV_FP64, fv.FV_MIXED])
+def test_lattice_sky_equals_numpy_fft2(precision):
+    """A lattice sky seen by a grid array: the visibilities are a 2-D DFT of the
+    fluxes (tests/_lattice.py), computed by numpy's FFT, not by the oracle."""
+    from tests._lattice import lattice_case
+    L = lattice_case(N=16, G=5)
+    p = fv.Plan.create(L["freqs"], L["lsts"], L["lat"], "uniform", (), precision, EPS[precision], False)
+    p.set_array(L["ant"], L["pairs"])
+    p.set_sky(L["ra"], L["dec"], L["flux"])
+    out = p.run()[0, 0, :, 0]
+    p.close()
+    assert rel_l2(out, L["expected"]) <= TOL[precision]
