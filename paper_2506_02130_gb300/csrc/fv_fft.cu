@@ -209,54 +209,95 @@ __device__ __forceinline__ unsigned fdiv(unsigned n, unsigned mul, unsigned sh)
 }
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
 
+// Where a stage's input and output live.  The first stage reads the
+// zero-padded row without the padding ever being stored: positions in
+// [zlo, zhi) are zeros.  The last stage (Ns = M / RD, so j = k and its
+// outputs are the frequencies m = k + q Ns) writes only the band, straight to
+// global memory, transposed: out[b][row] with b = m + H (mod M), every b < B.
+template <class G> struct StageIO {
+    int zlo, zhi;                 // first stage: zero positions of the input row
+    cpx<G> *out;                  // last stage: band output (nullptr: write y)
+    long rows, row0;
+    int nr, B, H;
+    float inv_nrows;
+};
+
 template <class G, int RD>
 __device__ __forceinline__ void stage(const cpx<G> *__restrict__ x, cpx<G> *__restrict__ y, const DimGeom &dg,
-                                      int s, int nrows, int Ns, const cpx<G> *__restrict__ tw)
+                                      int s, int nrows, int Ns, const cpx<G> *__restrict__ tw, bool first,
+                                      StageIO<G> io)
 {
     const int M = dg.M;
     const int MR = M / RD;
     const int per = nrows * MR;
     const int twstep = M / (Ns * RD);
+    const bool last = io.out != nullptr;
     for (int bi = threadIdx.x; bi < per; bi += kThreads) {
-        const int row = (int)fdiv((unsigned)bi, dg.mr_mul[s], dg.mr_sh[s]);
-        const int j = bi - row * MR;
-        const int jq = (int)fdiv((unsigned)j, dg.ns_mul[s], dg.ns_sh[s]);
+        int row, j;
+        if (last) {
+            // row fastest, so that consecutive threads write consecutive rows of one band index
+            j = (int)(((float)bi + 0.5f) * io.inv_nrows);
+            row = bi - j * nrows;
+        } else {
+            row = (int)fdiv((unsigned)bi, dg.mr_mul[s], dg.mr_sh[s]);
+            j = bi - row * MR;
+        }
+        const int jq = last ? 0 : (int)fdiv((unsigned)j, dg.ns_mul[s], dg.ns_sh[s]);
         const int k = j - jq * Ns;
         const int base = row * M;
         cpx<G> v[RD];
+        if (first) {
 #pragma unroll
-        for (int q = 0; q < RD; ++q) v[q] = x[pad(base + j + q * MR)];
+            for (int q = 0; q < RD; ++q) {
+                const int pos = j + q * MR;
+                v[q] = (pos >= io.zlo && pos < io.zhi) ? cmk<G>((G)0, (G)0) : x[pad(base + pos)];
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < RD; ++q) v[q] = x[pad(base + j + q * MR)];
+        }
         if (Ns > 1) {
 #pragma unroll
             for (int q = 1; q < RD; ++q) v[q] = cmul(v[q], tw[q * k * twstep]);
         }
         Dft<G, RD>::run(v);
-        const int o = base + jq * Ns * RD + k;
+        if (last) {
+            if (row < io.nr) {
 #pragma unroll
-        for (int q = 0; q < RD; ++q) y[pad(o + q * Ns)] = v[q];
+                for (int q = 0; q < RD; ++q) {
+                    int b = k + q * Ns + io.H;
+                    while (b >= M) b -= M;
+                    for (; b < io.B; b += M) io.out[(size_t)b * io.rows + io.row0 + row] = v[q];
+                }
+            }
+        } else {
+            const int o = base + jq * Ns * RD + k;
+#pragma unroll
+            for (int q = 0; q < RD; ++q) y[pad(o + q * Ns)] = v[q];
+        }
     }
     __syncthreads();
 }
 
 template <class G, int MAXRD>
 __device__ __forceinline__ void run_stage(int rd, const cpx<G> *x, cpx<G> *y, const DimGeom &dg, int s, int nrows,
-                                          int Ns, const cpx<G> *tw)
+                                          int Ns, const cpx<G> *tw, bool first, StageIO<G> io)
 {
     switch (rd) {
-    case 2: stage<G, 2>(x, y, dg, s, nrows, Ns, tw); break;
-    case 3: stage<G, 3>(x, y, dg, s, nrows, Ns, tw); break;
-    case 4: stage<G, 4>(x, y, dg, s, nrows, Ns, tw); break;
-    case 5: stage<G, 5>(x, y, dg, s, nrows, Ns, tw); break;
-    case 6: stage<G, 6>(x, y, dg, s, nrows, Ns, tw); break;
-    case 8: stage<G, 8>(x, y, dg, s, nrows, Ns, tw); break;
+    case 2: stage<G, 2>(x, y, dg, s, nrows, Ns, tw, first, io); break;
+    case 3: stage<G, 3>(x, y, dg, s, nrows, Ns, tw, first, io); break;
+    case 4: stage<G, 4>(x, y, dg, s, nrows, Ns, tw, first, io); break;
+    case 5: stage<G, 5>(x, y, dg, s, nrows, Ns, tw, first, io); break;
+    case 6: stage<G, 6>(x, y, dg, s, nrows, Ns, tw, first, io); break;
+    case 8: stage<G, 8>(x, y, dg, s, nrows, Ns, tw, first, io); break;
     default:
         if constexpr (MAXRD > 8) {
             switch (rd) {
-            case 9: stage<G, 9>(x, y, dg, s, nrows, Ns, tw); break;
-            case 10: stage<G, 10>(x, y, dg, s, nrows, Ns, tw); break;
-            case 12: stage<G, 12>(x, y, dg, s, nrows, Ns, tw); break;
-            case 15: stage<G, 15>(x, y, dg, s, nrows, Ns, tw); break;
-            default: stage<G, 16>(x, y, dg, s, nrows, Ns, tw); break;
+            case 9: stage<G, 9>(x, y, dg, s, nrows, Ns, tw, first, io); break;
+            case 10: stage<G, 10>(x, y, dg, s, nrows, Ns, tw, first, io); break;
+            case 12: stage<G, 12>(x, y, dg, s, nrows, Ns, tw, first, io); break;
+            case 15: stage<G, 15>(x, y, dg, s, nrows, Ns, tw, first, io); break;
+            default: stage<G, 16>(x, y, dg, s, nrows, Ns, tw, first, io); break;
             }
         }
         break;
@@ -304,8 +345,14 @@ __device__ __forceinline__ void prefetch_rows(Prefetch<G> &pf, const cpx<G> *__r
     }
 }
 
+// resident CTAs per SM the register allocation must allow (FP32 radix <= 8: 3 CTAs at <= 80 registers
+// without spills; the wider instances need more registers per thread)
+template <class G, int MAXRD> struct FftMinBlocks {
+    static constexpr int value = sizeof(G) == 4 ? (MAXRD <= 8 ? 3 : 2) : 1;
+};
+
 template <class G, int MAXRD>
-__global__ void __launch_bounds__(kThreads) k_fft_rows(const cpx<G> *__restrict__ in, cpx<G> *__restrict__ out,
+__global__ void __launch_bounds__(kThreads, (FftMinBlocks<G, MAXRD>::value)) k_fft_rows(const cpx<G> *__restrict__ in, cpx<G> *__restrict__ out,
                                                        long rows, DimGeom dg, const G *__restrict__ pre,
                                                        const cpx<G> *__restrict__ tw, int R)
 {
@@ -320,12 +367,8 @@ __global__ void __launch_bounds__(kThreads) k_fft_rows(const cpx<G> *__restrict_
     if (row0 < rows) prefetch_rows(pf, in, rows, row0, R, N);
     for (; row0 < rows; row0 += stride) {
         const int nr = (int)((rows - row0) < R ? (rows - row0) : R);
-        // zero padding, then the prefetched row values with the prescale: l -> slot (l - N/2) mod M
-        for (int idx = threadIdx.x; idx < R * M; idx += kThreads) {
-            const int r = idx / M;
-            const int m = idx - r * M;
-            if (m >= N - half && m < M - half) buf0[pad(idx)] = cmk<G>((G)0, (G)0);
-        }
+        // the prefetched row values with the prescale: l -> slot (l - N/2) mod M; the other slots are
+        // zeros that are never stored (the first stage knows where they are)
 #pragma unroll
         for (int k = 0; k < Prefetch<G>::kMax; ++k) {
             const int idx = threadIdx.x + k * kThreads;
@@ -342,22 +385,14 @@ __global__ void __launch_bounds__(kThreads) k_fft_rows(const cpx<G> *__restrict_
         if (row0 + stride < rows) prefetch_rows(pf, in, rows, row0 + stride, R, N);
         cpx<G> *x = buf0, *y = buf1;
         int Ns = 1;
+        StageIO<G> io{N - half, M - half, nullptr, rows, row0, nr, B, H, 1.0f / (float)R};
         for (int s = 0; s < dg.nstages; ++s) {
             const int rd = dg.radix[s];
-            run_stage<G, MAXRD>(rd, x, y, dg, s, R, Ns, tw);
+            io.out = s == dg.nstages - 1 ? out : nullptr;
+            run_stage<G, MAXRD>(rd, x, y, dg, s, R, Ns, tw, s == 0, io);
             cpx<G> *t = x; x = y; y = t;
             Ns *= rd;
         }
-        // band output, transposed: consecutive threads write consecutive rows of one band index
-        for (int idx = threadIdx.x; idx < B * nr; idx += kThreads) {
-            const int b = idx / nr;
-            const int r = idx - b * nr;
-            int m = b - H;
-            while (m < 0) m += M;
-            while (m >= M) m -= M;
-            out[(size_t)b * rows + row0 + r] = x[pad(r * M + m)];
-        }
-        __syncthreads();
     }
 }
 
@@ -401,7 +436,7 @@ cudaError_t launch_fft_pass(const cpx<G> *in, cpx<G> *out, long rows, const DimG
                             const cpx<G> *tw, cudaStream_t st)
 {
     if (rows <= 0) return cudaSuccess;
-    if (dg.M > fft_max_M(sizeof(G))) return cudaErrorInvalidValue;
+    if (dg.M > fft_max_M(sizeof(G)) || dg.nstages < 1) return cudaErrorInvalidValue;
     int maxrd = 1;
     for (int s = 0; s < dg.nstages; ++s) maxrd = dg.radix[s] > maxrd ? dg.radix[s] : maxrd;
     if (maxrd <= 8) return launch_rows<G, 8>(in, out, rows, dg, pre, tw, st);

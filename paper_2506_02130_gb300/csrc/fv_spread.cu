@@ -229,8 +229,8 @@ cudaError_t launch_prep(const double *sdir, const int *sidx, const int *nv_ptr, 
 // footprint overlaps (shared-memory integer atomics); each warp then adds the
 // sources of its own list.  No float atomics; every grid cell is stored once.
 constexpr int kGatherThreads = 256;
-constexpr int kGatherChunk = 128;
 constexpr int kWmax = 16;
+constexpr int kWpad = kWmax + 1;            // row stride of the staged x/y kernel values (bank spread)
 constexpr int kPatchX = 8, kPatchY = 4;     // one warp
 constexpr int kTileX = 32, kTileY = 8;      // one CTA (4 x 2 patches)
 constexpr int kPatches = 8;
@@ -243,8 +243,11 @@ __global__ void __launch_bounds__(kGatherThreads) k_spread_gather(const int *__r
                                                                   SliceGeom g, TimeBin tb, double r0, double r1,
                                                                   cpx<G> *__restrict__ grid)
 {
-    __shared__ int s_cx[kGatherChunk], s_cy[kGatherChunk];
-    __shared__ G s_wx[kGatherChunk][kWmax], s_wy[kGatherChunk][kWmax];
+    // candidates staged per round: 128 (96 in FP64, to keep the static shared memory under 48 KB)
+    constexpr int kGatherChunk = sizeof(G) == 8 ? 96 : 128;
+    __shared__ int s_cx[kGatherChunk], s_cy[kGatherChunk], s_cz[kGatherChunk];
+    __shared__ G s_fx[kGatherChunk], s_fy[kGatherChunk], s_fz[kGatherChunk];
+    __shared__ G s_wx[kGatherChunk * kWpad], s_wy[kGatherChunk * kWpad];
     __shared__ __align__(16) G s_wz[kGatherChunk][NZ];
     __shared__ cpx<G> s_c[NP][kGatherChunk];
     __shared__ unsigned char s_list[kPatches][kGatherChunk];
@@ -269,40 +272,32 @@ __global__ void __launch_bounds__(kGatherThreads) k_spread_gather(const int *__r
     const int by_lo = top_cell(qy_lo - 1.0, tb.nf1_top[1]) / tb.T[1];
     const int by_hi = top_cell(qy_hi + 1.0, tb.nf1_top[1]) / tb.T[1];
     const G two_over_w = (G)(2.0 / w), beta = (G)g.beta;
+    // floor(v / w) for v < kGatherChunk * kWmax by a float product: (v + 0.5) / w lies at least 1/(2w) from
+    // an integer, far more than the product's rounding error
+    const float inv_w = 1.0f / (float)w;
     __syncthreads();
     for (int by = by_lo; by <= by_hi; ++by) {
         const int i0 = offsets[by * tb.nbx + bx_lo], i1 = offsets[by * tb.nbx + bx_hi + 1];
         for (int base = i0; base < i1; base += kGatherChunk) {
             const int n = min(kGatherChunk, i1 - base);
+            // 1. one thread per candidate: position, strengths, and the patches its footprint overlaps
             if (threadIdx.x < n) {
                 const int i = base + threadIdx.x;
                 const int t = threadIdx.x;
                 const int cx = cell[i], cy = cell[n_src + i];
-                // patches of this tile that the footprint [cx, cx+w) x [cy, cy+w) overlaps
                 const int ax = max(cx - x0, 0), bx = min(cx + w - 1 - x0, kTileX - 1);
                 const int ay = max(cy - y0, 0), by2 = min(cy + w - 1 - y0, kTileY - 1);
+                s_cx[t] = cx;
+                s_cy[t] = cy;
+                s_fx[t] = frac[i];
+                s_fy[t] = frac[n_src + i];
+                if (g.d == 3) {
+                    s_cz[t] = cell[2 * n_src + i];
+                    s_fz[t] = frac[2 * n_src + i];
+                }
+#pragma unroll
+                for (int p = 0; p < NP; ++p) s_c[p][t] = cs[(size_t)p * n_src + i];
                 if (ax <= bx && ay <= by2) {
-                    s_cx[t] = cx;
-                    s_cy[t] = cy;
-                    const G fx = frac[i], fy = frac[n_src + i];
-                    for (int j = 0; j < w; ++j) {
-                        s_wx[t][j] = es_k<G>(two_over_w * (fx + (G)j), beta);
-                        s_wy[t][j] = es_k<G>(two_over_w * (fy + (G)j), beta);
-                    }
-                    if (g.d == 3) {
-                        const int cz = cell[2 * n_src + i];
-                        const G fz = frac[2 * n_src + i];
-#pragma unroll
-                        for (int z = 0; z < NZ; ++z) {
-                            const int jz = z - cz;
-                            s_wz[t][z] = (jz >= 0 && jz < w) ? es_k<G>(two_over_w * (fz + (G)jz), beta) : (G)0;
-                        }
-                    } else {
-#pragma unroll
-                        for (int z = 0; z < NZ; ++z) s_wz[t][z] = (G)(z == 0);
-                    }
-#pragma unroll
-                    for (int p = 0; p < NP; ++p) s_c[p][t] = cs[(size_t)p * n_src + i];
                     for (int qy = ay / kPatchY; qy <= by2 / kPatchY; ++qy)
                         for (int qx = ax / kPatchX; qx <= bx / kPatchX; ++qx) {
                             const int q = qy * 4 + qx;
@@ -312,15 +307,36 @@ __global__ void __launch_bounds__(kGatherThreads) k_spread_gather(const int *__r
                 }
             }
             __syncthreads();
+            // 2. every thread computes kernel values: x and y values (source, j), then z values placed at
+            //    absolute z (zero outside the footprint)
+            for (int v = threadIdx.x; v < n * w; v += kGatherThreads) {
+                const int t = (int)(((float)v + 0.5f) * inv_w);
+                const int j = v - t * w;
+                s_wx[t * kWpad + j] = es_k<G>(two_over_w * (s_fx[t] + (G)j), beta);
+                s_wy[t * kWpad + j] = es_k<G>(two_over_w * (s_fy[t] + (G)j), beta);
+            }
+            if (NZ > 1) {
+                for (int v = threadIdx.x; v < n * NZ; v += kGatherThreads) {
+                    const int t = v / NZ, z = v % NZ;
+                    const int jz = z - s_cz[t];
+                    s_wz[t][z] = (jz >= 0 && jz < w) ? es_k<G>(two_over_w * (s_fz[t] + (G)jz), beta) : (G)0;
+                }
+            }
+            __syncthreads();
+            // 3. each warp adds the sources of its patch list into its lanes' columns
             const int cnt = s_cnt[warp];
             for (int e = 0; e < cnt; ++e) {
                 const int t = s_list[warp][e];
                 const unsigned dx = (unsigned)(gx - s_cx[t]), dy = (unsigned)(gy - s_cy[t]);
                 if (dx < (unsigned)w && dy < (unsigned)w) {
-                    const G wxy = s_wx[t][dx] * s_wy[t][dy];
+                    const G wxy = s_wx[t * kWpad + dx] * s_wy[t * kWpad + dy];
                     G wz[NZ];
+                    if (NZ > 1) {
 #pragma unroll
-                    for (int z = 0; z < NZ; ++z) wz[z] = s_wz[t][z];
+                        for (int z = 0; z < NZ; ++z) wz[z] = s_wz[t][z];
+                    } else {
+                        wz[0] = (G)1;
+                    }
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
                         const cpx<G> cp = cscale(s_c[p][t], wxy);

@@ -52,9 +52,10 @@ def test_ragged_batch_autotuned_graph_matches_oracle():
         ref = oracle_vis(OracleProblem.from_workload(bs.problem, pairs=bs.problem.pairs[sel]))[0, 0]
         err = rel_l2(got[sel], ref)
         assert err <= TOL[bs.precision], (bs.problem.name, bs.precision, err)
-        # the same plan alone
+        # the same plan alone (equal up to the summation order of shared-memory atomics when the tuner
+        # picked the scatter spreader)
         alone = p.run()
-        assert rel_l2(got, alone[0, 0]) <= TOL[bs.precision] * 0.01
+        assert rel_l2(got, alone[0, 0]) <= TOL[bs.precision] * 0.1
     b.close()
     for p in plans:
         p.close()
