@@ -50,6 +50,10 @@ def parse():
                     help="hex127: the 127-antenna, 64-channel, 10-time simulation (default); batch: 2,048 ragged "
                          "single-slice problems on shared lanes, replayed from a CUDA graph; serve: a Poisson "
                          "stream of requests over resident plans with continuous batching")
+    ap.add_argument("--transform", default="type3", choices=["type3", "auto", "lattice"],
+                    help="hex127: route of the timed plan (type3: the type-3 NUFFT of every slice)")
+    ap.add_argument("--no-lattice-route", action="store_true",
+                    help="hex127: skip timing the lattice route (Section 2.2.1 with height terms) beside it")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=0.0,
                     help="serve: mean arrival rate (1/s); 0 = 70%% of the measured capacity for the request mix")
@@ -344,7 +348,7 @@ def run_batch(args, rank, world, local, dist):
         for bs in slices:
             prob = bs.problem
             p = fv.Plan.from_problem(prob, precision=fv.FV_FP64, eps=bs.nufft_eps, stream=stream.cuda_stream,
-                                     device=local, n_streams=1)
+                                     device=local, n_streams=1, transform="type3")
             p.set_sky(prob.sky.ra, prob.sky.dec, prob.sky.flux)
             o = torch.empty(p.out_shape, dtype=torch.complex128, device=dev)
             p.run(o)
@@ -355,8 +359,8 @@ def run_batch(args, rank, world, local, dist):
             tot += e0.elapsed_time(e1) / 1e3
             p.close()
         plain = {"value": world * n_vis / tot, "unit": "visibilities/s", "ms_per_step": 1e3 * tot,
-                 "what": "every slice alone through fv_execute on an FP64 plan (upsampling 2, the slice's "
-                         "transform tolerance), "
+                 "what": "every slice alone through fv_execute on an FP64 type-3 plan (upsampling 2, the "
+                         "slice's transform tolerance), "
                          "sum of the calls' device times"}
 
     # oracle on 2% of the slices (at most 256 sampled baselines each): errors per path and the CPU rate
@@ -488,7 +492,7 @@ def run_serve(args, rank, world, local, dist):
             fl = np.ascontiguousarray(sub.sky.flux[:, :, :4], dtype=np.float64)
             p64 = fv.Plan.create(sub.freqs_hz[:4], sub.lsts_rad[:1], sub.latitude_rad, sub.beam, sub.beam_param,
                                  fv.FV_FP64, 1e-11, sub.polarized, stream=ex.stream.cuda_stream, device=local,
-                                 n_streams=1)
+                                 n_streams=1, transform="type3")
             p64.set_array(sub.ant_enu, sub.pairs)
             p64.set_sky(sub.sky.ra, sub.sky.dec, fl)
             o = torch.empty(p64.out_shape, dtype=torch.complex128, device=dev)
@@ -503,7 +507,7 @@ def run_serve(args, rank, world, local, dist):
         t_plain = sum((r.f_range[1] - r.f_range[0]) * (r.t_range[1] - r.t_range[0]) * per[r.kind] for r in reqs)
         plain = {"value": world * summ["visibilities"] / t_plain, "unit": "visibilities/s",
                  "seconds_per_slice": per,
-                 "what": "the same requests' slices on FP64 plans (eps 1e-11, upsampling 2), device time per slice "
+                 "what": "the same requests' slices on FP64 type-3 plans (eps 1e-11, upsampling 2), device time per slice "
                          "measured on 4 channels of each array, summed over every slice with no queueing"}
 
     # oracle on ~1% of the requests (48 sampled baselines, every slice of the request)
@@ -592,7 +596,7 @@ def main():
     # a dedicated stream: the plan runs on it and the timing events are recorded on it
     stream = torch.cuda.Stream(device=dev)
     plan = fv.Plan.from_problem(prob, precision=precision, eps=eps, stream=stream.cuda_stream, device=local,
-                                n_streams=args.streams, spread=args.spread)
+                                n_streams=args.streams, spread=args.spread, transform=args.transform)
     fdt = torch.float32 if precision == fv.FV_MIXED else torch.float64
     cdt = torch.complex64 if precision == fv.FV_MIXED else torch.complex128
     flux_dev = torch.tensor(prob.sky.flux, dtype=fdt, device=dev)
@@ -682,12 +686,41 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": 1e3 * e2e_s / args.steps}
 
+    outs = {args.precision: out.cpu().numpy()}
+
+    # ---- the lattice route on the same workload: the hexagon's horizontal lattice (Section 2.2.1) with
+    # the 5 cm heights expanded in Chebyshev terms; same precision and eps, timed the same way
+    lat_route = None
+    if args.transform == "type3" and not args.no_lattice_route:
+        pl = fv.Plan.from_problem(prob, precision=precision, eps=eps, stream=stream.cuda_stream, device=local,
+                                  n_streams=args.streams, transform="lattice")
+        pl.set_sky(prob.sky.ra, prob.sky.dec, flux_dev)
+        ol = torch.empty(pl.out_shape, dtype=cdt, device=dev)
+        for _ in range(args.warmup):
+            pl.run(ol)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            pl.run(ol)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        msl = e0.elapsed_time(e1)
+        li = pl.info()
+        lat_route = {"value": world * n_vis * args.steps / (msl / 1e3), "unit": "visibilities/s",
+                     "ms_per_step": msl / args.steps, "lattice_terms": li["lattice_terms"],
+                     "lattice_modes": li["lattice_modes"], "lattice_grid": li["lattice_grid"],
+                     "what": "same workload, plan with transform=lattice (type-1 transforms on the horizontal "
+                             "lattice, heights by Chebyshev terms)"}
+        outs["lattice_route"] = ol.cpu().numpy()
+        pl.close()
+
     # ---- the plain FP64 path (one slice after another, no batching) on the same workload
     fp64 = None
-    outs = {args.precision: out.cpu().numpy()}
     if precision == fv.FV_MIXED and not args.no_fp64_compare:
         plan.close()
-        p64 = fv.Plan.from_problem(prob, precision=fv.FV_FP64, eps=1e-11, stream=stream.cuda_stream, device=local)
+        p64 = fv.Plan.from_problem(prob, precision=fv.FV_FP64, eps=1e-11, stream=stream.cuda_stream, device=local,
+                                   transform="type3")
         p64.set_sky(prob.sky.ra, prob.sky.dec, torch.tensor(prob.sky.flux, dtype=torch.float64, device=dev))
         o64 = torch.empty(p64.out_shape, dtype=torch.complex128, device=dev)
         p64.run(o64)
@@ -718,13 +751,13 @@ def main():
                        "n_src": int(prob.sky.n_src), "dims": info["dims"], "precision": args.precision,
                        "eps": eps, "kernel_width": info["kernel_width"], "upsampfac": info["upsampfac"],
                        "nf1_max": info["nf1_max"], "nf2_max": info["nf2_max"], "streams": args.streams or 4,
-                       "spread": args.spread,
+                       "spread": args.spread, "transform": args.transform,
                        "vis_per_step": n_vis,
                        "l2": "inputs larger than L2: a step streams the 640 slices' grids "
                              f"(~{info['workspace_bytes'] / 1e6:.0f} MB workspace reused per slice)",
                        "parallelism": f"{world} independent problems (one per GPU)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": gpu_launches,
-            "rel_l2_vs_oracle_sample": err, "fp64_plain": fp64,
+            "rel_l2_vs_oracle_sample": err, "fp64_plain": fp64, "lattice_route": lat_route,
             "kernels": {k: {"ms_per_step": v["ms"] / prof_steps, "launches_per_step": v["launches"] / prof_steps,
                             "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}
                         for k, v in prof.items() if v["launches"] > 0}}

@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define FV_ABI_VERSION 1
+#define FV_ABI_VERSION 2
 
 typedef struct fv_plan_s *fv_plan_t;   /* opaque plan handle; owns its device memory */
 
@@ -93,7 +93,45 @@ typedef struct {
     int spread_method;        /* fv_spread_method; FV_SPREAD_AUTO picks the fastest that fits */
     int fft_max_radix;        /* largest FFT stage radix: 8 (fewer registers, more stages) or 16;
                                  0 = 8 for FV_MIXED, 16 for FV_FP64 */
+    int transform;            /* fv_transform: which transform evaluates a slice */
+    double lattice_tol_m;     /* largest distance (m) of an antenna from its lattice point, and of its
+                                 height from the first antenna's, still accepted as a lattice;
+                                 0 = 1e-10 m (a phase error below 2 pi nu/c x 1e-10 rad) */
 } fv_opts;
+
+/* Transform choice (Section 2.2.1).  When the antennas' horizontal positions
+ * sit on a lattice x_0 + k_1 a_1 + k_2 a_2 (integer k), every baseline is
+ * n_1 a_1 + n_2 a_2 + b_up e_up and a slice is
+ *   V = sum_s c_s exp(-i n . x_s) exp(-i a u_s'),  x_sd = 2 pi nu a_d . s / c,
+ * a = 2 pi nu b_up / c, u_s' = up component of s.  For a flat array (b_up = 0)
+ * this is the type-1 transform to the integer modes n; for small heights the
+ * second factor is expanded in Chebyshev polynomials of u = 2 u_s' - 1,
+ *   exp(-i a u_s') = exp(-i a/2) sum_q eps_q (-i)^q J_q(a/2) T_q(u)
+ * (eps_0 = 1, else 2), truncated at the K terms whose tail bound
+ * 2 sum_{q>=K} (|a|/4)^q / q! is below eps / 10, so a slice is K type-1
+ * transforms with strengths c_s T_q(u_s) combined per baseline.  Each runs
+ * on a periodic grid of about 2 sigma (2 max|n_d| + 1) points per axis with no
+ * interpolation step.  FV_TRANSFORM_AUTO takes this route when the array is a
+ * lattice, K <= 24 and K times its grid is no larger than the type-3 grid of
+ * the top channel; FV_TRANSFORM_TYPE3 never takes it; FV_TRANSFORM_LATTICE
+ * always does, and fv_set_array fails with FV_ERR_UNSUPPORTED if the array is
+ * not a lattice or needs more than 24 terms. */
+typedef enum {
+    FV_TRANSFORM_AUTO = 0,
+    FV_TRANSFORM_TYPE3 = 1,
+    FV_TRANSFORM_LATTICE = 2
+} fv_transform;
+
+/* Lattice test of Section 2.2.1 on its own (host only, no device needed):
+ * whether the horizontal (east, north) positions of all n_ant antennas
+ * (enu_m: [n_ant][3] m) lie on one lattice within tol_m (0 = 1e-10 m).
+ * Returns 1 if they do and all heights agree within tol_m, 2 if they do but
+ * the heights differ, 0 if they do not.  On success basis[] = {a1_east,
+ * a1_north, a2_east, a2_north} (a reduced basis: the shortest antenna
+ * separation and the shortest one off its line) and index[] = [n_ant][2]
+ * integer coordinates relative to antenna 0.  A collinear array gets a second
+ * vector perpendicular to the first and all second coordinates 0. */
+int fv_lattice_detect(int n_ant, const double *enu_m, double tol_m, double basis[4], int *index);
 
 /* How the ES spreading step is run (all give the same result up to rounding). */
 typedef enum {
@@ -162,6 +200,12 @@ typedef struct {
     double src_centre[3];     /* C: centre of the visible source directions */
     double src_halfwidth[3];  /* S: half-extent of the visible source directions */
     long long workspace_bytes;   /* device memory held by the plan */
+    int transform;        /* FV_TRANSFORM_TYPE3 or FV_TRANSFORM_LATTICE: the route the slices take */
+    int lattice;          /* 1 if the array is a lattice (whatever the route) */
+    int lattice_modes[2]; /* lattice route: modes 2 max|n_d| + 1 per axis */
+    int lattice_grid[2];  /* lattice route: grid (and FFT) points per axis */
+    int lattice_terms;    /* lattice route: Chebyshev terms K of the height factor (1 for a flat array) */
+    double lattice_basis[4];  /* a1_east, a1_north, a2_east, a2_north (m) */
 } fv_info;
 
 fv_status fv_get_info(fv_plan_t p, fv_info *info);

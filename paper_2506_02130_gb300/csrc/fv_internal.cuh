@@ -16,6 +16,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <math.h>
 
 #define FV_C_LIGHT 299792458.0
 #define FV_MAX_STAGES 8
@@ -83,6 +84,68 @@ struct SliceGeom {
     BeamParams beam;
     DimGeom dim[3];
 };
+
+// Beam voltage A(theta) of the analytic beams (Section 2.4): Gaussian power beam,
+// Airy disc, or none.  rho = sin(zenith angle), s2 = cos(zenith angle).
+template <class G> __device__ __forceinline__ G voltage(const BeamParams &b, G rho, G s2, G nu);
+template <> __device__ __forceinline__ double voltage<double>(const BeamParams &b, double rho, double s2, double nu)
+{
+    if (b.kind == 0) {
+        double theta = atan2(rho, s2);
+        double fwhm = b.p0 * b.p1 / nu;
+        return exp(-2.0 * M_LN2 * theta * theta / (fwhm * fwhm));
+    }
+    if (b.kind == 1) {
+        double x = M_PI * b.p0 * nu * rho / FV_C_LIGHT;
+        return x < 1e-8 ? 1.0 - 0.125 * x * x : 2.0 * j1(x) / x;
+    }
+    return 1.0;
+}
+template <> __device__ __forceinline__ float voltage<float>(const BeamParams &b, float rho, float s2, float nu)
+{
+    if (b.kind == 0) {
+        float theta = atan2f(rho, s2);
+        float fwhm = (float)(b.p0 * b.p1) / nu;
+        return expf(-2.0f * 0.69314718055994531f * theta * theta / (fwhm * fwhm));
+    }
+    if (b.kind == 1) {
+        float x = (float)(M_PI * b.p0 / FV_C_LIGHT) * nu * rho;
+        return x < 1e-4f ? 1.0f - 0.125f * x * x : 2.0f * j1f(x) / x;
+    }
+    return 1.0f;
+}
+
+// Strengths of one source in one slice (Eq. 1-2 with the analytic beams): the
+// unpolarised product A^2 I, or the four products of J C J^dagger with
+// J = A R(az) for Stokes IQUV.  Beam in the grid precision G.  Returns n_pol.
+template <class G>
+__device__ __forceinline__ int source_strengths(const SliceGeom &g, double s0, double s1, double s2, long n,
+                                                const void *flux, int flux_fp64, long n_src, int n_freq, int f,
+                                                cpx<G> *c)
+{
+    const G rho = (G)sqrt(s0 * s0 + s1 * s1);
+    const G A = voltage<G>(g.beam, rho, (G)s2, (G)g.nu);
+    const G A2 = A * A;
+    auto ld = [&](int k) -> G {
+        size_t idx = ((size_t)k * n_src + n) * n_freq + f;
+        return flux_fp64 ? (G)((const double *)flux)[idx] : (G)((const float *)flux)[idx];
+    };
+    if (!g.polarized) {
+        c[0] = cmk<G>(A2 * ld(0), (G)0);
+        return 1;
+    }
+    const G I = ld(0), Q = ld(1), U = ld(2), V = ld(3);
+    G ca = (G)1, sa = (G)0;
+    if (rho > (G)0) { ca = (G)s1 / rho; sa = (G)s0 / rho; }
+    const G c2 = ca * ca - sa * sa, s2a = (G)2 * ca * sa;
+    const G Qr = Q * c2 - U * s2a, Ur = Q * s2a + U * c2;
+    c[0] = cmk<G>(A2 * (I + Qr), (G)0);
+    c[1] = cmk<G>(A2 * Ur, A2 * V);
+    c[2] = cmk<G>(A2 * Ur, -A2 * V);
+    c[3] = cmk<G>(A2 * (I - Qr), (G)0);
+    return 4;
+}
+
 
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return the launch error (cudaSuccess if fine).
@@ -168,6 +231,47 @@ cudaError_t launch_interp_zdirect(const cpx<G> *band, const double *bu, int n_u,
 // vis slice [n_bl][n_pol] (complex128 or complex64) <- Vu[bl2u[bl]].
 cudaError_t launch_scatter(const cpx<double> *Vu, const int *bl2u, int n_bl, int n_pol, void *out,
                            int out_fp64, cudaStream_t st);
+
+// ---------------------------------------------------------------- lattice arrays (Section 2.2.1)
+// Coplanar arrays whose antennas sit on a lattice x_a = x_0 + k_a1 a_1 + k_a2 a_2
+// (integer k): a baseline is b = n_1 a_1 + n_2 a_2, so with x_d = kappa a_d . s
+// (E, N components) a slice is V(n) = sum_s c_s exp(-i n . x_s), a type-1
+// transform to the integer modes |n_d| <= H_d.
+struct LatGeom {
+    double a[2][2];     // lattice vectors a_d = (east, north), m
+    int nf[2];          // type-1 grid points per axis (= FFT length)
+    int H[2];           // largest |n_d| over the baselines
+    int K;              // Chebyshev terms of the height factor (1: flat array)
+};
+
+// Per slice: strengths (no prephase), the split grid coordinates
+// t_d = frac(x_d / 2 pi) nf_d of the visible sources, and u = 2 up - 1 (in frac[2]).
+template <class G>
+cudaError_t launch_prep_lattice(const double *sdir, const int *sidx, const int *nv_ptr, long n_src,
+                                const void *flux, int flux_fp64, int n_freq, int f, const SliceGeom &g,
+                                const LatGeom &lg, int *cell, G *frac, cpx<G> *cs, cudaStream_t st);
+// Spreading onto the periodic type-1 grids [K][n_pol][nf_y][nf_x] (cleared by the caller), term q
+// with strengths c_s T_q(u_s): each CTA sums a block of sources into a private copy of some of the
+// grids in shared memory, then adds it to the grids.
+template <class G>
+cudaError_t launch_spread_lattice(const int *nv_ptr, const int *cell, const G *frac, const cpx<G> *cs, long n_src,
+                                  const SliceGeom &g, const LatGeom &lg, cpx<G> *grid, cudaStream_t st);
+// Visibilities of the baselines from the band [b_y][b_x][q][pol] of modes m = -n
+// (b_d = H_d - n_d): sum_q wq[bl][q] x band, times the deconvolution tables
+// dx[n_x + H_x] dy[n_y + H_y] (wq = nullptr: K = 1 and weight 1).
+template <class G>
+cudaError_t launch_gather_lattice(const cpx<G> *band, const int *bln, int n_bl, int n_pol, const LatGeom &lg,
+                                  const cpx<double> *wq, const double *dx, const double *dy, void *out, int out_fp64,
+                                  cudaStream_t st);
+// Per-baseline height-term weights of one channel: wq[bl][q] = e^{-i beta} eps_q (-i)^q J_q(beta),
+// beta = kappa b_up[bl] / 2 (FP64 series for J_q).
+cudaError_t launch_lattice_wterms(const double *b_up, int n_bl, int K, double kappa, cpx<double> *wq,
+                                  cudaStream_t st);
+// tab[n + H] = 1 / ((w/2) Phihat(pi w n / nf)), n in [-H, H] (FP64, Gauss-Legendre quadrature)
+cudaError_t launch_lattice_deconv(double *tab, int H, int nf, int w, double beta, const double *gl_x,
+                                  const double *gl_w, int nq, cudaStream_t st);
+// Host: lattice basis and integer indices of the antennas, or 0 (not a coplanar lattice within tol).
+int lattice_detect(int n_ant, const double *enu, double tol, double basis[4], int *index);
 
 size_t fft_pass_smem_bytes(int M, int elem_bytes);
 int fft_max_M(int elem_bytes);

@@ -356,7 +356,7 @@ cudaError_t launch_interp(const cpx<G> *band, const double *bu, int n_u, const d
 // so the band after the x and y passes, [b_y][b_x][pol][l_z], is read with
 // the z prescale folded into K.  One warp per target: the lanes split the
 // w x w footprint in (y, x) and reduce with shuffles.
-template <class G>
+template <class G, bool HASZ>
 __global__ void __launch_bounds__(256) k_interp_zdirect(const cpx<G> *__restrict__ band, const double *__restrict__ bu,
                                                         int n_u, const double *__restrict__ dec, SliceGeom g,
                                                         const G *__restrict__ prez, const cpx<G> *__restrict__ twz,
@@ -371,17 +371,21 @@ __global__ void __launch_bounds__(256) k_interp_zdirect(const cpx<G> *__restrict
     double x[3] = {0.0, 0.0, 0.0};
     G fr[3];
     int m0[3] = {0, 0, 0};
-    for (int i = 0; i < g.d; ++i) {
-        x[i] = -g.kappa * bu[3 * u + i];
-        double p = (x[i] - g.dim[i].D) * g.dim[i].pscale;
-        double m = ceil(p - 0.5 * w);
-        m0[i] = (int)m;
-        fr[i] = (G)(p - m);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        fr[i] = (G)0;
+        if (i < g.d) {
+            x[i] = -g.kappa * bu[3 * u + i];
+            double p = (x[i] - g.dim[i].D) * g.dim[i].pscale;
+            double m = ceil(p - 0.5 * w);
+            m0[i] = (int)m;
+            fr[i] = (G)(p - m);
+        }
     }
-    const int Nz = g.d == 3 ? g.dim[2].nf1 : 1;
+    const int Nz = HASZ ? g.dim[2].nf1 : 1;
     // lane lz < Nz builds K(l_z); the vector is then shared through shuffles
     cpx<G> Kmine = cmk<G>((G)1, (G)0);
-    if (g.d == 3 && lane < Nz) {
+    if (HASZ && lane < Nz) {
         const int Mz = g.dim[2].M;
         const int lc = lane - Nz / 2;
         cpx<G> acc = cmk<G>((G)0, (G)0);
@@ -397,10 +401,12 @@ __global__ void __launch_bounds__(256) k_interp_zdirect(const cpx<G> *__restrict
         }
         Kmine = cscale(acc, prez[lane]);
     }
-    cpx<G> K[16];
-    for (int lz = 0; lz < Nz; ++lz) {
-        K[lz].x = __shfl_sync(0xffffffffu, Kmine.x, lz);
-        K[lz].y = __shfl_sync(0xffffffffu, Kmine.y, lz);
+    cpx<G> K[HASZ ? 16 : 1];
+    if (HASZ) {
+        for (int lz = 0; lz < Nz; ++lz) {
+            K[lz].x = __shfl_sync(0xffffffffu, Kmine.x, lz);
+            K[lz].y = __shfl_sync(0xffffffffu, Kmine.y, lz);
+        }
     }
     const int np = g.n_pol;
     const int Bx = g.dim[0].B;
@@ -409,7 +415,8 @@ __global__ void __launch_bounds__(256) k_interp_zdirect(const cpx<G> *__restrict
     const G wxm = lane < w ? es_kernel(two_over_w * (fr[0] - (G)lane), beta) : (G)0;
     const G wym = lane < w ? es_kernel(two_over_w * (fr[1] - (G)lane), beta) : (G)0;
     G acc[8];
-    for (int k = 0; k < 2 * np; ++k) acc[k] = (G)0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = (G)0;
     const bool vec2 = (Nz % 2) == 0;   // z runs of even length are read as pairs of complex values
     for (int base = 0; base < w * w; base += 32) {   // same trip count on every lane (shuffles)
         const int idx = base + lane;
@@ -418,10 +425,14 @@ __global__ void __launch_bounds__(256) k_interp_zdirect(const cpx<G> *__restrict
         const G wt = __shfl_sync(0xffffffffu, wym, jy) * __shfl_sync(0xffffffffu, wxm, jx);
         if (valid) {
             const cpx<G> *cell = band + (((size_t)(by0 + jy) * Bx + (bx0 + jx)) * np) * Nz;
-            for (int p = 0; p < np; ++p) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                if (p >= np) break;
                 cpx<G> s = cmk<G>((G)0, (G)0);
                 const cpx<G> *c = cell + p * Nz;
-                if (vec2) {
+                if (!HASZ) {
+                    s = c[0];
+                } else if (vec2) {
                     for (int lz = 0; lz < Nz; lz += 2) {
                         cpx<G> v0, v1;
                         load_pair(c + lz, v0, v1);
@@ -435,19 +446,289 @@ __global__ void __launch_bounds__(256) k_interp_zdirect(const cpx<G> *__restrict
             }
         }
     }
-    for (int k = 0; k < 2 * np; ++k)
-        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if (k < 2 * np)   // np is uniform across the warp
+            for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
     if (lane == 0) {
         double ph = 0.0;
-        for (int i = 0; i < g.d; ++i) ph += x[i] * g.dim[i].C;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            if (i < g.d) ph += x[i] * g.dim[i].C;
         double sp, cp;
         sincos(ph, &sp, &cp);
         const double dk = dec[u];
-        for (int p = 0; p < np; ++p) {
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            if (p >= np) break;
             cpx<double> v = cmk<double>((double)acc[2 * p] * dk, (double)acc[2 * p + 1] * dk);
             Vu[(size_t)u * np + p] = cmul(v, cmk<double>(cp, sp));
         }
     }
+}
+
+// The same sum for one polarisation and a short, even z axis in FP32, read
+// row by row: one warp per target, lane = c * (Nz/2) + h holds z values
+// (2h, 2h+1) of footprint cell c of the current footprint row, so a warp
+// reads one row of the footprint (w cells x Nz values, contiguous in the
+// band) with a single 16-byte load per lane.  The lane applies K(2h),
+// K(2h+1) and the row's y weight, scales by its cell's x weight at the end,
+// and the warp reduces.  Needs w * Nz / 2 <= 32.
+__global__ void __launch_bounds__(256) k_interp_zrow(const cpx<float> *__restrict__ band,
+                                                     const double *__restrict__ bu, int n_u,
+                                                     const double *__restrict__ dec, SliceGeom g,
+                                                     const float *__restrict__ prez,
+                                                     const cpx<float> *__restrict__ twz, cpx<double> *__restrict__ Vu)
+{
+    const int lane = threadIdx.x & 31;
+    const int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (u >= n_u) return;
+    const int w = g.w;
+    const float two_over_w = (float)(2.0 / w);
+    const float beta = (float)g.beta;
+    double x[3] = {0.0, 0.0, 0.0};
+    float fr[3];
+    int m0[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        fr[i] = 0.0f;
+        if (i < g.d) {
+            x[i] = -g.kappa * bu[3 * u + i];
+            double p = (x[i] - g.dim[i].D) * g.dim[i].pscale;
+            double m = ceil(p - 0.5 * w);
+            m0[i] = (int)m;
+            fr[i] = (float)(p - m);
+        }
+    }
+    const int Nz = g.d == 3 ? g.dim[2].nf1 : 1;
+    const int L = Nz / 2;                    // lanes per footprint cell
+    // K(l_z) for l_z = lane < Nz, as in k_interp_zdirect
+    cpx<float> Kmine = cmk<float>(1.0f, 0.0f);
+    if (lane < Nz) {
+        const int Mz = g.dim[2].M;
+        const int lc = lane - Nz / 2;
+        cpx<float> acc = cmk<float>(0.0f, 0.0f);
+        int e = (lc * m0[2]) % Mz;
+        if (e < 0) e += Mz;
+        int step = lc % Mz;
+        if (step < 0) step += Mz;
+        for (int jz = 0; jz < w; ++jz) {
+            const float wt = es_kernel(two_over_w * (fr[2] - (float)jz), beta);
+            acc = cadd(acc, cscale(twz[e], wt));
+            e += step;
+            if (e >= Mz) e -= Mz;
+        }
+        Kmine = cscale(acc, prez[lane]);
+    }
+    const int c = lane / L, h = lane - c * L;
+    const bool active = c < w;
+    const int src = active ? 2 * h : 0;
+    const cpx<float> K0 = cmk<float>(__shfl_sync(0xffffffffu, Kmine.x, src), __shfl_sync(0xffffffffu, Kmine.y, src));
+    const cpx<float> K1 =
+        cmk<float>(__shfl_sync(0xffffffffu, Kmine.x, src + 1), __shfl_sync(0xffffffffu, Kmine.y, src + 1));
+    const float wxm = lane < w ? es_kernel(two_over_w * (fr[0] - (float)lane), beta) : 0.0f;
+    const float wym = lane < w ? es_kernel(two_over_w * (fr[1] - (float)lane), beta) : 0.0f;
+    const float wx = __shfl_sync(0xffffffffu, wxm, active ? c : 0);
+    const int Bx = g.dim[0].B;
+    const int bx0 = m0[0] + g.dim[0].H, by0 = m0[1] + g.dim[1].H;
+    float ax = 0.0f, ay = 0.0f;
+    for (int jy = 0; jy < w; ++jy) {        // same trip count on every lane (shuffle inside)
+        const float wy = __shfl_sync(0xffffffffu, wym, jy);
+        if (active) {
+            const cpx<float> *cell = band + ((size_t)(by0 + jy) * Bx + (bx0 + c)) * Nz + 2 * h;
+            cpx<float> v0, v1;
+            load_pair(cell, v0, v1);
+            const cpx<float> s = cadd(cmul(v0, K0), cmul(v1, K1));
+            ax += wy * s.x;
+            ay += wy * s.y;
+        }
+    }
+    ax *= wx;
+    ay *= wx;
+    for (int o = 16; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    }
+    if (lane == 0) {
+        double ph = 0.0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            if (i < g.d) ph += x[i] * g.dim[i].C;
+        double sp, cp;
+        sincos(ph, &sp, &cp);
+        const double dk = dec[u];
+        const cpx<double> v = cmk<double>((double)ax * dk, (double)ay * dk);
+        Vu[u] = cmul(v, cmk<double>(cp, sp));
+    }
+}
+
+// Interpolation with the per-target set-up spread over the threads.  A CTA
+// takes 64 targets: first threads 0-63 compute, one target each, the FP64
+// coordinates, the first footprint cell, the kernel values of x and y (and
+// for a short z axis the vector K(l_z) of the direct z sum), and the postphase
+// and deconvolution factor, into shared memory.  Then each of the 8 warps
+// walks 8 of the targets, all lanes reading footprint values from the band
+// (ZROW: one footprint row of w cells x Nz z values per load round, one
+// 16-byte load per lane; 2-D: lanes over the w x w cells, n_pol values each),
+// and reduces; lane 0 writes the target's value.
+constexpr int kIbThreads = 256;
+constexpr int kIbTargets = 64;
+constexpr int kIbPerWarp = kIbTargets / (kIbThreads / 32);
+constexpr int kIbMaxW = 16;
+
+template <class G, bool ZROW>
+__global__ void __launch_bounds__(kIbThreads) k_interp_batch(const cpx<G> *__restrict__ band,
+                                                             const double *__restrict__ bu, int n_u,
+                                                             const double *__restrict__ dec, SliceGeom g,
+                                                             const G *__restrict__ prez,
+                                                             const cpx<G> *__restrict__ twz,
+                                                             cpx<double> *__restrict__ Vu)
+{
+    __shared__ G s_wx[kIbTargets][kIbMaxW + 1], s_wy[kIbTargets][kIbMaxW + 1];
+    __shared__ cpx<G> s_K[ZROW ? kIbTargets : 1][ZROW ? 8 : 1];
+    __shared__ int s_bx[kIbTargets], s_by[kIbTargets];
+    __shared__ cpx<double> s_post[kIbTargets];
+    const long u0 = (long)blockIdx.x * kIbTargets;
+    const int w = g.w;
+    const G two_over_w = (G)(2.0 / w), beta = (G)g.beta;
+    // --- per-target set-up, one target per thread
+    if (threadIdx.x < kIbTargets) {
+        const int tl = threadIdx.x;
+        const long u = u0 + tl;
+        const bool valid = u < n_u;
+        double x[3] = {0.0, 0.0, 0.0};
+        int m0[3] = {0, 0, 0};
+        G fr[3] = {(G)0, (G)0, (G)0};
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (i < g.d && valid) {
+                x[i] = -g.kappa * bu[3 * u + i];
+                const double pp = (x[i] - g.dim[i].D) * g.dim[i].pscale;
+                const double m = ceil(pp - 0.5 * w);
+                m0[i] = (int)m;
+                fr[i] = (G)(pp - m);
+            }
+        }
+        for (int j = 0; j < w; ++j) {
+            s_wx[tl][j] = es_kernel(two_over_w * (fr[0] - (G)j), beta);
+            s_wy[tl][j] = es_kernel(two_over_w * (fr[1] - (G)j), beta);
+        }
+        s_bx[tl] = m0[0] + g.dim[0].H;
+        s_by[tl] = m0[1] + g.dim[1].H;
+        if (ZROW) {
+            const int Nz = g.dim[2].nf1, Mz = g.dim[2].M;
+            G phz[kIbMaxW];
+#pragma unroll
+            for (int jz = 0; jz < kIbMaxW; ++jz)
+                phz[jz] = jz < w ? es_kernel(two_over_w * (fr[2] - (G)jz), beta) : (G)0;
+            for (int lz = 0; lz < Nz; ++lz) {
+                const int lc = lz - Nz / 2;
+                int e = (lc * m0[2]) % Mz;
+                if (e < 0) e += Mz;
+                int step = lc % Mz;
+                if (step < 0) step += Mz;
+                cpx<G> acc = cmk<G>((G)0, (G)0);
+#pragma unroll
+                for (int jz = 0; jz < kIbMaxW; ++jz) {
+                    if (jz < w) {
+                        acc = cadd(acc, cscale(twz[e], phz[jz]));
+                        e += step;
+                        if (e >= Mz) e -= Mz;
+                    }
+                }
+                s_K[ZROW ? tl : 0][ZROW ? lz : 0] = cscale(acc, prez[lz]);
+            }
+        }
+        cpx<double> post = cmk<double>(0.0, 0.0);
+        if (valid) {
+            double ph = 0.0;
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                if (i < g.d) ph += x[i] * g.dim[i].C;
+            double sp, cp;
+            sincos(ph, &sp, &cp);
+            post = cmk<double>(cp * dec[u], sp * dec[u]);
+        }
+        s_post[tl] = post;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int np = g.n_pol;
+    const int Bx = g.dim[0].B;
+    const int t0 = warp * kIbPerWarp;
+    const int nt = (int)max(0L, min((long)kIbPerWarp, (long)n_u - u0 - t0));
+    if (ZROW) {
+        const int Nz = g.dim[2].nf1, L = Nz / 2;
+        const int c = lane / L, h = lane - c * L;
+        const bool active = c < w;
+        const size_t rstride = (size_t)Bx * Nz;
+        for (int tt = 0; tt < nt; ++tt) {
+            const int t = t0 + tt;
+            G ax = (G)0, ay = (G)0;
+            if (active) {
+                const cpx<G> K0 = s_K[ZROW ? t : 0][ZROW ? 2 * h : 0];
+                const cpx<G> K1 = s_K[ZROW ? t : 0][ZROW ? 2 * h + 1 : 0];
+                const cpx<G> *rowp = band + ((size_t)s_by[t] * Bx + (s_bx[t] + c)) * Nz + 2 * h;
+#pragma unroll 4
+                for (int jy = 0; jy < w; ++jy) {
+                    cpx<G> v0, v1;
+                    load_pair(rowp + jy * rstride, v0, v1);
+                    const cpx<G> sm = cadd(cmul(v0, K0), cmul(v1, K1));
+                    const G wy = s_wy[t][jy];
+                    ax += wy * sm.x;
+                    ay += wy * sm.y;
+                }
+                const G wx = s_wx[t][c];
+                ax *= wx;
+                ay *= wx;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                ax += __shfl_xor_sync(0xffffffffu, ax, o);
+                ay += __shfl_xor_sync(0xffffffffu, ay, o);
+            }
+            if (lane == 0) Vu[u0 + t] = cmul(cmk<double>((double)ax, (double)ay), s_post[t]);
+        }
+    } else {
+        const int ww = w * w;
+        for (int tt = 0; tt < nt; ++tt) {
+            const int t = t0 + tt;
+            G acc[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = (G)0;
+            const int bx0 = s_bx[t], by0 = s_by[t];
+            for (int idx = lane; idx < ww; idx += 32) {
+                const int jy = idx / w, jx = idx - jy * w;
+                const G wt = s_wx[t][jx] * s_wy[t][jy];
+                const cpx<G> *cell = band + ((size_t)(by0 + jy) * Bx + (bx0 + jx)) * np;
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    if (p < np) {
+                        const cpx<G> v = cell[p];
+                        acc[2 * p] += wt * v.x;
+                        acc[2 * p + 1] += wt * v.y;
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (k < 2 * np)   // np is the same on every lane
+                    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+            if (lane == 0) {
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+                    if (p < np)
+                        Vu[(size_t)(u0 + t) * np + p] =
+                            cmul(cmk<double>((double)acc[2 * p], (double)acc[2 * p + 1]), s_post[t]);
+            }
+        }
+    }
+}
+
+static bool zrow_fits(const SliceGeom &g, int elem_bytes)
+{
+    if (elem_bytes != 4 || g.d != 3 || g.n_pol != 1) return false;
+    const int Nz = g.dim[2].nf1;
+    return Nz >= 2 && Nz % 2 == 0 && g.w * (Nz / 2) <= 32;
 }
 
 template <class G>
@@ -458,7 +739,30 @@ cudaError_t launch_interp_zdirect(const cpx<G> *band, const double *bu, int n_u,
     if (n_u <= 0) return cudaSuccess;
     if (g.d == 3 && g.dim[2].nf1 > 16) return cudaErrorInvalidValue;
     long threads = (long)n_u * 32;
-    k_interp_zdirect<G><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(band, bu, n_u, dec, g, prez, twz, Vu);
+    const unsigned ib_blocks = (unsigned)((n_u + kIbTargets - 1) / kIbTargets);
+    if (g.w <= kIbMaxW) {
+        if (g.d == 2 && g.n_pol <= 4) {
+            k_interp_batch<G, false><<<ib_blocks, kIbThreads, 0, st>>>(band, bu, n_u, dec, g, prez, twz, Vu);
+            return cudaGetLastError();
+        }
+        if constexpr (sizeof(G) == 4) {
+            if (zrow_fits(g, 4) && g.dim[2].nf1 <= 8) {
+                k_interp_batch<G, true><<<ib_blocks, kIbThreads, 0, st>>>(band, bu, n_u, dec, g, prez, twz, Vu);
+                return cudaGetLastError();
+            }
+            if (zrow_fits(g, 4)) {
+                k_interp_zrow<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(band, bu, n_u, dec, g, prez, twz,
+                                                                                Vu);
+                return cudaGetLastError();
+            }
+        }
+    }
+    if (g.d == 3)
+        k_interp_zdirect<G, true><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(band, bu, n_u, dec, g, prez, twz,
+                                                                                     Vu);
+    else
+        k_interp_zdirect<G, false><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(band, bu, n_u, dec, g, prez,
+                                                                                      twz, Vu);
     return cudaGetLastError();
 }
 

@@ -91,6 +91,22 @@ struct fv_plan_s {
     double qscale_top[3] = {0, 0, 0};
     int nf1_top[3] = {1, 1, 1};
 
+    // lattice arrays (Section 2.2.1)
+    int transform_req = 0;            // fv_opts.transform
+    double lat_tol = 1e-10;
+    bool lat_ok = false;              // the array is a lattice
+    bool use_lattice = false;         // slices take the lattice route
+    double lat_basis[4] = {0, 0, 0, 0};
+    int lat_H[2] = {0, 0};
+    int *d_bln = nullptr;             // [n_bl][2] lattice offsets n of the baselines
+    fv::LatGeom lg{};
+    fv::DimGeom lat_dim[2]{};         // FFT geometry of the two passes
+    void *d_lat_pre = nullptr, *d_lat_tw = nullptr;   // ones (prescale) and twiddles per axis
+    double *d_lat_dec = nullptr;      // 1/Psihat per axis: [2H_x+1] then [2H_y+1]
+    std::vector<double> lat_bup;      // [n_bl] up component of each baseline (m)
+    double *d_lat_bup = nullptr;
+    cpx<double> *d_lat_wq = nullptr;  // [n_freq][n_bl][K] height-term weights (K > 1 only)
+
     long long ws_bytes = 0;
     std::vector<long> geo_sig;       // sizes behind the current tables and workspaces
     int nf1_max[3] = {1, 1, 1}, M_max[3] = {1, 1, 1};

@@ -199,6 +199,11 @@ static void free_geometry(fv_plan_s *p)
 {
     dfree(p->d_pre);
     dfree(p->d_tw);
+    dfree(p->d_lat_pre);
+    dfree(p->d_lat_tw);
+    dfree_t(p->d_lat_dec);
+    dfree_t(p->d_lat_bup);
+    dfree_t(p->d_lat_wq);
     free_workspaces(p->ws);
 }
 
@@ -227,6 +232,119 @@ static void resolve_spread(fv_plan_s *p, int gs, int w)
     p->T[1] = 4;
     p->nbx = (p->nf1_top[0] + p->T[0] - 1) / p->T[0];
     p->nby = (p->nf1_top[1] + p->T[1] - 1) / p->T[1];
+}
+
+// The lattice route (Section 2.2.1): grid and FFT geometry per axis, prescale (ones), twiddles and
+// deconvolution tables, and the workspace it needs; taken if the array is a lattice and, in auto
+// mode, its grid is no larger than the type-3 grid of the top channel.
+static fv_status prepare_lattice(fv_plan_s *p)
+{
+    p->use_lattice = false;
+    if (!p->lat_ok || p->transform_req == FV_TRANSFORM_TYPE3 || p->dims_req == 3) return FV_OK;
+    const int w = p->w;
+    LatGeom lg{};
+    DimGeom dg[2]{};
+    long cells = 1;
+    for (int k = 0; k < 2; ++k) {
+        lg.a[k][0] = p->lat_basis[2 * k];
+        lg.a[k][1] = p->lat_basis[2 * k + 1];
+        lg.H[k] = p->lat_H[k];
+        const int B = 2 * lg.H[k] + 1;
+        const int target = std::max((int)std::ceil(p->sigma * B - 1e-9), 2 * w);
+        DimGeom &d = dg[k];
+        d.M = fft_choose_length(target + (target & 1), d.radix, d.nstages, p->fft_max_radix);
+        if (d.M < 0 || d.M > fft_max_M((int)(p->precision == FV_FP64 ? sizeof(double) : sizeof(float))))
+            return p->fail(FV_ERR_UNSUPPORTED, "lattice grid too large");
+        d.nf1 = d.M;
+        d.H = lg.H[k];
+        d.B = B;
+        fft_stage_constants(d);
+        lg.nf[k] = d.M;
+        cells *= d.M;
+    }
+    // Chebyshev terms of the height factor: the tail 2 sum_{q>=K} (beta/2)^q / q! below eps / 10
+    double bup_max = 0.0;
+    for (double v : p->lat_bup) bup_max = std::max(bup_max, std::fabs(v));
+    const double beta = 0.5 * 2.0 * M_PI * p->freq[p->f_top] / FV_C_LIGHT * bup_max;
+    int K = 1;
+    if (bup_max > 0.0) {
+        const double h = 0.5 * beta;
+        for (K = 1; K <= 64; ++K) {
+            double term = 1.0, tail = 0.0;
+            for (int q = 1; q <= K; ++q) term *= h / q;          // (beta/2)^K / K!
+            for (int q = K; q < K + 60; ++q) {
+                tail += term;
+                term *= h / (q + 1);
+            }
+            if (2.0 * tail <= 0.1 * p->eps) break;
+        }
+    }
+    lg.K = K;
+    const DimGeom *top = p->gf[p->f_top].dim;
+    const long t3 = (long)top[0].nf1 * top[1].nf1 * (p->d == 3 ? top[2].nf1 : 1);
+    if (K > 24) {
+        if (p->transform_req == FV_TRANSFORM_LATTICE)
+            return p->fail(FV_ERR_UNSUPPORTED, "the lattice route would need " + std::to_string(K) +
+                                                   " height terms (at most 24)");
+        return FV_OK;
+    }
+    if (p->transform_req == FV_TRANSFORM_AUTO && cells * K > t3) return FV_OK;
+    p->use_lattice = true;
+    p->lg = lg;
+    p->lat_dim[0] = dg[0];
+    p->lat_dim[1] = dg[1];
+    const size_t es = p->elem();
+    const size_t gs = p->precision == FV_FP64 ? sizeof(double) : sizeof(float);
+    dfree(p->d_lat_pre);
+    dfree(p->d_lat_tw);
+    dfree_t(p->d_lat_dec);
+    const size_t npre = (size_t)lg.nf[0] + lg.nf[1];
+    CK(cudaMalloc(&p->d_lat_pre, npre * gs));
+    CK(cudaMalloc(&p->d_lat_tw, npre * es));
+    CK(cudaMalloc(&p->d_lat_dec, (size_t)(2 * lg.H[0] + 1 + 2 * lg.H[1] + 1) * sizeof(double)));
+    if (p->precision == FV_FP64) {
+        std::vector<double> ones(npre, 1.0);
+        CK(cudaMemcpyAsync(p->d_lat_pre, ones.data(), npre * gs, cudaMemcpyHostToDevice, p->stream));
+        CK(launch_twiddles<double>((cpx<double> *)p->d_lat_tw, lg.nf[0], p->stream));
+        CK(launch_twiddles<double>((cpx<double> *)p->d_lat_tw + lg.nf[0], lg.nf[1], p->stream));
+    } else {
+        std::vector<float> ones(npre, 1.0f);
+        CK(cudaMemcpyAsync(p->d_lat_pre, ones.data(), npre * gs, cudaMemcpyHostToDevice, p->stream));
+        CK(launch_twiddles<float>((cpx<float> *)p->d_lat_tw, lg.nf[0], p->stream));
+        CK(launch_twiddles<float>((cpx<float> *)p->d_lat_tw + lg.nf[0], lg.nf[1], p->stream));
+    }
+    CK(launch_lattice_deconv(p->d_lat_dec, lg.H[0], lg.nf[0], w, p->beta, p->d_glx, p->d_glw, p->nq, p->stream));
+    CK(launch_lattice_deconv(p->d_lat_dec + 2 * lg.H[0] + 1, lg.H[1], lg.nf[1], w, p->beta, p->d_glx, p->d_glw,
+                             p->nq, p->stream));
+    dfree_t(p->d_lat_bup);
+    dfree_t(p->d_lat_wq);
+    if (K > 1 && p->n_bl > 0) {
+        const int nf = (int)p->freq.size();
+        CK(cudaMalloc(&p->d_lat_bup, (size_t)p->n_bl * sizeof(double)));
+        CK(cudaMemcpyAsync(p->d_lat_bup, p->lat_bup.data(), (size_t)p->n_bl * sizeof(double), cudaMemcpyHostToDevice,
+                           p->stream));
+        CK(cudaMalloc(&p->d_lat_wq, (size_t)nf * p->n_bl * K * sizeof(cpx<double>)));
+        for (int f = 0; f < nf; ++f)
+            CK(launch_lattice_wterms(p->d_lat_bup, p->n_bl, K, 2.0 * M_PI * p->freq[f] / FV_C_LIGHT,
+                                     p->d_lat_wq + (size_t)f * p->n_bl * K, p->stream));
+    }
+    // workspace of one lattice slice: grid, the two bands, one-bin time binning, prepared sources
+    fv_plan_s::WsNeed nd;
+    const int np = p->n_pol;
+    nd.grid = (size_t)K * np * lg.nf[0] * lg.nf[1] * es;
+    nd.bufA = (size_t)(2 * lg.H[0] + 1) * K * np * lg.nf[1] * es;
+    nd.bufB = (size_t)(2 * lg.H[1] + 1) * (2 * lg.H[0] + 1) * K * np * es;
+    nd.vu = sizeof(cpx<double>);
+    nd.tiled = true;
+    nd.n_src = std::max<long>(p->n_src, 1);
+    nd.nb = 1;
+    nd.frac_per_src = 3 * gs;
+    nd.cs_per_src = (size_t)np * es;
+    free_workspaces(p->ws);
+    p->need = nd;
+    p->ws_bytes = (long long)(npre * (gs + es) + p->n_streams * workspace_layout(nd, nullptr, nullptr) +
+                              (K > 1 ? p->freq.size() * (size_t)p->n_bl * K * sizeof(cpx<double>) : 0));
+    return FV_OK;
 }
 
 // Per-channel geometry, tables and workspace; needs the array and the sky.
@@ -300,7 +418,13 @@ static fv_status prepare(fv_plan_s *p)
     // a new sky with the same grid sizes (the usual case: same array, same channels) keeps the
     // tables and workspaces of the previous one
     std::vector<long> sig = {(long)p->n_src, (long)p->n_pol, (long)p->n_streams, (long)p->spread_req, (long)p->d,
-                             (long)grid_e, (long)bufA_e, (long)bufB_e};
+                             (long)grid_e, (long)bufA_e, (long)bufB_e, (long)p->lat_ok, (long)p->lat_H[0],
+                             (long)p->lat_H[1]};
+    for (int k = 0; k < 4; ++k) {
+        long long bits;
+        std::memcpy(&bits, &p->lat_basis[k], sizeof(bits));
+        sig.push_back((long)bits);
+    }
     for (int f = 0; f < nf; ++f)
         for (int i = 0; i < 3; ++i) {
             sig.push_back(p->gf[f].dim[i].nf1);
@@ -312,7 +436,7 @@ static fv_status prepare(fv_plan_s *p)
     if (reuse) {
         resolve_spread(p, (int)gs, w);
         p->geo_sig = sig;
-        return FV_OK;
+        return FV_OK;        // the lattice route's tables and decision depend on the array only: kept
     }
     CK(cudaMalloc(&p->d_pre, std::max<size_t>(pre_total, 1) * gs));
     CK(cudaMalloc(&p->d_tw, std::max<size_t>(tw_total, 1) * es));
@@ -346,8 +470,76 @@ static fv_status prepare(fv_plan_s *p)
     p->ws_bytes = (long long)(pre_total * gs + tw_total * es +
                               p->n_streams * ((grid_e + bufA_e + bufB_e) * es +
                                               (size_t)p->n_u * p->n_pol * sizeof(cpx<double>) + bin_bytes));
+    fv_status ls = prepare_lattice(p);
+    if (ls != FV_OK) return ls;
     CK(cudaStreamSynchronize(p->stream));
     p->geo_sig = sig;
+    return FV_OK;
+}
+
+// Slices of a lattice array (Section 2.2.1): one-bin time binning (rotation and horizon cut), then per
+// slice strengths and periodic grid coordinates, spreading, the two FFT passes without padding, and the
+// per-baseline mode lookup with deconvolution.
+template <class G>
+static fv_status run_slices_lattice(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, char *vis,
+                                    size_t slice_bytes, long k_begin, long k_end, OutMap om)
+{
+    const int nf = (int)p->freq.size(), nt = (int)p->lst.size();
+    const LatGeom &lg = p->lg;
+    const int np = p->n_pol;
+    const double es = sizeof(cpx<G>);
+    cpx<G> *grid = (cpx<G> *)wk.grid, *A = (cpx<G> *)wk.bufA, *Bb = (cpx<G> *)wk.bufB;
+    const G *pre = (const G *)p->d_lat_pre;
+    const cpx<G> *tw = (const cpx<G> *)p->d_lat_tw;
+    const size_t gel = (size_t)lg.K * np * lg.nf[0] * lg.nf[1];
+    const int Bx = 2 * lg.H[0] + 1, By = 2 * lg.H[1] + 1;
+    const double nvis = 0.5 * p->n_src;
+    int t_binned = -1;
+    for (long k = k_begin; k < k_end; ++k) {
+        const int t = (int)(k / nf), f = (int)(k % nf);
+        if (t != t_binned) {
+            TimeBin tb{};
+            std::memcpy(tb.R, &p->Rt[(size_t)t * 9], 9 * sizeof(double));
+            for (int i = 0; i < 3; ++i) tb.nf1_top[i] = 1;
+            tb.T[0] = tb.T[1] = 1;
+            tb.nbx = tb.nby = 1;
+            CK(prof_begin(p, PC_BIN, st));
+            CK(launch_time_binning(p->d_e, p->n_src, tb, wk.bin_of, wk.counts, wk.offsets, wk.cursor, wk.sdir,
+                                   wk.sidx, st));
+            CK(prof_end(p, (double)p->n_src * 80.0));
+            t_binned = t;
+        }
+        SliceGeom g = p->gf[f];
+        std::memcpy(g.R, &p->Rt[(size_t)t * 9], 9 * sizeof(double));
+        G *frac = (G *)wk.frac;
+        cpx<G> *cs = (cpx<G> *)wk.cs;
+        CK(prof_begin(p, PC_PREP, st));
+        CK(launch_prep_lattice<G>(wk.sdir, wk.sidx, wk.offsets + 1, p->n_src, p->flux, p->flux_fp64, nf, f, g, lg,
+                                  wk.cell, frac, cs, st));
+        CK(prof_end(p, nvis * (24.0 + 4.0 + p->n_stokes * (p->flux_fp64 ? 8.0 : 4.0) + 8.0 + 2.0 * sizeof(G) +
+                               np * es)));
+        CK(prof_begin(p, PC_MEMSET, st));
+        CK(cudaMemsetAsync(grid, 0, gel * sizeof(cpx<G>), st));
+        CK(prof_end(p, gel * es));
+        CK(prof_begin(p, PC_SPREAD, st));
+        CK(launch_spread_lattice<G>(wk.offsets + 1, wk.cell, frac, cs, p->n_src, g, lg, grid, st));
+        CK(prof_end(p, nvis * (8.0 + 3.0 * sizeof(G) + np * es) + gel * es));
+        const long r1 = (long)lg.K * np * lg.nf[1];
+        CK(prof_begin(p, PC_FFT_X, st));
+        CK(launch_fft_pass<G>(grid, A, r1, p->lat_dim[0], pre, tw, st));
+        CK(prof_end(p, (double)r1 * (lg.nf[0] + Bx) * es));
+        const long r2 = (long)Bx * lg.K * np;
+        CK(prof_begin(p, PC_FFT_Y, st));
+        CK(launch_fft_pass<G>(A, Bb, r2, p->lat_dim[1], pre + lg.nf[0], tw + lg.nf[0], st));
+        CK(prof_end(p, (double)r2 * (lg.nf[1] + By) * es));
+        const int ntm = om.nt > 0 ? om.nt : nt;
+        char *out = vis + ((size_t)(f - om.f0) * ntm + (t - om.t0)) * slice_bytes;
+        CK(prof_begin(p, PC_INTERP, st));
+        const cpx<double> *wq = p->d_lat_wq ? p->d_lat_wq + (size_t)f * p->n_bl * lg.K : nullptr;
+        CK(launch_gather_lattice<G>(Bb, p->d_bln, p->n_bl, np, lg, wq, p->d_lat_dec, p->d_lat_dec + Bx, out,
+                                    p->precision == FV_FP64, st));
+        CK(prof_end(p, (double)p->n_bl * (8.0 + lg.K * (np * es + (wq ? 16.0 : 0.0))) + (double)slice_bytes));
+    }
     return FV_OK;
 }
 
@@ -355,6 +547,7 @@ template <class G>
 fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, char *vis, size_t slice_bytes,
                      long k_begin, long k_end, OutMap om)
 {
+    if (p->use_lattice) return run_slices_lattice<G>(p, wk, st, vis, slice_bytes, k_begin, k_end, om);
     const int nf = (int)p->freq.size(), nt = (int)p->lst.size();
     cpx<G> *grid = (cpx<G> *)wk.grid;
     cpx<G> *A = (cpx<G> *)wk.bufA, *Bb = (cpx<G> *)wk.bufB;
@@ -506,6 +699,14 @@ void fv_opts_default(fv_opts *o)
 
 int fv_abi_version(void) { return FV_ABI_VERSION; }
 
+int fv_lattice_detect(int n_ant, const double *enu_m, double tol_m, double basis[4], int *index)
+{
+    if (n_ant < 1 || !enu_m || !basis || !index) return 0;
+    for (long i = 0; i < 3L * n_ant; ++i)
+        if (!std::isfinite(enu_m[i])) return 0;
+    return lattice_detect(n_ant, enu_m, tol_m, basis, index);
+}
+
 const char *fv_last_error(fv_plan_t p) { return p ? p->err.c_str() : g_create_error.c_str(); }
 
 fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
@@ -532,6 +733,9 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
     if (o->spread_method < FV_SPREAD_AUTO || o->spread_method > FV_SPREAD_ATOMIC) return bad("unknown spread_method");
     if (o->n_streams < 0) return bad("n_streams < 0");
     if (o->fft_max_radix != 0 && o->fft_max_radix != 8 && o->fft_max_radix != 16) return bad("fft_max_radix must be 0, 8 or 16");
+    if (o->transform < FV_TRANSFORM_AUTO || o->transform > FV_TRANSFORM_LATTICE) return bad("unknown transform");
+    if (o->transform == FV_TRANSFORM_LATTICE && o->dims == 3) return bad("the lattice route has no dims = 3 form");
+    if (!(o->lattice_tol_m >= 0.0) || !std::isfinite(o->lattice_tol_m)) return bad("lattice_tol_m must be >= 0");
     double sigma = o->upsampfac == 0.0 ? 2.0 : o->upsampfac;
     if (!(sigma >= 1.25 && sigma <= 3.0)) return bad("upsampfac must be in [1.25, 3]");
     // the two deconvolutions amplify FP32 rounding by (Phihat(0)/Phihat(w pi/2 sigma))^2 at the band
@@ -605,6 +809,8 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
     // radix 8 needs fewer registers (more CTAs per SM), which wins in FP32; FP64 uses the same
     // register count either way and prefers fewer stages
     p->fft_max_radix = o->fft_max_radix > 0 ? o->fft_max_radix : (o->precision == FV_MIXED ? 8 : 16);
+    p->transform_req = o->transform;
+    p->lat_tol = o->lattice_tol_m > 0.0 ? o->lattice_tol_m : 1e-10;
     p->sub.assign(p->n_streams, nullptr);
     p->ev_join.assign(p->n_streams, nullptr);
     p->sub[0] = p->stream;
@@ -693,6 +899,35 @@ fv_status fv_set_array(fv_plan_t p, int n_ant, const double *enu_m, int n_bl, co
     }
     int d = p->dims_req ? p->dims_req : (nonplanar ? 3 : 2);
     if (d == 2 && nonplanar) return p->fail(FV_ERR_ARG, "dims = 2 requested for a non-coplanar array");
+    // lattice test (Section 2.2.1): baselines as integer combinations n of two lattice vectors
+    std::vector<int> bln;
+    bool lat_ok = false;
+    double lat_basis[4] = {0, 0, 0, 0};
+    int lat_H[2] = {0, 0};
+    if (n_ant <= 20000) {      // the test is O(n_ant^2) on the host
+        std::vector<int> kidx(2 * (size_t)n_ant);
+        lat_ok = lattice_detect(n_ant, enu_m, p->lat_tol, lat_basis, kidx.data()) != 0;
+        if (lat_ok) {
+            p->lat_bup.resize(n_bl);
+            for (int b = 0; b < n_bl; ++b) p->lat_bup[b] = enu_m[3 * pr[2 * b] + 2] - enu_m[3 * pr[2 * b + 1] + 2];
+            bln.resize(2 * (size_t)n_bl);
+            for (int b = 0; b < n_bl; ++b)
+                for (int k = 0; k < 2; ++k) {
+                    const int v = kidx[2 * pr[2 * b] + k] - kidx[2 * pr[2 * b + 1] + k];
+                    bln[2 * b + k] = v;
+                    lat_H[k] = std::max(lat_H[k], std::abs(v));
+                }
+        }
+    }
+    if (p->transform_req == FV_TRANSFORM_LATTICE && !lat_ok)
+        return p->fail(FV_ERR_UNSUPPORTED, "transform = FV_TRANSFORM_LATTICE, but the antennas are not a coplanar "
+                                           "lattice within lattice_tol_m");
+    if (!lat_ok) p->lat_bup.clear();
+    p->lat_ok = lat_ok;        // reported whatever the route; the lattice route also needs transform != TYPE3
+                               // and dims != 3
+    std::memcpy(p->lat_basis, lat_basis, sizeof(lat_basis));
+    p->lat_H[0] = lat_H[0];
+    p->lat_H[1] = lat_H[1];
     p->n_ant = n_ant;
     p->n_bl = n_bl;
     p->n_u = (int)(bu.size() / 3);
@@ -709,6 +944,12 @@ fv_status fv_set_array(fv_plan_t p, int n_ant, const double *enu_m, int n_bl, co
     dfree_t(p->d_bu);
     dfree_t(p->d_dec);
     dfree_t(p->d_bl2u);
+    dfree_t(p->d_bln);
+    if (lat_ok) {
+        CK(cudaMalloc(&p->d_bln, std::max<size_t>(bln.size(), 2) * sizeof(int)));
+        if (!bln.empty())
+            CK(cudaMemcpyAsync(p->d_bln, bln.data(), bln.size() * sizeof(int), cudaMemcpyHostToDevice, p->stream));
+    }
     const size_t nu = std::max(p->n_u, 1), nb = std::max(p->n_bl, 1);
     CK(cudaMalloc(&p->d_bu, nu * 3 * sizeof(double)));
     CK(cudaMalloc(&p->d_dec, nu * sizeof(double)));
@@ -839,6 +1080,7 @@ fv_status fv_destroy(fv_plan_t p)
     dfree_t(p->d_bu);
     dfree_t(p->d_dec);
     dfree_t(p->d_bl2u);
+    dfree_t(p->d_bln);
     dfree_t(p->d_e);
     dfree(p->d_flux_owned);
     for (cudaEvent_t ev : p->ev_pool) cudaEventDestroy(ev);
@@ -870,6 +1112,14 @@ fv_status fv_get_info(fv_plan_t p, fv_info *info)
         info->src_halfwidth[i] = p->S[i];
     }
     info->workspace_bytes = p->ws_bytes;
+    info->transform = p->use_lattice ? FV_TRANSFORM_LATTICE : FV_TRANSFORM_TYPE3;
+    info->lattice = p->lat_ok ? 1 : 0;
+    for (int k = 0; k < 2; ++k) {
+        info->lattice_modes[k] = p->use_lattice ? 2 * p->lat_H[k] + 1 : 0;
+        info->lattice_grid[k] = p->use_lattice ? p->lg.nf[k] : 0;
+    }
+    info->lattice_terms = p->use_lattice ? p->lg.K : 0;
+    for (int k = 0; k < 4; ++k) info->lattice_basis[k] = p->lat_basis[k];
     return FV_OK;
 }
 

@@ -64,7 +64,10 @@ __global__ void k_bin_count(const double *__restrict__ e, long n_src, TimeBin tb
     int cy = top_cell((s1 - tb.C[1]) * tb.qscale_top[1], tb.nf1_top[1]);
     int b = (cy / tb.T[1]) * tb.nbx + cx / tb.T[0];
     bin_of[n] = b;
-    atomicAdd(&counts[b], 1);
+    // warp-aggregated count: one atomic per distinct bin among the active lanes
+    const unsigned act = __activemask();
+    const unsigned grp = __match_any_sync(act, b);
+    if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&counts[b], __popc(grp));
 }
 
 // exclusive scan of counts[0..nb) into offsets[0..nb], cursor = offsets (one CTA of 1024 threads)
@@ -100,7 +103,15 @@ __global__ void k_bin_scatter(const double *__restrict__ e, long n_src, TimeBin 
     if (n >= n_src) return;
     const int b = bin_of[n];
     if (b < 0) return;
-    const int pos = atomicAdd(&cursor[b], 1);
+    // warp-aggregated slot reservation: the lowest lane of each group of equal bins reserves for all
+    const int lane = threadIdx.x & 31;
+    const unsigned act = __activemask();
+    const unsigned grp = __match_any_sync(act, b);
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&cursor[b], __popc(grp));
+    base = __shfl_sync(grp, base, leader);
+    const int pos = base + __popc(grp & ((1u << lane) - 1u));
     const double ex = e[n], ey = e[n_src + n], ez = e[2 * n_src + n];
     sdir[pos] = tb.R[0] * ex + tb.R[1] * ey + tb.R[2] * ez;
     sdir[n_src + pos] = tb.R[3] * ex + tb.R[4] * ey + tb.R[5] * ez;
@@ -122,34 +133,6 @@ cudaError_t launch_time_binning(const double *e, long n_src, const TimeBin &tb, 
 }
 
 // ------------------------------------------------------------------ per slice
-template <class G> __device__ __forceinline__ G voltage(const BeamParams &b, G rho, G s2, G nu);
-template <> __device__ __forceinline__ double voltage<double>(const BeamParams &b, double rho, double s2, double nu)
-{
-    if (b.kind == 0) {
-        double theta = atan2(rho, s2);
-        double fwhm = b.p0 * b.p1 / nu;
-        return exp(-2.0 * M_LN2 * theta * theta / (fwhm * fwhm));
-    }
-    if (b.kind == 1) {
-        double x = M_PI * b.p0 * nu * rho / FV_C_LIGHT;
-        return x < 1e-8 ? 1.0 - 0.125 * x * x : 2.0 * j1(x) / x;
-    }
-    return 1.0;
-}
-template <> __device__ __forceinline__ float voltage<float>(const BeamParams &b, float rho, float s2, float nu)
-{
-    if (b.kind == 0) {
-        float theta = atan2f(rho, s2);
-        float fwhm = (float)(b.p0 * b.p1) / nu;
-        return expf(-2.0f * 0.69314718055994531f * theta * theta / (fwhm * fwhm));
-    }
-    if (b.kind == 1) {
-        float x = (float)(M_PI * b.p0 / FV_C_LIGHT) * nu * rho;
-        return x < 1e-4f ? 1.0f - 0.125f * x * x : 2.0f * j1f(x) / x;
-    }
-    return 1.0f;
-}
-
 template <class G>
 __global__ void __launch_bounds__(256) k_prep(const double *__restrict__ sdir, const int *__restrict__ sidx,
                                               const int *__restrict__ nv_ptr, long n_src,
@@ -161,30 +144,8 @@ __global__ void __launch_bounds__(256) k_prep(const double *__restrict__ sdir, c
     if (i >= *nv_ptr) return;
     const double s0 = sdir[i], s1 = sdir[n_src + i], s2 = sdir[2 * n_src + i];
     const long n = sidx[i];
-    // strengths (Eq. 1-2); beam in the grid precision
-    const G rho = (G)sqrt(s0 * s0 + s1 * s1);
-    const G A = voltage<G>(g.beam, rho, (G)s2, (G)g.nu);
-    const G A2 = A * A;
-    auto ld = [&](int k) -> G {
-        size_t idx = ((size_t)k * n_src + n) * n_freq + f;
-        return flux_fp64 ? (G)((const double *)flux)[idx] : (G)((const float *)flux)[idx];
-    };
     cpx<G> c[4];
-    int np = 1;
-    if (!g.polarized) {
-        c[0] = cmk<G>(A2 * ld(0), (G)0);
-    } else {
-        np = 4;
-        const G I = ld(0), Q = ld(1), U = ld(2), V = ld(3);
-        G ca = (G)1, sa = (G)0;
-        if (rho > (G)0) { ca = (G)s1 / rho; sa = (G)s0 / rho; }
-        const G c2 = ca * ca - sa * sa, s2a = (G)2 * ca * sa;
-        const G Qr = Q * c2 - U * s2a, Ur = Q * s2a + U * c2;
-        c[0] = cmk<G>(A2 * (I + Qr), (G)0);
-        c[1] = cmk<G>(A2 * Ur, A2 * V);
-        c[2] = cmk<G>(A2 * Ur, -A2 * V);
-        c[3] = cmk<G>(A2 * (I - Qr), (G)0);
-    }
+    const int np = source_strengths<G>(g, s0, s1, s2, n, flux, flux_fp64, n_src, n_freq, f, c);
     // prephase: argument and reduction to [-pi, pi] in FP64, sincos in G
     const double st[3] = {s0 - g.dim[0].C, s1 - g.dim[1].C, s2 - g.dim[2].C};
     double ph = 0.0;
@@ -193,7 +154,9 @@ __global__ void __launch_bounds__(256) k_prep(const double *__restrict__ sdir, c
     G sp, cp;
     if (sizeof(G) == 4) { float a, b; sincosf((float)ph, &a, &b); sp = (G)a; cp = (G)b; }
     else { double a, b; sincos(ph, &a, &b); sp = (G)a; cp = (G)b; }
-    for (int p = 0; p < np; ++p) cs[(size_t)p * n_src + i] = cmul(c[p], cmk<G>(cp, sp));
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+        if (p < np) cs[(size_t)p * n_src + i] = cmul(c[p], cmk<G>(cp, sp));
     // grid coordinates, split in FP64
     for (int k = 0; k < 3; ++k) {
         if (k < g.d) {
@@ -235,8 +198,14 @@ constexpr int kPatchX = 8, kPatchY = 4;     // one warp
 constexpr int kTileX = 32, kTileY = 8;      // one CTA (4 x 2 patches)
 constexpr int kPatches = 8;
 
+// resident CTAs per SM the register allocation must allow without spills (fewer for the 32
+// accumulators of polarised 3-D tiles)
+template <int NP, int NZ> struct GatherMinBlocks {
+    static constexpr int value = NP * NZ >= 32 ? 2 : 4;
+};
+
 template <class G, int NP, int NZ>
-__global__ void __launch_bounds__(kGatherThreads) k_spread_gather(const int *__restrict__ offsets,
+__global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<NP, NZ>::value)) k_spread_gather(const int *__restrict__ offsets,
                                                                   const int *__restrict__ cell,
                                                                   const G *__restrict__ frac,
                                                                   const cpx<G> *__restrict__ cs, long n_src,
@@ -419,7 +388,7 @@ cudaError_t launch_spread_tile(const int *offsets, const int *cell, const G *fra
 constexpr int kScatX = 32, kScatY = 16, kScatRS = 40;
 
 template <class G, int NP>
-__global__ void __launch_bounds__(256) k_spread_scatter(const int *__restrict__ offsets, const int *__restrict__ cell,
+__global__ void __launch_bounds__(256, 4) k_spread_scatter(const int *__restrict__ offsets, const int *__restrict__ cell,
                                                         const G *__restrict__ frac, const cpx<G> *__restrict__ cs,
                                                         long n_src, SliceGeom g, TimeBin tb, double r0, double r1,
                                                         cpx<G> *__restrict__ grid)

@@ -25,6 +25,8 @@ FV_OK, FV_ERR_ARG, FV_ERR_OOM, FV_ERR_CUDA, FV_ERR_STATE, FV_ERR_TIMEOUT, FV_ERR
 FV_FP64, FV_MIXED = 0, 1
 SPREAD = {"auto": 0, "gather": 1, "scatter": 2, "atomic": 3}
 BEAMS = {"gauss": 0, "airy": 1, "uniform": 2}
+TRANSFORMS = {"auto": 0, "type3": 1, "lattice": 2}
+TRANSFORM_NAMES = {0: "auto", 1: "type3", 2: "lattice"}
 STATUS_NAMES = {0: "FV_OK", 1: "FV_ERR_ARG", 2: "FV_ERR_OOM", 3: "FV_ERR_CUDA", 4: "FV_ERR_STATE",
                 5: "FV_ERR_TIMEOUT", 6: "FV_ERR_UNSUPPORTED"}
 
@@ -42,14 +44,17 @@ class fv_opts(C.Structure):
                 ("latitude_rad", C.c_double), ("beam", C.c_int), ("beam_param", C.c_double * 3),
                 ("polarized", C.c_int), ("dims", C.c_int), ("upsampfac", C.c_double),
                 ("kernel_width", C.c_int), ("cuda_stream", C.c_void_p), ("device", C.c_int),
-                ("n_streams", C.c_int), ("spread_method", C.c_int), ("fft_max_radix", C.c_int)]
+                ("n_streams", C.c_int), ("spread_method", C.c_int), ("fft_max_radix", C.c_int),
+                ("transform", C.c_int), ("lattice_tol_m", C.c_double)]
 
 
 class fv_info(C.Structure):
     _fields_ = [("dims", C.c_int), ("kernel_width", C.c_int), ("beta", C.c_double),
                 ("upsampfac", C.c_double), ("n_unique", C.c_int), ("n_bl", C.c_int), ("n_src", C.c_long),
                 ("nf1_max", C.c_int * 3), ("nf2_max", C.c_int * 3), ("src_centre", C.c_double * 3),
-                ("src_halfwidth", C.c_double * 3), ("workspace_bytes", C.c_longlong)]
+                ("src_halfwidth", C.c_double * 3), ("workspace_bytes", C.c_longlong),
+                ("transform", C.c_int), ("lattice", C.c_int), ("lattice_modes", C.c_int * 2),
+                ("lattice_grid", C.c_int * 2), ("lattice_terms", C.c_int), ("lattice_basis", C.c_double * 4)]
 
 
 PROFILE_CLASSES = 12
@@ -63,6 +68,7 @@ class fv_profile_data(C.Structure):
 # Every function the header declares, with its C signature.
 SIGNATURES = {
     "fv_opts_default": (None, [C.POINTER(fv_opts)]),
+    "fv_lattice_detect": (C.c_int, [C.c_int, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
     "fv_plan": (C.c_int, [C.POINTER(fv_opts), C.POINTER(C.c_void_p)]),
     "fv_set_array": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
     "fv_set_sky": (C.c_int, [C.c_void_p, C.c_long, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int]),
@@ -157,6 +163,18 @@ def fv_set_sky(plan, ra: np.ndarray, dec: np.ndarray, flux) -> None:
                                      int(on_dev)), plan)
 
 
+def fv_lattice_detect(enu_m, tol_m: float = 0.0):
+    """(basis [a1_e, a1_n, a2_e, a2_n], index [n_ant][2], flat) if the antennas'
+    horizontal positions form a lattice within tol_m (0 = 1e-10 m), flat telling
+    whether the heights agree too; None otherwise (host only)."""
+    enu = np.ascontiguousarray(enu_m, dtype=np.float64)
+    n = len(enu)
+    basis = np.zeros(4)
+    index = np.zeros((max(n, 1), 2), dtype=np.int32)
+    ok = load_library().fv_lattice_detect(n, _ptr(enu), float(tol_m), _ptr(basis), _ptr(index))
+    return (basis, index[:n], ok == 1) if ok else None
+
+
 def fv_execute(plan, vis) -> None:
     """vis: numpy complex array (host) or CUDA tensor (device) of the full output shape."""
     on_dev = hasattr(vis, "is_cuda") and vis.is_cuda
@@ -181,7 +199,11 @@ def fv_get_info(plan) -> dict:
     return {"dims": i.dims, "kernel_width": i.kernel_width, "beta": i.beta, "upsampfac": i.upsampfac,
             "n_unique": i.n_unique, "n_bl": i.n_bl, "n_src": i.n_src, "nf1_max": list(i.nf1_max),
             "nf2_max": list(i.nf2_max), "src_centre": list(i.src_centre),
-            "src_halfwidth": list(i.src_halfwidth), "workspace_bytes": i.workspace_bytes}
+            "src_halfwidth": list(i.src_halfwidth), "workspace_bytes": i.workspace_bytes,
+            "transform": TRANSFORM_NAMES[i.transform], "lattice": bool(i.lattice),
+            "lattice_modes": list(i.lattice_modes), "lattice_grid": list(i.lattice_grid),
+            "lattice_terms": i.lattice_terms,
+            "lattice_basis": list(i.lattice_basis)}
 
 
 def fv_profile_enable(plan, enable: bool = True) -> None:
@@ -271,7 +293,7 @@ class Plan:
     @classmethod
     def create(cls, freqs_hz, lsts_rad, latitude_rad, beam="gauss", beam_param=(), precision=FV_FP64,
                eps=1e-10, polarized=False, dims=0, upsampfac=0.0, kernel_width=0, stream=None, device=-1,
-               n_streams=0, spread="auto", fft_max_radix=0):
+               n_streams=0, spread="auto", fft_max_radix=0, transform="auto", lattice_tol_m=0.0):
         o = fv_opts_default()
         freqs = np.ascontiguousarray(freqs_hz, dtype=np.float64)
         lsts = np.ascontiguousarray(lsts_rad, dtype=np.float64)
@@ -297,6 +319,8 @@ class Plan:
         o.n_streams = n_streams
         o.spread_method = SPREAD[spread]
         o.fft_max_radix = fft_max_radix
+        o.transform = TRANSFORMS[transform]
+        o.lattice_tol_m = lattice_tol_m
         h = fv_plan(o)
         return cls(h, len(freqs), len(lsts), 0, 4 if polarized else 1, precision)
 

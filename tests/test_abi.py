@@ -38,9 +38,10 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_defaults(lib):
-    assert lib.fv_abi_version() == 1
+    assert lib.fv_abi_version() == 2
     o = fv.fv_opts_default()
     assert o.precision == fv.FV_FP64 and o.eps == 1e-10 and o.upsampfac == 2.0 and o.device == -1
+    assert o.transform == 0 and o.lattice_tol_m == 0.0
     assert abs(o.beam_param[0] - np.radians(10)) < 1e-15 and o.beam_param[1] == 150e6
 
 
@@ -57,7 +58,8 @@ def _opts(**kw):
 @pytest.mark.parametrize("kw", [dict(eps=0.0), dict(eps=1e-15), dict(precision=1, eps=1e-9), dict(precision=7),
                                 dict(n_freq=0), dict(beam=9), dict(dims=4), dict(upsampfac=1.1),
                                 dict(kernel_width=40), dict(latitude_rad=2.0),
-                                dict(precision=1, eps=1e-6, upsampfac=1.25)])
+                                dict(precision=1, eps=1e-6, upsampfac=1.25), dict(transform=3),
+                                dict(lattice_tol_m=-1.0)])
 def test_invalid_options_rejected_before_device(lib, kw):
     o, keep = _opts(**kw)
     h = C.c_void_p()

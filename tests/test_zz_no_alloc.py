@@ -18,17 +18,18 @@ pytestmark = pytest.mark.gpu
 TOL = {fv.FV_FP64: 1e-9, fv.FV_MIXED: 2e-5}
 
 
-def _plan(prob, precision, eps):
-    p = fv.Plan.from_problem(prob, precision=precision, eps=eps)
+def _plan(prob, precision, eps, transform="auto"):
+    p = fv.Plan.from_problem(prob, precision=precision, eps=eps, transform=transform)
     p.set_sky(prob.sky.ra, prob.sky.dec, prob.sky.flux)
     return p
 
 
+@pytest.mark.parametrize("transform", ["type3", "lattice"])
 @pytest.mark.parametrize("precision,eps", [(fv.FV_MIXED, 1e-6), (fv.FV_FP64, 1e-11)])
-def test_static_scratch_matches_fv_execute_twice(precision, eps):
+def test_static_scratch_matches_fv_execute_twice(precision, eps, transform):
     torch = pytest.importorskip("torch")
     prob = W.config_hex127(seed=21, n_chan=3, n_time=2, n_point=1200, nside=8, radius=2)
-    p = _plan(prob, precision, eps)
+    p = _plan(prob, precision, eps, transform)
     cdt = torch.complex64 if precision == fv.FV_MIXED else torch.complex128
     ref = torch.empty(p.out_shape, dtype=cdt, device="cuda")
     fv.fv_execute(p.handle, ref)
@@ -46,11 +47,11 @@ def test_static_scratch_matches_fv_execute_twice(precision, eps):
 
 def test_static_scratch_refuses_oversize_plans_and_host_buffers():
     torch = pytest.importorskip("torch")
-    # 127 antennas at 200 MHz: about 100 MB of per-slice scratch > 64 MiB
+    # 127 antennas at 200 MHz on the type-3 route: about 100 MB of per-slice scratch > 64 MiB
     prob = W.config_hex127(seed=22, n_chan=1, n_time=1, n_point=500, nside=0)
     prob.freqs_hz = np.array([200e6])
     prob.sky.flux = prob.sky.flux[:, :, :1]
-    p = _plan(prob, fv.FV_MIXED, 1e-6)
+    p = _plan(prob, fv.FV_MIXED, 1e-6, "type3")
     out = torch.zeros(p.out_shape, dtype=torch.complex64, device="cuda")
     with pytest.raises(fv.FvError) as ei:
         fv.fv_execute_static(p.handle, out)
