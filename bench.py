@@ -319,11 +319,12 @@ def run_batch(args, rank, world, local, dist):
         fv.fv_profile_enable(p.handle, True)
     b.execute(use_graph=False)
     torch.cuda.synchronize(dev)
-    prof = {}
-    for p in plans:
+    prof, prof_by = {}, {"mixed": {}, "fp64": {}}
+    for p, q in zip(plans, precs):
         for k, v in fv.fv_profile_read(p.handle).items():
-            a = prof.setdefault(k, {"ms": 0.0, "launches": 0, "bytes": 0.0})
-            a["ms"] += v["ms"]; a["launches"] += v["launches"]; a["bytes"] += v["bytes"]
+            for tgt in (prof, prof_by["fp64" if q == fv.FV_FP64 else "mixed"]):
+                a = tgt.setdefault(k, {"ms": 0.0, "launches": 0, "bytes": 0.0})
+                a["ms"] += v["ms"]; a["launches"] += v["launches"]; a["bytes"] += v["bytes"]
         fv.fv_profile_enable(p.handle, False)
     ours = {k: v for k, v in prof.items() if k != "memset" and v["launches"] > 0}
     dom = max(ours, key=lambda k: ours[k]["ms"]) if ours else None
@@ -401,7 +402,11 @@ def run_batch(args, rank, world, local, dist):
             "rel_l2_vs_oracle_sample": err, "fp64_plain": plain,
             "kernels": {k: {"ms_per_step": v["ms"], "launches_per_step": v["launches"],
                             "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}
-                        for k, v in prof.items() if v["launches"] > 0}}
+                        for k, v in prof.items() if v["launches"] > 0},
+            "kernel_ms_by_precision": {q: {k: v["ms"] for k, v in d.items() if v["launches"] > 0}
+                                       for q, d in prof_by.items()},
+            "routes": {"lattice_slices": sum(1 for p in plans if p.info()["transform"] == "lattice"),
+                       "type3_slices": sum(1 for p in plans if p.info()["transform"] == "type3")}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     b.close()

@@ -149,8 +149,12 @@ cudaError_t launch_prep_lattice(const double *sdir, const int *sidx, const int *
 // SMEM: the copies are in shared memory (split real/imaginary planes) and are
 // added to the global grids at the end; otherwise the adds go straight to the
 // global grids.
+constexpr int kLatMaxTermsPerCta = 8;
+
+constexpr int kLatSpreadThreads = 512;
+
 template <class G, bool SMEM>
-__global__ void __launch_bounds__(256) k_spread_lattice(const int *__restrict__ nv_ptr, const int *__restrict__ cell,
+__global__ void __launch_bounds__(kLatSpreadThreads) k_spread_lattice(const int *__restrict__ nv_ptr, const int *__restrict__ cell,
                                                         const G *__restrict__ frac, const cpx<G> *__restrict__ cs,
                                                         long n_src, int w, G beta, int nfx, int nfy, int np, int K,
                                                         int kc, long per, cpx<G> *__restrict__ grid)
@@ -161,7 +165,7 @@ __global__ void __launch_bounds__(256) k_spread_lattice(const int *__restrict__ 
     if (start >= nv) return;                       // the same on every thread of the CTA
     const long end = min(nv, start + per);
     const int p = blockIdx.y;
-    const int q0 = blockIdx.z * kc, q1 = min(K, q0 + kc), nq = q1 - q0;
+    const int q0 = blockIdx.z * kc, q1 = min(K, q0 + kc), nq = q1 - q0;   // nq <= kLatMaxTermsPerCta
     const int ncell = nfx * nfy;
     G *sre = reinterpret_cast<G *>(smem_raw);      // [nq][ncell]
     G *sim = sre + (size_t)nq * ncell;
@@ -175,16 +179,40 @@ __global__ void __launch_bounds__(256) k_spread_lattice(const int *__restrict__ 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const G two_over_w = (G)2 / (G)w;
     const int ww = w * w;
+    // this lane's footprint cells in the first two rounds (w <= 8 needs no more)
+    const int jy0 = lane / w, jx0 = lane - jy0 * w;
+    const int l1 = lane + 32, jy1 = l1 / w, jx1 = l1 - jy1 * w;
     for (long i = start + warp; i < end; i += nwarps) {     // the same trip count on every lane of a warp
         const int cx = cell[i], cy = cell[n_src + i];
         const G fx = frac[i], fy = frac[n_src + i], u = frac[2 * n_src + i];
         const cpx<G> c = cs[(size_t)p * n_src + i];
         const G wxm = lane < w ? lat_es<G>(two_over_w * (fx + (G)lane), beta) : (G)0;
         const G wym = lane < w ? lat_es<G>(two_over_w * (fy + (G)lane), beta) : (G)0;
+        // T_q(u) for this CTA's terms, by the three-term recurrence
+        G tq[kLatMaxTermsPerCta];
+        {
+            G tm1 = (G)1, t = (G)1;
+            for (int q = 0; q < q0; ++q) {
+                const G tn = q == 0 ? u : (G)2 * u * t - tm1;
+                tm1 = t;
+                t = tn;
+            }
+#pragma unroll
+            for (int j = 0; j < kLatMaxTermsPerCta; ++j) {
+                tq[j] = t;
+                const G tn = (q0 + j) == 0 ? u : (G)2 * u * t - tm1;
+                tm1 = t;
+                t = tn;
+            }
+        }
         for (int base = 0; base < ww; base += 32) {
             const int idx = base + lane;
             const bool valid = idx < ww;
-            const int jy = valid ? idx / w : 0, jx = valid ? idx - jy * w : 0;
+            int jy, jx;
+            if (base == 0) { jy = jy0; jx = jx0; }
+            else if (base == 32) { jy = jy1; jx = jx1; }
+            else { jy = idx / w; jx = idx - jy * w; }
+            if (!valid) { jy = 0; jx = 0; }
             const G wt = __shfl_sync(0xffffffffu, wym, jy) * __shfl_sync(0xffffffffu, wxm, jx);
             if (valid) {
                 int lx = cx + jx, ly = cy + jy;
@@ -192,21 +220,18 @@ __global__ void __launch_bounds__(256) k_spread_lattice(const int *__restrict__ 
                 if (ly < 0) ly += nfy; else if (ly >= nfy) ly -= nfy;
                 const int o = ly * nfx + lx;
                 const cpx<G> cw = cscale(c, wt);
-                G tm1 = (G)1, tq = (G)1;           // T_{q-1}, T_q, starting at q = 0
-                for (int q = 0; q < q1; ++q) {
-                    if (q >= q0) {
+#pragma unroll
+                for (int j = 0; j < kLatMaxTermsPerCta; ++j) {
+                    if (j < nq) {
                         if (SMEM) {
-                            atomicAdd(&sre[(size_t)(q - q0) * ncell + o], cw.x * tq);
-                            atomicAdd(&sim[(size_t)(q - q0) * ncell + o], cw.y * tq);
+                            atomicAdd(&sre[(size_t)j * ncell + o], cw.x * tq[j]);
+                            atomicAdd(&sim[(size_t)j * ncell + o], cw.y * tq[j]);
                         } else {
-                            cpx<G> *gq = grid + ((size_t)q * np + p) * ncell;
-                            atomicAdd(&gq[o].x, cw.x * tq);
-                            atomicAdd(&gq[o].y, cw.y * tq);
+                            cpx<G> *gq = grid + ((size_t)(q0 + j) * np + p) * ncell;
+                            atomicAdd(&gq[o].x, cw.x * tq[j]);
+                            atomicAdd(&gq[o].y, cw.y * tq[j]);
                         }
                     }
-                    const G tn = q == 0 ? u : (G)2 * u * tq - tm1;
-                    tm1 = tq;
-                    tq = tn;
                 }
             }
         }
@@ -216,8 +241,8 @@ __global__ void __launch_bounds__(256) k_spread_lattice(const int *__restrict__ 
         for (int idx = threadIdx.x; idx < nq * ncell; idx += blockDim.x) {
             const G vr = sre[idx], vi = sim[idx];
             if (vr != (G)0 || vi != (G)0) {
-                const int q = q0 + idx / ncell, o = idx - (idx / ncell) * ncell;
-                cpx<G> *gq = grid + ((size_t)q * np + p) * ncell;
+                const int j = idx / ncell, o = idx - j * ncell;
+                cpx<G> *gq = grid + ((size_t)(q0 + j) * np + p) * ncell;
                 atomicAdd(&gq[o].x, vr);
                 atomicAdd(&gq[o].y, vi);
             }
@@ -242,13 +267,16 @@ cudaError_t launch_spread_lattice(const int *nv_ptr, const int *cell, const G *f
         e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
     }
+    // Terms per CTA: as many as keep the CTA's copy within 96 KB (so that two CTAs share an SM; every
+    // term block of a source repeats its kernel values and footprint), at least one if one term fits.  Source blocks: about four CTAs per SM in total,
+    // each of at least 512 sources (every CTA adds its whole copy to the grid at the end).
     const size_t plane = 2 * (size_t)lg.nf[0] * lg.nf[1] * sizeof(G);
-    const int kc = (int)std::min<size_t>((size_t)lg.K, kLatSmemMax / plane);   // terms per CTA (0: no room)
-    const bool smem_ok = kc >= 1;
-    const int kcu = smem_ok ? kc : lg.K;
+    int kc = (int)std::min<size_t>((size_t)std::min(lg.K, kLatMaxTermsPerCta), std::max<size_t>(96 * 1024 / plane, 1));
+    const bool smem_ok = plane * kc <= kLatSmemMax;
+    const int kcu = smem_ok ? kc : std::min(lg.K, kLatMaxTermsPerCta);
     const int nz = (lg.K + kcu - 1) / kcu;
-    // at least 1024 sources per CTA, at most a few CTAs per SM (each adds its whole copy at the end)
-    long nblk = std::max<long>(1, std::min<long>((n_src + 1023) / 1024, std::max(1L, 3L * sms[dev] / nz)));
+    const long slots = std::max(1L, 4L * sms[dev] / ((long)nz * g.n_pol));
+    long nblk = std::max<long>(1, std::min<long>((n_src + 511) / 512, slots));
     const long per = (n_src + nblk - 1) / nblk;
     nblk = (n_src + per - 1) / per;
     dim3 grid_dim((unsigned)nblk, (unsigned)g.n_pol, (unsigned)nz);
@@ -259,11 +287,11 @@ cudaError_t launch_spread_lattice(const int *nv_ptr, const int *cell, const G *f
             if (e != cudaSuccess) return e;
             attr[dev] = true;
         }
-        k_spread_lattice<G, true><<<grid_dim, 256, plane * kcu, st>>>(nv_ptr, cell, frac, cs, n_src, g.w,
+        k_spread_lattice<G, true><<<grid_dim, kLatSpreadThreads, plane * kcu, st>>>(nv_ptr, cell, frac, cs, n_src, g.w,
                                                                       (G)g.beta, lg.nf[0], lg.nf[1], g.n_pol, lg.K,
                                                                       kcu, per, grid);
     } else {
-        k_spread_lattice<G, false><<<grid_dim, 256, 0, st>>>(nv_ptr, cell, frac, cs, n_src, g.w, (G)g.beta,
+        k_spread_lattice<G, false><<<grid_dim, kLatSpreadThreads, 0, st>>>(nv_ptr, cell, frac, cs, n_src, g.w, (G)g.beta,
                                                               lg.nf[0], lg.nf[1], g.n_pol, lg.K, kcu, per, grid);
     }
     return cudaGetLastError();
@@ -306,8 +334,8 @@ cudaError_t launch_gather_lattice(const cpx<G> *band, const int *bln, int n_bl, 
 {
     const long n = (long)n_bl * n_pol;
     if (n <= 0) return cudaSuccess;
-    k_gather_lattice<G><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(band, bln, n_bl, n_pol, lg, wq, dx, dy, out,
-                                                                     out_fp64);
+    k_gather_lattice<G><<<(unsigned)((n + 63) / 64), 64, 0, st>>>(band, bln, n_bl, n_pol, lg, wq, dx, dy, out,
+                                                                   out_fp64);
     return cudaGetLastError();
 }
 

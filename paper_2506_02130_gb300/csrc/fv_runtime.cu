@@ -746,10 +746,8 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
         if (std::fabs(sigma - 2.0) < 1e-12)
             w = (int)std::ceil(std::log10(1.0 / o->eps) - 1e-12) + 1;   // Section 2.2 rule at sigma = 2
         else
-            // the estimate eps ~ exp(-pi w sqrt(1 - 1/sigma)) of the kernel's aliasing error, plus two
-            // points: the type-3 transform applies the kernel twice and divides by its transform twice, and
-            // at sigma = 1.25, eps = 1e-10 one extra point still left a relative L2 error of 1.04e-9 against
-            // the direct sum
+            // the estimate eps ~ exp(-pi w sqrt(1 - 1/sigma)) of the kernel's aliasing error, plus a margin
+            // of two points: the type-3 transform applies the kernel twice and divides by its transform twice
             w = (int)std::ceil(std::log(1.0 / o->eps) / (M_PI * std::sqrt(1.0 - 1.0 / sigma)) - 1e-12) + 2;
         w = std::max(2, w);
         if (w > 16) {
