@@ -245,7 +245,8 @@ struct LatGeom {
 };
 
 // Per slice: strengths (no prephase), the split grid coordinates
-// t_d = frac(x_d / 2 pi) nf_d of the visible sources, and u = 2 up - 1 (in frac[2]).
+// t_d = frac(x_d / 2 pi) nf_d of the visible sources, u = 2 up - 1 (in frac[2]), and the
+// kernel values of the footprints (after frac[0..3): [n_src][2w], x then y).
 template <class G>
 cudaError_t launch_prep_lattice(const double *sdir, const int *sidx, const int *nv_ptr, long n_src,
                                 const void *flux, int flux_fp64, int n_freq, int f, const SliceGeom &g,

@@ -128,6 +128,14 @@ __global__ void __launch_bounds__(256) k_prep_lattice(const double *__restrict__
         frac[(size_t)d * n_src + i] = (G)(l0 - gp);
     }
     frac[2 * (size_t)n_src + i] = (G)(2.0 * s2 - 1.0);   // Chebyshev argument of the height factor
+    // kernel values of the x and y footprints, once per source: kw[i][0..w) (x), kw[i][w..2w) (y)
+    G *kw = frac + 3 * (size_t)n_src + (size_t)i * 2 * g.w;
+    const G two_over_w = (G)2 / (G)g.w, beta = (G)g.beta;
+    const G fx = frac[i], fy = frac[(size_t)n_src + i];
+    for (int j = 0; j < g.w; ++j) {
+        kw[j] = lat_es<G>(two_over_w * (fx + (G)j), beta);
+        kw[g.w + j] = lat_es<G>(two_over_w * (fy + (G)j), beta);
+    }
 }
 
 template <class G>
@@ -177,17 +185,17 @@ __global__ void __launch_bounds__(kLatSpreadThreads) k_spread_lattice(const int 
         __syncthreads();
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const G two_over_w = (G)2 / (G)w;
     const int ww = w * w;
     // this lane's footprint cells in the first two rounds (w <= 8 needs no more)
     const int jy0 = lane / w, jx0 = lane - jy0 * w;
     const int l1 = lane + 32, jy1 = l1 / w, jx1 = l1 - jy1 * w;
     for (long i = start + warp; i < end; i += nwarps) {     // the same trip count on every lane of a warp
         const int cx = cell[i], cy = cell[n_src + i];
-        const G fx = frac[i], fy = frac[n_src + i], u = frac[2 * n_src + i];
+        const G u = frac[2 * n_src + i];
         const cpx<G> c = cs[(size_t)p * n_src + i];
-        const G wxm = lane < w ? lat_es<G>(two_over_w * (fx + (G)lane), beta) : (G)0;
-        const G wym = lane < w ? lat_es<G>(two_over_w * (fy + (G)lane), beta) : (G)0;
+        const G *kw = frac + 3 * (size_t)n_src + (size_t)i * 2 * w;   // kernel values from the preparation
+        const G wxm = lane < w ? kw[lane] : (G)0;
+        const G wym = lane < w ? kw[w + lane] : (G)0;
         // T_q(u) for this CTA's terms, by the three-term recurrence
         G tq[kLatMaxTermsPerCta];
         {

@@ -338,7 +338,7 @@ static fv_status prepare_lattice(fv_plan_s *p)
     nd.tiled = true;
     nd.n_src = std::max<long>(p->n_src, 1);
     nd.nb = 1;
-    nd.frac_per_src = 3 * gs;
+    nd.frac_per_src = (3 + 2 * (size_t)w) * gs;     // fx, fy, u and the 2w kernel values
     nd.cs_per_src = (size_t)np * es;
     free_workspaces(p->ws);
     p->need = nd;
