@@ -162,7 +162,8 @@ fv_status fv_set_array(fv_plan_t p, int n_ant, const double *enu_m, int n_bl, co
  * flux: [n_stokes][n_src][n_freq] Jy (n_stokes = 1: I; 4: I, Q, U, V), FP64 if
  * flux_is_fp64 else FP32.  With flux_on_device = 0 it is a host array copied
  * to the device; with flux_on_device = 1 it is a device pointer borrowed until
- * the next fv_set_sky or fv_destroy.  Diffuse maps enter as sources at pixel
+ * the next fv_set_sky or fv_destroy (its values may be rewritten between
+ * executions).  Diffuse maps enter as sources at pixel
  * centres with flux = brightness x pixel solid angle (Section 4.1).  Computes
  * the source extents over all times on the device (one synchronisation).
  * Errors: FV_ERR_ARG (n_src < 0, non-finite coordinate, n_stokes mismatch with

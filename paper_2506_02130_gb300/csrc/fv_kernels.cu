@@ -563,16 +563,16 @@ __global__ void __launch_bounds__(256) k_interp_zrow(const cpx<float> *__restric
 }
 
 // Interpolation with the per-target set-up spread over the threads.  A CTA
-// takes 64 targets: first threads 0-63 compute, one target each, the FP64
+// takes 32 targets: first threads 0-31 compute, one target each, the FP64
 // coordinates, the first footprint cell, the kernel values of x and y (and
 // for a short z axis the vector K(l_z) of the direct z sum), and the postphase
-// and deconvolution factor, into shared memory.  Then each of the 8 warps
+// and deconvolution factor, into shared memory.  Then each of the 4 warps
 // walks 8 of the targets, all lanes reading footprint values from the band
 // (ZROW: one footprint row of w cells x Nz z values per load round, one
 // 16-byte load per lane; 2-D: lanes over the w x w cells, n_pol values each),
 // and reduces; lane 0 writes the target's value.
-constexpr int kIbThreads = 256;
-constexpr int kIbTargets = 64;
+constexpr int kIbThreads = 128;
+constexpr int kIbTargets = 32;
 constexpr int kIbPerWarp = kIbTargets / (kIbThreads / 32);
 constexpr int kIbMaxW = 16;
 

@@ -136,3 +136,21 @@ def test_lattice_plans_in_a_batch_with_windows():
     assert rel_l2(got, full[2:5, 1:3]) <= 1e-6
     b.close()
     p.close()
+
+
+def test_fp64_lattice_borrowed_flux_rescaled_in_place():
+    """A borrowed device flux rewritten in place between executions (here x4) gives the linear
+    result on the FP64 lattice route."""
+    torch = pytest.importorskip("torch")
+    prob = _coplanar(69, n_chan=2, n_time=1)
+    p = fv.Plan.from_problem(prob, precision=fv.FV_FP64, eps=1e-11, transform="lattice")
+    flux = torch.tensor(prob.sky.flux, dtype=torch.float64, device="cuda")
+    p.set_sky(prob.sky.ra, prob.sky.dec, flux)
+    a = p.run()
+    flux.mul_(4.0)
+    torch.cuda.synchronize()
+    b = p.run()
+    assert rel_l2(b, 4.0 * a) <= 1e-12
+    ref = oracle_vis(OracleProblem.from_workload(prob))
+    assert rel_l2(a, ref) <= 1e-9
+    p.close()
