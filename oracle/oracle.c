@@ -33,7 +33,12 @@
  *    x = pi D nu sin(theta) / c; a uniform beam (A = 1) for analytic tests.
  *    The Jones matrix is A(theta) [[cos az, -sin az], [sin az, cos az]] with
  *    az measured east of north;
- *  - coherency C = [[I+Q, U+iV], [U-iV, I-Q]] exactly as printed in Eq. (2).
+ *  - coherency C = [[I+Q, U+iV], [U-iV, I-Q]] exactly as printed in Eq. (2);
+ *  - per-antenna beams (Section 2.2.3, Eq. 1 with A_i != A_j): antenna a has
+ *    J_a = A_{b(a)}(theta) R(az), so the product of baseline (i, j) is
+ *    J_i C J_j^dagger = A_{b(i)} A_{b(j)} R C R^dagger; evaluated as the
+ *    unit-beam strengths times the two voltages, per baseline (literal) or
+ *    folded into the antenna phasors (factored).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -68,6 +73,12 @@ typedef struct {
     int beam_kind;
     double beam_param[3];    /* GAUSS: fwhm_rad at ref, ref_hz; AIRY: dish diameter m */
     int polarized;           /* 0: one product (B I); 1: four products pq = 00, 01, 10, 11 */
+    /* per-antenna beams (Section 2.2.3): antenna a has beam beam_of_ant[a] of the n_beams beams
+     * (beam_kinds[k], beam_params[3k..3k+2]); beam_of_ant == NULL: every antenna has beam_kind. */
+    int n_beams;
+    const int *beam_kinds;
+    const double *beam_params;
+    const int *beam_of_ant;
 } oracle_problem;
 
 /* Equatorial (ra, dec) to topocentric East-North-Up unit vector at local
@@ -162,6 +173,12 @@ int oracle_vis(const oracle_problem *P, double *vis, int mode, int n_threads)
 #endif
     const int n_pol = P->polarized ? 4 : 1;
     const long NS = P->n_src;
+    const int multi = P->beam_of_ant != NULL && P->n_beams >= 1 && P->beam_kinds && P->beam_params;
+    if (multi)
+        for (int a = 0; a < P->n_ant; ++a)
+            if (P->beam_of_ant[a] < 0 || P->beam_of_ant[a] >= P->n_beams) return 1;
+    const int nbeam = multi ? P->n_beams : 1;
+    double *volt = (double *)malloc(sizeof(double) * nbeam * (NS > 0 ? NS : 1));   /* [v][beam] */
     double *dir = (double *)malloc(sizeof(double) * 3 * (NS > 0 ? NS : 1));
     double *str = (double *)malloc(sizeof(double) * 2 * n_pol * (NS > 0 ? NS : 1));
     long *vis_idx = (long *)malloc(sizeof(long) * (NS > 0 ? NS : 1));
@@ -169,8 +186,8 @@ int oracle_vis(const oracle_problem *P, double *vis, int mode, int n_threads)
     double *F = NULL;
     if (mode == ORACLE_FACTORED)
         F = (double *)malloc(sizeof(double) * 2 * (size_t)P->n_ant * BLK);
-    if (!dir || !str || !vis_idx || (mode == ORACLE_FACTORED && !F)) {
-        free(dir); free(str); free(vis_idx); free(F);
+    if (!dir || !str || !vis_idx || !volt || (mode == ORACLE_FACTORED && !F)) {
+        free(dir); free(str); free(vis_idx); free(F); free(volt);
         return 2;
     }
     for (int t = 0; t < P->n_time; ++t) {
@@ -191,8 +208,18 @@ int oracle_vis(const oracle_problem *P, double *vis, int mode, int n_threads)
             for (long v = 0; v < nv; ++v) {
                 double st[4];
                 stokes_of(P, vis_idx[v], f, st);
-                oracle_strength(P->beam_kind, P->beam_param, P->polarized, &dir[3 * v], nu, st,
-                                &str[2 * n_pol * v]);
+                if (!multi) {
+                    oracle_strength(P->beam_kind, P->beam_param, P->polarized, &dir[3 * v], nu, st,
+                                    &str[2 * n_pol * v]);
+                } else {
+                    /* unit-beam strengths; the voltages of the antennas' beams multiply them per baseline */
+                    double none[3] = {0.0, 0.0, 0.0};
+                    oracle_strength(ORACLE_BEAM_UNIFORM, none, P->polarized, &dir[3 * v], nu, st,
+                                    &str[2 * n_pol * v]);
+                    double theta = acos(dir[3 * v + 2] > 1.0 ? 1.0 : dir[3 * v + 2]);
+                    for (int k = 0; k < nbeam; ++k)
+                        volt[(size_t)v * nbeam + k] = oracle_voltage(P->beam_kinds[k], &P->beam_params[3 * k], theta, nu);
+                }
             }
             double *out = vis + (((size_t)f * P->n_time + t) * P->n_bl) * n_pol * 2;
             if (mode == ORACLE_LITERAL) {
@@ -201,10 +228,13 @@ int oracle_vis(const oracle_problem *P, double *vis, int mode, int n_threads)
                     const double *xi = &P->ant_enu[3 * P->pairs[2 * b]];
                     const double *xj = &P->ant_enu[3 * P->pairs[2 * b + 1]];
                     double bx = xi[0] - xj[0], by = xi[1] - xj[1], bz = xi[2] - xj[2];
+                    const int bi = multi ? P->beam_of_ant[P->pairs[2 * b]] : 0;
+                    const int bj = multi ? P->beam_of_ant[P->pairs[2 * b + 1]] : 0;
                     double acc[8] = {0};
                     for (long v = 0; v < nv; ++v) {
                         double ph = -k0 * (bx * dir[3 * v] + by * dir[3 * v + 1] + bz * dir[3 * v + 2]);
-                        double c = cos(ph), s = sin(ph);
+                        double g = multi ? volt[(size_t)v * nbeam + bi] * volt[(size_t)v * nbeam + bj] : 1.0;
+                        double c = g * cos(ph), s = g * sin(ph);
                         for (int p = 0; p < n_pol; ++p) {
                             double sr = str[2 * (n_pol * v + p)], si = str[2 * (n_pol * v + p) + 1];
                             acc[2 * p] += sr * c - si * s;
@@ -223,8 +253,9 @@ int oracle_vis(const oracle_problem *P, double *vis, int mode, int n_threads)
                         for (long v = 0; v < nb; ++v) {
                             const double *s = &dir[3 * (v0 + v)];
                             double ph = -k0 * (xa[0] * s[0] + xa[1] * s[1] + xa[2] * s[2]);
-                            F[2 * ((size_t)a * BLK + v)] = cos(ph);
-                            F[2 * ((size_t)a * BLK + v) + 1] = sin(ph);
+                            double g = multi ? volt[(size_t)(v0 + v) * nbeam + P->beam_of_ant[a]] : 1.0;
+                            F[2 * ((size_t)a * BLK + v)] = g * cos(ph);
+                            F[2 * ((size_t)a * BLK + v) + 1] = g * sin(ph);
                         }
                     }
 #pragma omp parallel for schedule(dynamic, 16)
@@ -249,7 +280,7 @@ int oracle_vis(const oracle_problem *P, double *vis, int mode, int n_threads)
             }
         }
     }
-    free(dir); free(str); free(vis_idx); free(F);
+    free(dir); free(str); free(vis_idx); free(F); free(volt);
     return 0;
 }
 

@@ -37,7 +37,9 @@ class _Problem(C.Structure):
                 ("n_freq", C.c_int), ("freq_hz", C.POINTER(C.c_double)),
                 ("n_time", C.c_int), ("lst_rad", C.POINTER(C.c_double)),
                 ("latitude_rad", C.c_double), ("beam_kind", C.c_int),
-                ("beam_param", C.c_double * 3), ("polarized", C.c_int)]
+                ("beam_param", C.c_double * 3), ("polarized", C.c_int),
+                ("n_beams", C.c_int), ("beam_kinds", C.POINTER(C.c_int)),
+                ("beam_params", C.POINTER(C.c_double)), ("beam_of_ant", C.POINTER(C.c_int))]
 
 
 def _load():
@@ -77,6 +79,9 @@ class OracleProblem:
     beam: str = "gauss"
     beam_param: tuple = ()
     polarized: bool = False
+    # per-antenna beams: [(kind, params), ...] and the beam index of every antenna (None: one beam)
+    beams: list | None = None
+    beam_of_ant: np.ndarray | None = None
 
     @classmethod
     def from_workload(cls, prob, pairs=None, freq_idx=None, time_idx=None, src_idx=None):
@@ -94,7 +99,8 @@ class OracleProblem:
         if time_idx is not None:
             lsts = lsts[time_idx]
         return cls(prob.ant_enu, prob.pairs if pairs is None else pairs, ra, dec, flux, freqs,
-                   lsts, prob.latitude_rad, prob.beam, tuple(prob.beam_param), prob.polarized)
+                   lsts, prob.latitude_rad, prob.beam, tuple(prob.beam_param), prob.polarized,
+                   getattr(prob, "beams", None), getattr(prob, "beam_of_ant", None))
 
 
 def oracle_vis(p: OracleProblem, mode: str = "factored", n_threads: int = 0) -> np.ndarray:
@@ -109,10 +115,20 @@ def oracle_vis(p: OracleProblem, mode: str = "factored", n_threads: int = 0) -> 
     lsts = np.ascontiguousarray(p.lsts_rad, dtype=np.float64)
     n_pol = 4 if p.polarized else 1
     bp = (C.c_double * 3)(*(list(p.beam_param) + [0.0] * (3 - len(p.beam_param))))
+    nb, kinds_p, params_p, boa_p = 0, None, None, None
+    if p.beam_of_ant is not None and p.beams:
+        kinds = np.ascontiguousarray([BEAMS[k] for k, _ in p.beams], dtype=np.int32)
+        params = np.ascontiguousarray([list(v) + [0.0] * (3 - len(v)) for _, v in p.beams], dtype=np.float64)
+        boa = np.ascontiguousarray(p.beam_of_ant, dtype=np.int32)
+        if len(boa) != len(ant):
+            raise ValueError("beam_of_ant needs one entry per antenna")
+        nb, kinds_p, params_p = len(kinds), kinds.ctypes.data_as(C.POINTER(C.c_int)), _p(params)
+        boa_p = boa.ctypes.data_as(C.POINTER(C.c_int))
+        keep = (kinds, params, boa)                      # alive for the call
     prob = _Problem(len(ant), _p(ant), len(pairs), pairs.ctypes.data_as(C.POINTER(C.c_int)),
                     len(ra), _p(ra), _p(dec), flux.shape[0], _p(flux), len(freqs), _p(freqs),
                     len(lsts), _p(lsts), float(p.latitude_rad), BEAMS[p.beam], bp,
-                    1 if p.polarized else 0)
+                    1 if p.polarized else 0, nb, kinds_p, params_p, boa_p)
     out = np.zeros((len(freqs), len(lsts), len(pairs), n_pol, 2), dtype=np.float64)
     rc = lib.oracle_vis(C.byref(prob), _p(out), 0 if mode == "literal" else 1, int(n_threads))
     if rc != 0:

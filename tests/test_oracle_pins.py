@@ -272,3 +272,78 @@ def test_lattice_sky_reduces_to_numpy_fft2(N, G, lst):
     for mode in ("literal", "factored"):
         v = oracle_vis(op, mode)[0, 0, :, 0]
         assert rel_l2(v, L["expected"]) <= 1e-13
+
+
+# ---------------------------------------------------------------- per-antenna beams (Section 2.2.3)
+def _two_beam_problem(polarized=False, seed=11):
+    rng = np.random.default_rng(seed)
+    ant = W.hex_array(2)
+    n = len(ant)
+    pairs = W.cross_pairs(n)
+    lst = 0.9
+    ra, dec = W.visible_hemisphere(60, rng, lst, LAT)
+    nst = 4 if polarized else 1
+    flux = rng.uniform(0.5, 2.0, (nst, 60, 2))
+    if polarized:
+        flux[1:] *= 0.2
+    beams = [("gauss", (math.radians(30.0), 150e6)), ("gauss", (math.radians(8.0), 150e6)),
+             ("airy", (6.0,))] if not polarized else [("airy", (14.0,)), ("airy", (5.0,))]
+    boa = rng.integers(0, len(beams), n)
+    return OracleProblem(ant, pairs, ra, dec, flux, np.array([120e6, 180e6]), np.array([lst]), LAT,
+                         "gauss", (math.radians(10.0), 150e6), polarized, beams, boa)
+
+
+def test_per_antenna_beams_one_beam_equals_the_shared_beam():
+    p = _two_beam_problem()
+    p.beams = [("gauss", (math.radians(10.0), 150e6))]
+    p.beam_of_ant = np.zeros(len(p.ant_enu), dtype=int)
+    v1 = oracle_vis(p)
+    p.beam_of_ant = None
+    v0 = oracle_vis(p)
+    assert rel_l2(v1, v0) <= 1e-14
+
+
+def test_per_antenna_beams_single_source_is_the_product_of_the_two_voltages():
+    """One source: V_ij = A_b(i)(theta) A_b(j)(theta) I exp(-2 pi i nu b.s / c), with the voltage of
+    each antenna's own beam (a swapped or shared assignment fails)."""
+    p = _two_beam_problem()
+    p.ra, p.dec, p.flux = p.ra[:1], p.dec[:1], p.flux[:, :1]
+    v = oracle_vis(p, "literal")
+    s = oracle_enu(p.ra[0], p.dec[0], p.lsts_rad[0], LAT)
+    theta = math.acos(s[2])
+    for f, nu in enumerate(p.freqs_hz):
+        A = [oracle_voltage(k, par, theta, nu) for k, par in p.beams]
+        for b, (i, j) in enumerate(p.pairs):
+            bvec = p.ant_enu[i] - p.ant_enu[j]
+            want = (A[p.beam_of_ant[i]] * A[p.beam_of_ant[j]] * p.flux[0, 0, f]
+                    * np.exp(-2j * math.pi * nu * np.dot(bvec, s) / C))
+            assert abs(v[f, 0, b, 0] - want) <= 1e-13 * abs(p.flux[0, 0, f])
+
+
+def test_per_antenna_beams_hermitian_and_factored_equals_literal():
+    p = _two_beam_problem()
+    lit = oracle_vis(p, "literal")
+    fac = oracle_vis(p, "factored")
+    assert rel_l2(fac, lit) <= 1e-13
+    q = OracleProblem(**{**p.__dict__, "pairs": p.pairs[:, ::-1].copy()})
+    assert np.array_equal(oracle_vis(q, "literal"), np.conj(lit))
+
+
+def test_per_antenna_beams_polarised_is_Ji_C_Jj_dagger():
+    """Polarised single source with different Airy dishes: the four products are J_i C J_j^dagger,
+    checked against numpy 2x2 matrix products (J = A R(az))."""
+    p = _two_beam_problem(polarized=True)
+    p.ra, p.dec, p.flux = p.ra[:1], p.dec[:1], p.flux[:, :1]
+    v = oracle_vis(p, "literal")
+    s = oracle_enu(p.ra[0], p.dec[0], p.lsts_rad[0], LAT)
+    theta, az = math.acos(s[2]), math.atan2(s[0], s[1])
+    R = np.array([[math.cos(az), -math.sin(az)], [math.sin(az), math.cos(az)]])
+    for f, nu in enumerate(p.freqs_hz):
+        I, Q, U, V = p.flux[:, 0, f]
+        Cm = np.array([[I + Q, U + 1j * V], [U - 1j * V, I - Q]])
+        A = [oracle_voltage(k, par, theta, nu) for k, par in p.beams]
+        for b, (i, j) in enumerate(p.pairs):
+            Ji, Jj = A[p.beam_of_ant[i]] * R, A[p.beam_of_ant[j]] * R
+            M = Ji @ Cm @ Jj.conj().T
+            ph = np.exp(-2j * math.pi * nu * np.dot(p.ant_enu[i] - p.ant_enu[j], s) / C)
+            np.testing.assert_allclose(v[f, 0, b], M.ravel() * ph, rtol=0, atol=1e-12 * I)
