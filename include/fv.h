@@ -158,6 +158,20 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out);
  * Errors: FV_ERR_ARG (n_ant < 1, index out of range, non-finite position). */
 fv_status fv_set_array(fv_plan_t p, int n_ant, const double *enu_m, int n_bl, const int *pairs);
 
+/* Per-antenna beams (Section 2.2.3).  Antenna a (of the array given to
+ * fv_set_array) gets beam beam_of_antenna[a] of n_beams analytic beams
+ * (kinds[k] a fv_beam_kind, params[3k..3k+2] its parameters as in
+ * fv_opts.beam_param).  Baseline (i, j) then sees J_i C J_j^dagger with
+ * J_a = A_{b(a)}(theta) R(az), and every unordered pair of beams present among
+ * the baselines is one transform per slice: at most n_beams (n_beams + 1) / 2
+ * transforms, each over its own baselines.  n_beams <= 0 or beam_of_antenna =
+ * NULL returns to the single beam of fv_opts.  Host arrays, copied.  A new
+ * fv_set_array with another antenna count also returns to the single beam.
+ * Errors: FV_ERR_STATE (before fv_set_array), FV_ERR_ARG (n_beams > 16, bad
+ * kind or parameter, index out of range). */
+fv_status fv_set_beams(fv_plan_t p, int n_beams, const int *kinds, const double *params,
+                       const int *beam_of_antenna);
+
 /* Set the sky: n_src point sources at (ra_rad, dec_rad), host arrays, copied.
  * flux: [n_stokes][n_src][n_freq] Jy (n_stokes = 1: I; 4: I, Q, U, V), FP64 if
  * flux_is_fp64 else FP32.  With flux_on_device = 0 it is a host array copied
@@ -207,6 +221,7 @@ typedef struct {
     int lattice_grid[2];  /* lattice route: grid (and FFT) points per axis */
     int lattice_terms;    /* lattice route: Chebyshev terms K of the height factor (1 for a flat array) */
     double lattice_basis[4];  /* a1_east, a1_north, a2_east, a2_north (m) */
+    int beam_groups;      /* transforms per slice: unordered beam pairs among the baselines (1: one beam) */
 } fv_info;
 
 fv_status fv_get_info(fv_plan_t p, fv_info *info);

@@ -82,6 +82,8 @@ struct SliceGeom {
     int polarized;
     int n_stokes;
     BeamParams beam;
+    BeamParams beam2;   // per-antenna beams (Section 2.2.3): the second antenna's beam of the baseline
+    int two_beams;      // 0: the product is beam x beam; 1: beam x beam2
     DimGeom dim[3];
 };
 
@@ -116,8 +118,9 @@ template <> __device__ __forceinline__ float voltage<float>(const BeamParams &b,
 }
 
 // Strengths of one source in one slice (Eq. 1-2 with the analytic beams): the
-// unpolarised product A^2 I, or the four products of J C J^dagger with
-// J = A R(az) for Stokes IQUV.  Beam in the grid precision G.  Returns n_pol.
+// unpolarised product A_i A_j I, or the four products of J_i C J_j^dagger with
+// J = A R(az) for Stokes IQUV (A_i = A_j = A for one shared beam).  Beam in the
+// grid precision G.  Returns n_pol.
 template <class G>
 __device__ __forceinline__ int source_strengths(const SliceGeom &g, double s0, double s1, double s2, long n,
                                                 const void *flux, int flux_fp64, long n_src, int n_freq, int f,
@@ -125,7 +128,8 @@ __device__ __forceinline__ int source_strengths(const SliceGeom &g, double s0, d
 {
     const G rho = (G)sqrt(s0 * s0 + s1 * s1);
     const G A = voltage<G>(g.beam, rho, (G)s2, (G)g.nu);
-    const G A2 = A * A;
+    // A_i A_j: the two antennas' voltages (one shared beam: A^2)
+    const G A2 = g.two_beams ? A * voltage<G>(g.beam2, rho, (G)s2, (G)g.nu) : A * A;
     auto ld = [&](int k) -> G {
         size_t idx = ((size_t)k * n_src + n) * n_freq + f;
         return flux_fp64 ? (G)((const double *)flux)[idx] : (G)((const float *)flux)[idx];
@@ -260,10 +264,11 @@ cudaError_t launch_spread_lattice(const int *nv_ptr, const int *cell, const G *f
 // Visibilities of the baselines from the band [b_y][b_x][q][pol] of modes m = -n
 // (b_d = H_d - n_d): sum_q wq[bl][q] x band, times the deconvolution tables
 // dx[n_x + H_x] dy[n_y + H_y] (wq = nullptr: K = 1 and weight 1).
+// bl_list: the n_bl baselines to evaluate (one beam group), or nullptr for baselines 0..n_bl-1.
 template <class G>
-cudaError_t launch_gather_lattice(const cpx<G> *band, const int *bln, int n_bl, int n_pol, const LatGeom &lg,
-                                  const cpx<double> *wq, const double *dx, const double *dy, void *out, int out_fp64,
-                                  cudaStream_t st);
+cudaError_t launch_gather_lattice(const cpx<G> *band, const int *bln, const int *bl_list, int n_bl, int n_pol,
+                                  const LatGeom &lg, const cpx<double> *wq, const double *dx, const double *dy,
+                                  void *out, int out_fp64, cudaStream_t st);
 // Per-baseline height-term weights of one channel: wq[bl][q] = e^{-i beta} eps_q (-i)^q J_q(beta),
 // beta = kappa b_up[bl] / 2 (FP64 series for J_q).
 cudaError_t launch_lattice_wterms(const double *b_up, int n_bl, int K, double kappa, cpx<double> *wq,

@@ -190,7 +190,7 @@ __device__ __forceinline__ int source_strengths(const SliceGeom &g, const void *
 {
     double rho = sqrt(s0 * s0 + s1 * s1);
     double A = voltage_beam(g.beam, rho, s2, g.nu);
-    double A2 = A * A;
+    double A2 = g.two_beams ? A * voltage_beam(g.beam2, rho, s2, g.nu) : A * A;
     double I = load_flux(flux, flux_fp64, (size_t)n * n_freq + f);
     if (!g.polarized) {
         c[0] = cmk<double>(A2 * I, 0.0);

@@ -306,14 +306,17 @@ cudaError_t launch_spread_lattice(const int *nv_ptr, const int *cell, const G *f
 }
 
 template <class G>
-__global__ void k_gather_lattice(const cpx<G> *__restrict__ band, const int *__restrict__ bln, int n_bl, int n_pol,
-                                 LatGeom lg, const cpx<double> *__restrict__ wq, const double *__restrict__ dx,
+__global__ void k_gather_lattice(const cpx<G> *__restrict__ band, const int *__restrict__ bln,
+                                 const int *__restrict__ bl_list, int n_bl, int n_pol, LatGeom lg,
+                                 const cpx<double> *__restrict__ wq, const double *__restrict__ dx,
                                  const double *__restrict__ dy, void *out, int out_fp64)
 {
-    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (i >= (long)n_bl * n_pol) return;
-    const long b = i / n_pol;
-    const int p = (int)(i - b * n_pol);
+    const long j = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (j >= (long)n_bl * n_pol) return;
+    const long jb = j / n_pol;
+    const int p = (int)(j - jb * n_pol);
+    const long b = bl_list ? bl_list[jb] : jb;          // baselines of one beam group, or all
+    const long i = b * n_pol + p;
     const int nx = bln[2 * b], ny = bln[2 * b + 1];
     const int Bx = 2 * lg.H[0] + 1, K = lg.K;
     const cpx<G> *cellp = band + (((size_t)(lg.H[1] - ny) * Bx + (lg.H[0] - nx)) * K) * n_pol + p;
@@ -336,14 +339,14 @@ __global__ void k_gather_lattice(const cpx<G> *__restrict__ band, const int *__r
 }
 
 template <class G>
-cudaError_t launch_gather_lattice(const cpx<G> *band, const int *bln, int n_bl, int n_pol, const LatGeom &lg,
-                                  const cpx<double> *wq, const double *dx, const double *dy, void *out, int out_fp64,
-                                  cudaStream_t st)
+cudaError_t launch_gather_lattice(const cpx<G> *band, const int *bln, const int *bl_list, int n_bl, int n_pol,
+                                  const LatGeom &lg, const cpx<double> *wq, const double *dx, const double *dy,
+                                  void *out, int out_fp64, cudaStream_t st)
 {
     const long n = (long)n_bl * n_pol;
     if (n <= 0) return cudaSuccess;
-    k_gather_lattice<G><<<(unsigned)((n + 63) / 64), 64, 0, st>>>(band, bln, n_bl, n_pol, lg, wq, dx, dy, out,
-                                                                   out_fp64);
+    k_gather_lattice<G><<<(unsigned)((n + 63) / 64), 64, 0, st>>>(band, bln, bl_list, n_bl, n_pol, lg, wq, dx, dy,
+                                                                   out, out_fp64);
     return cudaGetLastError();
 }
 
@@ -419,11 +422,11 @@ template cudaError_t launch_spread_lattice<float>(const int *, const int *, cons
 template cudaError_t launch_spread_lattice<double>(const int *, const int *, const double *, const cpx<double> *,
                                                    long, const SliceGeom &, const LatGeom &, cpx<double> *,
                                                    cudaStream_t);
-template cudaError_t launch_gather_lattice<float>(const cpx<float> *, const int *, int, int, const LatGeom &,
-                                                  const cpx<double> *, const double *, const double *, void *, int,
-                                                  cudaStream_t);
-template cudaError_t launch_gather_lattice<double>(const cpx<double> *, const int *, int, int, const LatGeom &,
-                                                   const cpx<double> *, const double *, const double *, void *, int,
-                                                   cudaStream_t);
+template cudaError_t launch_gather_lattice<float>(const cpx<float> *, const int *, const int *, int, int,
+                                                  const LatGeom &, const cpx<double> *, const double *,
+                                                  const double *, void *, int, cudaStream_t);
+template cudaError_t launch_gather_lattice<double>(const cpx<double> *, const int *, const int *, int, int,
+                                                   const LatGeom &, const cpx<double> *, const double *,
+                                                   const double *, void *, int, cudaStream_t);
 
 }  // namespace fv

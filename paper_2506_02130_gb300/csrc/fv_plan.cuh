@@ -32,7 +32,20 @@ struct fv_plan_s {
     int nq = 0;
     double *d_glx = nullptr, *d_glw = nullptr;
 
-    // array
+    // array (host copies kept so that fv_set_beams can regroup the baselines)
+    std::vector<double> enu_h;        // [n_ant][3]
+    std::vector<int> pairs_h;         // [n_bl][2]
+    // per-antenna beams (Section 2.2.3): empty beams = every antenna has opts.beam
+    std::vector<BeamParams> beams;
+    std::vector<int> beam_of_ant;
+    // baselines grouped by the unordered pair of their antennas' beams: group g has unique targets
+    // [u0, u1) and baselines d_grp_bl[bl0, bl1) (one group covering everything without per-antenna beams)
+    struct BeamGroup {
+        int a = 0, b = 0;
+        int u0 = 0, u1 = 0, bl0 = 0, bl1 = 0;
+    };
+    std::vector<BeamGroup> groups;
+    int *d_grp_bl = nullptr;
     bool have_array = false;
     int n_ant = 0, n_bl = 0, n_u = 0, d = 2;
     std::vector<double> bu;          // [n_u][3]

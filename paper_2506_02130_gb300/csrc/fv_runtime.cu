@@ -419,7 +419,7 @@ static fv_status prepare(fv_plan_s *p)
     // tables and workspaces of the previous one
     std::vector<long> sig = {(long)p->n_src, (long)p->n_pol, (long)p->n_streams, (long)p->spread_req, (long)p->d,
                              (long)grid_e, (long)bufA_e, (long)bufB_e, (long)p->lat_ok, (long)p->lat_H[0],
-                             (long)p->lat_H[1]};
+                             (long)p->lat_H[1], (long)p->n_u, (long)p->n_bl};
     for (int k = 0; k < 4; ++k) {
         long long bits;
         std::memcpy(&bits, &p->lat_basis[k], sizeof(bits));
@@ -477,6 +477,22 @@ static fv_status prepare(fv_plan_s *p)
     return FV_OK;
 }
 
+// Slice geometry of channel f at time t for beam group gr: the group's two beams (Section 2.2.3;
+// one shared beam: opts.beam and A^2).
+static SliceGeom slice_geom_for(const fv_plan_s *p, int f, int t, const fv_plan_s::BeamGroup &gr)
+{
+    SliceGeom g = p->gf[f];
+    std::memcpy(g.R, &p->Rt[(size_t)t * 9], 9 * sizeof(double));
+    if (!p->beams.empty()) {
+        g.beam = p->beams[gr.a];
+        g.beam2 = p->beams[gr.b];
+        g.two_beams = gr.a != gr.b;
+    } else {
+        g.two_beams = 0;
+    }
+    return g;
+}
+
 // Slices of a lattice array (Section 2.2.1): one-bin time binning (rotation and horizon cut), then per
 // slice strengths and periodic grid coordinates, spreading, the two FFT passes without padding, and the
 // per-baseline mode lookup with deconvolution.
@@ -509,36 +525,42 @@ static fv_status run_slices_lattice(fv_plan_s *p, fv_plan_s::Workspace &wk, cuda
             CK(prof_end(p, (double)p->n_src * 80.0));
             t_binned = t;
         }
-        SliceGeom g = p->gf[f];
-        std::memcpy(g.R, &p->Rt[(size_t)t * 9], 9 * sizeof(double));
-        G *frac = (G *)wk.frac;
-        cpx<G> *cs = (cpx<G> *)wk.cs;
-        CK(prof_begin(p, PC_PREP, st));
-        CK(launch_prep_lattice<G>(wk.sdir, wk.sidx, wk.offsets + 1, p->n_src, p->flux, p->flux_fp64, nf, f, g, lg,
-                                  wk.cell, frac, cs, st));
-        CK(prof_end(p, nvis * (24.0 + 4.0 + p->n_stokes * (p->flux_fp64 ? 8.0 : 4.0) + 8.0 + 2.0 * sizeof(G) +
-                               np * es)));
-        CK(prof_begin(p, PC_MEMSET, st));
-        CK(cudaMemsetAsync(grid, 0, gel * sizeof(cpx<G>), st));
-        CK(prof_end(p, gel * es));
-        CK(prof_begin(p, PC_SPREAD, st));
-        CK(launch_spread_lattice<G>(wk.offsets + 1, wk.cell, frac, cs, p->n_src, g, lg, grid, st));
-        CK(prof_end(p, nvis * (8.0 + 3.0 * sizeof(G) + np * es) + gel * es));
-        const long r1 = (long)lg.K * np * lg.nf[1];
-        CK(prof_begin(p, PC_FFT_X, st));
-        CK(launch_fft_pass<G>(grid, A, r1, p->lat_dim[0], pre, tw, st));
-        CK(prof_end(p, (double)r1 * (lg.nf[0] + Bx) * es));
-        const long r2 = (long)Bx * lg.K * np;
-        CK(prof_begin(p, PC_FFT_Y, st));
-        CK(launch_fft_pass<G>(A, Bb, r2, p->lat_dim[1], pre + lg.nf[0], tw + lg.nf[0], st));
-        CK(prof_end(p, (double)r2 * (lg.nf[1] + By) * es));
-        const int ntm = om.nt > 0 ? om.nt : nt;
-        char *out = vis + ((size_t)(f - om.f0) * ntm + (t - om.t0)) * slice_bytes;
-        CK(prof_begin(p, PC_INTERP, st));
-        const cpx<double> *wq = p->d_lat_wq ? p->d_lat_wq + (size_t)f * p->n_bl * lg.K : nullptr;
-        CK(launch_gather_lattice<G>(Bb, p->d_bln, p->n_bl, np, lg, wq, p->d_lat_dec, p->d_lat_dec + Bx, out,
-                                    p->precision == FV_FP64, st));
-        CK(prof_end(p, (double)p->n_bl * (8.0 + lg.K * (np * es + (wq ? 16.0 : 0.0))) + (double)slice_bytes));
+        // one set of transforms per beam group (Section 2.2.3), evaluated at the group's baselines
+        const bool single = p->groups.size() == 1;
+        for (const auto &gr : p->groups) {
+            const int nbl = gr.bl1 - gr.bl0;
+            if (nbl <= 0) continue;
+            SliceGeom g = slice_geom_for(p, f, t, gr);
+            G *frac = (G *)wk.frac;
+            cpx<G> *cs = (cpx<G> *)wk.cs;
+            CK(prof_begin(p, PC_PREP, st));
+            CK(launch_prep_lattice<G>(wk.sdir, wk.sidx, wk.offsets + 1, p->n_src, p->flux, p->flux_fp64, nf, f, g, lg,
+                                      wk.cell, frac, cs, st));
+            CK(prof_end(p, nvis * (24.0 + 4.0 + p->n_stokes * (p->flux_fp64 ? 8.0 : 4.0) + 8.0 + 2.0 * sizeof(G) +
+                                   np * es)));
+            CK(prof_begin(p, PC_MEMSET, st));
+            CK(cudaMemsetAsync(grid, 0, gel * sizeof(cpx<G>), st));
+            CK(prof_end(p, gel * es));
+            CK(prof_begin(p, PC_SPREAD, st));
+            CK(launch_spread_lattice<G>(wk.offsets + 1, wk.cell, frac, cs, p->n_src, g, lg, grid, st));
+            CK(prof_end(p, nvis * (8.0 + 3.0 * sizeof(G) + np * es) + gel * es));
+            const long r1 = (long)lg.K * np * lg.nf[1];
+            CK(prof_begin(p, PC_FFT_X, st));
+            CK(launch_fft_pass<G>(grid, A, r1, p->lat_dim[0], pre, tw, st));
+            CK(prof_end(p, (double)r1 * (lg.nf[0] + Bx) * es));
+            const long r2 = (long)Bx * lg.K * np;
+            CK(prof_begin(p, PC_FFT_Y, st));
+            CK(launch_fft_pass<G>(A, Bb, r2, p->lat_dim[1], pre + lg.nf[0], tw + lg.nf[0], st));
+            CK(prof_end(p, (double)r2 * (lg.nf[1] + By) * es));
+            const int ntm = om.nt > 0 ? om.nt : nt;
+            char *out = vis + ((size_t)(f - om.f0) * ntm + (t - om.t0)) * slice_bytes;
+            CK(prof_begin(p, PC_INTERP, st));
+            const cpx<double> *wq = p->d_lat_wq ? p->d_lat_wq + (size_t)f * p->n_bl * lg.K : nullptr;
+            CK(launch_gather_lattice<G>(Bb, p->d_bln, single ? nullptr : p->d_grp_bl + gr.bl0, nbl, np, lg, wq,
+                                        p->d_lat_dec, p->d_lat_dec + Bx, out,
+                                        p->precision == FV_FP64, st));
+            CK(prof_end(p, (double)nbl * (8.0 + lg.K * (np * es + (wq ? 16.0 : 0.0))) + (double)slice_bytes));
+        }
     }
     return FV_OK;
 }
@@ -582,60 +604,66 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
             CK(prof_end(p, (double)p->n_src * 80.0 + nb * 12.0));
             t_binned = t;
         }
-        SliceGeom g = p->gf[f];
-        std::memcpy(g.R, &p->Rt[(size_t)t * 9], 9 * sizeof(double));
-        const DimGeom *D = g.dim;
-        const size_t gel = (size_t)p->n_pol * D[0].nf1 * D[1].nf1 * D[2].nf1;
-        if (p->tiled) {
-            G *frac = (G *)wk.frac;
-            cpx<G> *cs = (cpx<G> *)wk.cs;
-            CK(prof_begin(p, PC_PREP, st));
-            CK(launch_prep<G>(wk.sdir, wk.sidx, wk.offsets + nb, p->n_src, p->flux, p->flux_fp64, nf, f, g, wk.cell,
-                              frac, cs, st));
-            CK(prof_end(p, prep_bytes));
-            const double r0 = D[0].qscale / p->qscale_top[0], r1 = D[1].qscale / p->qscale_top[1];
-            CK(prof_begin(p, PC_SPREAD, st));
-            if (p->spread_method == FV_SPREAD_SCATTER)
-                CK(launch_spread_scatter<G>(wk.offsets, wk.cell, frac, cs, p->n_src, g, tb, r0, r1, grid, st));
-            else
-                CK(launch_spread_tile<G>(wk.offsets, wk.cell, frac, cs, p->n_src, g, tb, r0, r1, grid, st));
-            CK(prof_end(p, spread_in_bytes + gel * es));
-        } else {
-            CK(prof_begin(p, PC_MEMSET, st));
-            CK(cudaMemsetAsync(grid, 0, gel * sizeof(cpx<G>), st));
-            CK(prof_end(p, gel * es));
-            CK(prof_begin(p, PC_SPREAD, st));
-            CK(launch_spread_direct<G>(p->d_e, p->n_src, p->flux, p->flux_fp64, nf, f, g, grid, st));
-            CK(prof_end(p, src_bytes + gel * es));
-        }
-        const size_t o0 = (size_t)f * 3;
-        // pass 1 along x: rows (pol, z, y)
-        const long r1 = (long)p->n_pol * D[2].nf1 * D[1].nf1;
-        CK(prof_begin(p, PC_FFT_X, st));
-        CK(launch_fft_pass<G>(grid, A, r1, D[0], pre + p->pre_off[o0], tw + p->tw_off[o0], st));
-        CK(prof_end(p, (double)r1 * (D[0].nf1 + D[0].B) * es));
-        // pass 2 along y: rows (bx, pol, z)
-        const long r2 = (long)D[0].B * p->n_pol * D[2].nf1;
-        CK(prof_begin(p, PC_FFT_Y, st));
-        CK(launch_fft_pass<G>(A, Bb, r2, D[1], pre + p->pre_off[o0 + 1], tw + p->tw_off[o0 + 1], st));
-        CK(prof_end(p, (double)r2 * (D[1].nf1 + D[1].B) * es));
-        if (p->d == 2 || D[2].nf1 <= FV_ZDIRECT_MAX) {
-            // z (if any) summed directly inside the interpolation: no z pass
-            const double wd = (double)p->w * p->w * D[2].nf1;
-            CK(prof_begin(p, PC_INTERP, st));
-            CK(launch_interp_zdirect<G>(Bb, p->d_bu, p->n_u, p->d_dec, g, pre + p->pre_off[o0 + 2],
-                                        tw + p->tw_off[o0 + 2], wk.Vu, st));
-            CK(prof_end(p, (double)p->n_u * (wd * p->n_pol * es + 4 * sizeof(double) + p->n_pol * 16.0)));
-        } else {
-            // pass 3 along z: rows (by, bx, pol)
-            const long r3 = (long)D[1].B * D[0].B * p->n_pol;
-            CK(prof_begin(p, PC_FFT_Z, st));
-            CK(launch_fft_pass<G>(Bb, A, r3, D[2], pre + p->pre_off[o0 + 2], tw + p->tw_off[o0 + 2], st));
-            CK(prof_end(p, (double)r3 * (D[2].nf1 + D[2].B) * es));
-            const double wd = std::pow((double)p->w, p->d);
-            CK(prof_begin(p, PC_INTERP, st));
-            CK(launch_interp<G>(A, p->d_bu, p->n_u, p->d_dec, g, wk.Vu, st));
-            CK(prof_end(p, (double)p->n_u * (wd * p->n_pol * es + 4 * sizeof(double) + p->n_pol * 16.0)));
+        // one transform per beam group: strengths with the group's two beams, targets [u0, u1)
+        for (const auto &gr : p->groups) {
+            if (gr.u1 <= gr.u0) continue;
+            SliceGeom g = slice_geom_for(p, f, t, gr);
+            const int nug = gr.u1 - gr.u0;
+            const double *bug = p->d_bu + 3 * (size_t)gr.u0, *decg = p->d_dec + gr.u0;
+            cpx<double> *Vug = wk.Vu + (size_t)gr.u0 * p->n_pol;
+            const DimGeom *D = g.dim;
+            const size_t gel = (size_t)p->n_pol * D[0].nf1 * D[1].nf1 * D[2].nf1;
+            if (p->tiled) {
+                G *frac = (G *)wk.frac;
+                cpx<G> *cs = (cpx<G> *)wk.cs;
+                CK(prof_begin(p, PC_PREP, st));
+                CK(launch_prep<G>(wk.sdir, wk.sidx, wk.offsets + nb, p->n_src, p->flux, p->flux_fp64, nf, f, g, wk.cell,
+                                  frac, cs, st));
+                CK(prof_end(p, prep_bytes));
+                const double r0 = D[0].qscale / p->qscale_top[0], r1 = D[1].qscale / p->qscale_top[1];
+                CK(prof_begin(p, PC_SPREAD, st));
+                if (p->spread_method == FV_SPREAD_SCATTER)
+                    CK(launch_spread_scatter<G>(wk.offsets, wk.cell, frac, cs, p->n_src, g, tb, r0, r1, grid, st));
+                else
+                    CK(launch_spread_tile<G>(wk.offsets, wk.cell, frac, cs, p->n_src, g, tb, r0, r1, grid, st));
+                CK(prof_end(p, spread_in_bytes + gel * es));
+            } else {
+                CK(prof_begin(p, PC_MEMSET, st));
+                CK(cudaMemsetAsync(grid, 0, gel * sizeof(cpx<G>), st));
+                CK(prof_end(p, gel * es));
+                CK(prof_begin(p, PC_SPREAD, st));
+                CK(launch_spread_direct<G>(p->d_e, p->n_src, p->flux, p->flux_fp64, nf, f, g, grid, st));
+                CK(prof_end(p, src_bytes + gel * es));
+            }
+            const size_t o0 = (size_t)f * 3;
+            // pass 1 along x: rows (pol, z, y)
+            const long r1 = (long)p->n_pol * D[2].nf1 * D[1].nf1;
+            CK(prof_begin(p, PC_FFT_X, st));
+            CK(launch_fft_pass<G>(grid, A, r1, D[0], pre + p->pre_off[o0], tw + p->tw_off[o0], st));
+            CK(prof_end(p, (double)r1 * (D[0].nf1 + D[0].B) * es));
+            // pass 2 along y: rows (bx, pol, z)
+            const long r2 = (long)D[0].B * p->n_pol * D[2].nf1;
+            CK(prof_begin(p, PC_FFT_Y, st));
+            CK(launch_fft_pass<G>(A, Bb, r2, D[1], pre + p->pre_off[o0 + 1], tw + p->tw_off[o0 + 1], st));
+            CK(prof_end(p, (double)r2 * (D[1].nf1 + D[1].B) * es));
+            if (p->d == 2 || D[2].nf1 <= FV_ZDIRECT_MAX) {
+                // z (if any) summed directly inside the interpolation: no z pass
+                const double wd = (double)p->w * p->w * D[2].nf1;
+                CK(prof_begin(p, PC_INTERP, st));
+                CK(launch_interp_zdirect<G>(Bb, bug, nug, decg, g, pre + p->pre_off[o0 + 2],
+                                            tw + p->tw_off[o0 + 2], Vug, st));
+                CK(prof_end(p, (double)nug * (wd * p->n_pol * es + 4 * sizeof(double) + p->n_pol * 16.0)));
+            } else {
+                // pass 3 along z: rows (by, bx, pol)
+                const long r3 = (long)D[1].B * D[0].B * p->n_pol;
+                CK(prof_begin(p, PC_FFT_Z, st));
+                CK(launch_fft_pass<G>(Bb, A, r3, D[2], pre + p->pre_off[o0 + 2], tw + p->tw_off[o0 + 2], st));
+                CK(prof_end(p, (double)r3 * (D[2].nf1 + D[2].B) * es));
+                const double wd = std::pow((double)p->w, p->d);
+                CK(prof_begin(p, PC_INTERP, st));
+                CK(launch_interp<G>(A, bug, nug, decg, g, Vug, st));
+                CK(prof_end(p, (double)nug * (wd * p->n_pol * es + 4 * sizeof(double) + p->n_pol * 16.0)));
+            }
         }
         const int ntm = om.nt > 0 ? om.nt : nt;
         char *out = vis + ((size_t)(f - om.f0) * ntm + (t - om.t0)) * slice_bytes;
@@ -857,44 +885,62 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
     return FV_OK;
 }
 
-fv_status fv_set_array(fv_plan_t p, int n_ant, const double *enu_m, int n_bl, const int *pairs)
+// Baselines, unique targets, beam groups, lattice test and device tables from the stored array
+// (p->enu_h, p->pairs_h) and beams.
+static fv_status setup_array(fv_plan_s *p)
 {
-    if (!p) return FV_ERR_ARG;
-    if (cudaSetDevice(p->device) != cudaSuccess) return p->fail(FV_ERR_CUDA, "cudaSetDevice failed");
-    if (n_ant < 1 || !enu_m) return p->fail(FV_ERR_ARG, "need n_ant >= 1 and positions");
-    for (long i = 0; i < 3L * n_ant; ++i)
-        if (!std::isfinite(enu_m[i])) return p->fail(FV_ERR_ARG, "non-finite antenna position");
-    std::vector<int> pr;
-    if (pairs) {
-        if (n_bl < 0) return p->fail(FV_ERR_ARG, "n_bl < 0");
-        pr.assign(pairs, pairs + 2L * n_bl);
-        for (int v : pr)
-            if (v < 0 || v >= n_ant) return p->fail(FV_ERR_ARG, "antenna index out of range");
-    } else {
-        for (int i = 0; i < n_ant; ++i)
-            for (int j = i + 1; j < n_ant; ++j) { pr.push_back(i); pr.push_back(j); }
-        n_bl = (int)(pr.size() / 2);
+    const int n_ant = (int)(p->enu_h.size() / 3), n_bl = (int)(p->pairs_h.size() / 2);
+    const double *enu_m = p->enu_h.data();
+    const std::vector<int> &pr = p->pairs_h;
+    const bool multi = !p->beams.empty();
+    // beam groups: unordered pairs of beam indices, in increasing order
+    auto pair_of = [&](int b) {
+        int ba = multi ? p->beam_of_ant[pr[2 * b]] : 0, bb = multi ? p->beam_of_ant[pr[2 * b + 1]] : 0;
+        return std::make_pair(std::min(ba, bb), std::max(ba, bb));
+    };
+    std::map<std::pair<int, int>, int> gid;
+    for (int b = 0; b < n_bl; ++b) gid.emplace(pair_of(b), 0);
+    std::vector<fv_plan_s::BeamGroup> groups;
+    for (auto &kv : gid) {
+        kv.second = (int)groups.size();
+        fv_plan_s::BeamGroup g;
+        g.a = kv.first.first;
+        g.b = kv.first.second;
+        groups.push_back(g);
     }
-    // unique baseline vectors, bit-exact (Fig. 1, panel E)
-    std::map<std::tuple<double, double, double>, int> uid;
+    std::vector<int> grp_of(n_bl, 0);
+    for (int b = 0; b < n_bl; ++b) grp_of[b] = gid[pair_of(b)];
+    // baselines by group; unique baseline vectors within a group, bit-exact (Fig. 1, panel E), numbered
+    // group by group so that every group's targets are contiguous
+    std::vector<int> grp_bl;
     std::vector<double> bu;
     std::vector<int> bl2u(n_bl);
     bool nonplanar = false;
-    for (int b = 0; b < n_bl; ++b) {
-        const double *xi = enu_m + 3 * pr[2 * b], *xj = enu_m + 3 * pr[2 * b + 1];
-        double v[3] = {xi[0] - xj[0], xi[1] - xj[1], xi[2] - xj[2]};
-        if (v[2] != 0.0) nonplanar = true;
-        auto key = std::make_tuple(v[0] + 0.0, v[1] + 0.0, v[2] + 0.0);   // +0.0 folds -0 into 0
-        auto it = uid.find(key);
-        if (it == uid.end()) {
-            int id = (int)(bu.size() / 3);
-            uid.emplace(key, id);
-            bu.insert(bu.end(), v, v + 3);
-            bl2u[b] = id;
-        } else {
-            bl2u[b] = it->second;
+    for (size_t g = 0; g < groups.size(); ++g) {
+        groups[g].bl0 = (int)grp_bl.size();
+        groups[g].u0 = (int)(bu.size() / 3);
+        std::map<std::tuple<double, double, double>, int> uid;
+        for (int b = 0; b < n_bl; ++b) {
+            if (grp_of[b] != (int)g) continue;
+            grp_bl.push_back(b);
+            const double *xi = enu_m + 3 * pr[2 * b], *xj = enu_m + 3 * pr[2 * b + 1];
+            double v[3] = {xi[0] - xj[0], xi[1] - xj[1], xi[2] - xj[2]};
+            if (v[2] != 0.0) nonplanar = true;
+            auto key = std::make_tuple(v[0] + 0.0, v[1] + 0.0, v[2] + 0.0);   // +0.0 folds -0 into 0
+            auto it = uid.find(key);
+            if (it == uid.end()) {
+                int id = (int)(bu.size() / 3);
+                uid.emplace(key, id);
+                bu.insert(bu.end(), v, v + 3);
+                bl2u[b] = id;
+            } else {
+                bl2u[b] = it->second;
+            }
         }
+        groups[g].bl1 = (int)grp_bl.size();
+        groups[g].u1 = (int)(bu.size() / 3);
     }
+    if (groups.empty()) groups.push_back(fv_plan_s::BeamGroup{});
     int d = p->dims_req ? p->dims_req : (nonplanar ? 3 : 2);
     if (d == 2 && nonplanar) return p->fail(FV_ERR_ARG, "dims = 2 requested for a non-coplanar array");
     // lattice test (Section 2.2.1): baselines as integer combinations n of two lattice vectors
@@ -918,8 +964,8 @@ fv_status fv_set_array(fv_plan_t p, int n_ant, const double *enu_m, int n_bl, co
         }
     }
     if (p->transform_req == FV_TRANSFORM_LATTICE && !lat_ok)
-        return p->fail(FV_ERR_UNSUPPORTED, "transform = FV_TRANSFORM_LATTICE, but the antennas are not a coplanar "
-                                           "lattice within lattice_tol_m");
+        return p->fail(FV_ERR_UNSUPPORTED, "transform = FV_TRANSFORM_LATTICE, but the antennas' horizontal "
+                                           "positions are not a lattice within lattice_tol_m");
     if (!lat_ok) p->lat_bup.clear();
     p->lat_ok = lat_ok;        // reported whatever the route; the lattice route also needs transform != TYPE3
                                // and dims != 3
@@ -932,6 +978,7 @@ fv_status fv_set_array(fv_plan_t p, int n_ant, const double *enu_m, int n_bl, co
     p->d = d;
     p->bu.swap(bu);
     p->bl2u.swap(bl2u);
+    p->groups.swap(groups);
     for (int i = 0; i < 3; ++i) {
         double lo = INFINITY, hi = -INFINITY;
         for (int u = 0; u < p->n_u; ++u) { lo = std::min(lo, p->bu[3 * u + i]); hi = std::max(hi, p->bu[3 * u + i]); }
@@ -943,6 +990,7 @@ fv_status fv_set_array(fv_plan_t p, int n_ant, const double *enu_m, int n_bl, co
     dfree_t(p->d_dec);
     dfree_t(p->d_bl2u);
     dfree_t(p->d_bln);
+    dfree_t(p->d_grp_bl);
     if (lat_ok) {
         CK(cudaMalloc(&p->d_bln, std::max<size_t>(bln.size(), 2) * sizeof(int)));
         if (!bln.empty())
@@ -952,14 +1000,79 @@ fv_status fv_set_array(fv_plan_t p, int n_ant, const double *enu_m, int n_bl, co
     CK(cudaMalloc(&p->d_bu, nu * 3 * sizeof(double)));
     CK(cudaMalloc(&p->d_dec, nu * sizeof(double)));
     CK(cudaMalloc(&p->d_bl2u, nb * sizeof(int)));
+    CK(cudaMalloc(&p->d_grp_bl, nb * sizeof(int)));
     if (p->n_u) CK(cudaMemcpyAsync(p->d_bu, p->bu.data(), (size_t)p->n_u * 3 * sizeof(double), cudaMemcpyHostToDevice, p->stream));
-    if (p->n_bl) CK(cudaMemcpyAsync(p->d_bl2u, p->bl2u.data(), (size_t)p->n_bl * sizeof(int), cudaMemcpyHostToDevice, p->stream));
+    if (p->n_bl) {
+        CK(cudaMemcpyAsync(p->d_bl2u, p->bl2u.data(), (size_t)p->n_bl * sizeof(int), cudaMemcpyHostToDevice, p->stream));
+        CK(cudaMemcpyAsync(p->d_grp_bl, grp_bl.data(), (size_t)p->n_bl * sizeof(int), cudaMemcpyHostToDevice,
+                           p->stream));
+    }
     CK(launch_target_deconv(p->d_bu, p->n_u, p->d, p->bcen, p->bhalf, p->w, p->beta, p->sigma, p->d_glx, p->d_glw,
                             p->nq, p->d_dec, p->stream));
     CK(cudaStreamSynchronize(p->stream));
     p->have_array = true;
     if (p->have_sky) return prepare(p);
     return FV_OK;
+}
+
+
+fv_status fv_set_array(fv_plan_t p, int n_ant, const double *enu_m, int n_bl, const int *pairs)
+{
+    if (!p) return FV_ERR_ARG;
+    if (cudaSetDevice(p->device) != cudaSuccess) return p->fail(FV_ERR_CUDA, "cudaSetDevice failed");
+    if (n_ant < 1 || !enu_m) return p->fail(FV_ERR_ARG, "need n_ant >= 1 and positions");
+    for (long i = 0; i < 3L * n_ant; ++i)
+        if (!std::isfinite(enu_m[i])) return p->fail(FV_ERR_ARG, "non-finite antenna position");
+    std::vector<int> pr;
+    if (pairs) {
+        if (n_bl < 0) return p->fail(FV_ERR_ARG, "n_bl < 0");
+        pr.assign(pairs, pairs + 2L * n_bl);
+        for (int v : pr)
+            if (v < 0 || v >= n_ant) return p->fail(FV_ERR_ARG, "antenna index out of range");
+    } else {
+        for (int i = 0; i < n_ant; ++i)
+            for (int j = i + 1; j < n_ant; ++j) { pr.push_back(i); pr.push_back(j); }
+    }
+    if (!p->beams.empty() && (int)p->beam_of_ant.size() != n_ant) {
+        // per-antenna beams set for another array: back to the shared beam
+        p->beams.clear();
+        p->beam_of_ant.clear();
+    }
+    p->enu_h.assign(enu_m, enu_m + 3L * n_ant);
+    p->pairs_h.swap(pr);
+    return setup_array(p);
+}
+
+fv_status fv_set_beams(fv_plan_t p, int n_beams, const int *kinds, const double *params, const int *beam_of_ant)
+{
+    if (!p) return FV_ERR_ARG;
+    if (cudaSetDevice(p->device) != cudaSuccess) return p->fail(FV_ERR_CUDA, "cudaSetDevice failed");
+    if (!p->have_array) return p->fail(FV_ERR_STATE, "fv_set_array must come before fv_set_beams");
+    if (n_beams <= 0 || !beam_of_ant) {
+        p->beams.clear();
+        p->beam_of_ant.clear();
+        return setup_array(p);
+    }
+    if (n_beams > 16) return p->fail(FV_ERR_ARG, "at most 16 beams");
+    if (!kinds || !params) return p->fail(FV_ERR_ARG, "NULL beam kinds or parameters");
+    std::vector<BeamParams> beams(n_beams);
+    for (int k = 0; k < n_beams; ++k) {
+        const double *q = params + 3 * k;
+        if (kinds[k] < FV_BEAM_GAUSS || kinds[k] > FV_BEAM_UNIFORM) return p->fail(FV_ERR_ARG, "unknown beam kind");
+        if (kinds[k] == FV_BEAM_GAUSS && !(q[0] > 0 && q[1] > 0))
+            return p->fail(FV_ERR_ARG, "Gaussian beam needs FWHM > 0 and reference frequency > 0");
+        if (kinds[k] == FV_BEAM_AIRY && !(q[0] > 0)) return p->fail(FV_ERR_ARG, "Airy beam needs a diameter > 0");
+        beams[k].kind = kinds[k];
+        beams[k].p0 = q[0];
+        beams[k].p1 = q[1];
+        beams[k].p2 = q[2];
+    }
+    std::vector<int> boa(beam_of_ant, beam_of_ant + p->n_ant);
+    for (int v : boa)
+        if (v < 0 || v >= n_beams) return p->fail(FV_ERR_ARG, "beam index out of range");
+    p->beams.swap(beams);
+    p->beam_of_ant.swap(boa);
+    return setup_array(p);
 }
 
 fv_status fv_set_sky(fv_plan_t p, long n_src, const double *ra_rad, const double *dec_rad, int n_stokes,
@@ -1079,6 +1192,7 @@ fv_status fv_destroy(fv_plan_t p)
     dfree_t(p->d_dec);
     dfree_t(p->d_bl2u);
     dfree_t(p->d_bln);
+    dfree_t(p->d_grp_bl);
     dfree_t(p->d_e);
     dfree(p->d_flux_owned);
     for (cudaEvent_t ev : p->ev_pool) cudaEventDestroy(ev);
@@ -1118,6 +1232,7 @@ fv_status fv_get_info(fv_plan_t p, fv_info *info)
     }
     info->lattice_terms = p->use_lattice ? p->lg.K : 0;
     for (int k = 0; k < 4; ++k) info->lattice_basis[k] = p->lat_basis[k];
+    info->beam_groups = (int)p->groups.size();
     return FV_OK;
 }
 

@@ -54,7 +54,8 @@ class fv_info(C.Structure):
                 ("nf1_max", C.c_int * 3), ("nf2_max", C.c_int * 3), ("src_centre", C.c_double * 3),
                 ("src_halfwidth", C.c_double * 3), ("workspace_bytes", C.c_longlong),
                 ("transform", C.c_int), ("lattice", C.c_int), ("lattice_modes", C.c_int * 2),
-                ("lattice_grid", C.c_int * 2), ("lattice_terms", C.c_int), ("lattice_basis", C.c_double * 4)]
+                ("lattice_grid", C.c_int * 2), ("lattice_terms", C.c_int), ("lattice_basis", C.c_double * 4),
+                ("beam_groups", C.c_int)]
 
 
 PROFILE_CLASSES = 12
@@ -71,6 +72,7 @@ SIGNATURES = {
     "fv_lattice_detect": (C.c_int, [C.c_int, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
     "fv_plan": (C.c_int, [C.POINTER(fv_opts), C.POINTER(C.c_void_p)]),
     "fv_set_array": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
+    "fv_set_beams": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fv_set_sky": (C.c_int, [C.c_void_p, C.c_long, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int]),
     "fv_execute": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "fv_destroy": (C.c_int, [C.c_void_p]),
@@ -202,7 +204,7 @@ def fv_get_info(plan) -> dict:
             "src_halfwidth": list(i.src_halfwidth), "workspace_bytes": i.workspace_bytes,
             "transform": TRANSFORM_NAMES[i.transform], "lattice": bool(i.lattice),
             "lattice_modes": list(i.lattice_modes), "lattice_grid": list(i.lattice_grid),
-            "lattice_terms": i.lattice_terms,
+            "lattice_terms": i.lattice_terms, "beam_groups": i.beam_groups,
             "lattice_basis": list(i.lattice_basis)}
 
 
@@ -334,6 +336,18 @@ class Plan:
     def set_array(self, enu_m, pairs=None):
         fv_set_array(self.handle, enu_m, pairs)
         self.n_bl = fv_get_info(self.handle)["n_bl"]
+
+    def set_beams(self, beams, beam_of_ant):
+        """Per-antenna beams: beams = [(kind, params), ...], beam_of_ant = beam index per antenna
+        (None or an empty list: the plan's single beam)."""
+        if not beams or beam_of_ant is None:
+            _check(load_library().fv_set_beams(self.handle, 0, None, None, None), self.handle)
+            return
+        kinds = np.ascontiguousarray([BEAMS[k] for k, _ in beams], dtype=np.int32)
+        params = np.ascontiguousarray([list(v) + [0.0] * (3 - len(v)) for _, v in beams], dtype=np.float64)
+        boa = np.ascontiguousarray(beam_of_ant, dtype=np.int32)
+        _check(load_library().fv_set_beams(self.handle, len(kinds), _ptr(kinds), _ptr(params), _ptr(boa)),
+               self.handle)
 
     def set_sky(self, ra, dec, flux):
         self._keep = (flux,)          # a device flux is borrowed by the plan

@@ -341,6 +341,9 @@ class Problem:
     polarized: bool = False
     eps: float = 1e-10
     meta: dict = field(default_factory=dict)
+    # per-antenna beams (Section 2.2.3): [(kind, params), ...] and the beam index of every antenna
+    beams: list | None = None
+    beam_of_ant: np.ndarray | None = None
 
     @property
     def n_vis(self) -> int:
