@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target oracle CPU time for the baseline")
     ap.add_argument("--streams", type=int, default=0, help="execution streams per plan (0 = library default)")
     ap.add_argument("--spread", default="auto", choices=["auto", "gather", "scatter", "atomic"])
+    ap.add_argument("--fft-radix", type=int, default=0, choices=[0, 8, 16],
+                    help="largest FFT stage radix of the timed plan (0: the library default)")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip timing the plain FP64 path (one slice after another) beside the mixed path")
     ap.add_argument("--workload", default="hex127", choices=["hex127", "batch", "serve"],
@@ -601,7 +603,8 @@ def main():
     # a dedicated stream: the plan runs on it and the timing events are recorded on it
     stream = torch.cuda.Stream(device=dev)
     plan = fv.Plan.from_problem(prob, precision=precision, eps=eps, stream=stream.cuda_stream, device=local,
-                                n_streams=args.streams, spread=args.spread, transform=args.transform)
+                                n_streams=args.streams, spread=args.spread, transform=args.transform,
+                                fft_max_radix=args.fft_radix)
     fdt = torch.float32 if precision == fv.FV_MIXED else torch.float64
     cdt = torch.complex64 if precision == fv.FV_MIXED else torch.complex128
     flux_dev = torch.tensor(prob.sky.flux, dtype=fdt, device=dev)
