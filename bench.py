@@ -80,24 +80,34 @@ def peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-def kernel_source_hash():
+# the source files that define each kernel class of the type-3 route (plus the shared device header)
+KERNEL_FILES = {"bin": "fv_spread.cu", "prep": "fv_spread.cu", "spread": "fv_spread.cu", "fft_x": "fv_fft.cu",
+                "fft_y": "fv_fft.cu", "fft_z": "fv_fft.cu", "interp": "fv_kernels.cu", "scatter": "fv_kernels.cu"}
+
+
+def kernel_source_hash(kernel_class):
+    """Digest of the sources a kernel class is compiled from: a traffic figure taken from an ncu
+    capture holds only while they are unchanged."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2506_02130_gb300", "csrc")
-    for n in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, n), "rb") as f:
-            h.update(n.encode() + f.read())
+    for n in ("fv_internal.cuh", KERNEL_FILES.get(kernel_class, "")):
+        if n:
+            with open(os.path.join(csrc, n), "rb") as f:
+                h.update(n.encode() + f.read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel_class, precision):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernels."""
+    """DRAM bytes per launch of a type-3 kernel class from the committed ncu summary, if its sources
+    are those the capture was taken with."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        if d.get("kernel_hash") != kernel_source_hash():
+        e = d["per_launch"][precision][kernel_class]
+        if e.get("source_hash") != kernel_source_hash(kernel_class):
             return None
-        return d["per_launch_bytes"][precision][kernel_class]
+        return e["dram_bytes"]
     except Exception:
         return None
 
@@ -658,7 +668,7 @@ def main():
     if dom:
         d = ours[dom]
         achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        tr = ncu_traffic(dom, args.precision)
+        tr = ncu_traffic(dom, args.precision) if args.transform == "type3" else None
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": tr, "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],

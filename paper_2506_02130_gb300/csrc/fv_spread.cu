@@ -221,6 +221,7 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<NP, NZ>::valu
     __shared__ cpx<G> s_c[NP][kGatherChunk];
     __shared__ unsigned char s_list[kPatches][kGatherChunk];
     __shared__ int s_cnt[kPatches];
+    __shared__ int s_row0[32], s_pre[32], s_total;
     const int nx = g.dim[0].nf1, ny = g.dim[1].nf1, nz = g.d == 3 ? g.dim[2].nf1 : 1;
     const int w = g.w;
     const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
@@ -245,13 +246,41 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<NP, NZ>::valu
     // an integer, far more than the product's rounding error
     const float inv_w = 1.0f / (float)w;
     __syncthreads();
-    for (int by = by_lo; by <= by_hi; ++by) {
-        const int i0 = offsets[by * tb.nbx + bx_lo], i1 = offsets[by * tb.nbx + bx_hi + 1];
-        for (int base = i0; base < i1; base += kGatherChunk) {
-            const int n = min(kGatherChunk, i1 - base);
+    // The candidates of the tile are the bins [bx_lo, bx_hi] of the rows [by_lo, by_hi]: one contiguous
+    // range of the sorted sources per row.  Rows are taken 32 at a time; their ranges are concatenated
+    // (lengths scanned by warp 0) and cut into full chunks, so that a chunk is not limited to one row.
+    for (int r0w = by_lo; r0w <= by_hi; r0w += 32) {
+        const int nrows = min(32, by_hi - r0w + 1);
+        if (warp == 0) {
+            int start = 0, len = 0;
+            if (lane < nrows) {
+                const int row = (r0w + lane) * tb.nbx;
+                start = offsets[row + bx_lo];
+                len = offsets[row + bx_hi + 1] - start;
+            }
+            int incl = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            s_row0[lane] = start;
+            s_pre[lane] = incl - len;
+            if (lane == 31) s_total = incl;
+        }
+        __syncthreads();
+        const int total = s_total;
+        for (int base = 0; base < total; base += kGatherChunk) {
+            const int n = min(kGatherChunk, total - base);
             // 1. one thread per candidate: position, strengths, and the patches its footprint overlaps
             if (threadIdx.x < n) {
-                const int i = base + threadIdx.x;
+                const int v = base + threadIdx.x;
+                // the row holding the v-th candidate: the last row whose prefix is <= v
+                int r = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (r + step < nrows && s_pre[r + step] <= v) r += step;
+                const int i = s_row0[r] + (v - s_pre[r]);
                 const int t = threadIdx.x;
                 const int cx = cell[i], cy = cell[n_src + i];
                 const int ax = max(cx - x0, 0), bx = min(cx + w - 1 - x0, kTileX - 1);
@@ -321,6 +350,7 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<NP, NZ>::valu
             if (threadIdx.x < kPatches) s_cnt[threadIdx.x] = 0;
             __syncthreads();
         }
+        __syncthreads();      // every thread has read s_total before warp 0 rewrites the row table
     }
     if (gx < nx && gy < ny) {
 #pragma unroll
