@@ -52,10 +52,15 @@ def parse():
                     help="hex127: the 127-antenna, 64-channel, 10-time simulation (default); batch: 2,048 ragged "
                          "single-slice problems on shared lanes, replayed from a CUDA graph; serve: a Poisson "
                          "stream of requests over resident plans with continuous batching")
-    ap.add_argument("--transform", default="type3", choices=["type3", "auto", "lattice"],
+    ap.add_argument("--transform", default="type3", choices=["type3", "auto", "lattice", "basis"],
                     help="hex127: route of the timed plan (type3: the type-3 NUFFT of every slice)")
     ap.add_argument("--no-lattice-route", action="store_true",
                     help="hex127: skip timing the lattice route (Section 2.2.1 with height terms) beside it")
+    ap.add_argument("--no-basis-route", action="store_true",
+                    help="hex127: skip timing the spectral-basis route (Appendix A) beside it")
+    ap.add_argument("--basis-terms", type=int, default=12,
+                    help="hex127: basis functions K of the spectral-basis route (12 keeps its truncation "
+                         "error near 1e-7 on this workload)")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=0.0,
                     help="serve: mean arrival rate (1/s); 0 = 70%% of the measured capacity for the request mix")
@@ -614,7 +619,8 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     plan = fv.Plan.from_problem(prob, precision=precision, eps=eps, stream=stream.cuda_stream, device=local,
                                 n_streams=args.streams, spread=args.spread, transform=args.transform,
-                                fft_max_radix=args.fft_radix)
+                                fft_max_radix=args.fft_radix,
+                                n_basis=args.basis_terms if args.transform == "basis" else 0)
     fdt = torch.float32 if precision == fv.FV_MIXED else torch.float64
     cdt = torch.complex64 if precision == fv.FV_MIXED else torch.complex128
     flux_dev = torch.tensor(prob.sky.flux, dtype=fdt, device=dev)
@@ -733,6 +739,40 @@ def main():
         outs["lattice_route"] = ol.cpu().numpy()
         pl.close()
 
+    # ---- the spectral-basis route (Appendix A) on the same workload: one transform per basis function
+    # and time on a grid sized for the whole band; same precision and eps, timed the same way
+    bas_route = None
+    if args.transform == "type3" and not args.no_basis_route:
+        pb = fv.Plan.from_problem(prob, precision=precision, eps=eps, stream=stream.cuda_stream, device=local,
+                                  n_streams=args.streams, transform="basis", n_basis=args.basis_terms)
+        pb.set_sky(prob.sky.ra, prob.sky.dec, flux_dev)
+        ob = torch.empty(pb.out_shape, dtype=cdt, device=dev)
+        for _ in range(args.warmup):
+            pb.run(ob)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            pb.run(ob)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        msb = e0.elapsed_time(e1)
+        fv.fv_profile_read(pb.handle)
+        fv.fv_profile_enable(pb.handle, True)
+        pb.run(ob)
+        torch.cuda.synchronize(dev)
+        bprof = fv.fv_profile_read(pb.handle)
+        fv.fv_profile_enable(pb.handle, False)
+        bi = pb.info()
+        bas_route = {"value": world * n_vis * args.steps / (msb / 1e3), "unit": "visibilities/s",
+                     "ms_per_step": msb / args.steps, "basis_terms": bi["basis_terms"], "grid": bi["basis_grid"],
+                     "kernels_ms_per_step": {k: v["ms"] for k, v in bprof.items() if v["launches"] > 0},
+                     "what": "same workload, plan with transform=basis: per time one transform per basis "
+                             "function of the band (Appendix A), expanded to the 64 channels in the "
+                             "interpolation; its error against the direct sum is in rel_l2_vs_oracle_sample"}
+        outs["basis_route"] = ob.cpu().numpy()
+        pb.close()
+
     # ---- the plain FP64 path (one slice after another, no batching) on the same workload
     fp64 = None
     if precision == fv.FV_MIXED and not args.no_fp64_compare:
@@ -776,6 +816,7 @@ def main():
                        "parallelism": f"{world} independent problems (one per GPU)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": gpu_launches,
             "rel_l2_vs_oracle_sample": err, "fp64_plain": fp64, "lattice_route": lat_route,
+            "basis_route": bas_route,
             "kernels": {k: {"ms_per_step": v["ms"] / prof_steps, "launches_per_step": v["launches"] / prof_steps,
                             "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}
                         for k, v in prof.items() if v["launches"] > 0}}

@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define FV_ABI_VERSION 2
+#define FV_ABI_VERSION 3
 
 typedef struct fv_plan_s *fv_plan_t;   /* opaque plan handle; owns its device memory */
 
@@ -97,6 +97,8 @@ typedef struct {
     double lattice_tol_m;     /* largest distance (m) of an antenna from its lattice point, and of its
                                  height from the first antenna's, still accepted as a lattice;
                                  0 = 1e-10 m (a phase error below 2 pi nu/c x 1e-10 rad) */
+    int n_basis;              /* FV_TRANSFORM_BASIS: number K of spectral basis functions,
+                                 1 <= K <= min(16, n_freq); ignored by the other routes */
 } fv_opts;
 
 /* Transform choice (Section 2.2.1).  When the antennas' horizontal positions
@@ -115,11 +117,33 @@ typedef struct {
  * lattice, K <= 24 and K times its grid is no larger than the type-3 grid of
  * the top channel; FV_TRANSFORM_TYPE3 never takes it; FV_TRANSFORM_LATTICE
  * always does, and fv_set_array fails with FV_ERR_UNSUPPORTED if the array is
- * not a lattice or needs more than 24 terms. */
+ * not a lattice or needs more than 24 terms.
+ *
+ * Spectral-basis route (Appendix A; FV_TRANSFORM_BASIS, never taken by
+ * FV_TRANSFORM_AUTO).  The n_freq channels of a time share one transform per
+ * function of a compact spectral basis instead of one transform per channel.
+ * The basis M ([n_freq][K], K = fv_opts.n_basis) spans the polynomials of
+ * degree < K in frequency (mapped to [-1, 1] over the band), with columns
+ * orthonormal over the channels.  Per source, the flux coefficients
+ * s_hat = M^T I (Eq. A1) and, per time, the beam coefficients
+ * b_hat = M^T B(theta_n(t), nu) (Eq. A2; B = A^2, or A_i A_j with per-antenna
+ * beams) give the product coefficients v_k = sum_ij s_hat_i b_hat_j d^k_ij
+ * with d^k_ij = sum_q M_qi M_qj M_qk (Eqs. A3-A4).  One type-3 transform per
+ * time takes the K strength vectors to the targets 2 pi nu_q b / c of every
+ * channel on one grid sized for the whole band (Eq. A5), and
+ * V(b, nu_q) = sum_k M_qk T_k(b, nu_q).  The result is the direct sum with each
+ * source's spectrum B I replaced by P[(P I)(P B)], P = M M^T: exact when flux
+ * and beam are polynomials of degree < K in frequency and for any sky at
+ * K = n_freq; otherwise that truncation error adds to eps and is set by the
+ * caller's choice of K.  Unpolarised plans only (fv_plan returns
+ * FV_ERR_UNSUPPORTED for a polarised one).  Executed by fv_execute;
+ * fv_batch_add and fv_execute_static return FV_ERR_UNSUPPORTED for such a
+ * plan. */
 typedef enum {
     FV_TRANSFORM_AUTO = 0,
     FV_TRANSFORM_TYPE3 = 1,
-    FV_TRANSFORM_LATTICE = 2
+    FV_TRANSFORM_LATTICE = 2,
+    FV_TRANSFORM_BASIS = 3
 } fv_transform;
 
 /* Lattice test of Section 2.2.1 on its own (host only, no device needed):
@@ -215,13 +239,15 @@ typedef struct {
     double src_centre[3];     /* C: centre of the visible source directions */
     double src_halfwidth[3];  /* S: half-extent of the visible source directions */
     long long workspace_bytes;   /* device memory held by the plan */
-    int transform;        /* FV_TRANSFORM_TYPE3 or FV_TRANSFORM_LATTICE: the route the slices take */
+    int transform;        /* FV_TRANSFORM_TYPE3, _LATTICE or _BASIS: the route the slices take */
     int lattice;          /* 1 if the array is a lattice (whatever the route) */
     int lattice_modes[2]; /* lattice route: modes 2 max|n_d| + 1 per axis */
     int lattice_grid[2];  /* lattice route: grid (and FFT) points per axis */
     int lattice_terms;    /* lattice route: Chebyshev terms K of the height factor (1 for a flat array) */
     double lattice_basis[4];  /* a1_east, a1_north, a2_east, a2_north (m) */
     int beam_groups;      /* transforms per slice: unordered beam pairs among the baselines (1: one beam) */
+    int basis_terms;      /* spectral-basis route: K (0 on the other routes) */
+    int basis_grid[3];    /* spectral-basis route: the one spreading grid of a time, per dim */
 } fv_info;
 
 fv_status fv_get_info(fv_plan_t p, fv_info *info);

@@ -1,0 +1,402 @@
+// Spectral-basis route (Appendix A): the basis, the per-source coefficient
+// kernels, the interpolation that expands the basis at every channel, the
+// per-target deconvolution and the scatter of all channels of a time.
+#include "fv_basis.cuh"
+#include "fv_plan.cuh"
+
+#include <cmath>
+#include <math.h>
+#include <vector>
+
+namespace fv {
+
+namespace {
+
+// Exponential-of-semicircle kernel phi(z) = exp(beta (sqrt(1 - z^2) - 1)) on [-1, 1], zero outside
+// (Section 2.2, spreading step).
+__device__ __forceinline__ double es_phi(double z, double beta)
+{
+    const double t = 1.0 - z * z;
+    return t >= 0.0 ? exp(beta * (sqrt(t) - 1.0)) : 0.0;
+}
+__device__ __forceinline__ float es_phi(float z, float beta)
+{
+    const float t = 1.0f - z * z;
+    return t >= 0.0f ? expf(beta * (sqrtf(t) - 1.0f)) : 0.0f;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ flux coefficients (Eq. A1)
+__global__ void __launch_bounds__(256) k_basis_sky(const void *__restrict__ flux, int flux_fp64, long n_src,
+                                                   int n_freq, const double *__restrict__ M, int K,
+                                                   double *__restrict__ shat)
+{
+    const long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (n >= n_src) return;
+    double acc[kBasisMax];
+#pragma unroll
+    for (int k = 0; k < kBasisMax; ++k) acc[k] = 0.0;
+    for (int q = 0; q < n_freq; ++q) {
+        const size_t idx = (size_t)n * n_freq + q;
+        const double I = flux_fp64 ? ((const double *)flux)[idx] : (double)((const float *)flux)[idx];
+#pragma unroll
+        for (int k = 0; k < kBasisMax; ++k)
+            if (k < K) acc[k] += M[q * K + k] * I;
+    }
+#pragma unroll
+    for (int k = 0; k < kBasisMax; ++k)
+        if (k < K) shat[(size_t)n * K + k] = acc[k];
+}
+
+cudaError_t launch_basis_sky(const void *flux, int flux_fp64, long n_src, int n_freq, const double *M, int K,
+                             double *shat, cudaStream_t st)
+{
+    if (n_src <= 0) return cudaSuccess;
+    if (K < 1 || K > kBasisMax) return cudaErrorInvalidValue;
+    k_basis_sky<<<(unsigned)((n_src + 255) / 256), 256, 0, st>>>(flux, flux_fp64, n_src, n_freq, M, K, shat);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ per time: strengths (Eqs. A2-A3)
+// One thread per visible source.  Beam and coefficient arithmetic in FP64 (a few thousand operations
+// per source, small next to the spreading); the structure constants sit in shared memory, read as
+// broadcasts.
+template <class G>
+__global__ void __launch_bounds__(128) k_prep_basis(const double *__restrict__ sdir, const int *__restrict__ sidx,
+                                                    const int *__restrict__ nv_ptr, long n_src,
+                                                    const double *__restrict__ shat, const double *__restrict__ M,
+                                                    const double *__restrict__ dK, const double *__restrict__ freq,
+                                                    int n_freq, int K, int Kp, SliceGeom g, int *__restrict__ cell,
+                                                    G *__restrict__ frac, cpx<G> *__restrict__ cs)
+{
+    __shared__ double s_d[kBasisMax * kBasisMax * kBasisMax];
+    const int KKK = K * K * K;
+    for (int e = threadIdx.x; e < KKK; e += blockDim.x) s_d[e] = dK[e];
+    __syncthreads();
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= *nv_ptr) return;
+    const double s0 = sdir[i], s1 = sdir[n_src + i], s2 = sdir[2 * n_src + i];
+    const long n = sidx[i];
+    const double rho = sqrt(s0 * s0 + s1 * s1);
+    // beam coefficients b_hat_k = sum_q M_qk B(nu_q)
+    double bh[kBasisMax];
+#pragma unroll
+    for (int k = 0; k < kBasisMax; ++k) bh[k] = 0.0;
+    for (int q = 0; q < n_freq; ++q) {
+        const double nu = freq[q];
+        const double A = voltage<double>(g.beam, rho, s2, nu);
+        const double B = g.two_beams ? A * voltage<double>(g.beam2, rho, s2, nu) : A * A;
+#pragma unroll
+        for (int k = 0; k < kBasisMax; ++k)
+            if (k < K) bh[k] += M[q * K + k] * B;
+    }
+    // v_k = sum_i s_hat_i sum_j b_hat_j d^k_ij
+    double v[kBasisMax];
+#pragma unroll
+    for (int k = 0; k < kBasisMax; ++k) v[k] = 0.0;
+    for (int a = 0; a < K; ++a) {
+        const double sa = shat[(size_t)n * K + a];
+        const double *da = s_d + a * K * K;
+#pragma unroll
+        for (int j = 0; j < kBasisMax; ++j) {
+            if (j < K) {
+                const double c = sa * bh[j];
+#pragma unroll
+                for (int k = 0; k < kBasisMax; ++k)
+                    if (k < K) v[k] += c * da[j * K + k];
+            }
+        }
+    }
+    // prephase e^{i D.(s - C)}: argument and reduction in FP64, sincos in G
+    const double st[3] = {s0 - g.dim[0].C, s1 - g.dim[1].C, s2 - g.dim[2].C};
+    double ph = 0.0;
+    for (int k = 0; k < g.d; ++k) ph += g.dim[k].D * st[k];
+    ph -= 6.283185307179586476925 * rint(ph * 0.15915494309189533577);
+    G sp, cp;
+    if (sizeof(G) == 4) { float a, b; sincosf((float)ph, &a, &b); sp = (G)a; cp = (G)b; }
+    else { double a, b; sincos(ph, &a, &b); sp = (G)a; cp = (G)b; }
+#pragma unroll
+    for (int k = 0; k < kBasisMax; ++k) {
+        if (k < K) cs[(size_t)k * n_src + i] = cmk<G>((G)v[k] * cp, (G)v[k] * sp);
+        else if (k < Kp) cs[(size_t)k * n_src + i] = cmk<G>((G)0, (G)0);
+    }
+    // grid coordinates, split in FP64
+    for (int k = 0; k < 3; ++k) {
+        if (k < g.d) {
+            const double q = st[k] * g.dim[k].qscale;
+            const double l0 = ceil(q - 0.5 * g.w);
+            cell[(size_t)k * n_src + i] = (int)l0 + g.dim[k].nf1 / 2;
+            frac[(size_t)k * n_src + i] = (G)(l0 - q);
+        } else {
+            cell[(size_t)k * n_src + i] = 0;
+            frac[(size_t)k * n_src + i] = (G)0;
+        }
+    }
+}
+
+template <class G>
+cudaError_t launch_prep_basis(const double *sdir, const int *sidx, const int *nv_ptr, long n_src, const double *shat,
+                              const double *M, const double *dK, const double *freq, int n_freq, int K, int Kp,
+                              const SliceGeom &g, int *cell, G *frac, cpx<G> *cs, cudaStream_t st)
+{
+    if (n_src <= 0) return cudaSuccess;
+    if (K < 1 || K > kBasisMax || Kp < K || Kp > kBasisMax) return cudaErrorInvalidValue;
+    k_prep_basis<G><<<(unsigned)((n_src + 127) / 128), 128, 0, st>>>(sdir, sidx, nv_ptr, n_src, shat, M, dK, freq,
+                                                                     n_freq, K, Kp, g, cell, frac, cs);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ interpolation with the expansion
+// One warp per target (u, q).  The band after the x and y passes holds, per (b_y, b_x) cell, the K
+// planes' z values contiguously ([k][l_z], K * Nz values).  Lane L holds the values j = L + 32 r
+// (r < R = ceil(K Nz / 32)) of that run, with the weights c_j = M_qk K(l_z), where
+// K(l_z) = sum_{m_z} phi((2/w)(p_z - m_z)) e^{2 pi i l_z m_z / M_z} (z prescale folded in) is the
+// direct z sum of the short z axis; each footprint tap is then R coalesced loads per warp, scaled by
+// the tap's x and y kernel values, and the warp reduces at the end.
+template <class G, bool HASZ>
+__global__ void __launch_bounds__(256) k_interp_basis(const cpx<G> *__restrict__ band, const double *__restrict__ bu,
+                                                      int u0, int n_ug, int n_u, const double *__restrict__ kappa,
+                                                      int n_freq, const double *__restrict__ M, int K,
+                                                      const double *__restrict__ dec, SliceGeom g,
+                                                      const G *__restrict__ prez, const cpx<G> *__restrict__ twz,
+                                                      cpx<double> *__restrict__ Vq)
+{
+    const int lane = threadIdx.x & 31;
+    const long tg = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+    if (tg >= (long)n_ug * n_freq) return;     // whole warps
+    const int u = u0 + (int)(tg / n_freq), q = (int)(tg % n_freq);
+    const int w = g.w;
+    const G two_over_w = (G)(2.0 / w);
+    const G beta = (G)g.beta;
+    const double kq = kappa[q];
+    double x[3] = {0.0, 0.0, 0.0};
+    G fr[3];
+    int m0[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        fr[i] = (G)0;
+        if (i < g.d) {
+            x[i] = -kq * bu[3 * u + i];
+            const double p = (x[i] - g.dim[i].D) * g.dim[i].pscale;
+            const double m = ceil(p - 0.5 * w);
+            m0[i] = (int)m;
+            fr[i] = (G)(p - m);
+        }
+    }
+    const int Nz = HASZ ? g.dim[2].nf1 : 1;
+    // lane lz < Nz builds K(l_z)
+    cpx<G> Kmine = cmk<G>((G)1, (G)0);
+    if (HASZ && lane < Nz) {
+        const int Mz = g.dim[2].M;
+        const int lc = lane - Nz / 2;
+        cpx<G> acc = cmk<G>((G)0, (G)0);
+        int e = (lc * m0[2]) % Mz;
+        if (e < 0) e += Mz;
+        int step = lc % Mz;
+        if (step < 0) step += Mz;
+        for (int jz = 0; jz < w; ++jz) {
+            const G wt = es_phi(two_over_w * (fr[2] - (G)jz), beta);
+            acc = cadd(acc, cscale(twz[e], wt));
+            e += step;
+            if (e >= Mz) e -= Mz;
+        }
+        Kmine = cscale(acc, prez[lane]);
+    }
+    // this lane's weights c_r = M_qk K(l_z) for j = lane + 32 r (shuffles taken by every lane)
+    const int KN = K * Nz;
+    const int R = (KN + 31) >> 5;
+    cpx<G> cf[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        cf[r] = cmk<G>((G)0, (G)0);
+        if (r < R) {                            // R is uniform across the warp
+            const int j = lane + 32 * r;
+            const bool valid = j < KN;
+            const int k = valid ? j / Nz : 0;
+            const int lz = valid ? j - k * Nz : 0;
+            const G kx = __shfl_sync(0xffffffffu, Kmine.x, lz);
+            const G ky = __shfl_sync(0xffffffffu, Kmine.y, lz);
+            if (valid) {
+                const G mk = (G)M[q * K + k];
+                cf[r] = cmk<G>(kx * mk, ky * mk);
+            }
+        }
+    }
+    const int Bx = g.dim[0].B;
+    const int bx0 = m0[0] + g.dim[0].H, by0 = m0[1] + g.dim[1].H;
+    // x and y kernel values: lane j < w holds the j-th
+    const G wxm = lane < w ? es_phi(two_over_w * (fr[0] - (G)lane), beta) : (G)0;
+    const G wym = lane < w ? es_phi(two_over_w * (fr[1] - (G)lane), beta) : (G)0;
+    G ax = (G)0, ay = (G)0;
+    for (int jy = 0; jy < w; ++jy) {
+        const G wy = __shfl_sync(0xffffffffu, wym, jy);
+        const cpx<G> *row = band + ((size_t)(by0 + jy) * Bx + bx0) * KN;
+        for (int jx = 0; jx < w; ++jx) {
+            const G wt = wy * __shfl_sync(0xffffffffu, wxm, jx);
+            const cpx<G> *c = row + (size_t)jx * KN;
+            G sx = (G)0, sy = (G)0;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int j = lane + 32 * r;
+                if (r < R && j < KN) {
+                    const cpx<G> v = c[j];
+                    sx += v.x * cf[r].x - v.y * cf[r].y;
+                    sy += v.x * cf[r].y + v.y * cf[r].x;
+                }
+            }
+            ax += wt * sx;
+            ay += wt * sy;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    }
+    if (lane == 0) {
+        double ph = 0.0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            if (i < g.d) ph += x[i] * g.dim[i].C;
+        double sp, cp;
+        sincos(ph, &sp, &cp);
+        const double dk = dec[(size_t)u * n_freq + q];
+        const cpx<double> v = cmk<double>((double)ax * dk, (double)ay * dk);
+        Vq[(size_t)q * n_u + u] = cmul(v, cmk<double>(cp, sp));
+    }
+}
+
+template <class G>
+cudaError_t launch_interp_basis(const cpx<G> *band, const double *bu, int u0, int n_ug, int n_u, const double *kappa,
+                                int n_freq, const double *M, int K, const double *dec, const SliceGeom &g,
+                                const G *prez, const cpx<G> *twz, cpx<double> *Vq, cudaStream_t st)
+{
+    if (n_ug <= 0) return cudaSuccess;
+    const int Nz = g.d == 3 ? g.dim[2].nf1 : 1;
+    if (K < 1 || K > kBasisMax || Nz > FV_ZDIRECT_MAX || K * Nz > 256 || g.w > 32) return cudaErrorInvalidValue;
+    const long threads = (long)n_ug * n_freq * 32;
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    if (g.d == 3)
+        k_interp_basis<G, true><<<blocks, 256, 0, st>>>(band, bu, u0, n_ug, n_u, kappa, n_freq, M, K, dec, g, prez,
+                                                        twz, Vq);
+    else
+        k_interp_basis<G, false><<<blocks, 256, 0, st>>>(band, bu, u0, n_ug, n_u, kappa, n_freq, M, K, dec, g, prez,
+                                                         twz, Vq);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ deconvolution of every target
+// dec[u * n_freq + q] = prod_i (4/w^2) / Phihat(a_i), a_i = (x_i - D_i) / X_i * w pi / (2 sigma) with
+// x = -kappa_q b_u, Phihat(k) = int_{-1}^{1} phi(z) cos(k z) dz by the plan's quadrature.
+__global__ void k_basis_deconv(const double *__restrict__ bu, int n_u, const double *__restrict__ kappa, int n_freq,
+                               int d, double D0, double D1, double D2, double X0, double X1, double X2, int w,
+                               double beta, double sigma, const double *__restrict__ gl_x,
+                               const double *__restrict__ gl_w, int nq, double *__restrict__ dec)
+{
+    const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e >= (long)n_u * n_freq) return;
+    const int u = (int)(e / n_freq), q = (int)(e % n_freq);
+    const double Dc[3] = {D0, D1, D2}, Xc[3] = {X0, X1, X2};
+    double r = 1.0;
+    for (int i = 0; i < d; ++i) {
+        const double x = -kappa[q] * bu[3 * u + i];
+        const double a = (x - Dc[i]) / Xc[i] * (w * M_PI / (2.0 * sigma));
+        double ph = 0.0;
+        for (int k = 0; k < nq; ++k) ph += gl_w[k] * es_phi(gl_x[k], beta) * cos(a * gl_x[k]);
+        r *= (4.0 / ((double)w * w)) / ph;
+    }
+    dec[e] = r;
+}
+
+cudaError_t launch_basis_deconv(const double *bu, int n_u, const double *kappa, int n_freq, int d, const double *D,
+                                const double *X, int w, double beta, double sigma, const double *gl_x,
+                                const double *gl_w, int nq, double *dec, cudaStream_t st)
+{
+    const long n = (long)n_u * n_freq;
+    if (n <= 0) return cudaSuccess;
+    k_basis_deconv<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(bu, n_u, kappa, n_freq, d, D[0], D[1], D[2], X[0],
+                                                                 X[1], X[2], w, beta, sigma, gl_x, gl_w, nq, dec);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ scatter of all channels of a time
+__global__ void k_scatter_basis(const cpx<double> *__restrict__ Vq, const int *__restrict__ bl2u, int n_bl, int n_u,
+                                int n_freq, int n_time, int t, char *__restrict__ vis, size_t slice_bytes,
+                                int out_fp64)
+{
+    const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e >= (long)n_bl * n_freq) return;
+    const int q = (int)(e / n_bl), bl = (int)(e % n_bl);
+    const cpx<double> v = Vq[(size_t)q * n_u + bl2u[bl]];
+    char *slice = vis + ((size_t)q * n_time + t) * slice_bytes;
+    if (out_fp64)
+        reinterpret_cast<double2 *>(slice)[bl] = make_double2(v.x, v.y);
+    else
+        reinterpret_cast<float2 *>(slice)[bl] = make_float2((float)v.x, (float)v.y);
+}
+
+cudaError_t launch_scatter_basis(const cpx<double> *Vq, const int *bl2u, int n_bl, int n_u, int n_freq, int n_time,
+                                 int t, char *vis, size_t slice_bytes, int out_fp64, cudaStream_t st)
+{
+    const long n = (long)n_bl * n_freq;
+    if (n <= 0) return cudaSuccess;
+    k_scatter_basis<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Vq, bl2u, n_bl, n_u, n_freq, n_time, t, vis,
+                                                                 slice_bytes, out_fp64);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_prep_basis<float>(const double *, const int *, const int *, long, const double *,
+                                              const double *, const double *, const double *, int, int, int,
+                                              const SliceGeom &, int *, float *, cpx<float> *, cudaStream_t);
+template cudaError_t launch_prep_basis<double>(const double *, const int *, const int *, long, const double *,
+                                               const double *, const double *, const double *, int, int, int,
+                                               const SliceGeom &, int *, double *, cpx<double> *, cudaStream_t);
+template cudaError_t launch_interp_basis<float>(const cpx<float> *, const double *, int, int, int, const double *, int,
+                                                const double *, int, const double *, const SliceGeom &,
+                                                const float *, const cpx<float> *, cpx<double> *, cudaStream_t);
+template cudaError_t launch_interp_basis<double>(const cpx<double> *, const double *, int, int, int, const double *,
+                                                 int, const double *, int, const double *, const SliceGeom &,
+                                                 const double *, const cpx<double> *, cpx<double> *, cudaStream_t);
+
+}  // namespace fv
+
+// ------------------------------------------------------------------ the basis (host)
+// Chebyshev polynomials T_0..T_{K-1} of x = (2 nu - nu_min - nu_max) / (nu_max - nu_min) at the
+// channels, orthonormalised column by column with modified Gram-Schmidt, each column twice (the
+// second sweep removes what rounding left of the earlier directions).  Fails if a column has no
+// component left (fewer distinct channels than K).
+bool basis_matrix(const std::vector<double> &freq, int K, std::vector<double> &M)
+{
+    const int nq = (int)freq.size();
+    if (K < 1 || K > nq) return false;
+    double lo = freq[0], hi = freq[0];
+    for (double f : freq) { lo = std::min(lo, f); hi = std::max(hi, f); }
+    M.assign((size_t)nq * K, 0.0);
+    for (int q = 0; q < nq; ++q) {
+        const double x = hi > lo ? (2.0 * freq[q] - lo - hi) / (hi - lo) : 0.0;
+        double t0 = 1.0, t1 = x;
+        for (int k = 0; k < K; ++k) {
+            double tk;
+            if (k == 0) tk = t0;
+            else if (k == 1) tk = t1;
+            else { tk = 2.0 * x * t1 - t0; t0 = t1; t1 = tk; }
+            M[(size_t)q * K + k] = tk;
+        }
+    }
+    for (int k = 0; k < K; ++k) {
+        double n0 = 0.0;
+        for (int q = 0; q < nq; ++q) n0 += M[(size_t)q * K + k] * M[(size_t)q * K + k];
+        for (int sweep = 0; sweep < 2; ++sweep)
+            for (int j = 0; j < k; ++j) {
+                double dot = 0.0;
+                for (int q = 0; q < nq; ++q) dot += M[(size_t)q * K + j] * M[(size_t)q * K + k];
+                for (int q = 0; q < nq; ++q) M[(size_t)q * K + k] -= dot * M[(size_t)q * K + j];
+            }
+        double nn = 0.0;
+        for (int q = 0; q < nq; ++q) nn += M[(size_t)q * K + k] * M[(size_t)q * K + k];
+        if (!(nn > 1e-24 * n0) || !(nn > 0.0)) return false;
+        const double inv = 1.0 / std::sqrt(nn);
+        for (int q = 0; q < nq; ++q) M[(size_t)q * K + k] *= inv;
+    }
+    return true;
+}

@@ -1,0 +1,53 @@
+// Spectral-basis route (Appendix A): declarations shared by the runtime and
+// the route's kernels.
+//
+// The channels q of a time share one type-3 transform per basis function k:
+//   strengths  v_nk = sum_ij s_hat_ni b_hat_nj d^k_ij            (Eqs. A1-A4)
+//   transform  T_k(x) = sum_n v_nk e^{i x . s_n}, x = -2 pi nu_q b / c
+//   expansion  V(b, nu_q) = sum_k M_qk T_k(x_qb)
+// with one grid per time sized for the targets of every channel (Eq. A5).
+// The interpolation applies the expansion: each target reads the K planes of
+// its footprint and weights plane k by M_qk.
+#pragma once
+#include "fv_internal.cuh"
+
+namespace fv {
+
+constexpr int kBasisMax = 16;
+
+// s_hat[n][k] = sum_q M[q][k] I_n(nu_q): the flux coefficients of every source (Eq. A1 with
+// orthonormal columns, so that (M^T M)^{-1} = 1).  flux: [n_src][n_freq] (Stokes I).
+cudaError_t launch_basis_sky(const void *flux, int flux_fp64, long n_src, int n_freq, const double *M, int K,
+                             double *shat, cudaStream_t st);
+
+// Per visible source i < *nv_ptr (sorted order of the time binning): beam coefficients
+// b_hat = M^T B(nu_.) at its direction with the slice geometry's beams (Eq. A2), product coefficients
+// v_k = sum_ij s_hat_i b_hat_j d^k_ij (Eq. A3), prephase e^{i D.(s - C)} and grid coordinates.
+// cs: [Kp][n_src], planes K..Kp-1 zero.
+template <class G>
+cudaError_t launch_prep_basis(const double *sdir, const int *sidx, const int *nv_ptr, long n_src, const double *shat,
+                              const double *M, const double *dK, const double *freq, int n_freq, int K, int Kp,
+                              const SliceGeom &g, int *cell, G *frac, cpx<G> *cs, cudaStream_t st);
+
+// Targets (u, q) for u in [u0, u0 + n_ug) and every channel q: interpolation of the K planes of the
+// band ([b_y][b_x][k][l_z] after the x and y passes) at x = -kappa_q b_u, with the z sum done directly
+// (short z), combined with weights M_qk, deconvolved by dec[u * n_freq + q] and postphased by
+// e^{i x.C}.  Vq[q * n_u + u] receives the result.
+template <class G>
+cudaError_t launch_interp_basis(const cpx<G> *band, const double *bu, int u0, int n_ug, int n_u, const double *kappa,
+                                int n_freq, const double *M, int K, const double *dec, const SliceGeom &g,
+                                const G *prez, const cpx<G> *twz, cpx<double> *Vq, cudaStream_t st);
+
+// Deconvolution factor of every target (u, q) of the one grid with target centre D and half-extent X
+// per dim: dec[u * n_freq + q] = prod_i (4/w^2) / Phihat(a_i), a_i = (x_i - D_i) / X_i * w pi / (2 sigma),
+// x = -kappa_q b_u.
+cudaError_t launch_basis_deconv(const double *bu, int n_u, const double *kappa, int n_freq, int d, const double *D,
+                                const double *X, int w, double beta, double sigma, const double *gl_x,
+                                const double *gl_w, int nq, double *dec, cudaStream_t st);
+
+// Output slices (q, t) of every channel: vis + (q * n_time + t) * slice_bytes holds, for baseline bl,
+// Vq[q * n_u + bl2u[bl]] (complex64 or complex128).
+cudaError_t launch_scatter_basis(const cpx<double> *Vq, const int *bl2u, int n_bl, int n_u, int n_freq, int n_time,
+                                 int t, char *vis, size_t slice_bytes, int out_fp64, cudaStream_t st);
+
+}  // namespace fv

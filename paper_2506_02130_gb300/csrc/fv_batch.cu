@@ -143,6 +143,8 @@ static fv_status add_items(fv_batch_t b, fv_plan_t p, void *vis, int t_lo, int t
     if (!p || !vis) return b->fail(FV_ERR_ARG, "NULL plan or output");
     if (p->device != b->device) return b->fail(FV_ERR_ARG, "plan and batch are on different devices");
     if (!p->have_array || !p->have_sky) return b->fail(FV_ERR_STATE, "plan needs its array and sky first");
+    if (p->use_basis)
+        return b->fail(FV_ERR_UNSUPPORTED, "a spectral-basis plan runs whole times: use fv_execute");
     const int nt = (int)p->lst.size(), nf = (int)p->freq.size();
     if (t_lo < 0 || t_hi > nt || t_lo >= t_hi || f_lo < 0 || f_hi > nf || f_lo >= f_hi)
         return b->fail(FV_ERR_ARG, "slice range out of bounds");

@@ -120,6 +120,19 @@ struct fv_plan_s {
     double *d_lat_bup = nullptr;
     cpx<double> *d_lat_wq = nullptr;  // [n_freq][n_bl][K] height-term weights (K > 1 only)
 
+    // spectral-basis route (Appendix A): one transform per basis function and time
+    int n_basis = 0;                  // fv_opts.n_basis (K)
+    bool use_basis = false;
+    int basis_np = 1;                 // strength vectors per spreading launch (4 or 1)
+    int basis_Kp = 0;                 // K rounded up to a multiple of basis_np (padded planes are zero)
+    SliceGeom bg{};                   // the grid of a time, sized for the whole band
+    double *d_bas_M = nullptr;        // [n_freq][K] orthonormal basis
+    double *d_bas_d = nullptr;        // [K][K][K] structure constants
+    double *d_bas_freq = nullptr;     // [n_freq] Hz
+    double *d_bas_kappa = nullptr;    // [n_freq] 2 pi nu / c
+    double *d_bas_dec = nullptr;      // [n_u][n_freq] deconvolution of each target
+    double *d_bas_shat = nullptr;     // [n_src][K] flux coefficients (recomputed by every execution)
+
     long long ws_bytes = 0;
     std::vector<long> geo_sig;       // sizes behind the current tables and workspaces
     int nf1_max[3] = {1, 1, 1}, M_max[3] = {1, 1, 1};
@@ -157,3 +170,10 @@ struct OutMap {
 template <class G>
 fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, char *vis, size_t slice_bytes,
                      long k_begin, long k_end, OutMap om = OutMap{});
+// Spectral-basis route: times [t_begin, t_end) of plan p (all channels), on stream st with workspace wk,
+// into the plan's full output layout.
+template <class G>
+fv_status run_basis(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, char *vis, size_t slice_bytes,
+                    int t_begin, int t_end);
+// Orthonormal basis of the polynomials of degree < K over the channel frequencies: M[q * K + k].
+bool basis_matrix(const std::vector<double> &freq, int K, std::vector<double> &M);

@@ -8,6 +8,7 @@
 // Execution: per (time, channel) slice, spread -> d FFT passes -> interpolate
 // -> scatter, all enqueued on the plan's stream.
 #include "../../include/fv.h"
+#include "fv_basis.cuh"
 #include "fv_internal.cuh"
 #include "fv_plan.cuh"
 
@@ -204,6 +205,12 @@ static void free_geometry(fv_plan_s *p)
     dfree_t(p->d_lat_dec);
     dfree_t(p->d_lat_bup);
     dfree_t(p->d_lat_wq);
+    dfree_t(p->d_bas_M);
+    dfree_t(p->d_bas_d);
+    dfree_t(p->d_bas_freq);
+    dfree_t(p->d_bas_kappa);
+    dfree_t(p->d_bas_dec);
+    dfree_t(p->d_bas_shat);
     free_workspaces(p->ws);
 }
 
@@ -348,8 +355,35 @@ static fv_status prepare_lattice(fv_plan_s *p)
 }
 
 // Per-channel geometry, tables and workspace; needs the array and the sky.
+// Grid and FFT geometry of one dimension of a transform whose targets have half-extent X and whose
+// sources have half-extent S (Eq. 5: nf1 >= 2 sigma X S / pi + w); D and C are left to the caller.
+static fv_status dim_geometry(fv_plan_s *p, double X, double S, DimGeom &dg)
+{
+    const int w = p->w;
+    const int maxM = fft_max_M((int)(p->precision == FV_FP64 ? sizeof(double) : sizeof(float)));
+    if (!(X > 0.0)) X = S > 0.0 ? 1.0 / S : 1.0;
+    double need = 2.0 * p->sigma * X * S / M_PI + w;
+    long nf1 = (long)std::ceil(need);
+    if (nf1 < w + 1) nf1 = w + 1;     // Eq. 5 is the requirement; no 2w floor is needed
+    if (nf1 > (1L << 20)) return p->fail(FV_ERR_UNSUPPORTED, "spreading grid too large");
+    dg.nf1 = next235even(nf1);
+    dg.M = fft_choose_length((int)std::ceil(p->sigma * dg.nf1 - 1e-9), dg.radix, dg.nstages, p->fft_max_radix);
+    if (dg.M < 0 || dg.M > maxM)
+        return p->fail(FV_ERR_UNSUPPORTED, "FFT length " + std::to_string(dg.M) + " exceeds " +
+                                               std::to_string(maxM) + " for one-CTA FFT passes");
+    dg.H = (int)std::ceil(dg.M / (2.0 * p->sigma) + 0.5 * w) + 1;
+    dg.B = 2 * dg.H + 1;
+    dg.qscale = p->sigma * X / M_PI;
+    dg.pscale = dg.M / (2.0 * p->sigma * X);
+    fft_stage_constants(dg);
+    return FV_OK;
+}
+
+static fv_status prepare_basis(fv_plan_s *p);
+
 static fv_status prepare(fv_plan_s *p)
 {
+    if (p->use_basis) return prepare_basis(p);
     const int nf = (int)p->freq.size();
     const int w = p->w;
     p->gf.assign(nf, SliceGeom{});
@@ -357,7 +391,6 @@ static fv_status prepare(fv_plan_s *p)
     p->tw_off.assign((size_t)nf * 3, 0);
     size_t pre_total = 0, tw_total = 0;
     for (int i = 0; i < 3; ++i) { p->nf1_max[i] = 1; p->M_max[i] = 1; }
-    const int maxM = fft_max_M((int)(p->precision == FV_FP64 ? sizeof(double) : sizeof(float)));
     size_t grid_e = 0, bufA_e = 0, bufB_e = 0;
     for (int f = 0; f < nf; ++f) {
         SliceGeom &g = p->gf[f];
@@ -377,25 +410,10 @@ static fv_status prepare(fv_plan_s *p)
                 dg.nstages = 0;
                 continue;
             }
-            double X = g.kappa * p->bhalf[i];
-            double S = p->S[i];
-            if (!(X > 0.0)) X = S > 0.0 ? 1.0 / S : 1.0;
-            double need = 2.0 * p->sigma * X * S / M_PI + w;
-            long nf1 = (long)std::ceil(need);
-            if (nf1 < w + 1) nf1 = w + 1;     // Eq. 5 is the requirement; no 2w floor is needed
-            if (nf1 > (1L << 20)) return p->fail(FV_ERR_UNSUPPORTED, "spreading grid too large");
-            dg.nf1 = next235even(nf1);
-            dg.M = fft_choose_length((int)std::ceil(p->sigma * dg.nf1 - 1e-9), dg.radix, dg.nstages, p->fft_max_radix);
-            if (dg.M < 0 || dg.M > maxM)
-                return p->fail(FV_ERR_UNSUPPORTED, "FFT length " + std::to_string(dg.M) + " exceeds " +
-                                                       std::to_string(maxM) + " for one-CTA FFT passes");
-            dg.H = (int)std::ceil(dg.M / (2.0 * p->sigma) + 0.5 * w) + 1;
-            dg.B = 2 * dg.H + 1;
-            dg.qscale = p->sigma * X / M_PI;
-            dg.pscale = dg.M / (2.0 * p->sigma * X);
+            const fv_status ds = dim_geometry(p, g.kappa * p->bhalf[i], p->S[i], dg);
+            if (ds != FV_OK) return ds;
             dg.D = -g.kappa * p->bcen[i];
             dg.C = p->C[i];
-            fft_stage_constants(dg);
             p->nf1_max[i] = std::max(p->nf1_max[i], dg.nf1);
             p->M_max[i] = std::max(p->M_max[i], dg.M);
             p->pre_off[(size_t)f * 3 + i] = pre_total;
@@ -569,6 +587,8 @@ template <class G>
 fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, char *vis, size_t slice_bytes,
                      long k_begin, long k_end, OutMap om)
 {
+    if (p->use_basis)
+        return p->fail(FV_ERR_UNSUPPORTED, "the spectral-basis route runs whole times: use fv_execute");
     if (p->use_lattice) return run_slices_lattice<G>(p, wk, st, vis, slice_bytes, k_begin, k_end, om);
     const int nf = (int)p->freq.size(), nt = (int)p->lst.size();
     cpx<G> *grid = (cpx<G> *)wk.grid;
@@ -679,6 +699,224 @@ template fv_status run_slices<float>(fv_plan_s *, fv_plan_s::Workspace &, cudaSt
 template fv_status run_slices<double>(fv_plan_s *, fv_plan_s::Workspace &, cudaStream_t, char *, size_t, long, long,
                                       OutMap);
 
+// The spectral-basis route (Appendix A): the basis and its structure constants, one grid per time
+// sized for the targets of every channel (Eq. A5), its FFT tables, the deconvolution of every
+// (baseline, channel) target and the workspace.
+static fv_status prepare_basis(fv_plan_s *p)
+{
+    const int nf = (int)p->freq.size(), K = p->n_basis, w = p->w;
+    const size_t gs = p->precision == FV_FP64 ? sizeof(double) : sizeof(float);
+    const size_t es = p->elem();
+    std::vector<double> M;
+    if (!basis_matrix(p->freq, K, M))
+        return p->fail(FV_ERR_ARG, "n_basis exceeds the number of distinct channel frequencies");
+    std::vector<double> dK((size_t)K * K * K, 0.0);
+    for (int i = 0; i < K; ++i)
+        for (int j = 0; j < K; ++j)
+            for (int k = 0; k < K; ++k) {
+                double acc = 0.0;
+                for (int q = 0; q < nf; ++q) acc += M[(size_t)q * K + i] * M[(size_t)q * K + j] * M[(size_t)q * K + k];
+                dK[((size_t)i * K + j) * K + k] = acc;
+            }
+    std::vector<double> kappa(nf);
+    double kmin = INFINITY, kmax = 0.0;
+    for (int q = 0; q < nf; ++q) {
+        kappa[q] = 2.0 * M_PI * p->freq[q] / FV_C_LIGHT;
+        kmin = std::min(kmin, kappa[q]);
+        kmax = std::max(kmax, kappa[q]);
+    }
+    // targets x = -kappa b: over the baselines' box and kappa in [kmin, kmax] the extremes sit at the
+    // box corners and the two ends of the band
+    SliceGeom g{};
+    g.nu = 0.0;
+    g.kappa = 1.0;
+    g.d = p->d;
+    g.w = w;
+    g.beta = p->beta;
+    g.polarized = 0;
+    g.n_stokes = 1;
+    g.beam = p->beam;
+    double Dc[3] = {0, 0, 0}, Xc[3] = {1, 1, 1};
+    for (int i = 0; i < 3; ++i) {
+        DimGeom &dg = g.dim[i];
+        if (i >= p->d) {
+            dg.nf1 = 1; dg.M = 1; dg.B = 1; dg.H = 0; dg.qscale = 0; dg.pscale = 0; dg.D = 0; dg.C = 0;
+            dg.nstages = 0;
+            continue;
+        }
+        const double blo = p->bcen[i] - p->bhalf[i], bhi = p->bcen[i] + p->bhalf[i];
+        const double xlo = std::min(-kmin * bhi, -kmax * bhi), xhi = std::max(-kmin * blo, -kmax * blo);
+        const fv_status ds = dim_geometry(p, 0.5 * (xhi - xlo), p->S[i], dg);
+        if (ds != FV_OK) return ds;
+        dg.D = 0.5 * (xhi + xlo);
+        dg.C = p->C[i];
+        Dc[i] = dg.D;
+        Xc[i] = dg.qscale * M_PI / p->sigma;      // the half-extent the geometry used (after the X = 0 fix-up)
+    }
+    const int nz = p->d == 3 ? g.dim[2].nf1 : 1;
+    if (nz > FV_ZDIRECT_MAX)
+        return p->fail(FV_ERR_UNSUPPORTED, "spectral-basis route: the grid's height axis is too long for the direct sum");
+    int nzt = 0, bx = 0, by = 0;
+    const int np = spread_gather_config((int)gs, 4, nz, w, &nzt, &bx, &by) ? 4
+                   : (spread_gather_config((int)gs, 1, nz, w, &nzt, &bx, &by) ? 1 : 0);
+    if (np == 0 || K * nz > 256)
+        return p->fail(FV_ERR_UNSUPPORTED, "spectral-basis route: no spreading kernel for this grid depth");
+    g.n_pol = np;
+    p->basis_np = np;
+    p->basis_Kp = (K + np - 1) / np * np;
+    p->bg = g;
+    // bins over the one grid of a time
+    p->spread_method = FV_SPREAD_GATHER;
+    p->tiled = true;
+    p->f_top = 0;
+    p->T[0] = 8;
+    p->T[1] = 4;
+    for (int i = 0; i < 3; ++i) {
+        p->nf1_top[i] = g.dim[i].nf1;
+        p->qscale_top[i] = g.dim[i].qscale;
+        p->nf1_max[i] = g.dim[i].nf1;
+        p->M_max[i] = g.dim[i].M;
+    }
+    p->nbx = (p->nf1_top[0] + p->T[0] - 1) / p->T[0];
+    p->nby = (p->nf1_top[1] + p->T[1] - 1) / p->T[1];
+    // tables
+    free_geometry(p);
+    p->geo_sig.clear();
+    p->pre_off.assign(3, 0);
+    p->tw_off.assign(3, 0);
+    size_t pre_total = 0, tw_total = 0;
+    for (int i = 0; i < p->d; ++i) {
+        p->pre_off[i] = pre_total;
+        pre_total += g.dim[i].nf1;
+        p->tw_off[i] = tw_total;
+        tw_total += g.dim[i].M;
+    }
+    CK(cudaMalloc(&p->d_pre, std::max<size_t>(pre_total, 1) * gs));
+    CK(cudaMalloc(&p->d_tw, std::max<size_t>(tw_total, 1) * es));
+    for (int i = 0; i < p->d; ++i) {
+        const DimGeom &dg = g.dim[i];
+        if (p->precision == FV_FP64) {
+            CK(launch_prescale_table<double>((double *)p->d_pre + p->pre_off[i], dg.nf1, dg.M, w, p->beta, p->d_glx,
+                                             p->d_glw, p->nq, p->stream));
+            CK(launch_twiddles<double>((cpx<double> *)p->d_tw + p->tw_off[i], dg.M, p->stream));
+        } else {
+            CK(launch_prescale_table<float>((float *)p->d_pre + p->pre_off[i], dg.nf1, dg.M, w, p->beta, p->d_glx,
+                                            p->d_glw, p->nq, p->stream));
+            CK(launch_twiddles<float>((cpx<float> *)p->d_tw + p->tw_off[i], dg.M, p->stream));
+        }
+    }
+    CK(cudaMalloc(&p->d_bas_M, M.size() * sizeof(double)));
+    CK(cudaMalloc(&p->d_bas_d, dK.size() * sizeof(double)));
+    CK(cudaMalloc(&p->d_bas_freq, nf * sizeof(double)));
+    CK(cudaMalloc(&p->d_bas_kappa, nf * sizeof(double)));
+    CK(cudaMalloc(&p->d_bas_shat, (size_t)std::max<long>(p->n_src, 1) * K * sizeof(double)));
+    CK(cudaMemcpyAsync(p->d_bas_M, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->d_bas_d, dK.data(), dK.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->d_bas_freq, p->freq.data(), nf * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->d_bas_kappa, kappa.data(), nf * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    // deconvolution of every target (u, q) on the device
+    const size_t nt_all = (size_t)p->n_u * nf;
+    CK(cudaMalloc(&p->d_bas_dec, std::max<size_t>(nt_all, 1) * sizeof(double)));
+    CK(launch_basis_deconv(p->d_bu, p->n_u, p->d_bas_kappa, nf, p->d, Dc, Xc, w, p->beta, p->sigma, p->d_glx,
+                           p->d_glw, p->nq, p->d_bas_dec, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    // workspace of one execution stream
+    const DimGeom *D = g.dim;
+    p->need = fv_plan_s::WsNeed{};
+    p->need.grid = (size_t)p->basis_Kp * D[0].nf1 * D[1].nf1 * D[2].nf1 * es;
+    p->need.bufA = (size_t)D[0].B * K * D[2].nf1 * D[1].nf1 * es;
+    p->need.bufB = (size_t)D[1].B * D[0].B * K * D[2].nf1 * es;
+    p->need.vu = std::max<size_t>(nt_all, 1) * sizeof(cpx<double>);
+    p->need.tiled = true;
+    p->need.n_src = std::max<long>(p->n_src, 1);
+    p->need.nb = p->nbx * p->nby;
+    p->need.frac_per_src = 3 * gs;
+    p->need.cs_per_src = (size_t)p->basis_Kp * es;
+    p->ws_bytes = (long long)(pre_total * gs + tw_total * es + (M.size() + dK.size() + 2 * nf + nt_all) * 8 +
+                              (size_t)p->need.n_src * K * 8 +
+                              p->n_streams * workspace_layout(p->need, nullptr, nullptr));
+    return FV_OK;
+}
+
+template <class G>
+fv_status run_basis(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, char *vis, size_t slice_bytes,
+                    int t_begin, int t_end)
+{
+    const int nf = (int)p->freq.size(), nt = (int)p->lst.size(), K = p->n_basis, Kp = p->basis_Kp;
+    const int np = p->basis_np;
+    cpx<G> *grid = (cpx<G> *)wk.grid;
+    cpx<G> *A = (cpx<G> *)wk.bufA, *Bb = (cpx<G> *)wk.bufB;
+    G *frac = (G *)wk.frac;
+    cpx<G> *cs = (cpx<G> *)wk.cs;
+    const G *pre = (const G *)p->d_pre;
+    const cpx<G> *tw = (const cpx<G> *)p->d_tw;
+    const double es = sizeof(cpx<G>);
+    const int nb = p->nbx * p->nby;
+    const double nvis = 0.5 * p->n_src;
+    const DimGeom *D = p->bg.dim;
+    const size_t plane = (size_t)D[0].nf1 * D[1].nf1 * D[2].nf1;
+    for (int t = t_begin; t < t_end; ++t) {
+        TimeBin tb{};
+        std::memcpy(tb.R, &p->Rt[(size_t)t * 9], 9 * sizeof(double));
+        for (int i = 0; i < 3; ++i) {
+            tb.C[i] = p->C[i];
+            tb.qscale_top[i] = p->qscale_top[i];
+            tb.nf1_top[i] = p->nf1_top[i];
+        }
+        tb.T[0] = p->T[0];
+        tb.T[1] = p->T[1];
+        tb.nbx = p->nbx;
+        tb.nby = p->nby;
+        CK(prof_begin(p, PC_BIN, st));
+        CK(launch_time_binning(p->d_e, p->n_src, tb, wk.bin_of, wk.counts, wk.offsets, wk.cursor, wk.sdir, wk.sidx,
+                               st));
+        CK(prof_end(p, (double)p->n_src * 80.0 + nb * 12.0));
+        for (const auto &gr : p->groups) {
+            if (gr.u1 <= gr.u0) continue;
+            SliceGeom g = p->bg;
+            std::memcpy(g.R, &p->Rt[(size_t)t * 9], 9 * sizeof(double));
+            if (!p->beams.empty()) {
+                g.beam = p->beams[gr.a];
+                g.beam2 = p->beams[gr.b];
+                g.two_beams = gr.a != gr.b;
+            } else {
+                g.two_beams = 0;
+            }
+            CK(prof_begin(p, PC_PREP, st));
+            CK(launch_prep_basis<G>(wk.sdir, wk.sidx, wk.offsets + nb, p->n_src, p->d_bas_shat, p->d_bas_M,
+                                    p->d_bas_d, p->d_bas_freq, nf, K, Kp, g, wk.cell, frac, cs, st));
+            CK(prof_end(p, nvis * (24.0 + 4.0 + K * 8.0 + 12.0 + 3.0 * sizeof(G) + Kp * es)));
+            for (int k0 = 0; k0 < Kp; k0 += np) {
+                CK(prof_begin(p, PC_SPREAD, st));
+                CK(launch_spread_tile<G>(wk.offsets, wk.cell, frac, cs + (size_t)k0 * p->n_src, p->n_src, g, tb, 1.0,
+                                         1.0, grid + (size_t)k0 * plane, st));
+                CK(prof_end(p, nvis * (12.0 + 3.0 * sizeof(G) + np * es) + np * plane * es));
+            }
+            const long r1 = (long)K * D[2].nf1 * D[1].nf1;
+            CK(prof_begin(p, PC_FFT_X, st));
+            CK(launch_fft_pass<G>(grid, A, r1, D[0], pre + p->pre_off[0], tw + p->tw_off[0], st));
+            CK(prof_end(p, (double)r1 * (D[0].nf1 + D[0].B) * es));
+            const long r2 = (long)D[0].B * K * D[2].nf1;
+            CK(prof_begin(p, PC_FFT_Y, st));
+            CK(launch_fft_pass<G>(A, Bb, r2, D[1], pre + p->pre_off[1], tw + p->tw_off[1], st));
+            CK(prof_end(p, (double)r2 * (D[1].nf1 + D[1].B) * es));
+            const int nug = gr.u1 - gr.u0;
+            CK(prof_begin(p, PC_INTERP, st));
+            CK(launch_interp_basis<G>(Bb, p->d_bu, gr.u0, nug, p->n_u, p->d_bas_kappa, nf, p->d_bas_M, K,
+                                      p->d_bas_dec, g, pre + p->pre_off[2], tw + p->tw_off[2], wk.Vu, st));
+            CK(prof_end(p, (double)nug * nf * ((double)p->w * p->w * K * D[2].nf1 * es + 8.0 + 16.0)));
+        }
+        CK(prof_begin(p, PC_SCATTER, st));
+        CK(launch_scatter_basis(wk.Vu, p->d_bl2u, p->n_bl, p->n_u, nf, nt, t, vis, slice_bytes,
+                                p->precision == FV_FP64, st));
+        CK(prof_end(p, (double)p->n_bl * nf * (4 + 16.0) + (double)slice_bytes * nf));
+    }
+    return FV_OK;
+}
+
+template fv_status run_basis<float>(fv_plan_s *, fv_plan_s::Workspace &, cudaStream_t, char *, size_t, int, int);
+template fv_status run_basis<double>(fv_plan_s *, fv_plan_s::Workspace &, cudaStream_t, char *, size_t, int, int);
+
 // All slices, t-major, split into contiguous chunks over the plan's streams
 // (each with its own workspace); the streams fork from and join back to the
 // plan's stream.
@@ -690,7 +928,12 @@ static fv_status execute_slices(fv_plan_s *p, char *vis, size_t slice_bytes)
         free_workspaces(p->ws);
         CK(alloc_workspaces(p->need, p->n_streams, p->ws));
     }
-    const long total = (long)p->freq.size() * p->lst.size();
+    // spectral-basis route: the unit of work is a time (all channels); the flux coefficients of this
+    // execution's flux come first, on the plan's stream, before the fork
+    const long total = p->use_basis ? (long)p->lst.size() : (long)p->freq.size() * p->lst.size();
+    if (p->use_basis)
+        CK(launch_basis_sky(p->flux, p->flux_fp64, p->n_src, (int)p->freq.size(), p->d_bas_M, p->n_basis,
+                            p->d_bas_shat, p->stream));
     const int S = (int)std::min<long>(p->n_streams, std::max<long>(total, 1));
     if (S > 1) {
         CK(cudaEventRecord(p->ev_fork, p->stream));
@@ -698,7 +941,8 @@ static fv_status execute_slices(fv_plan_s *p, char *vis, size_t slice_bytes)
     }
     for (int s = 0; s < S; ++s) {
         const long k0 = total * s / S, k1 = total * (s + 1) / S;
-        fv_status st = run_slices<G>(p, p->ws[s], p->sub[s], vis, slice_bytes, k0, k1);
+        fv_status st = p->use_basis ? run_basis<G>(p, p->ws[s], p->sub[s], vis, slice_bytes, (int)k0, (int)k1)
+                                    : run_slices<G>(p, p->ws[s], p->sub[s], vis, slice_bytes, k0, k1);
         if (st != FV_OK) return st;
     }
     if (S > 1) {
@@ -761,7 +1005,15 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
     if (o->spread_method < FV_SPREAD_AUTO || o->spread_method > FV_SPREAD_ATOMIC) return bad("unknown spread_method");
     if (o->n_streams < 0) return bad("n_streams < 0");
     if (o->fft_max_radix != 0 && o->fft_max_radix != 8 && o->fft_max_radix != 16) return bad("fft_max_radix must be 0, 8 or 16");
-    if (o->transform < FV_TRANSFORM_AUTO || o->transform > FV_TRANSFORM_LATTICE) return bad("unknown transform");
+    if (o->transform < FV_TRANSFORM_AUTO || o->transform > FV_TRANSFORM_BASIS) return bad("unknown transform");
+    if (o->transform == FV_TRANSFORM_BASIS) {
+        if (o->n_basis < 1 || o->n_basis > kBasisMax || o->n_basis > o->n_freq)
+            return bad("the spectral-basis route needs 1 <= n_basis <= min(16, n_freq)");
+        if (o->polarized) {
+            g_create_error = "the spectral-basis route is defined for unpolarised skies (Appendix A)";
+            return FV_ERR_UNSUPPORTED;
+        }
+    }
     if (o->transform == FV_TRANSFORM_LATTICE && o->dims == 3) return bad("the lattice route has no dims = 3 form");
     if (!(o->lattice_tol_m >= 0.0) || !std::isfinite(o->lattice_tol_m)) return bad("lattice_tol_m must be >= 0");
     double sigma = o->upsampfac == 0.0 ? 2.0 : o->upsampfac;
@@ -836,6 +1088,8 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
     // register count either way and prefers fewer stages
     p->fft_max_radix = o->fft_max_radix > 0 ? o->fft_max_radix : (o->precision == FV_MIXED ? 8 : 16);
     p->transform_req = o->transform;
+    p->use_basis = o->transform == FV_TRANSFORM_BASIS;
+    p->n_basis = p->use_basis ? o->n_basis : 0;
     p->lat_tol = o->lattice_tol_m > 0.0 ? o->lattice_tol_m : 1e-10;
     p->sub.assign(p->n_streams, nullptr);
     p->ev_join.assign(p->n_streams, nullptr);
@@ -1224,7 +1478,9 @@ fv_status fv_get_info(fv_plan_t p, fv_info *info)
         info->src_halfwidth[i] = p->S[i];
     }
     info->workspace_bytes = p->ws_bytes;
-    info->transform = p->use_lattice ? FV_TRANSFORM_LATTICE : FV_TRANSFORM_TYPE3;
+    info->transform = p->use_basis ? FV_TRANSFORM_BASIS : (p->use_lattice ? FV_TRANSFORM_LATTICE : FV_TRANSFORM_TYPE3);
+    info->basis_terms = p->use_basis ? p->n_basis : 0;
+    for (int i = 0; i < 3; ++i) info->basis_grid[i] = p->use_basis ? p->bg.dim[i].nf1 : 0;
     info->lattice = p->lat_ok ? 1 : 0;
     for (int k = 0; k < 2; ++k) {
         info->lattice_modes[k] = p->use_lattice ? 2 * p->lat_H[k] + 1 : 0;

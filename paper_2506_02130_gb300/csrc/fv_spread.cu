@@ -198,14 +198,14 @@ constexpr int kPatchX = 8, kPatchY = 4;     // one warp
 constexpr int kTileX = 32, kTileY = 8;      // one CTA (4 x 2 patches)
 constexpr int kPatches = 8;
 
-// resident CTAs per SM the register allocation must allow without spills (fewer for the 32
-// accumulators of polarised 3-D tiles)
-template <int NP, int NZ> struct GatherMinBlocks {
-    static constexpr int value = NP * NZ >= 32 ? 2 : 4;
+// resident CTAs per SM the register allocation must allow without spills (fewer when the complex
+// accumulators of a lane take 128 registers: 32 in FP32, 16 in FP64)
+template <class G, int NP, int NZ> struct GatherMinBlocks {
+    static constexpr int value = NP * NZ * (int)sizeof(G) >= 128 ? 2 : 4;
 };
 
 template <class G, int NP, int NZ>
-__global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<NP, NZ>::value)) k_spread_gather(const int *__restrict__ offsets,
+__global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::value)) k_spread_gather(const int *__restrict__ offsets,
                                                                   const int *__restrict__ cell,
                                                                   const G *__restrict__ frac,
                                                                   const cpx<G> *__restrict__ cs, long n_src,
@@ -379,7 +379,6 @@ int spread_gather_config(int elem_bytes, int n_pol, int nz, int w, int *nz_tmpl,
     if (NZ == 0) return 0;
     const int budget = elem_bytes == 4 ? 32 : 16;       // complex accumulators per lane
     if (n_pol * NZ > budget) return 0;
-    if (elem_bytes == 8 && NZ == 16) return 0;           // shared staging would exceed 48 KB
     *nz_tmpl = NZ;
     *bin_x = kPatchX;
     *bin_y = kPatchY;
@@ -398,9 +397,7 @@ cudaError_t launch_spread_tile(const int *offsets, const int *cell, const G *fra
     switch (key) {
     case 1: return gather_launch<G, 1, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
     case 8: return gather_launch<G, 1, 8>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
-    case 16:
-        if constexpr (sizeof(G) == 4) return gather_launch<G, 1, 16>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
-        else return cudaErrorInvalidValue;
+    case 16: return gather_launch<G, 1, 16>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
     case 101: return gather_launch<G, 4, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
     case 108:
         if constexpr (sizeof(G) == 4) return gather_launch<G, 4, 8>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);

@@ -62,6 +62,7 @@ extern "C" fv_status fv_execute_static(fv_plan_t p, void *vis)
     if (!p) return FV_ERR_ARG;
     if (!vis) return p->fail(FV_ERR_ARG, "vis is NULL");
     if (!p->have_array || !p->have_sky) return p->fail(FV_ERR_STATE, "fv_set_array and fv_set_sky must come first");
+    if (p->use_basis) return p->fail(FV_ERR_UNSUPPORTED, "a spectral-basis plan runs through fv_execute only");
     if (cudaSetDevice(p->device) != cudaSuccess) return p->fail(FV_ERR_CUDA, "cudaSetDevice failed");
     cudaPointerAttributes pa{};
     if (cudaPointerGetAttributes(&pa, vis) != cudaSuccess ||

@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_defaults(lib):
-    assert lib.fv_abi_version() == 2
+    assert lib.fv_abi_version() == 3
     o = fv.fv_opts_default()
     assert o.precision == fv.FV_FP64 and o.eps == 1e-10 and o.upsampfac == 2.0 and o.device == -1
     assert o.transform == 0 and o.lattice_tol_m == 0.0
