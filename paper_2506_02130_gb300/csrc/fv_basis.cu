@@ -1,6 +1,6 @@
 // Spectral-basis route (Appendix A): the basis, the per-source coefficient
-// kernels, the interpolation that expands the basis at every channel, the
-// per-target deconvolution and the scatter of all channels of a time.
+// kernels, the per-target constants, the interpolation that expands the
+// basis at every channel, and the scatter of all channels of a time.
 #include "fv_basis.cuh"
 #include "fv_plan.cuh"
 
@@ -59,18 +59,19 @@ cudaError_t launch_basis_sky(const void *flux, int flux_fp64, long n_src, int n_
 }
 
 // ------------------------------------------------------------------ per time: strengths (Eqs. A2-A3)
-// One thread per visible source.  Beam and coefficient arithmetic in FP64 (a few thousand operations
-// per source, small next to the spreading); the structure constants sit in shared memory, read as
-// broadcasts.
+// One thread per visible source.  The beam, its coefficients and the product coefficients are computed
+// in the grid precision G (the mixed path's strengths are FP32 anyway, and GB300's FP64 rate is a small
+// fraction of its FP32 rate); the prephase argument and the grid coordinates in FP64.  The structure
+// constants sit in shared memory, read as broadcasts.
 template <class G>
 __global__ void __launch_bounds__(128) k_prep_basis(const double *__restrict__ sdir, const int *__restrict__ sidx,
                                                     const int *__restrict__ nv_ptr, long n_src,
-                                                    const double *__restrict__ shat, const double *__restrict__ M,
-                                                    const double *__restrict__ dK, const double *__restrict__ freq,
+                                                    const double *__restrict__ shat, const G *__restrict__ M,
+                                                    const G *__restrict__ dK, const double *__restrict__ freq,
                                                     int n_freq, int K, int Kp, SliceGeom g, int *__restrict__ cell,
                                                     G *__restrict__ frac, cpx<G> *__restrict__ cs)
 {
-    __shared__ double s_d[kBasisMax * kBasisMax * kBasisMax];
+    __shared__ G s_d[kBasisMax * kBasisMax * kBasisMax];
     const int KKK = K * K * K;
     for (int e = threadIdx.x; e < KKK; e += blockDim.x) s_d[e] = dK[e];
     __syncthreads();
@@ -78,30 +79,30 @@ __global__ void __launch_bounds__(128) k_prep_basis(const double *__restrict__ s
     if (i >= *nv_ptr) return;
     const double s0 = sdir[i], s1 = sdir[n_src + i], s2 = sdir[2 * n_src + i];
     const long n = sidx[i];
-    const double rho = sqrt(s0 * s0 + s1 * s1);
+    const G rho = (G)sqrt(s0 * s0 + s1 * s1), up = (G)s2;
     // beam coefficients b_hat_k = sum_q M_qk B(nu_q)
-    double bh[kBasisMax];
+    G bh[kBasisMax];
 #pragma unroll
-    for (int k = 0; k < kBasisMax; ++k) bh[k] = 0.0;
+    for (int k = 0; k < kBasisMax; ++k) bh[k] = (G)0;
     for (int q = 0; q < n_freq; ++q) {
-        const double nu = freq[q];
-        const double A = voltage<double>(g.beam, rho, s2, nu);
-        const double B = g.two_beams ? A * voltage<double>(g.beam2, rho, s2, nu) : A * A;
+        const G nu = (G)freq[q];
+        const G A = voltage<G>(g.beam, rho, up, nu);
+        const G B = g.two_beams ? A * voltage<G>(g.beam2, rho, up, nu) : A * A;
 #pragma unroll
         for (int k = 0; k < kBasisMax; ++k)
             if (k < K) bh[k] += M[q * K + k] * B;
     }
     // v_k = sum_i s_hat_i sum_j b_hat_j d^k_ij
-    double v[kBasisMax];
+    G v[kBasisMax];
 #pragma unroll
-    for (int k = 0; k < kBasisMax; ++k) v[k] = 0.0;
+    for (int k = 0; k < kBasisMax; ++k) v[k] = (G)0;
     for (int a = 0; a < K; ++a) {
-        const double sa = shat[(size_t)n * K + a];
-        const double *da = s_d + a * K * K;
+        const G sa = (G)shat[(size_t)n * K + a];
+        const G *da = s_d + a * K * K;
 #pragma unroll
         for (int j = 0; j < kBasisMax; ++j) {
             if (j < K) {
-                const double c = sa * bh[j];
+                const G c = sa * bh[j];
 #pragma unroll
                 for (int k = 0; k < kBasisMax; ++k)
                     if (k < K) v[k] += c * da[j * K + k];
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(128) k_prep_basis(const double *__restrict__ s
     else { double a, b; sincos(ph, &a, &b); sp = (G)a; cp = (G)b; }
 #pragma unroll
     for (int k = 0; k < kBasisMax; ++k) {
-        if (k < K) cs[(size_t)k * n_src + i] = cmk<G>((G)v[k] * cp, (G)v[k] * sp);
+        if (k < K) cs[(size_t)k * n_src + i] = cmk<G>(v[k] * cp, v[k] * sp);
         else if (k < Kp) cs[(size_t)k * n_src + i] = cmk<G>((G)0, (G)0);
     }
     // grid coordinates, split in FP64
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(128) k_prep_basis(const double *__restrict__ s
 
 template <class G>
 cudaError_t launch_prep_basis(const double *sdir, const int *sidx, const int *nv_ptr, long n_src, const double *shat,
-                              const double *M, const double *dK, const double *freq, int n_freq, int K, int Kp,
+                              const G *M, const G *dK, const double *freq, int n_freq, int K, int Kp,
                               const SliceGeom &g, int *cell, G *frac, cpx<G> *cs, cudaStream_t st)
 {
     if (n_src <= 0) return cudaSuccess;
@@ -147,18 +148,72 @@ cudaError_t launch_prep_basis(const double *sdir, const int *sidx, const int *nv
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ per target constants
+// The targets (u, q) of a plan and its grid are the same at every time, so each target's footprint
+// origin m0 and offsets fr on the FFT grid (Section 2.2 step 3b) and the factor applied after the
+// interpolation, the deconvolution prod_i (4/w^2)/Phihat(a_i) times the postphase e^{i x.C}, are
+// computed once, in FP64: x = -kappa_q b_u, p = (x - D) M / (2 sigma X), m0 = ceil(p - w/2),
+// fr = p - m0, a = (x - D) / X * w pi / (2 sigma), Phihat by the plan's quadrature.
+template <class G>
+__global__ void k_basis_targets(const double *__restrict__ bu, int n_u, const double *__restrict__ kappa,
+                                int n_freq, SliceGeom g, double X0, double X1, double X2, double sigma,
+                                const double *__restrict__ gl_x, const double *__restrict__ gl_w, int nq,
+                                int4 *__restrict__ tm, G *__restrict__ tf, cpx<G> *__restrict__ ts)
+{
+    const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e >= (long)n_u * n_freq) return;
+    const int u = (int)(e / n_freq), q = (int)(e % n_freq);
+    const double Xc[3] = {X0, X1, X2};
+    const int w = g.w;
+    int m0[3] = {0, 0, 0};
+    double fr[3] = {0.0, 0.0, 0.0};
+    double r = 1.0, ph = 0.0;
+    for (int i = 0; i < g.d; ++i) {
+        const double x = -kappa[q] * bu[3 * u + i];
+        const double p = (x - g.dim[i].D) * g.dim[i].pscale;
+        const double m = ceil(p - 0.5 * w);
+        m0[i] = (int)m;
+        fr[i] = p - m;
+        const double a = (x - g.dim[i].D) / Xc[i] * (w * M_PI / (2.0 * sigma));
+        double phi_hat = 0.0;
+        for (int k = 0; k < nq; ++k) phi_hat += gl_w[k] * es_phi(gl_x[k], g.beta) * cos(a * gl_x[k]);
+        r *= (4.0 / ((double)w * w)) / phi_hat;
+        ph += x * g.dim[i].C;
+    }
+    double sp, cp;
+    sincos(ph, &sp, &cp);
+    tm[e] = make_int4(m0[0], m0[1], m0[2], 0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) tf[4 * e + i] = (G)fr[i];
+    tf[4 * e + 3] = (G)0;
+    ts[e] = cmk<G>((G)(r * cp), (G)(r * sp));
+}
+
+template <class G>
+cudaError_t launch_basis_targets(const double *bu, int n_u, const double *kappa, int n_freq, const SliceGeom &g,
+                                 const double *X, double sigma, const double *gl_x, const double *gl_w, int nq,
+                                 int4 *tm, G *tf, cpx<G> *ts, cudaStream_t st)
+{
+    const long n = (long)n_u * n_freq;
+    if (n <= 0) return cudaSuccess;
+    k_basis_targets<G><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(bu, n_u, kappa, n_freq, g, X[0], X[1], X[2],
+                                                                    sigma, gl_x, gl_w, nq, tm, tf, ts);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ interpolation with the expansion
 // One warp per target (u, q).  The band after the x and y passes holds, per (b_y, b_x) cell, the K
 // planes' z values contiguously ([k][l_z], K * Nz values).  Lane L holds the values j = L + 32 r
 // (r < R = ceil(K Nz / 32)) of that run, with the weights c_j = M_qk K(l_z), where
 // K(l_z) = sum_{m_z} phi((2/w)(p_z - m_z)) e^{2 pi i l_z m_z / M_z} (z prescale folded in) is the
 // direct z sum of the short z axis; each footprint tap is then R coalesced loads per warp, scaled by
-// the tap's x and y kernel values, and the warp reduces at the end.
+// the tap's x and y kernel values, and the warp reduces at the end.  The target's constants come from
+// the per-target table, so the kernel does no FP64 arithmetic.
 template <class G, bool HASZ>
-__global__ void __launch_bounds__(256) k_interp_basis(const cpx<G> *__restrict__ band, const double *__restrict__ bu,
-                                                      int u0, int n_ug, int n_u, const double *__restrict__ kappa,
-                                                      int n_freq, const double *__restrict__ M, int K,
-                                                      const double *__restrict__ dec, SliceGeom g,
+__global__ void __launch_bounds__(256) k_interp_basis(const cpx<G> *__restrict__ band, int u0, int n_ug, int n_u,
+                                                      int n_freq, const G *__restrict__ M, int K,
+                                                      const int4 *__restrict__ tm, const G *__restrict__ tf,
+                                                      const cpx<G> *__restrict__ ts, SliceGeom g,
                                                       const G *__restrict__ prez, const cpx<G> *__restrict__ twz,
                                                       cpx<double> *__restrict__ Vq)
 {
@@ -166,24 +221,12 @@ __global__ void __launch_bounds__(256) k_interp_basis(const cpx<G> *__restrict__
     const long tg = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
     if (tg >= (long)n_ug * n_freq) return;     // whole warps
     const int u = u0 + (int)(tg / n_freq), q = (int)(tg % n_freq);
+    const size_t tix = (size_t)u * n_freq + q;
     const int w = g.w;
     const G two_over_w = (G)(2.0 / w);
     const G beta = (G)g.beta;
-    const double kq = kappa[q];
-    double x[3] = {0.0, 0.0, 0.0};
-    G fr[3];
-    int m0[3] = {0, 0, 0};
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        fr[i] = (G)0;
-        if (i < g.d) {
-            x[i] = -kq * bu[3 * u + i];
-            const double p = (x[i] - g.dim[i].D) * g.dim[i].pscale;
-            const double m = ceil(p - 0.5 * w);
-            m0[i] = (int)m;
-            fr[i] = (G)(p - m);
-        }
-    }
+    const int4 mm = tm[tix];
+    const G frx = tf[4 * tix], fry = tf[4 * tix + 1], frz = tf[4 * tix + 2];
     const int Nz = HASZ ? g.dim[2].nf1 : 1;
     // lane lz < Nz builds K(l_z)
     cpx<G> Kmine = cmk<G>((G)1, (G)0);
@@ -191,12 +234,12 @@ __global__ void __launch_bounds__(256) k_interp_basis(const cpx<G> *__restrict__
         const int Mz = g.dim[2].M;
         const int lc = lane - Nz / 2;
         cpx<G> acc = cmk<G>((G)0, (G)0);
-        int e = (lc * m0[2]) % Mz;
+        int e = (lc * mm.z) % Mz;
         if (e < 0) e += Mz;
         int step = lc % Mz;
         if (step < 0) step += Mz;
         for (int jz = 0; jz < w; ++jz) {
-            const G wt = es_phi(two_over_w * (fr[2] - (G)jz), beta);
+            const G wt = es_phi(two_over_w * (frz - (G)jz), beta);
             acc = cadd(acc, cscale(twz[e], wt));
             e += step;
             if (e >= Mz) e -= Mz;
@@ -218,16 +261,16 @@ __global__ void __launch_bounds__(256) k_interp_basis(const cpx<G> *__restrict__
             const G kx = __shfl_sync(0xffffffffu, Kmine.x, lz);
             const G ky = __shfl_sync(0xffffffffu, Kmine.y, lz);
             if (valid) {
-                const G mk = (G)M[q * K + k];
+                const G mk = M[q * K + k];
                 cf[r] = cmk<G>(kx * mk, ky * mk);
             }
         }
     }
     const int Bx = g.dim[0].B;
-    const int bx0 = m0[0] + g.dim[0].H, by0 = m0[1] + g.dim[1].H;
+    const int bx0 = mm.x + g.dim[0].H, by0 = mm.y + g.dim[1].H;
     // x and y kernel values: lane j < w holds the j-th
-    const G wxm = lane < w ? es_phi(two_over_w * (fr[0] - (G)lane), beta) : (G)0;
-    const G wym = lane < w ? es_phi(two_over_w * (fr[1] - (G)lane), beta) : (G)0;
+    const G wxm = lane < w ? es_phi(two_over_w * (frx - (G)lane), beta) : (G)0;
+    const G wym = lane < w ? es_phi(two_over_w * (fry - (G)lane), beta) : (G)0;
     G ax = (G)0, ay = (G)0;
     for (int jy = 0; jy < w; ++jy) {
         const G wy = __shfl_sync(0xffffffffu, wym, jy);
@@ -254,22 +297,15 @@ __global__ void __launch_bounds__(256) k_interp_basis(const cpx<G> *__restrict__
         ay += __shfl_xor_sync(0xffffffffu, ay, o);
     }
     if (lane == 0) {
-        double ph = 0.0;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-            if (i < g.d) ph += x[i] * g.dim[i].C;
-        double sp, cp;
-        sincos(ph, &sp, &cp);
-        const double dk = dec[(size_t)u * n_freq + q];
-        const cpx<double> v = cmk<double>((double)ax * dk, (double)ay * dk);
-        Vq[(size_t)q * n_u + u] = cmul(v, cmk<double>(cp, sp));
+        const cpx<G> v = cmul(cmk<G>(ax, ay), ts[tix]);
+        Vq[(size_t)q * n_u + u] = cmk<double>((double)v.x, (double)v.y);
     }
 }
 
 template <class G>
-cudaError_t launch_interp_basis(const cpx<G> *band, const double *bu, int u0, int n_ug, int n_u, const double *kappa,
-                                int n_freq, const double *M, int K, const double *dec, const SliceGeom &g,
-                                const G *prez, const cpx<G> *twz, cpx<double> *Vq, cudaStream_t st)
+cudaError_t launch_interp_basis(const cpx<G> *band, int u0, int n_ug, int n_u, int n_freq, const G *M, int K,
+                                const int4 *tm, const G *tf, const cpx<G> *ts, const SliceGeom &g, const G *prez,
+                                const cpx<G> *twz, cpx<double> *Vq, cudaStream_t st)
 {
     if (n_ug <= 0) return cudaSuccess;
     const int Nz = g.d == 3 ? g.dim[2].nf1 : 1;
@@ -277,45 +313,11 @@ cudaError_t launch_interp_basis(const cpx<G> *band, const double *bu, int u0, in
     const long threads = (long)n_ug * n_freq * 32;
     const unsigned blocks = (unsigned)((threads + 255) / 256);
     if (g.d == 3)
-        k_interp_basis<G, true><<<blocks, 256, 0, st>>>(band, bu, u0, n_ug, n_u, kappa, n_freq, M, K, dec, g, prez,
-                                                        twz, Vq);
+        k_interp_basis<G, true><<<blocks, 256, 0, st>>>(band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz,
+                                                        Vq);
     else
-        k_interp_basis<G, false><<<blocks, 256, 0, st>>>(band, bu, u0, n_ug, n_u, kappa, n_freq, M, K, dec, g, prez,
-                                                         twz, Vq);
-    return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------ deconvolution of every target
-// dec[u * n_freq + q] = prod_i (4/w^2) / Phihat(a_i), a_i = (x_i - D_i) / X_i * w pi / (2 sigma) with
-// x = -kappa_q b_u, Phihat(k) = int_{-1}^{1} phi(z) cos(k z) dz by the plan's quadrature.
-__global__ void k_basis_deconv(const double *__restrict__ bu, int n_u, const double *__restrict__ kappa, int n_freq,
-                               int d, double D0, double D1, double D2, double X0, double X1, double X2, int w,
-                               double beta, double sigma, const double *__restrict__ gl_x,
-                               const double *__restrict__ gl_w, int nq, double *__restrict__ dec)
-{
-    const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (e >= (long)n_u * n_freq) return;
-    const int u = (int)(e / n_freq), q = (int)(e % n_freq);
-    const double Dc[3] = {D0, D1, D2}, Xc[3] = {X0, X1, X2};
-    double r = 1.0;
-    for (int i = 0; i < d; ++i) {
-        const double x = -kappa[q] * bu[3 * u + i];
-        const double a = (x - Dc[i]) / Xc[i] * (w * M_PI / (2.0 * sigma));
-        double ph = 0.0;
-        for (int k = 0; k < nq; ++k) ph += gl_w[k] * es_phi(gl_x[k], beta) * cos(a * gl_x[k]);
-        r *= (4.0 / ((double)w * w)) / ph;
-    }
-    dec[e] = r;
-}
-
-cudaError_t launch_basis_deconv(const double *bu, int n_u, const double *kappa, int n_freq, int d, const double *D,
-                                const double *X, int w, double beta, double sigma, const double *gl_x,
-                                const double *gl_w, int nq, double *dec, cudaStream_t st)
-{
-    const long n = (long)n_u * n_freq;
-    if (n <= 0) return cudaSuccess;
-    k_basis_deconv<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(bu, n_u, kappa, n_freq, d, D[0], D[1], D[2], X[0],
-                                                                 X[1], X[2], w, beta, sigma, gl_x, gl_w, nq, dec);
+        k_interp_basis<G, false><<<blocks, 256, 0, st>>>(band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz,
+                                                         Vq);
     return cudaGetLastError();
 }
 
@@ -346,17 +348,24 @@ cudaError_t launch_scatter_basis(const cpx<double> *Vq, const int *bl2u, int n_b
 }
 
 template cudaError_t launch_prep_basis<float>(const double *, const int *, const int *, long, const double *,
-                                              const double *, const double *, const double *, int, int, int,
+                                              const float *, const float *, const double *, int, int, int,
                                               const SliceGeom &, int *, float *, cpx<float> *, cudaStream_t);
 template cudaError_t launch_prep_basis<double>(const double *, const int *, const int *, long, const double *,
                                                const double *, const double *, const double *, int, int, int,
                                                const SliceGeom &, int *, double *, cpx<double> *, cudaStream_t);
-template cudaError_t launch_interp_basis<float>(const cpx<float> *, const double *, int, int, int, const double *, int,
-                                                const double *, int, const double *, const SliceGeom &,
+template cudaError_t launch_interp_basis<float>(const cpx<float> *, int, int, int, int, const float *, int,
+                                                const int4 *, const float *, const cpx<float> *, const SliceGeom &,
                                                 const float *, const cpx<float> *, cpx<double> *, cudaStream_t);
-template cudaError_t launch_interp_basis<double>(const cpx<double> *, const double *, int, int, int, const double *,
-                                                 int, const double *, int, const double *, const SliceGeom &,
-                                                 const double *, const cpx<double> *, cpx<double> *, cudaStream_t);
+template cudaError_t launch_interp_basis<double>(const cpx<double> *, int, int, int, int, const double *, int,
+                                                 const int4 *, const double *, const cpx<double> *,
+                                                 const SliceGeom &, const double *, const cpx<double> *,
+                                                 cpx<double> *, cudaStream_t);
+template cudaError_t launch_basis_targets<float>(const double *, int, const double *, int, const SliceGeom &,
+                                                 const double *, double, const double *, const double *, int, int4 *,
+                                                 float *, cpx<float> *, cudaStream_t);
+template cudaError_t launch_basis_targets<double>(const double *, int, const double *, int, const SliceGeom &,
+                                                  const double *, double, const double *, const double *, int,
+                                                  int4 *, double *, cpx<double> *, cudaStream_t);
 
 }  // namespace fv
 

@@ -22,28 +22,30 @@ cudaError_t launch_basis_sky(const void *flux, int flux_fp64, long n_src, int n_
 
 // Per visible source i < *nv_ptr (sorted order of the time binning): beam coefficients
 // b_hat = M^T B(nu_.) at its direction with the slice geometry's beams (Eq. A2), product coefficients
-// v_k = sum_ij s_hat_i b_hat_j d^k_ij (Eq. A3), prephase e^{i D.(s - C)} and grid coordinates.
-// cs: [Kp][n_src], planes K..Kp-1 zero.
+// v_k = sum_ij s_hat_i b_hat_j d^k_ij (Eq. A3), both in G; prephase e^{i D.(s - C)} and grid
+// coordinates.  M and dK are G copies of the basis and structure constants.  cs: [Kp][n_src], planes
+// K..Kp-1 zero.
 template <class G>
 cudaError_t launch_prep_basis(const double *sdir, const int *sidx, const int *nv_ptr, long n_src, const double *shat,
-                              const double *M, const double *dK, const double *freq, int n_freq, int K, int Kp,
+                              const G *M, const G *dK, const double *freq, int n_freq, int K, int Kp,
                               const SliceGeom &g, int *cell, G *frac, cpx<G> *cs, cudaStream_t st);
 
-// Targets (u, q) for u in [u0, u0 + n_ug) and every channel q: interpolation of the K planes of the
-// band ([b_y][b_x][k][l_z] after the x and y passes) at x = -kappa_q b_u, with the z sum done directly
-// (short z), combined with weights M_qk, deconvolved by dec[u * n_freq + q] and postphased by
-// e^{i x.C}.  Vq[q * n_u + u] receives the result.
+// Constants of every target t = u * n_freq + q of the one grid g (target centre D = g.dim[i].D,
+// half-extent X[i]): tm[t] = footprint origin (m0_x, m0_y, m0_z, 0) on the FFT grid, tf[4t + i] = offset
+// p_i - m0_i, ts[t] = prod_i (4/w^2)/Phihat(a_i) e^{i x.C} with x = -kappa_q b_u,
+// a_i = (x_i - D_i) / X_i * w pi / (2 sigma).
 template <class G>
-cudaError_t launch_interp_basis(const cpx<G> *band, const double *bu, int u0, int n_ug, int n_u, const double *kappa,
-                                int n_freq, const double *M, int K, const double *dec, const SliceGeom &g,
-                                const G *prez, const cpx<G> *twz, cpx<double> *Vq, cudaStream_t st);
+cudaError_t launch_basis_targets(const double *bu, int n_u, const double *kappa, int n_freq, const SliceGeom &g,
+                                 const double *X, double sigma, const double *gl_x, const double *gl_w, int nq,
+                                 int4 *tm, G *tf, cpx<G> *ts, cudaStream_t st);
 
-// Deconvolution factor of every target (u, q) of the one grid with target centre D and half-extent X
-// per dim: dec[u * n_freq + q] = prod_i (4/w^2) / Phihat(a_i), a_i = (x_i - D_i) / X_i * w pi / (2 sigma),
-// x = -kappa_q b_u.
-cudaError_t launch_basis_deconv(const double *bu, int n_u, const double *kappa, int n_freq, int d, const double *D,
-                                const double *X, int w, double beta, double sigma, const double *gl_x,
-                                const double *gl_w, int nq, double *dec, cudaStream_t st);
+// Targets (u, q) for u in [u0, u0 + n_ug) and every channel q: interpolation of the K planes of the
+// band ([b_y][b_x][k][l_z] after the x and y passes) with the z sum done directly (short z), combined
+// with weights M_qk, times the target's constant ts.  Vq[q * n_u + u] receives the result.
+template <class G>
+cudaError_t launch_interp_basis(const cpx<G> *band, int u0, int n_ug, int n_u, int n_freq, const G *M, int K,
+                                const int4 *tm, const G *tf, const cpx<G> *ts, const SliceGeom &g, const G *prez,
+                                const cpx<G> *twz, cpx<double> *Vq, cudaStream_t st);
 
 // Output slices (q, t) of every channel: vis + (q * n_time + t) * slice_bytes holds, for baseline bl,
 // Vq[q * n_u + bl2u[bl]] (complex64 or complex128).

@@ -130,7 +130,11 @@ struct fv_plan_s {
     double *d_bas_d = nullptr;        // [K][K][K] structure constants
     double *d_bas_freq = nullptr;     // [n_freq] Hz
     double *d_bas_kappa = nullptr;    // [n_freq] 2 pi nu / c
-    double *d_bas_dec = nullptr;      // [n_u][n_freq] deconvolution of each target
+    void *d_bas_Mg = nullptr;         // the basis and the structure constants in the grid precision
+    void *d_bas_dg = nullptr;
+    int4 *d_bas_tm = nullptr;         // per target (u, q): footprint origin on the FFT grid
+    void *d_bas_tf = nullptr;         //   offsets [4] in the grid precision
+    void *d_bas_ts = nullptr;         //   deconvolution x postphase (complex, grid precision)
     double *d_bas_shat = nullptr;     // [n_src][K] flux coefficients (recomputed by every execution)
 
     long long ws_bytes = 0;

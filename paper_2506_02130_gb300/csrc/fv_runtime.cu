@@ -209,7 +209,11 @@ static void free_geometry(fv_plan_s *p)
     dfree_t(p->d_bas_d);
     dfree_t(p->d_bas_freq);
     dfree_t(p->d_bas_kappa);
-    dfree_t(p->d_bas_dec);
+    dfree(p->d_bas_Mg);
+    dfree(p->d_bas_dg);
+    dfree_t(p->d_bas_tm);
+    dfree(p->d_bas_tf);
+    dfree(p->d_bas_ts);
     dfree_t(p->d_bas_shat);
     free_workspaces(p->ws);
 }
@@ -736,7 +740,7 @@ static fv_status prepare_basis(fv_plan_s *p)
     g.polarized = 0;
     g.n_stokes = 1;
     g.beam = p->beam;
-    double Dc[3] = {0, 0, 0}, Xc[3] = {1, 1, 1};
+    double Xc[3] = {1, 1, 1};
     for (int i = 0; i < 3; ++i) {
         DimGeom &dg = g.dim[i];
         if (i >= p->d) {
@@ -750,7 +754,6 @@ static fv_status prepare_basis(fv_plan_s *p)
         if (ds != FV_OK) return ds;
         dg.D = 0.5 * (xhi + xlo);
         dg.C = p->C[i];
-        Dc[i] = dg.D;
         Xc[i] = dg.qscale * M_PI / p->sigma;      // the half-extent the geometry used (after the X = 0 fix-up)
     }
     const int nz = p->d == 3 ? g.dim[2].nf1 : 1;
@@ -814,11 +817,27 @@ static fv_status prepare_basis(fv_plan_s *p)
     CK(cudaMemcpyAsync(p->d_bas_d, dK.data(), dK.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream));
     CK(cudaMemcpyAsync(p->d_bas_freq, p->freq.data(), nf * sizeof(double), cudaMemcpyHostToDevice, p->stream));
     CK(cudaMemcpyAsync(p->d_bas_kappa, kappa.data(), nf * sizeof(double), cudaMemcpyHostToDevice, p->stream));
-    // deconvolution of every target (u, q) on the device
+    // the basis and structure constants in the grid precision, and the constants of every target (u, q)
+    std::vector<float> Mf(M.begin(), M.end()), dKf(dK.begin(), dK.end());
+    CK(cudaMalloc(&p->d_bas_Mg, M.size() * gs));
+    CK(cudaMalloc(&p->d_bas_dg, dK.size() * gs));
     const size_t nt_all = (size_t)p->n_u * nf;
-    CK(cudaMalloc(&p->d_bas_dec, std::max<size_t>(nt_all, 1) * sizeof(double)));
-    CK(launch_basis_deconv(p->d_bu, p->n_u, p->d_bas_kappa, nf, p->d, Dc, Xc, w, p->beta, p->sigma, p->d_glx,
-                           p->d_glw, p->nq, p->d_bas_dec, p->stream));
+    CK(cudaMalloc(&p->d_bas_tm, std::max<size_t>(nt_all, 1) * sizeof(int4)));
+    CK(cudaMalloc(&p->d_bas_tf, std::max<size_t>(nt_all, 1) * 4 * gs));
+    CK(cudaMalloc(&p->d_bas_ts, std::max<size_t>(nt_all, 1) * es));
+    if (p->precision == FV_FP64) {
+        CK(cudaMemcpyAsync(p->d_bas_Mg, M.data(), M.size() * gs, cudaMemcpyHostToDevice, p->stream));
+        CK(cudaMemcpyAsync(p->d_bas_dg, dK.data(), dK.size() * gs, cudaMemcpyHostToDevice, p->stream));
+        CK(launch_basis_targets<double>(p->d_bu, p->n_u, p->d_bas_kappa, nf, g, Xc, p->sigma, p->d_glx, p->d_glw,
+                                        p->nq, p->d_bas_tm, (double *)p->d_bas_tf, (cpx<double> *)p->d_bas_ts,
+                                        p->stream));
+    } else {
+        CK(cudaMemcpyAsync(p->d_bas_Mg, Mf.data(), M.size() * gs, cudaMemcpyHostToDevice, p->stream));
+        CK(cudaMemcpyAsync(p->d_bas_dg, dKf.data(), dK.size() * gs, cudaMemcpyHostToDevice, p->stream));
+        CK(launch_basis_targets<float>(p->d_bu, p->n_u, p->d_bas_kappa, nf, g, Xc, p->sigma, p->d_glx, p->d_glw,
+                                       p->nq, p->d_bas_tm, (float *)p->d_bas_tf, (cpx<float> *)p->d_bas_ts,
+                                       p->stream));
+    }
     CK(cudaStreamSynchronize(p->stream));
     // workspace of one execution stream
     const DimGeom *D = g.dim;
@@ -832,7 +851,8 @@ static fv_status prepare_basis(fv_plan_s *p)
     p->need.nb = p->nbx * p->nby;
     p->need.frac_per_src = 3 * gs;
     p->need.cs_per_src = (size_t)p->basis_Kp * es;
-    p->ws_bytes = (long long)(pre_total * gs + tw_total * es + (M.size() + dK.size() + 2 * nf + nt_all) * 8 +
+    p->ws_bytes = (long long)(pre_total * gs + tw_total * es + (M.size() + dK.size() + 2 * nf) * (8 + gs) +
+                              nt_all * (sizeof(int4) + 4 * gs + es) +
                               (size_t)p->need.n_src * K * 8 +
                               p->n_streams * workspace_layout(p->need, nullptr, nullptr));
     return FV_OK;
@@ -883,8 +903,8 @@ fv_status run_basis(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, cha
                 g.two_beams = 0;
             }
             CK(prof_begin(p, PC_PREP, st));
-            CK(launch_prep_basis<G>(wk.sdir, wk.sidx, wk.offsets + nb, p->n_src, p->d_bas_shat, p->d_bas_M,
-                                    p->d_bas_d, p->d_bas_freq, nf, K, Kp, g, wk.cell, frac, cs, st));
+            CK(launch_prep_basis<G>(wk.sdir, wk.sidx, wk.offsets + nb, p->n_src, p->d_bas_shat, (const G *)p->d_bas_Mg,
+                                    (const G *)p->d_bas_dg, p->d_bas_freq, nf, K, Kp, g, wk.cell, frac, cs, st));
             CK(prof_end(p, nvis * (24.0 + 4.0 + K * 8.0 + 12.0 + 3.0 * sizeof(G) + Kp * es)));
             for (int k0 = 0; k0 < Kp; k0 += np) {
                 CK(prof_begin(p, PC_SPREAD, st));
@@ -902,9 +922,10 @@ fv_status run_basis(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, cha
             CK(prof_end(p, (double)r2 * (D[1].nf1 + D[1].B) * es));
             const int nug = gr.u1 - gr.u0;
             CK(prof_begin(p, PC_INTERP, st));
-            CK(launch_interp_basis<G>(Bb, p->d_bu, gr.u0, nug, p->n_u, p->d_bas_kappa, nf, p->d_bas_M, K,
-                                      p->d_bas_dec, g, pre + p->pre_off[2], tw + p->tw_off[2], wk.Vu, st));
-            CK(prof_end(p, (double)nug * nf * ((double)p->w * p->w * K * D[2].nf1 * es + 8.0 + 16.0)));
+            CK(launch_interp_basis<G>(Bb, gr.u0, nug, p->n_u, nf, (const G *)p->d_bas_Mg, K, p->d_bas_tm,
+                                      (const G *)p->d_bas_tf, (const cpx<G> *)p->d_bas_ts, g, pre + p->pre_off[2],
+                                      tw + p->tw_off[2], wk.Vu, st));
+            CK(prof_end(p, (double)nug * nf * ((double)p->w * p->w * K * D[2].nf1 * es + 16.0 + 4.0 * sizeof(G) + es + 16.0)));
         }
         CK(prof_begin(p, PC_SCATTER, st));
         CK(launch_scatter_basis(wk.Vu, p->d_bl2u, p->n_bl, p->n_u, nf, nt, t, vis, slice_bytes,
