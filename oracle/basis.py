@@ -18,8 +18,9 @@ steps in the appendix's order, in plain numpy:
   3. at each time, the beam b at every visible source and channel, and its
      coefficients b_hat = (M^T M)^{-1} M^T b (Eq. A2).  The appendix
      interpolates coefficients stored on a beam grid to the source
-     positions; for the analytic beams here the coefficients at the exact
-     position are computed instead.  b is the power beam |A|^2, or A_i A_j
+     positions; here the beam is evaluated at each source's position at every
+     channel (analytic, or bilinear in a gridded beam's samples, Section 2.4)
+     and projected.  b is the power beam |A|^2, or A_i A_j
      for a baseline whose antennas carry different beams (Section 2.2.3);
   4. the product coefficients v_k = sum_ij s_hat_i b_hat_j d^k_ij with the
      structure constants d^k_ij = sum_q M_qi M_qj M_qk (Eqs. A3-A4);
@@ -37,7 +38,7 @@ from dataclasses import replace
 
 import numpy as np
 
-from .oracle import OracleProblem, oracle_enu, oracle_vis, oracle_voltage
+from .oracle import OracleProblem, oracle_enu, oracle_vis, oracle_voltage, oracle_voltage_grid
 
 
 def basis_matrix(freqs_hz, K: int) -> np.ndarray:
@@ -80,10 +81,18 @@ def _beam_groups(p: OracleProblem):
     return out
 
 
-def _voltages(p: OracleProblem, beam: int, theta: np.ndarray) -> np.ndarray:
-    """[n_src][N_nu] voltage of beam `beam` (index into p.beams, or the plan's beam)."""
-    kind, param = (p.beams[beam] if p.beams and p.beam_of_ant is not None else (p.beam, p.beam_param))
+def _voltages(p: OracleProblem, beam: int, theta: np.ndarray, az: np.ndarray) -> np.ndarray:
+    """[n_src][N_nu] voltage of beam `beam` (index into p.beams, or the plan's beam); gridded beams
+    (Section 2.4) by the oracle's bilinear interpolation of their samples at each channel."""
+    per_antenna = bool(p.beams) and p.beam_of_ant is not None
+    kind, param = p.beams[beam] if per_antenna else (p.beam, p.beam_param)
     out = np.empty((len(theta), len(p.freqs_hz)))
+    if kind == "grid":
+        G = np.asarray(p.beam_grids[beam if per_antenna else -1], dtype=np.float64)
+        for n, (th, a) in enumerate(zip(theta, az)):
+            for q in range(len(p.freqs_hz)):
+                out[n, q] = oracle_voltage_grid(G[q], float(th), float(a))
+        return out
     for n, th in enumerate(theta):
         for q, nu in enumerate(p.freqs_hz):
             out[n, q] = oracle_voltage(kind, param, float(th), float(nu))
@@ -100,8 +109,9 @@ def basis_strengths(p: OracleProblem, M: np.ndarray, t: int, beams=(0, 0)):
                      for r, de in zip(p.ra, p.dec)]).reshape(-1, 3)
     vis = np.nonzero(dirs[:, 2] > 0.0)[0]
     theta = np.arccos(np.minimum(dirs[vis, 2], 1.0))
-    A = _voltages(p, beams[0], theta)
-    B = A * A if beams[0] == beams[1] else A * _voltages(p, beams[1], theta)
+    az = np.arctan2(dirs[vis, 0], dirs[vis, 1])
+    A = _voltages(p, beams[0], theta, az)
+    B = A * A if beams[0] == beams[1] else A * _voltages(p, beams[1], theta, az)
     b_hat = project(M, B)
     v = product_coefficients(s_hat[vis], b_hat, d)
     return vis, v @ M.T                                    # [n_vis][N_nu]
@@ -120,6 +130,6 @@ def basis_vis(p: OracleProblem, K: int | None = None, M: np.ndarray | None = Non
                 continue
             sub = replace(p, pairs=np.asarray(p.pairs)[bls], ra=np.asarray(p.ra)[vis], dec=np.asarray(p.dec)[vis],
                           flux=c[None], lsts_rad=np.asarray(p.lsts_rad)[t:t + 1], beam="uniform",
-                          beam_param=(), polarized=False, beams=None, beam_of_ant=None)
+                          beam_param=(), polarized=False, beams=None, beam_of_ant=None, beam_grids=None)
             out[:, t, bls, :] = oracle_vis(sub, mode)[:, 0]
     return out

@@ -38,7 +38,11 @@
  *    J_a = A_{b(a)}(theta) R(az), so the product of baseline (i, j) is
  *    J_i C J_j^dagger = A_{b(i)} A_{b(j)} R C R^dagger; evaluated as the
  *    unit-beam strengths times the two voltages, per baseline (literal) or
- *    folded into the antenna phasors (factored).
+ *    folded into the antenna phasors (factored);
+ *  - gridded (numerical) beams (Section 2.4): voltage samples per channel on
+ *    a regular grid of zenith angle (zenith to horizon) and azimuth (east of
+ *    north, periodic), interpolated bilinearly; they enter as per-antenna
+ *    beams (one gridded beam for every antenna is the shared-beam case).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -54,6 +58,7 @@
 #define ORACLE_BEAM_GAUSS 0
 #define ORACLE_BEAM_AIRY 1
 #define ORACLE_BEAM_UNIFORM 2
+#define ORACLE_BEAM_GRID 3
 
 typedef struct {
     int n_ant;
@@ -79,6 +84,11 @@ typedef struct {
     const int *beam_kinds;
     const double *beam_params;
     const int *beam_of_ant;
+    /* gridded beams (Section 2.4, numerical beams): beam k of kind ORACLE_BEAM_GRID has voltage samples
+     * beam_grids[((k * n_freq + f) * grid_n_theta + i) * grid_n_phi + j] at zenith angle
+     * i (pi/2) / (grid_n_theta - 1) and azimuth j 2 pi / grid_n_phi (east of north), channel f */
+    int grid_n_theta, grid_n_phi;
+    const double *beam_grids;
 } oracle_problem;
 
 /* Equatorial (ra, dec) to topocentric East-North-Up unit vector at local
@@ -95,6 +105,28 @@ void oracle_enu(double ra, double dec, double lst, double lat, double *out3)
     out3[0] = -cd * sh;
     out3[1] = sd * cl - cd * ch * sl;
     out3[2] = sd * sl + cd * ch * cl;
+}
+
+/* Voltage of a gridded beam at zenith angle theta and azimuth az (east of north) by bilinear
+ * interpolation (Section 2.4, numerical beams; bilinear is the lowest order the section names) in the
+ * samples plane[i * n_phi + j] at theta_i = i (pi/2) / (n_theta - 1), az_j = j 2 pi / n_phi, the
+ * azimuth periodic. */
+double oracle_voltage_grid(const double *plane, int n_theta, int n_phi, double theta, double az)
+{
+    const double dth = (M_PI / 2.0) / (n_theta - 1), dph = 2.0 * M_PI / n_phi;
+    double u = theta / dth;
+    int i = (int)floor(u);
+    if (i > n_theta - 2) i = n_theta - 2;
+    if (i < 0) i = 0;
+    const double a = u - i;
+    double azw = fmod(az, 2.0 * M_PI);
+    if (azw < 0.0) azw += 2.0 * M_PI;
+    const double v = azw / dph;
+    int j = (int)floor(v);
+    const double b = v - j;
+    const int j0 = ((j % n_phi) + n_phi) % n_phi, j1 = (j0 + 1) % n_phi;
+    return (1.0 - a) * (1.0 - b) * plane[i * n_phi + j0] + (1.0 - a) * b * plane[i * n_phi + j1] +
+           a * (1.0 - b) * plane[(i + 1) * n_phi + j0] + a * b * plane[(i + 1) * n_phi + j1];
 }
 
 /* Scalar voltage response A(theta, nu) of the beam (Section 2.4, analytic beams). */
@@ -217,8 +249,14 @@ int oracle_vis(const oracle_problem *P, double *vis, int mode, int n_threads)
                     oracle_strength(ORACLE_BEAM_UNIFORM, none, P->polarized, &dir[3 * v], nu, st,
                                     &str[2 * n_pol * v]);
                     double theta = acos(dir[3 * v + 2] > 1.0 ? 1.0 : dir[3 * v + 2]);
+                    double az = atan2(dir[3 * v], dir[3 * v + 1]);
                     for (int k = 0; k < nbeam; ++k)
-                        volt[(size_t)v * nbeam + k] = oracle_voltage(P->beam_kinds[k], &P->beam_params[3 * k], theta, nu);
+                        volt[(size_t)v * nbeam + k] =
+                            P->beam_kinds[k] == ORACLE_BEAM_GRID
+                                ? oracle_voltage_grid(P->beam_grids + ((size_t)k * P->n_freq + f) *
+                                                                          P->grid_n_theta * P->grid_n_phi,
+                                                      P->grid_n_theta, P->grid_n_phi, theta, az)
+                                : oracle_voltage(P->beam_kinds[k], &P->beam_params[3 * k], theta, nu);
                 }
             }
             double *out = vis + (((size_t)f * P->n_time + t) * P->n_bl) * n_pol * 2;

@@ -5,7 +5,7 @@ import ctypes as C
 import os
 import subprocess
 import threading
-from dataclasses import dataclass
+from dataclasses import dataclass, replace
 
 import numpy as np
 
@@ -15,7 +15,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-BEAMS = {"gauss": 0, "airy": 1, "uniform": 2}
+BEAMS = {"gauss": 0, "airy": 1, "uniform": 2, "grid": 3}
 
 
 def build(force: bool = False) -> str:
@@ -39,7 +39,8 @@ class _Problem(C.Structure):
                 ("latitude_rad", C.c_double), ("beam_kind", C.c_int),
                 ("beam_param", C.c_double * 3), ("polarized", C.c_int),
                 ("n_beams", C.c_int), ("beam_kinds", C.POINTER(C.c_int)),
-                ("beam_params", C.POINTER(C.c_double)), ("beam_of_ant", C.POINTER(C.c_int))]
+                ("beam_params", C.POINTER(C.c_double)), ("beam_of_ant", C.POINTER(C.c_int)),
+                ("grid_n_theta", C.c_int), ("grid_n_phi", C.c_int), ("beam_grids", C.POINTER(C.c_double))]
 
 
 def _load():
@@ -58,6 +59,8 @@ def _load():
                                             C.POINTER(C.c_double), C.POINTER(C.c_double)]
             lib.oracle_strength.restype = None
             lib.oracle_max_threads.restype = C.c_int
+            lib.oracle_voltage_grid.argtypes = [C.POINTER(C.c_double), C.c_int, C.c_int, C.c_double, C.c_double]
+            lib.oracle_voltage_grid.restype = C.c_double
             _lib = lib
     return _lib
 
@@ -82,6 +85,9 @@ class OracleProblem:
     # per-antenna beams: [(kind, params), ...] and the beam index of every antenna (None: one beam)
     beams: list | None = None
     beam_of_ant: np.ndarray | None = None
+    # gridded beams: voltage samples [n_freq][n_theta][n_phi] of the plan's beam (beam == "grid") and of
+    # per-antenna beam k (beams[k] == ("grid", ())), keyed by beam index (-1: the plan's beam)
+    beam_grids: dict | None = None
 
     @classmethod
     def from_workload(cls, prob, pairs=None, freq_idx=None, time_idx=None, src_idx=None):
@@ -98,9 +104,12 @@ class OracleProblem:
             flux = flux[:, :, freq_idx]
         if time_idx is not None:
             lsts = lsts[time_idx]
+        grids = getattr(prob, "beam_grids", None)
+        if grids is not None and freq_idx is not None:
+            grids = {k: np.asarray(v)[freq_idx] for k, v in grids.items()}
         return cls(prob.ant_enu, prob.pairs if pairs is None else pairs, ra, dec, flux, freqs,
                    lsts, prob.latitude_rad, prob.beam, tuple(prob.beam_param), prob.polarized,
-                   getattr(prob, "beams", None), getattr(prob, "beam_of_ant", None))
+                   getattr(prob, "beams", None), getattr(prob, "beam_of_ant", None), grids)
 
 
 def oracle_vis(p: OracleProblem, mode: str = "factored", n_threads: int = 0) -> np.ndarray:
@@ -116,6 +125,13 @@ def oracle_vis(p: OracleProblem, mode: str = "factored", n_threads: int = 0) -> 
     n_pol = 4 if p.polarized else 1
     bp = (C.c_double * 3)(*(list(p.beam_param) + [0.0] * (3 - len(p.beam_param))))
     nb, kinds_p, params_p, boa_p = 0, None, None, None
+    grids = p.beam_grids or {}
+    if p.beam == "grid" and not (p.beam_of_ant is not None and p.beams):
+        # one gridded beam for every antenna: the per-antenna form with a single beam
+        p = replace(p, beams=[("grid", ())], beam_of_ant=np.zeros(len(ant), dtype=np.int32),
+                    beam_grids={0: grids[-1]})
+        grids = p.beam_grids
+    gth, gph, grid_p = 0, 0, None
     if p.beam_of_ant is not None and p.beams:
         kinds = np.ascontiguousarray([BEAMS[k] for k, _ in p.beams], dtype=np.int32)
         params = np.ascontiguousarray([list(v) + [0.0] * (3 - len(v)) for _, v in p.beams], dtype=np.float64)
@@ -124,11 +140,21 @@ def oracle_vis(p: OracleProblem, mode: str = "factored", n_threads: int = 0) -> 
             raise ValueError("beam_of_ant needs one entry per antenna")
         nb, kinds_p, params_p = len(kinds), kinds.ctypes.data_as(C.POINTER(C.c_int)), _p(params)
         boa_p = boa.ctypes.data_as(C.POINTER(C.c_int))
-        keep = (kinds, params, boa)                      # alive for the call
+        gridded = [k for k, (kind, _) in enumerate(p.beams) if kind == "grid"]
+        if gridded:
+            shape = np.asarray(grids[gridded[0]]).shape
+            if len(shape) != 3 or shape[0] != len(freqs):
+                raise ValueError("gridded beams need [n_freq][n_theta][n_phi] samples")
+            allg = np.zeros((len(kinds),) + shape)
+            for k in gridded:
+                allg[k] = np.asarray(grids[k], dtype=np.float64)
+            allg = np.ascontiguousarray(allg)
+            gth, gph, grid_p = shape[1], shape[2], _p(allg)
+        keep = (kinds, params, boa, grid_p and allg)     # alive for the call
     prob = _Problem(len(ant), _p(ant), len(pairs), pairs.ctypes.data_as(C.POINTER(C.c_int)),
                     len(ra), _p(ra), _p(dec), flux.shape[0], _p(flux), len(freqs), _p(freqs),
                     len(lsts), _p(lsts), float(p.latitude_rad), BEAMS[p.beam], bp,
-                    1 if p.polarized else 0, nb, kinds_p, params_p, boa_p)
+                    1 if p.polarized else 0, nb, kinds_p, params_p, boa_p, gth, gph, grid_p)
     out = np.zeros((len(freqs), len(lsts), len(pairs), n_pol, 2), dtype=np.float64)
     rc = lib.oracle_vis(C.byref(prob), _p(out), 0 if mode == "literal" else 1, int(n_threads))
     if rc != 0:
@@ -155,6 +181,12 @@ def oracle_strength(beam: str, param, polarized: bool, s, nu: float, stokes) -> 
     out = np.zeros(2 * n_pol)
     _load().oracle_strength(BEAMS[beam], _p(bp), 1 if polarized else 0, _p(s), nu, _p(st), _p(out))
     return out[0::2] + 1j * out[1::2]
+
+
+def oracle_voltage_grid(plane, theta: float, az: float) -> float:
+    """Bilinear voltage of a gridded beam's samples plane[n_theta][n_phi] (see oracle.c)."""
+    a = np.ascontiguousarray(plane, dtype=np.float64)
+    return _load().oracle_voltage_grid(_p(a), a.shape[0], a.shape[1], float(theta), float(az))
 
 
 def max_threads() -> int:

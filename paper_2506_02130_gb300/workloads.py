@@ -344,6 +344,9 @@ class Problem:
     # per-antenna beams (Section 2.2.3): [(kind, params), ...] and the beam index of every antenna
     beams: list | None = None
     beam_of_ant: np.ndarray | None = None
+    # gridded beams (Section 2.4, numerical beams): voltage samples [n_freq][n_theta][n_phi] of the
+    # plan's beam (key -1, with beam == "grid") or of per-antenna beam k (beams[k] == ("grid", ()))
+    beam_grids: dict | None = None
 
     @property
     def n_vis(self) -> int:
@@ -351,6 +354,19 @@ class Problem:
 
 
 GAUSS_FWHM_150 = (math.radians(10.0), 150e6)   # 10 deg FWHM at 150 MHz, scaling as 1/nu
+
+
+def grid_beam(freqs_hz: np.ndarray, n_theta: int, n_phi: int, fwhm_ref_rad: float = np.radians(10.0),
+              ref_hz: float = 150e6, ellipticity: float = 0.0) -> np.ndarray:
+    """Synthetic numerical beam standing in for a simulated (CST/HFSS-style) beam file: voltage samples
+    [n_freq][n_theta][n_phi] on the grid theta_i = i (pi/2) / (n_theta - 1) (zenith angle, zenith to
+    horizon) x phi_j = j 2 pi / n_phi (azimuth east of north) of an elliptical Gaussian power pattern
+    exp(-4 ln2 theta^2 / FWHM^2), FWHM = fwhm_ref (ref / nu) (1 + ellipticity cos 2 phi)."""
+    th = np.linspace(0.0, np.pi / 2, n_theta)
+    ph = np.arange(n_phi) * (2 * np.pi / n_phi)
+    nu = np.asarray(freqs_hz, dtype=np.float64)
+    fwhm = fwhm_ref_rad * (ref_hz / nu)[:, None, None] * (1.0 + ellipticity * np.cos(2 * ph))[None, None, :]
+    return np.sqrt(np.exp(-4.0 * np.log(2.0) * th[None, :, None] ** 2 / fwhm ** 2))
 
 
 def config_small(seed: int = 0, n_src: int = 1000, eps: float = 1e-10) -> Problem:

@@ -107,3 +107,10 @@ def test_truncation_error_vanishes_as_the_basis_completes():
     errs = [rel_l2(basis_vis(p, K), ref) for K in (2, 4, 6, 8)]
     assert errs[3] < 1e-12
     assert errs[2] < errs[0]
+
+
+def test_complete_basis_with_a_gridded_beam():
+    p = _problem(n_chan=5)
+    p = replace(p, beam="grid", beam_grids={-1: W.grid_beam(p.freqs_hz, 31, 12, math.radians(40.0), 150e6,
+                                                           ellipticity=0.3)})
+    assert rel_l2(basis_vis(p, len(p.freqs_hz)), oracle_vis(p, "literal")) < 1e-12

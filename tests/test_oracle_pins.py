@@ -347,3 +347,69 @@ def test_per_antenna_beams_polarised_is_Ji_C_Jj_dagger():
             M = Ji @ Cm @ Jj.conj().T
             ph = np.exp(-2j * math.pi * nu * np.dot(p.ant_enu[i] - p.ant_enu[j], s) / C)
             np.testing.assert_allclose(v[f, 0, b], M.ravel() * ph, rtol=0, atol=1e-12 * I)
+
+
+# ---------------------------------------------------------------- gridded beams (Section 2.4)
+def test_grid_beam_nodes_rows_and_azimuth_wrap():
+    from oracle.oracle import oracle_voltage_grid
+    rng = np.random.default_rng(21)
+    nth, nph = 7, 6
+    T = rng.uniform(0.1, 1.0, size=(nth, nph))
+    dth, dph = (math.pi / 2) / (nth - 1), 2 * math.pi / nph
+    for i in range(nth - 1):
+        for j in range(nph):
+            assert oracle_voltage_grid(T, i * dth, j * dph) == pytest.approx(T[i, j], abs=1e-15)
+    # halfway between two rows, on a column: the mean of the two samples
+    assert oracle_voltage_grid(T, 2.5 * dth, 4 * dph) == pytest.approx(0.5 * (T[2, 4] + T[3, 4]), abs=1e-14)
+    # the azimuth is periodic: between the last column and column 0, from either side of 2 pi
+    mid = 0.5 * (T[3, nph - 1] + T[3, 0])
+    assert oracle_voltage_grid(T, 3 * dth, 2 * math.pi - 0.5 * dph) == pytest.approx(mid, abs=1e-14)
+    assert oracle_voltage_grid(T, 3 * dth, -0.5 * dph) == pytest.approx(mid, abs=1e-14)
+    # linear in theta and constant in azimuth is reproduced exactly anywhere
+    L = np.repeat((0.9 - 0.4 * np.arange(nth) * dth)[:, None], nph, axis=1)
+    for th, az in [(0.123, 0.3), (1.4, 5.9), (0.77, 2.2)]:
+        assert oracle_voltage_grid(L, th, az) == pytest.approx(0.9 - 0.4 * th, abs=1e-14)
+
+
+def test_grid_beam_azimuth_is_measured_east_of_north():
+    from oracle.oracle import oracle_voltage_grid
+    freqs = np.array([150e6])
+    G = W.grid_beam(freqs, 361, 360, math.radians(20.0), 150e6, ellipticity=0.4)[0]
+    th = math.radians(12.0)
+    # due north (az 0) the pattern is 1.4x wider than due east (az 90 deg): compare the two directions
+    for az, e in [(0.0, 1.4), (math.pi / 2, 0.6)]:
+        fwhm = math.radians(20.0) * e
+        want = math.sqrt(math.exp(-4 * math.log(2) * th ** 2 / fwhm ** 2))
+        assert oracle_voltage_grid(G, th, az) == pytest.approx(want, rel=2e-4)
+    # the ENU direction of a source east of the zenith has az = 90 deg: E = sin(th), N = 0
+    s_east = np.array([math.sin(th), 0.0, math.cos(th)])
+    assert math.atan2(s_east[0], s_east[1]) == pytest.approx(math.pi / 2)
+
+
+def test_grid_beam_visibilities_converge_to_the_analytic_beam_at_second_order():
+    prob = W.config_hex127(seed=22, n_chan=2, n_time=1, n_point=400, nside=0, radius=2)
+    prob.beam_param = (math.radians(30.0), 150e6)
+    ref = oracle_vis(OracleProblem.from_workload(prob), "literal")
+    errs = []
+    for nth in (46, 91, 181):
+        p = OracleProblem.from_workload(prob)
+        p.beam = "grid"
+        p.beam_grids = {-1: W.grid_beam(prob.freqs_hz, nth, 4, math.radians(30.0), 150e6)}
+        errs.append(rel_l2(oracle_vis(p, "literal"), ref))
+    assert errs[0] < 1e-2
+    for a, b in zip(errs, errs[1:]):
+        assert 3.0 < a / b < 5.0, errs
+
+
+def test_grid_beam_as_one_of_two_per_antenna_beams():
+    prob = W.config_hex127(seed=23, n_chan=2, n_time=1, n_point=300, nside=0, radius=2)
+    boa = np.arange(len(prob.ant_enu)) % 2
+    analytic = OracleProblem.from_workload(prob)
+    analytic.beams = [("gauss", (math.radians(25.0), 150e6)), ("airy", (6.0,))]
+    analytic.beam_of_ant = boa
+    gridded = OracleProblem.from_workload(prob)
+    gridded.beams = [("grid", ()), ("airy", (6.0,))]
+    gridded.beam_of_ant = boa
+    gridded.beam_grids = {0: W.grid_beam(prob.freqs_hz, 721, 4, math.radians(25.0), 150e6)}
+    assert rel_l2(oracle_vis(gridded, "literal"), oracle_vis(analytic, "literal")) < 2e-5
+    assert rel_l2(oracle_vis(gridded, "factored"), oracle_vis(gridded, "literal")) < 1e-12
