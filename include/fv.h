@@ -60,7 +60,9 @@ typedef enum {
                              FWHM(nu) = beam_param[0] * beam_param[1] / nu
                              (beam_param[0] = FWHM in rad at reference frequency beam_param[1] Hz) */
     FV_BEAM_AIRY = 1,     /* voltage 2 J1(x)/x, x = pi D nu sin(theta)/c, D = beam_param[0] m */
-    FV_BEAM_UNIFORM = 2   /* A = 1 (no beam) */
+    FV_BEAM_UNIFORM = 2,  /* A = 1 (no beam) */
+    FV_BEAM_GRID = 3      /* numerical beam: samples set by fv_set_beam_grid (not accepted by fv_plan
+                             or fv_set_beams, which take analytic beams only) */
 } fv_beam_kind;
 
 /* Plan options.  Analytic beams only (Section 2.4, item i); the Jones matrix of
@@ -195,6 +197,22 @@ fv_status fv_set_array(fv_plan_t p, int n_ant, const double *enu_m, int n_bl, co
  * kind or parameter, index out of range). */
 fv_status fv_set_beams(fv_plan_t p, int n_beams, const int *kinds, const double *params,
                        const int *beam_of_antenna);
+
+/* Gridded (numerical) beam (Section 2.4, the numerically sampled beam models
+ * that are interpolated to the source positions).  Beam `beam` becomes
+ * FV_BEAM_GRID with the voltage samples voltage[f][i][j] (host array
+ * [n_freq][n_theta][n_phi], copied) at channel f, zenith angle
+ * theta_i = i (pi/2) / (n_theta - 1) (zenith to horizon) and azimuth
+ * phi_j = j 2 pi / n_phi (east of north, periodic); a source's voltage is the
+ * bilinear interpolation in (theta, phi) of its channel's samples (the lowest
+ * order Section 2.4 names), in the plan's precision.  The Jones matrix of the
+ * polarised path is A(theta, phi) R(az) as for the analytic beams.  beam = -1
+ * is the plan's beam (all antennas); beam = k >= 0 is per-antenna beam k of
+ * the last fv_set_beams (a later fv_set_beams drops the per-antenna grids).
+ * May be called before or after fv_set_sky; applies to later executions.
+ * Errors: FV_ERR_ARG (beam out of range, n_theta < 2, n_phi < 1,
+ * n_theta * n_phi > 2^22, NULL or non-finite samples), FV_ERR_OOM. */
+fv_status fv_set_beam_grid(fv_plan_t p, int beam, int n_theta, int n_phi, const double *voltage);
 
 /* Set the sky: n_src point sources at (ra_rad, dec_rad), host arrays, copied.
  * flux: [n_stokes][n_src][n_freq] Jy (n_stokes = 1: I; 4: I, Q, U, V), FP64 if

@@ -79,15 +79,15 @@ __global__ void __launch_bounds__(128) k_prep_basis(const double *__restrict__ s
     if (i >= *nv_ptr) return;
     const double s0 = sdir[i], s1 = sdir[n_src + i], s2 = sdir[2 * n_src + i];
     const long n = sidx[i];
-    const G rho = (G)sqrt(s0 * s0 + s1 * s1), up = (G)s2;
+    const G rho = (G)sqrt(s0 * s0 + s1 * s1), up = (G)s2, east = (G)s0, north = (G)s1;
     // beam coefficients b_hat_k = sum_q M_qk B(nu_q)
     G bh[kBasisMax];
 #pragma unroll
     for (int k = 0; k < kBasisMax; ++k) bh[k] = (G)0;
     for (int q = 0; q < n_freq; ++q) {
         const G nu = (G)freq[q];
-        const G A = voltage<G>(g.beam, rho, up, nu);
-        const G B = g.two_beams ? A * voltage<G>(g.beam2, rho, up, nu) : A * A;
+        const G A = beam_voltage<G>(g.beam, east, north, rho, up, nu, q);
+        const G B = g.two_beams ? A * beam_voltage<G>(g.beam2, east, north, rho, up, nu, q) : A * A;
 #pragma unroll
         for (int k = 0; k < kBasisMax; ++k)
             if (k < K) bh[k] += M[q * K + k] * B;

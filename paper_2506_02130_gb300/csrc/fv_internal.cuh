@@ -53,8 +53,12 @@ struct DimGeom {
 };
 
 struct BeamParams {
-    int kind;           // 0 gauss, 1 airy, 2 uniform
+    int kind;           // 0 gauss, 1 airy, 2 uniform, 3 gridded
     double p0, p1, p2;
+    // gridded beams (Section 2.4, numerical beams): voltage samples [n_freq][n_th][n_ph] on the grid
+    // theta_i = i (pi/2) / (n_th - 1) (zenith angle), phi_j = j 2 pi / n_ph (azimuth east of north)
+    const void *grid;   // device samples, FP64 if grid_fp64 else FP32
+    int grid_fp64, n_th, n_ph;
 };
 
 // Per-time binning geometry: bins are tiles of the top (highest-frequency)
@@ -117,7 +121,47 @@ template <> __device__ __forceinline__ float voltage<float>(const BeamParams &b,
     return 1.0f;
 }
 
-// Strengths of one source in one slice (Eq. 1-2 with the analytic beams): the
+// Voltage of a gridded beam at channel q for the direction (s0, s1, s2) = (E, N, U), rho = sqrt(E^2 + N^2):
+// bilinear interpolation in zenith angle and azimuth (east of north, periodic) of the channel's samples.
+template <class G>
+__device__ __forceinline__ G grid_voltage(const BeamParams &b, G s0, G s1, G rho, G s2, int q)
+{
+    const G kHalfPi = (G)1.5707963267948966192, kTwoPi = (G)6.283185307179586477;
+    const G dth = kHalfPi / (G)(b.n_th - 1), dph = kTwoPi / (G)b.n_ph;
+    const G th = atan2(rho, s2);
+    G az = atan2(s0, s1);
+    if (az < (G)0) az += kTwoPi;
+    const G u = th / dth;
+    int i = (int)floor(u);
+    i = i < 0 ? 0 : (i > b.n_th - 2 ? b.n_th - 2 : i);
+    const G a = u - (G)i;
+    const G v = az / dph;
+    const int j = (int)floor(v);
+    const G c = v - (G)j;
+    int j0 = j % b.n_ph;
+    if (j0 < 0) j0 += b.n_ph;
+    const int j1 = j0 + 1 == b.n_ph ? 0 : j0 + 1;
+    const size_t base = ((size_t)q * b.n_th + i) * b.n_ph;
+    G t00, t01, t10, t11;
+    if (b.grid_fp64) {
+        const double *T = (const double *)b.grid + base;
+        t00 = (G)T[j0]; t01 = (G)T[j1]; t10 = (G)T[b.n_ph + j0]; t11 = (G)T[b.n_ph + j1];
+    } else {
+        const float *T = (const float *)b.grid + base;
+        t00 = (G)T[j0]; t01 = (G)T[j1]; t10 = (G)T[b.n_ph + j0]; t11 = (G)T[b.n_ph + j1];
+    }
+    return ((G)1 - a) * (((G)1 - c) * t00 + c * t01) + a * (((G)1 - c) * t10 + c * t11);
+}
+
+// Beam voltage at channel q (frequency nu) for the direction (s0, s1, s2): analytic beams by
+// voltage<G>, gridded beams from their samples.
+template <class G>
+__device__ __forceinline__ G beam_voltage(const BeamParams &b, G s0, G s1, G rho, G s2, G nu, int q)
+{
+    return b.kind == 3 ? grid_voltage<G>(b, s0, s1, rho, s2, q) : voltage<G>(b, rho, s2, nu);
+}
+
+// Strengths of one source in one slice (Eq. 1-2 with the slice's beams): the
 // unpolarised product A_i A_j I, or the four products of J_i C J_j^dagger with
 // J = A R(az) for Stokes IQUV (A_i = A_j = A for one shared beam).  Beam in the
 // grid precision G.  Returns n_pol.
@@ -127,9 +171,9 @@ __device__ __forceinline__ int source_strengths(const SliceGeom &g, double s0, d
                                                 cpx<G> *c)
 {
     const G rho = (G)sqrt(s0 * s0 + s1 * s1);
-    const G A = voltage<G>(g.beam, rho, (G)s2, (G)g.nu);
+    const G A = beam_voltage<G>(g.beam, (G)s0, (G)s1, rho, (G)s2, (G)g.nu, f);
     // A_i A_j: the two antennas' voltages (one shared beam: A^2)
-    const G A2 = g.two_beams ? A * voltage<G>(g.beam2, rho, (G)s2, (G)g.nu) : A * A;
+    const G A2 = g.two_beams ? A * beam_voltage<G>(g.beam2, (G)s0, (G)s1, rho, (G)s2, (G)g.nu, f) : A * A;
     auto ld = [&](int k) -> G {
         size_t idx = ((size_t)k * n_src + n) * n_freq + f;
         return flux_fp64 ? (G)((const double *)flux)[idx] : (G)((const float *)flux)[idx];

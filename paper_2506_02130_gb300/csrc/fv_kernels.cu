@@ -162,21 +162,6 @@ cudaError_t launch_target_deconv(const double *bu, int n_u, int d, const double 
 }
 
 // ------------------------------------------------------------------ weighting
-// Voltage beam A(theta, nu) from the direction (s0, s1, s2), s2 > 0.
-__device__ __forceinline__ double voltage_beam(const BeamParams &b, double rho, double s2, double nu)
-{
-    if (b.kind == 0) {
-        double theta = atan2(rho, s2);
-        double fwhm = b.p0 * b.p1 / nu;
-        return exp(-2.0 * M_LN2 * theta * theta / (fwhm * fwhm));
-    }
-    if (b.kind == 1) {
-        double x = M_PI * b.p0 * nu * rho / FV_C_LIGHT;
-        return x < 1e-8 ? 1.0 - 0.125 * x * x : 2.0 * j1(x) / x;
-    }
-    return 1.0;
-}
-
 __device__ __forceinline__ double load_flux(const void *flux, int fp64, size_t idx)
 {
     return fp64 ? ((const double *)flux)[idx] : (double)((const float *)flux)[idx];
@@ -189,8 +174,8 @@ __device__ __forceinline__ int source_strengths(const SliceGeom &g, const void *
                                                 double s2, cpx<double> *c)
 {
     double rho = sqrt(s0 * s0 + s1 * s1);
-    double A = voltage_beam(g.beam, rho, s2, g.nu);
-    double A2 = g.two_beams ? A * voltage_beam(g.beam2, rho, s2, g.nu) : A * A;
+    double A = beam_voltage<double>(g.beam, s0, s1, rho, s2, g.nu, f);
+    double A2 = g.two_beams ? A * beam_voltage<double>(g.beam2, s0, s1, rho, s2, g.nu, f) : A * A;
     double I = load_flux(flux, flux_fp64, (size_t)n * n_freq + f);
     if (!g.polarized) {
         c[0] = cmk<double>(A2 * I, 0.0);

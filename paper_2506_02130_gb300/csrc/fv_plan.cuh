@@ -38,6 +38,9 @@ struct fv_plan_s {
     // per-antenna beams (Section 2.2.3): empty beams = every antenna has opts.beam
     std::vector<BeamParams> beams;
     std::vector<int> beam_of_ant;
+    // gridded beams (Section 2.4): device samples of the plan's beam and of each per-antenna beam
+    void *d_grid_main = nullptr;
+    std::vector<void *> d_grid_beams;
     // baselines grouped by the unordered pair of their antennas' beams: group g has unique targets
     // [u0, u1) and baselines d_grp_bl[bl0, bl1) (one group covering everything without per-antenna beams)
     struct BeamGroup {

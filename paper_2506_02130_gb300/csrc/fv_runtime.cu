@@ -196,6 +196,13 @@ static void free_workspaces(std::vector<fv_plan_s::Workspace> &ws)
     ws.clear();
 }
 
+// Device samples of the per-antenna gridded beams (dropped with the beams they belong to).
+static void drop_beam_grids(fv_plan_s *p)
+{
+    for (auto &d : p->d_grid_beams) dfree(d);
+    p->d_grid_beams.clear();
+}
+
 static void free_geometry(fv_plan_s *p)
 {
     dfree(p->d_pre);
@@ -1018,6 +1025,7 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
     for (int i = 0; i < o->n_time; ++i)
         if (!std::isfinite(o->lst_rad[i])) return bad("LSTs must be finite");
     if (!(std::fabs(o->latitude_rad) <= M_PI / 2)) return bad("latitude out of range");
+    if (o->beam == FV_BEAM_GRID) return bad("a gridded beam is set by fv_set_beam_grid after fv_plan");
     if (o->beam < FV_BEAM_GAUSS || o->beam > FV_BEAM_UNIFORM) return bad("unknown beam");
     if (o->beam == FV_BEAM_GAUSS && !(o->beam_param[0] > 0 && o->beam_param[1] > 0))
         return bad("Gaussian beam needs FWHM > 0 and reference frequency > 0");
@@ -1324,6 +1332,7 @@ fv_status fv_set_beams(fv_plan_t p, int n_beams, const int *kinds, const double 
     if (cudaSetDevice(p->device) != cudaSuccess) return p->fail(FV_ERR_CUDA, "cudaSetDevice failed");
     if (!p->have_array) return p->fail(FV_ERR_STATE, "fv_set_array must come before fv_set_beams");
     if (n_beams <= 0 || !beam_of_ant) {
+        drop_beam_grids(p);
         p->beams.clear();
         p->beam_of_ant.clear();
         return setup_array(p);
@@ -1345,9 +1354,56 @@ fv_status fv_set_beams(fv_plan_t p, int n_beams, const int *kinds, const double 
     std::vector<int> boa(beam_of_ant, beam_of_ant + p->n_ant);
     for (int v : boa)
         if (v < 0 || v >= n_beams) return p->fail(FV_ERR_ARG, "beam index out of range");
+    drop_beam_grids(p);
     p->beams.swap(beams);
     p->beam_of_ant.swap(boa);
     return setup_array(p);
+}
+
+fv_status fv_set_beam_grid(fv_plan_t p, int beam, int n_theta, int n_phi, const double *voltage)
+{
+    if (!p) return FV_ERR_ARG;
+    if (cudaSetDevice(p->device) != cudaSuccess) return p->fail(FV_ERR_CUDA, "cudaSetDevice failed");
+    if (beam < -1 || beam >= (int)p->beams.size())
+        return p->fail(FV_ERR_ARG, "beam index out of range (per-antenna beams come from fv_set_beams)");
+    if (n_theta < 2 || n_phi < 1 || (long)n_theta * n_phi > (1L << 22))
+        return p->fail(FV_ERR_ARG, "need n_theta >= 2, n_phi >= 1 and n_theta * n_phi <= 2^22");
+    if (!voltage) return p->fail(FV_ERR_ARG, "NULL beam samples");
+    const size_t n = p->freq.size() * (size_t)n_theta * n_phi;
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(voltage[i])) return p->fail(FV_ERR_ARG, "non-finite beam sample");
+    const bool fp64 = p->precision == FV_FP64;
+    void *d = nullptr;
+    CK(cudaMalloc(&d, n * (fp64 ? sizeof(double) : sizeof(float))));
+    cudaError_t e;
+    if (fp64) {
+        e = cudaMemcpy(d, voltage, n * sizeof(double), cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> v32(voltage, voltage + n);
+        e = cudaMemcpy(d, v32.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return p->fail(FV_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (beam < 0) {
+        dfree(p->d_grid_main);
+        p->d_grid_main = d;
+    } else {
+        p->d_grid_beams.resize(p->beams.size(), nullptr);
+        dfree(p->d_grid_beams[beam]);
+        p->d_grid_beams[beam] = d;
+    }
+    BeamParams &b = beam < 0 ? p->beam : p->beams[beam];
+    b.kind = FV_BEAM_GRID;
+    b.grid = d;
+    b.grid_fp64 = fp64 ? 1 : 0;
+    b.n_th = n_theta;
+    b.n_ph = n_phi;
+    // the slices' geometry holds copies of the plan's beam
+    for (auto &g : p->gf) g.beam = p->beam;
+    p->bg.beam = p->beam;
+    return FV_OK;
 }
 
 fv_status fv_set_sky(fv_plan_t p, long n_src, const double *ra_rad, const double *dec_rad, int n_stokes,
@@ -1470,6 +1526,8 @@ fv_status fv_destroy(fv_plan_t p)
     dfree_t(p->d_grp_bl);
     dfree_t(p->d_e);
     dfree(p->d_flux_owned);
+    dfree(p->d_grid_main);
+    drop_beam_grids(p);
     for (cudaEvent_t ev : p->ev_pool) cudaEventDestroy(ev);
     for (size_t s = 1; s < p->sub.size(); ++s) {
         if (p->sub[s]) cudaStreamDestroy(p->sub[s]);

@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_PKG, "libfftvis_gb300.so")
 FV_OK, FV_ERR_ARG, FV_ERR_OOM, FV_ERR_CUDA, FV_ERR_STATE, FV_ERR_TIMEOUT, FV_ERR_UNSUPPORTED = range(7)
 FV_FP64, FV_MIXED = 0, 1
 SPREAD = {"auto": 0, "gather": 1, "scatter": 2, "atomic": 3}
-BEAMS = {"gauss": 0, "airy": 1, "uniform": 2}
+BEAMS = {"gauss": 0, "airy": 1, "uniform": 2, "grid": 3}
 TRANSFORMS = {"auto": 0, "type3": 1, "lattice": 2, "basis": 3}
 TRANSFORM_NAMES = {0: "auto", 1: "type3", 2: "lattice", 3: "basis"}
 STATUS_NAMES = {0: "FV_OK", 1: "FV_ERR_ARG", 2: "FV_ERR_OOM", 3: "FV_ERR_CUDA", 4: "FV_ERR_STATE",
@@ -73,6 +73,7 @@ SIGNATURES = {
     "fv_plan": (C.c_int, [C.POINTER(fv_opts), C.POINTER(C.c_void_p)]),
     "fv_set_array": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
     "fv_set_beams": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fv_set_beam_grid": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "fv_set_sky": (C.c_int, [C.c_void_p, C.c_long, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int]),
     "fv_execute": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "fv_destroy": (C.c_int, [C.c_void_p]),
@@ -330,25 +331,42 @@ class Plan:
 
     @classmethod
     def from_problem(cls, prob, precision=FV_FP64, eps=None, **kw):
-        p = cls.create(prob.freqs_hz, prob.lsts_rad, prob.latitude_rad, prob.beam, prob.beam_param, precision,
-                       prob.eps if eps is None else eps, prob.polarized, **kw)
+        grid = prob.beam == "grid"
+        p = cls.create(prob.freqs_hz, prob.lsts_rad, prob.latitude_rad, "uniform" if grid else prob.beam,
+                       () if grid else prob.beam_param, precision, prob.eps if eps is None else eps,
+                       prob.polarized, **kw)
         p.set_array(prob.ant_enu, prob.pairs)
+        if grid:
+            p.set_beam_grid(-1, prob.beam_grids[-1])
         return p
 
     def set_array(self, enu_m, pairs=None):
         fv_set_array(self.handle, enu_m, pairs)
         self.n_bl = fv_get_info(self.handle)["n_bl"]
 
-    def set_beams(self, beams, beam_of_ant):
+    def set_beams(self, beams, beam_of_ant, grids=None):
         """Per-antenna beams: beams = [(kind, params), ...], beam_of_ant = beam index per antenna
-        (None or an empty list: the plan's single beam)."""
+        (None or an empty list: the plan's single beam).  A beam of kind "grid" takes its samples
+        [n_freq][n_theta][n_phi] from grids[k] (fv_set_beam_grid)."""
         if not beams or beam_of_ant is None:
             _check(load_library().fv_set_beams(self.handle, 0, None, None, None), self.handle)
             return
-        kinds = np.ascontiguousarray([BEAMS[k] for k, _ in beams], dtype=np.int32)
+        kinds = np.ascontiguousarray([BEAMS["uniform" if k == "grid" else k] for k, _ in beams], dtype=np.int32)
         params = np.ascontiguousarray([list(v) + [0.0] * (3 - len(v)) for _, v in beams], dtype=np.float64)
         boa = np.ascontiguousarray(beam_of_ant, dtype=np.int32)
         _check(load_library().fv_set_beams(self.handle, len(kinds), _ptr(kinds), _ptr(params), _ptr(boa)),
+               self.handle)
+        for k, (kind, _) in enumerate(beams):
+            if kind == "grid":
+                self.set_beam_grid(k, grids[k])
+
+    def set_beam_grid(self, beam, samples):
+        """Gridded beam (fv_set_beam_grid): voltage samples [n_freq][n_theta][n_phi] for beam index
+        `beam` (-1: the plan's beam)."""
+        a = np.ascontiguousarray(samples, dtype=np.float64)
+        if a.ndim != 3 or a.shape[0] != self.n_freq:
+            raise ValueError("beam samples must be [n_freq][n_theta][n_phi]")
+        _check(load_library().fv_set_beam_grid(self.handle, int(beam), a.shape[1], a.shape[2], _ptr(a)),
                self.handle)
 
     def set_sky(self, ra, dec, flux):
