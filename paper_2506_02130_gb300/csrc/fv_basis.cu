@@ -209,7 +209,7 @@ cudaError_t launch_basis_targets(const double *bu, int n_u, const double *kappa,
 // direct z sum of the short z axis; each footprint tap is then R coalesced loads per warp, scaled by
 // the tap's x and y kernel values, and the warp reduces at the end.  The target's constants come from
 // the per-target table, so the kernel does no FP64 arithmetic.
-template <class G, bool HASZ>
+template <class G, bool HASZ, int R>
 __global__ void __launch_bounds__(256) k_interp_basis(const cpx<G> *__restrict__ band, int u0, int n_ug, int n_u,
                                                       int n_freq, const G *__restrict__ M, int K,
                                                       const int4 *__restrict__ tm, const G *__restrict__ tf,
@@ -247,13 +247,12 @@ __global__ void __launch_bounds__(256) k_interp_basis(const cpx<G> *__restrict__
         Kmine = cscale(acc, prez[lane]);
     }
     // this lane's weights c_r = M_qk K(l_z) for j = lane + 32 r (shuffles taken by every lane)
-    const int KN = K * Nz;
-    const int R = (KN + 31) >> 5;
-    cpx<G> cf[8];
+    const int KN = K * Nz;                      // R = ceil(KN / 32), a template parameter
+    cpx<G> cf[R];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
+    for (int r = 0; r < R; ++r) {
         cf[r] = cmk<G>((G)0, (G)0);
-        if (r < R) {                            // R is uniform across the warp
+        {
             const int j = lane + 32 * r;
             const bool valid = j < KN;
             const int k = valid ? j / Nz : 0;
@@ -280,9 +279,9 @@ __global__ void __launch_bounds__(256) k_interp_basis(const cpx<G> *__restrict__
             const cpx<G> *c = row + (size_t)jx * KN;
             G sx = (G)0, sy = (G)0;
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
+            for (int r = 0; r < R; ++r) {
                 const int j = lane + 32 * r;
-                if (r < R && j < KN) {
+                if (r < R - 1 || j < KN) {
                     const cpx<G> v = c[j];
                     sx += v.x * cf[r].x - v.y * cf[r].y;
                     sy += v.x * cf[r].y + v.y * cf[r].x;
@@ -302,6 +301,14 @@ __global__ void __launch_bounds__(256) k_interp_basis(const cpx<G> *__restrict__
     }
 }
 
+template <class G, bool HASZ, int R>
+static void interp_basis_launch(unsigned blocks, const cpx<G> *band, int u0, int n_ug, int n_u, int n_freq,
+                                const G *M, int K, const int4 *tm, const G *tf, const cpx<G> *ts, const SliceGeom &g,
+                                const G *prez, const cpx<G> *twz, cpx<double> *Vq, cudaStream_t st)
+{
+    k_interp_basis<G, HASZ, R><<<blocks, 256, 0, st>>>(band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq);
+}
+
 template <class G>
 cudaError_t launch_interp_basis(const cpx<G> *band, int u0, int n_ug, int n_u, int n_freq, const G *M, int K,
                                 const int4 *tm, const G *tf, const cpx<G> *ts, const SliceGeom &g, const G *prez,
@@ -312,12 +319,22 @@ cudaError_t launch_interp_basis(const cpx<G> *band, int u0, int n_ug, int n_u, i
     if (K < 1 || K > kBasisMax || Nz > FV_ZDIRECT_MAX || K * Nz > 256 || g.w > 32) return cudaErrorInvalidValue;
     const long threads = (long)n_ug * n_freq * 32;
     const unsigned blocks = (unsigned)((threads + 255) / 256);
-    if (g.d == 3)
-        k_interp_basis<G, true><<<blocks, 256, 0, st>>>(band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz,
-                                                        Vq);
-    else
-        k_interp_basis<G, false><<<blocks, 256, 0, st>>>(band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz,
-                                                         Vq);
+    const int R = (K * Nz + 31) / 32;
+    if (g.d == 3) {
+        switch (R) {
+        case 1: interp_basis_launch<G, true, 1>(blocks, band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq, st); break;
+        case 2: interp_basis_launch<G, true, 2>(blocks, band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq, st); break;
+        case 3: interp_basis_launch<G, true, 3>(blocks, band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq, st); break;
+        case 4: interp_basis_launch<G, true, 4>(blocks, band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq, st); break;
+        case 5: interp_basis_launch<G, true, 5>(blocks, band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq, st); break;
+        case 6: interp_basis_launch<G, true, 6>(blocks, band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq, st); break;
+        case 7: interp_basis_launch<G, true, 7>(blocks, band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq, st); break;
+        default: interp_basis_launch<G, true, 8>(blocks, band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq, st); break;
+        }
+    } else {
+        // a flat grid: Nz = 1, K <= 16 values per cell
+        interp_basis_launch<G, false, 1>(blocks, band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq, st);
+    }
     return cudaGetLastError();
 }
 
