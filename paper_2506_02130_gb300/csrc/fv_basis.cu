@@ -212,19 +212,21 @@ cudaError_t launch_basis_targets(const double *bu, int n_u, const double *kappa,
 template <class G, bool HASZ, int R>
 __global__ void __launch_bounds__(256) k_interp_basis(const cpx<G> *__restrict__ band, int u0, int n_ug, int n_u,
                                                       int n_freq, const G *__restrict__ M, int K,
-                                                      const int4 *__restrict__ tm, const G *__restrict__ tf,
-                                                      const cpx<G> *__restrict__ ts, SliceGeom g,
+                                                      const int *__restrict__ perm, const int4 *__restrict__ tm,
+                                                      const G *__restrict__ tf, const cpx<G> *__restrict__ ts,
+                                                      G beta, SliceGeom g,
                                                       const G *__restrict__ prez, const cpx<G> *__restrict__ twz,
                                                       cpx<double> *__restrict__ Vq)
 {
     const int lane = threadIdx.x & 31;
     const long tg = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
     if (tg >= (long)n_ug * n_freq) return;     // whole warps
-    const int u = u0 + (int)(tg / n_freq), q = (int)(tg % n_freq);
-    const size_t tix = (size_t)u * n_freq + q;
+    // targets in the plan's grid order (perm), so that neighbouring warps read neighbouring footprints
+    const int tix_i = perm[(long)u0 * n_freq + tg];
+    const size_t tix = (size_t)tix_i;
+    const int u = tix_i / n_freq, q = tix_i - u * n_freq;
     const int w = g.w;
-    const G two_over_w = (G)(2.0 / w);
-    const G beta = (G)g.beta;
+    const G two_over_w = (G)2 / (G)w;
     const int4 mm = tm[tix];
     const G frx = tf[4 * tix], fry = tf[4 * tix + 1], frz = tf[4 * tix + 2];
     const int Nz = HASZ ? g.dim[2].nf1 : 1;
@@ -303,16 +305,18 @@ __global__ void __launch_bounds__(256) k_interp_basis(const cpx<G> *__restrict__
 
 template <class G, bool HASZ, int R>
 static void interp_basis_launch(unsigned blocks, const cpx<G> *band, int u0, int n_ug, int n_u, int n_freq,
-                                const G *M, int K, const int4 *tm, const G *tf, const cpx<G> *ts, const SliceGeom &g,
-                                const G *prez, const cpx<G> *twz, cpx<double> *Vq, cudaStream_t st)
+                                const G *M, int K, const int *perm, const int4 *tm, const G *tf, const cpx<G> *ts,
+                                const SliceGeom &g, const G *prez, const cpx<G> *twz, cpx<double> *Vq,
+                                cudaStream_t st)
 {
-    k_interp_basis<G, HASZ, R><<<blocks, 256, 0, st>>>(band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq);
+    k_interp_basis<G, HASZ, R><<<blocks, 256, 0, st>>>(band, u0, n_ug, n_u, n_freq, M, K, perm, tm, tf, ts,
+                                                       (G)g.beta, g, prez, twz, Vq);
 }
 
 template <class G>
 cudaError_t launch_interp_basis(const cpx<G> *band, int u0, int n_ug, int n_u, int n_freq, const G *M, int K,
-                                const int4 *tm, const G *tf, const cpx<G> *ts, const SliceGeom &g, const G *prez,
-                                const cpx<G> *twz, cpx<double> *Vq, cudaStream_t st)
+                                const int *perm, const int4 *tm, const G *tf, const cpx<G> *ts, const SliceGeom &g,
+                                const G *prez, const cpx<G> *twz, cpx<double> *Vq, cudaStream_t st)
 {
     if (n_ug <= 0) return cudaSuccess;
     const int Nz = g.d == 3 ? g.dim[2].nf1 : 1;
@@ -322,18 +326,18 @@ cudaError_t launch_interp_basis(const cpx<G> *band, int u0, int n_ug, int n_u, i
     const int R = (K * Nz + 31) / 32;
     if (g.d == 3) {
         switch (R) {
-        case 1: interp_basis_launch<G, true, 1>(blocks, band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq, st); break;
-        case 2: interp_basis_launch<G, true, 2>(blocks, band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq, st); break;
-        case 3: interp_basis_launch<G, true, 3>(blocks, band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq, st); break;
-        case 4: interp_basis_launch<G, true, 4>(blocks, band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq, st); break;
-        case 5: interp_basis_launch<G, true, 5>(blocks, band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq, st); break;
-        case 6: interp_basis_launch<G, true, 6>(blocks, band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq, st); break;
-        case 7: interp_basis_launch<G, true, 7>(blocks, band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq, st); break;
-        default: interp_basis_launch<G, true, 8>(blocks, band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq, st); break;
+        case 1: interp_basis_launch<G, true, 1>(blocks, band, u0, n_ug, n_u, n_freq, M, K, perm, tm, tf, ts, g, prez, twz, Vq, st); break;
+        case 2: interp_basis_launch<G, true, 2>(blocks, band, u0, n_ug, n_u, n_freq, M, K, perm, tm, tf, ts, g, prez, twz, Vq, st); break;
+        case 3: interp_basis_launch<G, true, 3>(blocks, band, u0, n_ug, n_u, n_freq, M, K, perm, tm, tf, ts, g, prez, twz, Vq, st); break;
+        case 4: interp_basis_launch<G, true, 4>(blocks, band, u0, n_ug, n_u, n_freq, M, K, perm, tm, tf, ts, g, prez, twz, Vq, st); break;
+        case 5: interp_basis_launch<G, true, 5>(blocks, band, u0, n_ug, n_u, n_freq, M, K, perm, tm, tf, ts, g, prez, twz, Vq, st); break;
+        case 6: interp_basis_launch<G, true, 6>(blocks, band, u0, n_ug, n_u, n_freq, M, K, perm, tm, tf, ts, g, prez, twz, Vq, st); break;
+        case 7: interp_basis_launch<G, true, 7>(blocks, band, u0, n_ug, n_u, n_freq, M, K, perm, tm, tf, ts, g, prez, twz, Vq, st); break;
+        default: interp_basis_launch<G, true, 8>(blocks, band, u0, n_ug, n_u, n_freq, M, K, perm, tm, tf, ts, g, prez, twz, Vq, st); break;
         }
     } else {
         // a flat grid: Nz = 1, K <= 16 values per cell
-        interp_basis_launch<G, false, 1>(blocks, band, u0, n_ug, n_u, n_freq, M, K, tm, tf, ts, g, prez, twz, Vq, st);
+        interp_basis_launch<G, false, 1>(blocks, band, u0, n_ug, n_u, n_freq, M, K, perm, tm, tf, ts, g, prez, twz, Vq, st);
     }
     return cudaGetLastError();
 }
@@ -371,10 +375,11 @@ template cudaError_t launch_prep_basis<double>(const double *, const int *, cons
                                                const double *, const double *, const double *, int, int, int,
                                                const SliceGeom &, int *, double *, cpx<double> *, cudaStream_t);
 template cudaError_t launch_interp_basis<float>(const cpx<float> *, int, int, int, int, const float *, int,
-                                                const int4 *, const float *, const cpx<float> *, const SliceGeom &,
-                                                const float *, const cpx<float> *, cpx<double> *, cudaStream_t);
+                                                const int *, const int4 *, const float *, const cpx<float> *,
+                                                const SliceGeom &, const float *, const cpx<float> *, cpx<double> *,
+                                                cudaStream_t);
 template cudaError_t launch_interp_basis<double>(const cpx<double> *, int, int, int, int, const double *, int,
-                                                 const int4 *, const double *, const cpx<double> *,
+                                                 const int *, const int4 *, const double *, const cpx<double> *,
                                                  const SliceGeom &, const double *, const cpx<double> *,
                                                  cpx<double> *, cudaStream_t);
 template cudaError_t launch_basis_targets<float>(const double *, int, const double *, int, const SliceGeom &,

@@ -39,13 +39,14 @@ cudaError_t launch_basis_targets(const double *bu, int n_u, const double *kappa,
                                  const double *X, double sigma, const double *gl_x, const double *gl_w, int nq,
                                  int4 *tm, G *tf, cpx<G> *ts, cudaStream_t st);
 
-// Targets (u, q) for u in [u0, u0 + n_ug) and every channel q: interpolation of the K planes of the
-// band ([b_y][b_x][k][l_z] after the x and y passes) with the z sum done directly (short z), combined
-// with weights M_qk, times the target's constant ts.  Vq[q * n_u + u] receives the result.
+// Targets (u, q) for u in [u0, u0 + n_ug) and every channel q, taken in the order
+// perm[u0 * n_freq .. (u0 + n_ug) * n_freq) (a permutation of that range): interpolation of the K planes
+// of the band ([b_y][b_x][k][l_z] after the x and y passes) with the z sum done directly (short z),
+// combined with weights M_qk, times the target's constant ts.  Vq[q * n_u + u] receives the result.
 template <class G>
 cudaError_t launch_interp_basis(const cpx<G> *band, int u0, int n_ug, int n_u, int n_freq, const G *M, int K,
-                                const int4 *tm, const G *tf, const cpx<G> *ts, const SliceGeom &g, const G *prez,
-                                const cpx<G> *twz, cpx<double> *Vq, cudaStream_t st);
+                                const int *perm, const int4 *tm, const G *tf, const cpx<G> *ts, const SliceGeom &g,
+                                const G *prez, const cpx<G> *twz, cpx<double> *Vq, cudaStream_t st);
 
 // Output slices (q, t) of every channel: vis + (q * n_time + t) * slice_bytes holds, for baseline bl,
 // Vq[q * n_u + bl2u[bl]] (complex64 or complex128).

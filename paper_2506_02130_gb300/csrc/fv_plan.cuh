@@ -136,6 +136,7 @@ struct fv_plan_s {
     void *d_bas_Mg = nullptr;         // the basis and the structure constants in the grid precision
     void *d_bas_dg = nullptr;
     int4 *d_bas_tm = nullptr;         // per target (u, q): footprint origin on the FFT grid
+    int *d_bas_perm = nullptr;        //   the targets of each beam group in grid order (interpolation order)
     void *d_bas_tf = nullptr;         //   offsets [4] in the grid precision
     void *d_bas_ts = nullptr;         //   deconvolution x postphase (complex, grid precision)
     double *d_bas_shat = nullptr;     // [n_src][K] flux coefficients (recomputed by every execution)

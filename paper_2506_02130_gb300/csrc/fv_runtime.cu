@@ -219,6 +219,7 @@ static void free_geometry(fv_plan_s *p)
     dfree(p->d_bas_Mg);
     dfree(p->d_bas_dg);
     dfree_t(p->d_bas_tm);
+    dfree_t(p->d_bas_perm);
     dfree(p->d_bas_tf);
     dfree(p->d_bas_ts);
     dfree_t(p->d_bas_shat);
@@ -845,6 +846,22 @@ static fv_status prepare_basis(fv_plan_s *p)
                                        p->nq, p->d_bas_tm, (float *)p->d_bas_tf, (cpx<float> *)p->d_bas_ts,
                                        p->stream));
     }
+    // the interpolation takes each beam group's targets sorted by footprint row, then column, so that the
+    // warps of a CTA, and consecutive CTAs, read overlapping parts of the band
+    std::vector<int4> tmh(std::max<size_t>(nt_all, 1));
+    CK(cudaMemcpyAsync(tmh.data(), p->d_bas_tm, nt_all * sizeof(int4), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    std::vector<int> perm(std::max<size_t>(nt_all, 1));
+    for (size_t t = 0; t < nt_all; ++t) perm[t] = (int)t;
+    for (const auto &gr : p->groups) {
+        auto lo = perm.begin() + (size_t)gr.u0 * nf, hi = perm.begin() + (size_t)gr.u1 * nf;
+        std::sort(lo, hi, [&](int a, int b) {
+            const int4 &A = tmh[a], &B = tmh[b];
+            return A.y != B.y ? A.y < B.y : (A.x != B.x ? A.x < B.x : a < b);
+        });
+    }
+    CK(cudaMalloc(&p->d_bas_perm, perm.size() * sizeof(int)));
+    CK(cudaMemcpyAsync(p->d_bas_perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice, p->stream));
     CK(cudaStreamSynchronize(p->stream));
     // workspace of one execution stream
     const DimGeom *D = g.dim;
@@ -859,7 +876,7 @@ static fv_status prepare_basis(fv_plan_s *p)
     p->need.frac_per_src = 3 * gs;
     p->need.cs_per_src = (size_t)p->basis_Kp * es;
     p->ws_bytes = (long long)(pre_total * gs + tw_total * es + (M.size() + dK.size() + 2 * nf) * (8 + gs) +
-                              nt_all * (sizeof(int4) + 4 * gs + es) +
+                              nt_all * (sizeof(int4) + sizeof(int) + 4 * gs + es) +
                               (size_t)p->need.n_src * K * 8 +
                               p->n_streams * workspace_layout(p->need, nullptr, nullptr));
     return FV_OK;
@@ -929,7 +946,7 @@ fv_status run_basis(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, cha
             CK(prof_end(p, (double)r2 * (D[1].nf1 + D[1].B) * es));
             const int nug = gr.u1 - gr.u0;
             CK(prof_begin(p, PC_INTERP, st));
-            CK(launch_interp_basis<G>(Bb, gr.u0, nug, p->n_u, nf, (const G *)p->d_bas_Mg, K, p->d_bas_tm,
+            CK(launch_interp_basis<G>(Bb, gr.u0, nug, p->n_u, nf, (const G *)p->d_bas_Mg, K, p->d_bas_perm, p->d_bas_tm,
                                       (const G *)p->d_bas_tf, (const cpx<G> *)p->d_bas_ts, g, pre + p->pre_off[2],
                                       tw + p->tw_off[2], wk.Vu, st));
             CK(prof_end(p, (double)nug * nf * ((double)p->w * p->w * K * D[2].nf1 * es + 16.0 + 4.0 * sizeof(G) + es + 16.0)));
