@@ -71,6 +71,29 @@ def parse():
     return ap.parse_args()
 
 
+def kernel_profile(fv, prob, precision, eps, stream, device, flux_dev, args, **plan_kw):
+    """Per kernel class {ms, launches, bytes} of one step of a one-stream plan (fv_profile_enable): with
+    one stream no two kernels overlap, so every CUDA-event pair times one kernel alone."""
+    import torch
+    p = fv.Plan.from_problem(prob, precision=precision, eps=eps, stream=stream.cuda_stream, device=device,
+                             n_streams=1, spread=args.spread, fft_max_radix=args.fft_radix, **plan_kw)
+    try:
+        p.set_sky(prob.sky.ra, prob.sky.dec, flux_dev)
+        o = torch.empty(p.out_shape, dtype=torch.complex64 if precision == fv.FV_MIXED else torch.complex128,
+                        device=torch.device("cuda", device))
+        p.run(o)                                          # warm-up (lazy workspaces, caches)
+        torch.cuda.synchronize(device)
+        fv.fv_profile_read(p.handle)                      # reset counters
+        fv.fv_profile_enable(p.handle, True)
+        p.run(o)
+        torch.cuda.synchronize(device)
+        prof = fv.fv_profile_read(p.handle)
+        fv.fv_profile_enable(p.handle, False)
+        return prof
+    finally:
+        p.close()
+
+
 def workload(seed):
     from paper_2506_02130_gb300 import workloads as W
     return W.config_hex127(seed=seed)
@@ -656,14 +679,11 @@ def main():
         ms = float(t.item())
     value = world * n_vis * args.steps / (ms / 1e3)
 
-    # ---- per-kernel times: one more step with CUDA events around every launch, each on the
-    # stream it runs on (event records between launches would perturb the timed region above)
-    fv.fv_profile_read(plan.handle)                       # reset counters
-    fv.fv_profile_enable(plan.handle, True)
-    plan.run(out)
-    torch.cuda.synchronize(dev)
-    prof = fv.fv_profile_read(plan.handle)
-    fv.fv_profile_enable(plan.handle, False)
+    # ---- per-kernel times: one more step with CUDA events around every launch (event records between
+    # launches would perturb the timed region above), on a one-stream copy of the plan so that no two
+    # kernels overlap and each event pair brackets one kernel alone
+    prof = kernel_profile(fv, prob, precision, eps, stream, local, flux_dev, args,
+                          transform=args.transform, n_basis=args.basis_terms if args.transform == "basis" else 0)
     prof_steps = 1
 
     # ---- roofline of the dominant kernel class
@@ -680,7 +700,8 @@ def main():
                 "traffic": tr, "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
                 "avg_launch_ms": d["ms"] / d["launches"],
                 "share_of_kernel_time": d["ms"] / sum(v["ms"] for v in prof.values()),
-                "timing": "CUDA events around each launch on its own stream, one profiled step after the timed region"}
+                "timing": "CUDA events around each launch, one step of a one-stream copy of the plan after the "
+                          "timed region (kernels do not overlap, so each event pair times one kernel alone)"}
     gpu_launches = int(sum(v["launches"] for k, v in prof.items() if k != "memset")) * args.steps // prof_steps
 
     # ---- end to end through the C ABI with host buffers (pinned)
@@ -757,12 +778,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize(dev)
         msb = e0.elapsed_time(e1)
-        fv.fv_profile_read(pb.handle)
-        fv.fv_profile_enable(pb.handle, True)
-        pb.run(ob)
-        torch.cuda.synchronize(dev)
-        bprof = fv.fv_profile_read(pb.handle)
-        fv.fv_profile_enable(pb.handle, False)
+        bprof = kernel_profile(fv, prob, precision, eps, stream, local, flux_dev, args, transform="basis",
+                               n_basis=args.basis_terms)
         bi = pb.info()
         bas_route = {"value": world * n_vis * args.steps / (msb / 1e3), "unit": "visibilities/s",
                      "ms_per_step": msb / args.steps, "basis_terms": bi["basis_terms"], "grid": bi["basis_grid"],

@@ -242,7 +242,11 @@ static void resolve_spread(fv_plan_s *p, int gs, int w)
     const bool gather_ok = spread_gather_config(gs, p->n_pol, nzm, w, &nz_t, &bx, &by) != 0;
     const bool scatter_ok = spread_scatter_smem(gs, p->n_pol, nzm) <= FV_SPREAD_SMEM_MAX && w <= 32;
     int m = p->spread_req;
-    if (m == FV_SPREAD_AUTO) m = gather_ok ? FV_SPREAD_GATHER : (scatter_ok ? FV_SPREAD_SCATTER : FV_SPREAD_ATOMIC);
+    // FP64 tiles of 16 height planes hold 16 double-complex accumulators per lane: measured slower than
+    // the other methods for the per-channel slices, so auto takes them only where nothing else exists
+    const bool gather_auto = gather_ok && !(gs == 8 && nz_t == 16);
+    if (m == FV_SPREAD_AUTO)
+        m = gather_auto ? FV_SPREAD_GATHER : (scatter_ok ? FV_SPREAD_SCATTER : FV_SPREAD_ATOMIC);
     if (m == FV_SPREAD_GATHER && !gather_ok) m = FV_SPREAD_ATOMIC;
     if (m == FV_SPREAD_SCATTER && !scatter_ok) m = FV_SPREAD_ATOMIC;
     p->spread_method = m;
