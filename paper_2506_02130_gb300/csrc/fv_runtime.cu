@@ -953,7 +953,9 @@ fv_status run_basis(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, cha
             CK(launch_interp_basis<G>(Bb, gr.u0, nug, p->n_u, nf, (const G *)p->d_bas_Mg, K, p->d_bas_perm, p->d_bas_tm,
                                       (const G *)p->d_bas_tf, (const cpx<G> *)p->d_bas_ts, g, pre + p->pre_off[2],
                                       tw + p->tw_off[2], wk.Vu, st));
-            CK(prof_end(p, (double)nug * nf * ((double)p->w * p->w * K * D[2].nf1 * es + 16.0 + 4.0 * sizeof(G) + es + 16.0)));
+            // the K-plane band read once, each target's constants and perm entry, one FP64 complex out
+            CK(prof_end(p, (double)D[1].B * D[0].B * K * D[2].nf1 * es +
+                               (double)nug * nf * (16.0 + 4.0 + 4.0 * sizeof(G) + es + 16.0)));
         }
         CK(prof_begin(p, PC_SCATTER, st));
         CK(launch_scatter_basis(wk.Vu, p->d_bl2u, p->n_bl, p->n_u, nf, nt, t, vis, slice_bytes,
