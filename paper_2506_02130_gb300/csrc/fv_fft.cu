@@ -380,6 +380,15 @@ __global__ void __launch_bounds__(kThreads, (FftMinBlocks<G, MAXRD>::value)) k_f
                 buf0[pad(r * M + m)] = cscale(pf.v[k], pre[l]);
             }
         }
+        // a row longer than the prefetch holds (then R = 1): the rest of it straight from memory
+        for (int idx = Prefetch<G>::kMax * kThreads + threadIdx.x; idx < R * N; idx += kThreads) {
+            const int r = idx / N;
+            const int l = idx - r * N;
+            int m = l - half;
+            if (m < 0) m += M;
+            const cpx<G> v = row0 + r < rows ? in[row0 * N + idx] : cmk<G>((G)0, (G)0);
+            buf0[pad(r * M + m)] = cscale(v, pre[l]);
+        }
         __syncthreads();
         // issue the next block's loads before the stages
         if (row0 + stride < rows) prefetch_rows(pf, in, rows, row0 + stride, R, N);

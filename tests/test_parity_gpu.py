@@ -218,3 +218,21 @@ def test_lattice_sky_equals_numpy_fft2(precision):
     out = p.run()[0, 0, :, 0]
     p.close()
     assert rel_l2(out, L["expected"]) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision,span_m", [(fv.FV_FP64, 700.0), (fv.FV_MIXED, 1300.0)])
+def test_long_fft_rows_beyond_one_cta_block(precision, span_m):
+    # km-scale east-west baselines: the x axis of the grid is longer than the row block one FFT CTA
+    # prefetches (2,048 FP64 / 4,096 FP32 values), so part of each row is read straight from memory
+    rng = np.random.default_rng(12)
+    east = np.array([-span_m, -0.45 * span_m, 0.0, 0.3 * span_m, span_m])
+    ant = np.stack([east, rng.uniform(-20, 20, 5), np.zeros(5)], axis=1)
+    lst = 1.3
+    freqs = np.array([150e6])
+    sky = W.point_sky(300, freqs, rng, hemisphere=(lst, W.HERA_LATITUDE_RAD))
+    prob = W.Problem("long_rows", ant, W.cross_pairs(5), sky, freqs, np.array([lst]), W.HERA_LATITUDE_RAD,
+                     "gauss", (math.radians(30.0), 150e6), False, EPS[precision])
+    out, info = run_gpu(prob, precision, transform="type3")
+    limit = 2048 if precision == fv.FV_FP64 else 4096
+    assert info["nf1_max"][0] > limit
+    assert rel_l2(out, oracle(prob, mode="literal")) <= TOL[precision]
