@@ -825,7 +825,7 @@ def main():
                        "n_unique_targets": info["n_unique"], "n_freq": 64, "n_time": 10,
                        "n_src": int(prob.sky.n_src), "dims": info["dims"], "precision": args.precision,
                        "eps": eps, "kernel_width": info["kernel_width"], "upsampfac": info["upsampfac"],
-                       "nf1_max": info["nf1_max"], "nf2_max": info["nf2_max"], "streams": args.streams or 4,
+                       "nf1_max": info["nf1_max"], "nf2_max": info["nf2_max"], "streams": args.streams or (4 if args.transform == "basis" else 8),
                        "spread": args.spread, "transform": args.transform,
                        "vis_per_step": n_vis,
                        "l2": "inputs larger than L2: a step streams the 640 slices' grids "

@@ -91,7 +91,8 @@ typedef struct {
                                  legacy default stream is named by cudaStreamLegacy, not 0) */
     int device;               /* CUDA device ordinal; -1 = the current device */
     int n_streams;            /* slices run concurrently on this many streams, each with its own
-                                 workspace (forked from and joined back to cuda_stream); 0 = 4 */
+                                 workspace (forked from and joined back to cuda_stream); 0 = 8
+                                 (4 for FV_TRANSFORM_BASIS, whose times each fill the GPU) */
     int spread_method;        /* fv_spread_method; FV_SPREAD_AUTO picks the fastest that fits */
     int fft_max_radix;        /* largest FFT stage radix: 8 (fewer registers, more stages) or 16;
                                  0 = 8 for FV_MIXED, 16 for FV_FP64 */
