@@ -701,7 +701,10 @@ def main():
                 "avg_launch_ms": d["ms"] / d["launches"],
                 "share_of_kernel_time": d["ms"] / sum(v["ms"] for v in prof.values()),
                 "timing": "CUDA events around each launch, one step of a one-stream copy of the plan after the "
-                          "timed region (kernels do not overlap, so each event pair times one kernel alone)"}
+                          "timed region (kernels do not overlap, so each event pair times one kernel alone)",
+                "reading": "a slice's grid and band stay in the 129 MB L2 between its kernels, so DRAM sees far "
+                           "less than the algorithmic bytes (traffic); the per-slice kernels are bound by "
+                           "instruction issue and latency, not HBM (ncu summaries under profiles/)"}
     gpu_launches = int(sum(v["launches"] for k, v in prof.items() if k != "memset")) * args.steps // prof_steps
 
     # ---- end to end through the C ABI with host buffers (pinned)
