@@ -66,7 +66,7 @@ def parse():
                     help="serve: mean arrival rate (1/s); 0 = 70%% of the measured capacity for the request mix")
     ap.add_argument("--serve-scale", type=float, default=1.0, help="serve: sky size scale (1 = full skies)")
     ap.add_argument("--batch-slices", type=int, default=2048)
-    ap.add_argument("--lanes", type=int, default=4, help="batch execution lanes")
+    ap.add_argument("--lanes", type=int, default=8, help="batch and serving execution lanes")
     ap.add_argument("--no-tune", action="store_true", help="batch: default choices instead of the autotuner")
     return ap.parse_args()
 

@@ -323,6 +323,7 @@ fv_status fv_profile_read(fv_plan_t p, fv_profile_data *out);
  * Errors: FV_ERR_ARG (bad range, host output, device mismatch), FV_ERR_STATE,
  * FV_ERR_OOM, FV_ERR_CUDA; fv_batch_last_error gives the message. */
 typedef struct fv_batch_s *fv_batch_t;
+/* n_lanes: 1..32, 0 = 8.  device: -1 = the current device. */
 fv_status fv_batch_create(int device, void *cuda_stream, int n_lanes, fv_batch_t *out);
 fv_status fv_batch_add(fv_batch_t b, fv_plan_t p, void *vis, int t_lo, int t_hi, int f_lo, int f_hi);
 fv_status fv_batch_add_range(fv_batch_t b, fv_plan_t p, void *vis, int t_lo, int t_hi, int f_lo, int f_hi,

@@ -226,7 +226,7 @@ def summary(results, stats: Stats | None = None) -> dict:
 class GpuExecutor:
     """Runs ticks as fv batches on one stream (torch for buffers and events)."""
 
-    def __init__(self, device: int = 0, n_lanes: int = 4, stream=None):
+    def __init__(self, device: int = 0, n_lanes: int = 8, stream=None):
         import torch
         from . import fv
         self.torch, self.fv = torch, fv
