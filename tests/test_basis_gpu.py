@@ -126,3 +126,22 @@ def test_errors():
         fv.fv_execute_static(p.handle, out)
     assert e.value.status == fv.FV_ERR_UNSUPPORTED
     p.close()
+
+
+def test_empty_and_invisible_skies_and_a_single_time():
+    prob = _problem(seed=87, n_chan=4, n_time=1, n_point=50, nside=0)
+    n_f = len(prob.freqs_hz)
+    prob.sky = W.Sky(np.zeros(0), np.zeros(0), np.zeros((1, 0, n_f)))
+    out, _ = _run(prob, fv.FV_MIXED, 2)
+    assert np.all(out == 0)
+    prob.sky = W.Sky(np.array([0.1, 2.0]), np.array([np.pi / 2, np.pi / 2 - 1e-3]), np.ones((1, 2, n_f)))
+    out, _ = _run(prob, fv.FV_FP64, 3)      # around the north celestial pole: below the horizon at -30.7 deg
+    assert np.all(out == 0)
+
+
+@pytest.mark.parametrize("precision", [fv.FV_FP64, fv.FV_MIXED])
+def test_single_channel_single_basis_function_is_the_direct_sum(precision):
+    prob = _problem(seed=88, n_chan=1, n_time=2, n_point=400, nside=2)
+    out, info = _run(prob, precision, 1)
+    assert info["basis_terms"] == 1
+    assert rel_l2(out, oracle_vis(OracleProblem.from_workload(prob), "literal")) <= TOL[precision]

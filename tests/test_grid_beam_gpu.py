@@ -99,3 +99,10 @@ def test_beam_grid_set_after_the_sky_and_errors():
     with pytest.raises(fv.FvError) as e:
         fv.Plan.create(prob.freqs_hz, prob.lsts_rad, prob.latitude_rad, beam="grid")
     assert e.value.status == fv.FV_ERR_ARG
+
+
+def test_axisymmetric_grid_one_azimuth_column_fp64():
+    prob = _gridded(W.config_hex127(seed=97, n_chan=2, n_time=1, n_point=500, nside=2, radius=2),
+                    n_theta=91, n_phi=1, ellipticity=0.0)
+    out, _ = _run(prob, fv.FV_FP64, "type3")
+    assert rel_l2(out, oracle_vis(OracleProblem.from_workload(prob))) <= TOL[fv.FV_FP64]
