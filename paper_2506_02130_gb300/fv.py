@@ -21,6 +21,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfftvis_gb300.so")
 
+ABI_VERSION = 3          # FV_ABI_VERSION of include/fv.h that the structs below mirror
 FV_OK, FV_ERR_ARG, FV_ERR_OOM, FV_ERR_CUDA, FV_ERR_STATE, FV_ERR_TIMEOUT, FV_ERR_UNSUPPORTED = range(7)
 FV_FP64, FV_MIXED = 0, 1
 SPREAD = {"auto": 0, "gather": 1, "scatter": 2, "atomic": 3}
@@ -108,6 +109,11 @@ def load_library(path: str = LIB_PATH):
             fn = getattr(lib, name)
             fn.restype = res
             fn.argtypes = args
+        # the structs above mirror include/fv.h of this version; a library built from another one would
+        # read them with another layout
+        if lib.fv_abi_version() != ABI_VERSION:
+            raise FvError(FV_ERR_STATE, f"{path} has ABI version {lib.fv_abi_version()}, this binding "
+                                        f"expects {ABI_VERSION}: rebuild with __graft_entry__.build()")
         _lib = lib
     return _lib
 
