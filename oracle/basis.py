@@ -38,7 +38,8 @@ from dataclasses import replace
 
 import numpy as np
 
-from .oracle import OracleProblem, oracle_enu, oracle_vis, oracle_voltage, oracle_voltage_grid
+from .oracle import (OracleProblem, bspline_coefficients, oracle_enu, oracle_vis, oracle_voltage,
+                     oracle_voltage_grid, oracle_voltage_grid3)
 
 
 def basis_matrix(freqs_hz, K: int) -> np.ndarray:
@@ -89,9 +90,12 @@ def _voltages(p: OracleProblem, beam: int, theta: np.ndarray, az: np.ndarray) ->
     out = np.empty((len(theta), len(p.freqs_hz)))
     if kind == "grid":
         G = np.asarray(p.beam_grids[beam if per_antenna else -1], dtype=np.float64)
+        cubic = p.beam_grid_order == 3
+        coefs = [bspline_coefficients(G[q]) for q in range(len(p.freqs_hz))] if cubic else None
         for n, (th, a) in enumerate(zip(theta, az)):
             for q in range(len(p.freqs_hz)):
-                out[n, q] = oracle_voltage_grid(G[q], float(th), float(a))
+                out[n, q] = (oracle_voltage_grid3(G[q], float(th), float(a), coefs[q]) if cubic
+                             else oracle_voltage_grid(G[q], float(th), float(a)))
         return out
     for n, th in enumerate(theta):
         for q, nu in enumerate(p.freqs_hz):
@@ -130,6 +134,7 @@ def basis_vis(p: OracleProblem, K: int | None = None, M: np.ndarray | None = Non
                 continue
             sub = replace(p, pairs=np.asarray(p.pairs)[bls], ra=np.asarray(p.ra)[vis], dec=np.asarray(p.dec)[vis],
                           flux=c[None], lsts_rad=np.asarray(p.lsts_rad)[t:t + 1], beam="uniform",
-                          beam_param=(), polarized=False, beams=None, beam_of_ant=None, beam_grids=None)
+                          beam_param=(), polarized=False, beams=None, beam_of_ant=None, beam_grids=None,
+                          beam_grid_order=1)
             out[:, t, bls, :] = oracle_vis(sub, mode)[:, 0]
     return out

@@ -41,7 +41,8 @@
  *    folded into the antenna phasors (factored);
  *  - gridded (numerical) beams (Section 2.4): voltage samples per channel on
  *    a regular grid of zenith angle (zenith to horizon) and azimuth (east of
- *    north, periodic), interpolated bilinearly; they enter as per-antenna
+ *    north, periodic), interpolated bilinearly or by bicubic B-splines (the
+ *    zenith-angle axis mirrored at its ends); they enter as per-antenna
  *    beams (one gridded beam for every antenna is the shared-beam case).
  */
 #include <math.h>
@@ -89,6 +90,9 @@ typedef struct {
      * i (pi/2) / (grid_n_theta - 1) and azimuth j 2 pi / grid_n_phi (east of north), channel f */
     int grid_n_theta, grid_n_phi;
     const double *beam_grids;
+    /* 1: bilinear in the samples; 3: bicubic B-spline, beam_grids then holding the B-spline
+     * coefficients of each plane (oracle.py computes them from the samples) */
+    int grid_order;
 } oracle_problem;
 
 /* Equatorial (ra, dec) to topocentric East-North-Up unit vector at local
@@ -127,6 +131,47 @@ double oracle_voltage_grid(const double *plane, int n_theta, int n_phi, double t
     const int j0 = ((j % n_phi) + n_phi) % n_phi, j1 = (j0 + 1) % n_phi;
     return (1.0 - a) * (1.0 - b) * plane[i * n_phi + j0] + (1.0 - a) * b * plane[i * n_phi + j1] +
            a * (1.0 - b) * plane[(i + 1) * n_phi + j0] + a * b * plane[(i + 1) * n_phi + j1];
+}
+
+/* Cubic B-spline B3 at offsets (a + 1, a, 1 - a, 2 - a) from the four nearest knots, a in [0, 1). */
+static void bspline3_weights(double a, double w[4])
+{
+    const double b = 1.0 - a;
+    w[0] = b * b * b / 6.0;
+    w[1] = (3.0 * a * a * a - 6.0 * a * a + 4.0) / 6.0;
+    w[2] = (3.0 * b * b * b - 6.0 * b * b + 4.0) / 6.0;
+    w[3] = a * a * a / 6.0;
+}
+
+/* Voltage of a gridded beam by bicubic B-spline interpolation (Section 2.4 names bicubic among the
+ * orders of its beam interpolation): coef[i * n_phi + j] are the B-spline coefficients of the plane
+ * on the same grid as oracle_voltage_grid, the zenith-angle axis continued by mirror symmetry about
+ * its first and last samples, the azimuth axis periodic. */
+double oracle_voltage_grid3(const double *coef, int n_theta, int n_phi, double theta, double az)
+{
+    const double dth = (M_PI / 2.0) / (n_theta - 1), dph = 2.0 * M_PI / n_phi;
+    const double u = theta / dth;
+    int i = (int)floor(u);
+    if (i > n_theta - 2) i = n_theta - 2;
+    if (i < 0) i = 0;
+    double azw = fmod(az, 2.0 * M_PI);
+    if (azw < 0.0) azw += 2.0 * M_PI;
+    const double v = azw / dph;
+    const int j = (int)floor(v);
+    double wt[4], wp[4];
+    bspline3_weights(u - i, wt);
+    bspline3_weights(v - j, wp);
+    double acc = 0.0;
+    for (int r = 0; r < 4; ++r) {
+        int ii = i - 1 + r;
+        if (ii < 0) ii = -ii;
+        if (ii > n_theta - 1) ii = 2 * (n_theta - 1) - ii;
+        for (int c = 0; c < 4; ++c) {
+            const int jj = (((j - 1 + c) % n_phi) + n_phi) % n_phi;
+            acc += wt[r] * wp[c] * coef[ii * n_phi + jj];
+        }
+    }
+    return acc;
 }
 
 /* Scalar voltage response A(theta, nu) of the beam (Section 2.4, analytic beams). */
@@ -253,9 +298,9 @@ int oracle_vis(const oracle_problem *P, double *vis, int mode, int n_threads)
                     for (int k = 0; k < nbeam; ++k)
                         volt[(size_t)v * nbeam + k] =
                             P->beam_kinds[k] == ORACLE_BEAM_GRID
-                                ? oracle_voltage_grid(P->beam_grids + ((size_t)k * P->n_freq + f) *
-                                                                          P->grid_n_theta * P->grid_n_phi,
-                                                      P->grid_n_theta, P->grid_n_phi, theta, az)
+                                ? (P->grid_order == 3 ? oracle_voltage_grid3 : oracle_voltage_grid)(
+                                      P->beam_grids + ((size_t)k * P->n_freq + f) * P->grid_n_theta * P->grid_n_phi,
+                                      P->grid_n_theta, P->grid_n_phi, theta, az)
                                 : oracle_voltage(P->beam_kinds[k], &P->beam_params[3 * k], theta, nu);
                 }
             }

@@ -40,7 +40,8 @@ class _Problem(C.Structure):
                 ("beam_param", C.c_double * 3), ("polarized", C.c_int),
                 ("n_beams", C.c_int), ("beam_kinds", C.POINTER(C.c_int)),
                 ("beam_params", C.POINTER(C.c_double)), ("beam_of_ant", C.POINTER(C.c_int)),
-                ("grid_n_theta", C.c_int), ("grid_n_phi", C.c_int), ("beam_grids", C.POINTER(C.c_double))]
+                ("grid_n_theta", C.c_int), ("grid_n_phi", C.c_int), ("beam_grids", C.POINTER(C.c_double)),
+                ("grid_order", C.c_int)]
 
 
 def _load():
@@ -61,6 +62,8 @@ def _load():
             lib.oracle_max_threads.restype = C.c_int
             lib.oracle_voltage_grid.argtypes = [C.POINTER(C.c_double), C.c_int, C.c_int, C.c_double, C.c_double]
             lib.oracle_voltage_grid.restype = C.c_double
+            lib.oracle_voltage_grid3.argtypes = [C.POINTER(C.c_double), C.c_int, C.c_int, C.c_double, C.c_double]
+            lib.oracle_voltage_grid3.restype = C.c_double
             _lib = lib
     return _lib
 
@@ -88,6 +91,7 @@ class OracleProblem:
     # gridded beams: voltage samples [n_freq][n_theta][n_phi] of the plan's beam (beam == "grid") and of
     # per-antenna beam k (beams[k] == ("grid", ())), keyed by beam index (-1: the plan's beam)
     beam_grids: dict | None = None
+    beam_grid_order: int = 1            # 1 bilinear, 3 bicubic B-spline
 
     @classmethod
     def from_workload(cls, prob, pairs=None, freq_idx=None, time_idx=None, src_idx=None):
@@ -109,7 +113,8 @@ class OracleProblem:
             grids = {k: np.asarray(v)[freq_idx] for k, v in grids.items()}
         return cls(prob.ant_enu, prob.pairs if pairs is None else pairs, ra, dec, flux, freqs,
                    lsts, prob.latitude_rad, prob.beam, tuple(prob.beam_param), prob.polarized,
-                   getattr(prob, "beams", None), getattr(prob, "beam_of_ant", None), grids)
+                   getattr(prob, "beams", None), getattr(prob, "beam_of_ant", None), grids,
+                   getattr(prob, "beam_grid_order", 1))
 
 
 def oracle_vis(p: OracleProblem, mode: str = "factored", n_threads: int = 0) -> np.ndarray:
@@ -147,14 +152,16 @@ def oracle_vis(p: OracleProblem, mode: str = "factored", n_threads: int = 0) -> 
                 raise ValueError("gridded beams need [n_freq][n_theta][n_phi] samples")
             allg = np.zeros((len(kinds),) + shape)
             for k in gridded:
-                allg[k] = np.asarray(grids[k], dtype=np.float64)
+                g = np.asarray(grids[k], dtype=np.float64)
+                allg[k] = g if p.beam_grid_order == 1 else np.stack([bspline_coefficients(pl) for pl in g])
             allg = np.ascontiguousarray(allg)
             gth, gph, grid_p = shape[1], shape[2], _p(allg)
         keep = (kinds, params, boa, grid_p and allg)     # alive for the call
     prob = _Problem(len(ant), _p(ant), len(pairs), pairs.ctypes.data_as(C.POINTER(C.c_int)),
                     len(ra), _p(ra), _p(dec), flux.shape[0], _p(flux), len(freqs), _p(freqs),
                     len(lsts), _p(lsts), float(p.latitude_rad), BEAMS[p.beam], bp,
-                    1 if p.polarized else 0, nb, kinds_p, params_p, boa_p, gth, gph, grid_p)
+                    1 if p.polarized else 0, nb, kinds_p, params_p, boa_p, gth, gph, grid_p,
+                    int(p.beam_grid_order))
     out = np.zeros((len(freqs), len(lsts), len(pairs), n_pol, 2), dtype=np.float64)
     rc = lib.oracle_vis(C.byref(prob), _p(out), 0 if mode == "literal" else 1, int(n_threads))
     if rc != 0:
@@ -187,6 +194,41 @@ def oracle_voltage_grid(plane, theta: float, az: float) -> float:
     """Bilinear voltage of a gridded beam's samples plane[n_theta][n_phi] (see oracle.c)."""
     a = np.ascontiguousarray(plane, dtype=np.float64)
     return _load().oracle_voltage_grid(_p(a), a.shape[0], a.shape[1], float(theta), float(az))
+
+
+def _collocation(n: int, periodic: bool) -> np.ndarray:
+    """Cubic B-spline collocation matrix of n knots at the knots: sample i = (c[i-1] + 4 c[i] + c[i+1]) / 6,
+    the out-of-range knots mirrored about the end samples (c[-1] = c[1], c[n] = c[n-2]) or wrapped."""
+    B = np.zeros((n, n))
+    for i in range(n):
+        for off, wgt in ((-1, 1.0 / 6.0), (0, 4.0 / 6.0), (1, 1.0 / 6.0)):
+            k = i + off
+            if periodic:
+                k %= n
+            else:
+                if k < 0:
+                    k = -k
+                if k > n - 1:
+                    k = 2 * (n - 1) - k
+            B[i, k] += wgt
+    return B
+
+
+def bspline_coefficients(plane) -> np.ndarray:
+    """B-spline coefficients [n_theta][n_phi] that interpolate the samples plane[n_theta][n_phi] at the
+    grid nodes (mirror ends along zenith angle, periodic along azimuth): dense solves of the two
+    collocation systems, one axis after the other."""
+    F = np.asarray(plane, dtype=np.float64)
+    nth, nph = F.shape
+    Cth = np.linalg.solve(_collocation(nth, False), F) if nth > 1 else F.copy()
+    return np.linalg.solve(_collocation(nph, True), Cth.T).T
+
+
+def oracle_voltage_grid3(plane, theta: float, az: float, coef=None) -> float:
+    """Bicubic B-spline voltage of a gridded beam's samples plane[n_theta][n_phi] (see oracle.c); coef:
+    the plane's coefficients if already computed."""
+    c = np.ascontiguousarray(bspline_coefficients(plane) if coef is None else coef, dtype=np.float64)
+    return _load().oracle_voltage_grid3(_p(c), c.shape[0], c.shape[1], float(theta), float(az))
 
 
 def max_threads() -> int:

@@ -413,3 +413,48 @@ def test_grid_beam_as_one_of_two_per_antenna_beams():
     gridded.beam_grids = {0: W.grid_beam(prob.freqs_hz, 721, 4, math.radians(25.0), 150e6)}
     assert rel_l2(oracle_vis(gridded, "literal"), oracle_vis(analytic, "literal")) < 2e-5
     assert rel_l2(oracle_vis(gridded, "factored"), oracle_vis(gridded, "literal")) < 1e-12
+
+
+def test_bicubic_grid_beam_interpolates_and_matches_scipy_splines_per_axis():
+    from scipy import ndimage
+    from oracle.oracle import oracle_voltage_grid3
+    rng = np.random.default_rng(24)
+    nth, nph = 9, 10
+    dth, dph = (math.pi / 2) / (nth - 1), 2 * math.pi / nph
+    T = rng.uniform(0.2, 1.0, size=(nth, nph))
+    for i in range(nth - 1):
+        for j in range(nph):
+            assert oracle_voltage_grid3(T, i * dth, j * dph) == pytest.approx(T[i, j], abs=1e-12)
+    # zenith-angle axis: the cubic spline with whole-sample mirror ends (scipy's 'mirror')
+    f = rng.uniform(0.2, 1.0, nth)
+    A = np.repeat(f[:, None], nph, axis=1)
+    for u in (0.2, 0.5, 3.7, 6.01, 7.9):
+        want = ndimage.map_coordinates(f, [[u]], order=3, mode="mirror")[0]
+        assert oracle_voltage_grid3(A, u * dth, 1.234) == pytest.approx(want, abs=1e-12)
+    # azimuth axis: the periodic cubic spline (scipy's 'grid-wrap'), on both sides of 2 pi
+    g = rng.uniform(0.2, 1.0, nph)
+    P = np.repeat(g[None, :], nth, axis=0)
+    for v in (0.3, 4.5, 9.2, 9.9):
+        want = ndimage.map_coordinates(g, [[v]], order=3, mode="grid-wrap")[0]
+        assert oracle_voltage_grid3(P, 0.4, v * dph) == pytest.approx(want, abs=1e-12)
+        assert oracle_voltage_grid3(P, 0.4, v * dph - 2 * math.pi) == pytest.approx(want, abs=1e-12)
+    # a separable table gives the product of the two one-axis splines
+    S = np.outer(f, g)
+    for u, v in ((1.3, 2.6), (7.5, 9.7)):
+        want = (ndimage.map_coordinates(f, [[u]], order=3, mode="mirror")[0] *
+                ndimage.map_coordinates(g, [[v]], order=3, mode="grid-wrap")[0])
+        assert oracle_voltage_grid3(S, u * dth, v * dph) == pytest.approx(want, abs=1e-12)
+
+
+def test_bicubic_grid_beam_converges_at_fourth_order():
+    prob = W.config_hex127(seed=25, n_chan=2, n_time=1, n_point=400, nside=0, radius=2)
+    prob.beam_param = (math.radians(30.0), 150e6)
+    ref = oracle_vis(OracleProblem.from_workload(prob), "literal")
+    errs = []
+    for nth in (46, 91, 181):
+        p = OracleProblem.from_workload(prob)
+        p.beam, p.beam_grid_order = "grid", 3
+        p.beam_grids = {-1: W.grid_beam(prob.freqs_hz, nth, 4, math.radians(30.0), 150e6)}
+        errs.append(rel_l2(oracle_vis(p, "literal"), ref))
+    # fourth order: a factor 16 per halving of the grid step (second order, bilinear, gives 4)
+    assert 11.0 < math.sqrt(errs[0] / errs[2]) < 23.0, errs
