@@ -205,15 +205,19 @@ fv_status fv_set_beams(fv_plan_t p, int n_beams, const int *kinds, const double 
  * [n_freq][n_theta][n_phi], copied) at channel f, zenith angle
  * theta_i = i (pi/2) / (n_theta - 1) (zenith to horizon) and azimuth
  * phi_j = j 2 pi / n_phi (east of north, periodic); a source's voltage is the
- * bilinear interpolation in (theta, phi) of its channel's samples (the lowest
- * order Section 2.4 names), in the plan's precision.  The Jones matrix of the
+ * interpolation in (theta, phi) of its channel's samples, in the plan's
+ * precision: order 1 bilinear, order 3 bicubic B-spline (interpolating: the
+ * B-spline coefficients are solved for on the host in FP64, the zenith-angle
+ * axis continued by mirror symmetry about its end samples, the azimuth axis
+ * periodic), two of the orders Section 2.4 names.  The Jones matrix of the
  * polarised path is A(theta, phi) R(az) as for the analytic beams.  beam = -1
  * is the plan's beam (all antennas); beam = k >= 0 is per-antenna beam k of
  * the last fv_set_beams (a later fv_set_beams drops the per-antenna grids).
  * May be called before or after fv_set_sky; applies to later executions.
  * Errors: FV_ERR_ARG (beam out of range, n_theta < 2, n_phi < 1,
- * n_theta * n_phi > 2^22, NULL or non-finite samples), FV_ERR_OOM. */
-fv_status fv_set_beam_grid(fv_plan_t p, int beam, int n_theta, int n_phi, const double *voltage);
+ * n_theta * n_phi > 2^22, order not 1 or 3, NULL or non-finite samples),
+ * FV_ERR_OOM. */
+fv_status fv_set_beam_grid(fv_plan_t p, int beam, int n_theta, int n_phi, int order, const double *voltage);
 
 /* Set the sky: n_src point sources at (ra_rad, dec_rad), host arrays, copied.
  * flux: [n_stokes][n_src][n_freq] Jy (n_stokes = 1: I; 4: I, Q, U, V), FP64 if

@@ -57,8 +57,8 @@ struct BeamParams {
     double p0, p1, p2;
     // gridded beams (Section 2.4, numerical beams): voltage samples [n_freq][n_th][n_ph] on the grid
     // theta_i = i (pi/2) / (n_th - 1) (zenith angle), phi_j = j 2 pi / n_ph (azimuth east of north)
-    const void *grid;   // device samples, FP64 if grid_fp64 else FP32
-    int grid_fp64, n_th, n_ph;
+    const void *grid;   // device samples (order 1) or B-spline coefficients (order 3), FP64 if grid_fp64
+    int grid_fp64, n_th, n_ph, grid_order;
 };
 
 // Per-time binning geometry: bins are tiles of the top (highest-frequency)
@@ -153,12 +153,64 @@ __device__ __forceinline__ G grid_voltage(const BeamParams &b, G s0, G s1, G rho
     return ((G)1 - a) * (((G)1 - c) * t00 + c * t01) + a * (((G)1 - c) * t10 + c * t11);
 }
 
+// Cubic B-spline weights of the four knots around fractional offset a in [0, 1).
+template <class G> __device__ __forceinline__ void bspline3(G a, G w[4])
+{
+    const G b = (G)1 - a, s = (G)1 / (G)6;
+    w[0] = b * b * b * s;
+    w[1] = ((G)3 * a * a * a - (G)6 * a * a + (G)4) * s;
+    w[2] = ((G)3 * b * b * b - (G)6 * b * b + (G)4) * s;
+    w[3] = a * a * a * s;
+}
+
+// The same beam by bicubic B-spline interpolation of its coefficients (zenith-angle knots mirrored
+// about the end samples, azimuth periodic).
+template <class G>
+__device__ __forceinline__ G grid_voltage3(const BeamParams &b, G s0, G s1, G rho, G s2, int q)
+{
+    const G kHalfPi = (G)1.5707963267948966192, kTwoPi = (G)6.283185307179586477;
+    const G dth = kHalfPi / (G)(b.n_th - 1), dph = kTwoPi / (G)b.n_ph;
+    G az = atan2(s0, s1);
+    if (az < (G)0) az += kTwoPi;
+    const G u = atan2(rho, s2) / dth;
+    int i = (int)floor(u);
+    i = i < 0 ? 0 : (i > b.n_th - 2 ? b.n_th - 2 : i);
+    const G v = az / dph;
+    const int j = (int)floor(v);
+    G wt[4], wp[4];
+    bspline3<G>(u - (G)i, wt);
+    bspline3<G>(v - (G)j, wp);
+    int jj[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        int k = (j - 1 + c) % b.n_ph;
+        jj[c] = k < 0 ? k + b.n_ph : k;
+    }
+    const size_t plane = (size_t)q * b.n_th * b.n_ph;
+    G acc = (G)0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        int ii = i - 1 + r;
+        ii = ii < 0 ? -ii : (ii > b.n_th - 1 ? 2 * (b.n_th - 1) - ii : ii);
+        const size_t row = plane + (size_t)ii * b.n_ph;
+        G sr = (G)0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            sr += wp[c] * (b.grid_fp64 ? (G)((const double *)b.grid)[row + jj[c]]
+                                       : (G)((const float *)b.grid)[row + jj[c]]);
+        acc += wt[r] * sr;
+    }
+    return acc;
+}
+
 // Beam voltage at channel q (frequency nu) for the direction (s0, s1, s2): analytic beams by
 // voltage<G>, gridded beams from their samples.
 template <class G>
 __device__ __forceinline__ G beam_voltage(const BeamParams &b, G s0, G s1, G rho, G s2, G nu, int q)
 {
-    return b.kind == 3 ? grid_voltage<G>(b, s0, s1, rho, s2, q) : voltage<G>(b, rho, s2, nu);
+    if (b.kind == 3)
+        return b.grid_order == 3 ? grid_voltage3<G>(b, s0, s1, rho, s2, q) : grid_voltage<G>(b, s0, s1, rho, s2, q);
+    return voltage<G>(b, rho, s2, nu);
 }
 
 // Strengths of one source in one slice (Eq. 1-2 with the slice's beams): the

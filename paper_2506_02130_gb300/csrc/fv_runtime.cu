@@ -1386,7 +1386,61 @@ fv_status fv_set_beams(fv_plan_t p, int n_beams, const int *kinds, const double 
     return setup_array(p);
 }
 
-fv_status fv_set_beam_grid(fv_plan_t p, int beam, int n_theta, int n_phi, const double *voltage)
+// Cubic B-spline coefficients c of samples f along one axis, c[i-1] + 4 c[i] + c[i+1] = 6 f[i]:
+// with the out-of-range knots mirrored about the end samples (Thomas algorithm; rows 0 and n-1 carry a
+// 2 for the mirrored neighbour), or wrapped (cyclic tridiagonal, Sherman-Morrison).  In place,
+// elements f[k * stride], k < n.
+static void bspline_prefilter(double *f, int n, long stride, bool periodic)
+{
+    if (n == 1) return;
+    std::vector<double> r(n), x(n);
+    for (int k = 0; k < n; ++k) r[k] = 6.0 * f[k * stride];
+    if (n == 2) {
+        // both boundary rules give 4 c0 + 2 c1 = r0, 2 c0 + 4 c1 = r1
+        x[0] = (4.0 * r[0] - 2.0 * r[1]) / 12.0;
+        x[1] = (4.0 * r[1] - 2.0 * r[0]) / 12.0;
+    } else if (!periodic) {
+        std::vector<double> cp(n), dp(n);
+        // row 0: 4 c0 + 2 c1; rows 1..n-2: c_{k-1} + 4 c_k + c_{k+1}; row n-1: 2 c_{n-2} + 4 c_{n-1}
+        cp[0] = 2.0 / 4.0;
+        dp[0] = r[0] / 4.0;
+        for (int k = 1; k < n; ++k) {
+            const double a = k == n - 1 ? 2.0 : 1.0, c = k == n - 1 ? 0.0 : 1.0;
+            const double m = 4.0 - a * cp[k - 1];
+            cp[k] = c / m;
+            dp[k] = (r[k] - a * dp[k - 1]) / m;
+        }
+        x[n - 1] = dp[n - 1];
+        for (int k = n - 2; k >= 0; --k) x[k] = dp[k] - cp[k] * x[k + 1];
+    } else {
+        // A = tridiag(1, 4, 1) with corners 1 = B + u v^T, u = (g, 0.., 1), v = (1, 0.., 1/g), g = -4
+        const double g = -4.0;
+        auto thomas = [&](std::vector<double> &rhs, std::vector<double> &out) {
+            std::vector<double> cp(n), dp(n);
+            double b0 = 4.0 - g;
+            cp[0] = 1.0 / b0;
+            dp[0] = rhs[0] / b0;
+            for (int k = 1; k < n; ++k) {
+                const double b = k == n - 1 ? 4.0 - 1.0 / g : 4.0;
+                const double m = b - cp[k - 1];
+                cp[k] = 1.0 / m;
+                dp[k] = (rhs[k] - dp[k - 1]) / m;
+            }
+            out[n - 1] = dp[n - 1];
+            for (int k = n - 2; k >= 0; --k) out[k] = dp[k] - cp[k] * out[k + 1];
+        };
+        std::vector<double> u(n, 0.0), z(n);
+        u[0] = g;
+        u[n - 1] = 1.0;
+        thomas(r, x);
+        thomas(u, z);
+        const double fact = (x[0] + x[n - 1] / g) / (1.0 + z[0] + z[n - 1] / g);
+        for (int k = 0; k < n; ++k) x[k] -= fact * z[k];
+    }
+    for (int k = 0; k < n; ++k) f[k * stride] = x[k];
+}
+
+fv_status fv_set_beam_grid(fv_plan_t p, int beam, int n_theta, int n_phi, int order, const double *voltage)
 {
     if (!p) return FV_ERR_ARG;
     if (cudaSetDevice(p->device) != cudaSuccess) return p->fail(FV_ERR_CUDA, "cudaSetDevice failed");
@@ -1394,10 +1448,23 @@ fv_status fv_set_beam_grid(fv_plan_t p, int beam, int n_theta, int n_phi, const 
         return p->fail(FV_ERR_ARG, "beam index out of range (per-antenna beams come from fv_set_beams)");
     if (n_theta < 2 || n_phi < 1 || (long)n_theta * n_phi > (1L << 22))
         return p->fail(FV_ERR_ARG, "need n_theta >= 2, n_phi >= 1 and n_theta * n_phi <= 2^22");
+    if (order != 1 && order != 3) return p->fail(FV_ERR_ARG, "interpolation order must be 1 or 3");
     if (!voltage) return p->fail(FV_ERR_ARG, "NULL beam samples");
     const size_t n = p->freq.size() * (size_t)n_theta * n_phi;
     for (size_t i = 0; i < n; ++i)
         if (!std::isfinite(voltage[i])) return p->fail(FV_ERR_ARG, "non-finite beam sample");
+    std::vector<double> table;
+    if (order == 3) {
+        // bicubic: the B-spline coefficients of every channel's plane, zenith-angle columns then
+        // azimuth rows
+        table.assign(voltage, voltage + n);
+        for (size_t f = 0; f < p->freq.size(); ++f) {
+            double *pl = table.data() + f * (size_t)n_theta * n_phi;
+            for (int j = 0; j < n_phi; ++j) bspline_prefilter(pl + j, n_theta, n_phi, false);
+            for (int i = 0; i < n_theta; ++i) bspline_prefilter(pl + (size_t)i * n_phi, n_phi, 1, true);
+        }
+        voltage = table.data();
+    }
     const bool fp64 = p->precision == FV_FP64;
     void *d = nullptr;
     CK(cudaMalloc(&d, n * (fp64 ? sizeof(double) : sizeof(float))));
@@ -1426,6 +1493,7 @@ fv_status fv_set_beam_grid(fv_plan_t p, int beam, int n_theta, int n_phi, const 
     b.grid_fp64 = fp64 ? 1 : 0;
     b.n_th = n_theta;
     b.n_ph = n_phi;
+    b.grid_order = order;
     // the slices' geometry holds copies of the plan's beam
     for (auto &g : p->gf) g.beam = p->beam;
     p->bg.beam = p->beam;

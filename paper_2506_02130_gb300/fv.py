@@ -74,7 +74,7 @@ SIGNATURES = {
     "fv_plan": (C.c_int, [C.POINTER(fv_opts), C.POINTER(C.c_void_p)]),
     "fv_set_array": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
     "fv_set_beams": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
-    "fv_set_beam_grid": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "fv_set_beam_grid": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "fv_set_sky": (C.c_int, [C.c_void_p, C.c_long, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int]),
     "fv_execute": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "fv_destroy": (C.c_int, [C.c_void_p]),
@@ -343,17 +343,17 @@ class Plan:
                        prob.polarized, **kw)
         p.set_array(prob.ant_enu, prob.pairs)
         if grid:
-            p.set_beam_grid(-1, prob.beam_grids[-1])
+            p.set_beam_grid(-1, prob.beam_grids[-1], getattr(prob, "beam_grid_order", 1))
         return p
 
     def set_array(self, enu_m, pairs=None):
         fv_set_array(self.handle, enu_m, pairs)
         self.n_bl = fv_get_info(self.handle)["n_bl"]
 
-    def set_beams(self, beams, beam_of_ant, grids=None):
+    def set_beams(self, beams, beam_of_ant, grids=None, grid_order=1):
         """Per-antenna beams: beams = [(kind, params), ...], beam_of_ant = beam index per antenna
         (None or an empty list: the plan's single beam).  A beam of kind "grid" takes its samples
-        [n_freq][n_theta][n_phi] from grids[k] (fv_set_beam_grid)."""
+        [n_freq][n_theta][n_phi] from grids[k] (fv_set_beam_grid, interpolation order grid_order)."""
         if not beams or beam_of_ant is None:
             _check(load_library().fv_set_beams(self.handle, 0, None, None, None), self.handle)
             return
@@ -364,16 +364,16 @@ class Plan:
                self.handle)
         for k, (kind, _) in enumerate(beams):
             if kind == "grid":
-                self.set_beam_grid(k, grids[k])
+                self.set_beam_grid(k, grids[k], grid_order)
 
-    def set_beam_grid(self, beam, samples):
+    def set_beam_grid(self, beam, samples, order=1):
         """Gridded beam (fv_set_beam_grid): voltage samples [n_freq][n_theta][n_phi] for beam index
-        `beam` (-1: the plan's beam)."""
+        `beam` (-1: the plan's beam), interpolated bilinearly (order 1) or by bicubic B-splines (3)."""
         a = np.ascontiguousarray(samples, dtype=np.float64)
         if a.ndim != 3 or a.shape[0] != self.n_freq:
             raise ValueError("beam samples must be [n_freq][n_theta][n_phi]")
-        _check(load_library().fv_set_beam_grid(self.handle, int(beam), a.shape[1], a.shape[2], _ptr(a)),
-               self.handle)
+        _check(load_library().fv_set_beam_grid(self.handle, int(beam), a.shape[1], a.shape[2], int(order),
+                                               _ptr(a)), self.handle)
 
     def set_sky(self, ra, dec, flux):
         self._keep = (flux,)          # a device flux is borrowed by the plan

@@ -347,6 +347,7 @@ class Problem:
     # gridded beams (Section 2.4, numerical beams): voltage samples [n_freq][n_theta][n_phi] of the
     # plan's beam (key -1, with beam == "grid") or of per-antenna beam k (beams[k] == ("grid", ()))
     beam_grids: dict | None = None
+    beam_grid_order: int = 1       # 1 bilinear, 3 bicubic B-spline
 
     @property
     def n_vis(self) -> int:

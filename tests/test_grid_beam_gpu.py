@@ -16,9 +16,10 @@ TOL = {fv.FV_FP64: 1e-9, fv.FV_MIXED: 2e-5}
 EPS = {fv.FV_FP64: 1e-11, fv.FV_MIXED: 1e-6}
 
 
-def _gridded(prob, n_theta=46, n_phi=24, fwhm_deg=25.0, ellipticity=0.35):
+def _gridded(prob, n_theta=46, n_phi=24, fwhm_deg=25.0, ellipticity=0.35, order=1):
     prob.beam = "grid"
     prob.beam_param = ()
+    prob.beam_grid_order = order
     prob.beam_grids = {-1: W.grid_beam(prob.freqs_hz, n_theta, n_phi, math.radians(fwhm_deg), 150e6,
                                        ellipticity=ellipticity)}
     return prob
@@ -27,7 +28,7 @@ def _gridded(prob, n_theta=46, n_phi=24, fwhm_deg=25.0, ellipticity=0.35):
 def _run(prob, precision, transform, **kw):
     p = fv.Plan.from_problem(prob, precision=precision, eps=EPS[precision], transform=transform, **kw)
     if prob.beams is not None:
-        p.set_beams(prob.beams, prob.beam_of_ant, prob.beam_grids)
+        p.set_beams(prob.beams, prob.beam_of_ant, prob.beam_grids, prob.beam_grid_order)
     p.set_sky(prob.sky.ra, prob.sky.dec, prob.sky.flux)
     out = p.run()
     info = p.info()
@@ -90,11 +91,12 @@ def test_beam_grid_set_after_the_sky_and_errors():
     assert rel_l2(out, oracle_vis(OracleProblem.from_workload(prob))) <= TOL[fv.FV_MIXED]
     lib = fv.load_library()
     g = np.ascontiguousarray(grid)
-    assert lib.fv_set_beam_grid(p.handle, 0, 31, 12, g.ctypes.data) == fv.FV_ERR_ARG       # no per-antenna beams
-    assert lib.fv_set_beam_grid(p.handle, -1, 1, 12, g.ctypes.data) == fv.FV_ERR_ARG       # n_theta < 2
+    assert lib.fv_set_beam_grid(p.handle, 0, 31, 12, 1, g.ctypes.data) == fv.FV_ERR_ARG    # no per-antenna beams
+    assert lib.fv_set_beam_grid(p.handle, -1, 1, 12, 1, g.ctypes.data) == fv.FV_ERR_ARG    # n_theta < 2
+    assert lib.fv_set_beam_grid(p.handle, -1, 31, 12, 2, g.ctypes.data) == fv.FV_ERR_ARG   # order 2
     bad = g.copy()
     bad[0, 3, 4] = np.nan
-    assert lib.fv_set_beam_grid(p.handle, -1, 31, 12, bad.ctypes.data) == fv.FV_ERR_ARG
+    assert lib.fv_set_beam_grid(p.handle, -1, 31, 12, 1, bad.ctypes.data) == fv.FV_ERR_ARG
     p.close()
     with pytest.raises(fv.FvError) as e:
         fv.Plan.create(prob.freqs_hz, prob.lsts_rad, prob.latitude_rad, beam="grid")
@@ -106,3 +108,33 @@ def test_axisymmetric_grid_one_azimuth_column_fp64():
                     n_theta=91, n_phi=1, ellipticity=0.0)
     out, _ = _run(prob, fv.FV_FP64, "type3")
     assert rel_l2(out, oracle_vis(OracleProblem.from_workload(prob))) <= TOL[fv.FV_FP64]
+
+
+@pytest.mark.parametrize("precision", [fv.FV_FP64, fv.FV_MIXED])
+def test_bicubic_gridded_beam_type3(precision):
+    prob = _gridded(W.config_hex127(seed=98, n_chan=3, n_time=2, n_point=700, nside=4, radius=3), order=3)
+    out, _ = _run(prob, precision, "type3")
+    assert rel_l2(out, oracle_vis(OracleProblem.from_workload(prob))) <= TOL[precision]
+
+
+def test_bicubic_per_antenna_gridded_beam_on_the_basis_and_lattice_routes():
+    prob = W.config_hex127(seed=99, n_chan=6, n_time=1, n_point=500, nside=2, radius=3)
+    prob.ant_enu = W.hex_array(3)
+    prob.beams = [("grid", ()), ("gauss", (math.radians(30.0), 150e6))]
+    prob.beam_of_ant = np.arange(len(prob.ant_enu)) % 2
+    prob.beam_grids = {0: W.grid_beam(prob.freqs_hz, 31, 16, math.radians(35.0), 150e6, ellipticity=0.25)}
+    prob.beam_grid_order = 3
+    ref = oracle_vis(OracleProblem.from_workload(prob))
+    out, _ = _run(prob, fv.FV_MIXED, "lattice")
+    assert rel_l2(out, ref) <= TOL[fv.FV_MIXED]
+    out, _ = _run(prob, fv.FV_MIXED, "basis", n_basis=4)
+    assert rel_l2(out, basis_vis(OracleProblem.from_workload(prob), 4)) <= TOL[fv.FV_MIXED]
+
+
+def test_bicubic_fine_grid_is_closer_to_the_analytic_beam_than_bilinear():
+    prob = W.config_hex127(seed=100, n_chan=2, n_time=1, n_point=500, nside=0, radius=2)
+    prob.beam_param = (math.radians(25.0), 150e6)
+    analytic, _ = _run(prob, fv.FV_FP64, "type3")
+    lin, _ = _run(_gridded(prob, n_theta=181, n_phi=4, ellipticity=0.0, order=1), fv.FV_FP64, "type3")
+    cub, _ = _run(_gridded(prob, n_theta=181, n_phi=4, ellipticity=0.0, order=3), fv.FV_FP64, "type3")
+    assert rel_l2(cub, analytic) < 0.05 * rel_l2(lin, analytic)
