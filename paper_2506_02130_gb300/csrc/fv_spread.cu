@@ -214,12 +214,14 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
 {
     // candidates staged per round: 128 (96 in FP64, to keep the static shared memory under 48 KB)
     constexpr int kGatherChunk = sizeof(G) == 8 ? 96 : 128;
-    __shared__ int s_cx[kGatherChunk], s_cy[kGatherChunk], s_cz[kGatherChunk];
+    __shared__ int s_cz[kGatherChunk];
     __shared__ G s_fx[kGatherChunk], s_fy[kGatherChunk], s_fz[kGatherChunk];
     __shared__ G s_wx[kGatherChunk * kWpad], s_wy[kGatherChunk * kWpad];
     __shared__ __align__(16) G s_wz[kGatherChunk][NZ];
     __shared__ cpx<G> s_c[NP][kGatherChunk];
-    __shared__ unsigned char s_list[kPatches][kGatherChunk];
+    // patch lists: candidate t (bits 0-7) with its footprint origin relative to the tile, cx - x0 + 16
+    // (bits 8-15) and cy - y0 + 16 (bits 16-23), so that one shared load gives all three
+    __shared__ int s_list[kPatches][kGatherChunk];
     __shared__ int s_cnt[kPatches];
     __shared__ int s_row0[32], s_pre[32], s_total;
     const int nx = g.dim[0].nf1, ny = g.dim[1].nf1, nz = g.d == 3 ? g.dim[2].nf1 : 1;
@@ -285,8 +287,6 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
                 const int cx = cell[i], cy = cell[n_src + i];
                 const int ax = max(cx - x0, 0), bx = min(cx + w - 1 - x0, kTileX - 1);
                 const int ay = max(cy - y0, 0), by2 = min(cy + w - 1 - y0, kTileY - 1);
-                s_cx[t] = cx;
-                s_cy[t] = cy;
                 s_fx[t] = frac[i];
                 s_fy[t] = frac[n_src + i];
                 if (g.d == 3) {
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
                         for (int qx = ax / kPatchX; qx <= bx / kPatchX; ++qx) {
                             const int q = qy * 4 + qx;
                             const int pos = atomicAdd(&s_cnt[q], 1);
-                            s_list[q][pos] = (unsigned char)t;
+                            s_list[q][pos] = t | ((cx - x0 + 16) << 8) | ((cy - y0 + 16) << 16);
                         }
                 }
             }
@@ -323,9 +323,11 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
             __syncthreads();
             // 3. each warp adds the sources of its patch list into its lanes' columns
             const int cnt = s_cnt[warp];
+            const int lx16 = gx - x0 + 16, ly16 = gy - y0 + 16;
             for (int e = 0; e < cnt; ++e) {
-                const int t = s_list[warp][e];
-                const unsigned dx = (unsigned)(gx - s_cx[t]), dy = (unsigned)(gy - s_cy[t]);
+                const int ent = s_list[warp][e];
+                const int t = ent & 0xff;
+                const unsigned dx = (unsigned)(lx16 - ((ent >> 8) & 0xff)), dy = (unsigned)(ly16 - (ent >> 16));
                 if (dx < (unsigned)w && dy < (unsigned)w) {
                     const G wxy = s_wx[t * kWpad + dx] * s_wy[t * kWpad + dy];
                     G wz[NZ];
