@@ -257,15 +257,21 @@ __device__ __forceinline__ void stage(const cpx<G> *__restrict__ x, cpx<G> *__re
             for (int q = 0; q < RD; ++q) v[q] = x[pad(base + j + q * MR)];
         }
         if (Ns > 1) {
-            // twiddles w^q, w = e^{2 pi i k / (Ns RD)}: one table load and RD - 2 products (the FMA pipe
-            // has room, the load pipe less; the products add a few ulps, measured 9.2e-7 -> 9.4e-7 of
-            // relative L2 on the mixed 127-antenna workload)
-            const cpx<G> w1 = tw[k * twstep];
-            cpx<G> wq = w1;
+            if constexpr (sizeof(G) == 4) {
+                // FP32: twiddles w^q, w = e^{2 pi i k / (Ns RD)}, from one table load and RD - 2 products
+                // (the FMA pipe has room, the load pipe less; the products add a few ulps, measured
+                // 9.2e-7 -> 9.4e-7 of relative L2 on the mixed 127-antenna workload)
+                const cpx<G> w1 = tw[k * twstep];
+                cpx<G> wq = w1;
 #pragma unroll
-            for (int q = 1; q < RD; ++q) {
-                v[q] = cmul(v[q], wq);
-                if (q + 1 < RD) wq = cmul(wq, w1);
+                for (int q = 1; q < RD; ++q) {
+                    v[q] = cmul(v[q], wq);
+                    if (q + 1 < RD) wq = cmul(wq, w1);
+                }
+            } else {
+                // FP64: products would run on the narrow FP64 pipe, so every twiddle comes from the table
+#pragma unroll
+                for (int q = 1; q < RD; ++q) v[q] = cmul(v[q], tw[q * k * twstep]);
             }
         }
         Dft<G, RD>::run(v);
