@@ -4,7 +4,8 @@
 // One pass transforms every row of its input along the row's contiguous axis:
 //   load the N grid values of the row, multiply by the deconvolution prescale
 //   1/Phihat(l w pi / M) of this axis (Section 2.2, step 3a, applied on the
-//   grid side of the inner transform), place them at l - N/2 (mod M) of a
+//   grid side of the inner transform; pre = nullptr when the spreading kernel
+//   already applied it), place them at l - N/2 (mod M) of a
 //   zero-padded length-M vector, run a Stockham autosort FFT with the sign
 //   e^{+2 pi i l m / M}, and keep only the band m in [-H, B-1-H] that the
 //   interpolation reads, written transposed as out[b][row].
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, (FftMinBlocks<G, MAXRD>::value)) k_f
                 const int l = idx - r * N;
                 int m = l - half;
                 if (m < 0) m += M;
-                buf0[pad(r * M + m)] = cscale(pf.v[k], pre[l]);
+                buf0[pad(r * M + m)] = pre ? cscale(pf.v[k], pre[l]) : pf.v[k];
             }
         }
         // a row longer than the prefetch holds (then R = 1): the rest of it straight from memory
@@ -401,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, (FftMinBlocks<G, MAXRD>::value)) k_f
             int m = l - half;
             if (m < 0) m += M;
             const cpx<G> v = row0 + r < rows ? in[row0 * N + idx] : cmk<G>((G)0, (G)0);
-            buf0[pad(r * M + m)] = cscale(v, pre[l]);
+            buf0[pad(r * M + m)] = pre ? cscale(v, pre[l]) : v;
         }
         __syncthreads();
         // issue the next block's loads before the stages

@@ -89,6 +89,9 @@ struct SliceGeom {
     BeamParams beam2;   // per-antenna beams (Section 2.2.3): the second antenna's beam of the baseline
     int two_beams;      // 0: the product is beam x beam; 1: beam x beam2
     DimGeom dim[3];
+    // x and y prescale tables 1/Phihat (grid precision) that the tiled spreading kernels apply when they
+    // store each grid cell (the FFT passes then skip them); nullptr: the FFT passes apply them
+    const void *pre_x, *pre_y;
 };
 
 // Beam voltage A(theta) of the analytic beams (Section 2.4): Gaussian power beam,

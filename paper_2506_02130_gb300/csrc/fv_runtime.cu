@@ -580,11 +580,11 @@ static fv_status run_slices_lattice(fv_plan_s *p, fv_plan_s::Workspace &wk, cuda
             CK(prof_end(p, nvis * (8.0 + 3.0 * sizeof(G) + np * es) + gel * es));
             const long r1 = (long)lg.K * np * lg.nf[1];
             CK(prof_begin(p, PC_FFT_X, st));
-            CK(launch_fft_pass<G>(grid, A, r1, p->lat_dim[0], pre, tw, st));
+            CK(launch_fft_pass<G>(grid, A, r1, p->lat_dim[0], nullptr, tw, st));      // no prescale (ones)
             CK(prof_end(p, (double)r1 * (lg.nf[0] + Bx) * es));
             const long r2 = (long)Bx * lg.K * np;
             CK(prof_begin(p, PC_FFT_Y, st));
-            CK(launch_fft_pass<G>(A, Bb, r2, p->lat_dim[1], pre + lg.nf[0], tw + lg.nf[0], st));
+            CK(launch_fft_pass<G>(A, Bb, r2, p->lat_dim[1], nullptr, tw + lg.nf[0], st));
             CK(prof_end(p, (double)r2 * (lg.nf[1] + By) * es));
             const int ntm = om.nt > 0 ? om.nt : nt;
             char *out = vis + ((size_t)(f - om.f0) * ntm + (t - om.t0)) * slice_bytes;
@@ -657,6 +657,8 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
                                   frac, cs, st));
                 CK(prof_end(p, prep_bytes));
                 const double r0 = D[0].qscale / p->qscale_top[0], r1 = D[1].qscale / p->qscale_top[1];
+                g.pre_x = pre + p->pre_off[(size_t)f * 3];         // applied as the tile is stored
+                g.pre_y = pre + p->pre_off[(size_t)f * 3 + 1];
                 CK(prof_begin(p, PC_SPREAD, st));
                 if (p->spread_method == FV_SPREAD_SCATTER)
                     CK(launch_spread_scatter<G>(wk.offsets, wk.cell, frac, cs, p->n_src, g, tb, r0, r1, grid, st));
@@ -672,15 +674,18 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
                 CK(prof_end(p, src_bytes + gel * es));
             }
             const size_t o0 = (size_t)f * 3;
+            // the tiled spreading kernels stored the grid with its x and y prescale already applied
+            const G *pre_x = p->tiled ? nullptr : pre + p->pre_off[o0];
+            const G *pre_y = p->tiled ? nullptr : pre + p->pre_off[o0 + 1];
             // pass 1 along x: rows (pol, z, y)
             const long r1 = (long)p->n_pol * D[2].nf1 * D[1].nf1;
             CK(prof_begin(p, PC_FFT_X, st));
-            CK(launch_fft_pass<G>(grid, A, r1, D[0], pre + p->pre_off[o0], tw + p->tw_off[o0], st));
+            CK(launch_fft_pass<G>(grid, A, r1, D[0], pre_x, tw + p->tw_off[o0], st));
             CK(prof_end(p, (double)r1 * (D[0].nf1 + D[0].B) * es));
             // pass 2 along y: rows (bx, pol, z)
             const long r2 = (long)D[0].B * p->n_pol * D[2].nf1;
             CK(prof_begin(p, PC_FFT_Y, st));
-            CK(launch_fft_pass<G>(A, Bb, r2, D[1], pre + p->pre_off[o0 + 1], tw + p->tw_off[o0 + 1], st));
+            CK(launch_fft_pass<G>(A, Bb, r2, D[1], pre_y, tw + p->tw_off[o0 + 1], st));
             CK(prof_end(p, (double)r2 * (D[1].nf1 + D[1].B) * es));
             if (p->d == 2 || D[2].nf1 <= FV_ZDIRECT_MAX) {
                 // z (if any) summed directly inside the interpolation: no z pass
@@ -934,6 +939,8 @@ fv_status run_basis(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, cha
             CK(launch_prep_basis<G>(wk.sdir, wk.sidx, wk.offsets + nb, p->n_src, p->d_bas_shat, (const G *)p->d_bas_Mg,
                                     (const G *)p->d_bas_dg, p->d_bas_freq, nf, K, Kp, g, wk.cell, frac, cs, st));
             CK(prof_end(p, nvis * (24.0 + 4.0 + K * 8.0 + 12.0 + 3.0 * sizeof(G) + Kp * es)));
+            g.pre_x = pre + p->pre_off[0];                        // applied as the tile is stored
+            g.pre_y = pre + p->pre_off[1];
             for (int k0 = 0; k0 < Kp; k0 += np) {
                 CK(prof_begin(p, PC_SPREAD, st));
                 CK(launch_spread_tile<G>(wk.offsets, wk.cell, frac, cs + (size_t)k0 * p->n_src, p->n_src, g, tb, 1.0,
@@ -942,11 +949,11 @@ fv_status run_basis(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, cha
             }
             const long r1 = (long)K * D[2].nf1 * D[1].nf1;
             CK(prof_begin(p, PC_FFT_X, st));
-            CK(launch_fft_pass<G>(grid, A, r1, D[0], pre + p->pre_off[0], tw + p->tw_off[0], st));
+            CK(launch_fft_pass<G>(grid, A, r1, D[0], nullptr, tw + p->tw_off[0], st));
             CK(prof_end(p, (double)r1 * (D[0].nf1 + D[0].B) * es));
             const long r2 = (long)D[0].B * K * D[2].nf1;
             CK(prof_begin(p, PC_FFT_Y, st));
-            CK(launch_fft_pass<G>(A, Bb, r2, D[1], pre + p->pre_off[1], tw + p->tw_off[1], st));
+            CK(launch_fft_pass<G>(A, Bb, r2, D[1], nullptr, tw + p->tw_off[1], st));
             CK(prof_end(p, (double)r2 * (D[1].nf1 + D[1].B) * es));
             const int nug = gr.u1 - gr.u0;
             CK(prof_begin(p, PC_INTERP, st));

@@ -355,11 +355,13 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
         __syncthreads();      // every thread has read s_total before warp 0 rewrites the row table
     }
     if (gx < nx && gy < ny) {
+        // the x and y prescale of the FFT passes, applied here once per cell when the plan asks for it
+        const G sc = g.pre_x ? ((const G *)g.pre_x)[gx] * ((const G *)g.pre_y)[gy] : (G)1;
 #pragma unroll
         for (int p = 0; p < NP; ++p)
 #pragma unroll
             for (int z = 0; z < NZ; ++z)
-                if (z < nz) grid[(((size_t)p * nz + z) * ny + gy) * nx + gx] = acc[p][z];
+                if (z < nz) grid[(((size_t)p * nz + z) * ny + gy) * nx + gx] = cscale(acc[p][z], sc);
     }
 }
 
@@ -490,7 +492,10 @@ __global__ void __launch_bounds__(256, 4) k_spread_scatter(const int *__restrict
         rest /= kScatY;   // p * nz + z
         const int x = x0 + lx, y = y0 + ly;
         const int o = rest * kScatY * kScatRS + ly * kScatRS + lx;
-        if (x < nx && y < ny) grid[((size_t)rest * ny + y) * nx + x] = cmk<G>(tre[o], tim[o]);
+        if (x < nx && y < ny) {
+            const G sc = g.pre_x ? ((const G *)g.pre_x)[x] * ((const G *)g.pre_y)[y] : (G)1;
+            grid[((size_t)rest * ny + y) * nx + x] = cmk<G>(tre[o] * sc, tim[o] * sc);
+        }
     }
 }
 
