@@ -58,9 +58,9 @@ def parse():
                     help="hex127: skip timing the lattice route (Section 2.2.1 with height terms) beside it")
     ap.add_argument("--no-basis-route", action="store_true",
                     help="hex127: skip timing the spectral-basis route (Appendix A) beside it")
-    ap.add_argument("--basis-terms", type=int, default=12,
-                    help="hex127: basis functions K of the spectral-basis route (12 keeps its truncation "
-                         "error near 1e-7 on this workload)")
+    ap.add_argument("--basis-terms", type=int, default=0,
+                    help="hex127: basis functions K of the spectral-basis route (0: chosen by the plan from "
+                         "the sky's spectra against eps)")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=0.0,
                     help="serve: mean arrival rate (1/s); 0 = 70%% of the measured capacity for the request mix")
@@ -785,7 +785,9 @@ def main():
                                n_basis=args.basis_terms)
         bi = pb.info()
         bas_route = {"value": world * n_vis * args.steps / (msb / 1e3), "unit": "visibilities/s",
-                     "ms_per_step": msb / args.steps, "basis_terms": bi["basis_terms"], "grid": bi["basis_grid"],
+                     "ms_per_step": msb / args.steps, "basis_terms": bi["basis_terms"],
+                     "basis_terms_chosen_by_plan": args.basis_terms == 0, "basis_fit_error": bi["basis_fit_error"],
+                     "grid": bi["basis_grid"],
                      "kernels_ms_per_step": {k: v["ms"] for k, v in bprof.items() if v["launches"] > 0},
                      "what": "same workload, plan with transform=basis: per time one transform per basis "
                              "function of the band (Appendix A), expanded to the 64 channels in the "

@@ -101,7 +101,14 @@ typedef struct {
                                  height from the first antenna's, still accepted as a lattice;
                                  0 = 1e-10 m (a phase error below 2 pi nu/c x 1e-10 rad) */
     int n_basis;              /* FV_TRANSFORM_BASIS: number K of spectral basis functions,
-                                 1 <= K <= min(16, n_freq); ignored by the other routes */
+                                 1 <= K <= min(16, n_freq), or 0 to choose K at fv_set_sky: the
+                                 smallest K whose basis spectra P[(P I)(P B)] of the sources above
+                                 the horizon at the first, middle and last times differ from the
+                                 exact B I by at most eps in relative L2 over all sources and
+                                 channels (the largest basis if none does; fv_info.basis_fit_error
+                                 gives the value reached; the estimate, a difference of squared
+                                 norms, resolves about 1e-8, so a smaller eps gets the largest
+                                 basis); ignored by the other routes */
 } fv_opts;
 
 /* Transform choice (Section 2.2.1).  When the antennas' horizontal positions
@@ -271,6 +278,8 @@ typedef struct {
     int beam_groups;      /* transforms per slice: unordered beam pairs among the baselines (1: one beam) */
     int basis_terms;      /* spectral-basis route: K (0 on the other routes) */
     int basis_grid[3];    /* spectral-basis route: the one spreading grid of a time, per dim */
+    double basis_fit_error;   /* automatic K: the estimated relative error of the basis spectra at
+                                 the chosen K; -1 otherwise */
 } fv_info;
 
 fv_status fv_get_info(fv_plan_t p, fv_info *info);

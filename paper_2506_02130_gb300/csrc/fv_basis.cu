@@ -342,6 +342,99 @@ cudaError_t launch_interp_basis(const cpx<G> *band, int u0, int n_ug, int n_u, i
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ fit of the spectra (automatic K)
+// For source n at time blockIdx.y (rotation R[9 * blockIdx.y]), above the horizon: its spectrum
+// c_q = B(nu_q) I_q with the beam pair (b1, b2), the coefficients s_hat = M^T I, b_hat = M^T B and
+// c_hat = M^T c over the Kmax columns of M, and for every K <= Kmax the squared distance of the
+// route's spectrum M_K v_K (v_K = sum_ij s_hat_i b_hat_j d^k_ij over i, j, k < K) from c, which the
+// orthonormal columns give as |v_K|^2 - 2 v_K . c_hat + |c|^2.  Warp sums go to err[K - 1] and
+// err[Kmax] (the total |c|^2).  The first K columns of the Kmax basis are the K basis (Gram-Schmidt
+// keeps earlier columns), so d_K is the leading block of d_Kmax.
+__global__ void __launch_bounds__(128) k_basis_fit(const double *__restrict__ e, long n_src, const double *__restrict__ R,
+                                                   const void *__restrict__ flux, int flux_fp64, int n_freq,
+                                                   const double *__restrict__ freq, const double *__restrict__ M,
+                                                   const double *__restrict__ dK, int Kmax, BeamParams b1,
+                                                   BeamParams b2, int two_beams, double *__restrict__ err)
+{
+    const long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    const double *Rt = R + 9 * blockIdx.y;
+    double sh[kBasisMax], bh[kBasisMax], ch[kBasisMax];
+#pragma unroll
+    for (int k = 0; k < kBasisMax; ++k) sh[k] = bh[k] = ch[k] = 0.0;
+    double cc = 0.0;
+    bool up = false;
+    if (n < n_src) {
+        const double ex = e[n], ey = e[n_src + n], ez = e[2 * n_src + n];
+        const double s0 = Rt[0] * ex + Rt[1] * ey + Rt[2] * ez;
+        const double s1 = Rt[3] * ex + Rt[4] * ey + Rt[5] * ez;
+        const double s2 = Rt[6] * ex + Rt[7] * ey + Rt[8] * ez;
+        up = s2 > 0.0;
+        if (up) {
+            const double rho = sqrt(s0 * s0 + s1 * s1);
+            for (int q = 0; q < n_freq; ++q) {
+                const double nu = freq[q];
+                const double A = beam_voltage<double>(b1, s0, s1, rho, s2, nu, q);
+                const double B = two_beams ? A * beam_voltage<double>(b2, s0, s1, rho, s2, nu, q) : A * A;
+                const size_t idx = (size_t)n * n_freq + q;
+                const double I = flux_fp64 ? ((const double *)flux)[idx] : (double)((const float *)flux)[idx];
+                const double c = B * I;
+                cc += c * c;
+#pragma unroll
+                for (int k = 0; k < kBasisMax; ++k)
+                    if (k < Kmax) {
+                        const double m = M[q * Kmax + k];
+                        sh[k] += m * I;
+                        bh[k] += m * B;
+                        ch[k] += m * c;
+                    }
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31;
+    for (int K = 1; K <= Kmax; ++K) {
+        double e2 = 0.0;
+        if (up) {
+            double v[kBasisMax];
+#pragma unroll
+            for (int k = 0; k < kBasisMax; ++k) v[k] = 0.0;
+            for (int a = 0; a < K; ++a)
+#pragma unroll
+                for (int j = 0; j < kBasisMax; ++j)
+                    if (j < K) {
+                        const double c = sh[a] * bh[j];
+#pragma unroll
+                        for (int k = 0; k < kBasisMax; ++k)
+                            if (k < K) v[k] += c * dK[((size_t)a * Kmax + j) * Kmax + k];
+                    }
+            double vv = 0.0, vc = 0.0;
+#pragma unroll
+            for (int k = 0; k < kBasisMax; ++k)
+                if (k < K) {
+                    vv += v[k] * v[k];
+                    vc += v[k] * ch[k];
+                }
+            e2 = vv - 2.0 * vc + cc;
+        }
+        for (int o = 16; o > 0; o >>= 1) e2 += __shfl_down_sync(0xffffffffu, e2, o);
+        if (lane == 0) atomicAdd(&err[K - 1], e2);
+    }
+    for (int o = 16; o > 0; o >>= 1) cc += __shfl_down_sync(0xffffffffu, cc, o);
+    if (lane == 0) atomicAdd(&err[Kmax], cc);
+}
+
+cudaError_t launch_basis_fit(const double *e, long n_src, const double *R, int n_times, const void *flux,
+                             int flux_fp64, int n_freq, const double *freq, const double *M, const double *dK,
+                             int Kmax, const BeamParams &b1, const BeamParams &b2, int two_beams, double *err,
+                             cudaStream_t st)
+{
+    if (n_src <= 0 || n_times <= 0) return cudaSuccess;
+    if (Kmax < 1 || Kmax > kBasisMax) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((n_src + 127) / 128), (unsigned)n_times);
+    k_basis_fit<<<grid, 128, 0, st>>>(e, n_src, R, flux, flux_fp64, n_freq, freq, M, dK, Kmax, b1, b2, two_beams,
+                                      err);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ scatter of all channels of a time
 __global__ void k_scatter_basis(const cpx<double> *__restrict__ Vq, const int *__restrict__ bl2u, int n_bl, int n_u,
                                 int n_freq, int n_time, int t, char *__restrict__ vis, size_t slice_bytes,

@@ -48,6 +48,15 @@ cudaError_t launch_interp_basis(const cpx<G> *band, int u0, int n_ug, int n_u, i
                                 const int *perm, const int4 *tm, const G *tf, const cpx<G> *ts, const SliceGeom &g,
                                 const G *prez, const cpx<G> *twz, cpx<double> *Vq, cudaStream_t st);
 
+// Spectral fit for the automatic choice of K: over the sources above the horizon at each of the
+// n_times rotations R[n_times][9], err[K - 1] += |M_K v_K - B I|^2 (the route's spectrum against the
+// exact one, all channels) for K = 1..Kmax and err[Kmax] += |B I|^2, with the beam pair (b1, b2).
+// M: [n_freq][Kmax] orthonormal columns, dK: [Kmax]^3.  err must start at zero.
+cudaError_t launch_basis_fit(const double *e, long n_src, const double *R, int n_times, const void *flux,
+                             int flux_fp64, int n_freq, const double *freq, const double *M, const double *dK,
+                             int Kmax, const BeamParams &b1, const BeamParams &b2, int two_beams, double *err,
+                             cudaStream_t st);
+
 // Output slices (q, t) of every channel: vis + (q * n_time + t) * slice_bytes holds, for baseline bl,
 // Vq[q * n_u + bl2u[bl]] (complex64 or complex128).
 cudaError_t launch_scatter_basis(const cpx<double> *Vq, const int *bl2u, int n_bl, int n_u, int n_freq, int n_time,

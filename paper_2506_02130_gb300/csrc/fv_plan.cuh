@@ -124,7 +124,9 @@ struct fv_plan_s {
     cpx<double> *d_lat_wq = nullptr;  // [n_freq][n_bl][K] height-term weights (K > 1 only)
 
     // spectral-basis route (Appendix A): one transform per basis function and time
-    int n_basis = 0;                  // fv_opts.n_basis (K)
+    int n_basis = 0;                  // K in use
+    int n_basis_req = 0;              // fv_opts.n_basis (0: chosen from the sky at fv_set_sky)
+    double basis_fit_err = 0.0;       // estimated relative error of the basis spectra (automatic K)
     bool use_basis = false;
     int basis_np = 1;                 // strength vectors per spreading launch (4 or 1)
     int basis_Kp = 0;                 // K rounded up to a multiple of basis_np (padded planes are zero)

@@ -723,8 +723,81 @@ template fv_status run_slices<double>(fv_plan_s *, fv_plan_s::Workspace &, cudaS
 // The spectral-basis route (Appendix A): the basis and its structure constants, one grid per time
 // sized for the targets of every channel (Eq. A5), its FFT tables, the deconvolution of every
 // (baseline, channel) target and the workspace.
+// Automatic K (n_basis = 0): the smallest K whose spectra P[(P I)(P B)] of the sources above the
+// horizon at the first, middle and last times differ from the exact B I by at most eps in relative L2
+// over all sources and channels (measured on the device with the largest basis the channels allow);
+// K = that largest basis if none does.
+static fv_status choose_basis_terms(fv_plan_s *p)
+{
+    const int nf = (int)p->freq.size(), nt = (int)p->lst.size();
+    std::vector<double> M;
+    int Kmax = std::min(kBasisMax, nf);
+    while (Kmax > 1 && !basis_matrix(p->freq, Kmax, M)) --Kmax;
+    if (Kmax <= 1 || p->n_src == 0 || !p->any_visible) {
+        p->n_basis = 1;
+        p->basis_fit_err = 0.0;
+        return FV_OK;
+    }
+    std::vector<double> dK((size_t)Kmax * Kmax * Kmax, 0.0);
+    for (int i = 0; i < Kmax; ++i)
+        for (int j = 0; j < Kmax; ++j)
+            for (int k = 0; k < Kmax; ++k) {
+                double acc = 0.0;
+                for (int q = 0; q < nf; ++q)
+                    acc += M[(size_t)q * Kmax + i] * M[(size_t)q * Kmax + j] * M[(size_t)q * Kmax + k];
+                dK[((size_t)i * Kmax + j) * Kmax + k] = acc;
+            }
+    std::vector<int> ts = {0, nt / 2, nt - 1};
+    ts.erase(std::unique(ts.begin(), ts.end()), ts.end());
+    std::vector<double> R;
+    for (int t : ts) R.insert(R.end(), p->Rt.begin() + (size_t)t * 9, p->Rt.begin() + (size_t)t * 9 + 9);
+    BeamParams b1 = p->beam, b2 = p->beam;
+    int two = 0;
+    if (!p->beams.empty() && !p->groups.empty()) {
+        b1 = p->beams[p->groups[0].a];
+        b2 = p->beams[p->groups[0].b];
+        two = p->groups[0].a != p->groups[0].b;
+    }
+    double *d = nullptr;
+    const size_t nM = M.size(), nD = dK.size(), nR = R.size();
+    CK(cudaMalloc(&d, (nM + nD + nR + nf + Kmax + 1) * sizeof(double)));
+    double *dM = d, *dD = dM + nM, *dR = dD + nD, *dF = dR + nR, *dErr = dF + nf;
+    cudaError_t e = cudaMemcpyAsync(dM, M.data(), nM * sizeof(double), cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dD, dK.data(), nD * sizeof(double), cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dR, R.data(), nR * sizeof(double), cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dF, p->freq.data(), nf * sizeof(double), cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dErr, 0, (Kmax + 1) * sizeof(double), p->stream);
+    if (e == cudaSuccess)
+        e = launch_basis_fit(p->d_e, p->n_src, dR, (int)ts.size(), p->flux, p->flux_fp64, nf, dF, dM, dD, Kmax, b1,
+                             b2, two, dErr, p->stream);
+    std::vector<double> err(Kmax + 1, 0.0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(err.data(), dErr, (Kmax + 1) * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return p->fail(FV_ERR_CUDA, cudaGetErrorString(e));
+    const double total = err[Kmax];
+    int K = Kmax;
+    double r = 0.0;
+    for (int k = 1; k <= Kmax; ++k) {
+        const double rk = total > 0.0 ? std::sqrt(std::max(err[k - 1], 0.0) / total) : 0.0;
+        r = rk;
+        if (rk <= p->eps) {
+            K = k;
+            break;
+        }
+    }
+    p->n_basis = K;
+    p->basis_fit_err = r;
+    return FV_OK;
+}
+
 static fv_status prepare_basis(fv_plan_s *p)
 {
+    if (p->n_basis_req == 0) {
+        const fv_status ks = choose_basis_terms(p);
+        if (ks != FV_OK) return ks;
+    }
     const int nf = (int)p->freq.size(), K = p->n_basis, w = p->w;
     const size_t gs = p->precision == FV_FP64 ? sizeof(double) : sizeof(float);
     const size_t es = p->elem();
@@ -1066,8 +1139,8 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
     if (o->fft_max_radix != 0 && o->fft_max_radix != 8 && o->fft_max_radix != 16) return bad("fft_max_radix must be 0, 8 or 16");
     if (o->transform < FV_TRANSFORM_AUTO || o->transform > FV_TRANSFORM_BASIS) return bad("unknown transform");
     if (o->transform == FV_TRANSFORM_BASIS) {
-        if (o->n_basis < 1 || o->n_basis > kBasisMax || o->n_basis > o->n_freq)
-            return bad("the spectral-basis route needs 1 <= n_basis <= min(16, n_freq)");
+        if (o->n_basis < 0 || o->n_basis > kBasisMax || o->n_basis > o->n_freq)
+            return bad("the spectral-basis route needs 0 <= n_basis <= min(16, n_freq)");
         if (o->polarized) {
             g_create_error = "the spectral-basis route is defined for unpolarised skies (Appendix A)";
             return FV_ERR_UNSUPPORTED;
@@ -1151,7 +1224,8 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
     p->fft_max_radix = o->fft_max_radix > 0 ? o->fft_max_radix : (o->precision == FV_MIXED ? 8 : 16);
     p->transform_req = o->transform;
     p->use_basis = o->transform == FV_TRANSFORM_BASIS;
-    p->n_basis = p->use_basis ? o->n_basis : 0;
+    p->n_basis_req = p->use_basis ? o->n_basis : 0;
+    p->n_basis = p->n_basis_req;
     p->lat_tol = o->lattice_tol_m > 0.0 ? o->lattice_tol_m : 1e-10;
     p->sub.assign(p->n_streams, nullptr);
     p->ev_join.assign(p->n_streams, nullptr);
@@ -1660,6 +1734,7 @@ fv_status fv_get_info(fv_plan_t p, fv_info *info)
     info->workspace_bytes = p->ws_bytes;
     info->transform = p->use_basis ? FV_TRANSFORM_BASIS : (p->use_lattice ? FV_TRANSFORM_LATTICE : FV_TRANSFORM_TYPE3);
     info->basis_terms = p->use_basis ? p->n_basis : 0;
+    info->basis_fit_error = p->use_basis && p->n_basis_req == 0 ? p->basis_fit_err : -1.0;
     for (int i = 0; i < 3; ++i) info->basis_grid[i] = p->use_basis ? p->bg.dim[i].nf1 : 0;
     info->lattice = p->lat_ok ? 1 : 0;
     for (int k = 0; k < 2; ++k) {

@@ -56,7 +56,8 @@ class fv_info(C.Structure):
                 ("src_halfwidth", C.c_double * 3), ("workspace_bytes", C.c_longlong),
                 ("transform", C.c_int), ("lattice", C.c_int), ("lattice_modes", C.c_int * 2),
                 ("lattice_grid", C.c_int * 2), ("lattice_terms", C.c_int), ("lattice_basis", C.c_double * 4),
-                ("beam_groups", C.c_int), ("basis_terms", C.c_int), ("basis_grid", C.c_int * 3)]
+                ("beam_groups", C.c_int), ("basis_terms", C.c_int), ("basis_grid", C.c_int * 3),
+                ("basis_fit_error", C.c_double)]
 
 
 PROFILE_CLASSES = 12
@@ -213,7 +214,7 @@ def fv_get_info(plan) -> dict:
             "lattice_modes": list(i.lattice_modes), "lattice_grid": list(i.lattice_grid),
             "lattice_terms": i.lattice_terms, "beam_groups": i.beam_groups,
             "lattice_basis": list(i.lattice_basis), "basis_terms": i.basis_terms,
-            "basis_grid": list(i.basis_grid)}
+            "basis_grid": list(i.basis_grid), "basis_fit_error": i.basis_fit_error}
 
 
 def fv_profile_enable(plan, enable: bool = True) -> None:

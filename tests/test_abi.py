@@ -58,7 +58,8 @@ def _opts(**kw):
 @pytest.mark.parametrize("kw", [dict(eps=0.0), dict(eps=1e-15), dict(precision=1, eps=1e-9), dict(precision=7),
                                 dict(n_freq=0), dict(beam=9), dict(dims=4), dict(upsampfac=1.1),
                                 dict(kernel_width=40), dict(latitude_rad=2.0),
-                                dict(precision=1, eps=1e-6, upsampfac=1.25), dict(transform=3),
+                                dict(precision=1, eps=1e-6, upsampfac=1.25), dict(transform=4),
+                                dict(transform=3, n_basis=-1), dict(transform=3, n_basis=2),
                                 dict(lattice_tol_m=-1.0)])
 def test_invalid_options_rejected_before_device(lib, kw):
     o, keep = _opts(**kw)

@@ -95,7 +95,7 @@ def test_flux_rewritten_in_place_between_executions():
 
 def test_errors():
     prob = _problem(seed=86, n_chan=4, n_time=1, n_point=50, nside=0)
-    for K in (5, 0):
+    for K in (5, -1):
         with pytest.raises(fv.FvError) as e:
             fv.Plan.create(prob.freqs_hz, prob.lsts_rad, prob.latitude_rad, transform="basis", n_basis=K)
         assert e.value.status == fv.FV_ERR_ARG
@@ -145,3 +145,26 @@ def test_single_channel_single_basis_function_is_the_direct_sum(precision):
     out, info = _run(prob, precision, 1)
     assert info["basis_terms"] == 1
     assert rel_l2(out, oracle_vis(OracleProblem.from_workload(prob), "literal")) <= TOL[precision]
+
+
+def test_automatic_K_is_the_degree_of_a_polynomial_sky():
+    prob = _problem(seed=89, n_chan=9, n_time=2, n_point=300, nside=0)
+    prob.beam, prob.beam_param = "uniform", ()
+    x = (prob.freqs_hz - 150e6) / 50e6
+    a = np.random.default_rng(3).uniform(0.5, 2.0, size=(prob.sky.n_src, 3))
+    prob.sky.flux = (a[:, :1] + a[:, 1:2] * x[None] - 0.3 * a[:, 2:3] * x[None] ** 2)[None]
+    out, info = _run(prob, fv.FV_MIXED, 0)
+    assert info["basis_terms"] == 3
+    assert info["basis_fit_error"] < 1e-7          # the squared-norm estimate resolves about 1e-8
+    assert rel_l2(out, oracle_vis(OracleProblem.from_workload(prob), "literal")) <= TOL[fv.FV_MIXED]
+
+
+def test_automatic_K_meets_eps_on_a_power_law_sky_through_the_beam():
+    prob = _problem(seed=90, n_chan=16, n_time=2, n_point=800, nside=4, fwhm_deg=20.0)
+    out, info = _run(prob, fv.FV_MIXED, 0)
+    assert 1 < info["basis_terms"] <= 16
+    assert 0.0 <= info["basis_fit_error"] <= EPS[fv.FV_MIXED]
+    assert rel_l2(out, oracle_vis(OracleProblem.from_workload(prob), "literal")) <= TOL[fv.FV_MIXED]
+    # an explicit K reports no fit
+    _, info = _run(prob, fv.FV_MIXED, 4)
+    assert info["basis_fit_error"] == -1.0
