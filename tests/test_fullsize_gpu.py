@@ -39,8 +39,10 @@ def _run_on_stream(prob, precision, eps, flux_dtype, **plan_kw):
                                                      (fv.FV_FP64, 1e-11, 1e-9, {"transform": "type3"}),
                                                      (fv.FV_MIXED, 1e-6, 2e-5, {"transform": "lattice"}),
                                                      (fv.FV_MIXED, 1e-6, 2e-5, {"transform": "basis", "n_basis": 12}),
+                                                     (fv.FV_MIXED, 1e-6, 2e-5, {"transform": "basis", "n_basis": 0}),
                                                      (fv.FV_FP64, 1e-11, 1e-9, {"transform": "basis", "n_basis": 16})],
-                         ids=["type3-mixed", "type3-fp64", "lattice-mixed", "basis12-mixed", "basis16-fp64"])
+                         ids=["type3-mixed", "type3-fp64", "lattice-mixed", "basis12-mixed", "basisauto-mixed",
+                              "basis16-fp64"])
 def test_hex127_full_size_sampled_slices(precision, eps, tol, route):
     torch = pytest.importorskip("torch")
     prob = W.config_hex127(seed=1)
