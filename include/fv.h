@@ -145,7 +145,9 @@ typedef struct {
  * source's spectrum B I replaced by P[(P I)(P B)], P = M M^T: exact when flux
  * and beam are polynomials of degree < K in frequency and for any sky at
  * K = n_freq; otherwise that truncation error adds to eps and is set by the
- * caller's choice of K.  Unpolarised plans only (fv_plan returns
+ * caller's choice of K (or by the plan's, n_basis = 0).  The flux coefficients
+ * are recomputed by every fv_execute (a borrowed device flux may change between
+ * executions); an automatic K is chosen once, at fv_set_sky.  Unpolarised plans only (fv_plan returns
  * FV_ERR_UNSUPPORTED for a polarised one).  Executed by fv_execute;
  * fv_batch_add and fv_execute_static return FV_ERR_UNSUPPORTED for such a
  * plan. */
