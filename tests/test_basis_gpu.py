@@ -168,3 +168,11 @@ def test_automatic_K_meets_eps_on_a_power_law_sky_through_the_beam():
     # an explicit K reports no fit
     _, info = _run(prob, fv.FV_MIXED, 4)
     assert info["basis_fit_error"] == -1.0
+
+
+def test_sixteen_basis_functions_over_32_channels():
+    # the largest basis: K * Nz = 128 values per cell, four loads per footprint tap
+    prob = _problem(seed=91, n_chan=32, n_time=1, n_point=400, nside=2)
+    out, info = _run(prob, fv.FV_MIXED, 16)
+    assert info["basis_terms"] == 16
+    assert rel_l2(out, basis_vis(OracleProblem.from_workload(prob), 16)) <= TOL[fv.FV_MIXED]
