@@ -46,10 +46,13 @@ def parse():
     ap.add_argument("--spread", default="auto", choices=["auto", "gather", "scatter", "atomic"])
     ap.add_argument("--fft-radix", type=int, default=0, choices=[0, 8, 16],
                     help="largest FFT stage radix of the timed plan (0: the library default)")
+    ap.add_argument("--fp64-eps", type=float, default=1e-6,
+                    help="tolerance of the plain FP64 comparison leg (its error is reported beside the mixed path's)")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip timing the plain FP64 path (one slice after another) beside the mixed path")
-    ap.add_argument("--workload", default="hex127", choices=["hex127", "batch", "serve"],
-                    help="hex127: the 127-antenna, 64-channel, 10-time simulation (default); batch: 2,048 ragged "
+    ap.add_argument("--workload", default="hex350", choices=["hex350", "hex127", "batch", "serve"],
+                    help="hex350: the 350-antenna polarised simulation, 256 channels x 4 times, 886,432 sources "
+                         "(default); hex127: the 127-antenna, 64-channel, 10-time simulation; batch: 2,048 ragged "
                          "single-slice problems on shared lanes, replayed from a CUDA graph; serve: a Poisson "
                          "stream of requests over resident plans with continuous batching")
     ap.add_argument("--transform", default="type3", choices=["type3", "auto", "lattice", "basis"],
@@ -92,11 +95,6 @@ def kernel_profile(fv, prob, precision, eps, stream, device, flux_dev, args, **p
         return prof
     finally:
         p.close()
-
-
-def workload(seed):
-    from paper_2506_02130_gb300 import workloads as W
-    return W.config_hex127(seed=seed)
 
 
 def peaks():
@@ -184,67 +182,41 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample(prob, target_s, gpu_outs=None):
-    """Time the FP64 oracle (as it stands) on whole slices of the workload.
-
-    Runs one slice, then as many more as fit in ``target_s`` seconds; returns
-    vis/s, thread count, a description and, for every GPU output in the dict
-    ``gpu_outs``, its relative L2 error on those slices.
-    """
-    import numpy as np
-    from oracle.oracle import OracleProblem, oracle_vis, rel_l2, max_threads
-    nf, nt = len(prob.freqs_hz), len(prob.lsts_rad)
-    order = np.random.default_rng(123).permutation(nf * nt)
-    gpu_outs = gpu_outs or {}
-    done, t_total, refs = [], 0.0, []
-    gots = {k: [] for k in gpu_outs}
-    for k in order:
-        f, t = divmod(int(k), nt)
-        p = OracleProblem.from_workload(prob, freq_idx=[f], time_idx=[t])
-        t0 = time.perf_counter()
-        ref = oracle_vis(p, "factored")
-        t_total += time.perf_counter() - t0
-        done.append((f, t))
-        refs.append(ref[0, 0])
-        for k, v in gpu_outs.items():
-            gots[k].append(v[f, t])
-        if t_total >= target_s:
-            break
-    n_vis = len(done) * len(prob.pairs) * (4 if prob.polarized else 1)
-    err = {k: rel_l2(np.array(v), np.array(refs)) for k, v in gots.items()}
-    return {"value": n_vis / t_total, "unit": "visibilities/s", "cores": max_threads(), "kind": "oracle",
-            "sample": f"{len(done)} of {nf * nt} (time, channel) slices, all {len(prob.pairs)} baselines and "
-                      f"{prob.sky.n_src} sources, FP64 antenna-factored direct sum",
-            "seconds": t_total}, err
-
-
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 direct-sum oracle on the host cores."""
+    """Reference arm: the FP64 direct-sum oracle on the host cores, on the same workload as our arm; each
+    step is one (time, channel) slice (on the 350-antenna workload: its seeded 1% baseline subsample)."""
     if rank != 0:
         return
-    prob = workload(1)
-    n_bl = len(prob.pairs)
+    import numpy as np
     from oracle.oracle import OracleProblem, oracle_vis, max_threads
+    wl = SIM.get(args.workload, SIM["hex350"])
+    name = args.workload if args.workload in SIM else "hex350"
+    prob = sim_problem(name, 2 if name == "hex350" else 1)
+    sampler = OracleSampler(prob, wl["oracle_bl"])
+    pairs = prob.pairs if sampler.sel is None else prob.pairs[sampler.sel]
+    n_pol = 4 if prob.polarized else 1
     nf, nt = len(prob.freqs_hz), len(prob.lsts_rad)
     slices = [(k % nf, (k * 7) % nt) for k in range(args.warmup + args.steps)]
     times = []
     for i, (f, t) in enumerate(slices):
-        p = OracleProblem.from_workload(prob, freq_idx=[f], time_idx=[t])
+        p = OracleProblem.from_workload(prob, pairs=pairs, freq_idx=[f], time_idx=[t])
         t0 = time.perf_counter()
         oracle_vis(p, "factored")
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
     total = sum(times)
-    value = args.steps * n_bl / total
+    value = args.steps * len(pairs) * n_pol / total
+    sub = "" if sampler.sel is None else (f" ({len(pairs)} seeded baselines of {len(prob.pairs)}; "
+                                          "subsampled-rate: direct-sum cost is proportional to baselines)")
     line = {"metric": "visibilities/s at <=2e-5 rel err vs FP64 direct sum", "impl": "reference", "value": value,
             "unit": "visibilities/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "hex127_8001bl_64ch_10t_69152src", "step": "one (time, channel) slice, "
-                       "all baselines and sources, FP64 direct sum"},
+            "config": {"workload": wl["name"], "what": wl["what"],
+                       "step": "one (time, channel) slice, FP64 direct sum" + sub},
             "cpu_baseline": {"value": value, "unit": "visibilities/s", "cores": max_threads(), "kind": "oracle",
-                             "sample": f"{args.steps} timed slices of {nf * nt}, all {n_bl} baselines"},
+                             "sample": f"{args.steps} timed slices of {nf * nt}, {len(pairs)} baselines" + sub},
             "e2e": {"value": value, "unit": "visibilities/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -608,6 +580,343 @@ def run_serve(args, rank, world, local, dist):
         p.close()
 
 
+# The simulation workloads: name in the JSON line, generator, route extras that apply
+SIM = {
+    "hex350": {"name": "hex350_pol_61075bl_256ch_4t_886432src", "oracle_bl": 611,
+               "what": "350-antenna coplanar hexagon (61,075 cross baselines), 256 channels at 100-200 MHz x 4 "
+                       "times, 100,000 polarised power-law points + nside-256 polarised diffuse map (886,432 "
+                       "sources), 2x2 Jones Airy beam of a 14 m dish, four polarisation products"},
+    "hex127": {"name": "hex127_8001bl_64ch_10t_69152src", "oracle_bl": 0,
+               "what": "127-antenna hexagon with 5 cm height jitter (8,001 baselines, 3-D), 64 channels x 10 "
+                       "times, 20,000 points + nside-64 diffuse map (69,152 sources), Gaussian beam"},
+}
+
+
+def sim_problem(name, seed):
+    import numpy as np
+    from paper_2506_02130_gb300 import workloads as W
+    if name == "hex350":
+        return W.config_hex350_pol(seed=seed, dtype=np.float32)
+    return W.config_hex127(seed=seed)
+
+
+class OracleSampler:
+    """Relative L2 errors of several GPU outputs against the FP64 oracle on the same sampled slices
+    (and, on large arrays, a seeded subsample of baselines), plus the oracle's own rate.
+
+    Slices are taken in a seeded random order; each GPU output registers the slices it covers (copied
+    to the host before its buffers are freed), and ``run`` computes the oracle slice by slice until its
+    time budget is spent, accumulating every output's squared error per polarisation product."""
+
+    def __init__(self, prob, n_bl_sample, n_keep=48, seed=123):
+        import numpy as np
+        self.prob = prob
+        nf, nt, nb = len(prob.freqs_hz), len(prob.lsts_rad), len(prob.pairs)
+        rng = np.random.default_rng(seed)
+        self.order = [divmod(int(k), nt) for k in rng.permutation(nf * nt)[:n_keep]]
+        self.sel = np.sort(rng.choice(nb, size=n_bl_sample, replace=False)) if 0 < n_bl_sample < nb else None
+        self.got = {}
+
+    def take(self, key, out, slices=None):
+        """Copy the sampled slices of a GPU output [f][t][bl][pol] (torch tensor) to the host."""
+        import torch
+        sel = None if self.sel is None else torch.as_tensor(self.sel, device=out.device)
+        d = {}
+        for (f, t) in (slices if slices is not None else self.order):
+            v = out[f, t] if sel is None else out[f, t][sel]
+            d[(f, t)] = v.cpu().numpy()
+        self.got[key] = d
+
+    def run(self, target_s, extra=()):
+        """Oracle on the sampled slices (then on the slices of `extra`) until target_s seconds pass."""
+        import numpy as np
+        from oracle.oracle import OracleProblem, oracle_vis, max_threads
+        prob = self.prob
+        pairs = prob.pairs if self.sel is None else prob.pairs[self.sel]
+        acc = {k: [0.0, 0.0, None, None] for k in self.got}
+        t_total, n_vis, done = 0.0, 0, 0
+        todo = list(self.order) + [s for s in extra if s not in self.order]
+        n_main = len(self.order)
+        for i, (f, t) in enumerate(todo):
+            # the sampled slices while the budget lasts (at least one), then the slices `extra` asks for
+            if i < n_main and i > 0 and t_total >= target_s:
+                continue
+            op = OracleProblem.from_workload(prob, pairs=pairs, freq_idx=[f], time_idx=[t])
+            t0 = time.perf_counter()
+            ref = oracle_vis(op, "factored")[0, 0]
+            t_total += time.perf_counter() - t0
+            n_vis += ref.size
+            done += 1
+            for k, d in self.got.items():
+                if (f, t) not in d:
+                    continue
+                got = d[(f, t)].reshape(ref.shape)
+                e2 = (np.abs(got - ref) ** 2).sum(axis=0)
+                r2 = (np.abs(ref) ** 2).sum(axis=0)
+                a = acc[k]
+                a[0] += float(e2.sum()); a[1] += float(r2.sum())
+                a[2] = e2 if a[2] is None else a[2] + e2
+                a[3] = r2 if a[3] is None else a[3] + r2
+        err = {}
+        for k, (e, r, ep, rp) in acc.items():
+            if r > 0:
+                err[k] = float(np.sqrt(e / r))
+                if ep is not None and len(ep) > 1:
+                    err[k + "_per_product"] = [float(np.sqrt(x / y)) for x, y in zip(ep, rp)]
+        nb = len(pairs)
+        cpu = {"value": n_vis / t_total if t_total > 0 else None, "unit": "visibilities/s",
+               "cores": max_threads(), "kind": "oracle",
+               "sample": f"{done} (time, channel) slices of {len(prob.freqs_hz) * len(prob.lsts_rad)}, "
+                         + (f"{nb} seeded baselines of {len(prob.pairs)} (subsampled-rate: direct-sum cost is "
+                            f"proportional to baselines x slices x sources)" if self.sel is not None
+                            else f"all {nb} baselines")
+                         + f", all {prob.sky.n_src} sources, FP64 antenna-factored direct sum",
+               "seconds": t_total}
+        return cpu, err
+
+
+def timed_steps(run, stream, steps):
+    """Device time (ms) of `steps` calls of run(), bracketed by CUDA events on `stream`."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        run()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_sim(args, rank, world, local, dist):
+    """One whole simulation (every (time, channel) slice of the workload) per step."""
+    import numpy as np
+    import torch
+    from paper_2506_02130_gb300 import fv
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = SIM[args.workload]
+    precision = fv.FV_MIXED if args.precision == "mixed" else fv.FV_FP64
+    eps = 1e-6 if precision == fv.FV_MIXED else 1e-11
+    t_setup = time.perf_counter()
+    # each rank simulates its own independent problem (weak scaling)
+    prob = sim_problem(args.workload, (2 if args.workload == "hex350" else 1) + rank)
+    nf, nt = len(prob.freqs_hz), len(prob.lsts_rad)
+    sampler = OracleSampler(prob, wl["oracle_bl"])
+    # a dedicated stream: the plan runs on it and the timing events are recorded on it
+    stream = torch.cuda.Stream(device=dev)
+    plan = fv.Plan.from_problem(prob, precision=precision, eps=eps, stream=stream.cuda_stream, device=local,
+                                n_streams=args.streams, spread=args.spread, transform=args.transform,
+                                fft_max_radix=args.fft_radix,
+                                n_basis=args.basis_terms if args.transform == "basis" else 0)
+    fdt = torch.float32 if precision == fv.FV_MIXED else torch.float64
+    cdt = torch.complex64 if precision == fv.FV_MIXED else torch.complex128
+    flux_dev = torch.tensor(prob.sky.flux, dtype=fdt, device=dev)
+    plan.set_sky(prob.sky.ra, prob.sky.dec, flux_dev)
+    info = plan.info()
+    out = torch.empty(plan.out_shape, dtype=cdt, device=dev)
+    n_vis = int(np.prod(plan.out_shape))
+    setup_s = time.perf_counter() - t_setup
+
+    for _ in range(args.warmup):
+        plan.run(out)
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region: K steps, device-resident inputs and outputs, no per-launch instrumentation
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    step_ms = []
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for k in range(args.steps):
+        plan.run(out)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    ck = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms = ev[0].elapsed_time(ev[-1])
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n_vis * args.steps / (ms / 1e3)
+    sampler.take(args.precision, out)
+
+    # ---- per-kernel times: one more step with CUDA events around every launch (event records between
+    # launches would perturb the timed region above), on a one-stream copy of the plan so that no two
+    # kernels overlap and each event pair brackets one kernel alone
+    prof = kernel_profile(fv, prob, precision, eps, stream, local, flux_dev, args,
+                          transform=args.transform, n_basis=args.basis_terms if args.transform == "basis" else 0)
+
+    # ---- roofline of the dominant kernel class
+    ours = {k: v for k, v in prof.items() if k != "memset" and v["launches"] > 0}
+    dom = max(ours, key=lambda k: ours[k]["ms"]) if ours else None
+    peak, peak_kind = peaks()
+    roof = None
+    if dom:
+        d = ours[dom]
+        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        tr = ncu_traffic(dom, f"{args.workload}_{args.precision}") if args.transform == "type3" else None
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": tr, "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+                "avg_launch_ms": d["ms"] / d["launches"],
+                "share_of_kernel_time": d["ms"] / sum(v["ms"] for v in prof.values()),
+                "timing": "CUDA events around each launch, one step of a one-stream copy of the plan after the "
+                          "timed region (kernels do not overlap, so each event pair times one kernel alone)"}
+    gpu_launches = int(sum(v["launches"] for k, v in prof.items() if k != "memset")) * args.steps
+
+    # ---- end to end through the C ABI with host buffers (pinned): set_sky copies the step's inputs in,
+    # fv_execute copies the visibilities out
+    e2e = None
+    if not args.no_e2e:
+        flux_host = torch.from_numpy(np.ascontiguousarray(prob.sky.flux, dtype=np.float32 if
+                                                          precision == fv.FV_MIXED else np.float64)).pin_memory()
+        out_host = torch.empty(plan.out_shape, dtype=cdt).pin_memory()
+        ra = np.ascontiguousarray(prob.sky.ra); dec = np.ascontiguousarray(prob.sky.dec)
+        h2d = ra.nbytes + dec.nbytes + flux_host.numel() * flux_host.element_size()
+        d2h = out_host.numel() * out_host.element_size()
+        fh = flux_host.numpy()
+        plan.set_sky(ra, dec, fh)
+        plan.run(out_host.numpy())
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.set_sky(ra, dec, fh)                 # H2D of the step's inputs
+            plan.run(out_host.numpy())                # compute + D2H of the result
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([e2e_s], dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * n_vis * args.steps / e2e_s, "unit": "visibilities/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": 1e3 * e2e_s / args.steps}
+        del flux_host, out_host
+    plan.close()
+    plan = None
+    del out
+
+    def route_leg(key, **kw):
+        p = fv.Plan.from_problem(prob, precision=precision, eps=eps, stream=stream.cuda_stream, device=local,
+                                 n_streams=args.streams, **kw)
+        p.set_sky(prob.sky.ra, prob.sky.dec, flux_dev)
+        o = torch.empty(p.out_shape, dtype=cdt, device=dev)
+        for _ in range(args.warmup):
+            p.run(o)
+        torch.cuda.synchronize(dev)
+        msr = timed_steps(lambda: p.run(o), stream, args.steps)
+        sampler.take(key, o)
+        li = p.info()
+        p.close()
+        del o
+        return {"value": world * n_vis * args.steps / (msr / 1e3), "unit": "visibilities/s",
+                "ms_per_step": msr / args.steps}, li
+
+    # ---- the lattice route on the same workload (Section 2.2.1; heights, if any, by Chebyshev terms)
+    lat_route = None
+    if args.transform == "type3" and not args.no_lattice_route:
+        lat_route, li = route_leg("lattice_route", transform="lattice")
+        lat_route.update({"lattice_terms": li["lattice_terms"], "lattice_modes": li["lattice_modes"],
+                          "lattice_grid": li["lattice_grid"],
+                          "what": "same workload, plan with transform=lattice (type-1 transforms on the "
+                                  "horizontal lattice, heights by Chebyshev terms)"})
+
+    # ---- the spectral-basis route (Appendix A; scalar skies only)
+    bas_route = None
+    if args.transform == "type3" and not args.no_basis_route and not prob.polarized:
+        bas_route, bi = route_leg("basis_route", transform="basis", n_basis=args.basis_terms)
+        bprof = kernel_profile(fv, prob, precision, eps, stream, local, flux_dev, args, transform="basis",
+                               n_basis=args.basis_terms)
+        bas_route.update({"basis_terms": bi["basis_terms"], "basis_terms_chosen_by_plan": args.basis_terms == 0,
+                          "basis_fit_error": bi["basis_fit_error"], "grid": bi["basis_grid"],
+                          "kernels_ms_per_step": {k: v["ms"] for k, v in bprof.items() if v["launches"] > 0},
+                          "what": "same workload, plan with transform=basis: per time one transform per basis "
+                                  "function of the band (Appendix A), expanded to the channels in the "
+                                  "interpolation"})
+
+    # ---- the plain FP64 path at equal accuracy: one slice after another on one stream (no batching, no
+    # concurrent slices), at the tolerance whose error matches the mixed path's; on the 350-antenna
+    # workload a seeded subset of channels (all times) keeps the leg short
+    fp64 = None
+    extra_slices = []
+    if precision == fv.FV_MIXED and not args.no_fp64_compare:
+        del flux_dev
+        torch.cuda.empty_cache()
+        ch = list(range(0, nf, 16)) if nf > 64 else list(range(nf))
+        sub_flux = np.ascontiguousarray(prob.sky.flux[:, :, ch], dtype=np.float64)
+        p64 = fv.Plan.create(prob.freqs_hz[ch], prob.lsts_rad, prob.latitude_rad, prob.beam, prob.beam_param,
+                             fv.FV_FP64, args.fp64_eps, prob.polarized, stream=stream.cuda_stream, device=local,
+                             n_streams=1, transform="type3")
+        p64.set_array(prob.ant_enu, prob.pairs)
+        f64dev = torch.from_numpy(sub_flux).to(dev)
+        p64.set_sky(prob.sky.ra, prob.sky.dec, f64dev)
+        o64 = torch.empty(p64.out_shape, dtype=torch.complex128, device=dev)
+        p64.run(o64)
+        torch.cuda.synchronize(dev)
+        ms64 = timed_steps(lambda: p64.run(o64), stream, 3)
+        n64 = int(np.prod(p64.out_shape))
+        # sampled slices of the subset, mapped back to the workload's channel index
+        rng = np.random.default_rng(321)
+        picks = [(int(a), int(b)) for a, b in zip(rng.choice(len(ch), 2), rng.choice(nt, 2))]
+        sel = None if sampler.sel is None else torch.as_tensor(sampler.sel, device=dev)
+        sampler.got["fp64_plain"] = {(ch[a], b): (o64[a, b] if sel is None else o64[a, b][sel]).cpu().numpy()
+                                     for a, b in picks}
+        extra_slices = [(ch[a], b) for a, b in picks]
+        fp64 = {"value": world * n64 * 3 / (ms64 / 1e3), "unit": "visibilities/s", "ms_per_step": ms64 / 3,
+                "eps": args.fp64_eps, "steps": 3, "warmup": 1, "streams": 1, "channels": len(ch),
+                "visibilities_per_step": n64, "kernel_width": p64.info()["kernel_width"],
+                "what": "plain FP64 type-3 path, one slice after another on one stream, at the tolerance whose "
+                        "error against the direct sum matches the mixed path's (error in "
+                        "rel_l2_vs_oracle_sample.fp64_plain)"
+                        + (f"; channels {ch[0]}, {ch[1]}, ... (every 16th) of the {nf}, all times"
+                           if len(ch) < nf else "")}
+        p64.close()
+        del o64, f64dev
+
+    # ---- CPU baseline (oracle) on a bounded sample, rank 0 at N=1; reports the GPU errors on it too
+    cpu, err = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, err = sampler.run(args.cpu_seconds, extra_slices)
+
+    lat = sorted(step_ms)
+    line = {"metric": "visibilities/s at <=2e-5 rel err vs FP64 direct sum", "value": value,
+            "unit": "visibilities/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32/f64" if precision == fv.FV_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "what": wl["what"], "n_ant": int(len(prob.ant_enu)),
+                       "n_bl": info["n_bl"], "n_unique_targets": info["n_unique"], "n_freq": nf, "n_time": nt,
+                       "n_pol": 4 if prob.polarized else 1,
+                       "n_src": int(prob.sky.n_src), "dims": info["dims"], "precision": args.precision,
+                       "eps": eps, "kernel_width": info["kernel_width"], "upsampfac": info["upsampfac"],
+                       "nf1_max": info["nf1_max"], "nf2_max": info["nf2_max"],
+                       "streams": args.streams or (4 if args.transform == "basis" else 8),
+                       "spread": args.spread, "transform": args.transform, "vis_per_step": n_vis,
+                       "setup_seconds": setup_s,
+                       "l2": "inputs larger than L2: a step streams every slice's grid through the reused "
+                             f"workspaces (~{info['workspace_bytes'] / 1e6:.0f} MB) and reads "
+                             f"{prob.sky.flux.size * (4 if precision == fv.FV_MIXED else 8) / 1e9:.2f} GB of "
+                             "fluxes",
+                       "parallelism": f"{world} independent problems (one per GPU)"},
+            "step_latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                                "min": lat[0], "max": lat[-1]},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": gpu_launches,
+            "rel_l2_vs_oracle_sample": err, "fp64_plain_equal_accuracy": fp64, "lattice_route": lat_route,
+            "basis_route": bas_route,
+            "kernels": {k: {"ms_per_step": v["ms"], "launches_per_step": v["launches"],
+                            "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}
+                        for k, v in prof.items() if v["launches"] > 0}}
+    return line
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -627,225 +936,9 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
-
-    import numpy as np
-    import torch
-    from paper_2506_02130_gb300 import fv
-    if not torch.cuda.is_available():
-        raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    precision = fv.FV_MIXED if args.precision == "mixed" else fv.FV_FP64
-    eps = 1e-6 if precision == fv.FV_MIXED else 1e-11
-    prob = workload(1 + rank)             # each rank simulates its own independent problem (weak scaling)
-    # a dedicated stream: the plan runs on it and the timing events are recorded on it
-    stream = torch.cuda.Stream(device=dev)
-    plan = fv.Plan.from_problem(prob, precision=precision, eps=eps, stream=stream.cuda_stream, device=local,
-                                n_streams=args.streams, spread=args.spread, transform=args.transform,
-                                fft_max_radix=args.fft_radix,
-                                n_basis=args.basis_terms if args.transform == "basis" else 0)
-    fdt = torch.float32 if precision == fv.FV_MIXED else torch.float64
-    cdt = torch.complex64 if precision == fv.FV_MIXED else torch.complex128
-    flux_dev = torch.tensor(prob.sky.flux, dtype=fdt, device=dev)
-    plan.set_sky(prob.sky.ra, prob.sky.dec, flux_dev)
-    info = plan.info()
-    out = torch.empty(plan.out_shape, dtype=cdt, device=dev)
-    n_vis = int(np.prod(plan.out_shape))
-
-    for _ in range(args.warmup):
-        plan.run(out)
-    torch.cuda.synchronize(dev)
-
-    # ---- timed region: K steps, device-resident inputs and outputs, no per-launch instrumentation
-    clocks = Clocks(local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    clocks.start()
-    time.sleep(0.3)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        plan.run(out)
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    ck = clocks.stop()
-    if dist:
-        dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n_vis * args.steps / (ms / 1e3)
-
-    # ---- per-kernel times: one more step with CUDA events around every launch (event records between
-    # launches would perturb the timed region above), on a one-stream copy of the plan so that no two
-    # kernels overlap and each event pair brackets one kernel alone
-    prof = kernel_profile(fv, prob, precision, eps, stream, local, flux_dev, args,
-                          transform=args.transform, n_basis=args.basis_terms if args.transform == "basis" else 0)
-    prof_steps = 1
-
-    # ---- roofline of the dominant kernel class
-    ours = {k: v for k, v in prof.items() if k != "memset" and v["launches"] > 0}
-    dom = max(ours, key=lambda k: ours[k]["ms"]) if ours else None
-    peak, peak_kind = peaks()
-    roof = None
-    if dom:
-        d = ours[dom]
-        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        tr = ncu_traffic(dom, args.precision) if args.transform == "type3" else None
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": tr, "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
-                "avg_launch_ms": d["ms"] / d["launches"],
-                "share_of_kernel_time": d["ms"] / sum(v["ms"] for v in prof.values()),
-                "timing": "CUDA events around each launch, one step of a one-stream copy of the plan after the "
-                          "timed region (kernels do not overlap, so each event pair times one kernel alone)",
-                "reading": "a slice's grid and band stay in the 129 MB L2 between its kernels, so DRAM sees far "
-                           "less than the algorithmic bytes (traffic); the per-slice kernels are bound by "
-                           "instruction issue and latency, not HBM (ncu summaries under profiles/)"}
-    gpu_launches = int(sum(v["launches"] for k, v in prof.items() if k != "memset")) * args.steps // prof_steps
-
-    # ---- end to end through the C ABI with host buffers (pinned)
-    e2e = None
-    if not args.no_e2e:
-        flux_host = torch.tensor(prob.sky.flux, dtype=fdt).pin_memory()
-        out_host = torch.empty(plan.out_shape, dtype=cdt).pin_memory()
-        ra = np.ascontiguousarray(prob.sky.ra); dec = np.ascontiguousarray(prob.sky.dec)
-        h2d = ra.nbytes + dec.nbytes + flux_host.numel() * flux_host.element_size()
-        d2h = out_host.numel() * out_host.element_size()
-        fh = flux_host.numpy()
-        for _ in range(1):
-            plan.set_sky(ra, dec, fh)
-            plan.run(out_host.numpy())
-        if dist:
-            dist.barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            plan.set_sky(ra, dec, fh)                 # H2D of the step's inputs
-            plan.run(out_host.numpy())                # compute + D2H of the result
-        e2e_s = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e2e_s], dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * n_vis * args.steps / e2e_s, "unit": "visibilities/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": 1e3 * e2e_s / args.steps}
-
-    outs = {args.precision: out.cpu().numpy()}
-
-    # ---- the lattice route on the same workload: the hexagon's horizontal lattice (Section 2.2.1) with
-    # the 5 cm heights expanded in Chebyshev terms; same precision and eps, timed the same way
-    lat_route = None
-    if args.transform == "type3" and not args.no_lattice_route:
-        pl = fv.Plan.from_problem(prob, precision=precision, eps=eps, stream=stream.cuda_stream, device=local,
-                                  n_streams=args.streams, transform="lattice")
-        pl.set_sky(prob.sky.ra, prob.sky.dec, flux_dev)
-        ol = torch.empty(pl.out_shape, dtype=cdt, device=dev)
-        for _ in range(args.warmup):
-            pl.run(ol)
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            pl.run(ol)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        msl = e0.elapsed_time(e1)
-        li = pl.info()
-        lat_route = {"value": world * n_vis * args.steps / (msl / 1e3), "unit": "visibilities/s",
-                     "ms_per_step": msl / args.steps, "lattice_terms": li["lattice_terms"],
-                     "lattice_modes": li["lattice_modes"], "lattice_grid": li["lattice_grid"],
-                     "what": "same workload, plan with transform=lattice (type-1 transforms on the horizontal "
-                             "lattice, heights by Chebyshev terms)"}
-        outs["lattice_route"] = ol.cpu().numpy()
-        pl.close()
-
-    # ---- the spectral-basis route (Appendix A) on the same workload: one transform per basis function
-    # and time on a grid sized for the whole band; same precision and eps, timed the same way
-    bas_route = None
-    if args.transform == "type3" and not args.no_basis_route:
-        pb = fv.Plan.from_problem(prob, precision=precision, eps=eps, stream=stream.cuda_stream, device=local,
-                                  n_streams=args.streams, transform="basis", n_basis=args.basis_terms)
-        pb.set_sky(prob.sky.ra, prob.sky.dec, flux_dev)
-        ob = torch.empty(pb.out_shape, dtype=cdt, device=dev)
-        for _ in range(args.warmup):
-            pb.run(ob)
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            pb.run(ob)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        msb = e0.elapsed_time(e1)
-        bprof = kernel_profile(fv, prob, precision, eps, stream, local, flux_dev, args, transform="basis",
-                               n_basis=args.basis_terms)
-        bi = pb.info()
-        bas_route = {"value": world * n_vis * args.steps / (msb / 1e3), "unit": "visibilities/s",
-                     "ms_per_step": msb / args.steps, "basis_terms": bi["basis_terms"],
-                     "basis_terms_chosen_by_plan": args.basis_terms == 0, "basis_fit_error": bi["basis_fit_error"],
-                     "grid": bi["basis_grid"],
-                     "kernels_ms_per_step": {k: v["ms"] for k, v in bprof.items() if v["launches"] > 0},
-                     "what": "same workload, plan with transform=basis: per time one transform per basis "
-                             "function of the band (Appendix A), expanded to the 64 channels in the "
-                             "interpolation; its error against the direct sum is in rel_l2_vs_oracle_sample"}
-        outs["basis_route"] = ob.cpu().numpy()
-        pb.close()
-
-    # ---- the plain FP64 path (one slice after another, no batching) on the same workload
-    fp64 = None
-    if precision == fv.FV_MIXED and not args.no_fp64_compare:
-        plan.close()
-        p64 = fv.Plan.from_problem(prob, precision=fv.FV_FP64, eps=1e-11, stream=stream.cuda_stream, device=local,
-                                   transform="type3")
-        p64.set_sky(prob.sky.ra, prob.sky.dec, torch.tensor(prob.sky.flux, dtype=torch.float64, device=dev))
-        o64 = torch.empty(p64.out_shape, dtype=torch.complex128, device=dev)
-        p64.run(o64)
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        p64.run(o64)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms64 = e0.elapsed_time(e1)
-        fp64 = {"value": world * n_vis / (ms64 / 1e3), "unit": "visibilities/s", "ms_per_step": ms64,
-                "eps": 1e-11, "steps": 1, "warmup": 1, "info": p64.info()}
-        outs["fp64"] = o64.cpu().numpy()
-        p64.close()
-        plan = None
-
-    # ---- CPU baseline (oracle) on a bounded sample, rank 0 at N=1; reports the GPU errors on it too
-    cpu, err = None, None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, err = oracle_sample(prob, args.cpu_seconds, outs)
-
-    line = {"metric": "visibilities/s at <=2e-5 rel err vs FP64 direct sum", "value": value,
-            "unit": "visibilities/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32/f64" if precision == fv.FV_MIXED else "f64", "data": "synthetic",
-            "config": {"workload": "hex127_8001bl_64ch_10t_69152src", "n_ant": 127, "n_bl": info["n_bl"],
-                       "n_unique_targets": info["n_unique"], "n_freq": 64, "n_time": 10,
-                       "n_src": int(prob.sky.n_src), "dims": info["dims"], "precision": args.precision,
-                       "eps": eps, "kernel_width": info["kernel_width"], "upsampfac": info["upsampfac"],
-                       "nf1_max": info["nf1_max"], "nf2_max": info["nf2_max"], "streams": args.streams or (4 if args.transform == "basis" else 8),
-                       "spread": args.spread, "transform": args.transform,
-                       "vis_per_step": n_vis,
-                       "l2": "inputs larger than L2: a step streams the 640 slices' grids "
-                             f"(~{info['workspace_bytes'] / 1e6:.0f} MB workspace reused per slice)",
-                       "parallelism": f"{world} independent problems (one per GPU)"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": gpu_launches,
-            "rel_l2_vs_oracle_sample": err, "fp64_plain": fp64, "lattice_route": lat_route,
-            "basis_route": bas_route,
-            "kernels": {k: {"ms_per_step": v["ms"] / prof_steps, "launches_per_step": v["launches"] / prof_steps,
-                            "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}
-                        for k, v in prof.items() if v["launches"] > 0}}
+    line = run_sim(args, rank, world, local, dist)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if plan is not None:
-        plan.close()
     if dist:
         dist.destroy_process_group()
 

@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define FV_ABI_VERSION 3
+#define FV_ABI_VERSION 4
 
 typedef struct fv_plan_s *fv_plan_t;   /* opaque plan handle; owns its device memory */
 
@@ -109,6 +109,8 @@ typedef struct {
                                  gives the value reached; the estimate, a difference of squared
                                  norms, resolves about 1e-8, so a smaller eps gets the largest
                                  basis); ignored by the other routes */
+    int bin_size[2];          /* cells of the highest channel's grid per bin of the per-time source sort
+                                 in x and y; 0 = 8 x 4; 1 <= each <= 64 */
 } fv_opts;
 
 /* Transform choice (Section 2.2.1).  When the antennas' horizontal positions
@@ -172,7 +174,8 @@ int fv_lattice_detect(int n_ant, const double *enu_m, double tol_m, double basis
 /* How the ES spreading step is run (all give the same result up to rounding). */
 typedef enum {
     FV_SPREAD_AUTO = 0,
-    FV_SPREAD_GATHER = 1,     /* per-tile, each thread sums the sources covering its cells */
+    FV_SPREAD_GATHER = 1,     /* per-tile, each thread sums the sources covering its cells; the tile's
+                                 sorted sources are staged in shared memory by bulk asynchronous copies */
     FV_SPREAD_SCATTER = 2,    /* per-tile, warps add each source's footprint with shared atomics */
     FV_SPREAD_ATOMIC = 3      /* one thread per source, global atomics on a cleared grid */
 } fv_spread_method;

@@ -103,6 +103,7 @@ struct fv_plan_s {
     int spread_req = 0;         // fv_opts.spread_method
     int fft_max_radix = 16;
     int spread_method = 0;      // resolved method
+    int bin_req[2] = {0, 0};    // fv_opts.bin_size
     int T[2] = {32, 32}, nbx = 1, nby = 1, f_top = 0;
     double qscale_top[3] = {0, 0, 0};
     int nf1_top[3] = {1, 1, 1};
@@ -142,6 +143,13 @@ struct fv_plan_s {
     void *d_bas_tf = nullptr;         //   offsets [4] in the grid precision
     void *d_bas_ts = nullptr;         //   deconvolution x postphase (complex, grid precision)
     double *d_bas_shat = nullptr;     // [n_src][K] flux coefficients (recomputed by every execution)
+
+    // device status word: kernels with bounded waits or-in FV_DEVICE_TIMEOUT; copied to the pinned
+    // h_status after every execution (event ev_status) and checked when that copy has landed
+    int *d_status = nullptr;
+    int *h_status = nullptr;
+    cudaEvent_t ev_status = nullptr;
+    bool status_pending = false;
 
     long long ws_bytes = 0;
     std::vector<long> geo_sig;       // sizes behind the current tables and workspaces
@@ -185,5 +193,9 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
 template <class G>
 fv_status run_basis(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, char *vis, size_t slice_bytes,
                     int t_begin, int t_end);
+// Device status word of a plan: copy it behind an execution's work, and report (once) a bounded wait
+// that ran out in an earlier execution as FV_ERR_TIMEOUT.
+cudaError_t plan_post_status(fv_plan_s *p);
+fv_status plan_take_status(fv_plan_s *p, bool wait);
 // Orthonormal basis of the polynomials of degree < K over the channel frequencies: M[q * K + k].
 bool basis_matrix(const std::vector<double> &freq, int K, std::vector<double> &M);

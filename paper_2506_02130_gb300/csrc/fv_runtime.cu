@@ -10,6 +10,7 @@
 #include "../../include/fv.h"
 #include "fv_basis.cuh"
 #include "fv_internal.cuh"
+#include "fv_staged.cuh"
 #include "fv_plan.cuh"
 
 #include <algorithm>
@@ -169,8 +170,9 @@ size_t workspace_layout(const fv_plan_s::WsNeed &need, char *base, fv_plan_s::Wo
         o.sidx = (int *)take(ns * sizeof(int));
         o.cell = (int *)take(3 * ns * sizeof(int));
         o.sdir = (double *)take(3 * ns * sizeof(double));
-        o.frac = take(ns * need.frac_per_src);
-        o.cs = take(ns * need.cs_per_src);
+        // 64 bytes of slack: the band spreader's bulk copies round their ends up to 16 bytes
+        o.frac = take(ns * need.frac_per_src + 64);
+        o.cs = take(ns * need.cs_per_src + 64);
     }
     return off;
 }
@@ -241,18 +243,19 @@ static void resolve_spread(fv_plan_s *p, int gs, int w)
     int nz_t = 0, bx = 8, by = 4;
     const bool gather_ok = spread_gather_config(gs, p->n_pol, nzm, w, &nz_t, &bx, &by) != 0;
     const bool scatter_ok = spread_scatter_smem(gs, p->n_pol, nzm) <= FV_SPREAD_SMEM_MAX && w <= 32;
-    int m = p->spread_req;
     // FP64 tiles of 16 height planes hold 16 double-complex accumulators per lane: measured slower than
     // the other methods for the per-channel slices, so auto takes them only where nothing else exists
     const bool gather_auto = gather_ok && !(gs == 8 && nz_t == 16);
+    int m = p->spread_req;
     if (m == FV_SPREAD_AUTO)
         m = gather_auto ? FV_SPREAD_GATHER : (scatter_ok ? FV_SPREAD_SCATTER : FV_SPREAD_ATOMIC);
     if (m == FV_SPREAD_GATHER && !gather_ok) m = FV_SPREAD_ATOMIC;
     if (m == FV_SPREAD_SCATTER && !scatter_ok) m = FV_SPREAD_ATOMIC;
     p->spread_method = m;
     p->tiled = m != FV_SPREAD_ATOMIC;
-    p->T[0] = 8;
-    p->T[1] = 4;
+    // bins of the per-time sort: the plan's size, else 8 x 4 cells of the top channel's grid
+    p->T[0] = p->bin_req[0] > 0 ? p->bin_req[0] : 8;
+    p->T[1] = p->bin_req[1] > 0 ? p->bin_req[1] : 4;
     p->nbx = (p->nf1_top[0] + p->T[0] - 1) / p->T[0];
     p->nby = (p->nf1_top[1] + p->T[1] - 1) / p->T[1];
 }
@@ -496,8 +499,11 @@ static fv_status prepare(fv_plan_s *p)
     p->need.tiled = p->tiled;
     p->need.n_src = std::max<long>(p->n_src, 1);
     p->need.nb = p->nbx * p->nby;
-    p->need.frac_per_src = 3 * gs;
-    p->need.cs_per_src = (size_t)p->n_pol * es;
+    // the gather spreading reads staged records: 16 (FP32) or 32 (FP64) bytes per source where the split
+    // coordinates take 12 or 24, and strengths padded to 16 bytes
+    const bool staged = p->spread_method == FV_SPREAD_GATHER;
+    p->need.frac_per_src = staged ? 4 * gs : 3 * gs;
+    p->need.cs_per_src = staged ? (size_t)staged_cs_stride((int)gs, p->n_pol) * es : (size_t)p->n_pol * es;
     const size_t bin_bytes = p->tiled ? workspace_layout(p->need, nullptr, nullptr) -
                                             (p->need.grid + p->need.bufA + p->need.bufB + p->need.vu)
                                       : 0;
@@ -616,6 +622,11 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
     const double prep_bytes = nvis * (24.0 + 4.0 + p->n_stokes * (p->flux_fp64 ? 8.0 : 4.0) + 12.0 +
                                       3.0 * sizeof(G) + p->n_pol * es);
     const double spread_in_bytes = nvis * (12.0 + 3.0 * sizeof(G) + p->n_pol * es);
+    // staged records: one 16- or 32-byte record plus the (padded) strengths per source, read once
+    const double cs_staged = staged_cs_stride((int)sizeof(G), p->n_pol) * es;
+    const double spread_in_bytes_staged = nvis * (sizeof(SrcRec<G>) + cs_staged);
+    const double prep_bytes_staged = nvis * (24.0 + 4.0 + p->n_stokes * (p->flux_fp64 ? 8.0 : 4.0) +
+                                             sizeof(SrcRec<G>) + cs_staged);
     const int nb = p->nbx * p->nby;
     const G *pre = (const G *)p->d_pre;
     const cpx<G> *tw = (const cpx<G> *)p->d_tw;
@@ -652,19 +663,28 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
             if (p->tiled) {
                 G *frac = (G *)wk.frac;
                 cpx<G> *cs = (cpx<G> *)wk.cs;
+                // the gather spreading reads staged records (bulk-copied per chunk)
+                const bool staged = p->spread_method == FV_SPREAD_GATHER;
+                SrcRec<G> *rec = (SrcRec<G> *)wk.frac;
                 CK(prof_begin(p, PC_PREP, st));
-                CK(launch_prep<G>(wk.sdir, wk.sidx, wk.offsets + nb, p->n_src, p->flux, p->flux_fp64, nf, f, g, wk.cell,
-                                  frac, cs, st));
-                CK(prof_end(p, prep_bytes));
+                if (staged)
+                    CK(launch_prep_staged<G>(wk.sdir, wk.sidx, wk.offsets + nb, p->n_src, p->flux, p->flux_fp64, nf,
+                                             f, g, rec, cs, st));
+                else
+                    CK(launch_prep<G>(wk.sdir, wk.sidx, wk.offsets + nb, p->n_src, p->flux, p->flux_fp64, nf, f, g,
+                                      wk.cell, frac, cs, st));
+                CK(prof_end(p, staged ? prep_bytes_staged : prep_bytes));
                 const double r0 = D[0].qscale / p->qscale_top[0], r1 = D[1].qscale / p->qscale_top[1];
                 g.pre_x = pre + p->pre_off[(size_t)f * 3];         // applied as the tile is stored
                 g.pre_y = pre + p->pre_off[(size_t)f * 3 + 1];
                 CK(prof_begin(p, PC_SPREAD, st));
-                if (p->spread_method == FV_SPREAD_SCATTER)
+                if (p->spread_method == FV_SPREAD_GATHER)
+                    CK(launch_spread_gather_rec<G>(wk.offsets, rec, cs, g, tb, r0, r1, p->d_status, grid, st));
+                else if (p->spread_method == FV_SPREAD_SCATTER)
                     CK(launch_spread_scatter<G>(wk.offsets, wk.cell, frac, cs, p->n_src, g, tb, r0, r1, grid, st));
                 else
                     CK(launch_spread_tile<G>(wk.offsets, wk.cell, frac, cs, p->n_src, g, tb, r0, r1, grid, st));
-                CK(prof_end(p, spread_in_bytes + gel * es));
+                CK(prof_end(p, (staged ? spread_in_bytes_staged : spread_in_bytes) + gel * es));
             } else {
                 CK(prof_begin(p, PC_MEMSET, st));
                 CK(cudaMemsetAsync(grid, 0, gel * sizeof(cpx<G>), st));
@@ -1048,6 +1068,32 @@ fv_status run_basis(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, cha
 template fv_status run_basis<float>(fv_plan_s *, fv_plan_s::Workspace &, cudaStream_t, char *, size_t, int, int);
 template fv_status run_basis<double>(fv_plan_s *, fv_plan_s::Workspace &, cudaStream_t, char *, size_t, int, int);
 
+// The device status word after an execution: copied to pinned host memory behind the execution's work.
+cudaError_t plan_post_status(fv_plan_s *p)
+{
+    cudaError_t e = cudaMemcpyAsync(p->h_status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_status, p->stream);
+    if (e == cudaSuccess) p->status_pending = true;
+    return e;
+}
+
+// FV_ERR_TIMEOUT if a kernel of an earlier execution reported a bounded wait that ran out (its results
+// were not valid), once; the word is then cleared.  wait: block until the last copy has landed, else
+// look only if it already has.
+fv_status plan_take_status(fv_plan_s *p, bool wait)
+{
+    if (!p->status_pending) return FV_OK;
+    const cudaError_t q = wait ? cudaEventSynchronize(p->ev_status) : cudaEventQuery(p->ev_status);
+    if (q == cudaErrorNotReady) return FV_OK;
+    if (q != cudaSuccess) return p->fail(FV_ERR_CUDA, std::string("status event: ") + cudaGetErrorString(q));
+    p->status_pending = false;
+    if (*p->h_status == 0) return FV_OK;
+    *p->h_status = 0;
+    if (cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream) != cudaSuccess)
+        return p->fail(FV_ERR_CUDA, "clearing the status word failed");
+    return p->fail(FV_ERR_TIMEOUT, "a bounded wait in a kernel ran out; the results of that execution are invalid");
+}
+
 // All slices, t-major, split into contiguous chunks over the plan's streams
 // (each with its own workspace); the streams fork from and join back to the
 // plan's stream.
@@ -1135,6 +1181,8 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
     if (o->beam == FV_BEAM_AIRY && !(o->beam_param[0] > 0)) return bad("Airy beam needs a diameter > 0");
     if (o->dims != 0 && o->dims != 2 && o->dims != 3) return bad("dims must be 0, 2 or 3");
     if (o->spread_method < FV_SPREAD_AUTO || o->spread_method > FV_SPREAD_ATOMIC) return bad("unknown spread_method");
+    if (o->bin_size[0] < 0 || o->bin_size[0] > 64 || o->bin_size[1] < 0 || o->bin_size[1] > 64)
+        return bad("bin_size must be 0 or in [1, 64]");
     if (o->n_streams < 0) return bad("n_streams < 0");
     if (o->fft_max_radix != 0 && o->fft_max_radix != 8 && o->fft_max_radix != 16) return bad("fft_max_radix must be 0, 8 or 16");
     if (o->transform < FV_TRANSFORM_AUTO || o->transform > FV_TRANSFORM_BASIS) return bad("unknown transform");
@@ -1219,6 +1267,8 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
     // more ~1 GB workspaces
     p->n_streams = o->n_streams > 0 ? std::min(o->n_streams, 16) : (o->transform == FV_TRANSFORM_BASIS ? 4 : 8);
     p->spread_req = o->spread_method;
+    p->bin_req[0] = o->bin_size[0];
+    p->bin_req[1] = o->bin_size[1];
     // radix 8 needs fewer registers (more CTAs per SM), which wins in FP32; FP64 uses the same
     // register count either way and prefers fewer stages
     p->fft_max_radix = o->fft_max_radix > 0 ? o->fft_max_radix : (o->precision == FV_MIXED ? 8 : 16);
@@ -1264,8 +1314,12 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
     if (cudaMalloc(&p->d_glx, p->nq * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&p->d_glw, p->nq * sizeof(double)) != cudaSuccess ||
         cudaMemcpy(p->d_glx, zx.data(), p->nq * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(p->d_glw, zw.data(), p->nq * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(p->d_glw, zw.data(), p->nq * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess || cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&p->h_status, sizeof(int)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_status, cudaEventDisableTiming) != cudaSuccess)
         s = FV_ERR_CUDA;
+    if (p->h_status) *p->h_status = 0;
     if (s != FV_OK) {
         g_create_error = "device set-up failed";
         fv_destroy(p);
@@ -1659,6 +1713,8 @@ fv_status fv_execute(fv_plan_t p, void *vis, int vis_on_device)
     if (!vis) return p->fail(FV_ERR_ARG, "vis is NULL");
     if (!p->have_array || !p->have_sky) return p->fail(FV_ERR_STATE, "fv_set_array and fv_set_sky must come first");
     if (cudaSetDevice(p->device) != cudaSuccess) return p->fail(FV_ERR_CUDA, "cudaSetDevice failed");
+    fv_status prev = plan_take_status(p, false);
+    if (prev != FV_OK) return prev;
     const size_t cb = p->precision == FV_FP64 ? 16 : 8;
     const size_t slice_bytes = (size_t)p->n_bl * p->n_pol * cb;
     const size_t total = slice_bytes * p->freq.size() * p->lst.size();
@@ -1676,10 +1732,12 @@ fv_status fv_execute(fv_plan_t p, void *vis, int vis_on_device)
         s = p->precision == FV_FP64 ? execute_slices<double>(p, dst, slice_bytes)
                                     : execute_slices<float>(p, dst, slice_bytes);
     }
+    if (s == FV_OK) CK(plan_post_status(p));
     if (!vis_on_device) {
         if (s == FV_OK) CK(cudaMemcpyAsync(vis, tmp, total, cudaMemcpyDeviceToHost, p->stream));
         cudaFreeAsync(tmp, p->stream);
         CK(cudaStreamSynchronize(p->stream));
+        if (s == FV_OK) s = plan_take_status(p, true);
     }
     return s;
 }
@@ -1702,6 +1760,9 @@ fv_status fv_destroy(fv_plan_t p)
     dfree_t(p->d_e);
     dfree(p->d_flux_owned);
     dfree(p->d_grid_main);
+    dfree_t(p->d_status);
+    if (p->h_status) cudaFreeHost(p->h_status);
+    if (p->ev_status) cudaEventDestroy(p->ev_status);
     drop_beam_grids(p);
     for (cudaEvent_t ev : p->ev_pool) cudaEventDestroy(ev);
     for (size_t s = 1; s < p->sub.size(); ++s) {

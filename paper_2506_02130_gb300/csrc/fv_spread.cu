@@ -12,13 +12,16 @@
 //                  the first footprint cell (int) and an offset (FP32 or FP64);
 //   k_spread_gather one CTA per output tile: every thread owns (x, y) columns
 //                  of the tile and adds, in registers, the sources whose
-//                  footprint covers them (staged in shared memory with their
-//                  kernel values), then stores its cells once.  Every grid
-//                  cell is written by exactly one thread, so the grid needs
-//                  no clearing and there are no atomics.
+//                  footprint covers them (their records copied into shared
+//                  memory by bulk asynchronous copies, chunk by chunk, double
+//                  buffered, with their kernel values computed there), then
+//                  stores its cells once.  Every grid cell is written by
+//                  exactly one thread, so the grid needs no clearing and
+//                  there are no atomics.
 // A channel's grid coordinates are the top channel's scaled by r = qscale_f /
 // qscale_top <= 1 per axis, so a tile of channel f maps to a rectangle of top
 // bins, i.e. one contiguous range of sorted sources per bin row.
+#include "fv_staged.cuh"
 #include "fv_internal.cuh"
 
 #include <math.h>
@@ -38,6 +41,43 @@ __device__ __forceinline__ float es_kernel_f(float z, float beta)
 template <class G> __device__ __forceinline__ G es_k(G z, G beta);
 template <> __device__ __forceinline__ double es_k<double>(double z, double beta) { return es_kernel_d(z, beta); }
 template <> __device__ __forceinline__ float es_k<float>(float z, float beta) { return es_kernel_f(z, beta); }
+
+// Bulk asynchronous copies into shared memory, completion counted on an mbarrier (used by the gather
+// kernel's record staging), and the bounded wait on a barrier phase.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init1(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+// Wait for phase `parity` of *bar for at most about a second; false if the wait ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(smem_addr(bar)), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > 2000000000LL) return false;
+    }
+}
 
 __device__ __forceinline__ int top_cell(double q, int nf1)
 {
@@ -133,12 +173,15 @@ cudaError_t launch_time_binning(const double *e, long n_src, const TimeBin &tb, 
 }
 
 // ------------------------------------------------------------------ per slice
-template <class G>
+// Strengths with prephase and the split grid coordinates of the sorted visible sources.  STAGED: written
+// as staged records (rec[i], cs[i * stride + p]); otherwise as cell[3][n_src], frac[3][n_src],
+// cs[n_pol][n_src].
+template <class G, bool STAGED>
 __global__ void __launch_bounds__(256) k_prep(const double *__restrict__ sdir, const int *__restrict__ sidx,
                                               const int *__restrict__ nv_ptr, long n_src,
                                               const void *__restrict__ flux, int flux_fp64, int n_freq, int f,
                                               SliceGeom g, int *__restrict__ cell, G *__restrict__ frac,
-                                              cpx<G> *__restrict__ cs)
+                                              cpx<G> *__restrict__ cs, SrcRec<G> *__restrict__ rec)
 {
     const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= *nv_ptr) return;
@@ -156,17 +199,31 @@ __global__ void __launch_bounds__(256) k_prep(const double *__restrict__ sdir, c
     else { double a, b; sincos(ph, &a, &b); sp = (G)a; cp = (G)b; }
 #pragma unroll
     for (int p = 0; p < 4; ++p)
-        if (p < np) cs[(size_t)p * n_src + i] = cmul(c[p], cmk<G>(cp, sp));
-    // grid coordinates, split in FP64
+        if (p < np)
+            cs[STAGED ? (size_t)i * staged_cs_stride((int)sizeof(G), np) + p : (size_t)p * n_src + i] =
+                cmul(c[p], cmk<G>(cp, sp));
+    // grid coordinates, split in FP64: first footprint cell and offset l0 - q
+    int ci[3] = {0, 0, 0};
+    G fr[3] = {(G)0, (G)0, (G)0};
     for (int k = 0; k < 3; ++k) {
         if (k < g.d) {
             const double q = st[k] * g.dim[k].qscale;
             const double l0 = ceil(q - 0.5 * g.w);
-            cell[(size_t)k * n_src + i] = (int)l0 + g.dim[k].nf1 / 2;
-            frac[(size_t)k * n_src + i] = (G)(l0 - q);
-        } else {
-            cell[(size_t)k * n_src + i] = 0;
-            frac[(size_t)k * n_src + i] = (G)0;
+            ci[k] = (int)l0 + g.dim[k].nf1 / 2;
+            fr[k] = (G)(l0 - q);
+        }
+    }
+    if (STAGED) {
+        SrcRec<G> h;
+        h.cell = (unsigned)ci[0] | ((unsigned)ci[1] << 14) | ((unsigned)ci[2] << 28);
+        h.fx = fr[0];
+        h.fy = fr[1];
+        h.fz = fr[2];
+        rec[i] = h;
+    } else {
+        for (int k = 0; k < 3; ++k) {
+            cell[(size_t)k * n_src + i] = ci[k];
+            frac[(size_t)k * n_src + i] = fr[k];
         }
     }
 }
@@ -177,8 +234,19 @@ cudaError_t launch_prep(const double *sdir, const int *sidx, const int *nv_ptr, 
                         cudaStream_t st)
 {
     if (n_src <= 0) return cudaSuccess;
-    k_prep<G><<<(unsigned)((n_src + 255) / 256), 256, 0, st>>>(sdir, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f,
-                                                               g, cell, frac, cs);
+    k_prep<G, false><<<(unsigned)((n_src + 255) / 256), 256, 0, st>>>(sdir, sidx, nv_ptr, n_src, flux, flux_fp64,
+                                                                      n_freq, f, g, cell, frac, cs, nullptr);
+    return cudaGetLastError();
+}
+
+template <class G>
+cudaError_t launch_prep_staged(const double *sdir, const int *sidx, const int *nv_ptr, long n_src,
+                               const void *flux, int flux_fp64, int n_freq, int f, const SliceGeom &g,
+                               SrcRec<G> *rec, cpx<G> *cs, cudaStream_t st)
+{
+    if (n_src <= 0) return cudaSuccess;
+    k_prep<G, true><<<(unsigned)((n_src + 255) / 256), 256, 0, st>>>(sdir, sidx, nv_ptr, n_src, flux, flux_fp64,
+                                                                     n_freq, f, g, nullptr, nullptr, cs, rec);
     return cudaGetLastError();
 }
 
@@ -204,21 +272,32 @@ template <class G, int NP, int NZ> struct GatherMinBlocks {
     static constexpr int value = NP * NZ * (int)sizeof(G) >= 128 ? 2 : 4;
 };
 
-template <class G, int NP, int NZ>
+// REC: the candidates come as staged records (rec[i], strengths cs[i * stride + p], written by
+// launch_prep_staged); thread 0 copies each chunk's ranges into shared memory with bulk asynchronous
+// copies, double buffered, so that the next chunk arrives while the current one is added.  Otherwise
+// every thread loads its candidate from cell[3][n], frac[3][n], cs[n_pol][n].
+template <class G, int NP, int NZ, bool REC>
 __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::value)) k_spread_gather(const int *__restrict__ offsets,
                                                                   const int *__restrict__ cell,
                                                                   const G *__restrict__ frac,
                                                                   const cpx<G> *__restrict__ cs, long n_src,
                                                                   SliceGeom g, TimeBin tb, double r0, double r1,
+                                                                  const SrcRec<G> *__restrict__ rec,
+                                                                  int *__restrict__ status,
                                                                   cpx<G> *__restrict__ grid)
 {
     // candidates staged per round: 128 (96 in FP64, to keep the static shared memory under 48 KB)
     constexpr int kGatherChunk = sizeof(G) == 8 ? 96 : 128;
+    constexpr int kCsw = REC ? (NP * 2 * (int)sizeof(G) + 15) / 16 * 16 / (2 * (int)sizeof(G)) : NP;
     __shared__ int s_cz[kGatherChunk];
     __shared__ G s_fx[kGatherChunk], s_fy[kGatherChunk], s_fz[kGatherChunk];
     __shared__ G s_wx[kGatherChunk * kWpad], s_wy[kGatherChunk * kWpad];
     __shared__ __align__(16) G s_wz[kGatherChunk][NZ];
-    __shared__ cpx<G> s_c[NP][kGatherChunk];
+    __shared__ cpx<G> s_c[REC ? 1 : NP][REC ? 1 : kGatherChunk];
+    // record staging (REC): two buffers of [records][strengths], their barriers and sizes
+    __shared__ __align__(16) SrcRec<G> s_rec[REC ? 2 : 1][REC ? kGatherChunk : 1];
+    __shared__ __align__(16) cpx<G> s_cs[REC ? 2 : 1][REC ? kGatherChunk * kCsw : 1];
+    __shared__ __align__(8) uint64_t s_bar[2];
     // patch lists: candidate t (bits 0-7) with its footprint origin relative to the tile, cx - x0 + 16
     // (bits 8-15) and cy - y0 + 16 (bits 16-23), so that one shared load gives all three
     __shared__ int s_list[kPatches][kGatherChunk];
@@ -236,22 +315,47 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
 #pragma unroll
         for (int z = 0; z < NZ; ++z) acc[p][z] = cmk<G>((G)0, (G)0);
     if (threadIdx.x < kPatches) s_cnt[threadIdx.x] = 0;
-    // sources whose footprint can meet this tile (one-cell margin through the top-grid mapping)
-    const double qx_lo = (x0 - nx / 2 - 0.5 * w) / r0, qx_hi = (x0 + kTileX - nx / 2 + 0.5 * w - 1) / r0;
-    const double qy_lo = (y0 - ny / 2 - 0.5 * w) / r1, qy_hi = (y0 + kTileY - ny / 2 + 0.5 * w - 1) / r1;
-    const int bx_lo = top_cell(qx_lo - 1.0, tb.nf1_top[0]) / tb.T[0];
-    const int bx_hi = top_cell(qx_hi + 1.0, tb.nf1_top[0]) / tb.T[0];
-    const int by_lo = top_cell(qy_lo - 1.0, tb.nf1_top[1]) / tb.T[1];
-    const int by_hi = top_cell(qy_hi + 1.0, tb.nf1_top[1]) / tb.T[1];
+    // sources whose footprint can meet this tile (one-cell margin through the top-grid mapping): the bin
+    // rectangle, computed once per CTA in FP64 by one thread (GB300's FP64 rate is a sixty-fourth of FP32)
+    __shared__ int s_bins[4];
+    if (threadIdx.x == 0) {
+        const double qx_lo = (x0 - nx / 2 - 0.5 * w) / r0, qx_hi = (x0 + kTileX - nx / 2 + 0.5 * w - 1) / r0;
+        const double qy_lo = (y0 - ny / 2 - 0.5 * w) / r1, qy_hi = (y0 + kTileY - ny / 2 + 0.5 * w - 1) / r1;
+        s_bins[0] = top_cell(qx_lo - 1.0, tb.nf1_top[0]) / tb.T[0];
+        s_bins[1] = top_cell(qx_hi + 1.0, tb.nf1_top[0]) / tb.T[0];
+        s_bins[2] = top_cell(qy_lo - 1.0, tb.nf1_top[1]) / tb.T[1];
+        s_bins[3] = top_cell(qy_hi + 1.0, tb.nf1_top[1]) / tb.T[1];
+        if (REC) {
+            mbar_init1(&s_bar[0]);
+            mbar_init1(&s_bar[1]);
+        }
+    }
     const G two_over_w = (G)(2.0 / w), beta = (G)g.beta;
     // floor(v / w) for v < kGatherChunk * kWmax by a float product: (v + 0.5) / w lies at least 1/(2w) from
     // an integer, far more than the product's rounding error
     const float inv_w = 1.0f / (float)w;
     __syncthreads();
+    const int bx_lo = s_bins[0], bx_hi = s_bins[1], by_lo = s_bins[2], by_hi = s_bins[3];
+    bool ok = true;
+    unsigned phase = 0u;   // REC: bit b = parity of the next completion of buffer b's barrier
+    int kc = 0;            // REC: chunks consumed (buffer kc & 1)
+    // REC, thread 0: copy candidates [base, base + n) of the current rows table into buffer b
+    auto issue = [&](int b, int base, int n, int nrows) {
+        mbar_expect(&s_bar[b], (unsigned)n * (unsigned)(sizeof(SrcRec<G>) + kCsw * sizeof(cpx<G>)));
+        for (int r = 0; r < nrows; ++r) {
+            const int len = (r + 1 < nrows ? s_pre[r + 1] : s_total) - s_pre[r];
+            const int a = max(base, s_pre[r]), e = min(base + n, s_pre[r] + len);
+            if (a >= e) continue;
+            const int i0 = s_row0[r] + (a - s_pre[r]), m = e - a;
+            bulk_g2s(&s_rec[b][a - base], rec + i0, (unsigned)(m * sizeof(SrcRec<G>)), &s_bar[b]);
+            bulk_g2s(&s_cs[b][(a - base) * kCsw], cs + (size_t)i0 * kCsw, (unsigned)(m * kCsw * sizeof(cpx<G>)),
+                     &s_bar[b]);
+        }
+    };
     // The candidates of the tile are the bins [bx_lo, bx_hi] of the rows [by_lo, by_hi]: one contiguous
     // range of the sorted sources per row.  Rows are taken 32 at a time; their ranges are concatenated
     // (lengths scanned by warp 0) and cut into full chunks, so that a chunk is not limited to one row.
-    for (int r0w = by_lo; r0w <= by_hi; r0w += 32) {
+    for (int r0w = by_lo; r0w <= by_hi && ok; r0w += 32) {
         const int nrows = min(32, by_hi - r0w + 1);
         if (warp == 0) {
             int start = 0, len = 0;
@@ -269,32 +373,66 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
             s_row0[lane] = start;
             s_pre[lane] = incl - len;
             if (lane == 31) s_total = incl;
+            __syncwarp();
+            if (REC && lane == 0 && s_total > 0) issue(kc & 1, 0, min(kGatherChunk, s_total), nrows);
         }
         __syncthreads();
         const int total = s_total;
-        for (int base = 0; base < total; base += kGatherChunk) {
+        for (int base = 0; base < total; base += kGatherChunk, ++kc) {
             const int n = min(kGatherChunk, total - base);
+            const int b = kc & 1;
+            if (REC) {
+                // the next chunk goes into the other buffer, which every thread finished with
+                if (threadIdx.x == 0 && base + kGatherChunk < total)
+                    issue(b ^ 1, base + kGatherChunk, min(kGatherChunk, total - base - kGatherChunk), nrows);
+                const bool got = mbar_wait(&s_bar[b], (phase >> b) & 1u);
+                phase ^= 1u << b;
+                if (__syncthreads_or(!got)) {
+                    // a copy did not arrive in time: record it, let thread 0 wait (bounded) for the copy it
+                    // issued into the other buffer, and store zeros
+                    ok = false;
+                    if (threadIdx.x == 0) {
+                        atomicOr(status, FV_DEVICE_TIMEOUT);
+                        if (base + kGatherChunk < total) mbar_wait(&s_bar[b ^ 1], (phase >> (b ^ 1)) & 1u);
+                    }
+                    break;
+                }
+            }
             // 1. one thread per candidate: position, strengths, and the patches its footprint overlaps
             if (threadIdx.x < n) {
-                const int v = base + threadIdx.x;
-                // the row holding the v-th candidate: the last row whose prefix is <= v
-                int r = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1)
-                    if (r + step < nrows && s_pre[r + step] <= v) r += step;
-                const int i = s_row0[r] + (v - s_pre[r]);
                 const int t = threadIdx.x;
-                const int cx = cell[i], cy = cell[n_src + i];
+                int cx, cy;
+                if (REC) {
+                    const SrcRec<G> rr = s_rec[b][t];
+                    cx = (int)(rr.cell & 0x3fffu);
+                    cy = (int)((rr.cell >> 14) & 0x3fffu);
+                    s_fx[t] = rr.fx;
+                    s_fy[t] = rr.fy;
+                    if (g.d == 3) {
+                        s_cz[t] = (int)(rr.cell >> 28);
+                        s_fz[t] = rr.fz;
+                    }
+                } else {
+                    const int v = base + threadIdx.x;
+                    // the row holding the v-th candidate: the last row whose prefix is <= v
+                    int r = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1)
+                        if (r + step < nrows && s_pre[r + step] <= v) r += step;
+                    const int i = s_row0[r] + (v - s_pre[r]);
+                    cx = cell[i];
+                    cy = cell[n_src + i];
+                    s_fx[t] = frac[i];
+                    s_fy[t] = frac[n_src + i];
+                    if (g.d == 3) {
+                        s_cz[t] = cell[2 * n_src + i];
+                        s_fz[t] = frac[2 * n_src + i];
+                    }
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) s_c[REC ? 0 : p][REC ? 0 : t] = cs[(size_t)p * n_src + i];
+                }
                 const int ax = max(cx - x0, 0), bx = min(cx + w - 1 - x0, kTileX - 1);
                 const int ay = max(cy - y0, 0), by2 = min(cy + w - 1 - y0, kTileY - 1);
-                s_fx[t] = frac[i];
-                s_fy[t] = frac[n_src + i];
-                if (g.d == 3) {
-                    s_cz[t] = cell[2 * n_src + i];
-                    s_fz[t] = frac[2 * n_src + i];
-                }
-#pragma unroll
-                for (int p = 0; p < NP; ++p) s_c[p][t] = cs[(size_t)p * n_src + i];
                 if (ax <= bx && ay <= by2) {
                     for (int qy = ay / kPatchY; qy <= by2 / kPatchY; ++qy)
                         for (int qx = ax / kPatchX; qx <= bx / kPatchX; ++qx) {
@@ -339,7 +477,7 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
                     }
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
-                        const cpx<G> cp = cscale(s_c[p][t], wxy);
+                        const cpx<G> cp = cscale(REC ? s_cs[b][t * kCsw + p] : s_c[REC ? 0 : p][REC ? 0 : t], wxy);
 #pragma unroll
                         for (int z = 0; z < NZ; ++z) {
                             acc[p][z].x += cp.x * wz[z];
@@ -356,7 +494,7 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
     }
     if (gx < nx && gy < ny) {
         // the x and y prescale of the FFT passes, applied here once per cell when the plan asks for it
-        const G sc = g.pre_x ? ((const G *)g.pre_x)[gx] * ((const G *)g.pre_y)[gy] : (G)1;
+        const G sc = ok ? (g.pre_x ? ((const G *)g.pre_x)[gx] * ((const G *)g.pre_y)[gy] : (G)1) : (G)0;
 #pragma unroll
         for (int p = 0; p < NP; ++p)
 #pragma unroll
@@ -367,12 +505,16 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
 
 template <class G, int NP, int NZ>
 static cudaError_t gather_launch(const int *offsets, const int *cell, const G *frac, const cpx<G> *cs, long n_src,
-                                 const SliceGeom &g, const TimeBin &tb, double r0, double r1, cpx<G> *grid,
-                                 cudaStream_t st)
+                                 const SliceGeom &g, const TimeBin &tb, double r0, double r1,
+                                 const SrcRec<G> *rec, int *status, cpx<G> *grid, cudaStream_t st)
 {
     dim3 blocks((g.dim[0].nf1 + kTileX - 1) / kTileX, (g.dim[1].nf1 + kTileY - 1) / kTileY);
-    k_spread_gather<G, NP, NZ><<<blocks, kGatherThreads, 0, st>>>(offsets, cell, frac, cs, n_src, g, tb, r0, r1,
-                                                                   grid);
+    if (rec)
+        k_spread_gather<G, NP, NZ, true><<<blocks, kGatherThreads, 0, st>>>(offsets, cell, frac, cs, n_src, g, tb,
+                                                                            r0, r1, rec, status, grid);
+    else
+        k_spread_gather<G, NP, NZ, false><<<blocks, kGatherThreads, 0, st>>>(offsets, cell, frac, cs, n_src, g, tb,
+                                                                             r0, r1, rec, status, grid);
     return cudaGetLastError();
 }
 
@@ -389,26 +531,52 @@ int spread_gather_config(int elem_bytes, int n_pol, int nz, int w, int *nz_tmpl,
     return 1;
 }
 
+// The gather kernel for a slice: candidates from cell/frac/cs (rec == nullptr) or from staged records.
 template <class G>
-cudaError_t launch_spread_tile(const int *offsets, const int *cell, const G *frac, const cpx<G> *cs, long n_src,
-                               const SliceGeom &g, const TimeBin &tb, double r0, double r1, cpx<G> *grid,
-                               cudaStream_t st)
+static cudaError_t gather_dispatch(const int *offsets, const int *cell, const G *frac, const cpx<G> *cs, long n_src,
+                                   const SliceGeom &g, const TimeBin &tb, double r0, double r1, const SrcRec<G> *rec,
+                                   int *status, cpx<G> *grid, cudaStream_t st)
 {
     const int nz = g.d == 3 ? g.dim[2].nf1 : 1;
     int NZ = 0, bx = 0, by = 0;
     if (!spread_gather_config(sizeof(G), g.n_pol, nz, g.w, &NZ, &bx, &by)) return cudaErrorInvalidValue;
     const int key = (g.n_pol == 4 ? 100 : 0) + NZ;
+#define FV_GATHER_ARGS offsets, cell, frac, cs, n_src, g, tb, r0, r1, rec, status, grid, st
     switch (key) {
-    case 1: return gather_launch<G, 1, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
-    case 8: return gather_launch<G, 1, 8>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
-    case 16: return gather_launch<G, 1, 16>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
-    case 101: return gather_launch<G, 4, 1>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+    case 1: return gather_launch<G, 1, 1>(FV_GATHER_ARGS);
+    case 8: return gather_launch<G, 1, 8>(FV_GATHER_ARGS);
+    case 16: return gather_launch<G, 1, 16>(FV_GATHER_ARGS);
+    case 101: return gather_launch<G, 4, 1>(FV_GATHER_ARGS);
     case 108:
-        if constexpr (sizeof(G) == 4) return gather_launch<G, 4, 8>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, grid, st);
+        if constexpr (sizeof(G) == 4) return gather_launch<G, 4, 8>(FV_GATHER_ARGS);
         else return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
+#undef FV_GATHER_ARGS
 }
+
+template <class G>
+cudaError_t launch_spread_tile(const int *offsets, const int *cell, const G *frac, const cpx<G> *cs, long n_src,
+                               const SliceGeom &g, const TimeBin &tb, double r0, double r1, cpx<G> *grid,
+                               cudaStream_t st)
+{
+    return gather_dispatch<G>(offsets, cell, frac, cs, n_src, g, tb, r0, r1, nullptr, nullptr, grid, st);
+}
+
+template <class G>
+cudaError_t launch_spread_gather_rec(const int *offsets, const SrcRec<G> *rec, const cpx<G> *cs, const SliceGeom &g,
+                                     const TimeBin &tb, double r0, double r1, int *status, cpx<G> *grid,
+                                     cudaStream_t st)
+{
+    return gather_dispatch<G>(offsets, nullptr, nullptr, cs, 0, g, tb, r0, r1, rec, status, grid, st);
+}
+
+template cudaError_t launch_spread_gather_rec<float>(const int *, const SrcRec<float> *, const cpx<float> *,
+                                                     const SliceGeom &, const TimeBin &, double, double, int *,
+                                                     cpx<float> *, cudaStream_t);
+template cudaError_t launch_spread_gather_rec<double>(const int *, const SrcRec<double> *, const cpx<double> *,
+                                                      const SliceGeom &, const TimeBin &, double, double, int *,
+                                                      cpx<double> *, cudaStream_t);
 
 // Scatter form of the tiled spreading: a CTA owns a kScatX x kScatY tile with
 // all z cells in shared memory (real and imaginary parts in separate planes,
@@ -543,6 +711,12 @@ template cudaError_t launch_prep<double>(const double *, const int *, const int 
                                          const SliceGeom &, int *, double *, cpx<double> *, cudaStream_t);
 template cudaError_t launch_prep<float>(const double *, const int *, const int *, long, const void *, int, int, int,
                                         const SliceGeom &, int *, float *, cpx<float> *, cudaStream_t);
+template cudaError_t launch_prep_staged<double>(const double *, const int *, const int *, long, const void *, int,
+                                                int, int, const SliceGeom &, SrcRec<double> *, cpx<double> *,
+                                                cudaStream_t);
+template cudaError_t launch_prep_staged<float>(const double *, const int *, const int *, long, const void *, int,
+                                               int, int, const SliceGeom &, SrcRec<float> *, cpx<float> *,
+                                               cudaStream_t);
 template cudaError_t launch_spread_tile<double>(const int *, const int *, const double *, const cpx<double> *, long,
                                                 const SliceGeom &, const TimeBin &, double, double, cpx<double> *,
                                                 cudaStream_t);

@@ -21,7 +21,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfftvis_gb300.so")
 
-ABI_VERSION = 3          # FV_ABI_VERSION of include/fv.h that the structs below mirror
+ABI_VERSION = 4          # FV_ABI_VERSION of include/fv.h that the structs below mirror
 FV_OK, FV_ERR_ARG, FV_ERR_OOM, FV_ERR_CUDA, FV_ERR_STATE, FV_ERR_TIMEOUT, FV_ERR_UNSUPPORTED = range(7)
 FV_FP64, FV_MIXED = 0, 1
 SPREAD = {"auto": 0, "gather": 1, "scatter": 2, "atomic": 3}
@@ -46,7 +46,8 @@ class fv_opts(C.Structure):
                 ("polarized", C.c_int), ("dims", C.c_int), ("upsampfac", C.c_double),
                 ("kernel_width", C.c_int), ("cuda_stream", C.c_void_p), ("device", C.c_int),
                 ("n_streams", C.c_int), ("spread_method", C.c_int), ("fft_max_radix", C.c_int),
-                ("transform", C.c_int), ("lattice_tol_m", C.c_double), ("n_basis", C.c_int)]
+                ("transform", C.c_int), ("lattice_tol_m", C.c_double), ("n_basis", C.c_int),
+                ("bin_size", C.c_int * 2)]
 
 
 class fv_info(C.Structure):
@@ -304,7 +305,8 @@ class Plan:
     @classmethod
     def create(cls, freqs_hz, lsts_rad, latitude_rad, beam="gauss", beam_param=(), precision=FV_FP64,
                eps=1e-10, polarized=False, dims=0, upsampfac=0.0, kernel_width=0, stream=None, device=-1,
-               n_streams=0, spread="auto", fft_max_radix=0, transform="auto", lattice_tol_m=0.0, n_basis=0):
+               n_streams=0, spread="auto", fft_max_radix=0, transform="auto", lattice_tol_m=0.0, n_basis=0,
+               bin_size=(0, 0)):
         o = fv_opts_default()
         freqs = np.ascontiguousarray(freqs_hz, dtype=np.float64)
         lsts = np.ascontiguousarray(lsts_rad, dtype=np.float64)
@@ -333,6 +335,7 @@ class Plan:
         o.transform = TRANSFORMS[transform]
         o.lattice_tol_m = lattice_tol_m
         o.n_basis = n_basis
+        o.bin_size[0], o.bin_size[1] = int(bin_size[0]), int(bin_size[1])
         h = fv_plan(o)
         return cls(h, len(freqs), len(lsts), 0, 4 if polarized else 1, precision)
 
