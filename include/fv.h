@@ -321,8 +321,12 @@ fv_status fv_profile_read(fv_plan_t p, fv_profile_data *out);
  * back to the batch's stream (cuda_stream, borrowed, or NULL for an owned one).
  *  - fv_batch_add: slices t in [t_lo, t_hi), f in [f_lo, f_hi) of plan p,
  *    written into vis, a device buffer of p's full fv_execute output shape.
- *    p must stay alive, keep its array and sky, and be on the batch's device
- *    until the batch is cleared or destroyed.
+ *    p must stay alive and be on the batch's device until the batch is
+ *    cleared or destroyed: destroying a member plan first leaves the batch
+ *    (and its graph) pointing at freed memory.  A member's fv_set_sky,
+ *    fv_set_array, fv_set_beams or fv_set_beam_grid is allowed: the next
+ *    fv_batch_execute notices it and captures the graph again (and resizes
+ *    the lanes).
  *  - fv_batch_add_range: the same slices into a buffer laid out for a
  *    window of channels from vis_f0 and vis_nt times from vis_t0: slice
  *    (t, f) goes to slice index (f - vis_f0) * vis_nt + (t - vis_t0), each
@@ -338,8 +342,10 @@ fv_status fv_profile_read(fv_plan_t p, fv_profile_data *out);
  *    graph; later executions replay the graph.  Graph execution needs kernel
  *    timing (fv_profile_enable) off on every member plan.
  *  - fv_batch_clear: removes all items (and the graph).
- * Errors: FV_ERR_ARG (bad range, host output, device mismatch), FV_ERR_STATE,
- * FV_ERR_OOM, FV_ERR_CUDA; fv_batch_last_error gives the message. */
+ * Errors: FV_ERR_ARG (bad range, host output, plan or output on another
+ * device), FV_ERR_STATE, FV_ERR_OOM, FV_ERR_CUDA, FV_ERR_TIMEOUT (a bounded
+ * wait of an earlier execution ran out; reported once); fv_batch_last_error
+ * gives the message. */
 typedef struct fv_batch_s *fv_batch_t;
 /* n_lanes: 1..32, 0 = 8.  device: -1 = the current device. */
 fv_status fv_batch_create(int device, void *cuda_stream, int n_lanes, fv_batch_t *out);
@@ -367,11 +373,14 @@ long long fv_batch_workspace_bytes(fv_batch_t b);
  * allocates and frees nothing.  The plan (fv_plan / fv_set_array /
  * fv_set_sky) is created as usual beforehand; vis must be a device buffer of
  * the fv_execute output shape and type.
- *  - The array is reserved on every device that loads the library, until the
- *    process exits.
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *  - The array is committed on a device when the library's module is loaded
+ *    there, which under CUDA's default lazy module loading is the first
+ *    fv_execute_static call on that device; it stays until the process exits.
+ *    Callers holding a fixed HBM budget make one warm-up call (a tiny plan
+ *    will do) before fixing the budget.
+ *  - The first call on a device (and the first after a cudaDeviceReset) looks
+ *    up the array's device address (cudaGetSymbolAddress) with that device
+ *    current; make that first call before any stream capture.
  *  - Every call on a device shares the one array and leaves its contents
  *    behind; the call clears what must start at zero itself.  Calls whose
  *    work overlaps on the GPU (other host threads, other plans, other
@@ -379,7 +388,8 @@ long long fv_batch_workspace_bytes(fv_batch_t b);
  *  - Returns when the work is enqueued on the plan's stream.
  * Errors: FV_ERR_UNSUPPORTED if the plan needs more scratch than
  * FV_STATIC_SCRATCH_BYTES (the message gives both sizes), FV_ERR_ARG (NULL or
- * host vis), FV_ERR_STATE, FV_ERR_CUDA. */
+ * host vis, or vis on another device), FV_ERR_STATE, FV_ERR_CUDA,
+ * FV_ERR_TIMEOUT (a bounded wait of an earlier execution ran out). */
 #define FV_STATIC_SCRATCH_BYTES (64ull << 20)
 fv_status fv_execute_static(fv_plan_t p, void *vis);
 

@@ -29,6 +29,7 @@ struct fv_batch_s {
         long k0, k1;
         double cost;
         OutMap om;
+        unsigned long long gen;   // the plan's generation the item (and a captured graph) was made with
     };
     std::vector<Item> items;
     bool graph_valid = false;
@@ -154,6 +155,8 @@ static fv_status add_items(fv_batch_t b, fv_plan_t p, void *vis, int t_lo, int t
         cudaGetLastError();
         return b->fail(FV_ERR_ARG, "batch outputs must be device buffers");
     }
+    if (pa.type == cudaMemoryTypeDevice && pa.device != b->device)
+        return b->fail(FV_ERR_ARG, "the output buffer is on another device than the batch");
     if (om.nt < 0 || om.f0 < 0 || om.t0 < 0 || om.f0 > f_lo || om.t0 > t_lo ||
         (om.nt > 0 && t_hi > om.t0 + om.nt))
         return b->fail(FV_ERR_ARG, "output layout does not hold the slice range");
@@ -171,7 +174,8 @@ static fv_status add_items(fv_batch_t b, fv_plan_t p, void *vis, int t_lo, int t
     }
     const double per_slice = (double)(p->need.grid + p->need.bufA + p->need.bufB) + 64.0 * p->n_src;
     for (int t = t_lo; t < t_hi; ++t) {
-        fv_batch_s::Item it{p, (char *)vis, (long)t * nf + f_lo, (long)t * nf + f_hi, per_slice * (f_hi - f_lo), om};
+        fv_batch_s::Item it{p, (char *)vis, (long)t * nf + f_lo, (long)t * nf + f_hi, per_slice * (f_hi - f_lo), om,
+                            p->gen};
         b->items.push_back(it);
     }
     b->graph_valid = false;
@@ -203,6 +207,17 @@ fv_status fv_batch_execute(fv_batch_t b, int use_graph)
     if (!b) return FV_ERR_ARG;
     if (cudaSetDevice(b->device) != cudaSuccess) return b->fail(FV_ERR_CUDA, "cudaSetDevice failed");
     if (b->items.empty()) return FV_OK;
+    // a member plan given a new sky, array or beams since the graph was captured: its buffers (and so the
+    // graph's kernel arguments) may have moved, so the graph is captured again (and the lanes resized)
+    for (auto &it : b->items) {
+        if (it.p->gen != it.gen) {
+            if (!it.p->have_array || !it.p->have_sky)
+                return b->fail(FV_ERR_STATE, "a member plan lost its array or sky; clear the batch");
+            if (it.p->use_basis) return b->fail(FV_ERR_UNSUPPORTED, "a member plan became a spectral-basis plan");
+            it.gen = it.p->gen;
+            b->graph_valid = false;
+        }
+    }
     fv_plan_s::WsNeed need;
     for (const auto &it : b->items) {
         const auto &n = it.p->need;
@@ -247,6 +262,11 @@ fv_status fv_batch_execute(fv_batch_t b, int use_graph)
         b->graph = g;
         CKB(cudaGraphInstantiate(&b->exec, b->graph, 0));
         b->graph_valid = true;
+    }
+    // a bounded wait that ran out in an earlier execution of a member plan is reported once
+    for (const auto &it : b->items) {
+        fv_status ps = plan_take_status(it.p, false);
+        if (ps != FV_OK) return b->fail(ps, it.p->err);
     }
     CKB(cudaGraphLaunch(b->exec, b->stream));
     return FV_OK;

@@ -150,6 +150,9 @@ struct fv_plan_s {
     int *h_status = nullptr;
     cudaEvent_t ev_status = nullptr;
     bool status_pending = false;
+    // bumped by every call that may move or replace the device buffers a captured batch graph points at
+    // (fv_set_array, fv_set_sky, fv_set_beams, fv_set_beam_grid)
+    unsigned long long gen = 0;
 
     long long ws_bytes = 0;
     std::vector<long> geo_sig;       // sizes behind the current tables and workspaces

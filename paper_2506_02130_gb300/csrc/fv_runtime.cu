@@ -1462,6 +1462,7 @@ static fv_status setup_array(fv_plan_s *p)
 
 fv_status fv_set_array(fv_plan_t p, int n_ant, const double *enu_m, int n_bl, const int *pairs)
 {
+    if (p) ++p->gen;
     if (!p) return FV_ERR_ARG;
     if (cudaSetDevice(p->device) != cudaSuccess) return p->fail(FV_ERR_CUDA, "cudaSetDevice failed");
     if (n_ant < 1 || !enu_m) return p->fail(FV_ERR_ARG, "need n_ant >= 1 and positions");
@@ -1489,6 +1490,7 @@ fv_status fv_set_array(fv_plan_t p, int n_ant, const double *enu_m, int n_bl, co
 
 fv_status fv_set_beams(fv_plan_t p, int n_beams, const int *kinds, const double *params, const int *beam_of_ant)
 {
+    if (p) ++p->gen;
     if (!p) return FV_ERR_ARG;
     if (cudaSetDevice(p->device) != cudaSuccess) return p->fail(FV_ERR_CUDA, "cudaSetDevice failed");
     if (!p->have_array) return p->fail(FV_ERR_STATE, "fv_set_array must come before fv_set_beams");
@@ -1577,6 +1579,7 @@ static void bspline_prefilter(double *f, int n, long stride, bool periodic)
 
 fv_status fv_set_beam_grid(fv_plan_t p, int beam, int n_theta, int n_phi, int order, const double *voltage)
 {
+    if (p) ++p->gen;
     if (!p) return FV_ERR_ARG;
     if (cudaSetDevice(p->device) != cudaSuccess) return p->fail(FV_ERR_CUDA, "cudaSetDevice failed");
     if (beam < -1 || beam >= (int)p->beams.size())
@@ -1638,6 +1641,7 @@ fv_status fv_set_beam_grid(fv_plan_t p, int beam, int n_theta, int n_phi, int or
 fv_status fv_set_sky(fv_plan_t p, long n_src, const double *ra_rad, const double *dec_rad, int n_stokes,
                      const void *flux, int flux_is_fp64, int flux_on_device)
 {
+    if (p) ++p->gen;
     if (!p) return FV_ERR_ARG;
     if (cudaSetDevice(p->device) != cudaSuccess) return p->fail(FV_ERR_CUDA, "cudaSetDevice failed");
     if (!p->have_array) return p->fail(FV_ERR_STATE, "fv_set_array must come before fv_set_sky");

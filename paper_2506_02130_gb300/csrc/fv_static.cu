@@ -13,11 +13,16 @@
 // that is part of the library image.  The call itself allocates nothing: no
 // cudaMalloc, cudaFree, cudaMallocAsync or allocating library routine.
 //
-// The array is reserved on every device that loads this library's kernels,
-// for the life of the process.  Its device address is looked up once per
-// device (cudaGetSymbolAddress) by the first fv_execute_static call made on
-// that device.
+// The array is committed on a device when the module holding it is loaded
+// there: with CUDA's lazy module loading (the default) that is the first
+// fv_execute_static call on that device, which also looks up its device
+// address (cudaGetSymbolAddress) once per device.  Callers holding a fixed
+// HBM budget make one warm-up call (a tiny plan will do) before fixing it.
+// The cached address belongs to the device's primary context: after a
+// cudaDeviceReset in the same process the first call looks it up again.
 #include "fv_plan.cuh"
+
+#include <cuda.h>
 
 #include <algorithm>
 #include <cstring>
@@ -32,17 +37,42 @@ namespace {
 
 std::mutex g_scratch_mu;
 void *g_scratch_addr[64] = {};
+unsigned long long g_scratch_ctx[64] = {};   // the primary context the address was looked up in
+
+// Identifier of the current context (0 if the driver cannot say), through the driver's entry point.
+unsigned long long current_context_id()
+{
+    using CtxGetId = CUresult (*)(CUcontext, unsigned long long *);
+    static CtxGetId fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetId)f;
+        cudaGetLastError();
+        looked = true;
+    }
+    unsigned long long id = 0;
+    if (!fn || fn(nullptr, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 // Device address of fv_static_scratch on `dev` (which must be current).
 cudaError_t scratch_address(int dev, void **out)
 {
     std::lock_guard<std::mutex> lk(g_scratch_mu);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    // a context created since (cudaDeviceReset) holds the array at another address: look it up again
+    const unsigned long long ctx = current_context_id();
+    if (g_scratch_addr[dev] && g_scratch_ctx[dev] != ctx) g_scratch_addr[dev] = nullptr;
     if (!g_scratch_addr[dev]) {
         void *a = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&a, fv_static_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_addr[dev] = a;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_addr[dev];
     return cudaSuccess;
@@ -70,6 +100,10 @@ extern "C" fv_status fv_execute_static(fv_plan_t p, void *vis)
         cudaGetLastError();
         return p->fail(FV_ERR_ARG, "fv_execute_static needs a device output buffer");
     }
+    if (pa.type == cudaMemoryTypeDevice && pa.device != p->device)
+        return p->fail(FV_ERR_ARG, "the output buffer is on another device than the plan");
+    fv_status prev = plan_take_status(p, false);
+    if (prev != FV_OK) return prev;
     // the same carving as a plan's own execution workspace (fv_plan_s::need), over the static array
     const size_t need = workspace_layout(p->need, nullptr, nullptr);
     if (need > FV_STATIC_SCRATCH_BYTES)
@@ -89,6 +123,8 @@ extern "C" fv_status fv_execute_static(fv_plan_t p, void *vis)
         return FV_OK;
     }
     // every slice on the plan's stream, in order, through the one scratch workspace
-    return p->precision == FV_FP64 ? run_slices<double>(p, wk, p->stream, (char *)vis, slice_bytes, 0, total)
-                                   : run_slices<float>(p, wk, p->stream, (char *)vis, slice_bytes, 0, total);
+    fv_status s = p->precision == FV_FP64 ? run_slices<double>(p, wk, p->stream, (char *)vis, slice_bytes, 0, total)
+                                          : run_slices<float>(p, wk, p->stream, (char *)vis, slice_bytes, 0, total);
+    if (s == FV_OK) CKS(plan_post_status(p));   // a copy of the status word into pinned memory: no allocation
+    return s;
 }

@@ -107,3 +107,48 @@ def test_batch_window_pieces_land_in_one_request_buffer():
         assert ei.value.status == fv.FV_ERR_ARG
     b.close()
     p.close()
+
+
+def test_graph_is_captured_again_after_a_member_gets_a_new_sky():
+    """A member plan's fv_set_sky after the graph was captured frees and replaces the buffers the graph
+    points at (a larger sky, borrowed device flux at a new address): the next execution must capture again
+    and give the new sky's visibilities, not replay kernels on freed memory."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    prob_a = W.config_hex127(seed=36, n_chan=2, n_time=2, n_point=300, nside=4, radius=3)
+    prob_b = W.config_hex127(seed=37, n_chan=2, n_time=2, n_point=1500, nside=8, radius=3)
+    # the same plan (array, channels, times) with another sky
+    prob_b.ant_enu, prob_b.pairs, prob_b.lsts_rad = prob_a.ant_enu, prob_a.pairs, prob_a.lsts_rad
+    assert np.array_equal(prob_b.freqs_hz, prob_a.freqs_hz)
+    p = fv.Plan.from_problem(prob_a, precision=fv.FV_MIXED, eps=1e-6, stream=stream.cuda_stream)
+    flux_a = torch.tensor(prob_a.sky.flux, dtype=torch.float32, device=dev)
+    p.set_sky(prob_a.sky.ra, prob_a.sky.dec, flux_a)
+    out = torch.full(p.out_shape, float("nan"), dtype=torch.complex64, device=dev)
+    b = fv.Batch(stream=stream.cuda_stream, n_lanes=2)
+    b.add(p, out)
+    for _ in range(2):
+        b.execute(use_graph=True)
+    stream.synchronize()
+    ref_a = oracle_vis(OracleProblem.from_workload(prob_a))
+    assert rel_l2(out.cpu().numpy(), ref_a) <= 2e-5
+    ws_a = b.workspace_bytes
+    # a new, five times larger sky from a new device buffer; the old buffer is dropped
+    flux_b = torch.tensor(prob_b.sky.flux, dtype=torch.float32, device=dev)
+    p.set_sky(prob_b.sky.ra, prob_b.sky.dec, flux_b)
+    del flux_a
+    torch.cuda.empty_cache()
+    out.fill_(float("nan"))
+    for _ in range(2):
+        b.execute(use_graph=True)
+    stream.synchronize()
+    alone = torch.empty(p.out_shape, dtype=torch.complex64, device=dev)
+    p.run(alone)
+    stream.synchronize()
+    got = out.cpu().numpy()
+    assert np.isfinite(got).all()
+    assert rel_l2(got, alone.cpu().numpy()) <= 2e-7
+    assert rel_l2(got, oracle_vis(OracleProblem.from_workload(prob_b))) <= 2e-5
+    assert b.workspace_bytes >= ws_a
+    b.close()
+    p.close()
