@@ -65,6 +65,10 @@ def parse():
                     help="hex127: basis functions K of the spectral-basis route (0: chosen by the plan from "
                          "the sky's spectra against eps)")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
+    ap.add_argument("--leg-requests", type=int, default=200,
+                    help="hex350: requests of the serving leg run beside the headline")
+    ap.add_argument("--no-serve-leg", action="store_true", help="hex350: skip the serving leg")
+    ap.add_argument("--no-batch-leg", action="store_true", help="hex350: skip the batching leg")
     ap.add_argument("--rate", type=float, default=0.0,
                     help="serve: mean arrival rate (1/s); 0 = 70%% of the measured capacity for the request mix")
     ap.add_argument("--serve-scale", type=float, default=1.0, help="serve: sky size scale (1 = full skies)")
@@ -419,11 +423,10 @@ def run_batch(args, rank, world, local, dist):
                                        for q, d in prof_by.items()},
             "routes": {"lattice_slices": sum(1 for p in plans if p.info()["transform"] == "lattice"),
                        "type3_slices": sum(1 for p in plans if p.info()["transform"] == "type3")}}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     b.close()
     for p in plans:
         p.close()
+    return line
 
 
 def run_serve(args, rank, world, local, dist):
@@ -573,11 +576,10 @@ def run_serve(args, rank, world, local, dist):
                     "path": "the served run itself: wall clock from the first arrival to the last completion, "
                             "every result copied to the host on completion; requests carry only windows of "
                             "resident plans, so no input bytes cross per request"}}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     ex.close()
     for p in plans.values():
         p.close()
+    return line
 
 
 # The simulation workloads: name in the JSON line, generator, route extras that apply
@@ -887,6 +889,35 @@ def run_sim(args, rank, world, local, dist):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, err = sampler.run(args.cpu_seconds, extra_slices)
 
+    # ---- the serving and batching patterns on this GPU, beside the headline (each a short run of its own)
+    serving_leg = batch_leg = None
+    if args.workload == "hex350" and not args.no_serve_leg:
+        a2 = argparse.Namespace(**vars(args))
+        a2.requests, a2.rate, a2.no_fp64_compare = args.leg_requests, 0.0, True
+        sv = run_serve(a2, rank, world, local, dist)
+        serving_leg = {"value": sv["value"], "unit": sv["unit"], "requests": sv["config"]["requests"],
+                       "rate_hz": sv["config"]["rate_hz"], "capacity_hz_estimate": sv["config"]["capacity_hz_estimate"],
+                       "p50_latency_s": sv["serving"]["p50_latency_s"], "p99_latency_s": sv["serving"]["p99_latency_s"],
+                       "mean_latency_s": sv["serving"]["mean_latency_s"], "p50_queue_s": sv["serving"]["p50_queue_s"],
+                       "rel_l2_vs_oracle_max": sv["rel_l2_vs_oracle_sample"]["max"],
+                       "workload": sv["config"]["workload"], "seconds": sv["ms_per_step"] / 1e3,
+                       "what": "Poisson stream of requests (blocks of 1-256 channels x 1-20 times of resident 37-, "
+                               "127- and 350-antenna plans) at 70% of the measured capacity; continuous batching, "
+                               "admission by free HBM; latency from arrival to the result on the host"}
+        torch.cuda.empty_cache()
+    if args.workload == "hex350" and not args.no_batch_leg:
+        a2 = argparse.Namespace(**vars(args))
+        a2.steps, a2.warmup, a2.no_fp64_compare = 3, 2, True
+        bt = run_batch(a2, rank, world, local, dist)
+        batch_leg = {"value": bt["value"], "unit": bt["unit"], "ms_per_step": bt["ms_per_step"], "steps": 3,
+                     "slices": bt["config"]["slices"], "workload": bt["config"]["workload"],
+                     "rel_l2_vs_oracle_sample": bt["rel_l2_vs_oracle_sample"], "routes": bt["routes"],
+                     "tune_seconds": bt["config"]["tune_seconds"],
+                     "what": "2,048 ragged single-slice problems (37-331 antennas, 1e3-5e5 sources, eps 1e-6 on the "
+                             "mixed path or 1e-9 on the FP64 path), autotuned, on shared lanes replayed from one "
+                             "CUDA graph; errors per path on 2% of the slices against the direct sum"}
+        torch.cuda.empty_cache()
+
     lat = sorted(step_ms)
     line = {"metric": "visibilities/s at <=2e-5 rel err vs FP64 direct sum", "value": value,
             "unit": "visibilities/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -910,7 +941,7 @@ def run_sim(args, rank, world, local, dist):
                                 "min": lat[0], "max": lat[-1]},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": gpu_launches,
             "rel_l2_vs_oracle_sample": err, "fp64_plain_equal_accuracy": fp64, "lattice_route": lat_route,
-            "basis_route": bas_route,
+            "basis_route": bas_route, "serving": serving_leg, "batching": batch_leg,
             "kernels": {k: {"ms_per_step": v["ms"], "launches_per_step": v["launches"],
                             "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}
                         for k, v in prof.items() if v["launches"] > 0}}
@@ -932,7 +963,9 @@ def main():
             dist.destroy_process_group()
         return
     if args.workload in ("batch", "serve"):
-        (run_batch if args.workload == "batch" else run_serve)(args, rank, world, local, dist)
+        line = (run_batch if args.workload == "batch" else run_serve)(args, rank, world, local, dist)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
         if dist:
             dist.destroy_process_group()
         return

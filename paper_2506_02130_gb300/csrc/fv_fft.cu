@@ -72,26 +72,10 @@ constexpr SC sincos2pi(int m, int R)
     if (k == 2) return {-s0, -c0};
     return {-c0, s0};
 }
-struct Table {
-    double c[17 * 16];
-    double s[17 * 16];
-};
-constexpr Table make_table()
-{
-    Table t{};
-    for (int R = 2; R <= 16; ++R)
-        for (int m = 0; m < R; ++m) {
-            SC v = sincos2pi(m, R);
-            t.c[R * 16 + m] = v.c;
-            t.s[R * 16 + m] = v.s;
-        }
-    return t;
-}
 }  // namespace cx
 
-__constant__ cx::Table kTw = cx::make_table();
-
-// v * e^{2 pi i m / R} with compile-time m, R (exact for the quarter turns)
+// v * e^{2 pi i m / R} with compile-time m, R: exact for the quarter turns, otherwise a product by
+// constants folded at compile time (no table load, no FP64 conversion in the FP32 instances)
 template <class G, int M_, int R>
 __device__ __forceinline__ cpx<G> twm(cpx<G> v)
 {
@@ -100,7 +84,10 @@ __device__ __forceinline__ cpx<G> twm(cpx<G> v)
     else if constexpr (4 * m == R) return cmuli(v);
     else if constexpr (2 * m == R) return cmk<G>(-v.x, -v.y);
     else if constexpr (4 * m == 3 * R) return cmk<G>(v.y, -v.x);
-    else return cmul(v, cmk<G>((G)kTw.c[R * 16 + m], (G)kTw.s[R * 16 + m]));
+    else {
+        constexpr cx::SC w = cx::sincos2pi(m, R);
+        return cmul(v, cmk<G>((G)w.c, (G)w.s));
+    }
 }
 
 // ---------------------------------------------------------------- register DFTs (+ sign)
