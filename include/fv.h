@@ -297,7 +297,8 @@ fv_status fv_get_info(fv_plan_t p, fv_info *info);
  * per kernel class, copies them out and resets the counters.  A batch with a
  * plan whose timing is enabled is not captured into a graph (FV_ERR_STATE).  Classes: "memset", "bin" (per-time rotation, horizon cut and
  * sort), "prep" (per-slice strengths and grid coordinates), "spread",
- * "fft_x", "fft_y", "fft_z", "interp", "scatter" (FV_PROFILE_CLASSES
+ * "fft_x", "fft_y", "fft_z", "interp", "scatter", "flux_t" (the channel-major
+ * copy of a borrowed device flux made at each execution) (FV_PROFILE_CLASSES
  * entries; unused ones have an empty name or stay zero).
  * bytes[c] is the algorithmic HBM traffic the launches of class c imply
  * (each input read once, each output written once).  Launch counts are kept

@@ -81,6 +81,13 @@ static fv_status enqueue(fv_batch_s *b)
         per[l].push_back(i);
         load[l] += b->items[i].cost;
     }
+    // each member plan's channel-major flux copy from its borrowed buffer, once per execution, before the fork
+    std::vector<fv_plan_s *> seen;
+    for (const auto &it : b->items)
+        if (std::find(seen.begin(), seen.end(), it.p) == seen.end()) {
+            seen.push_back(it.p);
+            CKB(refresh_flux_t(it.p, b->stream));
+        }
     CKB(cudaEventRecord(b->ev_fork, b->stream));
     for (int l = 0; l < L; ++l) CKB(cudaStreamWaitEvent(b->lanes[l], b->ev_fork, 0));
     for (int l = 0; l < L; ++l) {

@@ -92,7 +92,18 @@ struct SliceGeom {
     // x and y prescale tables 1/Phihat (grid precision) that the tiled spreading kernels apply when they
     // store each grid cell (the FFT passes then skip them); nullptr: the FFT passes apply them
     const void *pre_x, *pre_y;
+    // the plan's channel-major copy of the fluxes, [n_freq][n_src][n_stokes] (flux precision), or nullptr:
+    // the caller's [n_stokes][n_src][n_freq]
+    const void *flux_t;
 };
+
+// Position of Stokes parameter k of source n at channel f in the fluxes a slice reads (flux_index) and
+// the array it is in: the channel-major copy when there is one (one channel's Stokes values of a
+// source are adjacent), else the caller's layout.
+__host__ __device__ __forceinline__ size_t flux_index(const SliceGeom &g, int k, long n, long n_src, int n_freq, int f)
+{
+    return g.flux_t ? ((size_t)f * n_src + n) * g.n_stokes + k : ((size_t)k * n_src + n) * n_freq + f;
+}
 
 // Beam voltage A(theta) of the analytic beams (Section 2.4): Gaussian power beam,
 // Airy disc, or none.  rho = sin(zenith angle), s2 = cos(zenith angle).
@@ -225,13 +236,16 @@ __device__ __forceinline__ int source_strengths(const SliceGeom &g, double s0, d
                                                 const void *flux, int flux_fp64, long n_src, int n_freq, int f,
                                                 cpx<G> *c)
 {
-    const G rho = (G)sqrt(s0 * s0 + s1 * s1);
-    const G A = beam_voltage<G>(g.beam, (G)s0, (G)s1, rho, (G)s2, (G)g.nu, f);
+    // the beam in the grid precision (sin of the zenith angle from the direction's E, N components)
+    const G e0 = (G)s0, e1 = (G)s1;
+    const G rho = sqrt(e0 * e0 + e1 * e1);
+    const G A = beam_voltage<G>(g.beam, e0, e1, rho, (G)s2, (G)g.nu, f);
     // A_i A_j: the two antennas' voltages (one shared beam: A^2)
-    const G A2 = g.two_beams ? A * beam_voltage<G>(g.beam2, (G)s0, (G)s1, rho, (G)s2, (G)g.nu, f) : A * A;
+    const G A2 = g.two_beams ? A * beam_voltage<G>(g.beam2, e0, e1, rho, (G)s2, (G)g.nu, f) : A * A;
+    const void *fl = g.flux_t ? g.flux_t : flux;
     auto ld = [&](int k) -> G {
-        size_t idx = ((size_t)k * n_src + n) * n_freq + f;
-        return flux_fp64 ? (G)((const double *)flux)[idx] : (G)((const float *)flux)[idx];
+        const size_t idx = flux_index(g, k, n, n_src, n_freq, f);
+        return flux_fp64 ? (G)((const double *)fl)[idx] : (G)((const float *)fl)[idx];
     };
     if (!g.polarized) {
         c[0] = cmk<G>(A2 * ld(0), (G)0);
@@ -239,7 +253,7 @@ __device__ __forceinline__ int source_strengths(const SliceGeom &g, double s0, d
     }
     const G I = ld(0), Q = ld(1), U = ld(2), V = ld(3);
     G ca = (G)1, sa = (G)0;
-    if (rho > (G)0) { ca = (G)s1 / rho; sa = (G)s0 / rho; }
+    if (rho > (G)0) { ca = e1 / rho; sa = e0 / rho; }
     const G c2 = ca * ca - sa * sa, s2a = (G)2 * ca * sa;
     const G Qr = Q * c2 - U * s2a, Ur = Q * s2a + U * c2;
     c[0] = cmk<G>(A2 * (I + Qr), (G)0);
@@ -252,6 +266,11 @@ __device__ __forceinline__ int source_strengths(const SliceGeom &g, double s0, d
 
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return the launch error (cudaSuccess if fine).
+
+// Channel-major copy of the fluxes: out[f][n][k] = flux[k][n][f] (n_stokes k, n_src n, n_freq f), in the
+// fluxes' precision.
+cudaError_t launch_flux_transpose(const void *flux, int fp64, long n_src, int n_stokes, int n_freq, void *out,
+                                  cudaStream_t st);
 
 // e[3][n]: equatorial unit vectors from (ra, dec).
 cudaError_t launch_radec_to_unit(const double *ra, const double *dec, long n, double *e, cudaStream_t st);

@@ -56,6 +56,48 @@ __global__ void k_radec_to_unit(const double *ra, const double *dec, long n, dou
     e[2 * n + i] = sd;
 }
 
+// out[f][n][k] = in[k][n][f] through a shared tile of 32 sources x 32 channels per Stokes parameter: reads
+// run along channels, writes along (source, Stokes).
+template <class T>
+__global__ void __launch_bounds__(256) k_flux_transpose(const T *__restrict__ in, long n_src, int n_stokes, int n_freq,
+                                                        T *__restrict__ out)
+{
+    __shared__ T tile[4][32][33];
+    const long n0 = (long)blockIdx.x * 32;
+    const int f0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    for (int k = 0; k < n_stokes; ++k)
+        for (int r = ty; r < 32; r += 8) {
+            const long n = n0 + r;
+            const int f = f0 + tx;
+            tile[k][r][tx] = (n < n_src && f < n_freq) ? in[((size_t)k * n_src + n) * n_freq + f] : (T)0;
+        }
+    __syncthreads();
+    const int per = 32 * n_stokes;                  // (source, Stokes) values of one channel in the tile
+    for (int c = 0; c < 32; ++c) {
+        const int f = f0 + c;
+        if (f >= n_freq) break;
+        for (int v = threadIdx.x; v < per; v += blockDim.x) {
+            const int r = v / n_stokes, k = v - r * n_stokes;
+            const long n = n0 + r;
+            if (n < n_src) out[((size_t)f * n_src + n) * n_stokes + k] = tile[k][r][c];
+        }
+    }
+}
+
+cudaError_t launch_flux_transpose(const void *flux, int fp64, long n_src, int n_stokes, int n_freq, void *out,
+                                  cudaStream_t st)
+{
+    if (n_src <= 0 || n_freq <= 0) return cudaSuccess;
+    if (n_stokes < 1 || n_stokes > 4) return cudaErrorInvalidValue;
+    dim3 blocks((unsigned)((n_src + 31) / 32), (unsigned)((n_freq + 31) / 32));
+    if (fp64)
+        k_flux_transpose<double><<<blocks, 256, 0, st>>>((const double *)flux, n_src, n_stokes, n_freq, (double *)out);
+    else
+        k_flux_transpose<float><<<blocks, 256, 0, st>>>((const float *)flux, n_src, n_stokes, n_freq, (float *)out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_radec_to_unit(const double *ra, const double *dec, long n, double *e, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
@@ -176,14 +218,15 @@ __device__ __forceinline__ int source_strengths(const SliceGeom &g, const void *
     double rho = sqrt(s0 * s0 + s1 * s1);
     double A = beam_voltage<double>(g.beam, s0, s1, rho, s2, g.nu, f);
     double A2 = g.two_beams ? A * beam_voltage<double>(g.beam2, s0, s1, rho, s2, g.nu, f) : A * A;
-    double I = load_flux(flux, flux_fp64, (size_t)n * n_freq + f);
+    const void *fl = g.flux_t ? g.flux_t : flux;
+    double I = load_flux(fl, flux_fp64, flux_index(g, 0, n, n_src, n_freq, f));
     if (!g.polarized) {
         c[0] = cmk<double>(A2 * I, 0.0);
         return 1;
     }
-    double Q = load_flux(flux, flux_fp64, ((size_t)n_src + n) * n_freq + f);
-    double U = load_flux(flux, flux_fp64, ((size_t)2 * n_src + n) * n_freq + f);
-    double V = load_flux(flux, flux_fp64, ((size_t)3 * n_src + n) * n_freq + f);
+    double Q = load_flux(fl, flux_fp64, flux_index(g, 1, n, n_src, n_freq, f));
+    double U = load_flux(fl, flux_fp64, flux_index(g, 2, n, n_src, n_freq, f));
+    double V = load_flux(fl, flux_fp64, flux_index(g, 3, n, n_src, n_freq, f));
     double ca = 1.0, sa = 0.0;
     if (rho > 0.0) { ca = s1 / rho; sa = s0 / rho; }
     double c2 = ca * ca - sa * sa, s2a = 2.0 * ca * sa;
@@ -709,6 +752,125 @@ __global__ void __launch_bounds__(kIbThreads) k_interp_batch(const cpx<G> *__res
     }
 }
 
+// 2-D interpolation with one warp per target.  Lane 0 computes the target's FP64 quantities (coordinate
+// on the FFT grid, first footprint cell, offset, postphase argument reduced to [-pi, pi]); lanes
+// (dx, j) = (lane / J, lane % J), J = 32 / w, then cover footprint column dx and, with four products,
+// product group j (each lane walks every row), or with one product, row group j.  A footprint row of a
+// product group is one coalesced load (w cells x n_pol values contiguous in the band).  The sums over
+// columns (and row groups) are shuffle reductions; the postphase sine and cosine run in the grid
+// precision after the FP64 reduction of their argument.
+template <class G, int NP>
+__global__ void __launch_bounds__(256) k_interp_warp(const cpx<G> *__restrict__ band, const double *__restrict__ bu,
+                                                     int n_u, const double *__restrict__ dec, SliceGeom g,
+                                                     cpx<double> *__restrict__ Vu)
+{
+    const int lane = threadIdx.x & 31;
+    const long u = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (u >= n_u) return;   // whole warps
+    const int w = g.w;
+    const G two_over_w = (G)(2.0 / w), beta = (G)g.beta;
+    // FP64 set-up on lane 0
+    int m0 = 0, m1 = 0;
+    G f0 = (G)0, f1 = (G)0, phr = (G)0;
+    if (lane == 0) {
+        double ph = 0.0;
+        double fr[2];
+        int mm[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const double x = -g.kappa * bu[3 * u + i];
+            const double pp = (x - g.dim[i].D) * g.dim[i].pscale;
+            const double m = ceil(pp - 0.5 * w);
+            mm[i] = (int)m;
+            fr[i] = pp - m;
+            ph += x * g.dim[i].C;
+        }
+        m0 = mm[0];
+        m1 = mm[1];
+        f0 = (G)fr[0];
+        f1 = (G)fr[1];
+        ph -= 6.283185307179586476925 * rint(ph * 0.15915494309189533577);
+        phr = (G)ph;
+    }
+    m0 = __shfl_sync(0xffffffffu, m0, 0);
+    m1 = __shfl_sync(0xffffffffu, m1, 0);
+    f0 = __shfl_sync(0xffffffffu, f0, 0);
+    f1 = __shfl_sync(0xffffffffu, f1, 0);
+    const int J = 32 / w;
+    const int dx = lane / J, j = lane - dx * J;
+    const bool on = dx < w;
+    // this lane's x weight, and the y weight of row r held by lane r * J (shuffled per row)
+    const G wx = on ? es_kernel(two_over_w * (f0 - (G)dx), beta) : (G)0;
+    const G wyl = on ? es_kernel(two_over_w * (f1 - (G)dx), beta) : (G)0;
+    const int Bx = g.dim[0].B;
+    const cpx<G> *col = band + ((size_t)(m1 + g.dim[1].H) * Bx + (m0 + g.dim[0].H + (on ? dx : 0))) * NP;
+    G ax[NP > 1 ? 4 : 1], ay[NP > 1 ? 4 : 1];
+#pragma unroll
+    for (int p = 0; p < (NP > 1 ? 4 : 1); ++p) ax[p] = ay[p] = (G)0;
+    for (int r = 0; r < w; ++r) {
+        const G wy = __shfl_sync(0xffffffffu, wyl, r * J);
+        if (NP == 1) {
+            if (on && r % J == j) {
+                const cpx<G> v = col[(size_t)r * Bx];
+                ax[0] += wy * v.x;
+                ay[0] += wy * v.y;
+            }
+        } else if (on) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int pp = j + q * J;
+                if (q * J < NP && pp < NP) {
+                    const cpx<G> v = col[(size_t)r * Bx * NP + pp];
+                    ax[q] += wy * v.x;
+                    ay[q] += wy * v.y;
+                }
+            }
+        }
+    }
+    const G phs = __shfl_sync(0xffffffffu, phr, 0);
+    G sp, cp;
+    if (sizeof(G) == 4) {
+        float a, b;
+        sincosf((float)phs, &a, &b);
+        sp = (G)a;
+        cp = (G)b;
+    } else {
+        // the FP64 path keeps the argument's FP64 reduction and an FP64 sine and cosine
+        double a, b;
+        sincos((double)phs, &a, &b);
+        sp = (G)a;
+        cp = (G)b;
+    }
+    const double dd = dec[u];
+    if (NP == 1) {
+        G x = ax[0] * wx, y = ay[0] * wx;
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+        }
+        if (lane == 0) Vu[u] = cmk<double>(((double)x * cp - (double)y * sp) * dd, ((double)x * sp + (double)y * cp) * dd);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (q * J >= NP) break;   // uniform
+            G x = ax[q] * wx, y = ay[q] * wx;
+            // sum over the columns: lanes with the same j are J apart; a partner past lane 31 adds nothing
+            // (a shuffle from there returns the caller's own value)
+            for (int o = J; o < 32; o <<= 1) {
+                const G tx = __shfl_down_sync(0xffffffffu, x, o), ty = __shfl_down_sync(0xffffffffu, y, o);
+                if (lane + o < 32) {
+                    x += tx;
+                    y += ty;
+                }
+            }
+            const int pp = j + q * J;
+            if (dx == 0 && pp < NP)
+                Vu[(size_t)u * NP + pp] =
+                    cmk<double>(((double)x * cp - (double)y * sp) * dd, ((double)x * sp + (double)y * cp) * dd);
+        }
+    }
+}
+
 static bool zrow_fits(const SliceGeom &g, int elem_bytes)
 {
     if (elem_bytes != 4 || g.d != 3 || g.n_pol != 1) return false;
@@ -726,8 +888,13 @@ cudaError_t launch_interp_zdirect(const cpx<G> *band, const double *bu, int n_u,
     long threads = (long)n_u * 32;
     const unsigned ib_blocks = (unsigned)((n_u + kIbTargets - 1) / kIbTargets);
     if (g.w <= kIbMaxW) {
-        if (g.d == 2 && g.n_pol <= 4) {
-            k_interp_batch<G, false><<<ib_blocks, kIbThreads, 0, st>>>(band, bu, n_u, dec, g, prez, twz, Vu);
+        if (g.d == 2) {
+            // one warp per target, 8 per CTA
+            const unsigned wb = (unsigned)((n_u + 7) / 8);
+            if (g.n_pol == 4)
+                k_interp_warp<G, 4><<<wb, 256, 0, st>>>(band, bu, n_u, dec, g, Vu);
+            else
+                k_interp_warp<G, 1><<<wb, 256, 0, st>>>(band, bu, n_u, dec, g, Vu);
             return cudaGetLastError();
         }
         if constexpr (sizeof(G) == 4) {

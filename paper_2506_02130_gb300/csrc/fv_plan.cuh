@@ -65,6 +65,11 @@ struct fv_plan_s {
     void *d_flux_owned = nullptr;
     const void *flux = nullptr;
     int flux_fp64 = 0;
+    // channel-major copy of the fluxes, [n_freq][n_src][n_stokes]: what the slices read (one channel's
+    // Stokes values of a source adjacent).  Made at fv_set_sky from an owned copy; from a borrowed device
+    // flux (which the caller may rewrite in place) at the start of every execution.
+    void *d_flux_t = nullptr;
+    bool flux_borrowed = false;
     double C[3] = {0, 0, 0}, S[3] = {0, 0, 0};
     bool any_visible = false;
 
@@ -196,6 +201,8 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
 template <class G>
 fv_status run_basis(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, char *vis, size_t slice_bytes,
                     int t_begin, int t_end);
+// Refresh the channel-major flux copy from a borrowed device flux, on stream st (no-op otherwise).
+cudaError_t refresh_flux_t(fv_plan_s *p, cudaStream_t st);
 // Device status word of a plan: copy it behind an execution's work, and report (once) a bounded wait
 // that ran out in an earlier execution as FV_ERR_TIMEOUT.
 cudaError_t plan_post_status(fv_plan_s *p);

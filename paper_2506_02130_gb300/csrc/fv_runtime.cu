@@ -88,9 +88,9 @@ template <class T> static void dfree_t(T *&ptr)
     ptr = nullptr;
 }
 
-static const char *k_prof_names[FV_PROFILE_CLASSES] = {"memset", "bin",   "prep",   "spread", "fft_x", "fft_y",
-                                                       "fft_z",  "interp", "scatter", "",      "",      ""};
-enum { PC_MEMSET = 0, PC_BIN, PC_PREP, PC_SPREAD, PC_FFT_X, PC_FFT_Y, PC_FFT_Z, PC_INTERP, PC_SCATTER };
+static const char *k_prof_names[FV_PROFILE_CLASSES] = {"memset", "bin",   "prep",    "spread",   "fft_x", "fft_y",
+                                                       "fft_z",  "interp", "scatter", "flux_t", "",      ""};
+enum { PC_MEMSET = 0, PC_BIN, PC_PREP, PC_SPREAD, PC_FFT_X, PC_FFT_Y, PC_FFT_Z, PC_INTERP, PC_SCATTER, PC_FLUX_T };
 
 // harvest recorded event pairs into the per-class totals (waits for each pair's end event, so it
 // holds whatever stream the launches ran on: the plan's own or a batch lane)
@@ -522,6 +522,7 @@ static fv_status prepare(fv_plan_s *p)
 static SliceGeom slice_geom_for(const fv_plan_s *p, int f, int t, const fv_plan_s::BeamGroup &gr)
 {
     SliceGeom g = p->gf[f];
+    g.flux_t = p->d_flux_t;
     std::memcpy(g.R, &p->Rt[(size_t)t * 9], 9 * sizeof(double));
     if (!p->beams.empty()) {
         g.beam = p->beams[gr.a];
@@ -1068,6 +1069,13 @@ fv_status run_basis(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, cha
 template fv_status run_basis<float>(fv_plan_s *, fv_plan_s::Workspace &, cudaStream_t, char *, size_t, int, int);
 template fv_status run_basis<double>(fv_plan_s *, fv_plan_s::Workspace &, cudaStream_t, char *, size_t, int, int);
 
+cudaError_t refresh_flux_t(fv_plan_s *p, cudaStream_t st)
+{
+    if (!p->flux_borrowed || !p->d_flux_t || p->n_src == 0) return cudaSuccess;
+    return launch_flux_transpose(p->flux, p->flux_fp64, p->n_src, p->n_stokes, (int)p->freq.size(), p->d_flux_t,
+                                 st);
+}
+
 // The device status word after an execution: copied to pinned host memory behind the execution's work.
 cudaError_t plan_post_status(fv_plan_s *p)
 {
@@ -1111,6 +1119,12 @@ static fv_status execute_slices(fv_plan_s *p, char *vis, size_t slice_bytes)
     if (p->use_basis)
         CK(launch_basis_sky(p->flux, p->flux_fp64, p->n_src, (int)p->freq.size(), p->d_bas_M, p->n_basis,
                             p->d_bas_shat, p->stream));
+    else if (p->flux_borrowed && p->d_flux_t) {
+        // the channel-major flux copy from the borrowed buffer (read and written once)
+        CK(prof_begin(p, PC_FLUX_T, p->stream));
+        CK(refresh_flux_t(p, p->stream));
+        CK(prof_end(p, 2.0 * p->n_src * p->n_stokes * p->freq.size() * (p->flux_fp64 ? 8 : 4)));
+    }
     const int S = (int)std::min<long>(p->n_streams, std::max<long>(total, 1));
     if (S > 1) {
         CK(cudaEventRecord(p->ev_fork, p->stream));
@@ -1655,7 +1669,9 @@ fv_status fv_set_sky(fv_plan_t p, long n_src, const double *ra_rad, const double
     p->have_sky = false;
     dfree_t(p->d_e);
     dfree(p->d_flux_owned);
+    dfree(p->d_flux_t);
     p->flux = nullptr;
+    p->flux_borrowed = false;
     p->n_src = n_src;
     p->n_stokes = n_stokes;
     p->flux_fp64 = flux_is_fp64 ? 1 : 0;
@@ -1671,10 +1687,19 @@ fv_status fv_set_sky(fv_plan_t p, long n_src, const double *ra_rad, const double
     const size_t fbytes = (size_t)n_stokes * n_src * p->freq.size() * (p->flux_fp64 ? 8 : 4);
     if (flux_on_device) {
         p->flux = flux;
+        p->flux_borrowed = true;
     } else if (n_src) {
         CK(cudaMalloc(&p->d_flux_owned, fbytes));
         CK(cudaMemcpyAsync(p->d_flux_owned, flux, fbytes, cudaMemcpyHostToDevice, p->stream));
         p->flux = p->d_flux_owned;
+    }
+    if (n_src && !p->use_basis) {
+        // the channel-major copy the slices read: made now from an owned copy, at every execution from a
+        // borrowed buffer
+        CK(cudaMalloc(&p->d_flux_t, fbytes));
+        if (!p->flux_borrowed)
+            CK(launch_flux_transpose(p->flux, p->flux_fp64, n_src, n_stokes, (int)p->freq.size(), p->d_flux_t,
+                                     p->stream));
     }
     // source extents over all times (visible directions only)
     const int nb = 304;
@@ -1763,6 +1788,7 @@ fv_status fv_destroy(fv_plan_t p)
     dfree_t(p->d_grp_bl);
     dfree_t(p->d_e);
     dfree(p->d_flux_owned);
+    dfree(p->d_flux_t);
     dfree(p->d_grid_main);
     dfree_t(p->d_status);
     if (p->h_status) cudaFreeHost(p->h_status);

@@ -202,15 +202,35 @@ __global__ void __launch_bounds__(256) k_prep(const double *__restrict__ sdir, c
         if (p < np)
             cs[STAGED ? (size_t)i * staged_cs_stride((int)sizeof(G), np) + p : (size_t)p * n_src + i] =
                 cmul(c[p], cmk<G>(cp, sp));
-    // grid coordinates, split in FP64: first footprint cell and offset l0 - q
+    // grid coordinates: first footprint cell l0 = ceil(q - w/2) and offset l0 - q of q = (s - C) qscale,
+    // the product in FP64.  FP64 grids split in FP64; FP32 grids split q into q_hi + q_lo (floats, q_lo
+    // the FP64 remainder) and take l0 and l0 - q_hi in FP32, exact but where q_hi - w/2 rounds onto an
+    // integer, which moves the footprint by one cell and drops a kernel value below e^-beta
     int ci[3] = {0, 0, 0};
     G fr[3] = {(G)0, (G)0, (G)0};
     for (int k = 0; k < 3; ++k) {
         if (k < g.d) {
             const double q = st[k] * g.dim[k].qscale;
-            const double l0 = ceil(q - 0.5 * g.w);
-            ci[k] = (int)l0 + g.dim[k].nf1 / 2;
-            fr[k] = (G)(l0 - q);
+            if (sizeof(G) == 4) {
+                const float qh = (float)q, ql = (float)(q - (double)qh);
+                const float l0 = ceilf(qh - 0.5f * (float)g.w);
+                ci[k] = (int)l0 + g.dim[k].nf1 / 2;
+                fr[k] = (G)((l0 - qh) - ql);
+            } else {
+                const double l0 = ceil(q - 0.5 * g.w);
+                ci[k] = (int)l0 + g.dim[k].nf1 / 2;
+                fr[k] = (G)(l0 - q);
+            }
+            // Eq. 5 keeps every footprint inside the grid; a rounding at its very edge moves the footprint
+            // back in by one cell (the offset follows, l0 - q stays exact)
+            const int hi = g.dim[k].nf1 - g.w;
+            if (ci[k] < 0) {
+                fr[k] -= (G)ci[k];
+                ci[k] = 0;
+            } else if (ci[k] > hi) {
+                fr[k] -= (G)(ci[k] - hi);
+                ci[k] = hi;
+            }
         }
     }
     if (STAGED) {

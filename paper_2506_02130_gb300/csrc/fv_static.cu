@@ -122,7 +122,9 @@ extern "C" fv_status fv_execute_static(fv_plan_t p, void *vis)
         CKS(cudaMemsetAsync(vis, 0, slice_bytes * total, p->stream));
         return FV_OK;
     }
-    // every slice on the plan's stream, in order, through the one scratch workspace
+    // the channel-major flux copy (a plan-owned buffer made at fv_set_sky), then every slice on the plan's
+    // stream, in order, through the one scratch workspace
+    CKS(refresh_flux_t(p, p->stream));
     fv_status s = p->precision == FV_FP64 ? run_slices<double>(p, wk, p->stream, (char *)vis, slice_bytes, 0, total)
                                           : run_slices<float>(p, wk, p->stream, (char *)vis, slice_bytes, 0, total);
     if (s == FV_OK) CKS(plan_post_status(p));   // a copy of the status word into pinned memory: no allocation

@@ -97,3 +97,53 @@ def test_upsampling_1_25_refuses_a_tolerance_its_widest_kernel_misses_and_meets_
     ref = oracle_vis(OracleProblem.from_workload(bs.problem))[0, 0]
     assert rel_l2(got, ref) <= 1e-7
     p.close()
+
+
+def _large_slices(seed):
+    """Slices of the batched workload at the top of its source range (3e5-5e5 sources), on the largest
+    arrays (331 antennas among them), with both drawn tolerances."""
+    pool = W.config_batch(seed=seed, n_slices=12, radii=(9, 10), n_src_range=(300000, 500000))
+    fp64 = [s for s in pool if s.precision == "fp64"][:2]
+    mixed = [s for s in pool if s.precision == "mixed"][:2]
+    assert fp64 and mixed
+    assert any(len(s.problem.ant_enu) == 331 for s in fp64 + mixed)
+    return mixed + fp64
+
+
+@pytest.mark.parametrize("route", ["batch", "type3"])
+def test_large_sky_slices_of_the_batched_workload_match_the_oracle(route):
+    """The spreading paths that only large skies reach (many candidate chunks per tile, many bin rows per
+    tile at the low channel ratio): through the autotuned graph batch (whatever route the plans take),
+    and forced onto the type-3 route (the tiled gather spreading)."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    slices = _large_slices(43)
+    rng = np.random.default_rng(1)
+    if route == "batch":
+        tuner = AT.Autotuner(AT.cuda_timer(stream, reps=1, warmup=1))
+        tuner.tune(slices, AT.key_of, AT.precision_of)
+        plans, outs, b = _run(slices, tuner, stream, dev, torch)
+        for _ in range(2):
+            b.execute(use_graph=True)
+        stream.synchronize()
+        results = [o.cpu().numpy()[0, 0] for o in outs]
+        b.close()
+        for p in plans:
+            p.close()
+    else:
+        results = []
+        for bs in slices:
+            q = AT.precision_of(bs)
+            p = fv.Plan.from_problem(bs.problem, precision=q, eps=bs.nufft_eps, stream=stream.cuda_stream,
+                                     transform="type3")
+            p.set_sky(bs.problem.sky.ra, bs.problem.sky.dec, bs.problem.sky.flux)
+            results.append(p.run()[0, 0])
+            p.close()
+    for bs, got in zip(slices, results):
+        assert np.isfinite(got).all()
+        nb = len(bs.problem.pairs)
+        sel = np.sort(rng.choice(nb, size=min(nb, 96), replace=False))
+        ref = oracle_vis(OracleProblem.from_workload(bs.problem, pairs=bs.problem.pairs[sel]))[0, 0]
+        err = rel_l2(got[sel], ref)
+        assert err <= TOL[bs.precision], (route, bs.problem.name, bs.problem.sky.n_src, bs.precision, err)
