@@ -309,10 +309,17 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
     // candidates staged per round: 128 (96 in FP64, to keep the static shared memory under 48 KB)
     constexpr int kGatherChunk = sizeof(G) == 8 ? 96 : 128;
     constexpr int kCsw = REC ? (NP * 2 * (int)sizeof(G) + 15) / 16 * 16 / (2 * (int)sizeof(G)) : NP;
-    __shared__ int s_cz[kGatherChunk];
-    __shared__ G s_fx[kGatherChunk], s_fy[kGatherChunk], s_fz[kGatherChunk];
-    __shared__ G s_wx[kGatherChunk * kWpad], s_wy[kGatherChunk * kWpad];
-    __shared__ __align__(16) G s_wz[kGatherChunk][NZ];
+    __shared__ int s_cz[NZ > 1 ? kGatherChunk : 1];
+    __shared__ G s_fx[kGatherChunk], s_fy[kGatherChunk], s_fz[NZ > 1 ? kGatherChunk : 1];
+    // x kernel values (3-D), or for 2-D grids the strengths already weighted by them: s_cwx[(t w + dx) NP + p]
+    // = c_p(t) psi_x(t, dx) in dynamic shared memory (kGatherChunk x w x NP complex values)
+    // and the y kernel values s_wy[t * w + j], after them (2-D) or alone (3-D)
+    constexpr bool CWX = NZ == 1;
+    __shared__ G s_wx[CWX ? 1 : kGatherChunk * kWpad];
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    cpx<G> *s_cwx = reinterpret_cast<cpx<G> *>(s_dyn);
+    G *s_wy = reinterpret_cast<G *>(s_dyn + (CWX ? (size_t)kGatherChunk * g.w * NP * sizeof(cpx<G>) : 0));
+    __shared__ __align__(16) G s_wz[NZ > 1 ? kGatherChunk : 1][NZ];
     __shared__ cpx<G> s_c[REC ? 1 : NP][REC ? 1 : kGatherChunk];
     // record staging (REC): two buffers of [records][strengths], their barriers and sizes
     __shared__ __align__(16) SrcRec<G> s_rec[REC ? 2 : 1][REC ? kGatherChunk : 1];
@@ -320,7 +327,7 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
     __shared__ __align__(8) uint64_t s_bar[2];
     // patch lists: candidate t (bits 0-7) with its footprint origin relative to the tile, cx - x0 + 16
     // (bits 8-15) and cy - y0 + 16 (bits 16-23), so that one shared load gives all three
-    __shared__ int s_list[kPatches][kGatherChunk];
+    __shared__ __align__(16) int s_list[kPatches][kGatherChunk];
     __shared__ int s_cnt[kPatches];
     __shared__ int s_row0[32], s_pre[32], s_total;
     const int nx = g.dim[0].nf1, ny = g.dim[1].nf1, nz = g.d == 3 ? g.dim[2].nf1 : 1;
@@ -429,8 +436,8 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
                     s_fx[t] = rr.fx;
                     s_fy[t] = rr.fy;
                     if (g.d == 3) {
-                        s_cz[t] = (int)(rr.cell >> 28);
-                        s_fz[t] = rr.fz;
+                        s_cz[NZ > 1 ? t : 0] = (int)(rr.cell >> 28);
+                        s_fz[NZ > 1 ? t : 0] = rr.fz;
                     }
                 } else {
                     const int v = base + threadIdx.x;
@@ -445,8 +452,8 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
                     s_fx[t] = frac[i];
                     s_fy[t] = frac[n_src + i];
                     if (g.d == 3) {
-                        s_cz[t] = cell[2 * n_src + i];
-                        s_fz[t] = frac[2 * n_src + i];
+                        s_cz[NZ > 1 ? t : 0] = cell[2 * n_src + i];
+                        s_fz[NZ > 1 ? t : 0] = frac[2 * n_src + i];
                     }
 #pragma unroll
                     for (int p = 0; p < NP; ++p) s_c[REC ? 0 : p][REC ? 0 : t] = cs[(size_t)p * n_src + i];
@@ -468,8 +475,16 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
             for (int v = threadIdx.x; v < n * w; v += kGatherThreads) {
                 const int t = (int)(((float)v + 0.5f) * inv_w);
                 const int j = v - t * w;
-                s_wx[t * kWpad + j] = es_k<G>(two_over_w * (s_fx[t] + (G)j), beta);
-                s_wy[t * kWpad + j] = es_k<G>(two_over_w * (s_fy[t] + (G)j), beta);
+                const G ex = es_k<G>(two_over_w * (s_fx[t] + (G)j), beta);
+                if (CWX) {
+#pragma unroll
+                    for (int p = 0; p < NP; ++p)
+                        s_cwx[(size_t)v * NP + p] =
+                            cscale(REC ? s_cs[b][t * kCsw + p] : s_c[REC ? 0 : p][REC ? 0 : t], ex);
+                } else {
+                    s_wx[CWX ? 0 : t * kWpad + j] = ex;
+                }
+                s_wy[v] = es_k<G>(two_over_w * (s_fy[t] + (G)j), beta);   // v = t * w + j
             }
             if (NZ > 1) {
                 for (int v = threadIdx.x; v < n * NZ; v += kGatherThreads) {
@@ -482,12 +497,64 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
             // 3. each warp adds the sources of its patch list into its lanes' columns
             const int cnt = s_cnt[warp];
             const int lx16 = gx - x0 + 16, ly16 = gy - y0 + 16;
-            for (int e = 0; e < cnt; ++e) {
+            if (CWX) {
+                // 2-D: acc_p += psi_y(dy) (c_p psi_x(dx)), the weighted strengths of footprint column dx.
+                // Four list entries per round, without branches (a lane outside a footprint adds a zero
+                // weight times a valid table entry), so that their shared-memory loads overlap.
+                cpx<G> acc2[NP];   // a second set of sums for alternate entries (independent FMA chains)
+#pragma unroll
+                for (int p = 0; p < NP; ++p) acc2[p] = cmk<G>((G)0, (G)0);
+                auto one = [&](int ent, cpx<G> *sum) {
+                    const int t = ent & 0xff;
+                    const unsigned dx = (unsigned)(lx16 - ((ent >> 8) & 0xff)), dy = (unsigned)(ly16 - (ent >> 16));
+                    const bool in = dx < (unsigned)w && dy < (unsigned)w;
+                    const int cx = in ? (int)dx : 0, cy = in ? (int)dy : 0;
+                    const G wy = in ? s_wy[t * w + cy] : (G)0;
+                    const cpx<G> *cw = s_cwx + ((size_t)t * w + cx) * NP;
+                    cpx<G> v[NP];
+                    if (NP == 4 && sizeof(G) == 4) {
+                        const float4 a = *reinterpret_cast<const float4 *>(cw);
+                        const float4 c = *reinterpret_cast<const float4 *>(cw + 2);
+                        v[0] = cmk<G>((G)a.x, (G)a.y);
+                        v[NP > 1 ? 1 : 0] = cmk<G>((G)a.z, (G)a.w);
+                        v[NP > 2 ? 2 : 0] = cmk<G>((G)c.x, (G)c.y);
+                        v[NP > 3 ? 3 : 0] = cmk<G>((G)c.z, (G)c.w);
+                    } else {
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) v[p] = cw[p];
+                    }
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        sum[p].x += wy * v[p].x;
+                        sum[p].y += wy * v[p].y;
+                    }
+                };
+                cpx<G> acc1[NP];
+#pragma unroll
+                for (int p = 0; p < NP; ++p) acc1[p] = acc[p][0];
+                int e = 0;
+                for (; e + 8 <= cnt; e += 8) {
+                    const int4 qa = *reinterpret_cast<const int4 *>(&s_list[warp][e]);
+                    const int4 qb = *reinterpret_cast<const int4 *>(&s_list[warp][e + 4]);
+                    one(qa.x, acc1);
+                    one(qa.y, acc2);
+                    one(qa.z, acc1);
+                    one(qa.w, acc2);
+                    one(qb.x, acc1);
+                    one(qb.y, acc2);
+                    one(qb.z, acc1);
+                    one(qb.w, acc2);
+                }
+                for (; e < cnt; ++e) one(s_list[warp][e], (e & 1) ? acc2 : acc1);
+#pragma unroll
+                for (int p = 0; p < NP; ++p) acc[p][0] = cadd(acc1[p], acc2[p]);
+            }
+            for (int e = 0; !CWX && e < cnt; ++e) {
                 const int ent = s_list[warp][e];
                 const int t = ent & 0xff;
                 const unsigned dx = (unsigned)(lx16 - ((ent >> 8) & 0xff)), dy = (unsigned)(ly16 - (ent >> 16));
                 if (dx < (unsigned)w && dy < (unsigned)w) {
-                    const G wxy = s_wx[t * kWpad + dx] * s_wy[t * kWpad + dy];
+                    const G wxy = s_wx[CWX ? 0 : t * kWpad + dx] * s_wy[t * w + dy];
                     G wz[NZ];
                     if (NZ > 1) {
 #pragma unroll
@@ -528,13 +595,31 @@ static cudaError_t gather_launch(const int *offsets, const int *cell, const G *f
                                  const SliceGeom &g, const TimeBin &tb, double r0, double r1,
                                  const SrcRec<G> *rec, int *status, cpx<G> *grid, cudaStream_t st)
 {
+    constexpr int kChunkG = sizeof(G) == 8 ? 96 : 128;
+    // dynamic shared memory: the weighted strengths (2-D) and the y kernel values, kChunkG x w each
+    const size_t per_w = (NZ == 1 ? NP * sizeof(cpx<G>) : 0) + sizeof(G);
+    const size_t dyn = (size_t)kChunkG * g.w * per_w;
+    static bool attr_set[64][2] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    const int ri = rec ? 1 : 0;
+    if (!attr_set[dev][ri]) {
+        const void *fn = rec ? (const void *)k_spread_gather<G, NP, NZ, true> : (const void *)k_spread_gather<G, NP, NZ, false>;
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kChunkG * kWmax * per_w));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        attr_set[dev][ri] = true;
+    }
     dim3 blocks((g.dim[0].nf1 + kTileX - 1) / kTileX, (g.dim[1].nf1 + kTileY - 1) / kTileY);
     if (rec)
-        k_spread_gather<G, NP, NZ, true><<<blocks, kGatherThreads, 0, st>>>(offsets, cell, frac, cs, n_src, g, tb,
-                                                                            r0, r1, rec, status, grid);
+        k_spread_gather<G, NP, NZ, true><<<blocks, kGatherThreads, dyn, st>>>(offsets, cell, frac, cs, n_src, g, tb,
+                                                                              r0, r1, rec, status, grid);
     else
-        k_spread_gather<G, NP, NZ, false><<<blocks, kGatherThreads, 0, st>>>(offsets, cell, frac, cs, n_src, g, tb,
-                                                                             r0, r1, rec, status, grid);
+        k_spread_gather<G, NP, NZ, false><<<blocks, kGatherThreads, dyn, st>>>(offsets, cell, frac, cs, n_src, g, tb,
+                                                                               r0, r1, rec, status, grid);
     return cudaGetLastError();
 }
 
