@@ -1,4 +1,4 @@
-"""Autotuner for batched slices: upsampling factor, spreading tile and FFT radix.
+"""Autotuner for batched slices: route, upsampling factor, spreading form, FFT radix and bin shape.
 
 The paper exposes only the tolerance eps; the grid sizes follow from it
 (Eq. 5) once the upsampling factor sigma and the kernel width w are fixed
@@ -16,7 +16,17 @@ Candidates (each meets the slice's transform tolerance by its choice of w):
   * spreading tile: "gather" (32 x 8-cell tiles built from 8 x 4-cell source
     bins, one warp per 8 x 4 patch) or "scatter" (32 x 16-cell tiles, one warp
     per source, shared-memory atomics);
-  * FFT radix cap: 8 or 16 (the largest butterfly held in registers).
+  * FFT radix cap: 8 or 16 (the largest butterfly held in registers);
+  * route (when the tuner is asked to choose it): "auto" (the lattice route of
+    Section 2.2.1 when the array is a lattice and its grid is the smaller,
+    else type-3) or "type3".  By default only "auto": a slice timed alone is
+    not a batch, and measured on the 2,048-slice batch (8 lanes) the slices
+    that timed faster alone on type-3 made the batch 18% slower than on the
+    lattice route, whose smaller kernels overlap better;
+  * bin shape of the per-time source sort (cells of the highest channel's grid
+    per bin): 8 x 4, 4 x 4, 8 x 8 or 16 x 4, tried in a second round for the
+    winner when it is a type-3 plan with the gather spreading (the bins decide
+    how many candidate sources each spreading tile stages).
 
 Classes group slices by precision, antenna count and source-count octave, so
 one measurement covers every slice of similar cost.  The choices are kept in
@@ -37,17 +47,29 @@ class Choice:
     upsampfac: float
     spread: str
     fft_max_radix: int
+    transform: str = "auto"
+    bin_size: tuple = (0, 0)
 
     def plan_kwargs(self) -> dict:
-        return {"upsampfac": self.upsampfac, "spread": self.spread, "fft_max_radix": self.fft_max_radix}
+        return {"upsampfac": self.upsampfac, "spread": self.spread, "fft_max_radix": self.fft_max_radix,
+                "transform": self.transform, "bin_size": tuple(self.bin_size)}
 
 
 DEFAULT = {fv.FV_FP64: Choice(2.0, "gather", 16), fv.FV_MIXED: Choice(2.0, "gather", 8)}
 
+BIN_SHAPES = ((4, 4), (8, 8), (16, 4))
 
-def candidates(precision: int) -> list[Choice]:
+
+def candidates(precision: int, routes=("auto",)) -> list[Choice]:
     sig = (1.25, 2.0) if precision == fv.FV_FP64 else (1.5, 2.0)
-    return [Choice(s, sp, r) for s in sig for sp in ("gather", "scatter") for r in (8, 16)]
+    return [Choice(s, sp, r, tr) for tr in routes for s in sig for sp in ("gather", "scatter") for r in (8, 16)]
+
+
+def bin_candidates(best: Choice) -> list[Choice]:
+    """Second round: other bin shapes for a type-3 plan with the gather spreading."""
+    if best.spread != "gather":
+        return []
+    return [Choice(best.upsampfac, best.spread, best.fft_max_radix, "type3", b) for b in BIN_SHAPES]
 
 
 def class_key(precision: int, n_ant: int, n_src: int) -> str:
@@ -57,12 +79,14 @@ def class_key(precision: int, n_ant: int, n_src: int) -> str:
 
 
 class Autotuner:
-    """Picks a Choice per class by timing; `timer(choice, slice) -> seconds`."""
+    """Picks a Choice per class by timing; `timer(choice, slice)` returns the seconds, or (seconds, route)
+    with the route the plan took ("type3", "lattice", ...)."""
 
-    def __init__(self, timer: Callable | None = None):
+    def __init__(self, timer: Callable | None = None, routes=("auto",)):
         self.table: dict[str, Choice] = {}
         self.timings: dict[str, dict[str, float]] = {}
         self.timer = timer
+        self.routes = tuple(routes)
 
     def choice(self, precision: int, n_ant: int, n_src: int) -> Choice:
         return self.table.get(class_key(precision, n_ant, n_src), DEFAULT[precision])
@@ -78,15 +102,27 @@ class Autotuner:
                 continue
             members = sorted(members, key=lambda s: s.problem.sky.n_src)
             rep = members[len(members) // 2]
-            times = {}
-            for c in candidates(precision_of(rep)):
+            times, routes = {}, {}
+
+            def measure(c):
                 try:
-                    times[c] = self.timer(c, rep)
+                    r = self.timer(c, rep)
                 except fv.FvError:
-                    continue          # a candidate the plan rejects (grid or FFT too large) is skipped
-            if times:
-                self.table[key] = min(times, key=times.get)
-                self.timings[key] = {json.dumps(asdict(c)): t for c, t in times.items()}
+                    return            # a candidate the plan rejects (grid or FFT too large) is skipped
+                times[c], routes[c] = (r[0], r[1]) if isinstance(r, tuple) else (r, c.transform)
+
+            for c in candidates(precision_of(rep), self.routes):
+                measure(c)
+            if not times:
+                continue
+            best = min(times, key=times.get)
+            # "auto" resolves to the lattice route or type-3; only a type-3 winner has bins to tune
+            if routes[best] == "type3":
+                for c in bin_candidates(best):
+                    measure(c)
+                best = min(times, key=times.get)
+            self.table[key] = best
+            self.timings[key] = {json.dumps(asdict(c)): t for c, t in times.items()}
         return self.table
 
     def save(self, path: str) -> None:
@@ -95,7 +131,8 @@ class Autotuner:
 
     def load(self, path: str) -> None:
         with open(path) as f:
-            self.table.update({k: Choice(**v) for k, v in json.load(f).items()})
+            self.table.update({k: Choice(**{**v, "bin_size": tuple(v.get("bin_size", (0, 0)))})
+                               for k, v in json.load(f).items()})
 
 
 def precision_of(bs) -> int:
@@ -128,7 +165,7 @@ def cuda_timer(stream, reps: int = 3, warmup: int = 1):
                 p.run(out)
             e1.record(stream)
             e1.synchronize()
-            return e0.elapsed_time(e1) / 1e3 / reps
+            return e0.elapsed_time(e1) / 1e3 / reps, p.info()["transform"]
         finally:
             p.close()
 

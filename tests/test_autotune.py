@@ -6,14 +6,16 @@ from paper_2506_02130_gb300 import autotune as AT, fv, workloads as W
 
 
 def test_candidates_respect_the_mixed_sigma_floor():
-    mixed = AT.candidates(fv.FV_MIXED)
-    fp64 = AT.candidates(fv.FV_FP64)
+    mixed = AT.candidates(fv.FV_MIXED, ("auto", "type3"))
+    fp64 = AT.candidates(fv.FV_FP64, ("auto", "type3"))
+    assert {c.transform for c in AT.candidates(fv.FV_MIXED)} == {"auto"}
     assert {c.upsampfac for c in mixed} == {1.5, 2.0}
     assert {c.upsampfac for c in fp64} == {1.25, 2.0}
     for cs in (mixed, fp64):
         assert {c.spread for c in cs} == {"gather", "scatter"}
         assert {c.fft_max_radix for c in cs} == {8, 16}
-        assert len(set(cs)) == 8
+        assert {c.transform for c in cs} == {"auto", "type3"}
+        assert len(set(cs)) == 16
 
 
 def test_class_key_groups_by_precision_array_and_octave():
@@ -40,12 +42,13 @@ def test_tuner_takes_the_fastest_candidate_per_class(tmp_path):
         return 1.0 if choice == best else 2.0 + choice.fft_max_radix / 100
 
     slices = _slices()
-    t = AT.Autotuner(timer)
+    t = AT.Autotuner(timer, routes=("auto", "type3"))
     table = t.tune(slices, AT.key_of, AT.precision_of)
     keys = {AT.key_of(s) for s in slices}
     assert set(table) == keys
-    # one representative per class, every candidate tried once on it
-    assert len(calls) == 8 * len(keys)
+    # one representative per class, every candidate tried once on it (no bin round: the winners are not
+    # type-3 gather plans)
+    assert len(calls) == 16 * len(keys)
     for s in slices:
         c = t.choice(AT.precision_of(s), len(s.problem.ant_enu), s.problem.sky.n_src)
         assert c == (AT.Choice(2.0, "scatter", 8) if s.precision == "fp64" else AT.Choice(1.5, "gather", 16))
@@ -84,3 +87,46 @@ def test_batch_workload_shape():
     a, b = sorted(slices, key=lambda s: s.problem.sky.n_src)[:2]
     n = a.problem.sky.n_src
     assert (a.problem.sky.ra == b.problem.sky.ra[:n]).all()
+
+
+def test_bin_shapes_are_tuned_for_a_type3_gather_winner():
+    calls = []
+
+    def timer(choice, bs):
+        calls.append(choice)
+        t = 1.0 if (choice.transform == "type3" and choice.spread == "gather" and choice.fft_max_radix == 8
+                    and choice.upsampfac == 2.0) else 2.0
+        if tuple(choice.bin_size) == (4, 4):
+            t = 0.5
+        return t, ("lattice" if choice.transform == "auto" else "type3")
+
+    slices = [s for s in _slices() if s.precision == "mixed"][:1]
+    t = AT.Autotuner(timer, routes=("auto", "type3"))
+    table = t.tune(slices, AT.key_of, AT.precision_of)
+    (best,) = table.values()
+    assert best == AT.Choice(2.0, "gather", 8, "type3", (4, 4))
+    assert len(calls) == 16 + len(AT.BIN_SHAPES)
+    assert best.plan_kwargs()["bin_size"] == (4, 4)
+
+
+def test_an_auto_winner_that_took_the_lattice_route_gets_no_bin_round():
+    def timer(choice, bs):
+        return (1.0 if choice.transform == "auto" else 2.0), ("lattice" if choice.transform == "auto" else "type3")
+
+    slices = [s for s in _slices() if s.precision == "fp64"][:1]
+    t = AT.Autotuner(timer, routes=("auto", "type3"))
+    (best,) = t.tune(slices, AT.key_of, AT.precision_of).values()
+    assert best.transform == "auto" and tuple(best.bin_size) == (0, 0)
+    assert len(t.timings[AT.key_of(slices[0])]) == 16
+
+
+def test_default_route_set_is_auto_only_and_an_auto_type3_winner_gets_bins():
+    def timer(choice, bs):
+        t = 1.0 if tuple(choice.bin_size) == (8, 8) else 2.0
+        return t, "type3"          # a non-lattice array: auto resolves to type-3
+
+    slices = [s for s in _slices() if s.precision == "mixed"][:1]
+    t = AT.Autotuner(timer)
+    (best,) = t.tune(slices, AT.key_of, AT.precision_of).values()
+    assert tuple(best.bin_size) == (8, 8) and best.transform == "type3"
+    assert len(t.timings[AT.key_of(slices[0])]) == 8 + len(AT.BIN_SHAPES)
