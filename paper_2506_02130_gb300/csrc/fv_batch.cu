@@ -64,7 +64,8 @@ static bool covers(const fv_plan_s::WsNeed &have, const fv_plan_s::WsNeed &need)
 {
     return have.grid >= need.grid && have.bufA >= need.bufA && have.bufB >= need.bufB && have.vu >= need.vu &&
            (!need.tiled || (have.tiled && have.n_src >= need.n_src && have.nb >= need.nb &&
-                            have.frac_per_src >= need.frac_per_src && have.cs_per_src >= need.cs_per_src));
+                            have.frac_per_src >= need.frac_per_src && have.cs_per_src >= need.cs_per_src &&
+                            (have.tc || !need.tc)));
 }
 
 // Enqueue every item on its lane (fork/join around the batch stream).
@@ -238,6 +239,7 @@ fv_status fv_batch_execute(fv_batch_t b, int use_graph)
             need.nb = std::max(need.nb, n.nb);
             need.frac_per_src = std::max(need.frac_per_src, n.frac_per_src);
             need.cs_per_src = std::max(need.cs_per_src, n.cs_per_src);
+            need.tc = need.tc || n.tc;
         }
     }
     if (b->ws.empty() || !covers(b->ws_need, need)) {

@@ -55,6 +55,9 @@ struct DimGeom {
 struct BeamParams {
     int kind;           // 0 gauss, 1 airy, 2 uniform, 3 gridded
     double p0, p1, p2;
+    // the FP32 beam's constant, set on the host with the slice geometry (0: not set, derived from p0, p1):
+    // Gaussian FWHM(nu) nu = p0 p1 (rad Hz); Airy pi D / c (the argument per Hz and per unit sin theta)
+    float pf;
     // gridded beams (Section 2.4, numerical beams): voltage samples [n_freq][n_th][n_ph] on the grid
     // theta_i = i (pi/2) / (n_th - 1) (zenith angle), phi_j = j 2 pi / n_ph (azimuth east of north)
     const void *grid;   // device samples (order 1) or B-spline coefficients (order 3), FP64 if grid_fp64
@@ -67,6 +70,8 @@ struct TimeBin {
     double R[9];            // equatorial -> ENU rotation at this time
     double C[3];            // source centre
     double qscale_top[3];   // grid scale of the top channel
+    double D_top[3];        // target centre of the top channel (prephase D.(s - C))
+    int d;                  // dimensions of the transform
     int nf1_top[3];
     int T[2];               // tile (= bin) size in cells
     int nbx, nby;           // bins per axis
@@ -92,6 +97,9 @@ struct SliceGeom {
     // x and y prescale tables 1/Phihat (grid precision) that the tiled spreading kernels apply when they
     // store each grid cell (the FFT passes then skip them); nullptr: the FFT passes apply them
     const void *pre_x, *pre_y;
+    // kappa / kappa_top of this channel as a float pair (hi + lo): the FP32 grids scale the top channel's
+    // per-time coordinates and prephase by it
+    float rsc_hi, rsc_lo;
     // the plan's channel-major copy of the fluxes, [n_freq][n_src][n_stokes] (flux precision), or nullptr:
     // the caller's [n_stokes][n_src][n_freq]
     const void *flux_t;
@@ -125,11 +133,11 @@ template <> __device__ __forceinline__ float voltage<float>(const BeamParams &b,
 {
     if (b.kind == 0) {
         float theta = atan2f(rho, s2);
-        float fwhm = (float)(b.p0 * b.p1) / nu;
+        float fwhm = (b.pf > 0.0f ? b.pf : (float)(b.p0 * b.p1)) / nu;
         return expf(-2.0f * 0.69314718055994531f * theta * theta / (fwhm * fwhm));
     }
     if (b.kind == 1) {
-        float x = (float)(M_PI * b.p0 / FV_C_LIGHT) * nu * rho;
+        float x = (b.pf > 0.0f ? b.pf : (float)(M_PI * b.p0 / FV_C_LIGHT)) * nu * rho;
         return x < 1e-4f ? 1.0f - 0.125f * x * x : 2.0f * j1f(x) / x;
     }
     return 1.0f;
@@ -231,8 +239,8 @@ __device__ __forceinline__ G beam_voltage(const BeamParams &b, G s0, G s1, G rho
 // unpolarised product A_i A_j I, or the four products of J_i C J_j^dagger with
 // J = A R(az) for Stokes IQUV (A_i = A_j = A for one shared beam).  Beam in the
 // grid precision G.  Returns n_pol.
-template <class G>
-__device__ __forceinline__ int source_strengths(const SliceGeom &g, double s0, double s1, double s2, long n,
+template <class G, class S = double>
+__device__ __forceinline__ int source_strengths(const SliceGeom &g, S s0, S s1, S s2, long n,
                                                 const void *flux, int flux_fp64, long n_src, int n_freq, int f,
                                                 cpx<G> *c)
 {
@@ -303,8 +311,11 @@ cudaError_t launch_spread_direct(const double *e, long n_src, const void *flux, 
 // Per time: rotate, horizon cut and counting sort of the visible sources by
 // top-channel tile.  sdir[3][n_src] and sidx[n_src] hold the sorted visible
 // directions and source indices; offsets[nb] is the visible count.
+// tc (nullable): per sorted source, the top channel's grid coordinates (s - C) qscale_top and prephase
+// D_top.(s - C), computed in FP64 and stored as float pairs, and the direction in FP32:
+// tc[3i] = {qx_hi, qx_lo, qy_hi, qy_lo}, tc[3i+1] = {qz_hi, qz_lo, ph_hi, ph_lo}, tc[3i+2] = {s0, s1, s2, 0}.
 cudaError_t launch_time_binning(const double *e, long n_src, const TimeBin &tb, int *bin_of, int *counts,
-                                int *offsets, int *cursor, double *sdir, int *sidx, cudaStream_t st);
+                                int *offsets, int *cursor, double *sdir, int *sidx, float4 *tc, cudaStream_t st);
 
 // Per slice: strengths with prephase and split grid coordinates of the sorted sources.
 template <class G>

@@ -89,6 +89,7 @@ struct fv_plan_s {
         int *cell = nullptr;
         double *sdir = nullptr;
         void *frac = nullptr, *cs = nullptr;
+        float4 *tc = nullptr;     // per-time coordinate records of the sorted sources (FP32 grids)
     };
     std::vector<Workspace> ws;
     // what one execution workspace must hold for this plan (set by prepare)
@@ -98,6 +99,7 @@ struct fv_plan_s {
         int nb = 0;
         size_t frac_per_src = 0, cs_per_src = 0;       // bytes per source
         bool tiled = false;
+        bool tc = false;                               // per-time coordinate records (48 bytes per source)
     } need;
     int n_streams = 1;
     std::vector<cudaStream_t> sub;       // sub[0] is the plan's stream

@@ -173,6 +173,7 @@ size_t workspace_layout(const fv_plan_s::WsNeed &need, char *base, fv_plan_s::Wo
         // 64 bytes of slack: the band spreader's bulk copies round their ends up to 16 bytes
         o.frac = take(ns * need.frac_per_src + 64);
         o.cs = take(ns * need.cs_per_src + 64);
+        o.tc = need.tc ? (float4 *)take(ns * 3 * sizeof(float4)) : nullptr;
     }
     return off;
 }
@@ -504,6 +505,8 @@ static fv_status prepare(fv_plan_s *p)
     const bool staged = p->spread_method == FV_SPREAD_GATHER;
     p->need.frac_per_src = staged ? 4 * gs : 3 * gs;
     p->need.cs_per_src = staged ? (size_t)staged_cs_stride((int)gs, p->n_pol) * es : (size_t)p->n_pol * es;
+    // FP32 grids take each slice's coordinates and prephase from per-time records (no FP64 per slice)
+    p->need.tc = p->precision == FV_MIXED && p->tiled;
     const size_t bin_bytes = p->tiled ? workspace_layout(p->need, nullptr, nullptr) -
                                             (p->need.grid + p->need.bufA + p->need.bufB + p->need.vu)
                                       : 0;
@@ -519,10 +522,19 @@ static fv_status prepare(fv_plan_s *p)
 
 // Slice geometry of channel f at time t for beam group gr: the group's two beams (Section 2.2.3;
 // one shared beam: opts.beam and A^2).
+// The FP32 beam constant of a beam (Gaussian FWHM(nu) nu; Airy pi D / c).
+static void beam_float_constant(BeamParams &b)
+{
+    b.pf = b.kind == 0 ? (float)(b.p0 * b.p1) : (b.kind == 1 ? (float)(M_PI * b.p0 / FV_C_LIGHT) : 0.0f);
+}
+
 static SliceGeom slice_geom_for(const fv_plan_s *p, int f, int t, const fv_plan_s::BeamGroup &gr)
 {
     SliceGeom g = p->gf[f];
     g.flux_t = p->d_flux_t;
+    const double r = p->gf[f].kappa / p->gf[p->f_top].kappa;
+    g.rsc_hi = (float)r;
+    g.rsc_lo = (float)(r - (double)g.rsc_hi);
     std::memcpy(g.R, &p->Rt[(size_t)t * 9], 9 * sizeof(double));
     if (!p->beams.empty()) {
         g.beam = p->beams[gr.a];
@@ -531,6 +543,8 @@ static SliceGeom slice_geom_for(const fv_plan_s *p, int f, int t, const fv_plan_
     } else {
         g.two_beams = 0;
     }
+    beam_float_constant(g.beam);
+    beam_float_constant(g.beam2);
     return g;
 }
 
@@ -562,7 +576,7 @@ static fv_status run_slices_lattice(fv_plan_s *p, fv_plan_s::Workspace &wk, cuda
             tb.nbx = tb.nby = 1;
             CK(prof_begin(p, PC_BIN, st));
             CK(launch_time_binning(p->d_e, p->n_src, tb, wk.bin_of, wk.counts, wk.offsets, wk.cursor, wk.sdir,
-                                   wk.sidx, st));
+                                   wk.sidx, nullptr, st));
             CK(prof_end(p, (double)p->n_src * 80.0));
             t_binned = t;
         }
@@ -626,8 +640,9 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
     // staged records: one 16- or 32-byte record plus the (padded) strengths per source, read once
     const double cs_staged = staged_cs_stride((int)sizeof(G), p->n_pol) * es;
     const double spread_in_bytes_staged = nvis * (sizeof(SrcRec<G>) + cs_staged);
-    const double prep_bytes_staged = nvis * (24.0 + 4.0 + p->n_stokes * (p->flux_fp64 ? 8.0 : 4.0) +
-                                             sizeof(SrcRec<G>) + cs_staged);
+    const double prep_bytes_staged = nvis * ((p->need.tc && sizeof(G) == 4 ? 48.0 : 24.0) + 4.0 +
+                                             p->n_stokes * (p->flux_fp64 ? 8.0 : 4.0) + sizeof(SrcRec<G>) +
+                                             cs_staged);
     const int nb = p->nbx * p->nby;
     const G *pre = (const G *)p->d_pre;
     const cpx<G> *tw = (const cpx<G> *)p->d_tw;
@@ -646,10 +661,12 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
             tb.T[1] = p->T[1];
             tb.nbx = p->nbx;
             tb.nby = p->nby;
+            tb.d = p->d;
+            for (int i = 0; i < 3; ++i) tb.D_top[i] = p->gf[p->f_top].dim[i].D;
             CK(prof_begin(p, PC_BIN, st));
             CK(launch_time_binning(p->d_e, p->n_src, tb, wk.bin_of, wk.counts, wk.offsets, wk.cursor, wk.sdir,
-                                   wk.sidx, st));
-            CK(prof_end(p, (double)p->n_src * 80.0 + nb * 12.0));
+                                   wk.sidx, sizeof(G) == 4 ? wk.tc : nullptr, st));
+            CK(prof_end(p, (double)p->n_src * 80.0 + nb * 12.0 + (wk.tc ? p->n_src * 0.5 * 48.0 : 0.0)));
             t_binned = t;
         }
         // one transform per beam group: strengths with the group's two beams, targets [u0, u1)
@@ -668,7 +685,11 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
                 const bool staged = p->spread_method == FV_SPREAD_GATHER;
                 SrcRec<G> *rec = (SrcRec<G> *)wk.frac;
                 CK(prof_begin(p, PC_PREP, st));
-                if (staged)
+                if (sizeof(G) == 4 && wk.tc)
+                    CK(launch_prep_tc(wk.tc, wk.sidx, wk.offsets + nb, p->n_src, p->flux, p->flux_fp64, nf, f, g,
+                                      wk.cell, (float *)frac, (cpx<float> *)cs,
+                                      staged ? (SrcRec<float> *)rec : nullptr, st));
+                else if (staged)
                     CK(launch_prep_staged<G>(wk.sdir, wk.sidx, wk.offsets + nb, p->n_src, p->flux, p->flux_fp64, nf,
                                              f, g, rec, cs, st));
                 else
@@ -1015,7 +1036,7 @@ fv_status run_basis(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, cha
         tb.nbx = p->nbx;
         tb.nby = p->nby;
         CK(prof_begin(p, PC_BIN, st));
-        CK(launch_time_binning(p->d_e, p->n_src, tb, wk.bin_of, wk.counts, wk.offsets, wk.cursor, wk.sdir, wk.sidx,
+        CK(launch_time_binning(p->d_e, p->n_src, tb, wk.bin_of, wk.counts, wk.offsets, wk.cursor, wk.sdir, wk.sidx, nullptr,
                                st));
         CK(prof_end(p, (double)p->n_src * 80.0 + nb * 12.0));
         for (const auto &gr : p->groups) {

@@ -136,8 +136,16 @@ __global__ void k_bin_scan(const int *__restrict__ counts, int nb, int *__restri
     if (t == 1023) offsets[nb] = part[1023];
 }
 
+// Two floats hi + lo holding an FP64 value to about 2^-48 of its magnitude.
+__device__ __forceinline__ float2 split_f2(double v)
+{
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+
 __global__ void k_bin_scatter(const double *__restrict__ e, long n_src, TimeBin tb, const int *__restrict__ bin_of,
-                              int *__restrict__ cursor, double *__restrict__ sdir, int *__restrict__ sidx)
+                              int *__restrict__ cursor, double *__restrict__ sdir, int *__restrict__ sidx,
+                              float4 *__restrict__ tc)
 {
     long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (n >= n_src) return;
@@ -153,14 +161,30 @@ __global__ void k_bin_scatter(const double *__restrict__ e, long n_src, TimeBin 
     base = __shfl_sync(grp, base, leader);
     const int pos = base + __popc(grp & ((1u << lane) - 1u));
     const double ex = e[n], ey = e[n_src + n], ez = e[2 * n_src + n];
-    sdir[pos] = tb.R[0] * ex + tb.R[1] * ey + tb.R[2] * ez;
-    sdir[n_src + pos] = tb.R[3] * ex + tb.R[4] * ey + tb.R[5] * ez;
-    sdir[2 * n_src + pos] = tb.R[6] * ex + tb.R[7] * ey + tb.R[8] * ez;
+    const double s[3] = {tb.R[0] * ex + tb.R[1] * ey + tb.R[2] * ez, tb.R[3] * ex + tb.R[4] * ey + tb.R[5] * ez,
+                         tb.R[6] * ex + tb.R[7] * ey + tb.R[8] * ez};
+    sdir[pos] = s[0];
+    sdir[n_src + pos] = s[1];
+    sdir[2 * n_src + pos] = s[2];
     sidx[pos] = (int)n;
+    if (tc) {
+        // the top channel's grid coordinates and prephase, in FP64, kept as float pairs: every channel's
+        // are these times kappa / kappa_top
+        double q[3] = {0.0, 0.0, 0.0}, ph = 0.0;
+        for (int k = 0; k < tb.d; ++k) {
+            const double st = s[k] - tb.C[k];
+            q[k] = st * tb.qscale_top[k];
+            ph += tb.D_top[k] * st;
+        }
+        const float2 qx = split_f2(q[0]), qy = split_f2(q[1]), qz = split_f2(q[2]), pp = split_f2(ph);
+        tc[3 * (size_t)pos] = make_float4(qx.x, qx.y, qy.x, qy.y);
+        tc[3 * (size_t)pos + 1] = make_float4(qz.x, qz.y, pp.x, pp.y);
+        tc[3 * (size_t)pos + 2] = make_float4((float)s[0], (float)s[1], (float)s[2], 0.0f);
+    }
 }
 
 cudaError_t launch_time_binning(const double *e, long n_src, const TimeBin &tb, int *bin_of, int *counts,
-                                int *offsets, int *cursor, double *sdir, int *sidx, cudaStream_t st)
+                                int *offsets, int *cursor, double *sdir, int *sidx, float4 *tc, cudaStream_t st)
 {
     const int nb = tb.nbx * tb.nby;
     cudaError_t err = cudaMemsetAsync(counts, 0, (size_t)nb * sizeof(int), st);
@@ -168,7 +192,8 @@ cudaError_t launch_time_binning(const double *e, long n_src, const TimeBin &tb, 
     if (n_src > 0) k_bin_count<<<(unsigned)((n_src + 255) / 256), 256, 0, st>>>(e, n_src, tb, bin_of, counts);
     k_bin_scan<<<1, 1024, 0, st>>>(counts, nb, offsets, cursor);
     if (n_src > 0)
-        k_bin_scatter<<<(unsigned)((n_src + 255) / 256), 256, 0, st>>>(e, n_src, tb, bin_of, cursor, sdir, sidx);
+        k_bin_scatter<<<(unsigned)((n_src + 255) / 256), 256, 0, st>>>(e, n_src, tb, bin_of, cursor, sdir, sidx,
+                                                                       tc);
     return cudaGetLastError();
 }
 
@@ -246,6 +271,89 @@ __global__ void __launch_bounds__(256) k_prep(const double *__restrict__ sdir, c
             frac[(size_t)k * n_src + i] = fr[k];
         }
     }
+}
+
+// FP32 grids: the same strengths, prephase and grid coordinates from the per-time records tc (see
+// launch_time_binning) without FP64 arithmetic.  Every channel's coordinate and prephase are the top
+// channel's times r = kappa / kappa_top, formed in double-float arithmetic (an exact product by FMA plus
+// the cross terms, about 2^-44 relative); the prephase is reduced by 2 pi split in two floats; the first
+// footprint cell follows from the accurate offset l0 - q, which is brought into [-w/2, 1 - w/2).
+__device__ __forceinline__ float2 mul_df(float ah, float al, float bh, float bl)
+{
+    const float p = ah * bh;
+    const float e = fmaf(ah, bh, -p) + (ah * bl + al * bh);
+    return make_float2(p, e);
+}
+
+template <bool STAGED>
+__global__ void __launch_bounds__(256) k_prep_tc(const float4 *__restrict__ tc, const int *__restrict__ sidx,
+                                                 const int *__restrict__ nv_ptr, long n_src,
+                                                 const void *__restrict__ flux, int flux_fp64, int n_freq, int f,
+                                                 SliceGeom g, int *__restrict__ cell, float *__restrict__ frac,
+                                                 cpx<float> *__restrict__ cs, SrcRec<float> *__restrict__ rec)
+{
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= *nv_ptr) return;
+    const float4 a = tc[3 * i], b = tc[3 * i + 1], sd = tc[3 * i + 2];
+    const long n = sidx[i];
+    cpx<float> c[4];
+    const int np = source_strengths<float, float>(g, sd.x, sd.y, sd.z, n, flux, flux_fp64, n_src, n_freq, f, c);
+    // prephase r ph_top, reduced to about [-pi, pi]: 2 pi = 6.2831855 - 1.7484555e-7
+    const float2 ph = mul_df(g.rsc_hi, g.rsc_lo, b.z, b.w);
+    const float k = rintf(ph.x * 0.15915494f);
+    const float phr = fmaf(-k, -1.7484555e-7f, fmaf(-k, 6.2831855f, ph.x)) + ph.y;
+    float sp, cp;
+    sincosf(phr, &sp, &cp);
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+        if (p < np)
+            cs[STAGED ? (size_t)i * staged_cs_stride(4, np) + p : (size_t)p * n_src + i] = cmul(c[p], cmk<float>(cp, sp));
+    int ci[3] = {0, 0, 0};
+    float fr[3] = {0.0f, 0.0f, 0.0f};
+    const float hw = 0.5f * (float)g.w;
+#pragma unroll
+    for (int k3 = 0; k3 < 3; ++k3) {
+        if (k3 < g.d) {
+            const float qh = k3 == 0 ? a.x : (k3 == 1 ? a.z : b.x), ql = k3 == 0 ? a.y : (k3 == 1 ? a.w : b.y);
+            const float2 q = mul_df(g.rsc_hi, g.rsc_lo, qh, ql);
+            float l0 = ceilf(q.x - hw);
+            float o = (l0 - q.x) - q.y;                 // l0 - q
+            if (o >= 1.0f - hw) { l0 -= 1.0f; o -= 1.0f; }
+            else if (o < -hw) { l0 += 1.0f; o += 1.0f; }
+            ci[k3] = (int)l0 + g.dim[k3].nf1 / 2;
+            fr[k3] = o;
+            const int hi = g.dim[k3].nf1 - g.w;
+            if (ci[k3] < 0) { fr[k3] -= (float)ci[k3]; ci[k3] = 0; }
+            else if (ci[k3] > hi) { fr[k3] -= (float)(ci[k3] - hi); ci[k3] = hi; }
+        }
+    }
+    if (STAGED) {
+        SrcRec<float> h;
+        h.cell = (unsigned)ci[0] | ((unsigned)ci[1] << 14) | ((unsigned)ci[2] << 28);
+        h.fx = fr[0];
+        h.fy = fr[1];
+        h.fz = fr[2];
+        rec[i] = h;
+    } else {
+        for (int k3 = 0; k3 < 3; ++k3) {
+            cell[(size_t)k3 * n_src + i] = ci[k3];
+            frac[(size_t)k3 * n_src + i] = fr[k3];
+        }
+    }
+}
+
+cudaError_t launch_prep_tc(const float4 *tc, const int *sidx, const int *nv_ptr, long n_src, const void *flux,
+                           int flux_fp64, int n_freq, int f, const SliceGeom &g, int *cell, float *frac,
+                           cpx<float> *cs, SrcRec<float> *rec, cudaStream_t st)
+{
+    if (n_src <= 0) return cudaSuccess;
+    const unsigned nb = (unsigned)((n_src + 255) / 256);
+    if (rec)
+        k_prep_tc<true><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cell, frac, cs, rec);
+    else
+        k_prep_tc<false><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cell, frac, cs,
+                                             rec);
+    return cudaGetLastError();
 }
 
 template <class G>
@@ -477,10 +585,23 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
                 const int j = v - t * w;
                 const G ex = es_k<G>(two_over_w * (s_fx[t] + (G)j), beta);
                 if (CWX) {
+                    cpx<G> cw[NP];
 #pragma unroll
                     for (int p = 0; p < NP; ++p)
-                        s_cwx[(size_t)v * NP + p] =
-                            cscale(REC ? s_cs[b][t * kCsw + p] : s_c[REC ? 0 : p][REC ? 0 : t], ex);
+                        cw[p] = cscale(REC ? s_cs[b][t * kCsw + p] : s_c[REC ? 0 : p][REC ? 0 : t], ex);
+                    if (NP == 4 && sizeof(G) == 4) {
+                        // entry v holds two 16-byte halves, stored swapped when bit 2 of v is set: the eight
+                        // consecutive entries one list entry's lanes read then fall on distinct banks
+                        const int sw = (v >> 2) & 1;
+                        float4 *dst = reinterpret_cast<float4 *>(s_cwx + (size_t)v * NP);
+                        dst[sw] = make_float4((float)cw[0].x, (float)cw[0].y, (float)cw[NP > 1 ? 1 : 0].x,
+                                              (float)cw[NP > 1 ? 1 : 0].y);
+                        dst[sw ^ 1] = make_float4((float)cw[NP > 2 ? 2 : 0].x, (float)cw[NP > 2 ? 2 : 0].y,
+                                                  (float)cw[NP > 3 ? 3 : 0].x, (float)cw[NP > 3 ? 3 : 0].y);
+                    } else {
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) s_cwx[(size_t)v * NP + p] = cw[p];
+                    }
                 } else {
                     s_wx[CWX ? 0 : t * kWpad + j] = ex;
                 }
@@ -510,11 +631,13 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
                     const bool in = dx < (unsigned)w && dy < (unsigned)w;
                     const int cx = in ? (int)dx : 0, cy = in ? (int)dy : 0;
                     const G wy = in ? s_wy[t * w + cy] : (G)0;
-                    const cpx<G> *cw = s_cwx + ((size_t)t * w + cx) * NP;
+                    const int ve = t * w + cx;
+                    const cpx<G> *cw = s_cwx + (size_t)ve * NP;
                     cpx<G> v[NP];
                     if (NP == 4 && sizeof(G) == 4) {
-                        const float4 a = *reinterpret_cast<const float4 *>(cw);
-                        const float4 c = *reinterpret_cast<const float4 *>(cw + 2);
+                        const int sw = (ve >> 2) & 1;   // the halves' swizzle (see the table's stores)
+                        const float4 a = reinterpret_cast<const float4 *>(cw)[sw];
+                        const float4 c = reinterpret_cast<const float4 *>(cw)[sw ^ 1];
                         v[0] = cmk<G>((G)a.x, (G)a.y);
                         v[NP > 1 ? 1 : 0] = cmk<G>((G)a.z, (G)a.w);
                         v[NP > 2 ? 2 : 0] = cmk<G>((G)c.x, (G)c.y);

@@ -45,4 +45,10 @@ cudaError_t launch_prep_staged(const double *sdir, const int *sidx, const int *n
                                const void *flux, int flux_fp64, int n_freq, int f, const SliceGeom &g,
                                SrcRec<G> *rec, cpx<G> *cs, cudaStream_t st);
 
+// FP32 grids: the same, from the per-time records tc of launch_time_binning (no FP64 arithmetic); writes
+// staged records when rec is given, else cell[3][n] / frac[3][n] / cs[n_pol][n].
+cudaError_t launch_prep_tc(const float4 *tc, const int *sidx, const int *nv_ptr, long n_src, const void *flux,
+                           int flux_fp64, int n_freq, int f, const SliceGeom &g, int *cell, float *frac,
+                           cpx<float> *cs, SrcRec<float> *rec, cudaStream_t st);
+
 }  // namespace fv
