@@ -21,6 +21,7 @@ import dataclasses
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -59,11 +60,18 @@ def parse():
                     help="hex127: route of the timed plan (type3: the type-3 NUFFT of every slice)")
     ap.add_argument("--no-lattice-route", action="store_true",
                     help="hex127: skip timing the lattice route (Section 2.2.1 with height terms) beside it")
+    ap.add_argument("--heights", default="auto", choices=["auto", "grid", "terms"],
+                    help="up axis of a non-coplanar array on the type-3 route (the headline plan)")
+    ap.add_argument("--no-heights-route", action="store_true",
+                    help="skip the height-terms vs three-dimensional-grid comparison (non-coplanar arrays)")
     ap.add_argument("--no-basis-route", action="store_true",
                     help="hex127: skip timing the spectral-basis route (Appendix A) beside it")
     ap.add_argument("--basis-terms", type=int, default=0,
                     help="hex127: basis functions K of the spectral-basis route (0: chosen by the plan from "
                          "the sky's spectra against eps)")
+    ap.add_argument("--channels", type=int, default=0,
+                    help="hex350/hex127: keep this many channels across the same band (0 = all; a smaller case "
+                         "of the same kernels for profiling, not a bench line)")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--leg-requests", type=int, default=200,
                     help="hex350: requests of the serving leg run beside the headline")
@@ -594,12 +602,24 @@ SIM = {
 }
 
 
-def sim_problem(name, seed):
+def sim_problem(name, seed, n_chan=0):
+    """The workload's problem; n_chan > 0 keeps n_chan channels across the same band (a smaller case of
+    the same per-slice kernels, for profiling)."""
     import numpy as np
     from paper_2506_02130_gb300 import workloads as W
+    kw = {"n_chan": n_chan} if n_chan > 0 else {}
     if name == "hex350":
-        return W.config_hex350_pol(seed=seed, dtype=np.float32)
-    return W.config_hex127(seed=seed)
+        return W.config_hex350_pol(seed=seed, dtype=np.float32, **kw)
+    return W.config_hex127(seed=seed, **kw)
+
+
+def sim_workload(args):
+    """The workload's entry of SIM, renamed when --channels shrinks it."""
+    wl = dict(SIM[args.workload])
+    if args.channels > 0:
+        wl["name"] = re.sub(r"_\d+ch_", "_%dch_" % args.channels, wl["name"])
+        wl["what"] += "; reduced to %d channels across the same band" % args.channels
+    return wl
 
 
 class OracleSampler:
@@ -698,19 +718,19 @@ def run_sim(args, rank, world, local, dist):
         raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    wl = SIM[args.workload]
+    wl = sim_workload(args)
     precision = fv.FV_MIXED if args.precision == "mixed" else fv.FV_FP64
     eps = 1e-6 if precision == fv.FV_MIXED else 1e-11
     t_setup = time.perf_counter()
     # each rank simulates its own independent problem (weak scaling)
-    prob = sim_problem(args.workload, (2 if args.workload == "hex350" else 1) + rank)
+    prob = sim_problem(args.workload, (2 if args.workload == "hex350" else 1) + rank, args.channels)
     nf, nt = len(prob.freqs_hz), len(prob.lsts_rad)
     sampler = OracleSampler(prob, wl["oracle_bl"])
     # a dedicated stream: the plan runs on it and the timing events are recorded on it
     stream = torch.cuda.Stream(device=dev)
     plan = fv.Plan.from_problem(prob, precision=precision, eps=eps, stream=stream.cuda_stream, device=local,
                                 n_streams=args.streams, spread=args.spread, transform=args.transform,
-                                fft_max_radix=args.fft_radix,
+                                fft_max_radix=args.fft_radix, heights=args.heights,
                                 n_basis=args.basis_terms if args.transform == "basis" else 0)
     fdt = torch.float32 if precision == fv.FV_MIXED else torch.float64
     cdt = torch.complex64 if precision == fv.FV_MIXED else torch.complex128
@@ -832,6 +852,23 @@ def run_sim(args, rank, world, local, dist):
                           "what": "same workload, plan with transform=lattice (type-1 transforms on the "
                                   "horizontal lattice, heights by Chebyshev terms)"})
 
+    # ---- the up axis of a non-coplanar array on the type-3 route: Chebyshev height terms on a 2-D grid
+    # against the third grid dimension (Section 2.2.2), same workload, both timed like the headline
+    hts = None
+    nonplanar = bool(np.any(prob.ant_enu[:, 2] != prob.ant_enu[0, 2]))
+    if args.transform == "type3" and not args.no_heights_route and nonplanar:
+        hts = {"what": "same workload on the type-3 route: heights=terms (K two-dimensional transforms of "
+                       "c T_q(u), Bessel-weighted per target) against heights=grid (a three-dimensional grid)"}
+        for key, h in (("heights_terms", "terms"), ("heights_grid", "grid")):
+            try:
+                leg, hi = route_leg(key, transform="type3", heights=h)
+                leg.update({"dims": hi["dims"], "height_terms": hi["height_terms"], "nf1_max": hi["nf1_max"]})
+            except fv.FvError as e:
+                leg = {"unavailable": str(e)}
+            hts[h] = leg
+        if "ms_per_step" in hts["terms"] and "ms_per_step" in hts["grid"]:
+            hts["speedup_terms_over_grid"] = hts["grid"]["ms_per_step"] / hts["terms"]["ms_per_step"]
+
     # ---- the spectral-basis route (Appendix A; scalar skies only)
     bas_route = None
     if args.transform == "type3" and not args.no_basis_route and not prob.polarized:
@@ -926,7 +963,7 @@ def run_sim(args, rank, world, local, dist):
             "config": {"workload": wl["name"], "what": wl["what"], "n_ant": int(len(prob.ant_enu)),
                        "n_bl": info["n_bl"], "n_unique_targets": info["n_unique"], "n_freq": nf, "n_time": nt,
                        "n_pol": 4 if prob.polarized else 1,
-                       "n_src": int(prob.sky.n_src), "dims": info["dims"], "precision": args.precision,
+                       "n_src": int(prob.sky.n_src), "dims": info["dims"], "height_terms": info["height_terms"], "precision": args.precision,
                        "eps": eps, "kernel_width": info["kernel_width"], "upsampfac": info["upsampfac"],
                        "nf1_max": info["nf1_max"], "nf2_max": info["nf2_max"],
                        "streams": args.streams or (4 if args.transform == "basis" else 8),
@@ -941,6 +978,7 @@ def run_sim(args, rank, world, local, dist):
                                 "min": lat[0], "max": lat[-1]},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": gpu_launches,
             "rel_l2_vs_oracle_sample": err, "fp64_plain_equal_accuracy": fp64, "lattice_route": lat_route,
+            "heights_route": hts,
             "basis_route": bas_route, "serving": serving_leg, "batching": batch_leg,
             "kernels": {k: {"ms_per_step": v["ms"], "launches_per_step": v["launches"],
                             "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}

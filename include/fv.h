@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define FV_ABI_VERSION 4
+#define FV_ABI_VERSION 5
 
 typedef struct fv_plan_s *fv_plan_t;   /* opaque plan handle; owns its device memory */
 
@@ -111,7 +111,36 @@ typedef struct {
                                  basis); ignored by the other routes */
     int bin_size[2];          /* cells of the highest channel's grid per bin of the per-time source sort
                                  in x and y; 0 = 8 x 4; 1 <= each <= 64 */
+    int heights;              /* fv_heights: how the type-3 route evaluates the up axis of a
+                                 non-coplanar array (one whose baselines have b_up != 0) */
 } fv_opts;
+
+/* Up axis of a non-coplanar array on the type-3 route (Section 2.2.2 treats it
+ * as the third dimension of the transform).  For arrays that are nearly flat
+ * the height factor of a slice factorises:
+ *   exp(-i k b_up n) = exp(-i k b_up C) exp(-i a u),  u = (n - C) / S,
+ *   a = k b_up S,  k = 2 pi nu / c,
+ * with n the up component of a source direction and C, S the centre and
+ * half-extent of the visible sources' n (fv_info.src_centre[2],
+ * src_halfwidth[2]).  Expanding exp(-i a u) = sum_q eps_q (-i)^q J_q(a) T_q(u)
+ * (eps_0 = 1, else 2) and keeping the K terms whose tail bound
+ * 2 sum_{q>=K} (|a|/2)^q / q! at the top channel and largest |b_up| is below
+ * eps / 10 turns a slice into K two-dimensional transforms of the strengths
+ * c T_q(u) that share their sources and targets; each target sums them with
+ * its own weights exp(-i k b_up C) eps_q (-i)^q J_q(a).
+ * FV_HEIGHTS_AUTO takes the height terms when K is at most the number of up
+ * planes the three-dimensional grid of the top channel needs and the gather
+ * spreading can hold K planes (n_pol K <= 32 complex sums a lane in FP32, 16
+ * in FP64, K <= 16); FV_HEIGHTS_TERMS asks for them (fv_set_sky returns
+ * FV_ERR_UNSUPPORTED where they cannot be used: K > 16, too many sums a lane,
+ * or spread_method other than AUTO or GATHER; the call that completes the
+ * plan, fv_set_sky or fv_set_array, decides); FV_HEIGHTS_GRID keeps the
+ * three-dimensional grid.  fv_info.height_terms reports K (0: not taken). */
+typedef enum {
+    FV_HEIGHTS_AUTO = 0,
+    FV_HEIGHTS_GRID = 1,
+    FV_HEIGHTS_TERMS = 2
+} fv_heights;
 
 /* Transform choice (Section 2.2.1).  When the antennas' horizontal positions
  * sit on a lattice x_0 + k_1 a_1 + k_2 a_2 (integer k), every baseline is
@@ -262,7 +291,7 @@ const char *fv_last_error(fv_plan_t p);
 
 /* Read-only plan geometry for tests, logs and the autotuner. */
 typedef struct {
-    int dims;             /* 2 or 3 */
+    int dims;             /* 2 or 3: dimensions of the type-3 transform (2 with height terms) */
     int kernel_width;     /* w */
     double beta;          /* ES shape parameter */
     double upsampfac;     /* sigma */
@@ -285,6 +314,9 @@ typedef struct {
     int basis_grid[3];    /* spectral-basis route: the one spreading grid of a time, per dim */
     double basis_fit_error;   /* automatic K: the estimated relative error of the basis spectra at
                                  the chosen K; -1 otherwise */
+    int height_terms;     /* type-3 route of a non-coplanar array: Chebyshev terms K of the height
+                             factor (fv_heights), 0 where the up axis is a grid dimension or absent;
+                             dims is then 2 */
 } fv_info;
 
 fv_status fv_get_info(fv_plan_t p, fv_info *info);

@@ -103,7 +103,76 @@ struct SliceGeom {
     // the plan's channel-major copy of the fluxes, [n_freq][n_src][n_stokes] (flux precision), or nullptr:
     // the caller's [n_stokes][n_src][n_freq]
     const void *flux_t;
+    // Chebyshev height terms of a non-coplanar array on a two-dimensional grid (0: none): dim[2].nf1 = K
+    // planes; a source's term argument is u = (n - hc) / hs (n its up component), a target's weights
+    // follow from k b_up (height_weight)
+    int K;
+    double hc, hs;
+    float hc_f, hs_inv_f;
 };
+
+// J_q(x) by its power series sum_m (-1)^m (x/2)^(2m+q) / (m! (m+q)!) (FP64; |x| is a few units at most here,
+// so the terms fall fast and do not cancel badly)
+__device__ __forceinline__ double bessel_jq(int q, double x, double rel_tol = 1e-18)
+{
+    const double h = 0.5 * x;
+    double term = 1.0;
+    for (int k = 1; k <= q; ++k) term *= h / k;
+    double sum = term;
+    const double h2 = h * h;
+    for (int m = 1; m < 80; ++m) {
+        term *= -h2 / ((double)m * (double)(m + q));
+        sum += term;
+        if (fabs(term) <= rel_tol * fabs(sum)) break;
+    }
+    return sum;
+}
+
+// Weight of height term q of the target with up baseline component b_up (m):
+//   exp(-i k b_up hc) eps_q (-i)^q J_q(k b_up hs),  k = 2 pi nu / c,
+// so that sum_q weight_q T_q((n - hc) / hs) = exp(-i k b_up n) (Jacobi-Anger).
+template <class G>
+__device__ __forceinline__ cpx<G> height_weight(const SliceGeom &g, double b_up, int q)
+{
+    const double a = g.kappa * b_up;
+    if (sizeof(G) == 4 && fabs(a * g.hs) <= 2.0) {
+        // FP32 grids, |a hs| <= 2: every term of the series is below the first, so FP32 arithmetic keeps
+        // its 7 digits; the phase a hc is reduced to [-pi, pi] in FP64 first
+        const float x = (float)(a * g.hs), h = 0.5f * x;
+        float term = 1.0f;
+        for (int k = 1; k <= q; ++k) term *= h / (float)k;
+        float sum = term;
+        const float h2 = h * h;
+        for (int m = 1; m < 24; ++m) {
+            term *= -h2 / ((float)m * (float)(m + q));
+            sum += term;
+            if (fabsf(term) <= 1e-8f * fabsf(sum)) break;
+        }
+        double ph = a * g.hc;
+        ph -= 6.283185307179586476925 * rint(ph * 0.15915494309189533577);
+        float sb, cb;
+        sincosf((float)ph, &sb, &cb);
+        const float j = (q == 0 ? 1.0f : 2.0f) * sum;
+        float re = cb * j, im = -sb * j;
+        for (int k = 0; k < (q & 3); ++k) {
+            const float t = re;
+            re = im;
+            im = -t;
+        }
+        return cmk<G>((G)re, (G)im);
+    }
+    // FP32 grids keep about 7 digits: the series stops at 1e-10 relative there
+    const double j = (q == 0 ? 1.0 : 2.0) * bessel_jq(q, a * g.hs, sizeof(G) == 4 ? 1e-10 : 1e-18);
+    double sb, cb;
+    sincos(a * g.hc, &sb, &cb);
+    double re = cb * j, im = -sb * j;                  // exp(-i a hc) eps_q J_q
+    for (int k = 0; k < (q & 3); ++k) {                // times (-i)^q
+        const double t = re;
+        re = im;
+        im = -t;
+    }
+    return cmk<G>((G)re, (G)im);
+}
 
 // Position of Stokes parameter k of source n at channel f in the fluxes a slice reads (flux_index) and
 // the array it is in: the channel-major copy when there is one (one channel's Stokes values of a

@@ -383,7 +383,9 @@ cudaError_t launch_interp(const cpx<G> *band, const double *bu, int n_u, const d
 //     K(l_z) = sum_{m_z} phi((2/w)(p_z - m_z)) e^{2 pi i l_z m_z / M_z},
 // so the band after the x and y passes, [b_y][b_x][pol][l_z], is read with
 // the z prescale folded into K.  One warp per target: the lanes split the
-// w x w footprint in (y, x) and reduce with shuffles.
+// w x w footprint in (y, x) and reduce with shuffles.  With height terms
+// (g.K > 0) the band's l_z are the terms q and K(q) is the target's weight of
+// term q (height_weight): the same sum.
 template <class G, bool HASZ>
 __global__ void __launch_bounds__(256) k_interp_zdirect(const cpx<G> *__restrict__ band, const double *__restrict__ bu,
                                                         int n_u, const double *__restrict__ dec, SliceGeom g,
@@ -413,7 +415,9 @@ __global__ void __launch_bounds__(256) k_interp_zdirect(const cpx<G> *__restrict
     const int Nz = HASZ ? g.dim[2].nf1 : 1;
     // lane lz < Nz builds K(l_z); the vector is then shared through shuffles
     cpx<G> Kmine = cmk<G>((G)1, (G)0);
-    if (HASZ && lane < Nz) {
+    if (HASZ && lane < Nz && g.K) {
+        Kmine = height_weight<G>(g, bu[3 * u + 2], lane);     // height terms: the target's weights
+    } else if (HASZ && lane < Nz) {
         const int Mz = g.dim[2].M;
         const int lc = lane - Nz / 2;
         cpx<G> acc = cmk<G>((G)0, (G)0);
@@ -429,9 +433,12 @@ __global__ void __launch_bounds__(256) k_interp_zdirect(const cpx<G> *__restrict
         }
         Kmine = cscale(acc, prez[lane]);
     }
+    // the vector in registers: loops over it are unrolled to the largest Nz (16) with a guard, so that it is
+    // never indexed dynamically
     cpx<G> K[HASZ ? 16 : 1];
     if (HASZ) {
-        for (int lz = 0; lz < Nz; ++lz) {
+#pragma unroll
+        for (int lz = 0; lz < 16; ++lz) {
             K[lz].x = __shfl_sync(0xffffffffu, Kmine.x, lz);
             K[lz].y = __shfl_sync(0xffffffffu, Kmine.y, lz);
         }
@@ -461,13 +468,18 @@ __global__ void __launch_bounds__(256) k_interp_zdirect(const cpx<G> *__restrict
                 if (!HASZ) {
                     s = c[0];
                 } else if (vec2) {
-                    for (int lz = 0; lz < Nz; lz += 2) {
-                        cpx<G> v0, v1;
-                        load_pair(c + lz, v0, v1);
-                        s = cadd(s, cadd(cmul(v0, K[lz]), cmul(v1, K[lz + 1])));
+#pragma unroll
+                    for (int lz = 0; lz < (HASZ ? 16 : 1); lz += 2) {
+                        if (lz < Nz) {
+                            cpx<G> v0, v1;
+                            load_pair(c + lz, v0, v1);
+                            s = cadd(s, cadd(cmul(v0, K[lz]), cmul(v1, K[lz + 1])));
+                        }
                     }
                 } else {
-                    for (int lz = 0; lz < Nz; ++lz) s = cadd(s, cmul(c[lz], K[lz]));
+#pragma unroll
+                    for (int lz = 0; lz < (HASZ ? 16 : 1); ++lz)
+                        if (lz < Nz) s = cadd(s, cmul(c[lz], K[lz]));
                 }
                 acc[2 * p] += wt * s.x;
                 acc[2 * p + 1] += wt * s.y;
@@ -528,11 +540,13 @@ __global__ void __launch_bounds__(256) k_interp_zrow(const cpx<float> *__restric
             fr[i] = (float)(p - m);
         }
     }
-    const int Nz = g.d == 3 ? g.dim[2].nf1 : 1;
+    const int Nz = g.d == 3 || g.K ? g.dim[2].nf1 : 1;     // up planes or height terms
     const int L = Nz / 2;                    // lanes per footprint cell
     // K(l_z) for l_z = lane < Nz, as in k_interp_zdirect
     cpx<float> Kmine = cmk<float>(1.0f, 0.0f);
-    if (lane < Nz) {
+    if (lane < Nz && g.K) {
+        Kmine = height_weight<float>(g, bu[3 * u + 2], lane);
+    } else if (lane < Nz) {
         const int Mz = g.dim[2].M;
         const int lc = lane - Nz / 2;
         cpx<float> acc = cmk<float>(0.0f, 0.0f);
@@ -643,7 +657,9 @@ __global__ void __launch_bounds__(kIbThreads) k_interp_batch(const cpx<G> *__res
         }
         s_bx[tl] = m0[0] + g.dim[0].H;
         s_by[tl] = m0[1] + g.dim[1].H;
-        if (ZROW) {
+        if (ZROW && g.K) {
+            // height terms: the weights are computed by all threads below
+        } else if (ZROW) {
             const int Nz = g.dim[2].nf1, Mz = g.dim[2].M;
             G phz[kIbMaxW];
 #pragma unroll
@@ -678,6 +694,15 @@ __global__ void __launch_bounds__(kIbThreads) k_interp_batch(const cpx<G> *__res
             post = cmk<double>(cp * dec[u], sp * dec[u]);
         }
         s_post[tl] = post;
+    }
+    if (ZROW && g.K) {
+        // height weights of the CTA's targets, one (target, term) pair per thread and round
+        const int Nz = g.dim[2].nf1;
+        for (int idx = threadIdx.x; idx < kIbTargets * Nz; idx += kIbThreads) {
+            const int tl = idx / Nz, lz = idx - tl * Nz;
+            const long u = u0 + tl;
+            s_K[ZROW ? tl : 0][ZROW ? lz : 0] = u < n_u ? height_weight<G>(g, bu[3 * u + 2], lz) : cmk<G>((G)0, (G)0);
+        }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -873,7 +898,7 @@ __global__ void __launch_bounds__(256) k_interp_warp(const cpx<G> *__restrict__ 
 
 static bool zrow_fits(const SliceGeom &g, int elem_bytes)
 {
-    if (elem_bytes != 4 || g.d != 3 || g.n_pol != 1) return false;
+    if (elem_bytes != 4 || (g.d != 3 && g.K == 0) || g.n_pol != 1) return false;
     const int Nz = g.dim[2].nf1;
     return Nz >= 2 && Nz % 2 == 0 && g.w * (Nz / 2) <= 32;
 }
@@ -884,11 +909,11 @@ cudaError_t launch_interp_zdirect(const cpx<G> *band, const double *bu, int n_u,
                                   cudaStream_t st)
 {
     if (n_u <= 0) return cudaSuccess;
-    if (g.d == 3 && g.dim[2].nf1 > 16) return cudaErrorInvalidValue;
+    if ((g.d == 3 || g.K) && g.dim[2].nf1 > 16) return cudaErrorInvalidValue;
     long threads = (long)n_u * 32;
     const unsigned ib_blocks = (unsigned)((n_u + kIbTargets - 1) / kIbTargets);
     if (g.w <= kIbMaxW) {
-        if (g.d == 2) {
+        if (g.d == 2 && g.K == 0) {
             // one warp per target, 8 per CTA
             const unsigned wb = (unsigned)((n_u + 7) / 8);
             if (g.n_pol == 4)
@@ -909,7 +934,7 @@ cudaError_t launch_interp_zdirect(const cpx<G> *band, const double *bu, int n_u,
             }
         }
     }
-    if (g.d == 3)
+    if (g.d == 3 || g.K)
         k_interp_zdirect<G, true><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(band, bu, n_u, dec, g, prez, twz,
                                                                                      Vu);
     else

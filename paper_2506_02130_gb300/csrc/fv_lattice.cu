@@ -350,22 +350,6 @@ cudaError_t launch_gather_lattice(const cpx<G> *band, const int *bln, const int 
     return cudaGetLastError();
 }
 
-// J_q(x) by its power series sum_m (-1)^m (x/2)^(2m+q) / (m! (m+q)!) (FP64; |x| is small here)
-__device__ double bessel_j_series(int q, double x)
-{
-    const double h = 0.5 * x;
-    double term = 1.0;
-    for (int k = 1; k <= q; ++k) term *= h / k;
-    double sum = term;
-    const double h2 = h * h;
-    for (int m = 1; m < 80; ++m) {
-        term *= -h2 / ((double)m * (double)(m + q));
-        sum += term;
-        if (fabs(term) <= 1e-18 * fabs(sum)) break;
-    }
-    return sum;
-}
-
 __global__ void k_lattice_wterms(const double *__restrict__ b_up, int n_bl, int K, double kappa,
                                  cpx<double> *__restrict__ wq)
 {
@@ -374,7 +358,7 @@ __global__ void k_lattice_wterms(const double *__restrict__ b_up, int n_bl, int 
     const long b = i / K;
     const int q = (int)(i - b * K);
     const double beta = 0.5 * kappa * b_up[b];
-    const double j = (q == 0 ? 1.0 : 2.0) * bessel_j_series(q, beta);
+    const double j = (q == 0 ? 1.0 : 2.0) * bessel_jq(q, beta);
     double sb, cb;
     sincos(beta, &sb, &cb);
     cpx<double> f = cmk<double>(cb * j, -sb * j);          // e^{-i beta} eps_q J_q

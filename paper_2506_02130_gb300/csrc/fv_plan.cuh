@@ -20,6 +20,13 @@ struct fv_plan_s {
     BeamParams beam{};
     int polarized = 0, n_pol = 1;
     int dims_req = 0;
+    // up axis of a non-coplanar array (fv_opts.heights): the array's dimension (3 if any b_up != 0), the
+    // Chebyshev height terms the type-3 route takes (0: none; the transform is then d_array-dimensional)
+    // and the dimension the per-target deconvolution table was computed for
+    int heights_req = 0;
+    int d_array = 2;
+    int hK = 0;
+    int dec_d = 0;
     double sigma = 2.0;
     int w = 0;
     double beta = 0.0;

@@ -240,16 +240,17 @@ static void resolve_spread(fv_plan_s *p, int gs, int w)
         p->qscale_top[i] = p->gf[p->f_top].dim[i].qscale;
         p->nf1_top[i] = p->gf[p->f_top].dim[i].nf1;
     }
-    const int nzm = p->d == 3 ? p->nf1_max[2] : 1;
+    const int nzm = p->d == 3 ? p->nf1_max[2] : (p->hK > 0 ? p->hK : 1);
     int nz_t = 0, bx = 8, by = 4;
     const bool gather_ok = spread_gather_config(gs, p->n_pol, nzm, w, &nz_t, &bx, &by) != 0;
     const bool scatter_ok = spread_scatter_smem(gs, p->n_pol, nzm) <= FV_SPREAD_SMEM_MAX && w <= 32;
     // FP64 tiles of 16 height planes hold 16 double-complex accumulators per lane: measured slower than
     // the other methods for the per-channel slices, so auto takes them only where nothing else exists
-    const bool gather_auto = gather_ok && !(gs == 8 && nz_t == 16);
+    const bool gather_auto = gather_ok && !(gs == 8 && nz_t > 8);
     int m = p->spread_req;
     if (m == FV_SPREAD_AUTO)
         m = gather_auto ? FV_SPREAD_GATHER : (scatter_ok ? FV_SPREAD_SCATTER : FV_SPREAD_ATOMIC);
+    if (p->hK > 0) m = FV_SPREAD_GATHER;    // the height terms are spread by the gather kernel only (checked)
     if (m == FV_SPREAD_GATHER && !gather_ok) m = FV_SPREAD_ATOMIC;
     if (m == FV_SPREAD_SCATTER && !scatter_ok) m = FV_SPREAD_ATOMIC;
     p->spread_method = m;
@@ -308,7 +309,7 @@ static fv_status prepare_lattice(fv_plan_s *p)
     }
     lg.K = K;
     const DimGeom *top = p->gf[p->f_top].dim;
-    const long t3 = (long)top[0].nf1 * top[1].nf1 * (p->d == 3 ? top[2].nf1 : 1);
+    const long t3 = (long)top[0].nf1 * top[1].nf1 * top[2].nf1;     // up planes or height terms included
     if (K > 24) {
         if (p->transform_req == FV_TRANSFORM_LATTICE)
             return p->fail(FV_ERR_UNSUPPORTED, "the lattice route would need " + std::to_string(K) +
@@ -401,8 +402,77 @@ static fv_status dim_geometry(fv_plan_s *p, double X, double S, DimGeom &dg)
 
 static fv_status prepare_basis(fv_plan_s *p);
 
+// Height terms (fv_heights) of a non-coplanar array on the type-3 route: K from the tail bound of the
+// Jacobi-Anger expansion at the top channel and the largest |b_up|, taken where the options allow it and
+// the gather spreading can hold K planes (automatic: where K is at most the up planes of the top channel's
+// three-dimensional grid).  Sets p->d (2 with height terms, else the array's) and p->hK, and recomputes
+// the per-target deconvolution table when its dimension changes.
+static fv_status choose_heights(fv_plan_s *p)
+{
+    p->d = p->d_array;
+    p->hK = 0;
+    const bool asked = p->heights_req == FV_HEIGHTS_TERMS;
+    const bool may = asked || (p->heights_req == FV_HEIGHTS_AUTO && p->dims_req == 0);
+    if (p->d_array == 3 && may && !p->use_basis) {
+        const int nf = (int)p->freq.size();
+        int f_top = 0;
+        for (int f = 1; f < nf; ++f)
+            if (p->freq[f] > p->freq[f_top]) f_top = f;
+        double bup_max = 0.0;
+        for (int u = 0; u < p->n_u; ++u) bup_max = std::max(bup_max, std::fabs(p->bu[3 * (size_t)u + 2]));
+        const double kappa_top = 2.0 * M_PI * p->freq[f_top] / FV_C_LIGHT;
+        const double a = kappa_top * bup_max * p->S[2];
+        // smallest K with 2 sum_{q>=K} (a/2)^q / q! <= eps / 10 (|J_q(a)| <= (a/2)^q / q!)
+        int K = 1;
+        if (a > 0.0) {
+            const double h = 0.5 * a;
+            for (K = 1; K <= 64; ++K) {
+                double term = 1.0, tail = 0.0;
+                for (int q = 1; q <= K; ++q) term *= h / q;
+                for (int q = K; q < K + 60; ++q) {
+                    tail += term;
+                    term *= h / (q + 1);
+                }
+                if (2.0 * tail <= 0.1 * p->eps) break;
+            }
+        }
+        // FP32 grids of one product: an even K (one more term where the bound gives an odd one), so that the
+        // interpolation reads the terms of a footprint cell in pairs
+        if (p->precision == FV_MIXED && p->n_pol == 1 && K > 1 && (K & 1)) ++K;
+        const int gs = p->precision == FV_FP64 ? (int)sizeof(double) : (int)sizeof(float);
+        int nzt = 0, bx = 0, by = 0;
+        const bool fits = K <= 16 && spread_gather_config(gs, p->n_pol, K, p->w, &nzt, &bx, &by) != 0 &&
+                          (p->spread_req == FV_SPREAD_AUTO || p->spread_req == FV_SPREAD_GATHER);
+        if (asked && !fits)
+            return p->fail(FV_ERR_UNSUPPORTED, "heights = FV_HEIGHTS_TERMS: " + std::to_string(K) +
+                                                   " height terms do not fit the gather spreading (at most 16, "
+                                                   "n_pol K complex sums a lane within its budget, spread_method "
+                                                   "AUTO or GATHER)");
+        bool take = fits;
+        if (take && !asked) {
+            // the up planes the three-dimensional grid of the top channel would take
+            DimGeom dz{};
+            const fv_status ds = dim_geometry(p, kappa_top * p->bhalf[2], p->S[2], dz);
+            take = ds != FV_OK || K <= dz.nf1;
+            p->err.clear();
+        }
+        if (take) {
+            p->d = 2;
+            p->hK = K;
+        }
+    }
+    if (p->dec_d != p->d && p->n_u > 0) {
+        CK(launch_target_deconv(p->d_bu, p->n_u, p->d, p->bcen, p->bhalf, p->w, p->beta, p->sigma, p->d_glx,
+                                p->d_glw, p->nq, p->d_dec, p->stream));
+        p->dec_d = p->d;
+    }
+    return FV_OK;
+}
+
 static fv_status prepare(fv_plan_s *p)
 {
+    const fv_status hs = choose_heights(p);
+    if (hs != FV_OK) return hs;
     if (p->use_basis) return prepare_basis(p);
     const int nf = (int)p->freq.size();
     const int w = p->w;
@@ -423,10 +493,17 @@ static fv_status prepare(fv_plan_s *p)
         g.polarized = p->polarized;
         g.n_stokes = p->n_stokes;
         g.beam = p->beam;
+        g.K = p->hK;
+        g.hc = p->C[2];
+        g.hs = p->S[2] > 0.0 ? p->S[2] : 1.0;
+        g.hc_f = (float)g.hc;
+        g.hs_inv_f = (float)(1.0 / g.hs);
         for (int i = 0; i < 3; ++i) {
             DimGeom &dg = g.dim[i];
             if (i >= p->d) {
-                dg.nf1 = 1; dg.M = 1; dg.B = 1; dg.H = 0; dg.qscale = 0; dg.pscale = 0; dg.D = 0; dg.C = 0;
+                // no grid dimension: one plane, or the K planes of the height terms
+                dg.nf1 = i == 2 && p->hK > 0 ? p->hK : 1;
+                dg.M = 1; dg.B = 1; dg.H = 0; dg.qscale = 0; dg.pscale = 0; dg.D = 0; dg.C = 0;
                 dg.nstages = 0;
                 continue;
             }
@@ -456,6 +533,7 @@ static fv_status prepare(fv_plan_s *p)
     // a new sky with the same grid sizes (the usual case: same array, same channels) keeps the
     // tables and workspaces of the previous one
     std::vector<long> sig = {(long)p->n_src, (long)p->n_pol, (long)p->n_streams, (long)p->spread_req, (long)p->d,
+                             (long)p->hK,
                              (long)grid_e, (long)bufA_e, (long)bufB_e, (long)p->lat_ok, (long)p->lat_H[0],
                              (long)p->lat_H[1], (long)p->n_u, (long)p->n_bl};
     for (int k = 0; k < 4; ++k) {
@@ -1218,6 +1296,7 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
     if (o->spread_method < FV_SPREAD_AUTO || o->spread_method > FV_SPREAD_ATOMIC) return bad("unknown spread_method");
     if (o->bin_size[0] < 0 || o->bin_size[0] > 64 || o->bin_size[1] < 0 || o->bin_size[1] > 64)
         return bad("bin_size must be 0 or in [1, 64]");
+    if (o->heights < FV_HEIGHTS_AUTO || o->heights > FV_HEIGHTS_TERMS) return bad("heights must be 0, 1 or 2");
     if (o->n_streams < 0) return bad("n_streams < 0");
     if (o->fft_max_radix != 0 && o->fft_max_radix != 8 && o->fft_max_radix != 16) return bad("fft_max_radix must be 0, 8 or 16");
     if (o->transform < FV_TRANSFORM_AUTO || o->transform > FV_TRANSFORM_BASIS) return bad("unknown transform");
@@ -1304,6 +1383,7 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
     p->spread_req = o->spread_method;
     p->bin_req[0] = o->bin_size[0];
     p->bin_req[1] = o->bin_size[1];
+    p->heights_req = o->heights;
     // radix 8 needs fewer registers (more CTAs per SM), which wins in FP32; FP64 uses the same
     // register count either way and prefers fewer stages
     p->fft_max_radix = o->fft_max_radix > 0 ? o->fft_max_radix : (o->precision == FV_MIXED ? 8 : 16);
@@ -1455,6 +1535,8 @@ static fv_status setup_array(fv_plan_s *p)
     p->n_bl = n_bl;
     p->n_u = (int)(bu.size() / 3);
     p->d = d;
+    p->d_array = d;
+    p->hK = 0;
     p->bu.swap(bu);
     p->bl2u.swap(bl2u);
     p->groups.swap(groups);
@@ -1488,6 +1570,7 @@ static fv_status setup_array(fv_plan_s *p)
     }
     CK(launch_target_deconv(p->d_bu, p->n_u, p->d, p->bcen, p->bhalf, p->w, p->beta, p->sigma, p->d_glx, p->d_glw,
                             p->nq, p->d_dec, p->stream));
+    p->dec_d = p->d;
     CK(cudaStreamSynchronize(p->stream));
     p->have_array = true;
     if (p->have_sky) return prepare(p);
@@ -1830,7 +1913,7 @@ fv_status fv_get_info(fv_plan_t p, fv_info *info)
 {
     if (!p || !info) return FV_ERR_ARG;
     std::memset(info, 0, sizeof(*info));
-    info->dims = p->d;
+    info->dims = p->use_lattice ? p->d_array : p->d;
     info->kernel_width = p->w;
     info->beta = p->beta;
     info->upsampfac = p->sigma;
@@ -1847,6 +1930,7 @@ fv_status fv_get_info(fv_plan_t p, fv_info *info)
     info->transform = p->use_basis ? FV_TRANSFORM_BASIS : (p->use_lattice ? FV_TRANSFORM_LATTICE : FV_TRANSFORM_TYPE3);
     info->basis_terms = p->use_basis ? p->n_basis : 0;
     info->basis_fit_error = p->use_basis && p->n_basis_req == 0 ? p->basis_fit_err : -1.0;
+    info->height_terms = p->use_lattice || p->use_basis ? 0 : p->hK;
     for (int i = 0; i < 3; ++i) info->basis_grid[i] = p->use_basis ? p->bg.dim[i].nf1 : 0;
     info->lattice = p->lat_ok ? 1 : 0;
     for (int k = 0; k < 2; ++k) {

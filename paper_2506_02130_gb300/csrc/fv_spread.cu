@@ -258,6 +258,7 @@ __global__ void __launch_bounds__(256) k_prep(const double *__restrict__ sdir, c
             }
         }
     }
+    if (g.K) fr[2] = (G)((s2 - g.hc) / g.hs);     // height terms: the argument u of T_q (no up grid axis)
     if (STAGED) {
         SrcRec<G> h;
         h.cell = (unsigned)ci[0] | ((unsigned)ci[1] << 14) | ((unsigned)ci[2] << 28);
@@ -327,6 +328,7 @@ __global__ void __launch_bounds__(256) k_prep_tc(const float4 *__restrict__ tc, 
             else if (ci[k3] > hi) { fr[k3] -= (float)(ci[k3] - hi); ci[k3] = hi; }
         }
     }
+    if (g.K) fr[2] = (sd.z - g.hc_f) * g.hs_inv_f;    // height terms: the argument u of T_q
     if (STAGED) {
         SrcRec<float> h;
         h.cell = (unsigned)ci[0] | ((unsigned)ci[1] << 14) | ((unsigned)ci[2] << 28);
@@ -395,9 +397,9 @@ constexpr int kTileX = 32, kTileY = 8;      // one CTA (4 x 2 patches)
 constexpr int kPatches = 8;
 
 // resident CTAs per SM the register allocation must allow without spills (fewer when the complex
-// accumulators of a lane take 128 registers: 32 in FP32, 16 in FP64)
+// accumulators of a lane take 48 registers or more: 24 complex sums in FP32, 12 in FP64)
 template <class G, int NP, int NZ> struct GatherMinBlocks {
-    static constexpr int value = NP * NZ * (int)sizeof(G) >= 128 ? 2 : 4;
+    static constexpr int value = NP * NZ * (int)sizeof(G) >= 96 ? 2 : 4;
 };
 
 // REC: the candidates come as staged records (rec[i], strengths cs[i * stride + p], written by
@@ -438,7 +440,7 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
     __shared__ __align__(16) int s_list[kPatches][kGatherChunk];
     __shared__ int s_cnt[kPatches];
     __shared__ int s_row0[32], s_pre[32], s_total;
-    const int nx = g.dim[0].nf1, ny = g.dim[1].nf1, nz = g.d == 3 ? g.dim[2].nf1 : 1;
+    const int nx = g.dim[0].nf1, ny = g.dim[1].nf1, nz = g.d == 3 || g.K ? g.dim[2].nf1 : 1;
     const int w = g.w;
     const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -543,7 +545,7 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
                     cy = (int)((rr.cell >> 14) & 0x3fffu);
                     s_fx[t] = rr.fx;
                     s_fy[t] = rr.fy;
-                    if (g.d == 3) {
+                    if (g.d == 3 || g.K) {
                         s_cz[NZ > 1 ? t : 0] = (int)(rr.cell >> 28);
                         s_fz[NZ > 1 ? t : 0] = rr.fz;
                     }
@@ -559,7 +561,7 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
                     cy = cell[n_src + i];
                     s_fx[t] = frac[i];
                     s_fy[t] = frac[n_src + i];
-                    if (g.d == 3) {
+                    if (g.d == 3 || g.K) {
                         s_cz[NZ > 1 ? t : 0] = cell[2 * n_src + i];
                         s_fz[NZ > 1 ? t : 0] = frac[2 * n_src + i];
                     }
@@ -607,7 +609,21 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
                 }
                 s_wy[v] = es_k<G>(two_over_w * (s_fy[t] + (G)j), beta);   // v = t * w + j
             }
-            if (NZ > 1) {
+            if (NZ > 1 && g.K) {
+                // height terms: plane q takes T_q(u) (three-term recurrence), zero for q >= K
+                for (int t = threadIdx.x; t < n; t += kGatherThreads) {
+                    const G u = s_fz[t];
+                    G tm = (G)1, tq = u;
+                    s_wz[t][0] = (G)1;
+#pragma unroll
+                    for (int q = 1; q < NZ; ++q) {
+                        s_wz[t][q] = q < g.K ? tq : (G)0;
+                        const G tn = (G)2 * u * tq - tm;
+                        tm = tq;
+                        tq = tn;
+                    }
+                }
+            } else if (NZ > 1) {
                 for (int v = threadIdx.x; v < n * NZ; v += kGatherThreads) {
                     const int t = v / NZ, z = v % NZ;
                     const int jz = z - s_cz[t];
@@ -749,7 +765,7 @@ static cudaError_t gather_launch(const int *offsets, const int *cell, const G *f
 int spread_gather_config(int elem_bytes, int n_pol, int nz, int w, int *nz_tmpl, int *bin_x, int *bin_y)
 {
     if (w > kWmax) return 0;
-    const int NZ = nz <= 1 ? 1 : (nz <= 8 ? 8 : (nz <= 16 ? 16 : 0));
+    const int NZ = nz <= 1 ? 1 : (nz <= 8 ? 8 : (nz <= 12 ? 12 : (nz <= 16 ? 16 : 0)));
     if (NZ == 0) return 0;
     const int budget = elem_bytes == 4 ? 32 : 16;       // complex accumulators per lane
     if (n_pol * NZ > budget) return 0;
@@ -765,7 +781,7 @@ static cudaError_t gather_dispatch(const int *offsets, const int *cell, const G 
                                    const SliceGeom &g, const TimeBin &tb, double r0, double r1, const SrcRec<G> *rec,
                                    int *status, cpx<G> *grid, cudaStream_t st)
 {
-    const int nz = g.d == 3 ? g.dim[2].nf1 : 1;
+    const int nz = g.d == 3 || g.K ? g.dim[2].nf1 : 1;     // up planes or height terms
     int NZ = 0, bx = 0, by = 0;
     if (!spread_gather_config(sizeof(G), g.n_pol, nz, g.w, &NZ, &bx, &by)) return cudaErrorInvalidValue;
     const int key = (g.n_pol == 4 ? 100 : 0) + NZ;
@@ -773,6 +789,7 @@ static cudaError_t gather_dispatch(const int *offsets, const int *cell, const G 
     switch (key) {
     case 1: return gather_launch<G, 1, 1>(FV_GATHER_ARGS);
     case 8: return gather_launch<G, 1, 8>(FV_GATHER_ARGS);
+    case 12: return gather_launch<G, 1, 12>(FV_GATHER_ARGS);
     case 16: return gather_launch<G, 1, 16>(FV_GATHER_ARGS);
     case 101: return gather_launch<G, 4, 1>(FV_GATHER_ARGS);
     case 108:

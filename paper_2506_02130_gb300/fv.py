@@ -21,13 +21,14 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfftvis_gb300.so")
 
-ABI_VERSION = 4          # FV_ABI_VERSION of include/fv.h that the structs below mirror
+ABI_VERSION = 5          # FV_ABI_VERSION of include/fv.h that the structs below mirror
 FV_OK, FV_ERR_ARG, FV_ERR_OOM, FV_ERR_CUDA, FV_ERR_STATE, FV_ERR_TIMEOUT, FV_ERR_UNSUPPORTED = range(7)
 FV_FP64, FV_MIXED = 0, 1
 SPREAD = {"auto": 0, "gather": 1, "scatter": 2, "atomic": 3}
 BEAMS = {"gauss": 0, "airy": 1, "uniform": 2, "grid": 3}
 TRANSFORMS = {"auto": 0, "type3": 1, "lattice": 2, "basis": 3}
 TRANSFORM_NAMES = {0: "auto", 1: "type3", 2: "lattice", 3: "basis"}
+HEIGHTS = {"auto": 0, "grid": 1, "terms": 2}
 STATUS_NAMES = {0: "FV_OK", 1: "FV_ERR_ARG", 2: "FV_ERR_OOM", 3: "FV_ERR_CUDA", 4: "FV_ERR_STATE",
                 5: "FV_ERR_TIMEOUT", 6: "FV_ERR_UNSUPPORTED"}
 
@@ -47,7 +48,8 @@ class fv_opts(C.Structure):
                 ("kernel_width", C.c_int), ("cuda_stream", C.c_void_p), ("device", C.c_int),
                 ("n_streams", C.c_int), ("spread_method", C.c_int), ("fft_max_radix", C.c_int),
                 ("transform", C.c_int), ("lattice_tol_m", C.c_double), ("n_basis", C.c_int),
-                ("bin_size", C.c_int * 2)]
+                ("bin_size", C.c_int * 2),
+                ("heights", C.c_int)]
 
 
 class fv_info(C.Structure):
@@ -58,7 +60,8 @@ class fv_info(C.Structure):
                 ("transform", C.c_int), ("lattice", C.c_int), ("lattice_modes", C.c_int * 2),
                 ("lattice_grid", C.c_int * 2), ("lattice_terms", C.c_int), ("lattice_basis", C.c_double * 4),
                 ("beam_groups", C.c_int), ("basis_terms", C.c_int), ("basis_grid", C.c_int * 3),
-                ("basis_fit_error", C.c_double)]
+                ("basis_fit_error", C.c_double),
+                ("height_terms", C.c_int)]
 
 
 PROFILE_CLASSES = 12
@@ -215,7 +218,8 @@ def fv_get_info(plan) -> dict:
             "lattice_modes": list(i.lattice_modes), "lattice_grid": list(i.lattice_grid),
             "lattice_terms": i.lattice_terms, "beam_groups": i.beam_groups,
             "lattice_basis": list(i.lattice_basis), "basis_terms": i.basis_terms,
-            "basis_grid": list(i.basis_grid), "basis_fit_error": i.basis_fit_error}
+            "basis_grid": list(i.basis_grid), "basis_fit_error": i.basis_fit_error,
+            "height_terms": i.height_terms}
 
 
 def fv_profile_enable(plan, enable: bool = True) -> None:
@@ -306,7 +310,7 @@ class Plan:
     def create(cls, freqs_hz, lsts_rad, latitude_rad, beam="gauss", beam_param=(), precision=FV_FP64,
                eps=1e-10, polarized=False, dims=0, upsampfac=0.0, kernel_width=0, stream=None, device=-1,
                n_streams=0, spread="auto", fft_max_radix=0, transform="auto", lattice_tol_m=0.0, n_basis=0,
-               bin_size=(0, 0)):
+               bin_size=(0, 0), heights="auto"):
         o = fv_opts_default()
         freqs = np.ascontiguousarray(freqs_hz, dtype=np.float64)
         lsts = np.ascontiguousarray(lsts_rad, dtype=np.float64)
@@ -336,6 +340,7 @@ class Plan:
         o.lattice_tol_m = lattice_tol_m
         o.n_basis = n_basis
         o.bin_size[0], o.bin_size[1] = int(bin_size[0]), int(bin_size[1])
+        o.heights = HEIGHTS[heights]
         h = fv_plan(o)
         return cls(h, len(freqs), len(lsts), 0, 4 if polarized else 1, precision)
 

@@ -38,11 +38,11 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_defaults(lib):
-    assert lib.fv_abi_version() == 4
+    assert lib.fv_abi_version() == 5
     o = fv.fv_opts_default()
     assert o.precision == fv.FV_FP64 and o.eps == 1e-10 and o.upsampfac == 2.0 and o.device == -1
     assert o.transform == 0 and o.lattice_tol_m == 0.0
-    assert list(o.bin_size) == [0, 0] and o.spread_method == 0
+    assert list(o.bin_size) == [0, 0] and o.spread_method == 0 and o.heights == 0
     assert abs(o.beam_param[0] - np.radians(10)) < 1e-15 and o.beam_param[1] == 150e6
 
 
@@ -63,7 +63,7 @@ def _opts(**kw):
                                 dict(transform=3, n_basis=-1), dict(transform=3, n_basis=2),
                                 dict(lattice_tol_m=-1.0), dict(spread_method=4),
                                 dict(bin_size=(C.c_int * 2)(0, 65)),
-                                dict(bin_size=(C.c_int * 2)(-2, 4))])
+                                dict(bin_size=(C.c_int * 2)(-2, 4)), dict(heights=3), dict(heights=-1)])
 def test_invalid_options_rejected_before_device(lib, kw):
     o, keep = _opts(**kw)
     h = C.c_void_p()

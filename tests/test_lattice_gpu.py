@@ -66,7 +66,7 @@ def test_height_terms_on_a_jittered_lattice_match_oracle_and_type3(precision):
     assert info["lattice_terms"] > 1
     ref = oracle_vis(OracleProblem.from_workload(prob))
     assert rel_l2(out, ref) <= TOL[precision]
-    t3, info3 = _run(prob, precision, "type3")
+    t3, info3 = _run(prob, precision, "type3", heights="grid")
     assert info3["dims"] == 3
     assert rel_l2(out, t3) <= 2 * TOL[precision]
 

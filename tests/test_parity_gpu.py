@@ -50,11 +50,14 @@ def test_hex37_one_slice(precision):
     assert err <= TOL[precision], err
 
 
+@pytest.mark.parametrize("heights", ["grid", "terms"])
 @pytest.mark.parametrize("precision", [fv.FV_FP64, fv.FV_MIXED])
-def test_non_coplanar_multichannel_point_plus_diffuse(precision):
+def test_non_coplanar_multichannel_point_plus_diffuse(precision, heights):
+    """The up axis as a third grid dimension, or as Chebyshev height terms on a 2-D grid."""
     prob = small_3d()
-    out, info = run_gpu(prob, precision)
-    assert info["dims"] == 3
+    out, info = run_gpu(prob, precision, transform="type3", heights=heights)
+    assert info["dims"] == (3 if heights == "grid" else 2)
+    assert (info["height_terms"] > 0) == (heights == "terms")
     ref = oracle(prob)
     err = rel_l2(out, ref)
     assert err <= TOL[precision], err
