@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target oracle CPU time for the baseline")
     ap.add_argument("--streams", type=int, default=0, help="execution streams per plan (0 = library default)")
-    ap.add_argument("--spread", default="auto", choices=["auto", "gather", "scatter", "atomic"])
+    ap.add_argument("--spread", default="auto", choices=["auto", "gather", "scatter", "atomic", "tensor"])
     ap.add_argument("--fft-radix", type=int, default=0, choices=[0, 8, 16],
                     help="largest FFT stage radix of the timed plan (0: the library default)")
     ap.add_argument("--fp64-eps", type=float, default=1e-6,

@@ -206,7 +206,11 @@ typedef enum {
     FV_SPREAD_GATHER = 1,     /* per-tile, each thread sums the sources covering its cells; the tile's
                                  sorted sources are staged in shared memory by bulk asynchronous copies */
     FV_SPREAD_SCATTER = 2,    /* per-tile, warps add each source's footprint with shared atomics */
-    FV_SPREAD_ATOMIC = 3      /* one thread per source, global atomics on a cleared grid */
+    FV_SPREAD_ATOMIC = 3,     /* one thread per source, global atomics on a cleared grid */
+    FV_SPREAD_TENSOR = 4      /* the gather with each warp's 8 x 8 block of cells summed on the tensor
+                                 cores (m16n8k8 TF32 products, three-term split for FP32 accuracy);
+                                 FV_MIXED two-dimensional grids without height terms, n_pol 1 or 4;
+                                 elsewhere it falls back to FV_SPREAD_GATHER */
 } fv_spread_method;
 
 /* Fill *o with defaults: FV_FP64, eps 1e-10, Gaussian beam 10 deg at 150 MHz,
@@ -317,6 +321,7 @@ typedef struct {
     int height_terms;     /* type-3 route of a non-coplanar array: Chebyshev terms K of the height
                              factor (fv_heights), 0 where the up axis is a grid dimension or absent;
                              dims is then 2 */
+    int spread_method;    /* type-3 route: the fv_spread_method the slices use (AUTO resolved) */
 } fv_info;
 
 fv_status fv_get_info(fv_plan_t p, fv_info *info);

@@ -247,9 +247,14 @@ static void resolve_spread(fv_plan_s *p, int gs, int w)
     // FP64 tiles of 16 height planes hold 16 double-complex accumulators per lane: measured slower than
     // the other methods for the per-channel slices, so auto takes them only where nothing else exists
     const bool gather_auto = gather_ok && !(gs == 8 && nz_t > 8);
+    // the tensor-core gather: FP32 two-dimensional grids without height terms
+    const bool tensor_ok = gather_ok && gs == 4 && p->d == 2 && p->hK == 0 && (p->n_pol == 1 || p->n_pol == 4) &&
+                           w <= kTcWmax && p->precision == FV_MIXED;
     int m = p->spread_req;
+    if (m == FV_SPREAD_TENSOR && !tensor_ok) m = FV_SPREAD_GATHER;
     if (m == FV_SPREAD_AUTO)
-        m = gather_auto ? FV_SPREAD_GATHER : (scatter_ok ? FV_SPREAD_SCATTER : FV_SPREAD_ATOMIC);
+        m = tensor_ok ? FV_SPREAD_TENSOR
+                      : (gather_auto ? FV_SPREAD_GATHER : (scatter_ok ? FV_SPREAD_SCATTER : FV_SPREAD_ATOMIC));
     if (p->hK > 0) m = FV_SPREAD_GATHER;    // the height terms are spread by the gather kernel only (checked)
     if (m == FV_SPREAD_GATHER && !gather_ok) m = FV_SPREAD_ATOMIC;
     if (m == FV_SPREAD_SCATTER && !scatter_ok) m = FV_SPREAD_ATOMIC;
@@ -580,8 +585,8 @@ static fv_status prepare(fv_plan_s *p)
     p->need.nb = p->nbx * p->nby;
     // the gather spreading reads staged records: 16 (FP32) or 32 (FP64) bytes per source where the split
     // coordinates take 12 or 24, and strengths padded to 16 bytes
-    const bool staged = p->spread_method == FV_SPREAD_GATHER;
-    p->need.frac_per_src = staged ? 4 * gs : 3 * gs;
+    const bool staged = p->spread_method == FV_SPREAD_GATHER || p->spread_method == FV_SPREAD_TENSOR;
+    p->need.frac_per_src = p->spread_method == FV_SPREAD_TENSOR ? sizeof(TcRec) : (staged ? 4 * gs : 3 * gs);
     p->need.cs_per_src = staged ? (size_t)staged_cs_stride((int)gs, p->n_pol) * es : (size_t)p->n_pol * es;
     // FP32 grids take each slice's coordinates and prephase from per-time records (no FP64 per slice)
     p->need.tc = p->precision == FV_MIXED && p->tiled;
@@ -714,13 +719,13 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
     const double nvis = 0.5 * p->n_src;
     const double prep_bytes = nvis * (24.0 + 4.0 + p->n_stokes * (p->flux_fp64 ? 8.0 : 4.0) + 12.0 +
                                       3.0 * sizeof(G) + p->n_pol * es);
-    const double spread_in_bytes = nvis * (12.0 + 3.0 * sizeof(G) + p->n_pol * es);
-    // staged records: one 16- or 32-byte record plus the (padded) strengths per source, read once
+    // staged records: one 16- or 32-byte record (80 bytes with the tensor-core gather's kernel values) plus
+    // the (padded) strengths per source, read once
+    const bool tensor = p->spread_method == FV_SPREAD_TENSOR && sizeof(G) == 4 && p->need.tc;
+    const double rec_bytes = tensor ? (double)sizeof(TcRec) : (double)sizeof(SrcRec<G>);
     const double cs_staged = staged_cs_stride((int)sizeof(G), p->n_pol) * es;
-    const double spread_in_bytes_staged = nvis * (sizeof(SrcRec<G>) + cs_staged);
     const double prep_bytes_staged = nvis * ((p->need.tc && sizeof(G) == 4 ? 48.0 : 24.0) + 4.0 +
-                                             p->n_stokes * (p->flux_fp64 ? 8.0 : 4.0) + sizeof(SrcRec<G>) +
-                                             cs_staged);
+                                             p->n_stokes * (p->flux_fp64 ? 8.0 : 4.0) + rec_bytes + cs_staged);
     const int nb = p->nbx * p->nby;
     const G *pre = (const G *)p->d_pre;
     const cpx<G> *tw = (const cpx<G> *)p->d_tw;
@@ -760,13 +765,14 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
                 G *frac = (G *)wk.frac;
                 cpx<G> *cs = (cpx<G> *)wk.cs;
                 // the gather spreading reads staged records (bulk-copied per chunk)
-                const bool staged = p->spread_method == FV_SPREAD_GATHER;
+                const bool staged = p->spread_method == FV_SPREAD_GATHER || p->spread_method == FV_SPREAD_TENSOR;
                 SrcRec<G> *rec = (SrcRec<G> *)wk.frac;
                 CK(prof_begin(p, PC_PREP, st));
                 if (sizeof(G) == 4 && wk.tc)
                     CK(launch_prep_tc(wk.tc, wk.sidx, wk.offsets + nb, p->n_src, p->flux, p->flux_fp64, nf, f, g,
                                       wk.cell, (float *)frac, (cpx<float> *)cs,
-                                      staged ? (SrcRec<float> *)rec : nullptr, st));
+                                      staged && !tensor ? (SrcRec<float> *)rec : nullptr,
+                                      tensor ? (TcRec *)wk.frac : nullptr, st));
                 else if (staged)
                     CK(launch_prep_staged<G>(wk.sdir, wk.sidx, wk.offsets + nb, p->n_src, p->flux, p->flux_fp64, nf,
                                              f, g, rec, cs, st));
@@ -778,13 +784,19 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
                 g.pre_x = pre + p->pre_off[(size_t)f * 3];         // applied as the tile is stored
                 g.pre_y = pre + p->pre_off[(size_t)f * 3 + 1];
                 CK(prof_begin(p, PC_SPREAD, st));
-                if (p->spread_method == FV_SPREAD_GATHER)
+                if (tensor)
+                    CK(launch_spread_mma(wk.offsets, (const TcRec *)wk.frac, (const cpx<float> *)cs, g, tb, r0, r1,
+                                         p->d_status, (cpx<float> *)grid, st));
+                else if (p->spread_method == FV_SPREAD_GATHER || p->spread_method == FV_SPREAD_TENSOR)
                     CK(launch_spread_gather_rec<G>(wk.offsets, rec, cs, g, tb, r0, r1, p->d_status, grid, st));
                 else if (p->spread_method == FV_SPREAD_SCATTER)
                     CK(launch_spread_scatter<G>(wk.offsets, wk.cell, frac, cs, p->n_src, g, tb, r0, r1, grid, st));
                 else
                     CK(launch_spread_tile<G>(wk.offsets, wk.cell, frac, cs, p->n_src, g, tb, r0, r1, grid, st));
-                CK(prof_end(p, (staged ? spread_in_bytes_staged : spread_in_bytes) + gel * es));
+                // algorithmic bytes of the spreading step, whatever the staging: the visible sources' fluxes
+                // read once and the grid written once (the records and strengths it reads are the prep's
+                // output, counted there)
+                CK(prof_end(p, nvis * p->n_stokes * (p->flux_fp64 ? 8.0 : 4.0) + gel * es));
             } else {
                 CK(prof_begin(p, PC_MEMSET, st));
                 CK(cudaMemsetAsync(grid, 0, gel * sizeof(cpx<G>), st));
@@ -1293,7 +1305,7 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
         return bad("Gaussian beam needs FWHM > 0 and reference frequency > 0");
     if (o->beam == FV_BEAM_AIRY && !(o->beam_param[0] > 0)) return bad("Airy beam needs a diameter > 0");
     if (o->dims != 0 && o->dims != 2 && o->dims != 3) return bad("dims must be 0, 2 or 3");
-    if (o->spread_method < FV_SPREAD_AUTO || o->spread_method > FV_SPREAD_ATOMIC) return bad("unknown spread_method");
+    if (o->spread_method < FV_SPREAD_AUTO || o->spread_method > FV_SPREAD_TENSOR) return bad("unknown spread_method");
     if (o->bin_size[0] < 0 || o->bin_size[0] > 64 || o->bin_size[1] < 0 || o->bin_size[1] > 64)
         return bad("bin_size must be 0 or in [1, 64]");
     if (o->heights < FV_HEIGHTS_AUTO || o->heights > FV_HEIGHTS_TERMS) return bad("heights must be 0, 1 or 2");
@@ -1931,6 +1943,7 @@ fv_status fv_get_info(fv_plan_t p, fv_info *info)
     info->basis_terms = p->use_basis ? p->n_basis : 0;
     info->basis_fit_error = p->use_basis && p->n_basis_req == 0 ? p->basis_fit_err : -1.0;
     info->height_terms = p->use_lattice || p->use_basis ? 0 : p->hK;
+    info->spread_method = p->spread_method;
     for (int i = 0; i < 3; ++i) info->basis_grid[i] = p->use_basis ? p->bg.dim[i].nf1 : 0;
     info->lattice = p->lat_ok ? 1 : 0;
     for (int k = 0; k < 2; ++k) {

@@ -28,64 +28,6 @@
 
 namespace fv {
 
-__device__ __forceinline__ double es_kernel_d(double z, double beta)
-{
-    double t = 1.0 - z * z;
-    return t >= 0.0 ? exp(beta * (sqrt(t) - 1.0)) : 0.0;
-}
-__device__ __forceinline__ float es_kernel_f(float z, float beta)
-{
-    float t = 1.0f - z * z;
-    return t >= 0.0f ? __expf(beta * (sqrtf(t) - 1.0f)) : 0.0f;
-}
-template <class G> __device__ __forceinline__ G es_k(G z, G beta);
-template <> __device__ __forceinline__ double es_k<double>(double z, double beta) { return es_kernel_d(z, beta); }
-template <> __device__ __forceinline__ float es_k<float>(float z, float beta) { return es_kernel_f(z, beta); }
-
-// Bulk asynchronous copies into shared memory, completion counted on an mbarrier (used by the gather
-// kernel's record staging), and the bounded wait on a barrier phase.
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init1(uint64_t *bar)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect(uint64_t *bar, unsigned bytes)
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-// Wait for phase `parity` of *bar for at most about a second; false if the wait ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
-{
-    const long long t0 = clock64();
-    for (;;) {
-        uint32_t ok;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(ok)
-                     : "r"(smem_addr(bar)), "r"(parity)
-                     : "memory");
-        if (ok) return true;
-        if (clock64() - t0 > 2000000000LL) return false;
-    }
-}
-
-__device__ __forceinline__ int top_cell(double q, int nf1)
-{
-    double c = floor(q) + (double)(nf1 / 2);
-    int ci = (int)fmax(0.0, fmin(c, (double)(nf1 - 1)));
-    return ci;
-}
-
 // ------------------------------------------------------------------ per time
 __global__ void k_bin_count(const double *__restrict__ e, long n_src, TimeBin tb, int *__restrict__ bin_of,
                             int *__restrict__ counts)
@@ -286,13 +228,16 @@ __device__ __forceinline__ float2 mul_df(float ah, float al, float bh, float bl)
     return make_float2(p, e);
 }
 
-template <bool STAGED>
+// MODE 0: cell / frac / cs arrays; 1: staged records; 2: tensor-core records (kernel values included)
+template <int MODE>
 __global__ void __launch_bounds__(256) k_prep_tc(const float4 *__restrict__ tc, const int *__restrict__ sidx,
                                                  const int *__restrict__ nv_ptr, long n_src,
                                                  const void *__restrict__ flux, int flux_fp64, int n_freq, int f,
                                                  SliceGeom g, int *__restrict__ cell, float *__restrict__ frac,
-                                                 cpx<float> *__restrict__ cs, SrcRec<float> *__restrict__ rec)
+                                                 cpx<float> *__restrict__ cs, SrcRec<float> *__restrict__ rec,
+                                                 TcRec *__restrict__ trec)
 {
+    constexpr bool STAGED = MODE > 0;
     const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= *nv_ptr) return;
     const float4 a = tc[3 * i], b = tc[3 * i + 1], sd = tc[3 * i + 2];
@@ -329,7 +274,18 @@ __global__ void __launch_bounds__(256) k_prep_tc(const float4 *__restrict__ tc, 
         }
     }
     if (g.K) fr[2] = (sd.z - g.hc_f) * g.hs_inv_f;    // height terms: the argument u of T_q
-    if (STAGED) {
+    if (MODE == 2) {
+        TcRec h;
+        h.cell = (unsigned)ci[0] | ((unsigned)ci[1] << 14);
+        h.pad[0] = h.pad[1] = h.pad[2] = 0u;
+        const float two_over_w = 2.0f / (float)g.w, beta = (float)g.beta;
+#pragma unroll
+        for (int j = 0; j < kTcWmax; ++j) {
+            h.wx[j] = j < g.w ? es_kernel_f(two_over_w * (fr[0] + (float)j), beta) : 0.0f;
+            h.wy[j] = j < g.w ? es_kernel_f(two_over_w * (fr[1] + (float)j), beta) : 0.0f;
+        }
+        trec[i] = h;
+    } else if (STAGED) {
         SrcRec<float> h;
         h.cell = (unsigned)ci[0] | ((unsigned)ci[1] << 14) | ((unsigned)ci[2] << 28);
         h.fx = fr[0];
@@ -346,15 +302,20 @@ __global__ void __launch_bounds__(256) k_prep_tc(const float4 *__restrict__ tc, 
 
 cudaError_t launch_prep_tc(const float4 *tc, const int *sidx, const int *nv_ptr, long n_src, const void *flux,
                            int flux_fp64, int n_freq, int f, const SliceGeom &g, int *cell, float *frac,
-                           cpx<float> *cs, SrcRec<float> *rec, cudaStream_t st)
+                           cpx<float> *cs, SrcRec<float> *rec, TcRec *trec, cudaStream_t st)
 {
     if (n_src <= 0) return cudaSuccess;
+    if (trec && (g.w > kTcWmax || g.d != 2 || g.K)) return cudaErrorInvalidValue;
     const unsigned nb = (unsigned)((n_src + 255) / 256);
-    if (rec)
-        k_prep_tc<true><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cell, frac, cs, rec);
+    if (trec)
+        k_prep_tc<2><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cell, frac, cs, rec,
+                                         trec);
+    else if (rec)
+        k_prep_tc<1><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cell, frac, cs, rec,
+                                         trec);
     else
-        k_prep_tc<false><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cell, frac, cs,
-                                             rec);
+        k_prep_tc<0><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cell, frac, cs, rec,
+                                         trec);
     return cudaGetLastError();
 }
 

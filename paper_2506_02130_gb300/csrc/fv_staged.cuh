@@ -9,6 +9,65 @@ namespace fv {
 // Status bits a kernel may set in the plan's device status word.
 #define FV_DEVICE_TIMEOUT 1
 
+// ES kernel phi(z) = exp(beta (sqrt(1 - z^2) - 1)) on [-1, 1], zero outside (Section 2.2)
+__device__ __forceinline__ double es_kernel_d(double z, double beta)
+{
+    double t = 1.0 - z * z;
+    return t >= 0.0 ? exp(beta * (sqrt(t) - 1.0)) : 0.0;
+}
+__device__ __forceinline__ float es_kernel_f(float z, float beta)
+{
+    float t = 1.0f - z * z;
+    return t >= 0.0f ? __expf(beta * (sqrtf(t) - 1.0f)) : 0.0f;
+}
+template <class G> __device__ __forceinline__ G es_k(G z, G beta);
+template <> __device__ __forceinline__ double es_k<double>(double z, double beta) { return es_kernel_d(z, beta); }
+template <> __device__ __forceinline__ float es_k<float>(float z, float beta) { return es_kernel_f(z, beta); }
+
+// Bulk asynchronous copies into shared memory, completion counted on an mbarrier (used by the gather
+// kernel's record staging), and the bounded wait on a barrier phase.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init1(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+// Wait for phase `parity` of *bar for at most about a second; false if the wait ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(smem_addr(bar)), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > 2000000000LL) return false;
+    }
+}
+
+__device__ __forceinline__ int top_cell(double q, int nf1)
+{
+    double c = floor(q) + (double)(nf1 / 2);
+    int ci = (int)fmax(0.0, fmin(c, (double)(nf1 - 1)));
+    return ci;
+}
+
 // One source of one slice as the gather spreader reads it (16- or 32-byte records, copied in bulk):
 // cell = cx | cy << 14 | cz << 28 (first footprint cell per axis; cx, cy < 16384, cz < 16) and the
 // offsets frac = l0 - q of the grid coordinate split (Section 2.2).
@@ -20,6 +79,16 @@ template <> struct __align__(16) SrcRec<float> {
 template <> struct __align__(16) SrcRec<double> {
     unsigned cell, pad;
     double fx, fy, fz;
+};
+
+// One source of one slice as the tensor-core gather reads it (80 bytes, copied in bulk): the packed first
+// footprint cell (as in SrcRec) and the kernel values of its footprint columns and rows, phi((2/w)(f + j))
+// for j < w, zero for w <= j < 8.
+constexpr int kTcWmax = 8;
+struct __align__(16) TcRec {
+    unsigned cell;
+    unsigned pad[3];
+    float wx[kTcWmax], wy[kTcWmax];
 };
 
 // Complex strengths per source in the staged layout: n_pol values padded to a multiple of 16 bytes.
@@ -38,6 +107,12 @@ cudaError_t launch_spread_gather_rec(const int *offsets, const SrcRec<G> *rec, c
                                      const TimeBin &tb, double r0, double r1, int *status, cpx<G> *grid,
                                      cudaStream_t st);
 
+// The tensor-core form of the same spreading for FP32 two-dimensional grids (n_pol 1 or 4, no height
+// terms, w <= 8), reading tensor-core records: cudaErrorInvalidValue otherwise.
+cudaError_t launch_spread_mma(const int *offsets, const TcRec *rec, const cpx<float> *cs, const SliceGeom &g,
+                              const TimeBin &tb, double r0, double r1, int *status, cpx<float> *grid,
+                              cudaStream_t st);
+
 // Per slice: strengths with prephase and packed grid coordinates of the sorted sources, as staged
 // records (the same arithmetic as launch_prep).
 template <class G>
@@ -46,9 +121,10 @@ cudaError_t launch_prep_staged(const double *sdir, const int *sidx, const int *n
                                SrcRec<G> *rec, cpx<G> *cs, cudaStream_t st);
 
 // FP32 grids: the same, from the per-time records tc of launch_time_binning (no FP64 arithmetic); writes
-// staged records when rec is given, else cell[3][n] / frac[3][n] / cs[n_pol][n].
+// tensor-core records when trec is given (two-dimensional grids, w <= 8), else staged records when rec is
+// given, else cell[3][n] / frac[3][n] / cs[n_pol][n].
 cudaError_t launch_prep_tc(const float4 *tc, const int *sidx, const int *nv_ptr, long n_src, const void *flux,
                            int flux_fp64, int n_freq, int f, const SliceGeom &g, int *cell, float *frac,
-                           cpx<float> *cs, SrcRec<float> *rec, cudaStream_t st);
+                           cpx<float> *cs, SrcRec<float> *rec, TcRec *trec, cudaStream_t st);
 
 }  // namespace fv

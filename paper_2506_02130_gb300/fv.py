@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_PKG, "libfftvis_gb300.so")
 ABI_VERSION = 5          # FV_ABI_VERSION of include/fv.h that the structs below mirror
 FV_OK, FV_ERR_ARG, FV_ERR_OOM, FV_ERR_CUDA, FV_ERR_STATE, FV_ERR_TIMEOUT, FV_ERR_UNSUPPORTED = range(7)
 FV_FP64, FV_MIXED = 0, 1
-SPREAD = {"auto": 0, "gather": 1, "scatter": 2, "atomic": 3}
+SPREAD = {"auto": 0, "gather": 1, "scatter": 2, "atomic": 3, "tensor": 4}
 BEAMS = {"gauss": 0, "airy": 1, "uniform": 2, "grid": 3}
 TRANSFORMS = {"auto": 0, "type3": 1, "lattice": 2, "basis": 3}
 TRANSFORM_NAMES = {0: "auto", 1: "type3", 2: "lattice", 3: "basis"}
@@ -61,7 +61,7 @@ class fv_info(C.Structure):
                 ("lattice_grid", C.c_int * 2), ("lattice_terms", C.c_int), ("lattice_basis", C.c_double * 4),
                 ("beam_groups", C.c_int), ("basis_terms", C.c_int), ("basis_grid", C.c_int * 3),
                 ("basis_fit_error", C.c_double),
-                ("height_terms", C.c_int)]
+                ("height_terms", C.c_int), ("spread_method", C.c_int)]
 
 
 PROFILE_CLASSES = 12
@@ -219,7 +219,8 @@ def fv_get_info(plan) -> dict:
             "lattice_terms": i.lattice_terms, "beam_groups": i.beam_groups,
             "lattice_basis": list(i.lattice_basis), "basis_terms": i.basis_terms,
             "basis_grid": list(i.basis_grid), "basis_fit_error": i.basis_fit_error,
-            "height_terms": i.height_terms}
+            "height_terms": i.height_terms,
+            "spread": {v: k for k, v in SPREAD.items()}.get(i.spread_method, str(i.spread_method))}
 
 
 def fv_profile_enable(plan, enable: bool = True) -> None:

@@ -61,7 +61,7 @@ def _opts(**kw):
                                 dict(kernel_width=40), dict(latitude_rad=2.0),
                                 dict(precision=1, eps=1e-6, upsampfac=1.25), dict(transform=4),
                                 dict(transform=3, n_basis=-1), dict(transform=3, n_basis=2),
-                                dict(lattice_tol_m=-1.0), dict(spread_method=4),
+                                dict(lattice_tol_m=-1.0), dict(spread_method=5),
                                 dict(bin_size=(C.c_int * 2)(0, 65)),
                                 dict(bin_size=(C.c_int * 2)(-2, 4)), dict(heights=3), dict(heights=-1)])
 def test_invalid_options_rejected_before_device(lib, kw):

@@ -199,6 +199,28 @@ def test_spreading_methods_agree_with_oracle(spread, precision):
     assert rel_l2(out, oracle(pol)) <= 2 * TOL[precision]
 
 
+@pytest.mark.parametrize("case", ["scalar", "polarised"])
+def test_tensor_core_spreading(case):
+    """The tensor-core gather (TF32 products, three-term split) against the oracle and the FP32 gather,
+    on coplanar arrays (two-dimensional grids) with many tiles, ragged tile edges and several chunks."""
+    if case == "scalar":
+        prob = W.config_hex127(seed=15, n_chan=3, n_time=2, n_point=6000, nside=16, radius=5)
+        prob.ant_enu = W.hex_array(5)                     # coplanar
+    else:
+        prob = small_pol(seed=16, n_chan=2, n_time=1)
+    out_t, info = run_gpu(prob, fv.FV_MIXED, spread="tensor", transform="type3")
+    assert info["dims"] == 2 and info["spread"] == "tensor"
+    out_g, info_g = run_gpu(prob, fv.FV_MIXED, spread="gather", transform="type3")
+    assert info_g["spread"] == "gather"
+    ref = oracle(prob)
+    err = rel_l2(out_t, ref)
+    assert err <= TOL[fv.FV_MIXED], err
+    assert rel_l2(out_t, out_g) <= 5e-6
+    # FP64 plans and three-dimensional grids take the FP64 / register gather instead
+    _, i64 = run_gpu(prob, fv.FV_FP64, spread="tensor", transform="type3")
+    assert i64["spread"] == "gather"
+
+
 @pytest.mark.parametrize("max_radix", [8, 16])
 @pytest.mark.parametrize("n_streams", [1, 3])
 def test_fft_radix_cap_and_streams(max_radix, n_streams):
