@@ -97,6 +97,7 @@ struct fv_plan_s {
         double *sdir = nullptr;
         void *frac = nullptr, *cs = nullptr;
         float4 *tc = nullptr;     // per-time coordinate records of the sorted sources (FP32 grids)
+        int *tiles = nullptr;     // tile ticket of the tensor-core spreading (reset by the prep kernel)
     };
     std::vector<Workspace> ws;
     // what one execution workspace must hold for this plan (set by prepare)

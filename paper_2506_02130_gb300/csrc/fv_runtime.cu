@@ -174,6 +174,7 @@ size_t workspace_layout(const fv_plan_s::WsNeed &need, char *base, fv_plan_s::Wo
         o.frac = take(ns * need.frac_per_src + 64);
         o.cs = take(ns * need.cs_per_src + 64);
         o.tc = need.tc ? (float4 *)take(ns * 3 * sizeof(float4)) : nullptr;
+        o.tiles = (int *)take(4 * sizeof(int));
     }
     return off;
 }
@@ -772,7 +773,7 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
                     CK(launch_prep_tc(wk.tc, wk.sidx, wk.offsets + nb, p->n_src, p->flux, p->flux_fp64, nf, f, g,
                                       wk.cell, (float *)frac, (cpx<float> *)cs,
                                       staged && !tensor ? (SrcRec<float> *)rec : nullptr,
-                                      tensor ? (TcRec *)wk.frac : nullptr, st));
+                                      tensor ? (TcRec *)wk.frac : nullptr, tensor ? wk.tiles : nullptr, st));
                 else if (staged)
                     CK(launch_prep_staged<G>(wk.sdir, wk.sidx, wk.offsets + nb, p->n_src, p->flux, p->flux_fp64, nf,
                                              f, g, rec, cs, st));
@@ -786,7 +787,7 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
                 CK(prof_begin(p, PC_SPREAD, st));
                 if (tensor)
                     CK(launch_spread_mma(wk.offsets, (const TcRec *)wk.frac, (const cpx<float> *)cs, g, tb, r0, r1,
-                                         p->d_status, (cpx<float> *)grid, st));
+                                         wk.tiles, p->d_status, (cpx<float> *)grid, st));
                 else if (p->spread_method == FV_SPREAD_GATHER || p->spread_method == FV_SPREAD_TENSOR)
                     CK(launch_spread_gather_rec<G>(wk.offsets, rec, cs, g, tb, r0, r1, p->d_status, grid, st));
                 else if (p->spread_method == FV_SPREAD_SCATTER)

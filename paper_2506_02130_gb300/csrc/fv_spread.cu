@@ -235,9 +235,10 @@ __global__ void __launch_bounds__(256) k_prep_tc(const float4 *__restrict__ tc, 
                                                  const void *__restrict__ flux, int flux_fp64, int n_freq, int f,
                                                  SliceGeom g, int *__restrict__ cell, float *__restrict__ frac,
                                                  cpx<float> *__restrict__ cs, SrcRec<float> *__restrict__ rec,
-                                                 TcRec *__restrict__ trec)
+                                                 TcRec *__restrict__ trec, int *__restrict__ tile_ctr)
 {
     constexpr bool STAGED = MODE > 0;
+    if (tile_ctr && blockIdx.x == 0 && threadIdx.x == 0) *tile_ctr = 0;     // before any early return
     const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= *nv_ptr) return;
     const float4 a = tc[3 * i], b = tc[3 * i + 1], sd = tc[3 * i + 2];
@@ -302,20 +303,20 @@ __global__ void __launch_bounds__(256) k_prep_tc(const float4 *__restrict__ tc, 
 
 cudaError_t launch_prep_tc(const float4 *tc, const int *sidx, const int *nv_ptr, long n_src, const void *flux,
                            int flux_fp64, int n_freq, int f, const SliceGeom &g, int *cell, float *frac,
-                           cpx<float> *cs, SrcRec<float> *rec, TcRec *trec, cudaStream_t st)
+                           cpx<float> *cs, SrcRec<float> *rec, TcRec *trec, int *tile_ctr, cudaStream_t st)
 {
-    if (n_src <= 0) return cudaSuccess;
+    if (n_src <= 0) return tile_ctr ? cudaErrorInvalidValue : cudaSuccess;
     if (trec && (g.w > kTcWmax || g.d != 2 || g.K)) return cudaErrorInvalidValue;
     const unsigned nb = (unsigned)((n_src + 255) / 256);
     if (trec)
         k_prep_tc<2><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cell, frac, cs, rec,
-                                         trec);
+                                         trec, tile_ctr);
     else if (rec)
         k_prep_tc<1><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cell, frac, cs, rec,
-                                         trec);
+                                         trec, tile_ctr);
     else
         k_prep_tc<0><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cell, frac, cs, rec,
-                                         trec);
+                                         trec, tile_ctr);
     return cudaGetLastError();
 }
 

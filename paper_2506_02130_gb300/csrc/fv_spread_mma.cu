@@ -9,15 +9,17 @@
 //     B[j][x]       = psi_x,j(x)                   (J x 8)
 // and J the candidate sources of the block.  One warp owns one block and one D fragment per product; it
 // takes its candidates eight at a time as one m16n8k8 TF32 product.  FP32 accuracy comes from the
-// three-term split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (a_hi = tf32(a), a_lo = tf32(a - a_hi)),
-// which leaves a relative error near 2^-21 per product, with FP32 accumulation in the tensor core.
+// three-term split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (a_hi = tf32(a), a_lo = a - a_hi, of which the
+// tensor core reads the leading 11 bits), which leaves a relative error near 2^-21 per product, with FP32
+// accumulation in the tensor core.
 //
 // Operands are built in registers, which is why this uses the warp-level mma.sync form: the blocks' A and
 // B are sparse (a source covers at most 7 of a block's 8 rows and columns, about a quarter of them on
 // average) and change with every group of eight candidates, so staging them through shared memory in the
 // layouts tcgen05.mma reads would cost more than the products.
 //
-// A CTA owns a 32 x 16 tile (4 x 2 blocks): eight consumer warps, one per block, and one producer warp.
+// A CTA owns a 32 x 16 tile at a time (4 x 2 blocks): eight consumer warps, one per block, and one
+// producer warp.  CTAs are persistent (three per SM) and take tiles from an atomic ticket.
 // The tile's candidates are the sources of the bins it maps to (one contiguous range of the sorted sources
 // per bin row); the producer copies them into shared memory in chunks of 128 with bulk asynchronous copies
 // into a three-stage ring (a full and an empty mbarrier per stage, every wait bounded).  Each record
@@ -26,6 +28,8 @@
 // atomics) and runs them through the tensor cores; warps never wait for one another except through the
 // ring.  Every grid cell is stored once, with the x and y prescale of the FFT passes applied.
 #include "fv_staged.cuh"
+
+#include <algorithm>
 
 namespace fv {
 
@@ -42,13 +46,6 @@ __device__ __forceinline__ uint32_t to_tf32(float v)
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
     return r;
-}
-
-// v = hi + lo with hi, lo TF32 (lo carries the next 11 bits)
-__device__ __forceinline__ void split_tf32(float v, uint32_t &hi, uint32_t &lo)
-{
-    hi = to_tf32(v);
-    lo = to_tf32(v - __uint_as_float(hi));
 }
 
 // D += A B, m16n8k8, A row-major (a0..a3), B column-major (b0, b1), FP32 accumulators d0..d3
@@ -76,20 +73,23 @@ template <int NP>
 __global__ void __launch_bounds__(kTcThreads, 3) k_spread_mma(const int *__restrict__ offsets,
                                                             const TcRec *__restrict__ rec,
                                                             const cpx<float> *__restrict__ cs, SliceGeom g, TimeBin tb,
-                                                            double r0, double r1, int *__restrict__ status,
+                                                            double r0, double r1, int tiles_x, int n_tiles,
+                                                            int *__restrict__ tile_ctr, int *__restrict__ status,
                                                             cpx<float> *__restrict__ grid)
 {
     constexpr int kCsw = (NP * 8 + 15) / 16 * 16 / 8;           // staged strengths per source (16-byte rows)
     __shared__ __align__(16) TcRec s_rec[kTcStages][kTcChunk];
     __shared__ __align__(16) cpx<float> s_cs[kTcStages][kTcChunk * kCsw];
     __shared__ __align__(8) uint64_t s_full[kTcStages], s_empty[kTcStages];
-    __shared__ int s_n[kTcStages];                                // candidates of a stage; -1: no more
-    __shared__ unsigned char s_sel[kTcConsumers][kTcChunk];       // a warp's selected candidates
+    // per stage: candidates of a chunk, or -1 for a tile boundary whose next tile is s_tile
+    __shared__ int s_n[kTcStages], s_tile[kTcStages];
+    // a warp's selected candidates: t (bits 0-7) and the footprint origin relative to the block + 16 in x
+    // (bits 8-15) and y (bits 16-23)
+    __shared__ int s_sel[kTcConsumers][kTcChunk];
     __shared__ int s_row0[32], s_pre[32];                         // the producer's rows table
     __shared__ int s_abort;
     const int nx = g.dim[0].nf1, ny = g.dim[1].nf1;
     const int w = g.w;
-    const int x0 = blockIdx.x * kTcTileX, y0 = blockIdx.y * kTcTileY;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int b = 0; b < kTcStages; ++b) {
@@ -102,192 +102,230 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_spread_mma(const int *__restr
     __syncthreads();
     volatile int *abort_flag = &s_abort;
 
+    // Tiles are handed out by an atomic ticket (tile_ctr, zeroed by the prep kernel before this launch);
+    // the producer runs ahead across tile boundaries, so the next tile's first chunks are in flight while
+    // the consumers finish the current one.
     if (warp == kTcConsumers) {
-        // ---------------- producer warp: rows tables and bulk copies of the candidate chunks
-        int bins[4] = {0, 0, 0, 0};
-        if (lane == 0) {
-            // the bin rectangle of the tile (one-cell margin through the top-grid mapping), in FP64, once
-            const double qx_lo = (x0 - nx / 2 - 0.5 * w) / r0, qx_hi = (x0 + kTcTileX - nx / 2 + 0.5 * w - 1) / r0;
-            const double qy_lo = (y0 - ny / 2 - 0.5 * w) / r1, qy_hi = (y0 + kTcTileY - ny / 2 + 0.5 * w - 1) / r1;
-            bins[0] = top_cell(qx_lo - 1.0, tb.nf1_top[0]) / tb.T[0];
-            bins[1] = top_cell(qx_hi + 1.0, tb.nf1_top[0]) / tb.T[0];
-            bins[2] = top_cell(qy_lo - 1.0, tb.nf1_top[1]) / tb.T[1];
-            bins[3] = top_cell(qy_hi + 1.0, tb.nf1_top[1]) / tb.T[1];
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) bins[k] = __shfl_sync(0xffffffffu, bins[k], 0);
-        int kc = 0;              // chunks issued
+        // ---------------- producer warp: tiles, rows tables and bulk copies of the candidate chunks
+        int kc = 0;              // stages filled
         unsigned ephase = 0u;    // bit b: parity of the next completion of stage b's empty barrier
         int ok = 1;
-        for (int r0w = bins[2]; r0w <= bins[3] && ok; r0w += 32) {
-            const int nrows = min(32, bins[3] - r0w + 1);
-            int start = 0, len = 0;
-            if (lane < nrows) {
-                const int row = (r0w + lane) * tb.nbx;
-                start = offsets[row + bins[0]];
-                len = offsets[row + bins[1] + 1] - start;
+        // lane 0: wait until stage kc % kTcStages is free (its previous use consumed); false if that ran out
+        auto acquire = [&](int b) -> bool {
+            if (kc < kTcStages) return true;
+            const bool got = mbar_wait(&s_empty[b], (ephase >> b) & 1u);
+            ephase ^= 1u << b;
+            return got && !*abort_flag;
+        };
+        // lane 0: take the next tile and announce it with a boundary stage
+        auto next_tile = [&]() -> int {
+            const int t = atomicAdd(tile_ctr, 1);
+            const int b = kc % kTcStages;
+            if (!acquire(b)) {
+                ok = 0;
+                return n_tiles;
             }
-            int incl = len;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            s_row0[lane] = start;
-            s_pre[lane] = incl - len;
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            __syncwarp();
+            s_n[b] = -1;
+            s_tile[b] = t;
+            mbar_arrive(&s_full[b]);
+            ++kc;
+            return t;
+        };
+        int tile = lane == 0 ? next_tile() : 0;
+        tile = __shfl_sync(0xffffffffu, tile, 0);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        kc = __shfl_sync(0xffffffffu, kc, 0);
+        while (tile < n_tiles && ok) {
+            const int x0 = (tile % tiles_x) * kTcTileX, y0 = (tile / tiles_x) * kTcTileY;
+            int bins[4] = {0, 0, 0, 0};
             if (lane == 0) {
-                for (int base = 0; base < total; base += kTcChunk, ++kc) {
-                    const int b = kc % kTcStages;
-                    if (kc >= kTcStages) {
-                        // the consumers have finished the chunk this stage held
-                        const bool got = mbar_wait(&s_empty[b], (ephase >> b) & 1u);
-                        ephase ^= 1u << b;
-                        if (!got || *abort_flag) {
+                // the bin rectangle of the tile (one-cell margin through the top-grid mapping), in FP64
+                const double qx_lo = (x0 - nx / 2 - 0.5 * w) / r0, qx_hi = (x0 + kTcTileX - nx / 2 + 0.5 * w - 1) / r0;
+                const double qy_lo = (y0 - ny / 2 - 0.5 * w) / r1, qy_hi = (y0 + kTcTileY - ny / 2 + 0.5 * w - 1) / r1;
+                bins[0] = top_cell(qx_lo - 1.0, tb.nf1_top[0]) / tb.T[0];
+                bins[1] = top_cell(qx_hi + 1.0, tb.nf1_top[0]) / tb.T[0];
+                bins[2] = top_cell(qy_lo - 1.0, tb.nf1_top[1]) / tb.T[1];
+                bins[3] = top_cell(qy_hi + 1.0, tb.nf1_top[1]) / tb.T[1];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) bins[k] = __shfl_sync(0xffffffffu, bins[k], 0);
+            for (int r0w = bins[2]; r0w <= bins[3] && ok; r0w += 32) {
+                const int nrows = min(32, bins[3] - r0w + 1);
+                int start = 0, len = 0;
+                if (lane < nrows) {
+                    const int row = (r0w + lane) * tb.nbx;
+                    start = offsets[row + bins[0]];
+                    len = offsets[row + bins[1] + 1] - start;
+                }
+                int incl = len;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                s_row0[lane] = start;
+                s_pre[lane] = incl - len;
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                __syncwarp();
+                if (lane == 0) {
+                    for (int base = 0; base < total; base += kTcChunk) {
+                        const int b = kc % kTcStages;
+                        if (!acquire(b)) {
                             ok = 0;
                             break;
                         }
-                    }
-                    const int n = min(kTcChunk, total - base);
-                    s_n[b] = n;
-                    mbar_expect(&s_full[b], (unsigned)n * (unsigned)(sizeof(TcRec) + kCsw * sizeof(cpx<float>)));
-                    for (int r = 0; r < nrows; ++r) {
-                        const int rlen = (r + 1 < nrows ? s_pre[r + 1] : total) - s_pre[r];
-                        const int a = max(base, s_pre[r]), e = min(base + n, s_pre[r] + rlen);
-                        if (a >= e) continue;
-                        const int i0 = s_row0[r] + (a - s_pre[r]), m = e - a;
-                        bulk_g2s(&s_rec[b][a - base], rec + i0, (unsigned)(m * sizeof(TcRec)), &s_full[b]);
-                        bulk_g2s(&s_cs[b][(a - base) * kCsw], cs + (size_t)i0 * kCsw,
-                                 (unsigned)(m * kCsw * sizeof(cpx<float>)), &s_full[b]);
+                        const int n = min(kTcChunk, total - base);
+                        s_n[b] = n;
+                        mbar_expect(&s_full[b], (unsigned)n * (unsigned)(sizeof(TcRec) + kCsw * sizeof(cpx<float>)));
+                        for (int r = 0; r < nrows; ++r) {
+                            const int rlen = (r + 1 < nrows ? s_pre[r + 1] : total) - s_pre[r];
+                            const int a = max(base, s_pre[r]), e = min(base + n, s_pre[r] + rlen);
+                            if (a >= e) continue;
+                            const int i0 = s_row0[r] + (a - s_pre[r]), m = e - a;
+                            bulk_g2s(&s_rec[b][a - base], rec + i0, (unsigned)(m * sizeof(TcRec)), &s_full[b]);
+                            bulk_g2s(&s_cs[b][(a - base) * kCsw], cs + (size_t)i0 * kCsw,
+                                     (unsigned)(m * kCsw * sizeof(cpx<float>)), &s_full[b]);
+                        }
+                        ++kc;
                     }
                 }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                kc = __shfl_sync(0xffffffffu, kc, 0);
+                ephase = __shfl_sync(0xffffffffu, ephase, 0);
+                __syncwarp();    // lane 0 is done with the rows table before the next group rewrites it
             }
+            if (!ok) break;
+            tile = lane == 0 ? next_tile() : 0;
+            tile = __shfl_sync(0xffffffffu, tile, 0);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             kc = __shfl_sync(0xffffffffu, kc, 0);
             ephase = __shfl_sync(0xffffffffu, ephase, 0);
-            __syncwarp();    // lane 0 is done with the rows table before the next group rewrites it
         }
-        if (lane == 0) {
-            if (ok) {
-                // end of the stream: a stage with n = -1, completed by a plain arrival
-                const int b = kc % kTcStages;
-                bool got = true;
-                if (kc >= kTcStages) got = mbar_wait(&s_empty[b], (ephase >> b) & 1u);
-                if (got && !*abort_flag) {
-                    s_n[b] = -1;
-                    mbar_arrive(&s_full[b]);
-                } else {
-                    ok = 0;
-                }
-            }
-            if (!ok) {
-                // a wait ran out: tell the consumers, record it, and wait (bounded) for the copies in flight
-                *abort_flag = 1;
-                atomicOr(status, FV_DEVICE_TIMEOUT);
-                for (int k = max(0, kc - kTcStages); k < kc; ++k)
-                    mbar_wait(&s_full[k % kTcStages], (unsigned)(k / kTcStages) & 1u);
-            }
+        if (lane == 0 && !ok) {
+            // a wait ran out: tell the consumers, record it, and wait (bounded) for the copies in flight
+            *abort_flag = 1;
+            atomicOr(status, FV_DEVICE_TIMEOUT);
+            for (int k = max(0, kc - kTcStages); k < kc; ++k)
+                mbar_wait(&s_full[k % kTcStages], (unsigned)(k / kTcStages) & 1u);
         }
         return;
     }
 
-    // ---------------- consumer warps: one 8 x 8 block each
-    const int bx0 = x0 + (warp & 3) * 8, by0 = y0 + (warp >> 2) * 8;   // the block's first cell
+    // ---------------- consumer warps: one 8 x 8 block of each tile
     const int gq = lane >> 2, tq = lane & 3;                             // fragment group, k index
+    unsigned fphase = 0u;    // bit b: parity of the next completion of stage b's full barrier
+    int tile = -1;           // none yet
+    int bx0 = 0, by0 = 0;    // the block's first cell
     float d[NP][4];
 #pragma unroll
     for (int p = 0; p < NP; ++p)
 #pragma unroll
         for (int k = 0; k < 4; ++k) d[p][k] = 0.0f;
-    bool ok = true;
-    unsigned fphase = 0u;    // bit b: parity of the next completion of stage b's full barrier
     for (int kc = 0;; ++kc) {
         const int b = kc % kTcStages;
-        // the lanes decide together: a wait that ran out on any lane, or an abort, ends the warp's loop
+        // the lanes decide together: a wait that ran out on any lane, or an abort, ends the warp's work
         const bool got = __all_sync(0xffffffffu, mbar_wait(&s_full[b], (fphase >> b) & 1u));
         const int aborted = __shfl_sync(0xffffffffu, *abort_flag, 0);
         fphase ^= 1u << b;
         if (!got || aborted) {
-            ok = false;
             if (lane == 0 && !got) {
                 *abort_flag = 1;
                 atomicOr(status, FV_DEVICE_TIMEOUT);
             }
             break;
         }
-        const int n = s_n[b];
-        if (n < 0) break;
-        // the chunk's candidates whose footprint overlaps this block, in order
-        int L = 0;
-        for (int c0 = 0; c0 < n; c0 += 32) {
-            const int t = c0 + lane;
-            bool hit = false;
-            if (t < n) {
-                const unsigned cell = s_rec[b][t].cell;
-                const int cx = (int)(cell & 0x3fffu), cy = (int)((cell >> 14) & 0x3fffu);
-                hit = cx <= bx0 + 7 && cx + w > bx0 && cy <= by0 + 7 && cy + w > by0;
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, hit);
-            if (hit) s_sel[warp][L + __popc(m & ((1u << lane) - 1u))] = (unsigned char)t;
-            L += __popc(m);
-        }
-        __syncwarp();
-        // eight candidates per product: this lane supplies k = tq (h = 0) and k = tq + 4 (h = 1)
-        for (int e = 0; e < L; e += 8) {
-            uint32_t bh[2], bl[2];
-            float wy[2];
-            int tt[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int k = e + tq + 4 * h;
-                float wx = 0.0f;
-                wy[h] = 0.0f;
-                tt[h] = 0;
-                if (k < L) {
-                    const int t = s_sel[warp][k];
-                    const TcRec &r = s_rec[b][t];
-                    const unsigned cell = r.cell;
-                    const unsigned dx = (unsigned)(bx0 + gq - (int)(cell & 0x3fffu));
-                    const unsigned dy = (unsigned)(by0 + gq - (int)((cell >> 14) & 0x3fffu));
-                    if (dx < (unsigned)kTcWmax) wx = r.wx[dx];      // zero past w
-                    if (dy < (unsigned)kTcWmax) wy[h] = r.wy[dy];
-                    tt[h] = t;
+        const int n = s_n[b], next = s_tile[b];
+        if (n > 0) {
+            // the chunk's candidates whose footprint overlaps this block, in order
+            int L = 0;
+            for (int c0 = 0; c0 < n; c0 += 32) {
+                const int t = c0 + lane;
+                bool hit = false;
+                int ent = 0;
+                if (t < n) {
+                    const unsigned cell = s_rec[b][t].cell;
+                    const int cx = (int)(cell & 0x3fffu) - bx0, cy = (int)((cell >> 14) & 0x3fffu) - by0;
+                    hit = cx <= 7 && cx + w > 0 && cy <= 7 && cy + w > 0;    // then -15 < cx, cy <= 7
+                    ent = t | ((cx + 16) << 8) | ((cy + 16) << 16);
                 }
-                split_tf32(wx, bh[h], bl[h]);
+                const unsigned m = __ballot_sync(0xffffffffu, hit);
+                if (hit) s_sel[warp][L + __popc(m & ((1u << lane) - 1u))] = ent;
+                L += __popc(m);
             }
+            __syncwarp();
+            // eight candidates per product: this lane supplies k = tq (h = 0) and k = tq + 4 (h = 1)
+            for (int e = 0; e < L; e += 8) {
+                uint32_t bh[2], bl[2];
+                float wy[2];
+                float4 cv[2][NP > 1 ? 2 : 1];
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const cpx<float> c0 = s_cs[b][tt[0] * kCsw + p], c1 = s_cs[b][tt[1] * kCsw + p];
-                // a0 = (row gq, k tq): Re, a1 = (gq + 8, tq): Im, a2 = (gq, tq + 4): Re, a3 = (gq + 8, tq + 4): Im
-                uint32_t h0, l0, h1, l1, h2, l2, h3, l3;
-                split_tf32(c0.x * wy[0], h0, l0);
-                split_tf32(c0.y * wy[0], h1, l1);
-                split_tf32(c1.x * wy[1], h2, l2);
-                split_tf32(c1.y * wy[1], h3, l3);
-                mma_tf32(d[p], l0, l1, l2, l3, bh[0], bh[1]);
-                mma_tf32(d[p], h0, h1, h2, h3, bl[0], bl[1]);
-                mma_tf32(d[p], h0, h1, h2, h3, bh[0], bh[1]);
+                for (int h = 0; h < 2; ++h) {
+                    const int k = e + tq + 4 * h;
+                    float wx = 0.0f;
+                    wy[h] = 0.0f;
+                    int t = 0;
+                    if (k < L) {
+                        const int ent = s_sel[warp][k];
+                        t = ent & 0xff;
+                        const TcRec &r = s_rec[b][t];
+                        const unsigned dx = (unsigned)(gq + 16 - ((ent >> 8) & 0xff));
+                        const unsigned dy = (unsigned)(gq + 16 - (ent >> 16));
+                        if (dx < (unsigned)kTcWmax) wx = r.wx[dx];      // zero past w
+                        if (dy < (unsigned)kTcWmax) wy[h] = r.wy[dy];
+                    }
+                    // B: hi = tf32(wx); lo = the remainder, whose low bits the tensor core ignores
+                    bh[h] = to_tf32(wx);
+                    bl[h] = __float_as_uint(wx - __uint_as_float(bh[h]));
+                    const float4 *c4 = reinterpret_cast<const float4 *>(&s_cs[b][t * kCsw]);
+#pragma unroll
+                    for (int q = 0; q < (NP > 1 ? 2 : 1); ++q) cv[h][q] = c4[q];
+                }
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const float4 u0 = cv[0][p >> 1], u1 = cv[1][p >> 1];
+                    const float re0 = (p & 1) ? u0.z : u0.x, im0 = (p & 1) ? u0.w : u0.y;
+                    const float re1 = (p & 1) ? u1.z : u1.x, im1 = (p & 1) ? u1.w : u1.y;
+                    // a0 = (row gq, k tq): Re, a1 = (gq + 8, tq): Im, a2 = (gq, tq + 4): Re, a3 = (gq + 8, tq + 4): Im
+                    const float a0 = re0 * wy[0], a1 = im0 * wy[0], a2 = re1 * wy[1], a3 = im1 * wy[1];
+                    const uint32_t h0 = to_tf32(a0), h1 = to_tf32(a1), h2 = to_tf32(a2), h3 = to_tf32(a3);
+                    mma_tf32(d[p], __float_as_uint(a0 - __uint_as_float(h0)), __float_as_uint(a1 - __uint_as_float(h1)),
+                             __float_as_uint(a2 - __uint_as_float(h2)), __float_as_uint(a3 - __uint_as_float(h3)),
+                             bh[0], bh[1]);
+                    mma_tf32(d[p], h0, h1, h2, h3, bl[0], bl[1]);
+                    mma_tf32(d[p], h0, h1, h2, h3, bh[0], bh[1]);
+                }
             }
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&s_empty[b]);
-    }
-    // D fragment of product p: d0 = Re (row gq, column 2 tq), d1 = Re (gq, 2 tq + 1), d2 = Im (gq, 2 tq),
-    // d3 = Im (gq, 2 tq + 1); rows are y and columns x of the warp's block
-    const int gy = by0 + gq, gx = bx0 + 2 * tq;
-    if (gy < ny) {
-        const float *px = (const float *)g.pre_x, *py = (const float *)g.pre_y;
-        const float sy = ok ? (py ? py[gy] : 1.0f) : 0.0f;
+        if (lane == 0) mbar_arrive(&s_empty[b]);      // after the stage was read
+        if (n < 0) {
+            if (tile >= 0) {
+                // D fragment of product p: d0 = Re (row gq, column 2 tq), d1 = Re (gq, 2 tq + 1),
+                // d2 = Im (gq, 2 tq), d3 = Im (gq, 2 tq + 1); rows are y and columns x of the block
+                const int gy = by0 + gq, gx = bx0 + 2 * tq;
+                if (gy < ny) {
+                    const float *px = (const float *)g.pre_x, *py = (const float *)g.pre_y;
+                    const float sy = py ? py[gy] : 1.0f;
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int x = gx + c;
-            if (x < nx) {
-                const float sc = sy * (px ? px[x] : 1.0f);
+                    for (int c = 0; c < 2; ++c) {
+                        const int x = gx + c;
+                        if (x < nx) {
+                            const float sc = sy * (px ? px[x] : 1.0f);
+#pragma unroll
+                            for (int p = 0; p < NP; ++p)
+                                grid[((size_t)p * ny + gy) * nx + x] = cmk<float>(d[p][c] * sc, d[p][2 + c] * sc);
+                        }
+                    }
+                }
 #pragma unroll
                 for (int p = 0; p < NP; ++p)
-                    grid[((size_t)p * ny + gy) * nx + x] = cmk<float>(d[p][c] * sc, d[p][2 + c] * sc);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) d[p][k] = 0.0f;
             }
+            tile = next;
+            if (tile >= n_tiles) break;
+            bx0 = (tile % tiles_x) * kTcTileX + (warp & 3) * 8;
+            by0 = (tile / tiles_x) * kTcTileY + (warp >> 2) * 8;
         }
     }
 }
@@ -295,16 +333,29 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_spread_mma(const int *__restr
 // The tensor-core gather for an FP32 two-dimensional slice (n_pol 1 or 4, w <= 8) from tensor-core records
 // (launch_prep_tc); writes every cell of grid [n_pol][ny][nx].
 cudaError_t launch_spread_mma(const int *offsets, const TcRec *rec, const cpx<float> *cs, const SliceGeom &g,
-                              const TimeBin &tb, double r0, double r1, int *status, cpx<float> *grid,
+                              const TimeBin &tb, double r0, double r1, int *tile_ctr, int *status, cpx<float> *grid,
                               cudaStream_t st)
 {
     if (g.d != 2 || g.K != 0 || g.w > kTcWmax || (g.n_pol != 1 && g.n_pol != 4)) return cudaErrorInvalidValue;
-    const dim3 blocks((unsigned)((g.dim[0].nf1 + kTcTileX - 1) / kTcTileX),
-                      (unsigned)((g.dim[1].nf1 + kTcTileY - 1) / kTcTileY));
+    static int sms[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!sms[dev]) {
+        e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+    }
+    // persistent: three CTAs per SM (the register and shared-memory budget), each taking tiles by ticket
+    const int tiles_x = (g.dim[0].nf1 + kTcTileX - 1) / kTcTileX;
+    const int n_tiles = tiles_x * ((g.dim[1].nf1 + kTcTileY - 1) / kTcTileY);
+    const unsigned blocks = (unsigned)std::max(1, std::min(n_tiles, 3 * sms[dev]));
     if (g.n_pol == 4)
-        k_spread_mma<4><<<blocks, kTcThreads, 0, st>>>(offsets, rec, cs, g, tb, r0, r1, status, grid);
+        k_spread_mma<4><<<blocks, kTcThreads, 0, st>>>(offsets, rec, cs, g, tb, r0, r1, tiles_x, n_tiles, tile_ctr, status,
+                                                       grid);
     else
-        k_spread_mma<1><<<blocks, kTcThreads, 0, st>>>(offsets, rec, cs, g, tb, r0, r1, status, grid);
+        k_spread_mma<1><<<blocks, kTcThreads, 0, st>>>(offsets, rec, cs, g, tb, r0, r1, tiles_x, n_tiles, tile_ctr, status,
+                                                       grid);
     return cudaGetLastError();
 }
 

@@ -108,9 +108,10 @@ cudaError_t launch_spread_gather_rec(const int *offsets, const SrcRec<G> *rec, c
                                      cudaStream_t st);
 
 // The tensor-core form of the same spreading for FP32 two-dimensional grids (n_pol 1 or 4, no height
-// terms, w <= 8), reading tensor-core records: cudaErrorInvalidValue otherwise.
+// terms, w <= 8), reading tensor-core records: cudaErrorInvalidValue otherwise.  tile_ctr: a device int
+// that is zero at launch (launch_prep_tc sets it), the ticket of the persistent CTAs.
 cudaError_t launch_spread_mma(const int *offsets, const TcRec *rec, const cpx<float> *cs, const SliceGeom &g,
-                              const TimeBin &tb, double r0, double r1, int *status, cpx<float> *grid,
+                              const TimeBin &tb, double r0, double r1, int *tile_ctr, int *status, cpx<float> *grid,
                               cudaStream_t st);
 
 // Per slice: strengths with prephase and packed grid coordinates of the sorted sources, as staged
@@ -122,9 +123,10 @@ cudaError_t launch_prep_staged(const double *sdir, const int *sidx, const int *n
 
 // FP32 grids: the same, from the per-time records tc of launch_time_binning (no FP64 arithmetic); writes
 // tensor-core records when trec is given (two-dimensional grids, w <= 8), else staged records when rec is
-// given, else cell[3][n] / frac[3][n] / cs[n_pol][n].
+// given, else cell[3][n] / frac[3][n] / cs[n_pol][n].  tile_ctr (or nullptr): the tile ticket of the
+// tensor-core spreading that follows, set to zero.  n_src must be > 0 when tile_ctr is given.
 cudaError_t launch_prep_tc(const float4 *tc, const int *sidx, const int *nv_ptr, long n_src, const void *flux,
                            int flux_fp64, int n_freq, int f, const SliceGeom &g, int *cell, float *frac,
-                           cpx<float> *cs, SrcRec<float> *rec, TcRec *trec, cudaStream_t st);
+                           cpx<float> *cs, SrcRec<float> *rec, TcRec *trec, int *tile_ctr, cudaStream_t st);
 
 }  // namespace fv
