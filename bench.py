@@ -64,6 +64,8 @@ def parse():
                     help="up axis of a non-coplanar array on the type-3 route (the headline plan)")
     ap.add_argument("--no-heights-route", action="store_true",
                     help="skip the height-terms vs three-dimensional-grid comparison (non-coplanar arrays)")
+    ap.add_argument("--no-tensor-leg", action="store_true",
+                    help="skip the timing of the tensor-core spreading option")
     ap.add_argument("--no-basis-route", action="store_true",
                     help="hex127: skip timing the spectral-basis route (Appendix A) beside it")
     ap.add_argument("--basis-terms", type=int, default=0,
@@ -869,6 +871,20 @@ def run_sim(args, rank, world, local, dist):
         if "ms_per_step" in hts["terms"] and "ms_per_step" in hts["grid"]:
             hts["speedup_terms_over_grid"] = hts["grid"]["ms_per_step"] / hts["terms"]["ms_per_step"]
 
+    # ---- the optional tensor-core form of the gather spreading (FP32 two-dimensional grids), same workload
+    tens = None
+    if args.transform == "type3" and precision == fv.FV_MIXED and not args.no_tensor_leg:
+        try:
+            tens, ti = route_leg("tensor_spread", transform="type3", spread="tensor", heights=args.heights)
+            tens.update({"spread": ti["spread"],
+                         "what": "same workload with spread=tensor: each warp's 8 x 8 block of cells summed as "
+                                 "m16n8k8 TF32 tensor-core products with a three-term split (an option, off by "
+                                 "default; FP32 FMAs otherwise)"})
+            if ti["spread"] != "tensor":
+                tens = None                  # not applicable here (three-dimensional grid, FP64, ...)
+        except fv.FvError as e:
+            tens = {"unavailable": str(e)}
+
     # ---- the spectral-basis route (Appendix A; scalar skies only)
     bas_route = None
     if args.transform == "type3" and not args.no_basis_route and not prob.polarized:
@@ -978,7 +994,7 @@ def run_sim(args, rank, world, local, dist):
                                 "min": lat[0], "max": lat[-1]},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": gpu_launches,
             "rel_l2_vs_oracle_sample": err, "fp64_plain_equal_accuracy": fp64, "lattice_route": lat_route,
-            "heights_route": hts,
+            "heights_route": hts, "tensor_spread": tens,
             "basis_route": bas_route, "serving": serving_leg, "batching": batch_leg,
             "kernels": {k: {"ms_per_step": v["ms"], "launches_per_step": v["launches"],
                             "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}

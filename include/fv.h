@@ -204,13 +204,16 @@ int fv_lattice_detect(int n_ant, const double *enu_m, double tol_m, double basis
 typedef enum {
     FV_SPREAD_AUTO = 0,
     FV_SPREAD_GATHER = 1,     /* per-tile, each thread sums the sources covering its cells; the tile's
-                                 sorted sources are staged in shared memory by bulk asynchronous copies */
+                                 sorted sources are staged in shared memory by bulk asynchronous copies
+                                 (FV_MIXED two-dimensional grids: persistent CTAs, a producer warp
+                                 streaming chunks into a shared-memory ring, 8 x 8 blocks per warp) */
     FV_SPREAD_SCATTER = 2,    /* per-tile, warps add each source's footprint with shared atomics */
     FV_SPREAD_ATOMIC = 3,     /* one thread per source, global atomics on a cleared grid */
-    FV_SPREAD_TENSOR = 4      /* the gather with each warp's 8 x 8 block of cells summed on the tensor
-                                 cores (m16n8k8 TF32 products, three-term split for FP32 accuracy);
-                                 FV_MIXED two-dimensional grids without height terms, n_pol 1 or 4;
-                                 elsewhere it falls back to FV_SPREAD_GATHER */
+    FV_SPREAD_TENSOR = 4      /* an option, off by default: the gather of FV_MIXED two-dimensional grids
+                                 (no height terms, n_pol 1 or 4, w <= 8) with each warp's 8 x 8 block
+                                 of cells summed on the tensor cores (m16n8k8 TF32 products, three-term
+                                 split for FP32 accuracy) instead of by FP32 FMAs; elsewhere it falls
+                                 back to FV_SPREAD_GATHER */
 } fv_spread_method;
 
 /* Fill *o with defaults: FV_FP64, eps 1e-10, Gaussian beam 10 deg at 150 MHz,

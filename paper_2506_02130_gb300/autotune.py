@@ -13,10 +13,11 @@ Candidates (each meets the slice's transform tolerance by its choice of w):
   * sigma: 1.25 or 2 on the FP64 path; 1.5 or 2 on the mixed path, because the
     two deconvolutions amplify FP32 rounding too much at 1.25 (the plan
     rejects mixed plans below 1.5);
-  * spreading tile: "tensor" (mixed path: 32 x 16-cell tiles, one warp per
-    8 x 8 block summed with TF32 tensor-core products), "gather" (32 x 8-cell
-    tiles built from 8 x 4-cell source bins, one warp per 8 x 4 patch) or
-    "scatter" (32 x 16-cell tiles, one warp per source, shared-memory atomics);
+  * spreading tile: "gather" (the tile's sorted sources staged in shared
+    memory; on the mixed path's two-dimensional grids a persistent ring of
+    32 x 16-cell tiles, one warp per 8 x 8 block) or "scatter" (32 x 16-cell
+    tiles, one warp per source, shared-memory atomics).  The tensor-core form
+    of the gather is an explicit option, not a candidate;
   * FFT radix cap: 8 or 16 (the largest butterfly held in registers);
   * route (when the tuner is asked to choose it): "auto" (the lattice route of
     Section 2.2.1 when the array is a lattice and its grid is the smaller,
@@ -56,20 +57,19 @@ class Choice:
                 "transform": self.transform, "bin_size": tuple(self.bin_size)}
 
 
-DEFAULT = {fv.FV_FP64: Choice(2.0, "gather", 16), fv.FV_MIXED: Choice(2.0, "tensor", 8)}
+DEFAULT = {fv.FV_FP64: Choice(2.0, "gather", 16), fv.FV_MIXED: Choice(2.0, "gather", 8)}
 
 BIN_SHAPES = ((4, 4), (8, 8), (16, 4))
 
 
 def candidates(precision: int, routes=("auto",)) -> list[Choice]:
     sig = (1.25, 2.0) if precision == fv.FV_FP64 else (1.5, 2.0)
-    spreads = ("gather", "scatter") if precision == fv.FV_FP64 else ("tensor", "gather", "scatter")
-    return [Choice(s, sp, r, tr) for tr in routes for s in sig for sp in spreads for r in (8, 16)]
+    return [Choice(s, sp, r, tr) for tr in routes for s in sig for sp in ("gather", "scatter") for r in (8, 16)]
 
 
 def bin_candidates(best: Choice) -> list[Choice]:
-    """Second round: other bin shapes for a type-3 plan with a gather spreading."""
-    if best.spread not in ("gather", "tensor"):
+    """Second round: other bin shapes for a type-3 plan with the gather spreading."""
+    if best.spread != "gather":
         return []
     return [Choice(best.upsampfac, best.spread, best.fft_max_radix, "type3", b) for b in BIN_SHAPES]
 

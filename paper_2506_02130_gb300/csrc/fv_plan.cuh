@@ -118,6 +118,7 @@ struct fv_plan_s {
     int spread_req = 0;         // fv_opts.spread_method
     int fft_max_radix = 16;
     int spread_method = 0;      // resolved method
+    bool ring = false;          // FP32 2-D gather through the shared-memory ring (fv_spread_ring.cu)
     int bin_req[2] = {0, 0};    // fv_opts.bin_size
     int T[2] = {32, 32}, nbx = 1, nby = 1, f_top = 0;
     double qscale_top[3] = {0, 0, 0};

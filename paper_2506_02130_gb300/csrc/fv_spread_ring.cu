@@ -1,32 +1,31 @@
-// Gather spreading of FP32 two-dimensional grids with the tile sums on the tensor cores (Section 2.2,
-// step 1).
+// Gather spreading of FP32 two-dimensional grids through a shared-memory ring (Section 2.2, step 1).
 //
-// The grid value of cell (x, y) of one product is a sum of outer products over the sources j whose
-// footprint covers it,
-//     G(x, y) = sum_j c_j psi_y,j(y) psi_x,j(x),
-// i.e. for an 8 x 8 block of cells the matrix product D = A B with
-//     A[(ri, y)][j] = Re / Im (c_j) psi_y,j(y)     (16 x J: real and imaginary parts of the 8 rows)
-//     B[j][x]       = psi_x,j(x)                   (J x 8)
-// and J the candidate sources of the block.  One warp owns one block and one D fragment per product; it
-// takes its candidates eight at a time as one m16n8k8 TF32 product.  FP32 accuracy comes from the
-// three-term split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (a_hi = tf32(a), a_lo = a - a_hi, of which the
-// tensor core reads the leading 11 bits), which leaves a relative error near 2^-21 per product, with FP32
-// accumulation in the tensor core.
+// A CTA owns a 32 x 16 tile at a time (4 x 2 blocks of 8 x 8 cells): eight consumer warps, one per
+// block, and one producer warp.  CTAs are persistent (three per SM) and take tiles from an atomic
+// ticket.  A tile's candidates are the sources of the bins it maps to (one contiguous range of the sorted
+// sources per bin row); the producer copies them into shared memory in chunks of 128 with bulk
+// asynchronous copies into a three-stage ring (a full and an empty mbarrier per stage, every wait
+// bounded) and runs ahead across tile boundaries, so a tile's first chunks are in flight while the
+// consumers finish the previous one.  Each record already holds the source's kernel values (computed
+// once per slice by the prep kernel), so a consumer warp only selects the chunk's candidates that
+// overlap its block (ballot and prefix count, no shared atomics) and adds them; warps never wait for one
+// another except through the ring.  Every grid cell is stored once, with the x and y prescale of the FFT
+// passes applied.
 //
-// Operands are built in registers, which is why this uses the warp-level mma.sync form: the blocks' A and
-// B are sparse (a source covers at most 7 of a block's 8 rows and columns, about a quarter of them on
-// average) and change with every group of eight candidates, so staging them through shared memory in the
-// layouts tcgen05.mma reads would cost more than the products.
-//
-// A CTA owns a 32 x 16 tile at a time (4 x 2 blocks): eight consumer warps, one per block, and one
-// producer warp.  CTAs are persistent (three per SM) and take tiles from an atomic ticket.
-// The tile's candidates are the sources of the bins it maps to (one contiguous range of the sorted sources
-// per bin row); the producer copies them into shared memory in chunks of 128 with bulk asynchronous copies
-// into a three-stage ring (a full and an empty mbarrier per stage, every wait bounded).  Each record
-// already holds the source's kernel values (computed once per slice by the prep kernel), so a consumer
-// warp only selects the chunk's candidates that overlap its block (ballot and prefix count, no shared
-// atomics) and runs them through the tensor cores; warps never wait for one another except through the
-// ring.  Every grid cell is stored once, with the x and y prescale of the FFT passes applied.
+// The sum of a block's cells is
+//     G(x, y) = sum_j c_j psi_y,j(y) psi_x,j(x)
+// over its candidates j.  Two forms:
+//  * FP32 FMAs (the default): lane (x, y) with x = lane & 7 holds rows y = lane >> 3 and y + 4 of its
+//    column and adds c_j psi_x,j(x) psi_y,j(y) for every candidate, in FP32 with FP32 accumulation;
+//  * tensor cores (FV_SPREAD_TENSOR, an option): for an 8 x 8 block the sum is the matrix product D = A B
+//    with A[(ri, y)][j] = Re / Im (c_j) psi_y,j(y) (16 x J) and B[j][x] = psi_x,j(x) (J x 8), taken eight
+//    candidates at a time as m16n8k8 TF32 products with the three-term split
+//    a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (a_hi = tf32(a), a_lo = a - a_hi, of which the tensor core
+//    reads the leading 11 bits): a relative error near 2^-21 per product.  Its operands are built in
+//    registers, which is why it uses the warp-level mma.sync form: a block's A and B are sparse (a source
+//    covers at most 7 of its 8 rows and columns, about a quarter on average) and change with every group
+//    of eight candidates, so staging them through shared memory in the layouts tcgen05.mma reads would
+//    cost more than the products.
 #include "fv_staged.cuh"
 
 #include <algorithm>
@@ -69,8 +68,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 
 }  // namespace
 
-template <int NP>
-__global__ void __launch_bounds__(kTcThreads, 3) k_spread_mma(const int *__restrict__ offsets,
+template <int NP, bool TC>
+__global__ void __launch_bounds__(kTcThreads, 3) k_spread_ring(const int *__restrict__ offsets,
                                                             const TcRec *__restrict__ rec,
                                                             const cpx<float> *__restrict__ cs, SliceGeom g, TimeBin tb,
                                                             double r0, double r1, int tiles_x, int n_tiles,
@@ -253,8 +252,37 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_spread_mma(const int *__restr
                 L += __popc(m);
             }
             __syncwarp();
+            if (!TC) {
+                // FP32 FMAs: lane (x = lane & 7, rows lane >> 3 and + 4) adds every selected candidate's
+                // c psi_x(x) psi_y(y) into its two cells; out-of-footprint lanes add zero weights
+                const int lx = lane & 7, ly = lane >> 3;
+#pragma unroll 2
+                for (int e = 0; e < L; ++e) {
+                    const int ent = s_sel[warp][e];
+                    const int t = ent & 0xff;
+                    const TcRec &r = s_rec[b][t];
+                    const unsigned dx = (unsigned)(lx + 16 - ((ent >> 8) & 0xff));
+                    const unsigned dy0 = (unsigned)(ly + 16 - (ent >> 16)), dy1 = dy0 + 4u;
+                    const float wx = dx < (unsigned)kTcWmax ? r.wx[dx] : 0.0f;
+                    const float wy0 = dy0 < (unsigned)kTcWmax ? r.wy[dy0] : 0.0f;
+                    const float wy1 = dy1 < (unsigned)kTcWmax ? r.wy[dy1] : 0.0f;
+                    const float4 *c4 = reinterpret_cast<const float4 *>(&s_cs[b][t * kCsw]);
+                    float4 cv[NP > 1 ? 2 : 1];
+#pragma unroll
+                    for (int q = 0; q < (NP > 1 ? 2 : 1); ++q) cv[q] = c4[q];
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        const float4 u = cv[p >> 1];
+                        const float cr = ((p & 1) ? u.z : u.x) * wx, ci = ((p & 1) ? u.w : u.y) * wx;
+                        d[p][0] = fmaf(wy0, cr, d[p][0]);
+                        d[p][1] = fmaf(wy0, ci, d[p][1]);
+                        d[p][2] = fmaf(wy1, cr, d[p][2]);
+                        d[p][3] = fmaf(wy1, ci, d[p][3]);
+                    }
+                }
+            }
             // eight candidates per product: this lane supplies k = tq (h = 0) and k = tq + 4 (h = 1)
-            for (int e = 0; e < L; e += 8) {
+            for (int e = 0; TC && e < L; e += 8) {
                 uint32_t bh[2], bl[2];
                 float wy[2];
                 float4 cv[2][NP > 1 ? 2 : 1];
@@ -299,7 +327,22 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_spread_mma(const int *__restr
         __syncwarp();
         if (lane == 0) mbar_arrive(&s_empty[b]);      // after the stage was read
         if (n < 0) {
-            if (tile >= 0) {
+            if (tile >= 0 && !TC) {
+                // this lane's cells: (bx0 + lane & 7, by0 + lane >> 3) in d[p][0..1], four rows down in d[p][2..3]
+                const int x = bx0 + (lane & 7);
+                const float *px = (const float *)g.pre_x, *py = (const float *)g.pre_y;
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int y = by0 + (lane >> 3) + 4 * c;
+                    if (x < nx && y < ny) {
+                        const float sc = (py ? py[y] : 1.0f) * (px ? px[x] : 1.0f);
+#pragma unroll
+                        for (int p = 0; p < NP; ++p)
+                            grid[((size_t)p * ny + y) * nx + x] = cmk<float>(d[p][2 * c] * sc, d[p][2 * c + 1] * sc);
+                    }
+                }
+            }
+            if (tile >= 0 && TC) {
                 // D fragment of product p: d0 = Re (row gq, column 2 tq), d1 = Re (gq, 2 tq + 1),
                 // d2 = Im (gq, 2 tq), d3 = Im (gq, 2 tq + 1); rows are y and columns x of the block
                 const int gy = by0 + gq, gx = bx0 + 2 * tq;
@@ -317,6 +360,8 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_spread_mma(const int *__restr
                         }
                     }
                 }
+            }
+            if (tile >= 0) {
 #pragma unroll
                 for (int p = 0; p < NP; ++p)
 #pragma unroll
@@ -330,11 +375,11 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_spread_mma(const int *__restr
     }
 }
 
-// The tensor-core gather for an FP32 two-dimensional slice (n_pol 1 or 4, w <= 8) from tensor-core records
-// (launch_prep_tc); writes every cell of grid [n_pol][ny][nx].
-cudaError_t launch_spread_mma(const int *offsets, const TcRec *rec, const cpx<float> *cs, const SliceGeom &g,
-                              const TimeBin &tb, double r0, double r1, int *tile_ctr, int *status, cpx<float> *grid,
-                              cudaStream_t st)
+// The ring gather for an FP32 two-dimensional slice (n_pol 1 or 4, w <= 8) from ring records (launch_prep_tc);
+// tensor: the block sums on the tensor cores.  Writes every cell of grid [n_pol][ny][nx].
+cudaError_t launch_spread_ring(const int *offsets, const TcRec *rec, const cpx<float> *cs, const SliceGeom &g,
+                               const TimeBin &tb, double r0, double r1, int *tile_ctr, int *status, cpx<float> *grid,
+                               bool tensor, cudaStream_t st)
 {
     if (g.d != 2 || g.K != 0 || g.w > kTcWmax || (g.n_pol != 1 && g.n_pol != 4)) return cudaErrorInvalidValue;
     static int sms[64] = {};
@@ -350,12 +395,15 @@ cudaError_t launch_spread_mma(const int *offsets, const TcRec *rec, const cpx<fl
     const int tiles_x = (g.dim[0].nf1 + kTcTileX - 1) / kTcTileX;
     const int n_tiles = tiles_x * ((g.dim[1].nf1 + kTcTileY - 1) / kTcTileY);
     const unsigned blocks = (unsigned)std::max(1, std::min(n_tiles, 3 * sms[dev]));
-    if (g.n_pol == 4)
-        k_spread_mma<4><<<blocks, kTcThreads, 0, st>>>(offsets, rec, cs, g, tb, r0, r1, tiles_x, n_tiles, tile_ctr, status,
-                                                       grid);
-    else
-        k_spread_mma<1><<<blocks, kTcThreads, 0, st>>>(offsets, rec, cs, g, tb, r0, r1, tiles_x, n_tiles, tile_ctr, status,
-                                                       grid);
+#define FV_RING_ARGS offsets, rec, cs, g, tb, r0, r1, tiles_x, n_tiles, tile_ctr, status, grid
+    if (g.n_pol == 4) {
+        if (tensor) k_spread_ring<4, true><<<blocks, kTcThreads, 0, st>>>(FV_RING_ARGS);
+        else k_spread_ring<4, false><<<blocks, kTcThreads, 0, st>>>(FV_RING_ARGS);
+    } else {
+        if (tensor) k_spread_ring<1, true><<<blocks, kTcThreads, 0, st>>>(FV_RING_ARGS);
+        else k_spread_ring<1, false><<<blocks, kTcThreads, 0, st>>>(FV_RING_ARGS);
+    }
+#undef FV_RING_ARGS
     return cudaGetLastError();
 }
 

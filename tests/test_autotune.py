@@ -11,9 +11,8 @@ def test_candidates_respect_the_mixed_sigma_floor():
     assert {c.transform for c in AT.candidates(fv.FV_MIXED)} == {"auto"}
     assert {c.upsampfac for c in mixed} == {1.5, 2.0}
     assert {c.upsampfac for c in fp64} == {1.25, 2.0}
-    assert {c.spread for c in mixed} == {"tensor", "gather", "scatter"}
-    assert {c.spread for c in fp64} == {"gather", "scatter"}        # the tensor-core form is FP32 only
-    for cs, n in ((mixed, 24), (fp64, 16)):
+    for cs, n in ((mixed, 16), (fp64, 16)):
+        assert {c.spread for c in cs} == {"gather", "scatter"}
         assert {c.fft_max_radix for c in cs} == {8, 16}
         assert {c.transform for c in cs} == {"auto", "type3"}
         assert len(set(cs)) == n
@@ -48,9 +47,8 @@ def test_tuner_takes_the_fastest_candidate_per_class(tmp_path):
     keys = {AT.key_of(s) for s in slices}
     assert set(table) == keys
     # one representative per class, every candidate tried once on it (no bin round: the winners are not
-    # type-3 gather plans): 16 candidates on the FP64 path, 24 on the mixed path (the tensor-core form too)
-    n_fp64 = sum(1 for k in keys if k.startswith("fp64"))
-    assert len(calls) == 16 * n_fp64 + 24 * (len(keys) - n_fp64)
+    # type-3 gather plans)
+    assert len(calls) == 16 * len(keys)
     for s in slices:
         c = t.choice(AT.precision_of(s), len(s.problem.ant_enu), s.problem.sky.n_src)
         assert c == (AT.Choice(2.0, "scatter", 8) if s.precision == "fp64" else AT.Choice(1.5, "gather", 16))
@@ -107,7 +105,7 @@ def test_bin_shapes_are_tuned_for_a_type3_gather_winner():
     table = t.tune(slices, AT.key_of, AT.precision_of)
     (best,) = table.values()
     assert best == AT.Choice(2.0, "gather", 8, "type3", (4, 4))
-    assert len(calls) == 24 + len(AT.BIN_SHAPES)       # the mixed path has 24 first-round candidates
+    assert len(calls) == 16 + len(AT.BIN_SHAPES)
     assert best.plan_kwargs()["bin_size"] == (4, 4)
 
 
@@ -131,4 +129,4 @@ def test_default_route_set_is_auto_only_and_an_auto_type3_winner_gets_bins():
     t = AT.Autotuner(timer)
     (best,) = t.tune(slices, AT.key_of, AT.precision_of).values()
     assert tuple(best.bin_size) == (8, 8) and best.transform == "type3"
-    assert len(t.timings[AT.key_of(slices[0])]) == 12 + len(AT.BIN_SHAPES)   # 2 sigma x 3 forms x 2 radix caps
+    assert len(t.timings[AT.key_of(slices[0])]) == 8 + len(AT.BIN_SHAPES)
