@@ -121,8 +121,10 @@ def peaks():
 
 
 # the source files that define each kernel class of the type-3 route (plus the shared device header)
-KERNEL_FILES = {"bin": "fv_spread.cu", "prep": "fv_spread.cu", "spread": "fv_spread.cu", "fft_x": "fv_fft.cu",
-                "fft_y": "fv_fft.cu", "fft_z": "fv_fft.cu", "interp": "fv_kernels.cu", "scatter": "fv_kernels.cu"}
+KERNEL_FILES = {"bin": ("fv_spread.cu", "fv_staged.cuh"), "prep": ("fv_spread.cu", "fv_staged.cuh"),
+                "spread": ("fv_spread.cu", "fv_spread_ring.cu", "fv_staged.cuh"), "fft_x": ("fv_fft.cu",),
+                "fft_y": ("fv_fft.cu",), "fft_z": ("fv_fft.cu",), "interp": ("fv_kernels.cu",),
+                "scatter": ("fv_kernels.cu",)}
 
 
 def kernel_source_hash(kernel_class):
@@ -130,10 +132,9 @@ def kernel_source_hash(kernel_class):
     capture holds only while they are unchanged."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2506_02130_gb300", "csrc")
-    for n in ("fv_internal.cuh", KERNEL_FILES.get(kernel_class, "")):
-        if n:
-            with open(os.path.join(csrc, n), "rb") as f:
-                h.update(n.encode() + f.read())
+    for n in ("fv_internal.cuh",) + KERNEL_FILES.get(kernel_class, ()):
+        with open(os.path.join(csrc, n), "rb") as f:
+            h.update(n.encode() + f.read())
     return h.hexdigest()[:16]
 
 
@@ -795,6 +796,22 @@ def run_sim(args, rank, world, local, dist):
                 "share_of_kernel_time": d["ms"] / sum(v["ms"] for v in prof.values()),
                 "timing": "CUDA events around each launch, one step of a one-stream copy of the plan after the "
                           "timed region (kernels do not overlap, so each event pair times one kernel alone)"}
+        if dom == "spread":
+            # the spreading's arithmetic: n_pol w^2 complex-by-real multiply-adds (4 flops) per visible source
+            # (about half the sky), against the FP32 FMA peak of 152 SMs x 128 lanes x 2 flops at the
+            # maximum SM clock
+            w = info["kernel_width"]
+            flops = 0.5 * prob.sky.n_src * plan.n_pol * w * w * 4.0 if plan else 0.0
+            fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12
+            useful = flops / (d["ms"] / d["launches"] / 1e3) / 1e12
+            roof["secondary"] = {"bound": "alu", "achieved": useful, "peak": fp32_peak, "unit": "TFLOP/s",
+                                 "frac": useful / fp32_peak,
+                                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
+                                 "what": "useful FP32 flops of the spreading (n_pol w^2 complex x real "
+                                         "multiply-adds per visible source)"}
+            roof["note"] = ("neither bound is reached: the spreading is bound by instruction issue and "
+                            "shared-memory latency (a warp's lanes cover 8 x 8 cells, of which a source "
+                            "reaches about a quarter); ncu figures in profiles/")
     gpu_launches = int(sum(v["launches"] for k, v in prof.items() if k != "memset")) * args.steps
 
     # ---- end to end through the C ABI with host buffers (pinned): set_sky copies the step's inputs in,
@@ -983,7 +1000,8 @@ def run_sim(args, rank, world, local, dist):
                        "eps": eps, "kernel_width": info["kernel_width"], "upsampfac": info["upsampfac"],
                        "nf1_max": info["nf1_max"], "nf2_max": info["nf2_max"],
                        "streams": args.streams or (4 if args.transform == "basis" else 8),
-                       "spread": args.spread, "transform": args.transform, "vis_per_step": n_vis,
+                       "spread": info.get("spread", args.spread), "spread_requested": args.spread,
+                       "transform": args.transform, "vis_per_step": n_vis,
                        "setup_seconds": setup_s,
                        "l2": "inputs larger than L2: a step streams every slice's grid through the reused "
                              f"workspaces (~{info['workspace_bytes'] / 1e6:.0f} MB) and reads "

@@ -109,7 +109,17 @@ struct SliceGeom {
     int K;
     double hc, hs;
     float hc_f, hs_inv_f;
+    // nu and beta rounded to FP32 once on the host (a per-thread FP64 -> FP32 conversion runs on the
+    // narrow FP64 pipe)
+    float nu_f, beta_f;
 };
+
+template <class G> __device__ __forceinline__ G geom_nu(const SliceGeom &g);
+template <> __device__ __forceinline__ double geom_nu<double>(const SliceGeom &g) { return g.nu; }
+template <> __device__ __forceinline__ float geom_nu<float>(const SliceGeom &g) { return g.nu_f; }
+template <class G> __device__ __forceinline__ G geom_beta(const SliceGeom &g);
+template <> __device__ __forceinline__ double geom_beta<double>(const SliceGeom &g) { return g.beta; }
+template <> __device__ __forceinline__ float geom_beta<float>(const SliceGeom &g) { return g.beta_f; }
 
 // J_q(x) by its power series sum_m (-1)^m (x/2)^(2m+q) / (m! (m+q)!) (FP64; |x| is a few units at most here,
 // so the terms fall fast and do not cancel badly)
@@ -316,9 +326,9 @@ __device__ __forceinline__ int source_strengths(const SliceGeom &g, S s0, S s1, 
     // the beam in the grid precision (sin of the zenith angle from the direction's E, N components)
     const G e0 = (G)s0, e1 = (G)s1;
     const G rho = sqrt(e0 * e0 + e1 * e1);
-    const G A = beam_voltage<G>(g.beam, e0, e1, rho, (G)s2, (G)g.nu, f);
+    const G A = beam_voltage<G>(g.beam, e0, e1, rho, (G)s2, geom_nu<G>(g), f);
     // A_i A_j: the two antennas' voltages (one shared beam: A^2)
-    const G A2 = g.two_beams ? A * beam_voltage<G>(g.beam2, e0, e1, rho, (G)s2, (G)g.nu, f) : A * A;
+    const G A2 = g.two_beams ? A * beam_voltage<G>(g.beam2, e0, e1, rho, (G)s2, geom_nu<G>(g), f) : A * A;
     const void *fl = g.flux_t ? g.flux_t : flux;
     auto ld = [&](int k) -> G {
         const size_t idx = flux_index(g, k, n, n_src, n_freq, f);

@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(128) k_spread_direct(const double *__restrict_
         double q = st[i] * g.dim[i].qscale;
         double l0 = ceil(q - 0.5 * w);
         G fr = (G)(l0 - q);                        // offset of cell l0 from q, in [-w/2, 1-w/2)
-        for (int j = 0; j < w; ++j) kv[i][j] = es_kernel(two_over_w * (fr + (G)j), (G)g.beta);
+        for (int j = 0; j < w; ++j) kv[i][j] = es_kernel(two_over_w * (fr + (G)j), geom_beta<G>(g));
         int b = (int)l0 + g.dim[i].nf1 / 2;
         base[i] = b;
     }
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(128) k_interp(const cpx<G> *__restrict__ band,
         double p = (x[i] - g.dim[i].D) * g.dim[i].pscale;
         double m0 = ceil(p - 0.5 * w);
         G fr = (G)(p - m0);                            // offset of p from cell m0, in (w/2-1, w/2]
-        for (int j = 0; j < w; ++j) kv[i][j] = es_kernel(two_over_w * (fr - (G)j), (G)g.beta);
+        for (int j = 0; j < w; ++j) kv[i][j] = es_kernel(two_over_w * (fr - (G)j), geom_beta<G>(g));
         base[i] = (int)m0 + g.dim[i].H;
     }
     const int np = g.n_pol;
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(256) k_interp_zdirect(const cpx<G> *__restrict
     if (u >= n_u) return;
     const int w = g.w;
     const G two_over_w = (G)(2.0 / w);
-    const G beta = (G)g.beta;
+    const G beta = geom_beta<G>(g);
     double x[3] = {0.0, 0.0, 0.0};
     G fr[3];
     int m0[3] = {0, 0, 0};
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(256) k_interp_zrow(const cpx<float> *__restric
     if (u >= n_u) return;
     const int w = g.w;
     const float two_over_w = (float)(2.0 / w);
-    const float beta = (float)g.beta;
+    const float beta = g.beta_f;
     double x[3] = {0.0, 0.0, 0.0};
     float fr[3];
     int m0[3] = {0, 0, 0};
@@ -632,7 +632,7 @@ __global__ void __launch_bounds__(kIbThreads) k_interp_batch(const cpx<G> *__res
     __shared__ cpx<double> s_post[kIbTargets];
     const long u0 = (long)blockIdx.x * kIbTargets;
     const int w = g.w;
-    const G two_over_w = (G)(2.0 / w), beta = (G)g.beta;
+    const G two_over_w = (G)(2.0 / w), beta = geom_beta<G>(g);
     // --- per-target set-up, one target per thread
     if (threadIdx.x < kIbTargets) {
         const int tl = threadIdx.x;
@@ -793,7 +793,7 @@ __global__ void __launch_bounds__(256) k_interp_warp(const cpx<G> *__restrict__ 
     const long u = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (u >= n_u) return;   // whole warps
     const int w = g.w;
-    const G two_over_w = (G)(2.0 / w), beta = (G)g.beta;
+    const G two_over_w = (G)(2.0 / w), beta = geom_beta<G>(g);
     // FP64 set-up on lane 0
     int m0 = 0, m1 = 0;
     G f0 = (G)0, f1 = (G)0, phr = (G)0;

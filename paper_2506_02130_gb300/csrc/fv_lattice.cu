@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256) k_prep_lattice(const double *__restrict__
     frac[2 * (size_t)n_src + i] = (G)(2.0 * s2 - 1.0);   // Chebyshev argument of the height factor
     // kernel values of the x and y footprints, once per source: kw[i][0..w) (x), kw[i][w..2w) (y)
     G *kw = frac + 3 * (size_t)n_src + (size_t)i * 2 * g.w;
-    const G two_over_w = (G)2 / (G)g.w, beta = (G)g.beta;
+    const G two_over_w = (G)2 / (G)g.w, beta = geom_beta<G>(g);
     const G fx = frac[i], fy = frac[(size_t)n_src + i];
     for (int j = 0; j < g.w; ++j) {
         kw[j] = lat_es<G>(two_over_w * (fx + (G)j), beta);

@@ -495,6 +495,8 @@ static fv_status prepare(fv_plan_s *p)
         g.d = p->d;
         g.w = w;
         g.beta = p->beta;
+        g.nu_f = (float)g.nu;
+        g.beta_f = (float)g.beta;
         g.n_pol = p->n_pol;
         g.polarized = p->polarized;
         g.n_stokes = p->n_stokes;
@@ -961,6 +963,7 @@ static fv_status prepare_basis(fv_plan_s *p)
     g.d = p->d;
     g.w = w;
     g.beta = p->beta;
+    g.beta_f = (float)p->beta;
     g.polarized = 0;
     g.n_stokes = 1;
     g.beam = p->beam;
