@@ -95,7 +95,7 @@ typedef struct {
                                  (4 for FV_TRANSFORM_BASIS, whose times each fill the GPU) */
     int spread_method;        /* fv_spread_method; FV_SPREAD_AUTO picks the fastest that fits */
     int fft_max_radix;        /* largest FFT stage radix: 8 (fewer registers, more stages) or 16;
-                                 0 = 8 for FV_MIXED, 16 for FV_FP64 */
+                                 0 = 16 */
     int transform;            /* fv_transform: which transform evaluates a slice */
     double lattice_tol_m;     /* largest distance (m) of an antenna from its lattice point, and of its
                                  height from the first antenna's, still accepted as a lattice;

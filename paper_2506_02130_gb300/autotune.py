@@ -57,7 +57,7 @@ class Choice:
                 "transform": self.transform, "bin_size": tuple(self.bin_size)}
 
 
-DEFAULT = {fv.FV_FP64: Choice(2.0, "gather", 16), fv.FV_MIXED: Choice(2.0, "gather", 8)}
+DEFAULT = {fv.FV_FP64: Choice(2.0, "gather", 16), fv.FV_MIXED: Choice(2.0, "gather", 16)}
 
 BIN_SHAPES = ((4, 4), (8, 8), (16, 4))
 

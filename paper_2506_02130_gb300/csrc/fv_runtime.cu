@@ -1403,7 +1403,7 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
     p->heights_req = o->heights;
     // radix 8 needs fewer registers (more CTAs per SM), which wins in FP32; FP64 uses the same
     // register count either way and prefers fewer stages
-    p->fft_max_radix = o->fft_max_radix > 0 ? o->fft_max_radix : (o->precision == FV_MIXED ? 8 : 16);
+    p->fft_max_radix = o->fft_max_radix > 0 ? o->fft_max_radix : 16;
     p->transform_req = o->transform;
     p->use_basis = o->transform == FV_TRANSFORM_BASIS;
     p->n_basis_req = p->use_basis ? o->n_basis : 0;
