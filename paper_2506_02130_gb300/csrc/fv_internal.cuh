@@ -112,6 +112,14 @@ struct SliceGeom {
     // nu and beta rounded to FP32 once on the host (a per-thread FP64 -> FP32 conversion runs on the
     // narrow FP64 pipe)
     float nu_f, beta_f;
+    // FP32 two-dimensional interpolation without FP64: the target's grid coordinate is
+    // p_i = -(kappa pscale_i) (b_i - bcen_i) and its postphase argument -kappa (b . C), formed as
+    // double-float products of the per-channel factors (a_i = kappa pscale_i and kappa as float pairs)
+    // and the per-target tables tgt_db[u] = (b_x - bcen_x, b_y - bcen_y) and tgt_bc[u] = b . C (float
+    // pairs, channel independent; nullptr: the FP64 set-up)
+    const float4 *tgt_db;
+    const float2 *tgt_bc;
+    float a_hi[2], a_lo[2], kap_hi, kap_lo;
 };
 
 template <class G> __device__ __forceinline__ G geom_nu(const SliceGeom &g);
@@ -208,6 +216,25 @@ template <> __device__ __forceinline__ double voltage<double>(const BeamParams &
     }
     return 1.0;
 }
+// 2 J1(x) / x in FP32 for x >= 0 from the polynomial approximations of Abramowitz & Stegun (1964),
+// 9.4.4 (|x| <= 3: error of J1(x)/x below 1.3e-8) and 9.4.6 (x >= 3: modulus and phase in 3/x, errors
+// below 4e-8 and 9e-8), so that the FP32 beam needs no FP64 arithmetic
+__device__ __forceinline__ float airy_2j1_over_x(float x)
+{
+    if (x <= 3.0f) {
+        const float y = (x * (1.0f / 3.0f)) * (x * (1.0f / 3.0f));
+        const float p = 0.5f + y * (-0.56249985f + y * (0.21093573f + y * (-0.03954289f + y * (0.00443319f +
+                        y * (-0.00031761f + y * 0.00001109f)))));
+        return 2.0f * p;
+    }
+    const float z = 3.0f / x;
+    const float f1 = 0.79788456f + z * (0.00000156f + z * (0.01659667f + z * (0.00017105f + z * (-0.00249511f +
+                     z * (0.00113653f + z * (-0.00020033f))))));
+    const float th = x - 2.35619449f + z * (0.12499612f + z * (0.00005650f + z * (-0.00637879f + z * (0.00074348f +
+                     z * (0.00079824f + z * (-0.00029166f))))));
+    return 2.0f * f1 * cosf(th) / (x * sqrtf(x));
+}
+
 template <> __device__ __forceinline__ float voltage<float>(const BeamParams &b, float rho, float s2, float nu)
 {
     if (b.kind == 0) {
@@ -217,7 +244,7 @@ template <> __device__ __forceinline__ float voltage<float>(const BeamParams &b,
     }
     if (b.kind == 1) {
         float x = (b.pf > 0.0f ? b.pf : (float)(M_PI * b.p0 / FV_C_LIGHT)) * nu * rho;
-        return x < 1e-4f ? 1.0f - 0.125f * x * x : 2.0f * j1f(x) / x;
+        return airy_2j1_over_x(x);
     }
     return 1.0f;
 }

@@ -794,10 +794,41 @@ __global__ void __launch_bounds__(256) k_interp_warp(const cpx<G> *__restrict__ 
     if (u >= n_u) return;   // whole warps
     const int w = g.w;
     const G two_over_w = (G)(2.0 / w), beta = geom_beta<G>(g);
-    // FP64 set-up on lane 0
     int m0 = 0, m1 = 0;
     G f0 = (G)0, f1 = (G)0, phr = (G)0;
-    if (lane == 0) {
+    if (sizeof(G) == 4 && g.tgt_db) {
+        // FP32 set-up on every lane, no FP64: double-float products of the per-channel factors and the
+        // target's float pairs, then the first footprint cell m = ceil(p - w/2) and f = p - m brought into
+        // (w/2 - 1, w/2] (as the FP64 form), and the postphase reduced by 2 pi = 6.2831855 - 1.7484555e-7
+        const float4 db = g.tgt_db[u];
+        const float2 bc = g.tgt_bc[u];
+        const float hw = 0.5f * (float)w;
+        float mm[2], ff[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const float dh = i == 0 ? db.x : db.z, dl = i == 0 ? db.y : db.w;
+            float ph = g.a_hi[i] * dh;
+            float pl = fmaf(g.a_hi[i], dh, -ph) + (g.a_hi[i] * dl + g.a_lo[i] * dh);
+            ph = -ph;
+            pl = -pl;                                   // p = ph + pl
+            float m = ceilf(ph - hw);
+            float f = (ph - m) + pl;
+            if (f > hw) { m += 1.0f; f -= 1.0f; }
+            else if (f <= hw - 1.0f) { m -= 1.0f; f += 1.0f; }
+            mm[i] = m;
+            ff[i] = f;
+        }
+        m0 = (int)mm[0];
+        m1 = (int)mm[1];
+        f0 = (G)ff[0];
+        f1 = (G)ff[1];
+        float qh = g.kap_hi * bc.x;
+        const float ql = fmaf(g.kap_hi, bc.x, -qh) + (g.kap_hi * bc.y + g.kap_lo * bc.x);
+        qh = -qh;                                        // argument -kappa (b . C) = qh - ql
+        const float k = rintf(qh * 0.15915494f);
+        phr = (G)(fmaf(-k, -1.7484555e-7f, fmaf(-k, 6.2831855f, qh)) - ql);
+    } else if (lane == 0) {
+        // FP64 set-up on lane 0
         double ph = 0.0;
         double fr[2];
         int mm[2];
@@ -817,10 +848,12 @@ __global__ void __launch_bounds__(256) k_interp_warp(const cpx<G> *__restrict__ 
         ph -= 6.283185307179586476925 * rint(ph * 0.15915494309189533577);
         phr = (G)ph;
     }
-    m0 = __shfl_sync(0xffffffffu, m0, 0);
-    m1 = __shfl_sync(0xffffffffu, m1, 0);
-    f0 = __shfl_sync(0xffffffffu, f0, 0);
-    f1 = __shfl_sync(0xffffffffu, f1, 0);
+    if (!(sizeof(G) == 4 && g.tgt_db)) {
+        m0 = __shfl_sync(0xffffffffu, m0, 0);
+        m1 = __shfl_sync(0xffffffffu, m1, 0);
+        f0 = __shfl_sync(0xffffffffu, f0, 0);
+        f1 = __shfl_sync(0xffffffffu, f1, 0);
+    }
     const int J = 32 / w;
     const int dx = lane / J, j = lane - dx * J;
     const bool on = dx < w;
@@ -852,7 +885,7 @@ __global__ void __launch_bounds__(256) k_interp_warp(const cpx<G> *__restrict__ 
             }
         }
     }
-    const G phs = __shfl_sync(0xffffffffu, phr, 0);
+    const G phs = (sizeof(G) == 4 && g.tgt_db) ? phr : __shfl_sync(0xffffffffu, phr, 0);
     G sp, cp;
     if (sizeof(G) == 4) {
         float a, b;

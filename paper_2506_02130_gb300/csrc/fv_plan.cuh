@@ -62,6 +62,12 @@ struct fv_plan_s {
     std::vector<int> bl2u;           // [n_bl]
     double bcen[3] = {0, 0, 0}, bhalf[3] = {0, 0, 0};
     double *d_bu = nullptr, *d_dec = nullptr;
+    // per unique target, float pairs for the FP32 interpolation set-up (SliceGeom::tgt_db, tgt_bc)
+    float4 *d_tgt_db = nullptr;
+    float2 *d_tgt_bc = nullptr;
+    int tgt_n = 0;
+    std::vector<float4> h_tgt_db;
+    std::vector<float2> h_tgt_bc;
     int *d_bl2u = nullptr;
 
     // sky

@@ -526,6 +526,13 @@ static fv_status prepare(fv_plan_s *p)
             p->tw_off[(size_t)f * 3 + i] = tw_total;
             tw_total += dg.M;
         }
+        for (int i = 0; i < 2; ++i) {
+            const double a = g.kappa * g.dim[i].pscale;
+            g.a_hi[i] = (float)a;
+            g.a_lo[i] = (float)(a - (double)g.a_hi[i]);
+        }
+        g.kap_hi = (float)g.kappa;
+        g.kap_lo = (float)(g.kappa - (double)g.kap_hi);
         // buffer sizes (complex elements) for this channel
         const DimGeom *D = g.dim;
         size_t grid_c = (size_t)p->n_pol * D[0].nf1 * D[1].nf1 * D[2].nf1;
@@ -554,6 +561,35 @@ static fv_status prepare(fv_plan_s *p)
             sig.push_back(p->gf[f].dim[i].nf1);
             sig.push_back(p->gf[f].dim[i].M);
         }
+    // per-target float pairs of the FP32 interpolation set-up (they depend on the sky's centre C)
+    if (p->n_u > 0) {
+        if (p->tgt_n != p->n_u) {
+            dfree_t(p->d_tgt_db);
+            dfree_t(p->d_tgt_bc);
+            CK(cudaMalloc(&p->d_tgt_db, (size_t)p->n_u * sizeof(float4)));
+            CK(cudaMalloc(&p->d_tgt_bc, (size_t)p->n_u * sizeof(float2)));
+            p->tgt_n = p->n_u;
+        }
+        p->h_tgt_db.resize(p->n_u);
+        p->h_tgt_bc.resize(p->n_u);
+        auto pair = [](double v, float &hi, float &lo) {
+            hi = (float)v;
+            lo = (float)(v - (double)hi);
+        };
+        for (int u = 0; u < p->n_u; ++u) {
+            const double *b = &p->bu[3 * (size_t)u];
+            float4 &t = p->h_tgt_db[u];
+            pair(b[0] - p->bcen[0], t.x, t.y);
+            pair(b[1] - p->bcen[1], t.z, t.w);
+            double bc = 0.0;
+            for (int i = 0; i < p->d; ++i) bc += b[i] * p->C[i];
+            pair(bc, p->h_tgt_bc[u].x, p->h_tgt_bc[u].y);
+        }
+        CK(cudaMemcpyAsync(p->d_tgt_db, p->h_tgt_db.data(), (size_t)p->n_u * sizeof(float4), cudaMemcpyHostToDevice,
+                           p->stream));
+        CK(cudaMemcpyAsync(p->d_tgt_bc, p->h_tgt_bc.data(), (size_t)p->n_u * sizeof(float2), cudaMemcpyHostToDevice,
+                           p->stream));
+    }
     const bool reuse = p->d_pre != nullptr && sig == p->geo_sig;
     if (!reuse) free_geometry(p);
     p->geo_sig.clear();
@@ -759,6 +795,8 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
         for (const auto &gr : p->groups) {
             if (gr.u1 <= gr.u0) continue;
             SliceGeom g = slice_geom_for(p, f, t, gr);
+            g.tgt_db = p->d_tgt_db && p->tgt_n == p->n_u ? p->d_tgt_db + gr.u0 : nullptr;
+            g.tgt_bc = g.tgt_db ? p->d_tgt_bc + gr.u0 : nullptr;
             const int nug = gr.u1 - gr.u0;
             const double *bug = p->d_bu + 3 * (size_t)gr.u0, *decg = p->d_dec + gr.u0;
             cpx<double> *Vug = wk.Vu + (size_t)gr.u0 * p->n_pol;
@@ -1566,6 +1604,9 @@ static fv_status setup_array(fv_plan_s *p)
     }
     dfree_t(p->d_bu);
     dfree_t(p->d_dec);
+    dfree_t(p->d_tgt_db);
+    dfree_t(p->d_tgt_bc);
+    p->tgt_n = 0;
     dfree_t(p->d_bl2u);
     dfree_t(p->d_bln);
     dfree_t(p->d_grp_bl);
@@ -1904,6 +1945,9 @@ fv_status fv_destroy(fv_plan_t p)
     dfree_t(p->d_glw);
     dfree_t(p->d_bu);
     dfree_t(p->d_dec);
+    dfree_t(p->d_tgt_db);
+    dfree_t(p->d_tgt_bc);
+    p->tgt_n = 0;
     dfree_t(p->d_bl2u);
     dfree_t(p->d_bln);
     dfree_t(p->d_grp_bl);

@@ -270,14 +270,15 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_spread_ring(const int *__rest
                     float4 cv[NP > 1 ? 2 : 1];
 #pragma unroll
                     for (int q = 0; q < (NP > 1 ? 2 : 1); ++q) cv[q] = c4[q];
+                    const float k0 = wx * wy0, k1 = wx * wy1;     // the two cells' kernel weights
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
                         const float4 u = cv[p >> 1];
-                        const float cr = ((p & 1) ? u.z : u.x) * wx, ci = ((p & 1) ? u.w : u.y) * wx;
-                        d[p][0] = fmaf(wy0, cr, d[p][0]);
-                        d[p][1] = fmaf(wy0, ci, d[p][1]);
-                        d[p][2] = fmaf(wy1, cr, d[p][2]);
-                        d[p][3] = fmaf(wy1, ci, d[p][3]);
+                        const float cr = (p & 1) ? u.z : u.x, ci = (p & 1) ? u.w : u.y;
+                        d[p][0] = fmaf(k0, cr, d[p][0]);
+                        d[p][1] = fmaf(k0, ci, d[p][1]);
+                        d[p][2] = fmaf(k1, cr, d[p][2]);
+                        d[p][3] = fmaf(k1, ci, d[p][3]);
                     }
                 }
             }
