@@ -207,6 +207,9 @@ cudaError_t alloc_workspaces(const fv_plan_s::WsNeed &need, int n, std::vector<f
 // The default {0, 0, 0} (nt 0 = the plan's n_time) is the plan's full [n_freq][n_time] layout.
 struct OutMap {
     int f0 = 0, t0 = 0, nt = 0;
+    // pinned host memory laid out like vis, or nullptr: each slice is copied there (device to host, on
+    // the slice's stream) as soon as it is written, so the copies overlap the other slices' kernels
+    char *host = nullptr;
 };
 // Slices [k_begin, k_end) (index t * n_freq + f) of plan p, on stream st with workspace wk,
 // written into vis (slice_bytes per slice, placed by om).

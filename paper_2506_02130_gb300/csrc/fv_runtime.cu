@@ -738,6 +738,11 @@ static fv_status run_slices_lattice(fv_plan_s *p, fv_plan_s::Workspace &wk, cuda
                                         p->precision == FV_FP64, st));
             CK(prof_end(p, (double)nbl * (8.0 + lg.K * (np * es + (wq ? 16.0 : 0.0))) + (double)slice_bytes));
         }
+        if (om.host) {
+            const int ntm = om.nt > 0 ? om.nt : nt;
+            const size_t off = ((size_t)(f - om.f0) * ntm + (t - om.t0)) * slice_bytes;
+            CK(cudaMemcpyAsync(om.host + off, vis + off, slice_bytes, cudaMemcpyDeviceToHost, st));
+        }
     }
     return FV_OK;
 }
@@ -885,6 +890,7 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
         CK(prof_begin(p, PC_SCATTER, st));
         CK(launch_scatter(wk.Vu, p->d_bl2u, p->n_bl, p->n_pol, out, p->precision == FV_FP64, st));
         CK(prof_end(p, (double)p->n_bl * (4 + p->n_pol * 16.0) + (double)slice_bytes));
+        if (om.host) CK(cudaMemcpyAsync(om.host + (out - vis), out, slice_bytes, cudaMemcpyDeviceToHost, st));
     }
     return FV_OK;
 }
@@ -1260,7 +1266,7 @@ fv_status plan_take_status(fv_plan_s *p, bool wait)
 // (each with its own workspace); the streams fork from and join back to the
 // plan's stream.
 template <class G>
-static fv_status execute_slices(fv_plan_s *p, char *vis, size_t slice_bytes)
+static fv_status execute_slices(fv_plan_s *p, char *vis, size_t slice_bytes, char *host_pinned)
 {
     if ((int)p->ws.size() < p->n_streams) {
         // execution workspaces are allocated on first use (a plan run only through a batch never needs them)
@@ -1286,8 +1292,10 @@ static fv_status execute_slices(fv_plan_s *p, char *vis, size_t slice_bytes)
     }
     for (int s = 0; s < S; ++s) {
         const long k0 = total * s / S, k1 = total * (s + 1) / S;
+        OutMap om;
+        om.host = host_pinned;
         fv_status st = p->use_basis ? run_basis<G>(p, p->ws[s], p->sub[s], vis, slice_bytes, (int)k0, (int)k1)
-                                    : run_slices<G>(p, p->ws[s], p->sub[s], vis, slice_bytes, k0, k1);
+                                    : run_slices<G>(p, p->ws[s], p->sub[s], vis, slice_bytes, k0, k1, om);
         if (st != FV_OK) return st;
     }
     if (S > 1) {
@@ -1911,21 +1919,29 @@ fv_status fv_execute(fv_plan_t p, void *vis, int vis_on_device)
     const size_t total = slice_bytes * p->freq.size() * p->lst.size();
     char *dst = (char *)vis;
     void *tmp = nullptr;
+    // host output in pinned memory: every slice is copied out as soon as it is written (the slice routes),
+    // overlapping the copies with the other slices' kernels; pageable memory gets one copy at the end
+    char *host_pinned = nullptr;
     if (!vis_on_device) {
         CK(cudaMallocAsync(&tmp, std::max<size_t>(total, 1), p->stream));
         dst = (char *)tmp;
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, vis) == cudaSuccess && pa.type == cudaMemoryTypeHost && !p->use_basis)
+            host_pinned = (char *)vis;
+        cudaGetLastError();
     }
     fv_status s;
     if (!p->any_visible || p->n_src == 0) {
         CK(cudaMemsetAsync(dst, 0, total, p->stream));
+        host_pinned = nullptr;
         s = FV_OK;
     } else {
-        s = p->precision == FV_FP64 ? execute_slices<double>(p, dst, slice_bytes)
-                                    : execute_slices<float>(p, dst, slice_bytes);
+        s = p->precision == FV_FP64 ? execute_slices<double>(p, dst, slice_bytes, host_pinned)
+                                    : execute_slices<float>(p, dst, slice_bytes, host_pinned);
     }
     if (s == FV_OK) CK(plan_post_status(p));
     if (!vis_on_device) {
-        if (s == FV_OK) CK(cudaMemcpyAsync(vis, tmp, total, cudaMemcpyDeviceToHost, p->stream));
+        if (s == FV_OK && !host_pinned) CK(cudaMemcpyAsync(vis, tmp, total, cudaMemcpyDeviceToHost, p->stream));
         cudaFreeAsync(tmp, p->stream);
         CK(cudaStreamSynchronize(p->stream));
         if (s == FV_OK) s = plan_take_status(p, true);
