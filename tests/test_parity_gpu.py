@@ -288,3 +288,16 @@ def test_pinned_host_output_matches_device_output(transform):
     assert rel_l2(pinned.numpy(), ref) <= 1e-6
     assert rel_l2(pageable, ref) <= 1e-6
     assert np.all(np.isfinite(pinned.numpy()))
+
+
+@pytest.mark.parametrize("eps,sigma", [(1e-7, 2.0), (1e-6, 1.5)])
+def test_ring_gather_kernel_width_limit(eps, sigma):
+    """The ring gather holds 8 kernel values per axis: eps 1e-7 at sigma 2 (w = 8) takes it, sigma 1.5
+    (w = 10) the register gather; both meet the mixed gate on a coplanar array with sources over the
+    whole sky (tiles at the grid edges)."""
+    prob = W.config_hex127(seed=18, n_chan=2, n_time=2, n_point=3000, nside=8, radius=4)
+    prob.ant_enu = W.hex_array(4)                       # coplanar: two-dimensional grids
+    out, info = run_gpu(prob, fv.FV_MIXED, eps=eps, transform="type3", upsampfac=sigma)
+    assert (info["kernel_width"] == 8) if sigma == 2.0 else (info["kernel_width"] > 8)
+    assert info["dims"] == 2 and info["spread"] == "gather"
+    assert rel_l2(out, oracle(prob)) <= TOL[fv.FV_MIXED]
