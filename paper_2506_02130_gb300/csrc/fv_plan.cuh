@@ -76,6 +76,10 @@ struct fv_plan_s {
     int n_stokes = 1;
     double *d_e = nullptr;
     void *d_flux_owned = nullptr;
+    // sky buffers are kept across fv_set_sky calls of the same size (allocating and freeing gigabytes of
+    // fluxes each time cost more than the copies): capacities in bytes, and the small scratch of set_sky
+    size_t e_bytes = 0, flux_owned_bytes = 0, flux_t_bytes = 0, radec_bytes = 0;
+    double *d_radec = nullptr, *d_Rt = nullptr, *d_ext = nullptr;
     const void *flux = nullptr;
     int flux_fp64 = 0;
     // channel-major copy of the fluxes, [n_freq][n_src][n_stokes]: what the slices read (one channel's

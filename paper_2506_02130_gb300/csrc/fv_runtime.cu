@@ -1837,18 +1837,28 @@ fv_status fv_set_sky(fv_plan_t p, long n_src, const double *ra_rad, const double
         if (!std::isfinite(ra_rad[i]) || !std::isfinite(dec_rad[i]))
             return p->fail(FV_ERR_ARG, "non-finite source coordinate");
     p->have_sky = false;
-    dfree_t(p->d_e);
-    dfree(p->d_flux_owned);
-    dfree(p->d_flux_t);
+    // work still queued on the device may read the sky buffers this call rewrites (a plan's own streams,
+    // or a batch's lanes): wait for it, as freeing them would
+    CK(cudaDeviceSynchronize());
+    // (re)allocate a buffer only when its size changes
+    auto ensure = [&](void **ptr, size_t &cap, size_t bytes) -> cudaError_t {
+        if (*ptr && cap == bytes) return cudaSuccess;
+        if (*ptr) cudaFree(*ptr);
+        *ptr = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMalloc(ptr, bytes);
+        if (e == cudaSuccess) cap = bytes;
+        return e;
+    };
     p->flux = nullptr;
     p->flux_borrowed = false;
     p->n_src = n_src;
     p->n_stokes = n_stokes;
     p->flux_fp64 = flux_is_fp64 ? 1 : 0;
     const size_t ns = std::max<long>(n_src, 1);
-    CK(cudaMalloc(&p->d_e, ns * 3 * sizeof(double)));
-    double *d_tmp = nullptr;
-    CK(cudaMalloc(&d_tmp, ns * 2 * sizeof(double)));
+    CK(ensure((void **)&p->d_e, p->e_bytes, ns * 3 * sizeof(double)));
+    CK(ensure((void **)&p->d_radec, p->radec_bytes, ns * 2 * sizeof(double)));
+    double *d_tmp = p->d_radec;
     if (n_src) {
         CK(cudaMemcpyAsync(d_tmp, ra_rad, n_src * sizeof(double), cudaMemcpyHostToDevice, p->stream));
         CK(cudaMemcpyAsync(d_tmp + ns, dec_rad, n_src * sizeof(double), cudaMemcpyHostToDevice, p->stream));
@@ -1858,32 +1868,32 @@ fv_status fv_set_sky(fv_plan_t p, long n_src, const double *ra_rad, const double
     if (flux_on_device) {
         p->flux = flux;
         p->flux_borrowed = true;
+        dfree(p->d_flux_owned);
+        p->flux_owned_bytes = 0;
     } else if (n_src) {
-        CK(cudaMalloc(&p->d_flux_owned, fbytes));
+        CK(ensure(&p->d_flux_owned, p->flux_owned_bytes, fbytes));
         CK(cudaMemcpyAsync(p->d_flux_owned, flux, fbytes, cudaMemcpyHostToDevice, p->stream));
         p->flux = p->d_flux_owned;
     }
     if (n_src && !p->use_basis) {
         // the channel-major copy the slices read: made now from an owned copy, at every execution from a
         // borrowed buffer
-        CK(cudaMalloc(&p->d_flux_t, fbytes));
+        CK(ensure(&p->d_flux_t, p->flux_t_bytes, fbytes));
         if (!p->flux_borrowed)
             CK(launch_flux_transpose(p->flux, p->flux_fp64, n_src, n_stokes, (int)p->freq.size(), p->d_flux_t,
                                      p->stream));
     }
     // source extents over all times (visible directions only)
     const int nb = 304;
-    double *d_R = nullptr, *d_ext = nullptr;
-    CK(cudaMalloc(&d_R, p->Rt.size() * sizeof(double)));
-    CK(cudaMalloc(&d_ext, (size_t)nb * 6 * sizeof(double)));
+    if (!p->d_Rt) CK(cudaMalloc(&p->d_Rt, std::max<size_t>(p->Rt.size(), 1) * sizeof(double)));
+    if (!p->d_ext) CK(cudaMalloc(&p->d_ext, (size_t)nb * 6 * sizeof(double)));
+    double *d_R = p->d_Rt, *d_ext = p->d_ext;
     CK(cudaMemcpyAsync(d_R, p->Rt.data(), p->Rt.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream));
     CK(launch_source_extents(p->d_e, n_src, d_R, (int)p->lst.size(), d_ext, nb, p->stream));
     std::vector<double> ext((size_t)nb * 6);
     CK(cudaMemcpyAsync(ext.data(), d_ext, ext.size() * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));
-    cudaFree(d_R);
-    cudaFree(d_ext);
-    cudaFree(d_tmp);
+    (void)d_tmp;
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int b = 0; b < nb; ++b)
         for (int i = 0; i < 3; ++i) {
@@ -1970,6 +1980,9 @@ fv_status fv_destroy(fv_plan_t p)
     dfree_t(p->d_e);
     dfree(p->d_flux_owned);
     dfree(p->d_flux_t);
+    dfree_t(p->d_radec);
+    dfree_t(p->d_Rt);
+    dfree_t(p->d_ext);
     dfree(p->d_grid_main);
     dfree_t(p->d_status);
     if (p->h_status) cudaFreeHost(p->h_status);
