@@ -55,14 +55,21 @@ struct DimGeom {
 struct BeamParams {
     int kind;           // 0 gauss, 1 airy, 2 uniform, 3 gridded
     double p0, p1, p2;
-    // the FP32 beam's constant, set on the host with the slice geometry (0: not set, derived from p0, p1):
-    // Gaussian FWHM(nu) nu = p0 p1 (rad Hz); Airy pi D / c (the argument per Hz and per unit sin theta)
+    // the FP32 beam's constant, set on the host with the parameters (beam_float_constant): Gaussian
+    // FWHM(nu) nu = p0 p1 (rad Hz); Airy pi D / c (the argument per Hz and per unit sin theta)
     float pf;
     // gridded beams (Section 2.4, numerical beams): voltage samples [n_freq][n_th][n_ph] on the grid
     // theta_i = i (pi/2) / (n_th - 1) (zenith angle), phi_j = j 2 pi / n_ph (azimuth east of north)
     const void *grid;   // device samples (order 1) or B-spline coefficients (order 3), FP64 if grid_fp64
     int grid_fp64, n_th, n_ph, grid_order;
 };
+
+// The FP32 beam constant of a beam, set on the host when its parameters are (Gaussian FWHM(nu) nu;
+// Airy pi D / c; 0 otherwise).
+inline void beam_float_constant(BeamParams &b)
+{
+    b.pf = b.kind == 0 ? (float)(b.p0 * b.p1) : (b.kind == 1 ? (float)(M_PI * b.p0 / FV_C_LIGHT) : 0.0f);
+}
 
 // Per-time binning geometry: bins are tiles of the top (highest-frequency)
 // channel's grid in (x, y).
@@ -239,11 +246,11 @@ template <> __device__ __forceinline__ float voltage<float>(const BeamParams &b,
 {
     if (b.kind == 0) {
         float theta = atan2f(rho, s2);
-        float fwhm = (b.pf > 0.0f ? b.pf : (float)(b.p0 * b.p1)) / nu;
+        float fwhm = b.pf / nu;
         return expf(-2.0f * 0.69314718055994531f * theta * theta / (fwhm * fwhm));
     }
     if (b.kind == 1) {
-        float x = (b.pf > 0.0f ? b.pf : (float)(M_PI * b.p0 / FV_C_LIGHT)) * nu * rho;
+        float x = b.pf * nu * rho;
         return airy_2j1_over_x(x);
     }
     return 1.0f;

@@ -644,11 +644,6 @@ static fv_status prepare(fv_plan_s *p)
 
 // Slice geometry of channel f at time t for beam group gr: the group's two beams (Section 2.2.3;
 // one shared beam: opts.beam and A^2).
-// The FP32 beam constant of a beam (Gaussian FWHM(nu) nu; Airy pi D / c).
-static void beam_float_constant(BeamParams &b)
-{
-    b.pf = b.kind == 0 ? (float)(b.p0 * b.p1) : (b.kind == 1 ? (float)(M_PI * b.p0 / FV_C_LIGHT) : 0.0f);
-}
 
 static SliceGeom slice_geom_for(const fv_plan_s *p, int f, int t, const fv_plan_s::BeamGroup &gr)
 {
@@ -1421,6 +1416,7 @@ fv_status fv_plan(const fv_opts *o, fv_plan_t *out)
     p->beam.p0 = o->beam_param[0];
     p->beam.p1 = o->beam_param[1];
     p->beam.p2 = o->beam_param[2];
+    beam_float_constant(p->beam);
     p->polarized = o->polarized ? 1 : 0;
     p->n_pol = p->polarized ? 4 : 1;
     p->dims_req = o->dims;
@@ -1697,6 +1693,7 @@ fv_status fv_set_beams(fv_plan_t p, int n_beams, const int *kinds, const double 
         beams[k].p0 = q[0];
         beams[k].p1 = q[1];
         beams[k].p2 = q[2];
+        beam_float_constant(beams[k]);
     }
     std::vector<int> boa(beam_of_ant, beam_of_ant + p->n_ant);
     for (int v : boa)
