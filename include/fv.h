@@ -434,6 +434,16 @@ long long fv_batch_workspace_bytes(fv_batch_t b);
 #define FV_STATIC_SCRATCH_BYTES (64ull << 20)
 fv_status fv_execute_static(fv_plan_t p, void *vis);
 
+/* Check of the bounded waits (no counterpart in the paper).  Every wait of
+ * the spreading kernels on a bulk copy gives up after about a second, records
+ * the fact in the plan's device status word and returns, so that the context
+ * stays usable; the plan's next execution (fv_execute, fv_execute_static or a
+ * batch holding it) then returns FV_ERR_TIMEOUT once and clears the word.  This
+ * call enqueues on the plan's stream one warp that waits on a barrier phase that
+ * nothing completes, so its wait runs out and is recorded the same way (about a
+ * second of one warp; no fault, no copy issued).  Returns FV_OK when enqueued. */
+fv_status fv_selftest_wait(fv_plan_t p);
+
 /* ABI version (FV_ABI_VERSION of the library that was loaded). */
 int fv_abi_version(void);
 

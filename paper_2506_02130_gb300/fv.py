@@ -86,6 +86,7 @@ SIGNATURES = {
     "fv_last_error": (C.c_char_p, [C.c_void_p]),
     "fv_get_info": (C.c_int, [C.c_void_p, C.POINTER(fv_info)]),
     "fv_abi_version": (C.c_int, []),
+    "fv_selftest_wait": (C.c_int, [C.c_void_p]),
     "fv_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "fv_profile_read": (C.c_int, [C.c_void_p, C.POINTER(fv_profile_data)]),
     "fv_execute_static": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -201,6 +202,11 @@ STATIC_SCRATCH_BYTES = 64 << 20
 def fv_execute_static(plan, vis) -> None:
     """fv_execute into a device buffer with the library's static scratch (allocates nothing)."""
     _check(load_library().fv_execute_static(plan, _ptr(vis)), plan)
+
+
+def fv_selftest_wait(plan) -> None:
+    """Enqueue the bounded-wait check on the plan's stream: its next execution raises FV_ERR_TIMEOUT."""
+    _check(load_library().fv_selftest_wait(plan), plan)
 
 
 def fv_destroy(plan) -> None:

@@ -301,3 +301,24 @@ def test_ring_gather_kernel_width_limit(eps, sigma):
     assert (info["kernel_width"] == 8) if sigma == 2.0 else (info["kernel_width"] > 8)
     assert info["dims"] == 2 and info["spread"] == "gather"
     assert rel_l2(out, oracle(prob)) <= TOL[fv.FV_MIXED]
+
+
+def test_bounded_wait_reports_timeout_and_the_plan_recovers():
+    """A wait that runs out (the self-test's barrier phase that nothing completes, about a second) is
+    reported as FV_ERR_TIMEOUT by the plan's next execution; the execution after it is correct again."""
+    prob = W.config_small(seed=3, n_src=500)
+    p = fv.Plan.create(prob.freqs_hz, prob.lsts_rad, prob.latitude_rad, prob.beam, prob.beam_param, fv.FV_MIXED,
+                       1e-6, prob.polarized)
+    try:
+        p.set_array(prob.ant_enu, prob.pairs)
+        p.set_sky(prob.sky.ra, prob.sky.dec, prob.sky.flux)
+        out = np.empty(p.out_shape, dtype=np.complex64)
+        p.run(out)
+        fv.fv_selftest_wait(p.handle)
+        with pytest.raises(fv.FvError) as ei:
+            p.run(out)                       # host output: waits for the status word of this execution
+        assert ei.value.status == fv.FV_ERR_TIMEOUT
+        p.run(out)                           # the word was cleared: a normal execution
+    finally:
+        p.close()
+    assert rel_l2(out, oracle(prob, mode="literal")) <= TOL[fv.FV_MIXED]
