@@ -467,12 +467,26 @@ template <class G>
 cudaError_t launch_interp(const cpx<G> *band, const double *bu, int n_u, const double *dec, const SliceGeom &g,
                           cpx<double> *Vu, cudaStream_t st);
 
+// The slice output written straight by the two-dimensional interpolation (the scatter to the baselines
+// fused into it): out [n_bl][n_pol] in the grid precision; u_off[u] .. u_off[u + 1] index u_bl, the
+// baselines of unique target u; u_base: the plan-wide index of the launch's first target.
+struct SliceOut {
+    void *out;
+    const int *u_off, *u_bl;
+    int u_base;
+};
+
+// Whether launch_interp_zdirect can write a slice's output itself for this geometry (two-dimensional
+// grids without height terms, n_pol 1 or 4).
+bool interp_fuses_scatter(const SliceGeom &g);
+
 // Same, reading the band after the x and y passes only ([b_y][b_x][pol][l_z]),
-// with the z axis summed directly (nf1_z <= 16).
+// with the z axis summed directly (nf1_z <= 16).  so (or nullptr): write the output of the targets'
+// baselines directly instead of Vu (interp_fuses_scatter must hold).
 template <class G>
 cudaError_t launch_interp_zdirect(const cpx<G> *band, const double *bu, int n_u, const double *dec,
                                   const SliceGeom &g, const G *prez, const cpx<G> *twz, cpx<double> *Vu,
-                                  cudaStream_t st);
+                                  cudaStream_t st, const SliceOut *so = nullptr);
 
 // vis slice [n_bl][n_pol] (complex128 or complex64) <- Vu[bl2u[bl]].
 cudaError_t launch_scatter(const cpx<double> *Vu, const int *bl2u, int n_bl, int n_pol, void *out,

@@ -787,7 +787,7 @@ __global__ void __launch_bounds__(kIbThreads) k_interp_batch(const cpx<G> *__res
 template <class G, int NP>
 __global__ void __launch_bounds__(256) k_interp_warp(const cpx<G> *__restrict__ band, const double *__restrict__ bu,
                                                      int n_u, const double *__restrict__ dec, SliceGeom g,
-                                                     cpx<double> *__restrict__ Vu)
+                                                     cpx<double> *__restrict__ Vu, SliceOut so)
 {
     const int lane = threadIdx.x & 31;
     const long u = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -900,6 +900,62 @@ __global__ void __launch_bounds__(256) k_interp_warp(const cpx<G> *__restrict__ 
         cp = (G)b;
     }
     const double dd = dec[u];
+    if (so.out) {
+        // the scatter fused in: every lane gets the target's NP values (in the grid precision) and the warp
+        // writes them to the target's baselines, out[b][p]
+        const G ddg = (G)dd;
+        G rx[NP], ry[NP];
+        if (NP == 1) {
+            G x = ax[0] * wx, y = ay[0] * wx;
+            for (int o = 16; o > 0; o >>= 1) {
+                x += __shfl_xor_sync(0xffffffffu, x, o);
+                y += __shfl_xor_sync(0xffffffffu, y, o);
+            }
+            rx[0] = (x * cp - y * sp) * ddg;
+            ry[0] = (x * sp + y * cp) * ddg;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q * J >= NP) break;   // uniform
+                G x = ax[q] * wx, y = ay[q] * wx;
+                for (int o = J; o < 32; o <<= 1) {
+                    const G tx = __shfl_down_sync(0xffffffffu, x, o), ty = __shfl_down_sync(0xffffffffu, y, o);
+                    if (lane + o < 32) {
+                        x += tx;
+                        y += ty;
+                    }
+                }
+                const G fx = (x * cp - y * sp) * ddg, fy = (x * sp + y * cp) * ddg;
+                // product pp of this group sits on lane pp - q J (column 0)
+#pragma unroll
+                for (int pp = 0; pp < NP; ++pp) {
+                    const int src = pp - q * J;
+                    const bool mine = src >= 0 && src < J;
+                    const G vx = __shfl_sync(0xffffffffu, fx, mine ? src : 0);
+                    const G vy = __shfl_sync(0xffffffffu, fy, mine ? src : 0);
+                    if (mine) {
+                        rx[pp] = vx;
+                        ry[pp] = vy;
+                    }
+                }
+            }
+        }
+        const int gu = so.u_base + (int)u;
+        const int b0 = so.u_off[gu], nb = so.u_off[gu + 1] - b0;
+        cpx<G> *o = reinterpret_cast<cpx<G> *>(so.out);
+        for (int k = lane; k < nb * NP; k += 32) {
+            const int kb = NP == 1 ? k : k >> 2, p = NP == 1 ? 0 : k & 3;
+            G vx = rx[0], vy = ry[0];
+#pragma unroll
+            for (int q = 1; q < NP; ++q)
+                if (p == q) {
+                    vx = rx[q];
+                    vy = ry[q];
+                }
+            o[(size_t)so.u_bl[b0 + kb] * NP + p] = cmk<G>(vx, vy);
+        }
+        return;
+    }
     if (NP == 1) {
         G x = ax[0] * wx, y = ay[0] * wx;
         for (int o = 16; o > 0; o >>= 1) {
@@ -936,11 +992,18 @@ static bool zrow_fits(const SliceGeom &g, int elem_bytes)
     return Nz >= 2 && Nz % 2 == 0 && g.w * (Nz / 2) <= 32;
 }
 
+bool interp_fuses_scatter(const SliceGeom &g)
+{
+    return g.w <= kIbMaxW && g.d == 2 && g.K == 0 && (g.n_pol == 1 || g.n_pol == 4);
+}
+
 template <class G>
 cudaError_t launch_interp_zdirect(const cpx<G> *band, const double *bu, int n_u, const double *dec,
                                   const SliceGeom &g, const G *prez, const cpx<G> *twz, cpx<double> *Vu,
-                                  cudaStream_t st)
+                                  cudaStream_t st, const SliceOut *so)
 {
+    if (so && so->out && !interp_fuses_scatter(g)) return cudaErrorInvalidValue;
+    const SliceOut sov = so ? *so : SliceOut{nullptr, nullptr, nullptr, 0};
     if (n_u <= 0) return cudaSuccess;
     if ((g.d == 3 || g.K) && g.dim[2].nf1 > 16) return cudaErrorInvalidValue;
     long threads = (long)n_u * 32;
@@ -950,9 +1013,9 @@ cudaError_t launch_interp_zdirect(const cpx<G> *band, const double *bu, int n_u,
             // one warp per target, 8 per CTA
             const unsigned wb = (unsigned)((n_u + 7) / 8);
             if (g.n_pol == 4)
-                k_interp_warp<G, 4><<<wb, 256, 0, st>>>(band, bu, n_u, dec, g, Vu);
+                k_interp_warp<G, 4><<<wb, 256, 0, st>>>(band, bu, n_u, dec, g, Vu, sov);
             else
-                k_interp_warp<G, 1><<<wb, 256, 0, st>>>(band, bu, n_u, dec, g, Vu);
+                k_interp_warp<G, 1><<<wb, 256, 0, st>>>(band, bu, n_u, dec, g, Vu, sov);
             return cudaGetLastError();
         }
         if constexpr (sizeof(G) == 4) {
@@ -1012,10 +1075,10 @@ template cudaError_t launch_interp<double>(const cpx<double> *, const double *, 
                                            const SliceGeom &, cpx<double> *, cudaStream_t);
 template cudaError_t launch_interp_zdirect<double>(const cpx<double> *, const double *, int, const double *,
                                                    const SliceGeom &, const double *, const cpx<double> *,
-                                                   cpx<double> *, cudaStream_t);
+                                                   cpx<double> *, cudaStream_t, const SliceOut *);
 template cudaError_t launch_interp_zdirect<float>(const cpx<float> *, const double *, int, const double *,
                                                   const SliceGeom &, const float *, const cpx<float> *,
-                                                  cpx<double> *, cudaStream_t);
+                                                  cpx<double> *, cudaStream_t, const SliceOut *);
 template cudaError_t launch_interp<float>(const cpx<float> *, const double *, int, const double *,
                                           const SliceGeom &, cpx<double> *, cudaStream_t);
 

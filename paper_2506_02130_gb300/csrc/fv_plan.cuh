@@ -69,6 +69,9 @@ struct fv_plan_s {
     std::vector<float4> h_tgt_db;
     std::vector<float2> h_tgt_bc;
     int *d_bl2u = nullptr;
+    // unique target -> its baselines (CSR: d_u_off[n_u + 1] into d_u_bl[n_bl]), for the interpolation
+    // that writes a slice's output itself
+    int *d_u_off = nullptr, *d_u_bl = nullptr;
 
     // sky
     bool have_sky = false;

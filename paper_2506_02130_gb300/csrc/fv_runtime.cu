@@ -791,6 +791,10 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
             CK(prof_end(p, (double)p->n_src * 80.0 + nb * 12.0 + (wk.tc ? p->n_src * 0.5 * 48.0 : 0.0)));
             t_binned = t;
         }
+        const int ntm = om.nt > 0 ? om.nt : nt;
+        char *out = vis + ((size_t)(f - om.f0) * ntm + (t - om.t0)) * slice_bytes;
+        // two-dimensional grids: the interpolation writes the baselines' output itself (no scatter)
+        const bool fused = p->d == 2 && p->hK == 0 && p->d_u_off && interp_fuses_scatter(p->gf[f]);
         // one transform per beam group: strengths with the group's two beams, targets [u0, u1)
         for (const auto &gr : p->groups) {
             if (gr.u1 <= gr.u0) continue;
@@ -865,9 +869,13 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
                 // z (if any) summed directly inside the interpolation: no z pass
                 const double wd = (double)p->w * p->w * D[2].nf1;
                 CK(prof_begin(p, PC_INTERP, st));
+                const SliceOut so{out, p->d_u_off, p->d_u_bl, gr.u0};
                 CK(launch_interp_zdirect<G>(Bb, bug, nug, decg, g, pre + p->pre_off[o0 + 2],
-                                            tw + p->tw_off[o0 + 2], Vug, st));
-                CK(prof_end(p, (double)nug * (wd * p->n_pol * es + 4 * sizeof(double) + p->n_pol * 16.0)));
+                                            tw + p->tw_off[o0 + 2], Vug, st, fused ? &so : nullptr));
+                // with the scatter fused in, the baselines' output is written here
+                const double nbl_g = gr.bl1 - gr.bl0;
+                CK(prof_end(p, (double)nug * (wd * p->n_pol * es + 4 * sizeof(double) + p->n_pol * 16.0) +
+                                   (fused ? nbl_g * 4.0 + (double)slice_bytes * nbl_g / std::max(p->n_bl, 1) : 0.0)));
             } else {
                 // pass 3 along z: rows (by, bx, pol)
                 const long r3 = (long)D[1].B * D[0].B * p->n_pol;
@@ -880,11 +888,11 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
                 CK(prof_end(p, (double)nug * (wd * p->n_pol * es + 4 * sizeof(double) + p->n_pol * 16.0)));
             }
         }
-        const int ntm = om.nt > 0 ? om.nt : nt;
-        char *out = vis + ((size_t)(f - om.f0) * ntm + (t - om.t0)) * slice_bytes;
-        CK(prof_begin(p, PC_SCATTER, st));
-        CK(launch_scatter(wk.Vu, p->d_bl2u, p->n_bl, p->n_pol, out, p->precision == FV_FP64, st));
-        CK(prof_end(p, (double)p->n_bl * (4 + p->n_pol * 16.0) + (double)slice_bytes));
+        if (!fused) {
+            CK(prof_begin(p, PC_SCATTER, st));
+            CK(launch_scatter(wk.Vu, p->d_bl2u, p->n_bl, p->n_pol, out, p->precision == FV_FP64, st));
+            CK(prof_end(p, (double)p->n_bl * (4 + p->n_pol * 16.0) + (double)slice_bytes));
+        }
         if (om.host) CK(cudaMemcpyAsync(om.host + (out - vis), out, slice_bytes, cudaMemcpyDeviceToHost, st));
     }
     return FV_OK;
@@ -1612,6 +1620,8 @@ static fv_status setup_array(fv_plan_s *p)
     dfree_t(p->d_tgt_bc);
     p->tgt_n = 0;
     dfree_t(p->d_bl2u);
+    dfree_t(p->d_u_off);
+    dfree_t(p->d_u_bl);
     dfree_t(p->d_bln);
     dfree_t(p->d_grp_bl);
     if (lat_ok) {
@@ -1625,6 +1635,18 @@ static fv_status setup_array(fv_plan_s *p)
     CK(cudaMalloc(&p->d_bl2u, nb * sizeof(int)));
     CK(cudaMalloc(&p->d_grp_bl, nb * sizeof(int)));
     if (p->n_u) CK(cudaMemcpyAsync(p->d_bu, p->bu.data(), (size_t)p->n_u * 3 * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    {
+        // CSR of the baselines of every unique target (counting sort of bl2u)
+        std::vector<int> u_off((size_t)p->n_u + 1, 0), u_bl(std::max(p->n_bl, 1), 0);
+        for (int b = 0; b < p->n_bl; ++b) ++u_off[(size_t)p->bl2u[b] + 1];
+        for (int u = 0; u < p->n_u; ++u) u_off[(size_t)u + 1] += u_off[u];
+        std::vector<int> cur(u_off.begin(), u_off.end() - 1);
+        for (int b = 0; b < p->n_bl; ++b) u_bl[(size_t)cur[p->bl2u[b]]++] = b;
+        CK(cudaMalloc(&p->d_u_off, u_off.size() * sizeof(int)));
+        CK(cudaMalloc(&p->d_u_bl, u_bl.size() * sizeof(int)));
+        CK(cudaMemcpy(p->d_u_off, u_off.data(), u_off.size() * sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(p->d_u_bl, u_bl.data(), u_bl.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
     if (p->n_bl) {
         CK(cudaMemcpyAsync(p->d_bl2u, p->bl2u.data(), (size_t)p->n_bl * sizeof(int), cudaMemcpyHostToDevice, p->stream));
         CK(cudaMemcpyAsync(p->d_grp_bl, grp_bl.data(), (size_t)p->n_bl * sizeof(int), cudaMemcpyHostToDevice,
@@ -1972,6 +1994,8 @@ fv_status fv_destroy(fv_plan_t p)
     dfree_t(p->d_tgt_bc);
     p->tgt_n = 0;
     dfree_t(p->d_bl2u);
+    dfree_t(p->d_u_off);
+    dfree_t(p->d_u_bl);
     dfree_t(p->d_bln);
     dfree_t(p->d_grp_bl);
     dfree_t(p->d_e);
