@@ -228,23 +228,20 @@ __device__ __forceinline__ float2 mul_df(float ah, float al, float bh, float bl)
     return make_float2(p, e);
 }
 
-// MODE 0: cell / frac / cs arrays; 1: staged records; 2: tensor-core records (kernel values included)
-template <int MODE>
-__global__ void __launch_bounds__(256) k_prep_tc(const float4 *__restrict__ tc, const int *__restrict__ sidx,
-                                                 const int *__restrict__ nv_ptr, long n_src,
-                                                 const void *__restrict__ flux, int flux_fp64, int n_freq, int f,
-                                                 SliceGeom g, int *__restrict__ cell, float *__restrict__ frac,
-                                                 cpx<float> *__restrict__ cs, SrcRec<float> *__restrict__ rec,
-                                                 TcRec *__restrict__ trec, int *__restrict__ tile_ctr)
-{
-    constexpr bool STAGED = MODE > 0;
-    if (tile_ctr && blockIdx.x == 0 && threadIdx.x == 0) *tile_ctr = 0;     // before any early return
-    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (i >= *nv_ptr) return;
-    const float4 a = tc[3 * i], b = tc[3 * i + 1], sd = tc[3 * i + 2];
-    const long n = sidx[i];
+// One source of one slice from its per-time record (a, b, sd) and source index n: strengths with prephase
+// c[0..np), first footprint cells ci and offsets fr.
+struct PrepOne {
     cpx<float> c[4];
-    const int np = source_strengths<float, float>(g, sd.x, sd.y, sd.z, n, flux, flux_fp64, n_src, n_freq, f, c);
+    int np;
+    int ci[3];
+    float fr[3];
+};
+
+__device__ __forceinline__ void prep_tc_one(const float4 a, const float4 b, const float4 sd, long n, const void *flux,
+                                            int flux_fp64, long n_src, int n_freq, int f, const SliceGeom &g,
+                                            PrepOne &o)
+{
+    o.np = source_strengths<float, float>(g, sd.x, sd.y, sd.z, n, flux, flux_fp64, n_src, n_freq, f, o.c);
     // prephase r ph_top, reduced to about [-pi, pi]: 2 pi = 6.2831855 - 1.7484555e-7
     const float2 ph = mul_df(g.rsc_hi, g.rsc_lo, b.z, b.w);
     const float k = rintf(ph.x * 0.15915494f);
@@ -253,52 +250,108 @@ __global__ void __launch_bounds__(256) k_prep_tc(const float4 *__restrict__ tc, 
     sincosf(phr, &sp, &cp);
 #pragma unroll
     for (int p = 0; p < 4; ++p)
-        if (p < np)
-            cs[STAGED ? (size_t)i * staged_cs_stride(4, np) + p : (size_t)p * n_src + i] = cmul(c[p], cmk<float>(cp, sp));
-    int ci[3] = {0, 0, 0};
-    float fr[3] = {0.0f, 0.0f, 0.0f};
+        if (p < o.np) o.c[p] = cmul(o.c[p], cmk<float>(cp, sp));
     const float hw = 0.5f * (float)g.w;
 #pragma unroll
     for (int k3 = 0; k3 < 3; ++k3) {
+        o.ci[k3] = 0;
+        o.fr[k3] = 0.0f;
         if (k3 < g.d) {
             const float qh = k3 == 0 ? a.x : (k3 == 1 ? a.z : b.x), ql = k3 == 0 ? a.y : (k3 == 1 ? a.w : b.y);
             const float2 q = mul_df(g.rsc_hi, g.rsc_lo, qh, ql);
             float l0 = ceilf(q.x - hw);
-            float o = (l0 - q.x) - q.y;                 // l0 - q
-            if (o >= 1.0f - hw) { l0 -= 1.0f; o -= 1.0f; }
-            else if (o < -hw) { l0 += 1.0f; o += 1.0f; }
-            ci[k3] = (int)l0 + g.dim[k3].nf1 / 2;
-            fr[k3] = o;
+            float off = (l0 - q.x) - q.y;                 // l0 - q
+            if (off >= 1.0f - hw) { l0 -= 1.0f; off -= 1.0f; }
+            else if (off < -hw) { l0 += 1.0f; off += 1.0f; }
+            int c = (int)l0 + g.dim[k3].nf1 / 2;
             const int hi = g.dim[k3].nf1 - g.w;
-            if (ci[k3] < 0) { fr[k3] -= (float)ci[k3]; ci[k3] = 0; }
-            else if (ci[k3] > hi) { fr[k3] -= (float)(ci[k3] - hi); ci[k3] = hi; }
+            if (c < 0) { off -= (float)c; c = 0; }
+            else if (c > hi) { off -= (float)(c - hi); c = hi; }
+            o.ci[k3] = c;
+            o.fr[k3] = off;
         }
     }
-    if (g.K) fr[2] = (sd.z - g.hc_f) * g.hs_inv_f;    // height terms: the argument u of T_q
-    if (MODE == 2) {
+    if (g.K) o.fr[2] = (sd.z - g.hc_f) * g.hs_inv_f;    // height terms: the argument u of T_q
+}
+
+// MODE 0: cell / frac / cs arrays; 1: staged records
+template <int MODE>
+__global__ void __launch_bounds__(256) k_prep_tc(const float4 *__restrict__ tc, const int *__restrict__ sidx,
+                                                 const int *__restrict__ nv_ptr, long n_src,
+                                                 const void *__restrict__ flux, int flux_fp64, int n_freq, int f,
+                                                 SliceGeom g, int *__restrict__ cell, float *__restrict__ frac,
+                                                 cpx<float> *__restrict__ cs, SrcRec<float> *__restrict__ rec)
+{
+    constexpr bool STAGED = MODE > 0;
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= *nv_ptr) return;
+    PrepOne o;
+    prep_tc_one(tc[3 * i], tc[3 * i + 1], tc[3 * i + 2], sidx[i], flux, flux_fp64, n_src, n_freq, f, g, o);
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+        if (p < o.np) cs[STAGED ? (size_t)i * staged_cs_stride(4, o.np) + p : (size_t)p * n_src + i] = o.c[p];
+    if (STAGED) {
+        SrcRec<float> h;
+        h.cell = (unsigned)o.ci[0] | ((unsigned)o.ci[1] << 14) | ((unsigned)o.ci[2] << 28);
+        h.fx = o.fr[0];
+        h.fy = o.fr[1];
+        h.fz = o.fr[2];
+        rec[i] = h;
+    } else {
+        for (int k3 = 0; k3 < 3; ++k3) {
+            cell[(size_t)k3 * n_src + i] = o.ci[k3];
+            frac[(size_t)k3 * n_src + i] = o.fr[k3];
+        }
+    }
+}
+
+// Ring records (the ring gather of two-dimensional grids): the same per source plus the footprint's
+// kernel values.  A CTA's 256 sources are contiguous in the sorted order, so their per-time records are
+// read into shared memory and their ring records and strengths written out of it with coalesced 16-byte
+// accesses (each thread's own 48-byte read and 80 + 32-byte writes would touch a sector per lane).
+template <int NP>
+__global__ void __launch_bounds__(256) k_prep_ring(const float4 *__restrict__ tc, const int *__restrict__ sidx,
+                                                   const int *__restrict__ nv_ptr, long n_src,
+                                                   const void *__restrict__ flux, int flux_fp64, int n_freq, int f,
+                                                   SliceGeom g, cpx<float> *__restrict__ cs,
+                                                   TcRec *__restrict__ trec, int *__restrict__ tile_ctr)
+{
+    constexpr int kCsw = (NP * 8 + 15) / 16 * 16 / 8;            // strengths per source, 16-byte rows
+    constexpr int kRec4 = (int)(sizeof(TcRec) / sizeof(float4)), kCs4 = kCsw / 2;
+    __shared__ float4 s_in[256 * 3];
+    __shared__ float4 s_rec[256 * kRec4];
+    __shared__ float4 s_cs[256 * kCs4];
+    if (tile_ctr && blockIdx.x == 0 && threadIdx.x == 0) *tile_ctr = 0;
+    const long i0 = (long)blockIdx.x * 256;
+    const long nv = *nv_ptr;
+    if (i0 >= nv) return;                                       // the same on every thread of the CTA
+    const int cnt = (int)min(256L, nv - i0);
+    for (int k = threadIdx.x; k < cnt * 3; k += 256) s_in[k] = tc[3 * i0 + k];
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < cnt) {
+        PrepOne o;
+        prep_tc_one(s_in[3 * t], s_in[3 * t + 1], s_in[3 * t + 2], sidx[i0 + t], flux, flux_fp64, n_src, n_freq, f,
+                    g, o);
         TcRec h;
-        h.cell = (unsigned)ci[0] | ((unsigned)ci[1] << 14);
+        h.cell = (unsigned)o.ci[0] | ((unsigned)o.ci[1] << 14);
         h.pad[0] = h.pad[1] = h.pad[2] = 0u;
         const float two_over_w = 2.0f / (float)g.w, beta = g.beta_f;
 #pragma unroll
         for (int j = 0; j < kTcWmax; ++j) {
-            h.wx[j] = j < g.w ? es_kernel_f(two_over_w * (fr[0] + (float)j), beta) : 0.0f;
-            h.wy[j] = j < g.w ? es_kernel_f(two_over_w * (fr[1] + (float)j), beta) : 0.0f;
+            h.wx[j] = j < g.w ? es_kernel_f(two_over_w * (o.fr[0] + (float)j), beta) : 0.0f;
+            h.wy[j] = j < g.w ? es_kernel_f(two_over_w * (o.fr[1] + (float)j), beta) : 0.0f;
         }
-        trec[i] = h;
-    } else if (STAGED) {
-        SrcRec<float> h;
-        h.cell = (unsigned)ci[0] | ((unsigned)ci[1] << 14) | ((unsigned)ci[2] << 28);
-        h.fx = fr[0];
-        h.fy = fr[1];
-        h.fz = fr[2];
-        rec[i] = h;
-    } else {
-        for (int k3 = 0; k3 < 3; ++k3) {
-            cell[(size_t)k3 * n_src + i] = ci[k3];
-            frac[(size_t)k3 * n_src + i] = fr[k3];
-        }
+        reinterpret_cast<TcRec *>(s_rec)[t] = h;
+        cpx<float> *sc = reinterpret_cast<cpx<float> *>(s_cs) + (size_t)t * kCsw;
+#pragma unroll
+        for (int p = 0; p < kCsw; ++p) sc[p] = p < NP ? o.c[p] : cmk<float>(0.0f, 0.0f);
     }
+    __syncthreads();
+    float4 *gr = reinterpret_cast<float4 *>(trec + i0);
+    for (int k = threadIdx.x; k < cnt * kRec4; k += 256) gr[k] = s_rec[k];
+    float4 *gc = reinterpret_cast<float4 *>(cs + (size_t)i0 * kCsw);
+    for (int k = threadIdx.x; k < cnt * kCs4; k += 256) gc[k] = s_cs[k];
 }
 
 cudaError_t launch_prep_tc(const float4 *tc, const int *sidx, const int *nv_ptr, long n_src, const void *flux,
@@ -306,17 +359,22 @@ cudaError_t launch_prep_tc(const float4 *tc, const int *sidx, const int *nv_ptr,
                            cpx<float> *cs, SrcRec<float> *rec, TcRec *trec, int *tile_ctr, cudaStream_t st)
 {
     if (n_src <= 0) return tile_ctr ? cudaErrorInvalidValue : cudaSuccess;
-    if (trec && (g.w > kTcWmax || g.d != 2 || g.K)) return cudaErrorInvalidValue;
+    if (trec && (g.w > kTcWmax || g.d != 2 || g.K || (g.n_pol != 1 && g.n_pol != 4))) return cudaErrorInvalidValue;
     const unsigned nb = (unsigned)((n_src + 255) / 256);
-    if (trec)
-        k_prep_tc<2><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cell, frac, cs, rec,
-                                         trec, tile_ctr);
-    else if (rec)
-        k_prep_tc<1><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cell, frac, cs, rec,
-                                         trec, tile_ctr);
-    else
-        k_prep_tc<0><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cell, frac, cs, rec,
-                                         trec, tile_ctr);
+    if (trec) {
+        if (g.n_pol == 4)
+            k_prep_ring<4><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cs, trec,
+                                               tile_ctr);
+        else
+            k_prep_ring<1><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cs, trec,
+                                               tile_ctr);
+    } else if (rec) {
+        k_prep_tc<1><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cell, frac, cs,
+                                         rec);
+    } else {
+        k_prep_tc<0><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cell, frac, cs,
+                                         rec);
+    }
     return cudaGetLastError();
 }
 
