@@ -250,7 +250,7 @@ static void resolve_spread(fv_plan_s *p, int gs, int w)
     const bool gather_auto = gather_ok && !(gs == 8 && nz_t > 8);
     // the ring gather (and its tensor-core form): FP32 two-dimensional grids without height terms
     const bool ring_ok = gather_ok && gs == 4 && p->d == 2 && p->hK == 0 && (p->n_pol == 1 || p->n_pol == 4) &&
-                         w <= kTcWmax && p->precision == FV_MIXED;
+                         w <= kRingWmax && p->precision == FV_MIXED;
     int m = p->spread_req;
     if (m == FV_SPREAD_TENSOR && !ring_ok) m = FV_SPREAD_GATHER;
     if (m == FV_SPREAD_AUTO)
@@ -625,7 +625,7 @@ static fv_status prepare(fv_plan_s *p)
     // the gather spreading reads staged records: 16 (FP32) or 32 (FP64) bytes per source where the split
     // coordinates take 12 or 24, and strengths padded to 16 bytes
     const bool staged = p->spread_method == FV_SPREAD_GATHER || p->spread_method == FV_SPREAD_TENSOR;
-    p->need.frac_per_src = p->ring ? sizeof(TcRec) : (staged ? 4 * gs : 3 * gs);
+    p->need.frac_per_src = p->ring ? sizeof(RingRec) : (staged ? 4 * gs : 3 * gs);
     p->need.cs_per_src = staged ? (size_t)staged_cs_stride((int)gs, p->n_pol) * es : (size_t)p->n_pol * es;
     // FP32 grids take each slice's coordinates and prephase from per-time records (no FP64 per slice)
     p->need.tc = p->precision == FV_MIXED && p->tiled;
@@ -761,7 +761,7 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
     // staged records: one 16- or 32-byte record (80 bytes with the ring gather's kernel values) plus the
     // (padded) strengths per source, read once
     const bool ring = p->ring && sizeof(G) == 4 && p->need.tc;
-    const double rec_bytes = ring ? (double)sizeof(TcRec) : (double)sizeof(SrcRec<G>);
+    const double rec_bytes = ring ? (double)sizeof(RingRec) : (double)sizeof(SrcRec<G>);
     const double cs_staged = staged_cs_stride((int)sizeof(G), p->n_pol) * es;
     const double prep_bytes_staged = nvis * ((p->need.tc && sizeof(G) == 4 ? 48.0 : 24.0) + 4.0 +
                                              p->n_stokes * (p->flux_fp64 ? 8.0 : 4.0) + rec_bytes + cs_staged);
@@ -817,7 +817,7 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
                     CK(launch_prep_tc(wk.tc, wk.sidx, wk.offsets + nb, p->n_src, p->flux, p->flux_fp64, nf, f, g,
                                       wk.cell, (float *)frac, (cpx<float> *)cs,
                                       staged && !ring ? (SrcRec<float> *)rec : nullptr,
-                                      ring ? (TcRec *)wk.frac : nullptr, ring ? wk.tiles : nullptr, st));
+                                      ring ? (RingRec *)wk.frac : nullptr, ring ? wk.tiles : nullptr, st));
                 else if (staged)
                     CK(launch_prep_staged<G>(wk.sdir, wk.sidx, wk.offsets + nb, p->n_src, p->flux, p->flux_fp64, nf,
                                              f, g, rec, cs, st));
@@ -830,7 +830,7 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
                 g.pre_y = pre + p->pre_off[(size_t)f * 3 + 1];
                 CK(prof_begin(p, PC_SPREAD, st));
                 if (ring)
-                    CK(launch_spread_ring(wk.offsets, (const TcRec *)wk.frac, (const cpx<float> *)cs, g, tb, r0, r1,
+                    CK(launch_spread_ring(wk.offsets, (const RingRec *)wk.frac, (const cpx<float> *)cs, g, tb, r0, r1,
                                           wk.tiles, p->d_status, (cpx<float> *)grid,
                                           p->spread_method == FV_SPREAD_TENSOR, st));
                 else if (p->spread_method == FV_SPREAD_GATHER || p->spread_method == FV_SPREAD_TENSOR)

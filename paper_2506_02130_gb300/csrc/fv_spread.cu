@@ -314,10 +314,10 @@ __global__ void __launch_bounds__(256) k_prep_ring(const float4 *__restrict__ tc
                                                    const int *__restrict__ nv_ptr, long n_src,
                                                    const void *__restrict__ flux, int flux_fp64, int n_freq, int f,
                                                    SliceGeom g, cpx<float> *__restrict__ cs,
-                                                   TcRec *__restrict__ trec, int *__restrict__ tile_ctr)
+                                                   RingRec *__restrict__ ring_rec, int *__restrict__ tile_ctr)
 {
     constexpr int kCsw = (NP * 8 + 15) / 16 * 16 / 8;            // strengths per source, 16-byte rows
-    constexpr int kRec4 = (int)(sizeof(TcRec) / sizeof(float4)), kCs4 = kCsw / 2;
+    constexpr int kRec4 = (int)(sizeof(RingRec) / sizeof(float4)), kCs4 = kCsw / 2;
     __shared__ float4 s_in[256 * 3];
     __shared__ float4 s_rec[256 * kRec4];
     __shared__ float4 s_cs[256 * kCs4];
@@ -333,22 +333,22 @@ __global__ void __launch_bounds__(256) k_prep_ring(const float4 *__restrict__ tc
         PrepOne o;
         prep_tc_one(s_in[3 * t], s_in[3 * t + 1], s_in[3 * t + 2], sidx[i0 + t], flux, flux_fp64, n_src, n_freq, f,
                     g, o);
-        TcRec h;
+        RingRec h;
         h.cell = (unsigned)o.ci[0] | ((unsigned)o.ci[1] << 14);
         h.pad[0] = h.pad[1] = h.pad[2] = 0u;
         const float two_over_w = 2.0f / (float)g.w, beta = g.beta_f;
 #pragma unroll
-        for (int j = 0; j < kTcWmax; ++j) {
+        for (int j = 0; j < kRingWmax; ++j) {
             h.wx[j] = j < g.w ? es_kernel_f(two_over_w * (o.fr[0] + (float)j), beta) : 0.0f;
             h.wy[j] = j < g.w ? es_kernel_f(two_over_w * (o.fr[1] + (float)j), beta) : 0.0f;
         }
-        reinterpret_cast<TcRec *>(s_rec)[t] = h;
+        reinterpret_cast<RingRec *>(s_rec)[t] = h;
         cpx<float> *sc = reinterpret_cast<cpx<float> *>(s_cs) + (size_t)t * kCsw;
 #pragma unroll
         for (int p = 0; p < kCsw; ++p) sc[p] = p < NP ? o.c[p] : cmk<float>(0.0f, 0.0f);
     }
     __syncthreads();
-    float4 *gr = reinterpret_cast<float4 *>(trec + i0);
+    float4 *gr = reinterpret_cast<float4 *>(ring_rec + i0);
     for (int k = threadIdx.x; k < cnt * kRec4; k += 256) gr[k] = s_rec[k];
     float4 *gc = reinterpret_cast<float4 *>(cs + (size_t)i0 * kCsw);
     for (int k = threadIdx.x; k < cnt * kCs4; k += 256) gc[k] = s_cs[k];
@@ -356,17 +356,18 @@ __global__ void __launch_bounds__(256) k_prep_ring(const float4 *__restrict__ tc
 
 cudaError_t launch_prep_tc(const float4 *tc, const int *sidx, const int *nv_ptr, long n_src, const void *flux,
                            int flux_fp64, int n_freq, int f, const SliceGeom &g, int *cell, float *frac,
-                           cpx<float> *cs, SrcRec<float> *rec, TcRec *trec, int *tile_ctr, cudaStream_t st)
+                           cpx<float> *cs, SrcRec<float> *rec, RingRec *ring_rec, int *tile_ctr, cudaStream_t st)
 {
     if (n_src <= 0) return tile_ctr ? cudaErrorInvalidValue : cudaSuccess;
-    if (trec && (g.w > kTcWmax || g.d != 2 || g.K || (g.n_pol != 1 && g.n_pol != 4))) return cudaErrorInvalidValue;
+    if (ring_rec && (g.w > kRingWmax || g.d != 2 || g.K || (g.n_pol != 1 && g.n_pol != 4)))
+        return cudaErrorInvalidValue;
     const unsigned nb = (unsigned)((n_src + 255) / 256);
-    if (trec) {
+    if (ring_rec) {
         if (g.n_pol == 4)
-            k_prep_ring<4><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cs, trec,
+            k_prep_ring<4><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cs, ring_rec,
                                                tile_ctr);
         else
-            k_prep_ring<1><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cs, trec,
+            k_prep_ring<1><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cs, ring_rec,
                                                tile_ctr);
     } else if (rec) {
         k_prep_tc<1><<<nb, 256, 0, st>>>(tc, sidx, nv_ptr, n_src, flux, flux_fp64, n_freq, f, g, cell, frac, cs,

@@ -34,11 +34,11 @@ namespace fv {
 
 namespace {
 
-constexpr int kTcConsumers = 8;                       // 4 x 2 blocks of 8 x 8
-constexpr int kTcThreads = (kTcConsumers + 1) * 32;   // plus the producer warp
-constexpr int kTcTileX = 32, kTcTileY = 16;
-constexpr int kTcChunk = 128;
-constexpr int kTcStages = 3;
+constexpr int kRingConsumers = 8;                       // 4 x 2 blocks of 8 x 8
+constexpr int kRingThreads = (kRingConsumers + 1) * 32;   // plus the producer warp
+constexpr int kRingTileX = 32, kRingTileY = 16;
+constexpr int kRingChunk = 128;
+constexpr int kRingStages = 3;
 
 __device__ __forceinline__ uint32_t to_tf32(float v)
 {
@@ -69,31 +69,31 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 }  // namespace
 
 template <int NP, bool TC>
-__global__ void __launch_bounds__(kTcThreads, 3) k_spread_ring(const int *__restrict__ offsets,
-                                                            const TcRec *__restrict__ rec,
+__global__ void __launch_bounds__(kRingThreads, 3) k_spread_ring(const int *__restrict__ offsets,
+                                                            const RingRec *__restrict__ rec,
                                                             const cpx<float> *__restrict__ cs, SliceGeom g, TimeBin tb,
                                                             double r0, double r1, int tiles_x, int n_tiles,
                                                             int *__restrict__ tile_ctr, int *__restrict__ status,
                                                             cpx<float> *__restrict__ grid)
 {
     constexpr int kCsw = (NP * 8 + 15) / 16 * 16 / 8;           // staged strengths per source (16-byte rows)
-    __shared__ __align__(16) TcRec s_rec[kTcStages][kTcChunk];
-    __shared__ __align__(16) cpx<float> s_cs[kTcStages][kTcChunk * kCsw];
-    __shared__ __align__(8) uint64_t s_full[kTcStages], s_empty[kTcStages];
+    __shared__ __align__(16) RingRec s_rec[kRingStages][kRingChunk];
+    __shared__ __align__(16) cpx<float> s_cs[kRingStages][kRingChunk * kCsw];
+    __shared__ __align__(8) uint64_t s_full[kRingStages], s_empty[kRingStages];
     // per stage: candidates of a chunk, or -1 for a tile boundary whose next tile is s_tile
-    __shared__ int s_n[kTcStages], s_tile[kTcStages];
+    __shared__ int s_n[kRingStages], s_tile[kRingStages];
     // a warp's selected candidates: t (bits 0-7) and the footprint origin relative to the block + 16 in x
     // (bits 8-15) and y (bits 16-23)
-    __shared__ int s_sel[kTcConsumers][kTcChunk];
+    __shared__ int s_sel[kRingConsumers][kRingChunk];
     __shared__ int s_row0[32], s_pre[32];                         // the producer's rows table
     __shared__ int s_abort;
     const int nx = g.dim[0].nf1, ny = g.dim[1].nf1;
     const int w = g.w;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int b = 0; b < kTcStages; ++b) {
+        for (int b = 0; b < kRingStages; ++b) {
             mbar_init_n(&s_full[b], 1);
-            mbar_init_n(&s_empty[b], kTcConsumers);
+            mbar_init_n(&s_empty[b], kRingConsumers);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
@@ -104,14 +104,14 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_spread_ring(const int *__rest
     // Tiles are handed out by an atomic ticket (tile_ctr, zeroed by the prep kernel before this launch);
     // the producer runs ahead across tile boundaries, so the next tile's first chunks are in flight while
     // the consumers finish the current one.
-    if (warp == kTcConsumers) {
+    if (warp == kRingConsumers) {
         // ---------------- producer warp: tiles, rows tables and bulk copies of the candidate chunks
         int kc = 0;              // stages filled
         unsigned ephase = 0u;    // bit b: parity of the next completion of stage b's empty barrier
         int ok = 1;
-        // lane 0: wait until stage kc % kTcStages is free (its previous use consumed); false if that ran out
+        // lane 0: wait until stage kc % kRingStages is free (its previous use consumed); false if that ran out
         auto acquire = [&](int b) -> bool {
-            if (kc < kTcStages) return true;
+            if (kc < kRingStages) return true;
             const bool got = mbar_wait(&s_empty[b], (ephase >> b) & 1u);
             ephase ^= 1u << b;
             return got && !*abort_flag;
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_spread_ring(const int *__rest
         // lane 0: take the next tile and announce it with a boundary stage
         auto next_tile = [&]() -> int {
             const int t = atomicAdd(tile_ctr, 1);
-            const int b = kc % kTcStages;
+            const int b = kc % kRingStages;
             if (!acquire(b)) {
                 ok = 0;
                 return n_tiles;
@@ -135,12 +135,14 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_spread_ring(const int *__rest
         ok = __shfl_sync(0xffffffffu, ok, 0);
         kc = __shfl_sync(0xffffffffu, kc, 0);
         while (tile < n_tiles && ok) {
-            const int x0 = (tile % tiles_x) * kTcTileX, y0 = (tile / tiles_x) * kTcTileY;
+            const int x0 = (tile % tiles_x) * kRingTileX, y0 = (tile / tiles_x) * kRingTileY;
             int bins[4] = {0, 0, 0, 0};
             if (lane == 0) {
                 // the bin rectangle of the tile (one-cell margin through the top-grid mapping), in FP64
-                const double qx_lo = (x0 - nx / 2 - 0.5 * w) / r0, qx_hi = (x0 + kTcTileX - nx / 2 + 0.5 * w - 1) / r0;
-                const double qy_lo = (y0 - ny / 2 - 0.5 * w) / r1, qy_hi = (y0 + kTcTileY - ny / 2 + 0.5 * w - 1) / r1;
+                const double qx_lo = (x0 - nx / 2 - 0.5 * w) / r0;
+                const double qx_hi = (x0 + kRingTileX - nx / 2 + 0.5 * w - 1) / r0;
+                const double qy_lo = (y0 - ny / 2 - 0.5 * w) / r1;
+                const double qy_hi = (y0 + kRingTileY - ny / 2 + 0.5 * w - 1) / r1;
                 bins[0] = top_cell(qx_lo - 1.0, tb.nf1_top[0]) / tb.T[0];
                 bins[1] = top_cell(qx_hi + 1.0, tb.nf1_top[0]) / tb.T[0];
                 bins[2] = top_cell(qy_lo - 1.0, tb.nf1_top[1]) / tb.T[1];
@@ -167,21 +169,21 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_spread_ring(const int *__rest
                 const int total = __shfl_sync(0xffffffffu, incl, 31);
                 __syncwarp();
                 if (lane == 0) {
-                    for (int base = 0; base < total; base += kTcChunk) {
-                        const int b = kc % kTcStages;
+                    for (int base = 0; base < total; base += kRingChunk) {
+                        const int b = kc % kRingStages;
                         if (!acquire(b)) {
                             ok = 0;
                             break;
                         }
-                        const int n = min(kTcChunk, total - base);
+                        const int n = min(kRingChunk, total - base);
                         s_n[b] = n;
-                        mbar_expect(&s_full[b], (unsigned)n * (unsigned)(sizeof(TcRec) + kCsw * sizeof(cpx<float>)));
+                        mbar_expect(&s_full[b], (unsigned)n * (unsigned)(sizeof(RingRec) + kCsw * sizeof(cpx<float>)));
                         for (int r = 0; r < nrows; ++r) {
                             const int rlen = (r + 1 < nrows ? s_pre[r + 1] : total) - s_pre[r];
                             const int a = max(base, s_pre[r]), e = min(base + n, s_pre[r] + rlen);
                             if (a >= e) continue;
                             const int i0 = s_row0[r] + (a - s_pre[r]), m = e - a;
-                            bulk_g2s(&s_rec[b][a - base], rec + i0, (unsigned)(m * sizeof(TcRec)), &s_full[b]);
+                            bulk_g2s(&s_rec[b][a - base], rec + i0, (unsigned)(m * sizeof(RingRec)), &s_full[b]);
                             bulk_g2s(&s_cs[b][(a - base) * kCsw], cs + (size_t)i0 * kCsw,
                                      (unsigned)(m * kCsw * sizeof(cpx<float>)), &s_full[b]);
                         }
@@ -204,8 +206,8 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_spread_ring(const int *__rest
             // a wait ran out: tell the consumers, record it, and wait (bounded) for the copies in flight
             *abort_flag = 1;
             atomicOr(status, FV_DEVICE_TIMEOUT);
-            for (int k = max(0, kc - kTcStages); k < kc; ++k)
-                mbar_wait(&s_full[k % kTcStages], (unsigned)(k / kTcStages) & 1u);
+            for (int k = max(0, kc - kRingStages); k < kc; ++k)
+                mbar_wait(&s_full[k % kRingStages], (unsigned)(k / kRingStages) & 1u);
         }
         return;
     }
@@ -221,7 +223,7 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_spread_ring(const int *__rest
 #pragma unroll
         for (int k = 0; k < 4; ++k) d[p][k] = 0.0f;
     for (int kc = 0;; ++kc) {
-        const int b = kc % kTcStages;
+        const int b = kc % kRingStages;
         // the lanes decide together: a wait that ran out on any lane, or an abort, ends the warp's work
         const bool got = __all_sync(0xffffffffu, mbar_wait(&s_full[b], (fphase >> b) & 1u));
         const int aborted = __shfl_sync(0xffffffffu, *abort_flag, 0);
@@ -260,12 +262,12 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_spread_ring(const int *__rest
                 for (int e = 0; e < L; ++e) {
                     const int ent = s_sel[warp][e];
                     const int t = ent & 0xff;
-                    const TcRec &r = s_rec[b][t];
+                    const RingRec &r = s_rec[b][t];
                     const unsigned dx = (unsigned)(lx + 16 - ((ent >> 8) & 0xff));
                     const unsigned dy0 = (unsigned)(ly + 16 - (ent >> 16)), dy1 = dy0 + 4u;
-                    const float wx = dx < (unsigned)kTcWmax ? r.wx[dx] : 0.0f;
-                    const float wy0 = dy0 < (unsigned)kTcWmax ? r.wy[dy0] : 0.0f;
-                    const float wy1 = dy1 < (unsigned)kTcWmax ? r.wy[dy1] : 0.0f;
+                    const float wx = dx < (unsigned)kRingWmax ? r.wx[dx] : 0.0f;
+                    const float wy0 = dy0 < (unsigned)kRingWmax ? r.wy[dy0] : 0.0f;
+                    const float wy1 = dy1 < (unsigned)kRingWmax ? r.wy[dy1] : 0.0f;
                     const float4 *c4 = reinterpret_cast<const float4 *>(&s_cs[b][t * kCsw]);
                     float4 cv[NP > 1 ? 2 : 1];
 #pragma unroll
@@ -296,11 +298,11 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_spread_ring(const int *__rest
                     if (k < L) {
                         const int ent = s_sel[warp][k];
                         t = ent & 0xff;
-                        const TcRec &r = s_rec[b][t];
+                        const RingRec &r = s_rec[b][t];
                         const unsigned dx = (unsigned)(gq + 16 - ((ent >> 8) & 0xff));
                         const unsigned dy = (unsigned)(gq + 16 - (ent >> 16));
-                        if (dx < (unsigned)kTcWmax) wx = r.wx[dx];      // zero past w
-                        if (dy < (unsigned)kTcWmax) wy[h] = r.wy[dy];
+                        if (dx < (unsigned)kRingWmax) wx = r.wx[dx];      // zero past w
+                        if (dy < (unsigned)kRingWmax) wy[h] = r.wy[dy];
                     }
                     // B: hi = tf32(wx); lo = the remainder, whose low bits the tensor core ignores
                     bh[h] = to_tf32(wx);
@@ -370,19 +372,19 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_spread_ring(const int *__rest
             }
             tile = next;
             if (tile >= n_tiles) break;
-            bx0 = (tile % tiles_x) * kTcTileX + (warp & 3) * 8;
-            by0 = (tile / tiles_x) * kTcTileY + (warp >> 2) * 8;
+            bx0 = (tile % tiles_x) * kRingTileX + (warp & 3) * 8;
+            by0 = (tile / tiles_x) * kRingTileY + (warp >> 2) * 8;
         }
     }
 }
 
 // The ring gather for an FP32 two-dimensional slice (n_pol 1 or 4, w <= 8) from ring records (launch_prep_tc);
 // tensor: the block sums on the tensor cores.  Writes every cell of grid [n_pol][ny][nx].
-cudaError_t launch_spread_ring(const int *offsets, const TcRec *rec, const cpx<float> *cs, const SliceGeom &g,
+cudaError_t launch_spread_ring(const int *offsets, const RingRec *rec, const cpx<float> *cs, const SliceGeom &g,
                                const TimeBin &tb, double r0, double r1, int *tile_ctr, int *status, cpx<float> *grid,
                                bool tensor, cudaStream_t st)
 {
-    if (g.d != 2 || g.K != 0 || g.w > kTcWmax || (g.n_pol != 1 && g.n_pol != 4)) return cudaErrorInvalidValue;
+    if (g.d != 2 || g.K != 0 || g.w > kRingWmax || (g.n_pol != 1 && g.n_pol != 4)) return cudaErrorInvalidValue;
     static int sms[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -393,16 +395,16 @@ cudaError_t launch_spread_ring(const int *offsets, const TcRec *rec, const cpx<f
         if (e != cudaSuccess) return e;
     }
     // persistent: three CTAs per SM (the register and shared-memory budget), each taking tiles by ticket
-    const int tiles_x = (g.dim[0].nf1 + kTcTileX - 1) / kTcTileX;
-    const int n_tiles = tiles_x * ((g.dim[1].nf1 + kTcTileY - 1) / kTcTileY);
+    const int tiles_x = (g.dim[0].nf1 + kRingTileX - 1) / kRingTileX;
+    const int n_tiles = tiles_x * ((g.dim[1].nf1 + kRingTileY - 1) / kRingTileY);
     const unsigned blocks = (unsigned)std::max(1, std::min(n_tiles, 3 * sms[dev]));
 #define FV_RING_ARGS offsets, rec, cs, g, tb, r0, r1, tiles_x, n_tiles, tile_ctr, status, grid
     if (g.n_pol == 4) {
-        if (tensor) k_spread_ring<4, true><<<blocks, kTcThreads, 0, st>>>(FV_RING_ARGS);
-        else k_spread_ring<4, false><<<blocks, kTcThreads, 0, st>>>(FV_RING_ARGS);
+        if (tensor) k_spread_ring<4, true><<<blocks, kRingThreads, 0, st>>>(FV_RING_ARGS);
+        else k_spread_ring<4, false><<<blocks, kRingThreads, 0, st>>>(FV_RING_ARGS);
     } else {
-        if (tensor) k_spread_ring<1, true><<<blocks, kTcThreads, 0, st>>>(FV_RING_ARGS);
-        else k_spread_ring<1, false><<<blocks, kTcThreads, 0, st>>>(FV_RING_ARGS);
+        if (tensor) k_spread_ring<1, true><<<blocks, kRingThreads, 0, st>>>(FV_RING_ARGS);
+        else k_spread_ring<1, false><<<blocks, kRingThreads, 0, st>>>(FV_RING_ARGS);
     }
 #undef FV_RING_ARGS
     return cudaGetLastError();

@@ -84,11 +84,11 @@ template <> struct __align__(16) SrcRec<double> {
 // One source of one slice as the ring gather (FP32 two-dimensional grids) reads it (80 bytes, copied in
 // bulk): the packed first footprint cell (as in SrcRec) and the kernel values of its footprint columns and
 // rows, phi((2/w)(f + j)) for j < w, zero for w <= j < 8.
-constexpr int kTcWmax = 8;
-struct __align__(16) TcRec {
+constexpr int kRingWmax = 8;
+struct __align__(16) RingRec {
     unsigned cell;
     unsigned pad[3];
-    float wx[kTcWmax], wy[kTcWmax];
+    float wx[kRingWmax], wy[kRingWmax];
 };
 
 // Complex strengths per source in the staged layout: n_pol values padded to a multiple of 16 bytes.
@@ -112,7 +112,7 @@ cudaError_t launch_spread_gather_rec(const int *offsets, const SrcRec<G> *rec, c
 // shared-memory ring, consumer warps summing 8 x 8 blocks with FP32 FMAs, or on the tensor cores when
 // `tensor` is set.  cudaErrorInvalidValue for other slices.  tile_ctr: a device int that is zero at launch
 // (launch_prep_tc sets it), the ticket of the persistent CTAs.
-cudaError_t launch_spread_ring(const int *offsets, const TcRec *rec, const cpx<float> *cs, const SliceGeom &g,
+cudaError_t launch_spread_ring(const int *offsets, const RingRec *rec, const cpx<float> *cs, const SliceGeom &g,
                                const TimeBin &tb, double r0, double r1, int *tile_ctr, int *status, cpx<float> *grid,
                                bool tensor, cudaStream_t st);
 
@@ -124,11 +124,11 @@ cudaError_t launch_prep_staged(const double *sdir, const int *sidx, const int *n
                                SrcRec<G> *rec, cpx<G> *cs, cudaStream_t st);
 
 // FP32 grids: the same, from the per-time records tc of launch_time_binning (no FP64 arithmetic); writes
-// ring records when trec is given (two-dimensional grids, w <= 8), else staged records when rec is
+// ring records when ring_rec is given (two-dimensional grids, w <= 8), else staged records when rec is
 // given, else cell[3][n] / frac[3][n] / cs[n_pol][n].  tile_ctr (or nullptr): the tile ticket of the
 // ring spreading that follows, set to zero.  n_src must be > 0 when tile_ctr is given.
 cudaError_t launch_prep_tc(const float4 *tc, const int *sidx, const int *nv_ptr, long n_src, const void *flux,
                            int flux_fp64, int n_freq, int f, const SliceGeom &g, int *cell, float *frac,
-                           cpx<float> *cs, SrcRec<float> *rec, TcRec *trec, int *tile_ctr, cudaStream_t st);
+                           cpx<float> *cs, SrcRec<float> *rec, RingRec *ring_rec, int *tile_ctr, cudaStream_t st);
 
 }  // namespace fv
