@@ -85,6 +85,8 @@ def parse():
     ap.add_argument("--batch-slices", type=int, default=2048)
     ap.add_argument("--lanes", type=int, default=8, help="batch and serving execution lanes")
     ap.add_argument("--no-tune", action="store_true", help="batch: default choices instead of the autotuner")
+    ap.add_argument("--batch-routes", default="auto",
+                    help="batch: routes the autotuner may choose, comma separated (auto, type3)")
     return ap.parse_args()
 
 
@@ -254,7 +256,7 @@ def run_batch(args, rank, world, local, dist):
     t_setup = time.perf_counter()
     slices = W.config_batch(seed=4 + rank, n_slices=args.batch_slices)
     stream = torch.cuda.Stream(device=dev)
-    tuner = AT.Autotuner(AT.cuda_timer(stream))
+    tuner = AT.Autotuner(AT.cuda_timer(stream), routes=tuple(args.batch_routes.split(",")))
     t0 = time.perf_counter()
     if not args.no_tune:
         tuner.tune(slices, AT.key_of, AT.precision_of)

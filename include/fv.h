@@ -156,7 +156,10 @@ typedef enum {
  * on a periodic grid of about 2 sigma (2 max|n_d| + 1) points per axis with no
  * interpolation step.  FV_TRANSFORM_AUTO takes this route when the array is a
  * lattice, K <= 24 and K times its grid is no larger than the type-3 grid of
- * the top channel; FV_TRANSFORM_TYPE3 never takes it; FV_TRANSFORM_LATTICE
+ * the top channel (t3 cells), and, for four products, 6 n_src K < n_src + t3
+ * (the lattice spreading adds every product with global atomics into one small
+ * grid, which contends for many sources); FV_TRANSFORM_TYPE3 never takes it;
+ * FV_TRANSFORM_LATTICE
  * always does, and fv_set_array fails with FV_ERR_UNSUPPORTED if the array is
  * not a lattice or needs more than 24 terms.
  *

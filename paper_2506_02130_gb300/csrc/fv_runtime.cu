@@ -323,6 +323,14 @@ static fv_status prepare_lattice(fv_plan_s *p)
         return FV_OK;
     }
     if (p->transform_req == FV_TRANSFORM_AUTO && cells * K > t3) return FV_OK;
+    // four products: the lattice spreading adds every product of every source with global atomics into one
+    // small grid, which contends; measured per slice on the 350-antenna workload (886k sources, K = 1) the
+    // lattice route took 0.52 ms against the type-3 route's 0.20 ms (about 6 N K units against N + t3 for
+    // the type-3 spreading and FFT passes), so auto keeps polarised plans on the type-3 route unless
+    // 6 N K < N + t3
+    if (p->transform_req == FV_TRANSFORM_AUTO && p->n_pol == 4 &&
+        6.0 * (double)p->n_src * K >= (double)p->n_src + (double)t3)
+        return FV_OK;
     p->use_lattice = true;
     p->lg = lg;
     p->lat_dim[0] = dg[0];

@@ -154,3 +154,18 @@ def test_fp64_lattice_borrowed_flux_rescaled_in_place():
     ref = oracle_vis(OracleProblem.from_workload(prob))
     assert rel_l2(a, ref) <= 1e-9
     p.close()
+
+
+def test_auto_keeps_polarised_plans_with_many_sources_on_type3():
+    """Four products: auto takes the lattice route only while 6 n_src K < n_src + t3 (the lattice spreading's
+    global atomics contend for many sources); a few hundred sources stay on the lattice route."""
+    few = W.config_hex350_pol(seed=64, n_chan=1, n_time=1, n_point=300, nside=0, n_keep=None, radius=3)
+    _, info = _run(few, fv.FV_MIXED, "auto")
+    assert info["transform"] == "lattice"
+    many = W.config_hex350_pol(seed=64, n_chan=1, n_time=1, n_point=40000, nside=0, n_keep=None, radius=3)
+    out, info = _run(many, fv.FV_MIXED, "auto")
+    n_src, t3 = many.sky.n_src, info["nf1_max"][0] * info["nf1_max"][1]
+    assert 6 * n_src >= n_src + t3 and info["transform"] == "type3"
+    ref = oracle_vis(OracleProblem.from_workload(many))
+    for p in range(4):
+        assert rel_l2(out[..., p], ref[..., p]) <= 2 * TOL[fv.FV_MIXED], p
