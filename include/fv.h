@@ -289,8 +289,9 @@ fv_status fv_set_sky(fv_plan_t p, long n_src, const double *ra_rad, const double
  * n_pol = 4 if polarized else 1.  vis_on_device = 0: host buffer, the call
  * returns when it is filled.  vis_on_device = 1: device buffer; the call
  * returns once the work is enqueued on the plan's stream (synchronise that
- * stream before reading).  Errors: FV_ERR_STATE (no array or sky),
- * FV_ERR_ARG (NULL vis), FV_ERR_CUDA. */
+ * stream before reading; a device vis must be aligned to its element size,
+ * 8 or 16 bytes).  Errors: FV_ERR_STATE (no array or sky), FV_ERR_ARG (NULL
+ * vis, or a device vis not aligned to its element size), FV_ERR_CUDA. */
 fv_status fv_execute(fv_plan_t p, void *vis, int vis_on_device);
 
 /* Release every device and host resource of the plan.  NULL is accepted. */
@@ -387,7 +388,7 @@ fv_status fv_profile_read(fv_plan_t p, fv_profile_data *out);
  *    timing (fv_profile_enable) off on every member plan.
  *  - fv_batch_clear: removes all items (and the graph).
  * Errors: FV_ERR_ARG (bad range, host output, plan or output on another
- * device), FV_ERR_STATE, FV_ERR_OOM, FV_ERR_CUDA, FV_ERR_TIMEOUT (a bounded
+ * device, output not aligned to its element size), FV_ERR_STATE, FV_ERR_OOM, FV_ERR_CUDA, FV_ERR_TIMEOUT (a bounded
  * wait of an earlier execution ran out; reported once); fv_batch_last_error
  * gives the message. */
 typedef struct fv_batch_s *fv_batch_t;
@@ -432,7 +433,8 @@ long long fv_batch_workspace_bytes(fv_batch_t b);
  *  - Returns when the work is enqueued on the plan's stream.
  * Errors: FV_ERR_UNSUPPORTED if the plan needs more scratch than
  * FV_STATIC_SCRATCH_BYTES (the message gives both sizes), FV_ERR_ARG (NULL or
- * host vis, or vis on another device), FV_ERR_STATE, FV_ERR_CUDA,
+ * host vis, vis on another device, or vis not aligned to its element size),
+ * FV_ERR_STATE, FV_ERR_CUDA,
  * FV_ERR_TIMEOUT (a bounded wait of an earlier execution ran out). */
 #define FV_STATIC_SCRATCH_BYTES (64ull << 20)
 fv_status fv_execute_static(fv_plan_t p, void *vis);

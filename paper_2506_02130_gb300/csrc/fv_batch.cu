@@ -10,6 +10,7 @@
 #include "fv_plan.cuh"
 
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 #include <numeric>
 
@@ -65,7 +66,8 @@ static bool covers(const fv_plan_s::WsNeed &have, const fv_plan_s::WsNeed &need)
     return have.grid >= need.grid && have.bufA >= need.bufA && have.bufB >= need.bufB && have.vu >= need.vu &&
            (!need.tiled || (have.tiled && have.n_src >= need.n_src && have.nb >= need.nb &&
                             have.frac_per_src >= need.frac_per_src && have.cs_per_src >= need.cs_per_src &&
-                            (have.tc || !need.tc)));
+                            (have.tc || !need.tc) && have.ring_tiles >= need.ring_tiles &&
+                            have.ring_slots >= need.ring_slots && have.ring_np >= need.ring_np));
 }
 
 // Enqueue every item on its lane (fork/join around the batch stream).
@@ -165,6 +167,8 @@ static fv_status add_items(fv_batch_t b, fv_plan_t p, void *vis, int t_lo, int t
     }
     if (pa.type == cudaMemoryTypeDevice && pa.device != b->device)
         return b->fail(FV_ERR_ARG, "the output buffer is on another device than the batch");
+    if ((uintptr_t)vis % (p->precision == FV_FP64 ? 16u : 8u) != 0)
+        return b->fail(FV_ERR_ARG, "batch outputs must be aligned to their element size");
     if (om.nt < 0 || om.f0 < 0 || om.t0 < 0 || om.f0 > f_lo || om.t0 > t_lo ||
         (om.nt > 0 && t_hi > om.t0 + om.nt))
         return b->fail(FV_ERR_ARG, "output layout does not hold the slice range");
@@ -240,6 +244,9 @@ fv_status fv_batch_execute(fv_batch_t b, int use_graph)
             need.frac_per_src = std::max(need.frac_per_src, n.frac_per_src);
             need.cs_per_src = std::max(need.cs_per_src, n.cs_per_src);
             need.tc = need.tc || n.tc;
+            need.ring_tiles = std::max(need.ring_tiles, n.ring_tiles);
+            need.ring_slots = std::max(need.ring_slots, n.ring_slots);
+            need.ring_np = std::max(need.ring_np, n.ring_np);
         }
     }
     if (b->ws.empty() || !covers(b->ws_need, need)) {

@@ -24,7 +24,8 @@
 
 namespace fv {
 
-template <class T> struct cpx { T x, y; };
+// aligned to its size, so that a complex value moves with one 8- or 16-byte load or store
+template <class T> struct alignas(2 * sizeof(T)) cpx { T x, y; };
 
 template <class T> __host__ __device__ __forceinline__ cpx<T> cmk(T a, T b) { cpx<T> r; r.x = a; r.y = b; return r; }
 template <class T> __host__ __device__ __forceinline__ cpx<T> cadd(cpx<T> a, cpx<T> b) { return cmk<T>(a.x + b.x, a.y + b.y); }

@@ -110,7 +110,13 @@ struct fv_plan_s {
         double *sdir = nullptr;
         void *frac = nullptr, *cs = nullptr;
         float4 *tc = nullptr;     // per-time coordinate records of the sorted sources (FP32 grids)
-        int *tiles = nullptr;     // tile ticket of the tensor-core spreading (reset by the prep kernel)
+        int *tiles = nullptr;     // ring gather: ticket and work-list counts (reset by the prep kernel)
+        // ring gather work list (fv_spread_ring.cu): tiles' bin rectangles, unsplit tiles, parts of split
+        // tiles, per-block part counters and the parts' block sums
+        int4 *ring_bins = nullptr, *ring_parts = nullptr;
+        int *ring_light = nullptr, *ring_cnt = nullptr;
+        float4 *ring_partial = nullptr;
+        int ring_tiles = 0, ring_slots = 0;
     };
     std::vector<Workspace> ws;
     // what one execution workspace must hold for this plan (set by prepare)
@@ -121,6 +127,7 @@ struct fv_plan_s {
         size_t frac_per_src = 0, cs_per_src = 0;       // bytes per source
         bool tiled = false;
         bool tc = false;                               // per-time coordinate records (48 bytes per source)
+        int ring_tiles = 0, ring_slots = 0, ring_np = 0; // ring gather: tiles of the largest grid, part slots, n_pol
     } need;
     int n_streams = 1;
     std::vector<cudaStream_t> sub;       // sub[0] is the plan's stream

@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -175,6 +176,16 @@ size_t workspace_layout(const fv_plan_s::WsNeed &need, char *base, fv_plan_s::Wo
         o.cs = take(ns * need.cs_per_src + 64);
         o.tc = need.tc ? (float4 *)take(ns * 3 * sizeof(float4)) : nullptr;
         o.tiles = (int *)take(4 * sizeof(int));
+        if (need.ring_tiles > 0) {
+            const size_t nt = (size_t)need.ring_tiles, sl = (size_t)need.ring_slots;
+            o.ring_tiles = need.ring_tiles;
+            o.ring_slots = need.ring_slots;
+            o.ring_bins = (int4 *)take(nt * sizeof(int4));
+            o.ring_light = (int *)take(nt * sizeof(int));
+            o.ring_cnt = (int *)take(nt * kRingBlocks * sizeof(int));
+            o.ring_parts = (int4 *)take(sl * sizeof(int4));
+            o.ring_partial = (float4 *)take(sl * kRingBlocks * need.ring_np * 32 * sizeof(float4));
+        }
     }
     return off;
 }
@@ -634,6 +645,12 @@ static fv_status prepare(fv_plan_s *p)
     // coordinates take 12 or 24, and strengths padded to 16 bytes
     const bool staged = p->spread_method == FV_SPREAD_GATHER || p->spread_method == FV_SPREAD_TENSOR;
     p->need.frac_per_src = p->ring ? sizeof(RingRec) : (staged ? 4 * gs : 3 * gs);
+    // ring gather: a work list over the tiles of the largest grid, and slots for the parts of split tiles
+    // (a tile's candidates come to at most 4 n_src, split tiles have more than kRingPart candidates each,
+    // so there are at most 8 n_src / kRingPart parts; beyond kRingSlotsMax tiles run whole)
+    p->need.ring_tiles = p->ring ? ring_tiles(p->nf1_max[0], p->nf1_max[1]) : 0;
+    p->need.ring_slots = p->ring ? (int)std::min<long>(kRingSlotsMax, 8 * std::max<long>(p->n_src, 1) / kRingPart + 1) : 0;
+    p->need.ring_np = p->ring ? p->n_pol : 0;
     p->need.cs_per_src = staged ? (size_t)staged_cs_stride((int)gs, p->n_pol) * es : (size_t)p->n_pol * es;
     // FP32 grids take each slice's coordinates and prephase from per-time records (no FP64 per slice)
     p->need.tc = p->precision == FV_MIXED && p->tiled;
@@ -839,8 +856,9 @@ fv_status run_slices(fv_plan_s *p, fv_plan_s::Workspace &wk, cudaStream_t st, ch
                 CK(prof_begin(p, PC_SPREAD, st));
                 if (ring)
                     CK(launch_spread_ring(wk.offsets, (const RingRec *)wk.frac, (const cpx<float> *)cs, g, tb, r0, r1,
-                                          wk.tiles, p->d_status, (cpx<float> *)grid,
-                                          p->spread_method == FV_SPREAD_TENSOR, st));
+                                          RingWork{wk.tiles, wk.ring_bins, wk.ring_light, wk.ring_parts, wk.ring_cnt,
+                                                   wk.ring_partial, wk.ring_tiles, wk.ring_slots},
+                                          p->d_status, (cpx<float> *)grid, p->spread_method == FV_SPREAD_TENSOR, st));
                 else if (p->spread_method == FV_SPREAD_GATHER || p->spread_method == FV_SPREAD_TENSOR)
                     CK(launch_spread_gather_rec<G>(wk.offsets, rec, cs, g, tb, r0, r1, p->d_status, grid, st));
                 else if (p->spread_method == FV_SPREAD_SCATTER)
@@ -1949,9 +1967,11 @@ fv_status fv_execute(fv_plan_t p, void *vis, int vis_on_device)
     if (!vis) return p->fail(FV_ERR_ARG, "vis is NULL");
     if (!p->have_array || !p->have_sky) return p->fail(FV_ERR_STATE, "fv_set_array and fv_set_sky must come first");
     if (cudaSetDevice(p->device) != cudaSuccess) return p->fail(FV_ERR_CUDA, "cudaSetDevice failed");
+    const size_t cb = p->precision == FV_FP64 ? 16 : 8;
+    if (vis_on_device && (uintptr_t)vis % cb != 0)
+        return p->fail(FV_ERR_ARG, "vis must be aligned to its element size (" + std::to_string(cb) + " bytes)");
     fv_status prev = plan_take_status(p, false);
     if (prev != FV_OK) return prev;
-    const size_t cb = p->precision == FV_FP64 ? 16 : 8;
     const size_t slice_bytes = (size_t)p->n_bl * p->n_pol * cb;
     const size_t total = slice_bytes * p->freq.size() * p->lst.size();
     char *dst = (char *)vis;

@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(256) k_prep_ring(const float4 *__restrict__ tc
     __shared__ float4 s_in[256 * 3];
     __shared__ float4 s_rec[256 * kRec4];
     __shared__ float4 s_cs[256 * kCs4];
-    if (tile_ctr && blockIdx.x == 0 && threadIdx.x == 0) *tile_ctr = 0;
+    if (tile_ctr && blockIdx.x == 0 && threadIdx.x < 4) tile_ctr[threadIdx.x] = 0;
     const long i0 = (long)blockIdx.x * 256;
     const long nv = *nv_ptr;
     if (i0 >= nv) return;                                       // the same on every thread of the CTA
@@ -335,10 +335,10 @@ __global__ void __launch_bounds__(256) k_prep_ring(const float4 *__restrict__ tc
                     g, o);
         RingRec h;
         h.cell = (unsigned)o.ci[0] | ((unsigned)o.ci[1] << 14);
-        h.pad[0] = h.pad[1] = h.pad[2] = 0u;
+        h.pad = 0u;
         const float two_over_w = 2.0f / (float)g.w, beta = g.beta_f;
 #pragma unroll
-        for (int j = 0; j < kRingWmax; ++j) {
+        for (int j = 0; j <= kRingWmax; ++j) {
             h.wx[j] = j < g.w ? es_kernel_f(two_over_w * (o.fr[0] + (float)j), beta) : 0.0f;
             h.wy[j] = j < g.w ? es_kernel_f(two_over_w * (o.fr[1] + (float)j), beta) : 0.0f;
         }

@@ -29,14 +29,14 @@
 #include "fv_staged.cuh"
 
 #include <algorithm>
+#include <climits>
 
 namespace fv {
 
 namespace {
 
-constexpr int kRingConsumers = 8;                       // 4 x 2 blocks of 8 x 8
+constexpr int kRingConsumers = kRingBlocks;               // 4 x 2 blocks of 8 x 8
 constexpr int kRingThreads = (kRingConsumers + 1) * 32;   // plus the producer warp
-constexpr int kRingTileX = 32, kRingTileY = 16;
 constexpr int kRingChunk = 128;
 constexpr int kRingStages = 3;
 
@@ -66,25 +66,94 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
+// One selected candidate (list entry ent) into one half of a consumer lane's cells: a[p] += c_p psi_x psi_y
+// with the lane's column and row given as ux = x + 16 and uy = y + 16 (the origin is stored + 16)
+template <int NP>
+__device__ __forceinline__ void ring_add(int ent, const RingRec *rec, const cpx<float> *cs, unsigned ux, unsigned uy,
+                                         float2 (&a)[NP])
+{
+    constexpr int kCsw = (NP * 8 + 15) / 16 * 16 / 8;
+    const int t = ent & 0xff;
+    const RingRec &r = rec[t];
+    const float wx = r.wx[min(ux - (((unsigned)ent >> 8) & 0xffu), (unsigned)kRingWmax)];
+    const float wy = r.wy[min(uy - ((unsigned)ent >> 16), (unsigned)kRingWmax)];
+    const float k = wx * wy;
+    const float4 *c4 = reinterpret_cast<const float4 *>(cs + t * kCsw);
+    float4 cv[NP > 1 ? 2 : 1];
+#pragma unroll
+    for (int q = 0; q < (NP > 1 ? 2 : 1); ++q) cv[q] = c4[q];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const float4 u = cv[p >> 1];
+        a[p] = __ffma2_rn(make_float2(k, k), (p & 1) ? make_float2(u.z, u.w) : make_float2(u.x, u.y), a[p]);
+    }
+}
+
 }  // namespace
+
+// The work list of one slice, one thread per tile: the tile's bin rectangle (the bins whose sources can
+// reach it, through the top-grid mapping q = (x - nx / 2) / r with a margin of 1.25 top cells, which holds
+// the FP32 rounding here and in the sources' coordinates many times over) and its candidate count; a tile
+// with more than kRingPart candidates gets ceil(count / kRingPart) consecutive part slots (while slots are
+// left), the others go to the unsplit list, those with candidates first.
+__device__ __forceinline__ int ring_top_bin(float q, int nf1, int T)
+{
+    const float c = floorf(q) + (float)(nf1 / 2);
+    return (int)fmaxf(0.0f, fminf(c, (float)(nf1 - 1))) / T;
+}
+
+__global__ void __launch_bounds__(64) k_ring_items(const int *__restrict__ offsets, TimeBin tb, int nx, int ny, int w,
+                                                   float inv_r0, float inv_r1, int tiles_x, int n_tiles, RingWork rw)
+{
+    const int tile = blockIdx.x * 64 + threadIdx.x;
+    if (tile >= n_tiles) return;
+    const int x0 = (tile % tiles_x) * kRingTileX, y0 = (tile / tiles_x) * kRingTileY;
+    const float hw = 0.5f * (float)w;
+    const int4 bn = make_int4(ring_top_bin(((float)(x0 - nx / 2) - hw) * inv_r0 - 1.25f, tb.nf1_top[0], tb.T[0]),
+                              ring_top_bin(((float)(x0 + kRingTileX - 1 - nx / 2) + hw) * inv_r0 + 1.25f, tb.nf1_top[0], tb.T[0]),
+                              ring_top_bin(((float)(y0 - ny / 2) - hw) * inv_r1 - 1.25f, tb.nf1_top[1], tb.T[1]),
+                              ring_top_bin(((float)(y0 + kRingTileY - 1 - ny / 2) + hw) * inv_r1 + 1.25f, tb.nf1_top[1], tb.T[1]));
+    rw.bins[tile] = bn;
+    long total = 0;
+#pragma unroll 4
+    for (int r = bn.z; r <= bn.w; ++r) total += offsets[r * tb.nbx + bn.y + 1] - offsets[r * tb.nbx + bn.x];
+    if (total == 0) {
+        rw.light[n_tiles - 1 - atomicAdd(&rw.hdr[3], 1)] = tile;
+        return;
+    }
+    if (total > kRingPart) {
+        // consecutive slots for the parts; where they run past the end, the slots that were taken are
+        // marked empty (tile -1) and the tile runs whole
+        const int np = (int)((total + kRingPart - 1) / kRingPart);
+        const int first = atomicAdd(&rw.hdr[1], np);
+        if (first + np <= rw.slots) {
+            for (int k = 0; k < np; ++k) rw.parts[first + k] = make_int4(tile, k, np, first);
+            for (int b = 0; b < kRingBlocks; ++b) rw.cnt[tile * kRingBlocks + b] = 0;
+            return;
+        }
+        for (int k = first; k < rw.slots; ++k) rw.parts[k] = make_int4(-1, 0, 1, 0);
+    }
+    rw.light[atomicAdd(&rw.hdr[2], 1)] = tile;     // unsplit
+}
 
 template <int NP, bool TC>
 __global__ void __launch_bounds__(kRingThreads, 3) k_spread_ring(const int *__restrict__ offsets,
                                                             const RingRec *__restrict__ rec,
                                                             const cpx<float> *__restrict__ cs, SliceGeom g, TimeBin tb,
-                                                            double r0, double r1, int tiles_x, int n_tiles,
-                                                            int *__restrict__ tile_ctr, int *__restrict__ status,
-                                                            cpx<float> *__restrict__ grid)
+                                                            int tiles_x, int n_tiles, RingWork rw,
+                                                            int *__restrict__ status, cpx<float> *__restrict__ grid)
 {
     constexpr int kCsw = (NP * 8 + 15) / 16 * 16 / 8;           // staged strengths per source (16-byte rows)
     __shared__ __align__(16) RingRec s_rec[kRingStages][kRingChunk];
     __shared__ __align__(16) cpx<float> s_cs[kRingStages][kRingChunk * kCsw];
     __shared__ __align__(8) uint64_t s_full[kRingStages], s_empty[kRingStages];
-    // per stage: candidates of a chunk, or -1 for a tile boundary whose next tile is s_tile
-    __shared__ int s_n[kRingStages], s_tile[kRingStages];
+    // per stage: candidates of a chunk, or -1 for a work-item boundary whose next item is tile s_tile,
+    // part (bits 0-15) of s_part >> 16 parts, the tile's first part slot s_slot
+    __shared__ int s_n[kRingStages], s_tile[kRingStages], s_part[kRingStages], s_slot[kRingStages];
     // a warp's selected candidates: t (bits 0-7) and the footprint origin relative to the block + 16 in x
-    // (bits 8-15) and y (bits 16-23)
-    __shared__ int s_sel[kRingConsumers][kRingChunk];
+    // (bits 8-15) and y (bits 16-23); the FP32 form keeps the candidates that reach the block's rows 0-3
+    // from the front and those that reach rows 4-7 from the back (a candidate may be in both)
+    __shared__ int s_sel[kRingConsumers][TC ? kRingChunk : 2 * kRingChunk];
     __shared__ int s_row0[32], s_pre[32];                         // the producer's rows table
     __shared__ int s_abort;
     const int nx = g.dim[0].nf1, ny = g.dim[1].nf1;
@@ -101,14 +170,17 @@ __global__ void __launch_bounds__(kRingThreads, 3) k_spread_ring(const int *__re
     __syncthreads();
     volatile int *abort_flag = &s_abort;
 
-    // Tiles are handed out by an atomic ticket (tile_ctr, zeroed by the prep kernel before this launch);
-    // the producer runs ahead across tile boundaries, so the next tile's first chunks are in flight while
-    // the consumers finish the current one.
+    // Work items (a tile, or a part of a split tile) are handed out by an atomic ticket (rw.hdr[0], zeroed
+    // by the prep kernel before this launch); the producer runs ahead across item boundaries, so the next
+    // item's first chunks are in flight while the consumers finish the current one.
     if (warp == kRingConsumers) {
-        // ---------------- producer warp: tiles, rows tables and bulk copies of the candidate chunks
+        // ---------------- producer warp: work items, rows tables and bulk copies of the candidate chunks
         int kc = 0;              // stages filled
         unsigned ephase = 0u;    // bit b: parity of the next completion of stage b's empty barrier
         int ok = 1;
+        // the work list (complete: the work-list kernel ran before this launch): parts of split tiles, then
+        // unsplit tiles with candidates, then tiles without
+        const int n_split = min(rw.hdr[1], rw.slots), n_light = rw.hdr[2], n_empty = rw.hdr[3];
         // lane 0: wait until stage kc % kRingStages is free (its previous use consumed); false if that ran out
         auto acquire = [&](int b) -> bool {
             if (kc < kRingStages) return true;
@@ -116,47 +188,53 @@ __global__ void __launch_bounds__(kRingThreads, 3) k_spread_ring(const int *__re
             ephase ^= 1u << b;
             return got && !*abort_flag;
         };
-        // lane 0: take the next tile and announce it with a boundary stage
-        auto next_tile = [&]() -> int {
-            const int t = atomicAdd(tile_ctr, 1);
+        // lane 0: take the next work item (tile, part, parts, first slot; tile n_tiles when none is left)
+        // and announce it with a boundary stage
+        auto next_item = [&]() -> int4 {
+            int t = atomicAdd(&rw.hdr[0], 1);
+            // slots marked empty are passed over (at most n_split of them)
+            while (t < n_split && rw.parts[t].x < 0) t = atomicAdd(&rw.hdr[0], 1);
+            int4 it = make_int4(n_tiles, 0, 1, 0);
+            if (t < n_split) it = rw.parts[t];
+            else if (t < n_split + n_light) it.x = rw.light[t - n_split];
+            else if (t < n_split + n_light + n_empty) it.x = rw.light[n_tiles - 1 - (t - n_split - n_light)];
             const int b = kc % kRingStages;
             if (!acquire(b)) {
                 ok = 0;
-                return n_tiles;
+                it.x = n_tiles;
+                return it;
             }
             s_n[b] = -1;
-            s_tile[b] = t;
+            s_tile[b] = it.x;
+            s_part[b] = it.y | (it.z << 16);
+            s_slot[b] = it.w;
             mbar_arrive(&s_full[b]);
             ++kc;
-            return t;
+            return it;
         };
-        int tile = lane == 0 ? next_tile() : 0;
-        tile = __shfl_sync(0xffffffffu, tile, 0);
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        kc = __shfl_sync(0xffffffffu, kc, 0);
-        while (tile < n_tiles && ok) {
-            const int x0 = (tile % tiles_x) * kRingTileX, y0 = (tile / tiles_x) * kRingTileY;
-            int bins[4] = {0, 0, 0, 0};
-            if (lane == 0) {
-                // the bin rectangle of the tile (one-cell margin through the top-grid mapping), in FP64
-                const double qx_lo = (x0 - nx / 2 - 0.5 * w) / r0;
-                const double qx_hi = (x0 + kRingTileX - nx / 2 + 0.5 * w - 1) / r0;
-                const double qy_lo = (y0 - ny / 2 - 0.5 * w) / r1;
-                const double qy_hi = (y0 + kRingTileY - ny / 2 + 0.5 * w - 1) / r1;
-                bins[0] = top_cell(qx_lo - 1.0, tb.nf1_top[0]) / tb.T[0];
-                bins[1] = top_cell(qx_hi + 1.0, tb.nf1_top[0]) / tb.T[0];
-                bins[2] = top_cell(qy_lo - 1.0, tb.nf1_top[1]) / tb.T[1];
-                bins[3] = top_cell(qy_hi + 1.0, tb.nf1_top[1]) / tb.T[1];
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) bins[k] = __shfl_sync(0xffffffffu, bins[k], 0);
-            for (int r0w = bins[2]; r0w <= bins[3] && ok; r0w += 32) {
-                const int nrows = min(32, bins[3] - r0w + 1);
+        int4 item = make_int4(n_tiles, 0, 1, 0);
+        if (lane == 0) item = next_item();
+        auto share = [&]() {
+            item.x = __shfl_sync(0xffffffffu, item.x, 0);
+            item.y = __shfl_sync(0xffffffffu, item.y, 0);
+            item.z = __shfl_sync(0xffffffffu, item.z, 0);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            kc = __shfl_sync(0xffffffffu, kc, 0);
+            ephase = __shfl_sync(0xffffffffu, ephase, 0);
+        };
+        share();
+        while (item.x < n_tiles && ok) {
+            const int4 bn = rw.bins[item.x];       // bin rectangle: x0, x1, y0, y1
+            // the part's range [plo, phi) of the tile's candidates in row order (all of an unsplit tile's)
+            const long plo = (long)item.y * kRingPart, phi = item.z > 1 ? plo + kRingPart : LONG_MAX;
+            long gbase = 0;                          // candidates in the bin rows before this group
+            for (int r0w = bn.z; r0w <= bn.w && ok && gbase < phi; r0w += 32) {
+                const int nrows = min(32, bn.w - r0w + 1);
                 int start = 0, len = 0;
                 if (lane < nrows) {
                     const int row = (r0w + lane) * tb.nbx;
-                    start = offsets[row + bins[0]];
-                    len = offsets[row + bins[1] + 1] - start;
+                    start = offsets[row + bn.x];
+                    len = offsets[row + bn.y + 1] - start;
                 }
                 int incl = len;
 #pragma unroll
@@ -167,15 +245,17 @@ __global__ void __launch_bounds__(kRingThreads, 3) k_spread_ring(const int *__re
                 s_row0[lane] = start;
                 s_pre[lane] = incl - len;
                 const int total = __shfl_sync(0xffffffffu, incl, 31);
+                // this part's candidates among the group's
+                const int a0 = (int)max(plo - gbase, 0L), a1 = (int)min(phi - gbase, (long)total);
                 __syncwarp();
                 if (lane == 0) {
-                    for (int base = 0; base < total; base += kRingChunk) {
+                    for (int base = a0; base < a1; base += kRingChunk) {
                         const int b = kc % kRingStages;
                         if (!acquire(b)) {
                             ok = 0;
                             break;
                         }
-                        const int n = min(kRingChunk, total - base);
+                        const int n = min(kRingChunk, a1 - base);
                         s_n[b] = n;
                         mbar_expect(&s_full[b], (unsigned)n * (unsigned)(sizeof(RingRec) + kCsw * sizeof(cpx<float>)));
                         for (int r = 0; r < nrows; ++r) {
@@ -190,17 +270,15 @@ __global__ void __launch_bounds__(kRingThreads, 3) k_spread_ring(const int *__re
                         ++kc;
                     }
                 }
+                gbase += total;
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 kc = __shfl_sync(0xffffffffu, kc, 0);
                 ephase = __shfl_sync(0xffffffffu, ephase, 0);
                 __syncwarp();    // lane 0 is done with the rows table before the next group rewrites it
             }
             if (!ok) break;
-            tile = lane == 0 ? next_tile() : 0;
-            tile = __shfl_sync(0xffffffffu, tile, 0);
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            kc = __shfl_sync(0xffffffffu, kc, 0);
-            ephase = __shfl_sync(0xffffffffu, ephase, 0);
+            if (lane == 0) item = next_item();
+            share();
         }
         if (lane == 0 && !ok) {
             // a wait ran out: tell the consumers, record it, and wait (bounded) for the copies in flight
@@ -216,12 +294,16 @@ __global__ void __launch_bounds__(kRingThreads, 3) k_spread_ring(const int *__re
     const int gq = lane >> 2, tq = lane & 3;                             // fragment group, k index
     unsigned fphase = 0u;    // bit b: parity of the next completion of stage b's full barrier
     int tile = -1;           // none yet
+    int part = 0, nparts = 1, slot0 = 0;    // the current item's part of its tile, and the tile's first slot
     int bx0 = 0, by0 = 0;    // the block's first cell
-    float d[NP][4];
+    float d[NP][4];         // tensor form: the D fragments
+    float2 acc[2][NP];      // FP32 form: rows y and y + 4 of the lane's column, (Re, Im) per product
 #pragma unroll
-    for (int p = 0; p < NP; ++p)
+    for (int p = 0; p < NP; ++p) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) d[p][k] = 0.0f;
+        acc[0][p] = acc[1][p] = make_float2(0.0f, 0.0f);
+    }
     for (int kc = 0;; ++kc) {
         const int b = kc % kRingStages;
         // the lanes decide together: a wait that ran out on any lane, or an abort, ends the warp's work
@@ -235,54 +317,47 @@ __global__ void __launch_bounds__(kRingThreads, 3) k_spread_ring(const int *__re
             }
             break;
         }
-        const int n = s_n[b], next = s_tile[b];
+        const int n = s_n[b], next = s_tile[b], next_part = s_part[b], next_slot = s_slot[b];
         if (n > 0) {
             // the chunk's candidates whose footprint overlaps this block, in order
-            int L = 0;
+            int L = 0, L4 = 0;
             for (int c0 = 0; c0 < n; c0 += 32) {
                 const int t = c0 + lane;
-                bool hit = false;
+                bool hit = false, top = false;
                 int ent = 0;
                 if (t < n) {
                     const unsigned cell = s_rec[b][t].cell;
                     const int cx = (int)(cell & 0x3fffu) - bx0, cy = (int)((cell >> 14) & 0x3fffu) - by0;
                     hit = cx <= 7 && cx + w > 0 && cy <= 7 && cy + w > 0;    // then -15 < cx, cy <= 7
                     ent = t | ((cx + 16) << 8) | ((cy + 16) << 16);
+                    if (!TC) {
+                        top = hit && cy + w > 4;       // reaches rows 4-7
+                        hit = hit && cy <= 3;          // reaches rows 0-3
+                    }
                 }
+                const unsigned below = (1u << lane) - 1u;
                 const unsigned m = __ballot_sync(0xffffffffu, hit);
-                if (hit) s_sel[warp][L + __popc(m & ((1u << lane) - 1u))] = ent;
+                if (hit) s_sel[warp][L + __popc(m & below)] = ent;
                 L += __popc(m);
+                if (!TC) {
+                    const unsigned m4 = __ballot_sync(0xffffffffu, top);
+                    if (top) s_sel[warp][2 * kRingChunk - 1 - (L4 + __popc(m4 & below))] = ent;
+                    L4 += __popc(m4);
+                }
             }
             __syncwarp();
             if (!TC) {
-                // FP32 FMAs: lane (x = lane & 7, rows lane >> 3 and + 4) adds every selected candidate's
-                // c psi_x(x) psi_y(y) into its two cells; out-of-footprint lanes add zero weights
-                const int lx = lane & 7, ly = lane >> 3;
+                // FP32 FMAs: lane (x = lane & 7, rows y = lane >> 3 and y + 4) adds c psi_x(x) psi_y(y) of every
+                // selected candidate into its cells, the real and imaginary parts by one packed FP32 x 2 FMA.
+                // A candidate is taken once per half of the block it reaches; lanes outside its footprint
+                // read the zero kernel value at index 8.
+                const unsigned ux = (unsigned)((lane & 7) + 16), uy = (unsigned)((lane >> 3) + 16);
 #pragma unroll 2
-                for (int e = 0; e < L; ++e) {
-                    const int ent = s_sel[warp][e];
-                    const int t = ent & 0xff;
-                    const RingRec &r = s_rec[b][t];
-                    const unsigned dx = (unsigned)(lx + 16 - ((ent >> 8) & 0xff));
-                    const unsigned dy0 = (unsigned)(ly + 16 - (ent >> 16)), dy1 = dy0 + 4u;
-                    const float wx = dx < (unsigned)kRingWmax ? r.wx[dx] : 0.0f;
-                    const float wy0 = dy0 < (unsigned)kRingWmax ? r.wy[dy0] : 0.0f;
-                    const float wy1 = dy1 < (unsigned)kRingWmax ? r.wy[dy1] : 0.0f;
-                    const float4 *c4 = reinterpret_cast<const float4 *>(&s_cs[b][t * kCsw]);
-                    float4 cv[NP > 1 ? 2 : 1];
-#pragma unroll
-                    for (int q = 0; q < (NP > 1 ? 2 : 1); ++q) cv[q] = c4[q];
-                    const float k0 = wx * wy0, k1 = wx * wy1;     // the two cells' kernel weights
-#pragma unroll
-                    for (int p = 0; p < NP; ++p) {
-                        const float4 u = cv[p >> 1];
-                        const float cr = (p & 1) ? u.z : u.x, ci = (p & 1) ? u.w : u.y;
-                        d[p][0] = fmaf(k0, cr, d[p][0]);
-                        d[p][1] = fmaf(k0, ci, d[p][1]);
-                        d[p][2] = fmaf(k1, cr, d[p][2]);
-                        d[p][3] = fmaf(k1, ci, d[p][3]);
-                    }
-                }
+                for (int e = 0; e < L; ++e)
+                    ring_add<NP>(s_sel[warp][e], s_rec[b], s_cs[b], ux, uy, acc[0]);
+#pragma unroll 2
+                for (int e = 0; e < L4; ++e)
+                    ring_add<NP>(s_sel[warp][2 * kRingChunk - 1 - e], s_rec[b], s_cs[b], ux, uy + 4u, acc[1]);
             }
             // eight candidates per product: this lane supplies k = tq (h = 0) and k = tq + 4 (h = 1)
             for (int e = 0; TC && e < L; e += 8) {
@@ -330,8 +405,45 @@ __global__ void __launch_bounds__(kRingThreads, 3) k_spread_ring(const int *__re
         __syncwarp();
         if (lane == 0) mbar_arrive(&s_empty[b]);      // after the stage was read
         if (n < 0) {
-            if (tile >= 0 && !TC) {
-                // this lane's cells: (bx0 + lane & 7, by0 + lane >> 3) in d[p][0..1], four rows down in d[p][2..3]
+            bool store = tile >= 0;
+            if (store && nparts > 1) {
+                // a part of a split tile: its block sums go to the part's slot, and the last of the tile's
+                // parts to finish this block adds the others' to its own and stores the block
+                float4 *mine = rw.partial + ((size_t)(slot0 + part) * kRingBlocks + warp) * NP * 32 + lane;
+#pragma unroll
+                for (int p = 0; p < NP; ++p)
+                    mine[p * 32] = TC ? make_float4(d[p][0], d[p][1], d[p][2], d[p][3])
+                                      : make_float4(acc[0][p].x, acc[0][p].y, acc[1][p].x, acc[1][p].y);
+                __threadfence();
+                __syncwarp();
+                int done = 0;
+                if (lane == 0) done = atomicAdd(&rw.cnt[tile * kRingBlocks + warp], 1);
+                store = __shfl_sync(0xffffffffu, done, 0) == nparts - 1;
+                if (store) {
+                    __threadfence();
+                    for (int j = 0; j < nparts; ++j) {
+                        if (j == part) continue;
+                        const float4 *o = rw.partial + ((size_t)(slot0 + j) * kRingBlocks + warp) * NP * 32 + lane;
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) {
+                            const float4 v = __ldcg(o + p * 32);
+                            if (TC) {
+                                d[p][0] += v.x;
+                                d[p][1] += v.y;
+                                d[p][2] += v.z;
+                                d[p][3] += v.w;
+                            } else {
+                                acc[0][p].x += v.x;
+                                acc[0][p].y += v.y;
+                                acc[1][p].x += v.z;
+                                acc[1][p].y += v.w;
+                            }
+                        }
+                    }
+                }
+            }
+            if (store && !TC) {
+                // this lane's cells: (bx0 + lane & 7, by0 + lane >> 3) in acc[0], four rows down in acc[1]
                 const int x = bx0 + (lane & 7);
                 const float *px = (const float *)g.pre_x, *py = (const float *)g.pre_y;
 #pragma unroll
@@ -341,11 +453,11 @@ __global__ void __launch_bounds__(kRingThreads, 3) k_spread_ring(const int *__re
                         const float sc = (py ? py[y] : 1.0f) * (px ? px[x] : 1.0f);
 #pragma unroll
                         for (int p = 0; p < NP; ++p)
-                            grid[((size_t)p * ny + y) * nx + x] = cmk<float>(d[p][2 * c] * sc, d[p][2 * c + 1] * sc);
+                            grid[((size_t)p * ny + y) * nx + x] = cmk<float>(acc[c][p].x * sc, acc[c][p].y * sc);
                     }
                 }
             }
-            if (tile >= 0 && TC) {
+            if (store && TC) {
                 // D fragment of product p: d0 = Re (row gq, column 2 tq), d1 = Re (gq, 2 tq + 1),
                 // d2 = Im (gq, 2 tq), d3 = Im (gq, 2 tq + 1); rows are y and columns x of the block
                 const int gy = by0 + gq, gx = bx0 + 2 * tq;
@@ -366,11 +478,16 @@ __global__ void __launch_bounds__(kRingThreads, 3) k_spread_ring(const int *__re
             }
             if (tile >= 0) {
 #pragma unroll
-                for (int p = 0; p < NP; ++p)
+                for (int p = 0; p < NP; ++p) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) d[p][k] = 0.0f;
+                    acc[0][p] = acc[1][p] = make_float2(0.0f, 0.0f);
+                }
             }
             tile = next;
+            part = next_part & 0xffff;
+            nparts = next_part >> 16;
+            slot0 = next_slot;
             if (tile >= n_tiles) break;
             bx0 = (tile % tiles_x) * kRingTileX + (warp & 3) * 8;
             by0 = (tile / tiles_x) * kRingTileY + (warp >> 2) * 8;
@@ -381,10 +498,13 @@ __global__ void __launch_bounds__(kRingThreads, 3) k_spread_ring(const int *__re
 // The ring gather for an FP32 two-dimensional slice (n_pol 1 or 4, w <= 8) from ring records (launch_prep_tc);
 // tensor: the block sums on the tensor cores.  Writes every cell of grid [n_pol][ny][nx].
 cudaError_t launch_spread_ring(const int *offsets, const RingRec *rec, const cpx<float> *cs, const SliceGeom &g,
-                               const TimeBin &tb, double r0, double r1, int *tile_ctr, int *status, cpx<float> *grid,
-                               bool tensor, cudaStream_t st)
+                               const TimeBin &tb, double r0, double r1, const RingWork &rw, int *status,
+                               cpx<float> *grid, bool tensor, cudaStream_t st)
 {
     if (g.d != 2 || g.K != 0 || g.w > kRingWmax || (g.n_pol != 1 && g.n_pol != 4)) return cudaErrorInvalidValue;
+    const int tiles_x = (g.dim[0].nf1 + kRingTileX - 1) / kRingTileX;
+    const int n_tiles = ring_tiles(g.dim[0].nf1, g.dim[1].nf1);
+    if (!rw.hdr || n_tiles > rw.tiles || rw.slots < 0) return cudaErrorInvalidValue;
     static int sms[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -394,11 +514,11 @@ cudaError_t launch_spread_ring(const int *offsets, const RingRec *rec, const cpx
         e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
     }
-    // persistent: three CTAs per SM (the register and shared-memory budget), each taking tiles by ticket
-    const int tiles_x = (g.dim[0].nf1 + kRingTileX - 1) / kRingTileX;
-    const int n_tiles = tiles_x * ((g.dim[1].nf1 + kRingTileY - 1) / kRingTileY);
-    const unsigned blocks = (unsigned)std::max(1, std::min(n_tiles, 3 * sms[dev]));
-#define FV_RING_ARGS offsets, rec, cs, g, tb, r0, r1, tiles_x, n_tiles, tile_ctr, status, grid
+    k_ring_items<<<(n_tiles + 63) / 64, 64, 0, st>>>(offsets, tb, g.dim[0].nf1, g.dim[1].nf1, g.w, (float)(1.0 / r0),
+                                                     (float)(1.0 / r1), tiles_x, n_tiles, rw);
+    // persistent: three CTAs per SM (the register and shared-memory budget), each taking work items by ticket
+    const unsigned blocks = (unsigned)std::max(1, std::min(n_tiles + rw.slots, 3 * sms[dev]));
+#define FV_RING_ARGS offsets, rec, cs, g, tb, tiles_x, n_tiles, rw, status, grid
     if (g.n_pol == 4) {
         if (tensor) k_spread_ring<4, true><<<blocks, kRingThreads, 0, st>>>(FV_RING_ARGS);
         else k_spread_ring<4, false><<<blocks, kRingThreads, 0, st>>>(FV_RING_ARGS);

@@ -83,13 +83,15 @@ template <> struct __align__(16) SrcRec<double> {
 
 // One source of one slice as the ring gather (FP32 two-dimensional grids) reads it (80 bytes, copied in
 // bulk): the packed first footprint cell (as in SrcRec) and the kernel values of its footprint columns and
-// rows, phi((2/w)(f + j)) for j < w, zero for w <= j < 8.
+// rows, phi((2/w)(f + j)) for j < w, zero for w <= j <= 8 (index 8 is always zero, so that a lookup
+// clamped to 8 needs no test).
 constexpr int kRingWmax = 8;
 struct __align__(16) RingRec {
     unsigned cell;
-    unsigned pad[3];
-    float wx[kRingWmax], wy[kRingWmax];
+    float wx[kRingWmax + 1], wy[kRingWmax + 1];
+    unsigned pad;
 };
+static_assert(sizeof(RingRec) == 80, "ring records are 80 bytes (five 16-byte rows)");
 
 // Complex strengths per source in the staged layout: n_pol values padded to a multiple of 16 bytes.
 __host__ __device__ inline int staged_cs_stride(int elem, int n_pol)   // complex elements per source
@@ -107,14 +109,39 @@ cudaError_t launch_spread_gather_rec(const int *offsets, const SrcRec<G> *rec, c
                                      const TimeBin &tb, double r0, double r1, int *status, cpx<G> *grid,
                                      cudaStream_t st);
 
+// Tiles of the ring gather: 32 x 16 cells, eight 8 x 8 blocks (one per consumer warp).  A tile with more
+// than kRingPart candidates is split into parts of kRingPart candidates that different CTAs take; each
+// part leaves its block sums in a slot and the last part of a tile to finish adds them up and stores the
+// tile.  At most kRingSlotsMax parts per slice; tiles beyond them run whole.
+constexpr int kRingTileX = 32, kRingTileY = 16, kRingBlocks = 8;
+constexpr int kRingPart = 1024;
+constexpr int kRingSlotsMax = 2048;
+__host__ __device__ inline int ring_tiles(int nx, int ny)
+{
+    return ((nx + kRingTileX - 1) / kRingTileX) * ((ny + kRingTileY - 1) / kRingTileY);
+}
+
+// The work list of one ring-gather launch (device arrays of an execution workspace).
+struct RingWork {
+    int *hdr;          // [4]: ticket, parts of split tiles, unsplit tiles with candidates, tiles without
+                       // (zero at the start of a slice: launch_prep_tc clears them)
+    int4 *bins;        // [tiles]: bin rectangle (x0, x1, y0, y1) of a tile
+    int *light;        // [tiles]: unsplit tiles with candidates from the front, tiles without from the back
+    int4 *parts;       // [slots]: (tile, part, parts of the tile, the tile's first slot); tile -1: unused
+    int *cnt;          // [tiles][kRingBlocks]: parts of a split tile finished, per block
+    float4 *partial;   // [slots][kRingBlocks][n_pol][32 lanes]: a part's block sums
+    int tiles, slots;
+};
+
 // The ring form of the same spreading for FP32 two-dimensional grids (n_pol 1 or 4, no height terms,
-// w <= 8), reading ring records: persistent CTAs, a producer warp streaming candidate chunks into a
-// shared-memory ring, consumer warps summing 8 x 8 blocks with FP32 FMAs, or on the tensor cores when
-// `tensor` is set.  cudaErrorInvalidValue for other slices.  tile_ctr: a device int that is zero at launch
-// (launch_prep_tc sets it), the ticket of the persistent CTAs.
+// w <= 8), reading ring records: a work-list kernel (bin rectangle and candidate count per tile, heavy
+// tiles split into parts) and the gather itself: persistent CTAs, a producer warp streaming candidate
+// chunks into a shared-memory ring, consumer warps summing 8 x 8 blocks with FP32 FMAs, or on the tensor
+// cores when `tensor` is set.  cudaErrorInvalidValue for other slices or when the grid has more tiles
+// than rw holds.  rw.hdr must be zero at launch (launch_prep_tc clears it).
 cudaError_t launch_spread_ring(const int *offsets, const RingRec *rec, const cpx<float> *cs, const SliceGeom &g,
-                               const TimeBin &tb, double r0, double r1, int *tile_ctr, int *status, cpx<float> *grid,
-                               bool tensor, cudaStream_t st);
+                               const TimeBin &tb, double r0, double r1, const RingWork &rw, int *status,
+                               cpx<float> *grid, bool tensor, cudaStream_t st);
 
 // Per slice: strengths with prephase and packed grid coordinates of the sorted sources, as staged
 // records (the same arithmetic as launch_prep).
@@ -125,8 +152,8 @@ cudaError_t launch_prep_staged(const double *sdir, const int *sidx, const int *n
 
 // FP32 grids: the same, from the per-time records tc of launch_time_binning (no FP64 arithmetic); writes
 // ring records when ring_rec is given (two-dimensional grids, w <= 8), else staged records when rec is
-// given, else cell[3][n] / frac[3][n] / cs[n_pol][n].  tile_ctr (or nullptr): the tile ticket of the
-// ring spreading that follows, set to zero.  n_src must be > 0 when tile_ctr is given.
+// given, else cell[3][n] / frac[3][n] / cs[n_pol][n].  tile_ctr (or nullptr): the four counters of the
+// ring spreading's work list (RingWork::hdr), set to zero.  n_src must be > 0 when tile_ctr is given.
 cudaError_t launch_prep_tc(const float4 *tc, const int *sidx, const int *nv_ptr, long n_src, const void *flux,
                            int flux_fp64, int n_freq, int f, const SliceGeom &g, int *cell, float *frac,
                            cpx<float> *cs, SrcRec<float> *rec, RingRec *ring_rec, int *tile_ctr, cudaStream_t st);

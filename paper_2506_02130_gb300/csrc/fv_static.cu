@@ -25,6 +25,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 
@@ -102,6 +103,8 @@ extern "C" fv_status fv_execute_static(fv_plan_t p, void *vis)
     }
     if (pa.type == cudaMemoryTypeDevice && pa.device != p->device)
         return p->fail(FV_ERR_ARG, "the output buffer is on another device than the plan");
+    if ((uintptr_t)vis % (p->precision == FV_FP64 ? 16u : 8u) != 0)
+        return p->fail(FV_ERR_ARG, "vis must be aligned to its element size");
     fv_status prev = plan_take_status(p, false);
     if (prev != FV_OK) return prev;
     // the same carving as a plan's own execution workspace (fv_plan_s::need), over the static array

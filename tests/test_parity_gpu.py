@@ -303,6 +303,29 @@ def test_ring_gather_kernel_width_limit(eps, sigma):
     assert rel_l2(out, oracle(prob)) <= TOL[fv.FV_MIXED]
 
 
+@pytest.mark.parametrize("polarized", [False, True])
+def test_ring_gather_splits_crowded_tiles(polarized):
+    """Many sources on a small coplanar array's grid put thousands of candidates on a tile: such tiles are
+    split into parts of 1,024 candidates that different CTAs sum, the last part of a tile adding the
+    others' block sums.  The result matches the scatter spreading (which has no tiles) on every baseline
+    and meets the mixed gate against the oracle on sampled baselines."""
+    if polarized:
+        prob = W.config_hex350_pol(seed=31, n_chan=2, n_time=1, n_point=200000, nside=16, n_keep=None, radius=3)
+    else:
+        prob = W.config_hex127(seed=31, n_chan=2, n_time=1, n_point=200000, nside=16, radius=3)
+        prob.ant_enu = W.hex_array(3)                   # coplanar: two-dimensional grids
+    out, info = run_gpu(prob, fv.FV_MIXED, transform="type3")
+    assert info["dims"] == 2 and info["spread"] == "gather"
+    # crowded: about half the sources are visible, on the tiles of the central half of each grid axis
+    nx, ny = info["nf1_max"][0], info["nf1_max"][1]
+    tiles = math.pi / 4 * (nx / 64 + 1) * (ny / 32 + 1)
+    assert 0.5 * prob.sky.n_src / tiles > 2 * 1024
+    ref, _ = run_gpu(prob, fv.FV_MIXED, transform="type3", spread="scatter")
+    assert rel_l2(out, ref) <= 1e-5
+    sel = np.sort(np.random.default_rng(0).choice(len(prob.pairs), 64, replace=False))
+    assert rel_l2(out[:, :, sel], oracle(prob, pairs=prob.pairs[sel])) <= TOL[fv.FV_MIXED]
+
+
 def test_bounded_wait_reports_timeout_and_the_plan_recovers():
     """A wait that runs out (the self-test's barrier phase that nothing completes, about a second) is
     reported as FV_ERR_TIMEOUT by the plan's next execution; the execution after it is correct again."""

@@ -114,3 +114,23 @@ def test_static_scratch_refuses_oversize_plans_and_host_buffers():
         fv.fv_execute_static(small.handle, np.zeros(small.out_shape, np.complex64))
     assert ei.value.status == fv.FV_ERR_ARG
     small.close()
+
+
+@pytest.mark.parametrize("precision,eps,dtype", [(fv.FV_MIXED, 1e-6, "float32"), (fv.FV_FP64, 1e-11, "float64")])
+def test_device_output_not_aligned_to_its_element_size_is_refused(precision, eps, dtype):
+    # the kernels store a complex value with one 8- or 16-byte access, so an output that starts half an
+    # element off is refused before anything is enqueued
+    torch = pytest.importorskip("torch")
+    prob = W.config_small(seed=24, n_src=200)
+    p = _plan(prob, precision, eps)
+    n = int(np.prod(p.out_shape)) * 2
+    buf = torch.zeros(n + 1, dtype=getattr(torch, dtype), device="cuda")
+    for call in (fv.fv_execute, fv.fv_execute_static):
+        with pytest.raises(fv.FvError) as ei:
+            call(p.handle, buf[1:])
+        assert ei.value.status == fv.FV_ERR_ARG and "aligned" in str(ei.value)
+    # the plan is unharmed: an aligned view of the same buffer works
+    fv.fv_execute(p.handle, buf[:n])
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(buf[:n]).all())
+    p.close()
