@@ -1,22 +1,28 @@
 // Gather spreading of FP32 two-dimensional grids through a shared-memory ring (Section 2.2, step 1).
 //
-// A CTA owns a 32 x 16 tile at a time (4 x 2 blocks of 8 x 8 cells): eight consumer warps, one per
-// block, and one producer warp.  CTAs are persistent (three per SM) and take tiles from an atomic
-// ticket.  A tile's candidates are the sources of the bins it maps to (one contiguous range of the sorted
-// sources per bin row); the producer copies them into shared memory in chunks of 128 with bulk
-// asynchronous copies into a three-stage ring (a full and an empty mbarrier per stage, every wait
-// bounded) and runs ahead across tile boundaries, so a tile's first chunks are in flight while the
-// consumers finish the previous one.  Each record already holds the source's kernel values (computed
-// once per slice by the prep kernel), so a consumer warp only selects the chunk's candidates that
-// overlap its block (ballot and prefix count, no shared atomics) and adds them; warps never wait for one
-// another except through the ring.  Every grid cell is stored once, with the x and y prescale of the FFT
-// passes applied.
+// A CTA works on a 32 x 16 tile at a time (4 x 2 blocks of 8 x 8 cells): eight consumer warps, one per
+// block, and one producer warp.  A tile's candidates are the sources of the bins it maps to (one
+// contiguous range of the sorted sources per bin row).  Sources are densest at the rim of the source
+// disk, so a few tiles hold several times the mean count; a work-list kernel (k_ring_items) counts each
+// tile's candidates and splits a tile with more than kRingPart of them into parts of kRingPart, so that
+// the crowded tiles are summed by several CTAs at once.  CTAs are persistent (three per SM) and take
+// work items (the parts first, then whole tiles) from an atomic ticket.  The producer copies an item's
+// candidates into shared memory in chunks of 128 with bulk asynchronous copies into a three-stage ring
+// (a full and an empty mbarrier per stage, every wait bounded) and runs ahead across item boundaries,
+// so an item's first chunks are in flight while the consumers finish the previous one.  Each record
+// already holds the source's kernel values (computed once per slice by the prep kernel), so a consumer
+// warp only selects the chunk's candidates that overlap its block (ballot and prefix count, no shared
+// atomics) and adds them; warps never wait for one another except through the ring.  A part leaves its
+// block sums in a slot, and the last part of a tile to finish a block adds the other parts' sums to its
+// own (a per-block counter, no waiting).  Every grid cell is stored once, with the x and y prescale of
+// the FFT passes applied.
 //
 // The sum of a block's cells is
 //     G(x, y) = sum_j c_j psi_y,j(y) psi_x,j(x)
 // over its candidates j.  Two forms:
 //  * FP32 FMAs (the default): lane (x, y) with x = lane & 7 holds rows y = lane >> 3 and y + 4 of its
-//    column and adds c_j psi_x,j(x) psi_y,j(y) for every candidate, in FP32 with FP32 accumulation;
+//    column and adds c_j psi_x,j(x) psi_y,j(y) for every candidate that reaches those rows (one list per
+//    half of the block), real and imaginary parts by one packed FP32 x 2 FMA, with FP32 accumulation;
 //  * tensor cores (FV_SPREAD_TENSOR, an option): for an 8 x 8 block the sum is the matrix product D = A B
 //    with A[(ri, y)][j] = Re / Im (c_j) psi_y,j(y) (16 x J) and B[j][x] = psi_x,j(x) (J x 8), taken eight
 //    candidates at a time as m16n8k8 TF32 products with the three-term split
