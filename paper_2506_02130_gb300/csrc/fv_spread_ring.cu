@@ -358,10 +358,10 @@ __global__ void __launch_bounds__(kRingThreads, 3) k_spread_ring(const int *__re
                 // A candidate is taken once per half of the block it reaches; lanes outside its footprint
                 // read the zero kernel value at index 8.
                 const unsigned ux = (unsigned)((lane & 7) + 16), uy = (unsigned)((lane >> 3) + 16);
-#pragma unroll 2
+#pragma unroll 4
                 for (int e = 0; e < L; ++e)
                     ring_add<NP>(s_sel[warp][e], s_rec[b], s_cs[b], ux, uy, acc[0]);
-#pragma unroll 2
+#pragma unroll 4
                 for (int e = 0; e < L4; ++e)
                     ring_add<NP>(s_sel[warp][2 * kRingChunk - 1 - e], s_rec[b], s_cs[b], ux, uy + 4u, acc[1]);
             }
