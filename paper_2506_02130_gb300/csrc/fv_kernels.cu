@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(128) k_spread_direct(const double *__restrict_
     G kv[3][16];
     int base[3] = {0, 0, 0};
     const int w = g.w;
-    const G two_over_w = (G)(2.0 / w);
+    const G two_over_w = (G)2 / (G)w;
     for (int i = 0; i < 3; ++i) {
         if (i >= g.d) { kv[i][0] = (G)1; base[i] = 0; continue; }
         double q = st[i] * g.dim[i].qscale;
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(128) k_interp(const cpx<G> *__restrict__ band,
     int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= n_u) return;
     const int w = g.w;
-    const G two_over_w = (G)(2.0 / w);
+    const G two_over_w = (G)2 / (G)w;
     double x[3] = {0.0, 0.0, 0.0};
     G kv[3][16];
     int base[3] = {0, 0, 0};
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(256) k_interp_zdirect(const cpx<G> *__restrict
     const int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (u >= n_u) return;
     const int w = g.w;
-    const G two_over_w = (G)(2.0 / w);
+    const G two_over_w = (G)2 / (G)w;
     const G beta = geom_beta<G>(g);
     double x[3] = {0.0, 0.0, 0.0};
     G fr[3];
@@ -524,7 +524,7 @@ __global__ void __launch_bounds__(256) k_interp_zrow(const cpx<float> *__restric
     const int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (u >= n_u) return;
     const int w = g.w;
-    const float two_over_w = (float)(2.0 / w);
+    const float two_over_w = 2.0f / (float)w;
     const float beta = g.beta_f;
     double x[3] = {0.0, 0.0, 0.0};
     float fr[3];
@@ -632,7 +632,7 @@ __global__ void __launch_bounds__(kIbThreads) k_interp_batch(const cpx<G> *__res
     __shared__ cpx<double> s_post[kIbTargets];
     const long u0 = (long)blockIdx.x * kIbTargets;
     const int w = g.w;
-    const G two_over_w = (G)(2.0 / w), beta = geom_beta<G>(g);
+    const G two_over_w = (G)2 / (G)w, beta = geom_beta<G>(g);
     // --- per-target set-up, one target per thread
     if (threadIdx.x < kIbTargets) {
         const int tl = threadIdx.x;
@@ -793,7 +793,7 @@ __global__ void __launch_bounds__(256) k_interp_warp(const cpx<G> *__restrict__ 
     const long u = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (u >= n_u) return;   // whole warps
     const int w = g.w;
-    const G two_over_w = (G)(2.0 / w), beta = geom_beta<G>(g);
+    const G two_over_w = (G)2 / (G)w, beta = geom_beta<G>(g);
     int m0 = 0, m1 = 0;
     G f0 = (G)0, f1 = (G)0, phr = (G)0;
     if (sizeof(G) == 4 && g.tgt_db) {

@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(kGatherThreads, (GatherMinBlocks<G, NP, NZ>::v
             mbar_init1(&s_bar[1]);
         }
     }
-    const G two_over_w = (G)(2.0 / w), beta = geom_beta<G>(g);
+    const G two_over_w = (G)2 / (G)w, beta = geom_beta<G>(g);
     // floor(v / w) for v < kGatherChunk * kWmax by a float product: (v + 0.5) / w lies at least 1/(2w) from
     // an integer, far more than the product's rounding error
     const float inv_w = 1.0f / (float)w;
@@ -872,7 +872,7 @@ __global__ void __launch_bounds__(256, 4) k_spread_scatter(const int *__restrict
     const int bx_hi = top_cell(qx_hi + 1.0, tb.nf1_top[0]) / tb.T[0];
     const int by_lo = top_cell(qy_lo - 1.0, tb.nf1_top[1]) / tb.T[1];
     const int by_hi = top_cell(qy_hi + 1.0, tb.nf1_top[1]) / tb.T[1];
-    const G two_over_w = (G)(2.0 / w), beta = geom_beta<G>(g);
+    const G two_over_w = (G)2 / (G)w, beta = geom_beta<G>(g);
     __syncthreads();
     int k = 0;   // running candidate count across bin rows, dealt to warps round robin
     for (int by = by_lo; by <= by_hi; ++by) {
