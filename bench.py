@@ -1,11 +1,15 @@
 #!/usr/bin/env python
 """Visibility-path benchmark: visibilities/s of the type-3 NUFFT simulator.
 
-Workload: 127-antenna hexagon (8,001 cross baselines, 5 cm height jitter, so
-the transform is 3-D), 64 channels at 100-200 MHz, 10 integrations at 10.7 s,
-69,152 sources (20,000 power-law points + a 49,152-pixel HEALPix diffuse map),
-Gaussian beam; synthetic, seeded.  One step = fv_execute over all 640
-(time, channel) slices = 5,120,640 visibilities.
+Default workload (``--workload hex350``): 350-antenna coplanar hexagon (61,075
+cross baselines), 256 channels at 100-200 MHz x 4 integrations, 886,432
+polarised sources (100,000 power-law points + an nside-256 HEALPix diffuse
+map), 2x2 Jones Airy beam of a 14 m dish, four polarisation products;
+synthetic, seeded.  One step = fv_execute over all 1,024 (time, channel)
+slices = 250,163,200 visibilities.  ``--workload hex127``: 127-antenna
+hexagon with 5 cm height jitter, 64 channels x 10 integrations, 69,152
+unpolarised sources, Gaussian beam (640 slices, 5,120,640 visibilities);
+``batch`` and ``serve``: the ragged-slice batch and the request stream.
 
 Default precision is the mixed path (FP32 spread/FFT/interp, FP64 phases,
 eps 1e-6, accuracy gate 2e-5 relative L2); ``--precision fp64`` runs the FP64
